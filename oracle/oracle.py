@@ -1,0 +1,250 @@
+"""ctypes driver for the plain-C oracle (test infrastructure only).
+
+Every function here marshals numpy arrays into ``qisg_oracle.c`` and back;
+the arithmetic of the method lives in the C file, whose comments cite the
+paper passage each step follows (Sec. 1 Eq. (2)-(3), Sec. 2.1, Sec. 2.1.1,
+Appendix E.1).  ``build()`` compiles it with gcc; nothing of the product
+package is imported.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qisg_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+N_SEED_BITS = 64
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, OpenMP,
+    no floating-point contraction so every product is rounded on its own)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            lib = ctypes.CDLL(path)
+            P = ctypes.c_void_p
+            i32, i64, u64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+            lib.orc_philox4x32_10.argtypes = [P, P, P]
+            lib.orc_philox4x32_10.restype = None
+            lib.orc_ladder_linear.argtypes = [f64, f64, i32, f64, P, P]
+            lib.orc_ladder_linear.restype = None
+            lib.orc_thresholds.argtypes = [i32, P, P, P]
+            lib.orc_thresholds.restype = None
+            lib.orc_pt_bases.argtypes = [i32, P, P, P, P, P, P]
+            lib.orc_pt_bases.restype = None
+            lib.orc_init_couplings.argtypes = [i32, i64, i64, u64, P]
+            lib.orc_init_couplings.restype = None
+            lib.orc_init_spins.argtypes = [i32, i32, i32, i32, i64, i64, u64, P]
+            lib.orc_init_spins.restype = None
+            lib.orc_run.argtypes = [i32, i32, i32, i32, i64, i64, u64, P, P, i32, i32,
+                                    P, P, P, u64, i64, P, P, P, P, P, P, P, i32]
+            lib.orc_run.restype = i32
+            lib.orc_energies.argtypes = [i32, i32, i32, i32, i64, P, P, P, P]
+            lib.orc_energies.restype = None
+            lib.orc_pt_only.argtypes = [i32, i32, i64, u64, P, P, u64, P, P, P]
+            lib.orc_pt_only.restype = None
+            lib.orc_pow_by_squaring.argtypes = [f64, u64]
+            lib.orc_pow_by_squaring.restype = f64
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of one counter (4 x uint32) under one key (2 x uint32)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def ladder_linear(lo: float, hi: float, n: int, gamma: float):
+    k = np.zeros(n, dtype=np.float64)
+    kt = np.zeros(n, dtype=np.float64)
+    _load().orc_ladder_linear(lo, hi, n, gamma, _ptr(k), _ptr(kt))
+    return k, kt
+
+
+def thresholds(k, ktau) -> np.ndarray:
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    kt = np.ascontiguousarray(ktau, dtype=np.float64)
+    T = np.zeros((len(k), 5, 3), dtype=np.uint32)
+    _load().orc_thresholds(len(k), _ptr(k), _ptr(kt), _ptr(T))
+    return T
+
+
+def pt_bases(k, ktau):
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    kt = np.ascontiguousarray(ktau, dtype=np.float64)
+    n = len(k)
+    out = [np.zeros(max(n - 1, 1), dtype=np.float64) for _ in range(4)]
+    _load().orc_pt_bases(n, _ptr(k), _ptr(kt), *[_ptr(o) for o in out])
+    return tuple(o[: max(n - 1, 0)] for o in out)
+
+
+def pow_by_squaring(b: float, e: int) -> float:
+    return _load().orc_pow_by_squaring(float(b), int(e))
+
+
+def init_couplings(L: int, a_lo: int, n_a: int, seed: int) -> np.ndarray:
+    J = np.zeros((n_a, L * L, 2), dtype=np.int8)
+    _load().orc_init_couplings(L, a_lo, n_a, seed, _ptr(J))
+    return J
+
+
+def init_spins(L: int, Ltau: int, n_slots: int, n_rep: int, a_lo: int, n_a: int,
+               seed: int) -> np.ndarray:
+    S = np.zeros((n_a, n_rep, n_slots, L * L * Ltau), dtype=np.int8)
+    _load().orc_init_spins(L, Ltau, n_slots, n_rep, a_lo, n_a, seed, _ptr(S))
+    return S
+
+
+def energies(L: int, Ltau: int, J: np.ndarray, S: np.ndarray):
+    """A, B (by walker) of configurations S[n_a][n_rep][n_slots][N]."""
+    n_a, n_rep, n_slots, _ = S.shape
+    A = np.zeros((n_a, n_rep, n_slots), dtype=np.int64)
+    B = np.zeros_like(A)
+    _load().orc_energies(L, Ltau, n_slots, n_rep, n_a, _ptr(np.ascontiguousarray(J)),
+                         _ptr(np.ascontiguousarray(S)), _ptr(A), _ptr(B))
+    return A, B
+
+
+def pt_only(a: int, seed: int, k, ktau, t: int, walker_at_a: np.ndarray,
+            A_a: np.ndarray, B_a: np.ndarray) -> None:
+    """One PT pass of every replica chain of sample a, energies by walker.
+    ``walker_at_a`` [n_rep][n_slots] is updated in place."""
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    kt = np.ascontiguousarray(ktau, dtype=np.float64)
+    n_rep, n_slots = walker_at_a.shape
+    _load().orc_pt_only(n_slots, n_rep, a, seed, _ptr(k), _ptr(kt), t, _ptr(walker_at_a),
+                        _ptr(np.ascontiguousarray(A_a, dtype=np.int64)),
+                        _ptr(np.ascontiguousarray(B_a, dtype=np.int64)))
+
+
+@dataclass
+class OracleState:
+    """State of a set of samples a_lo .. a_lo+n_a-1 of one instance."""
+    L: int
+    Ltau: int
+    k: np.ndarray
+    ktau: np.ndarray
+    n_rep: int
+    a_lo: int
+    n_a: int
+    seed: int
+    J: np.ndarray            # [n_a][L*L][2] int8
+    S: np.ndarray            # [n_a][n_rep][n_slots][N] int8, by walker
+    walker_at: np.ndarray    # [n_a][n_rep][n_slots] int32
+    t: int = 0               # sweeps done
+    A: np.ndarray = None     # [n_a][n_rep][n_slots] by slot
+    B: np.ndarray = None
+    sumA: np.ndarray = None
+    sumB: np.ndarray = None
+    sumq: np.ndarray = None  # [n_a][n_slots][n_pairs]
+    sumq2: np.ndarray = None
+    n_meas: int = 0
+
+    @property
+    def n_slots(self) -> int:
+        return len(self.k)
+
+    @property
+    def N(self) -> int:
+        return self.L * self.L * self.Ltau
+
+
+def new_state(L, Ltau, k, ktau, n_rep, seed, a_lo=0, n_a=1) -> OracleState:
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    kt = np.ascontiguousarray(ktau, dtype=np.float64)
+    n_slots = len(k)
+    J = init_couplings(L, a_lo, n_a, seed)
+    S = init_spins(L, Ltau, n_slots, n_rep, a_lo, n_a, seed)
+    wa = np.tile(np.arange(n_slots, dtype=np.int32), (n_a, n_rep, 1)).copy()
+    st = OracleState(L, Ltau, k, kt, n_rep, a_lo, n_a, seed, J, S, wa)
+    alloc_obs(st)
+    return st
+
+
+def alloc_obs(st: OracleState) -> None:
+    n_pairs = st.n_rep * (st.n_rep - 1) // 2
+    shp = (st.n_a, st.n_rep, st.n_slots)
+    st.A = np.zeros(shp, dtype=np.int64)
+    st.B = np.zeros(shp, dtype=np.int64)
+    st.sumA = np.zeros(shp, dtype=np.int64)
+    st.sumB = np.zeros(shp, dtype=np.int64)
+    st.sumq = np.zeros((st.n_a, st.n_slots, max(n_pairs, 1)), dtype=np.int64)
+    st.sumq2 = np.zeros_like(st.sumq)
+
+
+def run(st: OracleState, n_sweeps: int, pt_every: int = 1, measure_every: int = 0,
+        n_threads: int = 0) -> OracleState:
+    """Advance the state by n_sweeps sweeps (in place)."""
+    lib = _load()
+    n_meas = ctypes.c_int64(st.n_meas)
+    rc = lib.orc_run(st.L, st.Ltau, st.n_slots, st.n_rep, st.a_lo, st.n_a, st.seed,
+                     _ptr(st.k), _ptr(st.ktau), pt_every, measure_every,
+                     _ptr(st.J), _ptr(st.S), _ptr(st.walker_at), st.t, n_sweeps,
+                     _ptr(st.A), _ptr(st.B), _ptr(st.sumA), _ptr(st.sumB),
+                     _ptr(st.sumq), _ptr(st.sumq2), ctypes.byref(n_meas), n_threads)
+    if rc != 0:
+        raise MemoryError("oracle run failed")
+    st.t += n_sweeps
+    st.n_meas = n_meas.value
+    return st
+
+
+def slot_means(st: OracleState, n_samples_total: int | None = None):
+    """FP64 per-slot means over (sample, replica, measurement), summed in the
+    fixed order sample, replica (slot-major output): e_s = A/(2N),
+    e_t = B/N and the mean squared overlap q^2/N^2 over replica pairs."""
+    n_pairs = st.n_rep * (st.n_rep - 1) // 2
+    N = float(st.N)
+    m = float(st.n_meas)
+    e_s = np.zeros(st.n_slots)
+    e_t = np.zeros(st.n_slots)
+    q2 = np.zeros(st.n_slots)
+    for s in range(st.n_slots):
+        sa = 0.0
+        sb = 0.0
+        for a in range(st.n_a):
+            for r in range(st.n_rep):
+                sa += float(st.sumA[a, r, s])
+                sb += float(st.sumB[a, r, s])
+        e_s[s] = sa / (m * st.n_a * st.n_rep * 2.0 * N)
+        e_t[s] = sb / (m * st.n_a * st.n_rep * N)
+        sq = 0.0
+        for a in range(st.n_a):
+            for p in range(n_pairs):
+                sq += float(st.sumq2[a, s, p])
+        q2[s] = sq / (m * st.n_a * max(n_pairs, 1) * N * N)
+    return e_s, e_t, q2

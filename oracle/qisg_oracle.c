@@ -1,0 +1,429 @@
+/*
+ * qisg_oracle.c -- plain, slow CPU oracle for the MCQSG hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library may link, load
+ * or call this file; only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark use it.  It shares no code, header or table with the CUDA
+ * path: it rebuilds every table it needs from the formulas below.
+ *
+ * What it computes (the paper's notation):
+ *   - the Trotter-Suzuki classical model of Eq. (2)-(3) (Sec. 1): spins
+ *     S_{x,tau} = +-1 on an L x L x L_tau prism, periodic in x, y and tau,
+ *     with spatial bonds k*J_xy (J = +-1) and imaginary-time bonds k_tau.
+ *     The paper's single coupling k is generalised to a (k, k_tau) pair per
+ *     ladder slot, exp(-2 k_tau) = tanh(k Gamma); k_tau = k recovers the
+ *     equal-coupling relation of Sec. 1.
+ *   - checkerboard Metropolis (Sec. 2.1): red sites (x+y+tau even), then
+ *     blue; the Metropolis factor is precomputed for every local energy
+ *     class (Sec. 2.1) as a uint32 threshold built in FP64.
+ *   - parallel tempering (Sec. 2.1): adjacent slots s, s+1 exchange their
+ *     configurations with probability min(1, exp(Dk*DA + Dk_tau*DB)).
+ *   - observables: integer energies and the replica overlap (Appendix E.1).
+ *   - Philox4x32-10 (Sec. 2.1.1), the counter-based generator of Salmon et
+ *     al. (SC'11), written here from its published definition.
+ *
+ * Storage is one int8 spin per (sample, replica, walker, site); every loop
+ * runs in plain order.  Floating point is IEEE double with no contraction
+ * (compile with -ffp-contract=off).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Philox counter domains: one per kind of draw. */
+enum { ORC_DOM_J = 1, ORC_DOM_INIT = 2, ORC_DOM_SWEEP = 3, ORC_DOM_PT = 4 };
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Sec. 2.1.1; Salmon, Moraes, Dror, Shaw, SC'11).            */
+/* One round: (hi0,lo0) = M0*c0, (hi1,lo1) = M1*c2,                          */
+/*   c' = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); the key is bumped by the  */
+/*   Weyl constants between rounds.                                          */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    int round;
+    for (round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint32_t philox_word(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                            uint64_t seed, int which)
+{
+    uint32_t ctr[4], key[2], out[4];
+    ctr[0] = c0; ctr[1] = c1; ctr[2] = c2; ctr[3] = c3;
+    key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32);
+    orc_philox4x32_10(ctr, key, out);
+    return out[which];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ladder and tables (host FP64).                                           */
+/* ------------------------------------------------------------------------ */
+
+/* k_s linear in [lo, hi] (both ends included), k_tau from exp(-2 k_tau) =
+ * tanh(k Gamma) (Sec. 1, generalised to a separate imaginary-time coupling). */
+void orc_ladder_linear(double lo, double hi, int n, double gamma, double *k, double *ktau)
+{
+    int s;
+    for (s = 0; s < n; ++s) {
+        k[s] = (n == 1) ? lo : lo + (hi - lo) * (double)s / (double)(n - 1);
+        ktau[s] = -0.5 * log(tanh(k[s] * gamma));
+    }
+}
+
+/* Log Metropolis factor of flipping a spin with u_s unsatisfied spatial bonds
+ * (of 4) and u_t unsatisfied imaginary-time bonds (of 2): flipping turns
+ * satisfied bonds into unsatisfied ones and back, so the weight
+ * exp(k*A + k_tau*B) changes by exp(-4k(2-u_s) - 4k_tau(1-u_t)). */
+static double log_metropolis_factor(double k, double ktau, int us, int ut)
+{
+    double spatial = (double)(4 * (2 - us)) * k;     /* exact: 8k, 4k, 0, ... */
+    double temporal = (double)(4 * (1 - ut)) * ktau; /* exact: 4k_tau, 0, ... */
+    return -spatial - temporal;
+}
+
+/* T[s][u_s][u_t]: flip iff T == 0xFFFFFFFF or R < T, R a uniform uint32.
+ * p = min(1, e^Delta); T = 0xFFFFFFFF when p >= 1, else
+ * min(0xFFFFFFFE, floor(p * 2^32)), so P(flip) lies in [p - 2^-32, p].     */
+void orc_thresholds(int n_slots, const double *k, const double *ktau, uint32_t *T)
+{
+    int s, us, ut;
+    for (s = 0; s < n_slots; ++s)
+        for (us = 0; us <= 4; ++us)
+            for (ut = 0; ut <= 2; ++ut) {
+                double p = exp(log_metropolis_factor(k[s], ktau[s], us, ut));
+                uint32_t t;
+                if (p >= 1.0) {
+                    t = 0xFFFFFFFFu;
+                } else {
+                    double f = floor(ldexp(p, 32));
+                    t = (f >= 4294967294.0) ? 0xFFFFFFFEu : (uint32_t)f;
+                }
+                T[(s * 5 + us) * 3 + ut] = t;
+            }
+}
+
+/* PT bases for the pair (s, s+1): alpha+- = exp(+-(k_s - k_{s+1})),
+ * beta+- = exp(+-(k_tau,s - k_tau,s+1)). */
+void orc_pt_bases(int n_slots, const double *k, const double *ktau,
+                  double *ap, double *am, double *bp, double *bm)
+{
+    int s;
+    for (s = 0; s + 1 < n_slots; ++s) {
+        double dk = k[s] - k[s + 1];
+        double dkt = ktau[s] - ktau[s + 1];
+        ap[s] = exp(dk);
+        am[s] = exp(-dk);
+        bp[s] = exp(dkt);
+        bm[s] = exp(-dkt);
+    }
+}
+
+/* b^e by right-to-left binary powering, round-to-nearest multiplies only. */
+static double pow_by_squaring(double b, uint64_t e)
+{
+    double res = 1.0;
+    while (e) {
+        if (e & 1u) res = res * b;
+        b = b * b;
+        e >>= 1;
+    }
+    return res;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Disorder and start state (the paper keeps separate seeds for J, the      */
+/* initial configuration and the Monte Carlo stream; here they are Philox    */
+/* domains under one seed).                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* J[a][x + L*y][dir], dir 0 = bond to (x+1, y), dir 1 = bond to (x, y+1). */
+void orc_init_couplings(int L, int64_t a_lo, int64_t n_a, uint64_t seed, int8_t *J)
+{
+    int64_t ai;
+    int i, dir;
+    for (ai = 0; ai < n_a; ++ai)
+        for (i = 0; i < L * L; ++i)
+            for (dir = 0; dir < 2; ++dir) {
+                uint32_t x0 = philox_word((uint32_t)i, (uint32_t)dir, (uint32_t)(a_lo + ai),
+                                          (uint32_t)ORC_DOM_J << 28, seed, 0);
+                J[(ai * L * L + i) * 2 + dir] = (x0 & 1u) ? 1 : -1;
+            }
+}
+
+/* S[a][r][w][site]; walker w starts at slot w. */
+void orc_init_spins(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64_t n_a,
+                    uint64_t seed, int8_t *S)
+{
+    int64_t N = (int64_t)L * L * Ltau, ai, site;
+    int r, w;
+    for (ai = 0; ai < n_a; ++ai)
+        for (r = 0; r < n_rep; ++r)
+            for (w = 0; w < n_slots; ++w)
+                for (site = 0; site < N; ++site) {
+                    uint32_t x0 = philox_word((uint32_t)site, (uint32_t)w, (uint32_t)(a_lo + ai),
+                                              ((uint32_t)ORC_DOM_INIT << 28) | (uint32_t)r, seed, 0);
+                    S[((ai * n_rep + r) * n_slots + w) * N + site] = (x0 & 1u) ? 1 : -1;
+                }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The Markov chain.                                                         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int L, Ltau, n_slots, n_rep;
+    uint64_t seed;
+    const uint32_t *T;                  /* [n_slots][5][3] */
+    const double *ap, *am, *bp, *bm;    /* [n_slots-1] */
+} orc_model;
+
+/* A = sum over spatial bonds of J S S, B = sum over imaginary-time bonds of
+ * S S (Eq. (3) splits -E into these two sums). */
+static void energies_of(const orc_model *m, const int8_t *J, const int8_t *S,
+                        int64_t *A, int64_t *B)
+{
+    int L = m->L, Lt = m->Ltau, x, y, t;
+    int64_t a = 0, b = 0;
+    for (t = 0; t < Lt; ++t)
+        for (y = 0; y < L; ++y)
+            for (x = 0; x < L; ++x) {
+                int64_t i = x + (int64_t)L * y + (int64_t)L * L * t;
+                int64_t ix = ((x + 1) % L) + (int64_t)L * y + (int64_t)L * L * t;
+                int64_t iy = x + (int64_t)L * ((y + 1) % L) + (int64_t)L * L * t;
+                int64_t it = x + (int64_t)L * y + (int64_t)L * L * ((t + 1) % Lt);
+                int i2 = x + L * y;
+                a += J[i2 * 2 + 0] * S[i] * S[ix];
+                a += J[i2 * 2 + 1] * S[i] * S[iy];
+                b += S[i] * S[it];
+            }
+    *A = a;
+    *B = b;
+}
+
+/* One half sweep of one sample a: every site of the given colour, every
+ * replica r and slot s, for the walker w currently at slot s. */
+static void half_sweep(const orc_model *m, int64_t a, const int8_t *J, int8_t *S_a,
+                       const int32_t *walker_at_a, uint64_t t, int colour)
+{
+    int L = m->L, Lt = m->Ltau, n_slots = m->n_slots, n_rep = m->n_rep;
+    int64_t N = (int64_t)L * L * Lt;
+    int x, y, tau, r, s;
+    for (tau = 0; tau < Lt; ++tau)
+        for (y = 0; y < L; ++y)
+            for (x = 0; x < L; ++x) {
+                int xp, xm, yp, ym, tp, tm, i2;
+                int64_t site;
+                if (((x + y + tau) & 1) != colour) continue;
+                site = x + (int64_t)L * y + (int64_t)L * L * tau;
+                xp = (x + 1) % L; xm = (x + L - 1) % L;
+                yp = (y + 1) % L; ym = (y + L - 1) % L;
+                tp = (tau + 1) % Lt; tm = (tau + Lt - 1) % Lt;
+                i2 = x + L * y;
+                for (r = 0; r < n_rep; ++r)
+                    for (s = 0; s < n_slots; ++s) {
+                        int w = walker_at_a[r * n_slots + s];
+                        int8_t *Sw = S_a + ((int64_t)r * n_slots + w) * N;
+                        int si = Sw[site];
+                        int us = 0, ut = 0;
+                        uint32_t thr, R;
+                        us += (J[i2 * 2 + 0] * si * Sw[xp + L * y + (int64_t)L * L * tau] == -1);
+                        us += (J[(xm + L * y) * 2 + 0] * si * Sw[xm + L * y + (int64_t)L * L * tau] == -1);
+                        us += (J[i2 * 2 + 1] * si * Sw[x + L * yp + (int64_t)L * L * tau] == -1);
+                        us += (J[(x + L * ym) * 2 + 1] * si * Sw[x + L * ym + (int64_t)L * L * tau] == -1);
+                        ut += (si * Sw[x + L * y + (int64_t)L * L * tp] == -1);
+                        ut += (si * Sw[x + L * y + (int64_t)L * L * tm] == -1);
+                        thr = m->T[(s * 5 + us) * 3 + ut];
+                        R = philox_word((uint32_t)site, (uint32_t)t,
+                                        (uint32_t)s | ((uint32_t)(r >> 2) << 16),
+                                        ((uint32_t)ORC_DOM_SWEEP << 28) | (uint32_t)(a >> 6),
+                                        m->seed, r & 3);
+                        if (thr == 0xFFFFFFFFu || R < thr) Sw[site] = (int8_t)(-si);
+                    }
+            }
+}
+
+/* One PT pass of chain (a, r) after sweep t: pairs (s, s+1) in increasing s.
+ * Walker X sits at s, Y at s+1; the exchange is accepted with probability
+ * min(1, exp((k_s - k_{s+1})(A_Y - A_X) + (kt_s - kt_{s+1})(B_Y - B_X))),
+ * evaluated as a product of powers of the precomputed bases. */
+static void pt_pass(const orc_model *m, int64_t a, int r, uint64_t t,
+                    int32_t *walker_at_ar, const int64_t *A_ar, const int64_t *B_ar)
+{
+    int s;
+    for (s = 0; s + 1 < m->n_slots; ++s) {
+        int X = walker_at_ar[s], Y = walker_at_ar[s + 1];
+        int64_t dm = A_ar[Y] - A_ar[X];
+        int64_t dn = B_ar[Y] - B_ar[X];
+        double fa = pow_by_squaring(dm >= 0 ? m->ap[s] : m->am[s],
+                                    (uint64_t)(dm >= 0 ? dm : -dm));
+        double fb = pow_by_squaring(dn >= 0 ? m->bp[s] : m->bm[s],
+                                    (uint64_t)(dn >= 0 ? dn : -dn));
+        double P = fa * fb;
+        uint32_t x = philox_word((uint32_t)s, (uint32_t)t, (uint32_t)a,
+                                 ((uint32_t)ORC_DOM_PT << 28) | (uint32_t)(r >> 2), m->seed, r & 3);
+        double u = ldexp((double)x, -32);
+        if (u < P) {
+            walker_at_ar[s] = Y;
+            walker_at_ar[s + 1] = X;
+        }
+    }
+}
+
+/*
+ * Run n_sweeps sweeps (sweep indices t0 .. t0+n_sweeps-1) for samples
+ * a_lo .. a_lo+n_a-1.  Per sweep t: red half sweep, blue half sweep, then a
+ * PT pass of every chain when pt_every > 0 and (t+1) % pt_every == 0, then
+ * a measurement when measure_every > 0 and (t+1) % measure_every == 0.
+ *
+ * Arrays (per sample offset ai = a - a_lo):
+ *   J         [n_a][L*L][2]                       int8 +-1
+ *   S         [n_a][n_rep][n_slots walkers][N]    int8 +-1, in/out
+ *   walker_at [n_a][n_rep][n_slots]               in/out
+ *   A, B      [n_a][n_rep][n_slots] by slot       out: energies after the run
+ *   sumA,sumB [n_a][n_rep][n_slots] by slot       in/out: measurement sums
+ *   sumq,sumq2[n_a][n_slots][n_rep(n_rep-1)/2]    in/out: overlap sums
+ *   n_meas                                        in/out: measurements taken
+ * Observables may be NULL when measure_every == 0.
+ */
+int orc_run(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64_t n_a, uint64_t seed,
+            const double *k, const double *ktau, int pt_every, int measure_every,
+            const int8_t *J, int8_t *S, int32_t *walker_at, uint64_t t0, int64_t n_sweeps,
+            int64_t *A, int64_t *B, int64_t *sumA, int64_t *sumB, int64_t *sumq, int64_t *sumq2,
+            int64_t *n_meas, int n_threads)
+{
+    orc_model m;
+    uint32_t *T;
+    double *ap, *am, *bp, *bm;
+    int64_t N = (int64_t)L * L * Ltau;
+    int n_pairs = n_rep * (n_rep - 1) / 2;
+    int64_t ai;
+    int64_t meas_total = 0;
+
+    T = (uint32_t *)malloc(sizeof(uint32_t) * 15 * (size_t)n_slots);
+    ap = (double *)malloc(sizeof(double) * 4 * (size_t)(n_slots > 1 ? n_slots : 2));
+    if (!T || !ap) { free(T); free(ap); return -1; }
+    am = ap + n_slots; bp = am + n_slots; bm = bp + n_slots;
+    orc_thresholds(n_slots, k, ktau, T);
+    orc_pt_bases(n_slots, k, ktau, ap, am, bp, bm);
+    m.L = L; m.Ltau = Ltau; m.n_slots = n_slots; m.n_rep = n_rep; m.seed = seed;
+    m.T = T; m.ap = ap; m.am = am; m.bp = bp; m.bm = bm;
+
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : meas_total)
+#endif
+    for (ai = 0; ai < n_a; ++ai) {
+        int64_t a = a_lo + ai;
+        const int8_t *Ja = J + ai * L * L * 2;
+        int8_t *Sa = S + ai * n_rep * n_slots * N;
+        int32_t *wa = walker_at + ai * n_rep * n_slots;
+        int64_t *Aw = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)n_rep * n_slots);
+        int64_t *Bw = Aw + n_rep * n_slots;   /* by walker */
+        int64_t it;
+        int r, s, w;
+        int64_t local_meas = 0;
+        for (it = 0; it < n_sweeps; ++it) {
+            uint64_t t = t0 + (uint64_t)it;
+            half_sweep(&m, a, Ja, Sa, wa, t, 0);
+            half_sweep(&m, a, Ja, Sa, wa, t, 1);
+            for (r = 0; r < n_rep; ++r)
+                for (w = 0; w < n_slots; ++w)
+                    energies_of(&m, Ja, Sa + ((int64_t)r * n_slots + w) * N,
+                                &Aw[r * n_slots + w], &Bw[r * n_slots + w]);
+            if (pt_every > 0 && (t + 1) % (uint64_t)pt_every == 0)
+                for (r = 0; r < n_rep; ++r)
+                    pt_pass(&m, a, r, t, wa + r * n_slots, Aw + r * n_slots, Bw + r * n_slots);
+            if (measure_every > 0 && (t + 1) % (uint64_t)measure_every == 0) {
+                int r1, r2, p;
+                for (r = 0; r < n_rep; ++r)
+                    for (s = 0; s < n_slots; ++s) {
+                        w = wa[r * n_slots + s];
+                        sumA[(ai * n_rep + r) * n_slots + s] += Aw[r * n_slots + w];
+                        sumB[(ai * n_rep + r) * n_slots + s] += Bw[r * n_slots + w];
+                    }
+                /* overlap q = sum_i S^{r1}_i S^{r2}_i of the configurations at
+                 * slot s of replicas r1 < r2 (Appendix E.1, same sample) */
+                for (s = 0; s < n_slots; ++s) {
+                    p = 0;
+                    for (r1 = 0; r1 < n_rep; ++r1)
+                        for (r2 = r1 + 1; r2 < n_rep; ++r2, ++p) {
+                            const int8_t *S1 = Sa + ((int64_t)r1 * n_slots + wa[r1 * n_slots + s]) * N;
+                            const int8_t *S2 = Sa + ((int64_t)r2 * n_slots + wa[r2 * n_slots + s]) * N;
+                            int64_t q = 0, i;
+                            for (i = 0; i < N; ++i) q += S1[i] * S2[i];
+                            sumq[(ai * n_slots + s) * n_pairs + p] += q;
+                            sumq2[(ai * n_slots + s) * n_pairs + p] += q * q;
+                        }
+                }
+                ++local_meas;
+            }
+        }
+        /* energies of the final state, reported by slot */
+        for (r = 0; r < n_rep; ++r)
+            for (w = 0; w < n_slots; ++w)
+                energies_of(&m, Ja, Sa + ((int64_t)r * n_slots + w) * N,
+                            &Aw[r * n_slots + w], &Bw[r * n_slots + w]);
+        for (r = 0; r < n_rep; ++r)
+            for (s = 0; s < n_slots; ++s) {
+                w = wa[r * n_slots + s];
+                A[(ai * n_rep + r) * n_slots + s] = Aw[r * n_slots + w];
+                B[(ai * n_rep + r) * n_slots + s] = Bw[r * n_slots + w];
+            }
+        if (ai == 0) meas_total += local_meas;
+        free(Aw);
+    }
+    if (n_meas) *n_meas += meas_total;
+    free(T);
+    free(ap);
+    return 0;
+}
+
+/* Energies A, B (by walker) of given configurations: [n_a][n_rep][n_slots]. */
+void orc_energies(int L, int Ltau, int n_slots, int n_rep, int64_t n_a, const int8_t *J,
+                  const int8_t *S, int64_t *A, int64_t *B)
+{
+    orc_model m;
+    int64_t N = (int64_t)L * L * Ltau, c;
+    m.L = L; m.Ltau = Ltau; m.n_slots = n_slots; m.n_rep = n_rep;
+    for (c = 0; c < n_a * n_rep * n_slots; ++c)
+        energies_of(&m, J + (c / (n_rep * n_slots)) * L * L * 2, S + c * N, &A[c], &B[c]);
+}
+
+/* One PT pass with given energies by walker (for the PT-only tests). */
+void orc_pt_only(int n_slots, int n_rep, int64_t a, uint64_t seed, const double *k,
+                 const double *ktau, uint64_t t, int32_t *walker_at_a,
+                 const int64_t *A_a, const int64_t *B_a)
+{
+    orc_model m;
+    double *ap = (double *)malloc(sizeof(double) * 4 * (size_t)(n_slots > 1 ? n_slots : 2));
+    int r;
+    m.n_slots = n_slots; m.n_rep = n_rep; m.seed = seed;
+    m.ap = ap; m.am = ap + n_slots; m.bp = ap + 2 * n_slots; m.bm = ap + 3 * n_slots;
+    orc_pt_bases(n_slots, k, ktau, ap, ap + n_slots, ap + 2 * n_slots, ap + 3 * n_slots);
+    for (r = 0; r < n_rep; ++r)
+        pt_pass(&m, a, r, t, walker_at_a + r * n_slots, A_a + r * n_slots, B_a + r * n_slots);
+    free(ap);
+}
+
+double orc_pow_by_squaring(double b, uint64_t e) { return pow_by_squaring(b, e); }

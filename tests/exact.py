@@ -1,0 +1,72 @@
+"""Exact results for tiny lattices, written from the definitions only.
+
+These are the pins the oracle is checked against; nothing here calls the
+oracle or the CUDA library.
+
+* ``enumerate_AB``: brute-force Boltzmann averages of A = sum_spatial J S S
+  and B = sum_tau S S over all 2^N configurations of an L x L x L_tau prism
+  (periodic), weight exp(k A + k_tau B) -- Eq. (2)-(3) with a separate
+  imaginary-time coupling.
+* ``chain_B``: closed form for k = 0, where every spatial site carries an
+  independent periodic Ising chain of L_tau spins with coupling k_tau.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _all_configs(n: int) -> np.ndarray:
+    idx = np.arange(1 << n, dtype=np.int64)
+    bits = (idx[:, None] >> np.arange(n, dtype=np.int64)[None, :]) & 1
+    return (1 - 2 * bits).astype(np.int8)       # bit 1 -> spin -1
+
+
+def AB_of_configs(S: np.ndarray, J: np.ndarray, L: int, Ltau: int):
+    """A and B of a batch of configurations S[m][N] (site = x + L y + L^2 tau);
+    J[L*L][2] with dir 0 = +x, dir 1 = +y."""
+    m = S.shape[0]
+    V = S.reshape(m, Ltau, L, L).astype(np.int64)            # [m][tau][y][x]
+    Jx = J[:, 0].reshape(L, L).astype(np.int64)              # [y][x]
+    Jy = J[:, 1].reshape(L, L).astype(np.int64)
+    A = (Jx[None, None] * V * np.roll(V, -1, axis=3)).sum(axis=(1, 2, 3))
+    A += (Jy[None, None] * V * np.roll(V, -1, axis=2)).sum(axis=(1, 2, 3))
+    B = (V * np.roll(V, -1, axis=1)).sum(axis=(1, 2, 3))
+    return A, B
+
+
+def enumerate_AB(J: np.ndarray, L: int, Ltau: int, k: float, ktau: float):
+    """Exact <A>, <B>, <A^2>, <B^2> at (k, k_tau) by enumeration (N <= 20)."""
+    n = L * L * Ltau
+    assert n <= 20
+    S = _all_configs(n)
+    A, B = AB_of_configs(S, J, L, Ltau)
+    logw = k * A.astype(np.float64) + ktau * B.astype(np.float64)
+    logw -= logw.max()
+    w = np.exp(logw)
+    Z = w.sum()
+    return ((w * A).sum() / Z, (w * B).sum() / Z,
+            (w * A * A).sum() / Z, (w * B * B).sum() / Z)
+
+
+def layer_A(J: np.ndarray, L: int, k: float) -> float:
+    """Exact <A_layer> of one 2D +-J layer (k_tau = 0), by enumeration."""
+    n = L * L
+    S = _all_configs(n)
+    A, _ = AB_of_configs(S, J, L, 1)
+    # with L_tau = 1 the tau-roll pairs a spin with itself; only A is used
+    logw = k * A.astype(np.float64)
+    logw -= logw.max()
+    w = np.exp(logw)
+    return float((w * A).sum() / w.sum())
+
+
+def chain_B(L: int, Ltau: int, ktau: float) -> float:
+    """<B> for k = 0: L^2 independent periodic chains of Ltau spins,
+    Z = (2 cosh K)^n + (2 sinh K)^n, <sum S S_{+1}> = d ln Z / dK."""
+    n = Ltau
+    c, s = np.cosh(ktau), np.sinh(ktau)
+    # divide numerator and denominator by (2 cosh K)^n
+    t = np.tanh(ktau)
+    num = n * (s / c + t ** (n - 1))
+    den = 1.0 + t ** n
+    return float(L * L * num / den)
