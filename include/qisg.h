@@ -1,0 +1,212 @@
+/*
+ * qisg.h -- C ABI of the GB300 library for the MCQSG hot path: checkerboard
+ * Metropolis sweeps plus parallel tempering for the 2D +-J quantum Ising spin
+ * glass in Trotter-Suzuki form (an L x L x L_tau classical Ising prism).
+ *
+ * Paper: "The QISG suite: high-performance codes for studying Quantum Ising
+ * Spin Glasses" (Bernaschi, Gonzalez-Adalid Pemartin, Martin-Mayor, Parisi).
+ *   Sec. 1, Eq. (2)-(3)   the classical model: p(S) ~ exp(-k E(S)), E sums the
+ *                         spatial bonds J S S and the imaginary-time bonds S S.
+ *                         Here each ladder slot carries its own (k, k_tau)
+ *                         with exp(-2 k_tau) = tanh(k Gamma); k_tau = k is the
+ *                         paper's equal-coupling case.
+ *   Sec. 2.1              red/blue checkerboard Metropolis with precomputed
+ *                         Metropolis factors; multispin coding; parallel
+ *                         tempering with P = min(1, exp((k_a-k_b)(E_a-E_b))).
+ *   Sec. 2.1.1            counter-based Philox4x32-10 random numbers, one
+ *                         counter per clone, reproducible for any work split.
+ *   Appendix A            EMCS = ptfr sweeps + one PT update; an online energy
+ *                         measurement every mesfr EMCS.
+ *   Appendix E.1          the replica overlap q.
+ *
+ * Conventions (all entry points):
+ *   - Return 0 (QISG_OK) or a negative QISG_E* code; qisg_last_error() gives
+ *     a message for the calling thread's most recent failure.
+ *   - Host arrays are owned by the caller; sizes are stated per call.  The
+ *     handle owns all device memory it allocates.
+ *   - Work is stream-ordered on opts.cuda_stream (a cudaStream_t; NULL means
+ *     the legacy default stream).  Getters synchronise that stream.
+ *   - A handle must not be used from two threads at once.
+ *   - Sites are indexed site = x + L*y + L*L*tau; colour (x+y+tau) mod 2;
+ *     red (0) is updated first.  Samples a, replicas r, ladder slots s,
+ *     walkers w (walker w starts at slot w).
+ *   - Results depend only on (L, L_tau, ladder, n_replicas, n_samples, seed,
+ *     sweep count, pt_every), never on the packing, word width or schedule.
+ */
+#ifndef QISG_H
+#define QISG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QISG_OK        0
+#define QISG_EINVAL   (-1)   /* bad argument (see each call)                  */
+#define QISG_ENOMEM   (-2)   /* device allocation failed or over mem_budget   */
+#define QISG_ECUDA    (-3)   /* a CUDA call failed                            */
+#define QISG_ETIMEOUT (-4)   /* a bounded device wait expired                 */
+#define QISG_ECORRUPT (-5)   /* a state buffer failed its consistency check   */
+#define QISG_ESTATE   (-6)   /* call not valid in the current state           */
+
+/* Packings of independent systems into one word (Sec. 2.1, multispin coding).
+ * LANES: a word holds the n_replicas x n_slots systems of ONE sample (lane =
+ *   replica-in-word * n_slots + walker); every lane draws its own random
+ *   number; PT swaps the slot labels, not the spins (Sec. 2.1).
+ * SAMPLES: a word holds 32 or 64 SAMPLES at one (replica, slot); the draw of
+ *   a (replica, slot, site, sweep) is shared by the 64 samples of a sample
+ *   block, as in Ito-Kanada's multi-sample coding (Sec. 2.1.1); PT moves the
+ *   spin bits of each sample between slot words.                           */
+#define QISG_LAYOUT_AUTO    0
+#define QISG_LAYOUT_LANES   1
+#define QISG_LAYOUT_SAMPLES 2
+
+typedef struct qisg_handle qisg_handle;
+
+/* One ladder slot: spatial coupling k and imaginary-time coupling k_tau. */
+typedef struct {
+    double k;
+    double k_tau;
+} qisg_slot;
+
+typedef struct {
+    int word_bits;          /* 32 | 64; 0 = choose                                */
+    void *cuda_stream;      /* cudaStream_t, NULL = legacy default stream          */
+    size_t mem_budget;      /* bytes of device memory the handle may take; 0 = any */
+    int pt_every;           /* sweeps per PT pass (the paper's ptfr); 0 = never    */
+    int measure_every;      /* sweeps per measurement (mesfr); 0 = never           */
+    int layout;             /* QISG_LAYOUT_*                                       */
+    int per_sample_launch;  /* LANES only: 1 = one kernel launch per sample per
+                               half sweep (the plain per-instance form)            */
+} qisg_opts;
+
+/* Fill *opts with defaults: word_bits 0, NULL stream, no budget, pt_every 1,
+ * measure_every 0, layout AUTO, per_sample_launch 0. */
+void qisg_opts_default(qisg_opts *opts);
+
+/* Linear ladder (k_s = lo + (hi-lo) s/(n-1), both ends included; k_s = lo for
+ * n = 1) with k_tau,s = -1/2 log tanh(k_s Gamma), the separate-coupling form
+ * of Sec. 1's relation between k and Gamma.  out: caller array of n slots.
+ * EINVAL: n < 1, gamma <= 0, lo <= 0 or a non-finite k_tau. */
+int qisg_ladder_linear(double lo, double hi, int n, double gamma, qisg_slot *out);
+
+/* Create an instance: n_samples disorder samples (J = +-1, p = 1/2), each
+ * with n_replicas independent replicas of an n_slots PT ladder, on an
+ * L x L x L_tau prism periodic in all three directions (Sec. 1, Sec. 2.1).
+ * Couplings and the start configuration are drawn from Philox under `seed`
+ * (the paper's separate J / start / Monte Carlo seeds, Appendix A, become
+ * counter domains).  Walker w starts at slot w.  The uint32 Metropolis table
+ * and the PT bases are built once here, on the host, in FP64 (Sec. 2.1:
+ * Metropolis factors precomputed for every possible value).
+ *   ladder: host array of n_slots slots (copied).  opts may be NULL.
+ * EINVAL: L odd or < 2; L_tau odd or < 2; n_slots < 1; n_replicas < 1;
+ *   n_samples < 1; a k or k_tau negative or non-finite; a packing that cannot
+ *   hold the systems (LANES needs n_slots <= word bits).
+ * ENOMEM: allocation failed or the state exceeds opts->mem_budget.        */
+int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, int n_slots,
+                int n_replicas, int64_t n_samples, uint64_t seed, const qisg_opts *opts);
+
+/* Run n_sweeps sweeps.  Sweep t (0-based count of sweeps done before it):
+ * red half sweep, blue half sweep (the blue pass also counts the integer
+ * energies of every system), then a PT pass when pt_every > 0 and
+ * (t+1) % pt_every == 0, then a measurement when measure_every > 0 and
+ * (t+1) % measure_every == 0 (Appendix A's EMCS cadence).  Asynchronous.
+ * EINVAL: n_sweeps < 0.                                                     */
+int qisg_sweep(qisg_handle *h, int64_t n_sweeps);
+
+/* One explicit PT pass on the current configurations (Sec. 2.1), drawing the
+ * numbers a PT pass after the last completed sweep would draw, so that
+ * pt_every = 0 plus one qisg_pt_swap per sweep reproduces pt_every = 1.
+ * ESTATE: no sweep has run yet.                                             */
+int qisg_pt_swap(qisg_handle *h);
+
+/* Integer energies of the configurations now at each slot, by slot:
+ * A = sum over spatial bonds of J S S, B = sum over tau bonds of S S
+ * (Eq. (3): -E = A + B at k_tau = k).  A, B: host int64
+ * [n_samples][n_replicas][n_slots].  Synchronises.                          */
+int qisg_energies(qisg_handle *h, int64_t *A, int64_t *B);
+
+/* Replica overlaps of the configurations now at each slot (Appendix E.1):
+ * q[a][s][p] = sum_i S^{r1}_i S^{r2}_i over pairs p = (r1 < r2) in
+ * lexicographic order.  q: host int64 [n_samples][n_slots][n_pairs],
+ * n_pairs = n_replicas (n_replicas-1) / 2.  Synchronises.                  */
+int qisg_overlaps(qisg_handle *h, int64_t *q);
+
+/* PT permutation: walker_at[a][r][s] = walker now at slot s.  Host int32
+ * [n_samples][n_replicas][n_slots].  Synchronises.                        */
+int qisg_permutation(qisg_handle *h, int32_t *walker_at);
+
+/* Unpacked +-1 spins of samples a_lo .. a_lo+n_a-1, by walker:
+ * S[a - a_lo][r][w][site], host int8, n_a*n_replicas*n_slots*L*L*L_tau
+ * bytes.  EINVAL: the sample range is outside [0, n_samples).  Synchronises. */
+int qisg_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S);
+
+/* Couplings of samples a_lo .. a_lo+n_a-1: J[a - a_lo][x + L*y][dir], int8
+ * +-1, dir 0 = bond to (x+1, y), dir 1 = bond to (x, y+1). */
+int qisg_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J);
+
+/* Replace the couplings of every sample (host int8 [n_samples][L*L][2],
+ * entries +-1; EINVAL otherwise).  Energies are recomputed. */
+int qisg_set_couplings(qisg_handle *h, const int8_t *J);
+
+/* Replace the state: spins by walker (host int8 [n_samples][n_replicas]
+ * [n_slots][N], entries +-1), the permutation (host int32
+ * [n_samples][n_replicas][n_slots], each row a permutation of 0..n_slots-1)
+ * and the sweep counter.  Measurement sums are cleared; energies are
+ * recomputed.  Because every draw is a function of the counters, resuming
+ * from a saved state is bit-exact with the uninterrupted run.
+ * ECORRUPT: a row of walker_at is not a permutation or a spin is not +-1. */
+int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, uint64_t sweep);
+
+/* Measurement sums since creation (or the last qisg_set_state), by slot:
+ *   sumA, sumB  [n_samples][n_replicas][n_slots]  sums of A and B
+ *   sumq, sumq2 [n_samples][n_slots][n_pairs]     sums of q and q^2
+ *   n_meas      number of measurements taken.
+ * Any output pointer may be NULL.  Synchronises.                           */
+int qisg_measurements(qisg_handle *h, int64_t *sumA, int64_t *sumB, int64_t *sumq,
+                      int64_t *sumq2, int64_t *n_meas);
+
+/* FP64 per-slot means over samples, replicas (pairs) and measurements:
+ * e_s[s] = <A>/(2N), e_t[s] = <B>/N, q2[s] = <q^2>/N^2, N = L*L*L_tau;
+ * the integer sums are added in the fixed order sample, replica (pair).
+ * Host double arrays of n_slots.  ESTATE: no measurement yet.             */
+int qisg_slot_means(qisg_handle *h, double *e_s, double *e_t, double *q2);
+
+/* The uint32 Metropolis table in use: T[s][u_s][u_t] (u_s unsatisfied
+ * spatial bonds 0..4, u_t unsatisfied tau bonds 0..2); a spin flips iff
+ * T == 0xFFFFFFFF or its draw R < T.  Host uint32 [n_slots][5][3].         */
+int qisg_thresholds(qisg_handle *h, uint32_t *T);
+
+/* Sweeps done so far. */
+int qisg_sweep_count(qisg_handle *h, uint64_t *t);
+
+/* Layout and word width the handle chose (QISG_LAYOUT_LANES or _SAMPLES). */
+int qisg_layout(qisg_handle *h, int *layout, int *word_bits);
+
+/* Kernel launches this handle has issued since creation (diagnostics). */
+int qisg_launch_count(qisg_handle *h, int64_t *n);
+
+/* Block until the handle's stream is idle; reports any device error flag. */
+int qisg_sync(qisg_handle *h);
+
+/* Free the handle and its device memory (NULL is a no-op). */
+void qisg_destroy(qisg_handle *h);
+
+/* Text of a QISG_E* code; a message for the last failure on this thread. */
+const char *qisg_strerror(int code);
+const char *qisg_last_error(void);
+
+/* Philox4x32-10 on the device (Sec. 2.1.1): out[4i..4i+3] = Philox of
+ * counter ctr[4i..4i+3] under key key[2i..2i+1], i < n.  All pointers are
+ * DEVICE pointers; stream as in qisg_opts.  Used to check the device
+ * generator against others.  EINVAL: n < 0 or a NULL pointer with n > 0. */
+int qisg_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                       void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QISG_H */

@@ -192,7 +192,16 @@ def new_state(L, Ltau, k, ktau, n_rep, seed, a_lo=0, n_a=1) -> OracleState:
     wa = np.tile(np.arange(n_slots, dtype=np.int32), (n_a, n_rep, 1)).copy()
     st = OracleState(L, Ltau, k, kt, n_rep, a_lo, n_a, seed, J, S, wa)
     alloc_obs(st)
+    refresh_energies(st)
     return st
+
+
+def refresh_energies(st: OracleState) -> None:
+    """Set st.A, st.B (by slot) from the current configurations."""
+    Aw, Bw = energies(st.L, st.Ltau, st.J, st.S)
+    idx = st.walker_at.astype(np.int64)
+    st.A = np.take_along_axis(Aw, idx, axis=2)
+    st.B = np.take_along_axis(Bw, idx, axis=2)
 
 
 def alloc_obs(st: OracleState) -> None:

@@ -1,0 +1,571 @@
+// LANES packing: one word (32 or 64 bits) holds the replica x walker systems
+// of one disorder sample; lane = (r - g*rpw) * n_slots + w for the word group
+// g = r / rpw.  Every lane is a different system at a different ladder slot,
+// so each lane draws its own number and looks up its own Metropolis
+// threshold.  PT exchanges slot labels only (Sec. 2.1: "there is no need to
+// swap the spin systems, since it is sufficient to swap the k values").
+//
+// Device arrays (a = sample, N = L*L*L_tau):
+//   spins  Word [a][g][site]           bit = 1 <=> spin -1
+//   J      uint8 [a][x + L*y]          bit0: J(+x) = -1, bit1: J(+y) = -1
+//   U      u64 [a][r][w][2]            unsatisfied spatial / tau bonds of walker w
+#include <algorithm>
+#include <cstring>
+
+#include "qisg_internal.cuh"
+
+namespace qisg {
+namespace {
+
+constexpr int kBlock = 256;
+
+template <typename Word>
+struct LanesArgs {
+  Word *spins;
+  const uint8_t *J;
+  const int32_t *walker;
+  const uint32_t *T;
+  unsigned long long *U;
+  const unsigned long long *d_t;
+  uint2 key;
+  int64_t N, half_N;
+  int L, Lt, n_slots, n_rep, rpw, n_groups, sites_per_block;
+};
+
+template <typename Word>
+__device__ __forceinline__ Word all_ones_if(bool b) {
+  return b ? ~Word(0) : Word(0);
+}
+
+template <typename Word>
+__device__ __forceinline__ uint32_t bit_at(Word w, int lane) {
+  return (uint32_t)(w >> lane) & 1u;
+}
+
+// One half sweep (colour 0 = red, 1 = blue) of samples a0 + blockIdx.y.
+// Thread (site j of the colour, slot s): one Philox call per group of four
+// replicas serves the four replicas of slot s at this site.  Flips of the
+// lanes of one site are OR-ed in shared memory, then applied once.  In the
+// blue pass the unsatisfied bonds after the flip are counted: every bond
+// has exactly one blue end, so the blue pass counts each bond once.
+template <typename Word>
+__global__ void __launch_bounds__(kBlock) lanes_half_sweep_kernel(LanesArgs<Word> p, int colour,
+                                                                  int count_only, int64_t a0) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n_slots = p.n_slots, n_rep = p.n_rep, n_groups = p.n_groups;
+  const int64_t a = a0 + blockIdx.y;
+  uint32_t *T_s = reinterpret_cast<uint32_t *>(smem_raw);            // [n_slots*15]
+  int *wa_s = reinterpret_cast<int *>(T_s + n_slots * 15);             // [n_rep*n_slots]
+  int *e_s = wa_s + n_rep * n_slots;                                   // [n_rep*n_slots*2]
+  size_t off = (size_t)(n_slots * 15 + 3 * n_rep * n_slots) * 4;
+  off = (off + 7) & ~size_t(7);
+  Word *flip_s = reinterpret_cast<Word *>(smem_raw + off);             // [spb*n_groups]
+
+  for (int i = threadIdx.x; i < n_slots * 15; i += blockDim.x) T_s[i] = p.T[i];
+  for (int i = threadIdx.x; i < n_rep * n_slots; i += blockDim.x) {
+    wa_s[i] = p.walker[a * n_rep * n_slots + i];
+    e_s[2 * i] = 0;
+    e_s[2 * i + 1] = 0;
+  }
+  for (int i = threadIdx.x; i < p.sites_per_block * n_groups; i += blockDim.x) flip_s[i] = 0;
+  __syncthreads();
+
+  const int s = threadIdx.x % n_slots;
+  const int jl = threadIdx.x / n_slots;
+  const int64_t j = (int64_t)blockIdx.x * p.sites_per_block + jl;
+  if (jl < p.sites_per_block && j < p.half_N) {
+    const int L = p.L, Lt = p.Lt;
+    const SiteXYT c = site_of_colour(j, L, colour);
+    const int xp = c.x + 1 == L ? 0 : c.x + 1, xm = c.x == 0 ? L - 1 : c.x - 1;
+    const int yp = c.y + 1 == L ? 0 : c.y + 1, ym = c.y == 0 ? L - 1 : c.y - 1;
+    const int tp = c.tau + 1 == Lt ? 0 : c.tau + 1, tm = c.tau == 0 ? Lt - 1 : c.tau - 1;
+    const int64_t plane = (int64_t)L * L;
+    const int64_t site = c.x + (int64_t)L * c.y + plane * c.tau;
+    const int64_t off_t = plane * c.tau;
+    const int64_t i_xp = xp + (int64_t)L * c.y + off_t, i_xm = xm + (int64_t)L * c.y + off_t;
+    const int64_t i_yp = c.x + (int64_t)L * yp + off_t, i_ym = c.x + (int64_t)L * ym + off_t;
+    const int64_t i_tp = c.x + (int64_t)L * c.y + plane * tp;
+    const int64_t i_tm = c.x + (int64_t)L * c.y + plane * tm;
+    const uint8_t *Ja = p.J + a * plane;
+    const uint8_t j_here = __ldg(Ja + c.x + L * c.y);
+    const Word Jxp = all_ones_if<Word>(j_here & 1u);
+    const Word Jyp = all_ones_if<Word>(j_here & 2u);
+    const Word Jxm = all_ones_if<Word>(__ldg(Ja + xm + L * c.y) & 1u);
+    const Word Jym = all_ones_if<Word>(__ldg(Ja + c.x + L * ym) & 2u);
+    const unsigned long long t = *p.d_t;
+
+    int cur_q = -1;
+    uint4 R = make_uint4(0, 0, 0, 0);
+    for (int g = 0; g < n_groups; ++g) {
+      const Word *base = p.spins + (a * n_groups + g) * p.N;
+      const Word sc = base[site];
+      // unsatisfied-bond bits: J S_i S_j = -1 <=> j ^ s_i ^ s_j = 1
+      const Word b1 = sc ^ base[i_xp] ^ Jxp;
+      const Word b2 = sc ^ base[i_xm] ^ Jxm;
+      const Word b3 = sc ^ base[i_yp] ^ Jyp;
+      const Word b4 = sc ^ base[i_ym] ^ Jym;
+      const Word t1 = sc ^ base[i_tp];
+      const Word t2 = sc ^ base[i_tm];
+      // bit-sliced counts u_s = b1+b2+b3+b4 (3 bits), u_t = t1+t2 (2 bits)
+      const Word s1 = b1 ^ b2 ^ b3;
+      const Word c1 = (b1 & b2) | (b3 & (b1 ^ b2));
+      const Word us0 = s1 ^ b4;
+      const Word c2 = s1 & b4;
+      const Word us1 = c1 ^ c2;
+      const Word us2 = c1 & c2;
+      const Word ut0 = t1 ^ t2;
+      const Word ut1 = t1 & t2;
+
+      Word fw = 0;
+      const int r_lo = g * p.rpw;
+      const int r_hi = min(n_rep, r_lo + p.rpw);
+      for (int r = r_lo; r < r_hi; ++r) {
+        const int q = r >> 2;
+        if (q != cur_q) {
+          R = philox(make_uint4((uint32_t)site, (uint32_t)t, (uint32_t)s | ((uint32_t)q << 16),
+                                (DOM_SWEEP << 28) | (uint32_t)(a >> 6)),
+                     p.key);
+          cur_q = q;
+        }
+        const int w = wa_s[r * n_slots + s];
+        const int lane = (r - r_lo) * n_slots + w;
+        const int us = (int)(bit_at(us0, lane) | (bit_at(us1, lane) << 1) | (bit_at(us2, lane) << 2));
+        const int ut = (int)(bit_at(ut0, lane) | (bit_at(ut1, lane) << 1));
+        const uint32_t thr = T_s[s * 15 + us * 3 + ut];
+        const bool flip = !count_only && (thr == 0xFFFFFFFFu || pick4(R, r & 3) < thr);
+        if (flip) fw |= Word(1) << lane;
+        if (colour == 1) {
+          atomicAdd(&e_s[2 * (r * n_slots + s)], flip ? 4 - us : us);
+          atomicAdd(&e_s[2 * (r * n_slots + s) + 1], flip ? 2 - ut : ut);
+        }
+      }
+      if (fw) {
+        if (sizeof(Word) == 8)
+          atomicOr(reinterpret_cast<unsigned long long *>(&flip_s[jl * n_groups + g]),
+                   (unsigned long long)fw);
+        else
+          atomicOr(reinterpret_cast<unsigned int *>(&flip_s[jl * n_groups + g]), (unsigned int)fw);
+      }
+    }
+  }
+  __syncthreads();
+
+  if (!count_only) {
+    for (int i = threadIdx.x; i < p.sites_per_block * n_groups; i += blockDim.x) {
+      const int jl2 = i / n_groups, g = i - jl2 * n_groups;
+      const int64_t j2 = (int64_t)blockIdx.x * p.sites_per_block + jl2;
+      const Word fw = flip_s[i];
+      if (j2 < p.half_N && fw) {
+        const SiteXYT c = site_of_colour(j2, p.L, colour);
+        const int64_t site = c.x + (int64_t)p.L * c.y + (int64_t)p.L * p.L * c.tau;
+        p.spins[(a * n_groups + g) * p.N + site] ^= fw;
+      }
+    }
+  }
+  if (colour == 1) {
+    for (int i = threadIdx.x; i < n_rep * n_slots; i += blockDim.x) {
+      const int r = i / n_slots;
+      const int w = wa_s[i];
+      unsigned long long *u = p.U + ((a * n_rep + r) * n_slots + w) * 2;
+      if (e_s[2 * i]) atomicAdd(u, (unsigned long long)e_s[2 * i]);
+      if (e_s[2 * i + 1]) atomicAdd(u + 1, (unsigned long long)e_s[2 * i + 1]);
+    }
+  }
+}
+
+__global__ void zero_u64_kernel(unsigned long long *p, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0;
+}
+
+// PT pass (Sec. 2.1) of chain (a, r): pairs (s, s+1) in increasing s.  The
+// exchange is accepted iff u < P with P = alpha^|m| beta^|n| (bases chosen
+// by the signs of m = A_Y - A_X, n = B_Y - B_X), u = x * 2^-32.
+__global__ void lanes_pt_kernel(int32_t *walker, const unsigned long long *U, const double *bases,
+                                const unsigned long long *d_t, uint2 key, int64_t a0, int64_t n_a,
+                                int n_rep, int n_slots, int64_t N, int explicit_pass) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_a * n_rep) return;
+  const int64_t a = a0 + c / n_rep;
+  const int r = (int)(c % n_rep);
+  const unsigned long long t = explicit_pass ? *d_t - 1ull : *d_t;
+  int32_t *wa = walker + (a * n_rep + r) * n_slots;
+  const unsigned long long *Ua = U + (a * n_rep + r) * n_slots * 2;
+  const double *ap = bases, *am = bases + n_slots, *bp = bases + 2 * n_slots,
+               *bm = bases + 3 * n_slots;
+  for (int s = 0; s + 1 < n_slots; ++s) {
+    const int X = wa[s], Y = wa[s + 1];
+    // A = 2N - 2 U_s, B = N - 2 U_t
+    const long long m = -2 * ((long long)Ua[2 * Y] - (long long)Ua[2 * X]);
+    const long long n = -2 * ((long long)Ua[2 * Y + 1] - (long long)Ua[2 * X + 1]);
+    const double fa = pow_rn(m >= 0 ? ap[s] : am[s], (unsigned long long)(m >= 0 ? m : -m));
+    const double fb = pow_rn(n >= 0 ? bp[s] : bm[s], (unsigned long long)(n >= 0 ? n : -n));
+    const double P = __dmul_rn(fa, fb);
+    const uint4 x = philox(make_uint4((uint32_t)s, (uint32_t)t, (uint32_t)a,
+                                      (DOM_PT << 28) | (uint32_t)(r >> 2)),
+                           key);
+    const double u = __dmul_rn((double)pick4(x, r & 3), 0x1p-32);
+    if (u < P) {
+      wa[s] = Y;
+      wa[s + 1] = X;
+    }
+  }
+}
+
+// Overlaps of the configurations at slot s (Appendix E.1): count the sites
+// where the replicas r1 < r2 differ; q = N - 2 * count.  Grid (chunks,
+// n_slots, n_a); accumulates counts into qcnt[a][s][pair].
+template <typename Word>
+__global__ void __launch_bounds__(kBlock) lanes_overlap_kernel(const Word *spins, const int32_t *walker,
+                                                               long long *qcnt, int64_t a0, int64_t N,
+                                                               int n_rep, int n_slots, int rpw,
+                                                               int n_groups) {
+  extern __shared__ long long q_s[];  // [n_pairs]
+  const int n_pairs = n_rep * (n_rep - 1) / 2;
+  const int s = blockIdx.y;
+  const int64_t a = a0 + blockIdx.z;
+  for (int i = threadIdx.x; i < n_pairs; i += blockDim.x) q_s[i] = 0;
+  __syncthreads();
+  const int32_t *wa = walker + a * n_rep * n_slots;
+  const Word *base = spins + a * n_groups * N;
+  for (int64_t site = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; site < N;
+       site += (int64_t)gridDim.x * blockDim.x) {
+    int p = 0;
+    for (int r1 = 0; r1 < n_rep; ++r1) {
+      const int g1 = r1 / rpw;
+      const int l1 = (r1 - g1 * rpw) * n_slots + wa[r1 * n_slots + s];
+      const uint32_t b1 = (uint32_t)(base[g1 * N + site] >> l1) & 1u;
+      for (int r2 = r1 + 1; r2 < n_rep; ++r2, ++p) {
+        const int g2 = r2 / rpw;
+        const int l2 = (r2 - g2 * rpw) * n_slots + wa[r2 * n_slots + s];
+        const uint32_t b2 = (uint32_t)(base[g2 * N + site] >> l2) & 1u;
+        const uint32_t d = b1 ^ b2;
+        // warp reduce then one shared atomic per warp
+        const unsigned act = __activemask();
+        const uint32_t cnt = __popc(__ballot_sync(act, d));
+        if ((int)(threadIdx.x & 31) == __ffs(act) - 1 && cnt)
+          atomicAdd(reinterpret_cast<unsigned long long *>(&q_s[p]), (unsigned long long)cnt);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_pairs; i += blockDim.x)
+    if (q_s[i])
+      atomicAdd(reinterpret_cast<unsigned long long *>(&qcnt[(a * n_slots + s) * n_pairs + i]),
+                (unsigned long long)q_s[i]);
+}
+
+// Measurement finalisation: sums by slot of A, B, q, q^2; turns the
+// difference counts into q and clears them.  One thread per (a, s).
+__global__ void lanes_finalize_kernel(const int32_t *walker, const unsigned long long *U,
+                                      long long *qcnt, long long *sumA, long long *sumB,
+                                      long long *sumq, long long *sumq2, int64_t n_a, int n_rep,
+                                      int n_slots, int64_t N, int to_q_only) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_a * n_slots) return;
+  const int64_t a = c / n_slots;
+  const int s = (int)(c % n_slots);
+  const int n_pairs = n_rep * (n_rep - 1) / 2;
+  if (to_q_only) {
+    for (int p = 0; p < n_pairs; ++p) {
+      long long *qc = &qcnt[(a * n_slots + s) * n_pairs + p];
+      *qc = N - 2 * *qc;
+    }
+    return;
+  }
+  for (int r = 0; r < n_rep; ++r) {
+    const int w = walker[(a * n_rep + r) * n_slots + s];
+    const unsigned long long *u = U + ((a * n_rep + r) * n_slots + w) * 2;
+    sumA[(a * n_rep + r) * n_slots + s] += 2 * N - 2 * (long long)u[0];
+    sumB[(a * n_rep + r) * n_slots + s] += N - 2 * (long long)u[1];
+  }
+  for (int p = 0; p < n_pairs; ++p) {
+    long long *qc = &qcnt[(a * n_slots + s) * n_pairs + p];
+    const long long q = N - 2 * *qc;
+    sumq[(a * n_slots + s) * n_pairs + p] += q;
+    sumq2[(a * n_slots + s) * n_pairs + p] += q * q;
+    *qc = 0;
+  }
+}
+
+__global__ void lanes_by_slot_kernel(const int32_t *walker, const unsigned long long *U,
+                                     long long *out, int64_t n_a, int n_rep, int n_slots,
+                                     int64_t N) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t total = n_a * n_rep * n_slots;
+  if (c >= total) return;
+  const int64_t ar = c / n_slots;
+  const int w = walker[c];
+  const unsigned long long *u = U + (ar * n_slots + w) * 2;
+  out[c] = 2 * N - 2 * (long long)u[0];
+  out[total + c] = N - 2 * (long long)u[1];
+}
+
+// Start state: J and spins from Philox domains DOM_J and DOM_INIT.
+__global__ void lanes_init_J_kernel(uint8_t *J, int64_t n_a, int L, uint2 key) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t plane = (int64_t)L * L;
+  if (c >= n_a * plane) return;
+  const int64_t a = c / plane;
+  const uint32_t i2 = (uint32_t)(c % plane);
+  uint8_t v = 0;
+  for (uint32_t dir = 0; dir < 2; ++dir) {
+    const uint4 x = philox(make_uint4(i2, dir, (uint32_t)a, DOM_J << 28), key);
+    if (!(x.x & 1u)) v |= (uint8_t)(1u << dir);  // J = -1 <=> bit set
+  }
+  J[c] = v;
+}
+
+template <typename Word>
+__global__ void lanes_init_spins_kernel(Word *spins, int64_t n_a, int64_t N, int n_rep, int n_slots,
+                                        int rpw, int n_groups, uint2 key) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_a * n_groups * N) return;
+  const int64_t site = c % N;
+  const int64_t ag = c / N;
+  const int g = (int)(ag % n_groups);
+  const int64_t a = ag / n_groups;
+  Word v = 0;
+  const int r_lo = g * rpw, r_hi = min(n_rep, r_lo + rpw);
+  for (int r = r_lo; r < r_hi; ++r)
+    for (int w = 0; w < n_slots; ++w) {
+      const uint4 x = philox(make_uint4((uint32_t)site, (uint32_t)w, (uint32_t)a,
+                                        (DOM_INIT << 28) | (uint32_t)r),
+                             key);
+      if (!(x.x & 1u)) v |= Word(1) << ((r - r_lo) * n_slots + w);  // spin -1
+    }
+  spins[c] = v;
+}
+
+template <typename Word>
+LanesArgs<Word> make_args(qisg_handle *h) {
+  LanesArgs<Word> p;
+  p.spins = reinterpret_cast<Word *>(h->spins);
+  p.J = reinterpret_cast<const uint8_t *>(h->J);
+  p.walker = h->d_walker;
+  p.T = h->d_T;
+  p.U = h->d_U;
+  p.d_t = h->d_t;
+  p.key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  p.N = h->N;
+  p.half_N = h->N / 2;
+  p.L = h->L;
+  p.Lt = h->Lt;
+  p.n_slots = h->n_slots;
+  p.n_rep = h->n_rep;
+  p.rpw = h->rpw;
+  p.n_groups = h->n_groups;
+  p.sites_per_block = kBlock / h->n_slots;
+  return p;
+}
+
+template <typename Word>
+int half_sweep_t(qisg_handle *h, int colour, int count_only) {
+  LanesArgs<Word> p = make_args<Word>(h);
+  const int64_t blocks = (p.half_N + p.sites_per_block - 1) / p.sites_per_block;
+  size_t smem = (size_t)(h->n_slots * 15 + 3 * h->n_rep * h->n_slots) * 4;
+  smem = (smem + 7) & ~size_t(7);
+  smem += (size_t)p.sites_per_block * h->n_groups * sizeof(Word);
+  if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+  if (colour == 0) {
+    const int64_t n = h->n_samples * h->n_rep * h->n_slots * 2;
+    zero_u64_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, h->stream>>>(h->d_U, n);
+    h->launches++;
+  }
+  if (h->per_sample_launch) {
+    for (int64_t a = 0; a < h->n_samples; ++a) {
+      lanes_half_sweep_kernel<Word><<<dim3((unsigned)blocks, 1), kBlock, smem, h->stream>>>(
+          p, colour, count_only, a);
+      h->launches++;
+    }
+  } else {
+    for (int64_t a0 = 0; a0 < h->n_samples; a0 += 65535) {
+      const int64_t na = std::min<int64_t>(65535, h->n_samples - a0);
+      lanes_half_sweep_kernel<Word><<<dim3((unsigned)blocks, (unsigned)na), kBlock, smem, h->stream>>>(
+          p, colour, count_only, a0);
+      h->launches++;
+    }
+  }
+  return cuda_check(cudaGetLastError(), "lanes half sweep");
+}
+
+template <typename Word>
+int measure_t(qisg_handle *h, int force_to_q) {
+  const int n_pairs = h->n_pairs();
+  if (n_pairs > 0) {
+    const int64_t chunks = std::min<int64_t>((h->N + kBlock - 1) / kBlock, 64);
+    const size_t smem = (size_t)n_pairs * 8;
+    for (int64_t a0 = 0; a0 < h->n_samples; a0 += 65535) {
+      const int64_t na = std::min<int64_t>(65535, h->n_samples - a0);
+      lanes_overlap_kernel<Word><<<dim3((unsigned)chunks, (unsigned)h->n_slots, (unsigned)na), kBlock,
+                                   smem, h->stream>>>(reinterpret_cast<const Word *>(h->spins),
+                                                      h->d_walker, h->d_q, a0, h->N, h->n_rep,
+                                                      h->n_slots, h->rpw, h->n_groups);
+      h->launches++;
+    }
+  }
+  const int64_t n = h->n_samples * h->n_slots;
+  lanes_finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+      h->d_walker, h->d_U, h->d_q, h->d_sumA, h->d_sumB, h->d_sumq, h->d_sumq2, h->n_samples,
+      h->n_rep, h->n_slots, h->N, force_to_q);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "lanes measure");
+}
+
+int lane_of(const qisg_handle *h, int r, int w, int *g) {
+  *g = r / h->rpw;
+  return (r - *g * h->rpw) * h->n_slots + w;
+}
+
+}  // namespace
+
+int lanes_init(qisg_handle *h) {
+  const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  const int64_t nJ = h->n_samples * h->L * h->L;
+  lanes_init_J_kernel<<<(unsigned)((nJ + 255) / 256), 256, 0, h->stream>>>(
+      reinterpret_cast<uint8_t *>(h->J), h->n_samples, h->L, key);
+  const int64_t nS = h->n_samples * h->n_groups * h->N;
+  if ((nS + 255) / 256 > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large");
+  if (h->W == 64)
+    lanes_init_spins_kernel<unsigned long long><<<(unsigned)((nS + 255) / 256), 256, 0, h->stream>>>(
+        reinterpret_cast<unsigned long long *>(h->spins), h->n_samples, h->N, h->n_rep, h->n_slots,
+        h->rpw, h->n_groups, key);
+  else
+    lanes_init_spins_kernel<unsigned int><<<(unsigned)((nS + 255) / 256), 256, 0, h->stream>>>(
+        reinterpret_cast<unsigned int *>(h->spins), h->n_samples, h->N, h->n_rep, h->n_slots,
+        h->rpw, h->n_groups, key);
+  h->launches += 2;
+  return cuda_check(cudaGetLastError(), "lanes init");
+}
+
+int lanes_half_sweep(qisg_handle *h, int colour, int count_only) {
+  return h->W == 64 ? half_sweep_t<unsigned long long>(h, colour, count_only)
+                    : half_sweep_t<unsigned int>(h, colour, count_only);
+}
+
+int lanes_pt(qisg_handle *h, int explicit_pass) {
+  const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  if (h->per_sample_launch) {
+    for (int64_t a = 0; a < h->n_samples; ++a) {
+      lanes_pt_kernel<<<(unsigned)((h->n_rep + 127) / 128), 128, 0, h->stream>>>(
+          h->d_walker, h->d_U, h->d_bases, h->d_t, key, a, 1, h->n_rep, h->n_slots, h->N,
+          explicit_pass);
+      h->launches++;
+    }
+  } else {
+    const int64_t n = h->n_samples * h->n_rep;
+    lanes_pt_kernel<<<(unsigned)((n + 127) / 128), 128, 0, h->stream>>>(
+        h->d_walker, h->d_U, h->d_bases, h->d_t, key, 0, h->n_samples, h->n_rep, h->n_slots, h->N,
+        explicit_pass);
+    h->launches++;
+  }
+  return cuda_check(cudaGetLastError(), "lanes pt");
+}
+
+int lanes_measure(qisg_handle *h, int force_to_q) {
+  return h->W == 64 ? measure_t<unsigned long long>(h, force_to_q)
+                    : measure_t<unsigned int>(h, force_to_q);
+}
+
+int lanes_energies_by_slot(qisg_handle *h) {
+  const int64_t n = h->n_samples * h->n_rep * h->n_slots;
+  lanes_by_slot_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+      h->d_walker, h->d_U, h->d_out, h->n_samples, h->n_rep, h->n_slots, h->N);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "lanes energies");
+}
+
+int lanes_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
+  const size_t wb = h->W / 8;
+  const size_t per_a = (size_t)h->n_groups * h->N * wb;
+  std::vector<unsigned char> buf(per_a * n_a);
+  int rc = cuda_check(cudaMemcpyAsync(buf.data(), (const unsigned char *)h->spins + a_lo * per_a,
+                                      buf.size(), cudaMemcpyDeviceToHost, h->stream),
+                      "copy spins");
+  if (rc) return rc;
+  rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  if (rc) return rc;
+  for (int64_t ai = 0; ai < n_a; ++ai)
+    for (int r = 0; r < h->n_rep; ++r)
+      for (int w = 0; w < h->n_slots; ++w) {
+        int g;
+        const int lane = lane_of(h, r, w, &g);
+        int8_t *dst = S + ((ai * h->n_rep + r) * h->n_slots + w) * h->N;
+        const unsigned char *src = buf.data() + ai * per_a + (size_t)g * h->N * wb;
+        for (int64_t i = 0; i < h->N; ++i) {
+          uint64_t v;
+          if (wb == 8) {
+            std::memcpy(&v, src + i * 8, 8);
+          } else {
+            uint32_t v32;
+            std::memcpy(&v32, src + i * 4, 4);
+            v = v32;
+          }
+          dst[i] = ((v >> lane) & 1u) ? -1 : 1;
+        }
+      }
+  return QISG_OK;
+}
+
+int lanes_set_spins(qisg_handle *h, const int8_t *S) {
+  const size_t wb = h->W / 8;
+  const size_t per_a = (size_t)h->n_groups * h->N * wb;
+  std::vector<unsigned char> buf(per_a * h->n_samples, 0);
+  for (int64_t a = 0; a < h->n_samples; ++a)
+    for (int r = 0; r < h->n_rep; ++r)
+      for (int w = 0; w < h->n_slots; ++w) {
+        int g;
+        const int lane = lane_of(h, r, w, &g);
+        const int8_t *src = S + ((a * h->n_rep + r) * h->n_slots + w) * h->N;
+        unsigned char *dst = buf.data() + a * per_a + (size_t)g * h->N * wb;
+        for (int64_t i = 0; i < h->N; ++i) {
+          if (src[i] != -1) continue;
+          if (wb == 8) {
+            uint64_t v;
+            std::memcpy(&v, dst + i * 8, 8);
+            v |= 1ull << lane;
+            std::memcpy(dst + i * 8, &v, 8);
+          } else {
+            uint32_t v;
+            std::memcpy(&v, dst + i * 4, 4);
+            v |= 1u << lane;
+            std::memcpy(dst + i * 4, &v, 4);
+          }
+        }
+      }
+  int rc = cuda_check(cudaMemcpyAsync(h->spins, buf.data(), buf.size(), cudaMemcpyHostToDevice,
+                                      h->stream),
+                      "copy spins");
+  if (rc) return rc;
+  return cuda_check(cudaStreamSynchronize(h->stream), "sync");
+}
+
+int lanes_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J) {
+  const int64_t plane = (int64_t)h->L * h->L;
+  std::vector<uint8_t> buf(plane * n_a);
+  int rc = cuda_check(cudaMemcpyAsync(buf.data(), (const uint8_t *)h->J + a_lo * plane, buf.size(),
+                                      cudaMemcpyDeviceToHost, h->stream),
+                      "copy J");
+  if (rc) return rc;
+  rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  if (rc) return rc;
+  for (int64_t i = 0; i < plane * n_a; ++i) {
+    J[2 * i] = (buf[i] & 1u) ? -1 : 1;
+    J[2 * i + 1] = (buf[i] & 2u) ? -1 : 1;
+  }
+  return QISG_OK;
+}
+
+int lanes_set_couplings(qisg_handle *h, const int8_t *J) {
+  const int64_t plane = (int64_t)h->L * h->L;
+  std::vector<uint8_t> buf(plane * h->n_samples);
+  for (int64_t i = 0; i < plane * h->n_samples; ++i)
+    buf[i] = (uint8_t)((J[2 * i] == -1 ? 1u : 0u) | (J[2 * i + 1] == -1 ? 2u : 0u));
+  int rc = cuda_check(cudaMemcpyAsync(h->J, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream),
+                      "copy J");
+  if (rc) return rc;
+  return cuda_check(cudaStreamSynchronize(h->stream), "sync");
+}
+
+}  // namespace qisg

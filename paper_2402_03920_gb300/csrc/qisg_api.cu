@@ -1,0 +1,534 @@
+// Host side of the C ABI declared in include/qisg.h: argument checks, the
+// FP64 tables built once per instance (Sec. 2.1: Metropolis factors
+// precomputed for every possible value; the PT bases), device memory, and the
+// sweep schedule (Appendix A: EMCS = pt_every sweeps + one PT update, an
+// energy measurement every measure_every sweeps).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qisg_internal.cuh"
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+namespace qisg {
+
+int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_check(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return QISG_OK;
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return QISG_ENOMEM;
+  return QISG_ECUDA;
+}
+
+__global__ void advance_kernel(unsigned long long *d_t) { *d_t += 1ull; }
+
+int advance_counter(qisg_handle *h) {
+  advance_kernel<<<1, 1, 0, h->stream>>>(h->d_t);
+  h->launches++;
+  h->t++;
+  return cuda_check(cudaGetLastError(), "advance counter");
+}
+
+__global__ void philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+  const uint4 r = philox(c, make_uint2(key[2 * i], key[2 * i + 1]));
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+}  // namespace qisg
+
+using namespace qisg;
+
+namespace {
+
+// FP64 table of the Metropolis test (Sec. 2.1).  Flipping a spin with u_s of
+// its 4 spatial bonds and u_t of its 2 tau bonds unsatisfied multiplies the
+// weight exp(k A + k_tau B) by exp(Delta), Delta = -4k(2-u_s) - 4k_tau(1-u_t).
+// Both products are exact (k times 8, 4, 0, -4 or -8), so Delta is rounded
+// once.  T = 0xFFFFFFFF when e^Delta >= 1, else min(0xFFFFFFFE,
+// floor(e^Delta 2^32)); a spin flips iff T == 0xFFFFFFFF or its draw R < T.
+void build_thresholds(qisg_handle *h) {
+  h->T.assign((size_t)h->n_slots * 15, 0);
+  for (int s = 0; s < h->n_slots; ++s)
+    for (int us = 0; us <= 4; ++us)
+      for (int ut = 0; ut <= 2; ++ut) {
+        const double dk = (double)(4 * (2 - us)) * h->k[s];
+        const double dkt = (double)(4 * (1 - ut)) * h->kt[s];
+        const double p = std::exp(-dk - dkt);
+        uint32_t v;
+        if (p >= 1.0) {
+          v = 0xFFFFFFFFu;
+        } else {
+          const double f = std::floor(std::ldexp(p, 32));
+          v = f >= 4294967294.0 ? 0xFFFFFFFEu : (uint32_t)f;
+        }
+        h->T[(size_t)s * 15 + us * 3 + ut] = v;
+      }
+}
+
+// PT bases of the pair (s, s+1): alpha+- = exp(+-(k_s - k_{s+1})),
+// beta+- = exp(+-(k_tau,s - k_tau,s+1)).
+void build_bases(qisg_handle *h) {
+  const int n = h->n_slots;
+  h->bases.assign((size_t)4 * n, 1.0);
+  for (int s = 0; s + 1 < n; ++s) {
+    const double dk = h->k[s] - h->k[s + 1];
+    const double dkt = h->kt[s] - h->kt[s + 1];
+    h->bases[s] = std::exp(dk);
+    h->bases[n + s] = std::exp(-dk);
+    h->bases[2 * n + s] = std::exp(dkt);
+    h->bases[3 * n + s] = std::exp(-dkt);
+  }
+}
+
+template <typename T>
+int dalloc(qisg_handle *h, T **p, size_t bytes) {
+  if (h->mem_budget && h->device_bytes + bytes > h->mem_budget)
+    return fail(QISG_ENOMEM, "state exceeds the memory budget");
+  void *q = nullptr;
+  const cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e != cudaSuccess) return cuda_check(e, "cudaMalloc");
+  h->device_bytes += bytes;
+  *p = reinterpret_cast<T *>(q);
+  return QISG_OK;
+}
+
+int recompute_energies(qisg_handle *h) {
+  int rc;
+  if (h->layout == QISG_LAYOUT_LANES) {
+    if ((rc = lanes_half_sweep(h, 0, 1))) return rc;
+    return lanes_half_sweep(h, 1, 1);
+  }
+  if ((rc = samples_half_sweep(h, 0, 1))) return rc;
+  return samples_half_sweep(h, 1, 1);
+}
+
+int sync_handle(qisg_handle *h) {
+  int rc = cuda_check(cudaStreamSynchronize(h->stream), "stream synchronize");
+  if (rc) return rc;
+  int err = 0;
+  rc = cuda_check(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+  if (rc) return rc;
+  if (err) return fail(QISG_ETIMEOUT, "a bounded device wait expired");
+  return QISG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qisg_opts_default(qisg_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->pt_every = 1;
+}
+
+int qisg_ladder_linear(double lo, double hi, int n, double gamma, qisg_slot *out) {
+  if (!out || n < 1 || !(gamma > 0) || !(lo > 0) || !std::isfinite(hi))
+    return fail(QISG_EINVAL, "ladder: need n >= 1, gamma > 0, lo > 0");
+  for (int s = 0; s < n; ++s) {
+    const double k = (n == 1) ? lo : lo + (hi - lo) * (double)s / (double)(n - 1);
+    const double kt = -0.5 * std::log(std::tanh(k * gamma));
+    if (!std::isfinite(kt) || kt < 0 || !(k > 0)) return fail(QISG_EINVAL, "ladder: k_tau not finite");
+    out[s].k = k;
+    out[s].k_tau = kt;
+  }
+  return QISG_OK;
+}
+
+int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, int n_slots,
+                int n_replicas, int64_t n_samples, uint64_t seed, const qisg_opts *opts) {
+  if (!out) return fail(QISG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (L < 2 || (L & 1)) return fail(QISG_EINVAL, "L must be even and >= 2");
+  if (L_tau < 2 || (L_tau & 1)) return fail(QISG_EINVAL, "L_tau must be even and >= 2");
+  if (n_slots < 1 || !ladder) return fail(QISG_EINVAL, "need at least one ladder slot");
+  if (n_replicas < 1 || n_replicas > 1024) return fail(QISG_EINVAL, "n_replicas must be in 1..1024");
+  if (n_samples < 1) return fail(QISG_EINVAL, "n_samples must be >= 1");
+  if (n_slots > 4096) return fail(QISG_EINVAL, "n_slots must be <= 4096");
+  if ((int64_t)L * L * L_tau > ((int64_t)1 << 31)) return fail(QISG_EINVAL, "lattice too large");
+  for (int s = 0; s < n_slots; ++s)
+    if (!std::isfinite(ladder[s].k) || !std::isfinite(ladder[s].k_tau) || ladder[s].k < 0 ||
+        ladder[s].k_tau < 0)
+      return fail(QISG_EINVAL, "ladder couplings must be finite and >= 0");
+  qisg_opts o;
+  qisg_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.word_bits != 0 && o.word_bits != 32 && o.word_bits != 64)
+    return fail(QISG_EINVAL, "word_bits must be 0, 32 or 64");
+  if (o.pt_every < 0 || o.measure_every < 0) return fail(QISG_EINVAL, "negative cadence");
+  if (o.layout < 0 || o.layout > 2) return fail(QISG_EINVAL, "unknown layout");
+
+  qisg_handle *h = new (std::nothrow) qisg_handle();
+  if (!h) return fail(QISG_ENOMEM, "host allocation");
+  h->L = L;
+  h->Lt = L_tau;
+  h->N = (int64_t)L * L * L_tau;
+  h->n_slots = n_slots;
+  h->n_rep = n_replicas;
+  h->n_samples = n_samples;
+  h->seed = seed;
+  h->pt_every = o.pt_every;
+  h->measure_every = o.measure_every;
+  h->stream = reinterpret_cast<cudaStream_t>(o.cuda_stream);
+  h->mem_budget = o.mem_budget;
+  h->per_sample_launch = o.per_sample_launch;
+  h->k.resize(n_slots);
+  h->kt.resize(n_slots);
+  for (int s = 0; s < n_slots; ++s) {
+    h->k[s] = ladder[s].k;
+    h->kt[s] = ladder[s].k_tau;
+  }
+  int layout = o.layout;
+  if (layout == QISG_LAYOUT_AUTO) layout = n_samples >= 32 ? QISG_LAYOUT_SAMPLES : QISG_LAYOUT_LANES;
+  h->layout = layout;
+  if (layout == QISG_LAYOUT_LANES) {
+    int W = o.word_bits;
+    if (W == 0) W = (n_slots * n_replicas <= 32) ? 32 : 64;
+    if (n_slots > W) {
+      delete h;
+      return fail(QISG_EINVAL, "LANES packing needs n_slots <= word bits");
+    }
+    if (n_replicas > 64) {
+      delete h;
+      return fail(QISG_EINVAL, "LANES packing needs n_replicas <= 64");
+    }
+    h->W = W;
+    h->rpw = W / n_slots;
+    h->n_groups = (n_replicas + h->rpw - 1) / h->rpw;
+    h->n_a_pad = n_samples;
+  } else {
+    int W = o.word_bits;
+    if (W == 0) W = n_samples <= 32 ? 32 : 64;
+    h->W = W;
+    h->n_b = (n_samples + W - 1) / W;
+    h->n_q = (n_replicas + 3) / 4;
+    h->n_a_pad = h->n_b * W;
+  }
+  build_thresholds(h);
+  build_bases(h);
+
+  int rc = cuda_check(cudaGetDevice(&h->device), "cudaGetDevice");
+  if (!rc) rc = cuda_check(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device),
+                           "device attribute");
+  const int64_t n_chain_slots = h->n_a_pad * n_replicas * n_slots;
+  const int n_pairs = h->n_pairs();
+  if (!rc) {
+    if (layout == QISG_LAYOUT_LANES) {
+      h->spins_bytes = (size_t)n_samples * h->n_groups * h->N * (h->W / 8);
+      h->J_bytes = (size_t)n_samples * L * L;
+    } else {
+      h->spins_bytes = (size_t)h->n_b * n_slots * h->n_q * h->N * 4 * (h->W / 8);
+      h->J_bytes = (size_t)h->n_b * L * L * 2 * (h->W / 8);
+    }
+    rc = dalloc(h, &h->spins, h->spins_bytes);
+  }
+  if (!rc) rc = dalloc(h, &h->J, h->J_bytes);
+  if (!rc) rc = dalloc(h, &h->d_T, h->T.size() * 4);
+  if (!rc) rc = dalloc(h, &h->d_bases, h->bases.size() * 8);
+  if (!rc) rc = dalloc(h, &h->d_walker, (size_t)n_chain_slots * 4);
+  if (!rc) rc = dalloc(h, &h->d_U, (size_t)n_chain_slots * 2 * 8);
+  if (!rc) rc = dalloc(h, &h->d_sumA, (size_t)n_chain_slots * 8);
+  if (!rc) rc = dalloc(h, &h->d_sumB, (size_t)n_chain_slots * 8);
+  const size_t qn = (size_t)h->n_a_pad * n_slots * (n_pairs > 0 ? n_pairs : 1);
+  if (!rc) rc = dalloc(h, &h->d_sumq, qn * 8);
+  if (!rc) rc = dalloc(h, &h->d_sumq2, qn * 8);
+  if (!rc) rc = dalloc(h, &h->d_q, qn * 8);
+  if (!rc) rc = dalloc(h, &h->d_out, (size_t)2 * n_chain_slots * 8 + qn * 8);
+  if (!rc) rc = dalloc(h, &h->d_t, 8);
+  if (!rc) rc = dalloc(h, &h->d_err, 4);
+  if (!rc && layout == QISG_LAYOUT_SAMPLES)
+    rc = dalloc(h, &h->d_acc, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8));
+  if (rc) {
+    qisg_destroy(h);
+    return rc;
+  }
+  // walker w starts at slot w
+  std::vector<int32_t> wa((size_t)n_chain_slots);
+  for (int64_t i = 0; i < n_chain_slots; ++i) wa[(size_t)i] = (int32_t)(i % n_slots);
+  rc = cuda_check(cudaMemcpyAsync(h->d_walker, wa.data(), wa.size() * 4, cudaMemcpyHostToDevice, h->stream),
+                  "copy walker");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(h->d_T, h->T.data(), h->T.size() * 4, cudaMemcpyHostToDevice, h->stream),
+                           "copy T");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(h->d_bases, h->bases.data(), h->bases.size() * 8,
+                                           cudaMemcpyHostToDevice, h->stream),
+                           "copy bases");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumA, 0, (size_t)n_chain_slots * 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumB, 0, (size_t)n_chain_slots * 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumq, 0, qn * 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumq2, 0, qn * 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_q, 0, qn * 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_t, 0, 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_err, 0, 4, h->stream), "memset");
+  if (!rc && h->d_acc)
+    rc = cuda_check(cudaMemsetAsync(h->d_acc, 0, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8), h->stream),
+                    "memset");
+  if (!rc) rc = (layout == QISG_LAYOUT_LANES) ? lanes_init(h) : samples_init(h);
+  if (!rc) rc = recompute_energies(h);
+  if (!rc) rc = sync_handle(h);
+  if (rc) {
+    qisg_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return QISG_OK;
+}
+
+int qisg_sweep(qisg_handle *h, int64_t n_sweeps) {
+  if (!h || n_sweeps < 0) return fail(QISG_EINVAL, "bad handle or n_sweeps < 0");
+  const bool lanes = h->layout == QISG_LAYOUT_LANES;
+  for (int64_t i = 0; i < n_sweeps; ++i) {
+    const uint64_t t = h->t;
+    int rc = lanes ? lanes_half_sweep(h, 0, 0) : samples_half_sweep(h, 0, 0);
+    if (!rc) rc = lanes ? lanes_half_sweep(h, 1, 0) : samples_half_sweep(h, 1, 0);
+    if (!rc && h->pt_every > 0 && (t + 1) % (uint64_t)h->pt_every == 0)
+      rc = lanes ? lanes_pt(h, 0) : samples_pt(h, 0);
+    if (!rc && h->measure_every > 0 && (t + 1) % (uint64_t)h->measure_every == 0) {
+      rc = lanes ? lanes_measure(h, 0) : samples_measure(h, 0);
+      h->n_meas++;
+    }
+    if (!rc) rc = advance_counter(h);
+    if (rc) return rc;
+  }
+  return QISG_OK;
+}
+
+int qisg_pt_swap(qisg_handle *h) {
+  if (!h) return fail(QISG_EINVAL, "NULL handle");
+  if (h->t == 0) return fail(QISG_ESTATE, "no sweep has run yet");
+  return h->layout == QISG_LAYOUT_LANES ? lanes_pt(h, 1) : samples_pt(h, 1);
+}
+
+int qisg_energies(qisg_handle *h, int64_t *A, int64_t *B) {
+  if (!h || !A || !B) return fail(QISG_EINVAL, "NULL argument");
+  int rc = h->layout == QISG_LAYOUT_LANES ? lanes_energies_by_slot(h) : samples_energies_by_slot(h);
+  if (rc) return rc;
+  const size_t n = (size_t)h->n_samples * h->n_rep * h->n_slots;
+  const size_t stride = (size_t)h->n_a_pad * h->n_rep * h->n_slots;
+  rc = cuda_check(cudaMemcpyAsync(A, h->d_out, n * 8, cudaMemcpyDeviceToHost, h->stream), "copy A");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(B, h->d_out + stride, n * 8, cudaMemcpyDeviceToHost, h->stream),
+                           "copy B");
+  if (!rc) rc = sync_handle(h);
+  return rc;
+}
+
+int qisg_overlaps(qisg_handle *h, int64_t *q) {
+  if (!h || !q) return fail(QISG_EINVAL, "NULL argument");
+  const int n_pairs = h->n_pairs();
+  if (n_pairs == 0) return QISG_OK;
+  int rc = h->layout == QISG_LAYOUT_LANES ? lanes_measure(h, 1) : samples_measure(h, 1);
+  if (rc) return rc;
+  const size_t n = (size_t)h->n_samples * h->n_slots * n_pairs;
+  rc = cuda_check(cudaMemcpyAsync(q, h->d_q, n * 8, cudaMemcpyDeviceToHost, h->stream), "copy q");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_q, 0, (size_t)h->n_a_pad * h->n_slots * n_pairs * 8, h->stream),
+                           "memset");
+  if (!rc) rc = sync_handle(h);
+  return rc;
+}
+
+int qisg_permutation(qisg_handle *h, int32_t *walker_at) {
+  if (!h || !walker_at) return fail(QISG_EINVAL, "NULL argument");
+  const size_t n = (size_t)h->n_samples * h->n_rep * h->n_slots;
+  int rc = cuda_check(cudaMemcpyAsync(walker_at, h->d_walker, n * 4, cudaMemcpyDeviceToHost, h->stream),
+                      "copy walker");
+  if (!rc) rc = sync_handle(h);
+  return rc;
+}
+
+int qisg_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
+  if (!h || (!S && n_a > 0)) return fail(QISG_EINVAL, "NULL argument");
+  if (a_lo < 0 || n_a < 0 || a_lo + n_a > h->n_samples) return fail(QISG_EINVAL, "sample range");
+  int rc = sync_handle(h);
+  if (rc) return rc;
+  return h->layout == QISG_LAYOUT_LANES ? lanes_get_spins(h, a_lo, n_a, S)
+                                        : samples_get_spins(h, a_lo, n_a, S);
+}
+
+int qisg_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J) {
+  if (!h || (!J && n_a > 0)) return fail(QISG_EINVAL, "NULL argument");
+  if (a_lo < 0 || n_a < 0 || a_lo + n_a > h->n_samples) return fail(QISG_EINVAL, "sample range");
+  int rc = sync_handle(h);
+  if (rc) return rc;
+  return h->layout == QISG_LAYOUT_LANES ? lanes_get_couplings(h, a_lo, n_a, J)
+                                        : samples_get_couplings(h, a_lo, n_a, J);
+}
+
+int qisg_set_couplings(qisg_handle *h, const int8_t *J) {
+  if (!h || !J) return fail(QISG_EINVAL, "NULL argument");
+  const int64_t n = h->n_samples * h->L * h->L * 2;
+  for (int64_t i = 0; i < n; ++i)
+    if (J[i] != 1 && J[i] != -1) return fail(QISG_EINVAL, "couplings must be +-1");
+  int rc = sync_handle(h);
+  if (!rc) rc = h->layout == QISG_LAYOUT_LANES ? lanes_set_couplings(h, J) : samples_set_couplings(h, J);
+  if (!rc) rc = recompute_energies(h);
+  if (!rc) rc = sync_handle(h);
+  return rc;
+}
+
+int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, uint64_t sweep) {
+  if (!h || !S || !walker_at) return fail(QISG_EINVAL, "NULL argument");
+  const int64_t rows = h->n_samples * h->n_rep;
+  std::vector<char> seen((size_t)h->n_slots);
+  for (int64_t c = 0; c < rows; ++c) {
+    std::fill(seen.begin(), seen.end(), 0);
+    for (int s = 0; s < h->n_slots; ++s) {
+      const int32_t w = walker_at[c * h->n_slots + s];
+      if (w < 0 || w >= h->n_slots || seen[(size_t)w]) return fail(QISG_ECORRUPT, "walker_at row is not a permutation");
+      seen[(size_t)w] = 1;
+    }
+  }
+  const int64_t nS = rows * h->n_slots * h->N;
+  for (int64_t i = 0; i < nS; ++i)
+    if (S[i] != 1 && S[i] != -1) return fail(QISG_ECORRUPT, "spins must be +-1");
+  int rc = sync_handle(h);
+  if (rc) return rc;
+  rc = h->layout == QISG_LAYOUT_LANES ? lanes_set_spins(h, S) : samples_set_spins(h, S);
+  if (rc) return rc;
+  // the permutation (padding lanes keep the identity)
+  std::vector<int32_t> wa((size_t)h->n_a_pad * h->n_rep * h->n_slots);
+  for (size_t i = 0; i < wa.size(); ++i) wa[i] = (int32_t)(i % h->n_slots);
+  std::memcpy(wa.data(), walker_at, (size_t)rows * h->n_slots * 4);
+  rc = cuda_check(cudaMemcpyAsync(h->d_walker, wa.data(), wa.size() * 4, cudaMemcpyHostToDevice, h->stream),
+                  "copy walker");
+  if (rc) return rc;
+  if (h->layout == QISG_LAYOUT_SAMPLES) {
+    // SAMPLES keeps the spins by slot: the host repacked S by slot above
+  }
+  unsigned long long tt = sweep;
+  rc = cuda_check(cudaMemcpyAsync(h->d_t, &tt, 8, cudaMemcpyHostToDevice, h->stream), "copy t");
+  const size_t n_cs = (size_t)h->n_a_pad * h->n_rep * h->n_slots;
+  const size_t qn = (size_t)h->n_a_pad * h->n_slots * (h->n_pairs() > 0 ? h->n_pairs() : 1);
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumA, 0, n_cs * 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumB, 0, n_cs * 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumq, 0, qn * 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumq2, 0, qn * 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_q, 0, qn * 8, h->stream), "memset");
+  if (!rc) rc = recompute_energies(h);
+  if (!rc) rc = sync_handle(h);
+  if (!rc) {
+    h->t = sweep;
+    h->n_meas = 0;
+  }
+  return rc;
+}
+
+int qisg_measurements(qisg_handle *h, int64_t *sumA, int64_t *sumB, int64_t *sumq, int64_t *sumq2,
+                      int64_t *n_meas) {
+  if (!h) return fail(QISG_EINVAL, "NULL handle");
+  int rc = QISG_OK;
+  const size_t ncs = (size_t)h->n_samples * h->n_rep * h->n_slots;
+  const size_t nq = (size_t)h->n_samples * h->n_slots * h->n_pairs();
+  if (sumA) rc = cuda_check(cudaMemcpyAsync(sumA, h->d_sumA, ncs * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+  if (!rc && sumB) rc = cuda_check(cudaMemcpyAsync(sumB, h->d_sumB, ncs * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+  if (!rc && sumq && nq) rc = cuda_check(cudaMemcpyAsync(sumq, h->d_sumq, nq * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+  if (!rc && sumq2 && nq) rc = cuda_check(cudaMemcpyAsync(sumq2, h->d_sumq2, nq * 8, cudaMemcpyDeviceToHost, h->stream), "copy");
+  if (!rc) rc = sync_handle(h);
+  if (!rc && n_meas) *n_meas = h->n_meas;
+  return rc;
+}
+
+int qisg_slot_means(qisg_handle *h, double *e_s, double *e_t, double *q2) {
+  if (!h || !e_s || !e_t || !q2) return fail(QISG_EINVAL, "NULL argument");
+  if (h->n_meas == 0) return fail(QISG_ESTATE, "no measurement taken yet");
+  const int n_pairs = h->n_pairs();
+  std::vector<int64_t> A((size_t)h->n_samples * h->n_rep * h->n_slots), B(A.size()),
+      Q2((size_t)h->n_samples * h->n_slots * (n_pairs > 0 ? n_pairs : 1), 0);
+  int rc = qisg_measurements(h, A.data(), B.data(), nullptr, n_pairs ? Q2.data() : nullptr, nullptr);
+  if (rc) return rc;
+  const double m = (double)h->n_meas, N = (double)h->N;
+  for (int s = 0; s < h->n_slots; ++s) {
+    double sa = 0.0, sb = 0.0, sq = 0.0;
+    for (int64_t a = 0; a < h->n_samples; ++a)
+      for (int r = 0; r < h->n_rep; ++r) {
+        sa += (double)A[((size_t)a * h->n_rep + r) * h->n_slots + s];
+        sb += (double)B[((size_t)a * h->n_rep + r) * h->n_slots + s];
+      }
+    for (int64_t a = 0; a < h->n_samples; ++a)
+      for (int p = 0; p < n_pairs; ++p) sq += (double)Q2[((size_t)a * h->n_slots + s) * n_pairs + p];
+    e_s[s] = sa / (m * (double)h->n_samples * (double)h->n_rep * 2.0 * N);
+    e_t[s] = sb / (m * (double)h->n_samples * (double)h->n_rep * N);
+    q2[s] = sq / (m * (double)h->n_samples * (double)(n_pairs > 0 ? n_pairs : 1) * N * N);
+  }
+  return QISG_OK;
+}
+
+int qisg_thresholds(qisg_handle *h, uint32_t *T) {
+  if (!h || !T) return fail(QISG_EINVAL, "NULL argument");
+  std::memcpy(T, h->T.data(), h->T.size() * 4);
+  return QISG_OK;
+}
+
+int qisg_sweep_count(qisg_handle *h, uint64_t *t) {
+  if (!h || !t) return fail(QISG_EINVAL, "NULL argument");
+  *t = h->t;
+  return QISG_OK;
+}
+
+int qisg_layout(qisg_handle *h, int *layout, int *word_bits) {
+  if (!h) return fail(QISG_EINVAL, "NULL handle");
+  if (layout) *layout = h->layout;
+  if (word_bits) *word_bits = h->W;
+  return QISG_OK;
+}
+
+int qisg_launch_count(qisg_handle *h, int64_t *n) {
+  if (!h || !n) return fail(QISG_EINVAL, "NULL argument");
+  *n = h->launches;
+  return QISG_OK;
+}
+
+int qisg_sync(qisg_handle *h) {
+  if (!h) return fail(QISG_EINVAL, "NULL handle");
+  return sync_handle(h);
+}
+
+void qisg_destroy(qisg_handle *h) {
+  if (!h) return;
+  if (h->stream || true) cudaStreamSynchronize(h->stream);
+  void *ptrs[] = {h->spins, h->J, h->d_T, h->d_bases, h->d_walker, h->d_U, h->d_sumA, h->d_sumB,
+                  h->d_sumq, h->d_sumq2, h->d_q, h->d_out, h->d_t, h->d_acc, h->d_err};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete h;
+}
+
+const char *qisg_strerror(int code) {
+  switch (code) {
+    case QISG_OK: return "ok";
+    case QISG_EINVAL: return "invalid argument";
+    case QISG_ENOMEM: return "out of device memory or over budget";
+    case QISG_ECUDA: return "CUDA error";
+    case QISG_ETIMEOUT: return "bounded device wait expired";
+    case QISG_ECORRUPT: return "corrupt state";
+    case QISG_ESTATE: return "call not valid in this state";
+    default: return "unknown error";
+  }
+}
+
+const char *qisg_last_error(void) { return g_last_error.c_str(); }
+
+int qisg_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                       void *cuda_stream) {
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(QISG_EINVAL, "bad arguments");
+  if (n == 0) return QISG_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  philox_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctr, key, out, n);
+  return cuda_check(cudaGetLastError(), "philox kernel");
+}
+
+}  // extern "C"

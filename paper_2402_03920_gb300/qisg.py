@@ -1,0 +1,277 @@
+"""Python binding of libqisg (ctypes; argument marshalling only).
+
+Every call here forwards to the C ABI of ``include/qisg.h``; every step of
+the sweep, PT and measurement path runs in the library's CUDA kernels.  The
+binding only converts numpy arrays and the torch stream into plain pointers.
+If the library cannot be loaded the import fails loudly: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build_lib
+
+QISG_LAYOUT_AUTO, QISG_LAYOUT_LANES, QISG_LAYOUT_SAMPLES = 0, 1, 2
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ECORRUPT", -6: "ESTATE"}
+
+
+class QisgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"QISG_{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Slot(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("k_tau", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("word_bits", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("mem_budget", ctypes.c_size_t), ("pt_every", ctypes.c_int),
+                ("measure_every", ctypes.c_int), ("layout", ctypes.c_int),
+                ("per_sample_launch", ctypes.c_int)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build_lib.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libqisg.so (building it first when asked and stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build_lib.build() if build_if_missing else _build_lib.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libqisg.so not found at {path}; run the build first")
+    lib = ctypes.CDLL(path)
+    P, I, I64, U64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    sig = {
+        "qisg_opts_default": (None, [P]),
+        "qisg_ladder_linear": (I, [D, D, I, D, P]),
+        "qisg_create": (I, [P, I, I, P, I, I, I64, U64, P]),
+        "qisg_sweep": (I, [P, I64]),
+        "qisg_pt_swap": (I, [P]),
+        "qisg_energies": (I, [P, P, P]),
+        "qisg_overlaps": (I, [P, P]),
+        "qisg_permutation": (I, [P, P]),
+        "qisg_get_spins": (I, [P, I64, I64, P]),
+        "qisg_get_couplings": (I, [P, I64, I64, P]),
+        "qisg_set_couplings": (I, [P, P]),
+        "qisg_set_state": (I, [P, P, P, U64]),
+        "qisg_measurements": (I, [P, P, P, P, P, P]),
+        "qisg_slot_means": (I, [P, P, P, P]),
+        "qisg_thresholds": (I, [P, P]),
+        "qisg_sweep_count": (I, [P, P]),
+        "qisg_layout": (I, [P, P, P]),
+        "qisg_launch_count": (I, [P, P]),
+        "qisg_sync": (I, [P]),
+        "qisg_destroy": (None, [P]),
+        "qisg_strerror": (ctypes.c_char_p, [I]),
+        "qisg_last_error": (ctypes.c_char_p, []),
+        "qisg_philox4x32_10": (I, [P, P, P, I64, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return ["qisg_opts_default", "qisg_ladder_linear", "qisg_create", "qisg_sweep", "qisg_pt_swap",
+            "qisg_energies", "qisg_overlaps", "qisg_permutation", "qisg_get_spins",
+            "qisg_get_couplings", "qisg_set_couplings", "qisg_set_state", "qisg_measurements",
+            "qisg_slot_means", "qisg_thresholds", "qisg_sweep_count", "qisg_layout",
+            "qisg_launch_count", "qisg_sync", "qisg_destroy", "qisg_strerror", "qisg_last_error",
+            "qisg_philox4x32_10"]
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load().qisg_last_error()
+        raise QisgError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def ladder_linear(lo: float, hi: float, n: int, gamma: float) -> np.ndarray:
+    """[n][2] array of (k, k_tau), k linear in [lo, hi], k_tau from
+    exp(-2 k_tau) = tanh(k Gamma)."""
+    arr = (Slot * n)()
+    _check(load().qisg_ladder_linear(lo, hi, n, gamma, ctypes.cast(arr, ctypes.c_void_p)))
+    return np.array([[s.k, s.k_tau] for s in arr], dtype=np.float64)
+
+
+def current_stream_ptr() -> int | None:
+    """cudaStream_t of torch's current stream (torch is used for streams only)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover - torch is optional for the binding
+        pass
+    return None
+
+
+@dataclass
+class Config:
+    L: int
+    L_tau: int
+    ladder: np.ndarray          # [n_slots][2] (k, k_tau)
+    n_replicas: int
+    n_samples: int
+    seed: int
+    word_bits: int = 0
+    pt_every: int = 1
+    measure_every: int = 0
+    layout: int = QISG_LAYOUT_AUTO
+    per_sample_launch: int = 0
+    mem_budget: int = 0
+
+
+class Instance:
+    """One qisg_handle: n_samples x n_replicas chains of an n_slots ladder."""
+
+    def __init__(self, cfg: Config, stream: int | None = None):
+        lib = load()
+        self.cfg = cfg
+        ladder = np.ascontiguousarray(cfg.ladder, dtype=np.float64)
+        self.n_slots = ladder.shape[0]
+        self.L, self.L_tau = cfg.L, cfg.L_tau
+        self.N = cfg.L * cfg.L * cfg.L_tau
+        self.n_rep, self.n_samples = cfg.n_replicas, cfg.n_samples
+        opts = Opts()
+        lib.qisg_opts_default(ctypes.byref(opts))
+        opts.word_bits = cfg.word_bits
+        opts.cuda_stream = stream if stream is not None else current_stream_ptr()
+        opts.mem_budget = cfg.mem_budget
+        opts.pt_every = cfg.pt_every
+        opts.measure_every = cfg.measure_every
+        opts.layout = cfg.layout
+        opts.per_sample_launch = cfg.per_sample_launch
+        self._h = ctypes.c_void_p()
+        _check(lib.qisg_create(ctypes.byref(self._h), cfg.L, cfg.L_tau, _ptr(ladder), self.n_slots,
+                               cfg.n_replicas, cfg.n_samples, cfg.seed, ctypes.byref(opts)))
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().qisg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- path --------------------------------------------------------------
+    def sweep(self, n: int = 1):
+        _check(load().qisg_sweep(self._h, n))
+
+    def pt_swap(self):
+        _check(load().qisg_pt_swap(self._h))
+
+    def sync(self):
+        _check(load().qisg_sync(self._h))
+
+    # -- results -----------------------------------------------------------
+    @property
+    def n_pairs(self) -> int:
+        return self.n_rep * (self.n_rep - 1) // 2
+
+    def energies(self):
+        A = np.zeros((self.n_samples, self.n_rep, self.n_slots), dtype=np.int64)
+        B = np.zeros_like(A)
+        _check(load().qisg_energies(self._h, _ptr(A), _ptr(B)))
+        return A, B
+
+    def overlaps(self) -> np.ndarray:
+        q = np.zeros((self.n_samples, self.n_slots, max(self.n_pairs, 1)), dtype=np.int64)
+        _check(load().qisg_overlaps(self._h, _ptr(q)))
+        return q[:, :, : self.n_pairs]
+
+    def permutation(self) -> np.ndarray:
+        wa = np.zeros((self.n_samples, self.n_rep, self.n_slots), dtype=np.int32)
+        _check(load().qisg_permutation(self._h, _ptr(wa)))
+        return wa
+
+    def spins(self, a_lo: int = 0, n_a: int | None = None) -> np.ndarray:
+        n_a = self.n_samples - a_lo if n_a is None else n_a
+        S = np.zeros((n_a, self.n_rep, self.n_slots, self.N), dtype=np.int8)
+        _check(load().qisg_get_spins(self._h, a_lo, n_a, _ptr(S)))
+        return S
+
+    def couplings(self, a_lo: int = 0, n_a: int | None = None) -> np.ndarray:
+        n_a = self.n_samples - a_lo if n_a is None else n_a
+        J = np.zeros((n_a, self.L * self.L, 2), dtype=np.int8)
+        _check(load().qisg_get_couplings(self._h, a_lo, n_a, _ptr(J)))
+        return J
+
+    def set_couplings(self, J: np.ndarray):
+        _check(load().qisg_set_couplings(self._h, _ptr(np.ascontiguousarray(J, dtype=np.int8))))
+
+    def set_state(self, S: np.ndarray, walker_at: np.ndarray, sweep: int):
+        _check(load().qisg_set_state(self._h, _ptr(np.ascontiguousarray(S, dtype=np.int8)),
+                                     _ptr(np.ascontiguousarray(walker_at, dtype=np.int32)), sweep))
+
+    def measurements(self):
+        ncs = (self.n_samples, self.n_rep, self.n_slots)
+        nq = (self.n_samples, self.n_slots, max(self.n_pairs, 1))
+        sA, sB = np.zeros(ncs, np.int64), np.zeros(ncs, np.int64)
+        sq, sq2 = np.zeros(nq, np.int64), np.zeros(nq, np.int64)
+        nm = ctypes.c_int64()
+        _check(load().qisg_measurements(self._h, _ptr(sA), _ptr(sB), _ptr(sq), _ptr(sq2),
+                                        ctypes.byref(nm)))
+        return sA, sB, sq[:, :, : self.n_pairs], sq2[:, :, : self.n_pairs], nm.value
+
+    def slot_means(self):
+        e_s, e_t, q2 = (np.zeros(self.n_slots) for _ in range(3))
+        _check(load().qisg_slot_means(self._h, _ptr(e_s), _ptr(e_t), _ptr(q2)))
+        return e_s, e_t, q2
+
+    def thresholds(self) -> np.ndarray:
+        T = np.zeros((self.n_slots, 5, 3), dtype=np.uint32)
+        _check(load().qisg_thresholds(self._h, _ptr(T)))
+        return T
+
+    def sweep_count(self) -> int:
+        t = ctypes.c_uint64()
+        _check(load().qisg_sweep_count(self._h, ctypes.byref(t)))
+        return t.value
+
+    def layout(self):
+        lay, wb = ctypes.c_int(), ctypes.c_int()
+        _check(load().qisg_layout(self._h, ctypes.byref(lay), ctypes.byref(wb)))
+        return lay.value, wb.value
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64()
+        _check(load().qisg_launch_count(self._h, ctypes.byref(n)))
+        return n.value
+
+
+def philox4x32_10_device(ctr_dev_ptr: int, key_dev_ptr: int, out_dev_ptr: int, n: int,
+                         stream: int | None = None):
+    """Device Philox on device buffers (pointers from torch tensors)."""
+    _check(load().qisg_philox4x32_10(ctr_dev_ptr, key_dev_ptr, out_dev_ptr, n, stream))
