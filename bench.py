@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the MCQSG hot path (checkerboard Metropolis + PT for the 2D
++-J quantum Ising spin glass in Trotter-Suzuki form) on one GB300.
+
+Workload: 32 disorder samples, L=16, L_tau=256, 4 replicas on a 16-slot PT
+ladder (k in [0.2, 0.5], Gamma = 1), PT every sweep, measurements every 10
+sweeps; synthetic +-J couplings from Philox.  One step = 10 sweeps (red
+half sweep, blue half sweep with energy counting, PT pass) plus one
+measurement, i.e. one pass over every step of the path.  The full workload
+is 10^4 sweeps = 1000 steps.
+
+Metric: ps per spin update (lower is better), for the batched form (one
+launch per half sweep for all samples) next to the per-instance form (one
+launch per sample per half sweep), both bit-exact with the oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+samples (weak scaling, no collective on the data path); the time is the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ps/spin-update, batched vs per-instance (bit-exact); % of INT/HBM roofline"
+UNIT = "ps/spin-update"
+SWEEPS_PER_STEP = 10
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--forms", default="batched,per_instance")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    from paper_2402_03920_gb300.workloads import PRODUCTION
+    return PRODUCTION
+
+
+def updates_per_step(w):
+    return w.n_samples * w.n_replicas * w.n_slots * w.L * w.L * w.L_tau * SWEEPS_PER_STEP
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def make_instance(qisg, w, form, seed):
+    ladder = qisg.ladder_linear(w.k_lo, w.k_hi, w.n_slots, w.gamma)
+    if form == "per_instance":
+        cfg = qisg.Config(w.L, w.L_tau, ladder, w.n_replicas, w.n_samples, seed, word_bits=64,
+                          measure_every=w.measure_every, layout=qisg.QISG_LAYOUT_LANES,
+                          per_sample_launch=1)
+    else:
+        cfg = qisg.Config(w.L, w.L_tau, ladder, w.n_replicas, w.n_samples, seed, word_bits=0,
+                          measure_every=w.measure_every, layout=batched_layout(qisg))
+    return qisg.Instance(cfg)
+
+
+def batched_layout(qisg):
+    return int(os.environ.get("QISG_BENCH_LAYOUT", qisg.QISG_LAYOUT_SAMPLES))
+
+
+def time_form(torch, qisg, w, form, steps, warmup, seed):
+    """Device time of `steps` steps (CUDA events on the library's stream,
+    L2 flushed between steps), plus live per-kernel timing."""
+    inst = make_instance(qisg, w, form, seed)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    for _ in range(warmup):
+        inst.sweep(SWEEPS_PER_STEP)
+    inst.sync()
+    torch.cuda.synchronize()
+    launches0 = inst.launch_count()
+    inst.profile(True)
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        inst.sweep(SWEEPS_PER_STEP)
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    launches = inst.launch_count() - launches0
+    kern = {}
+    for kind, name in ((qisg.KERNEL_SWEEP, "sweep"), (qisg.KERNEL_PT, "pt"),
+                       (qisg.KERNEL_MEASURE, "measure"), (qisg.KERNEL_PERMUTE, "permute")):
+        ms, nt, nl = inst.profile_read(kind)
+        kern[name] = {"ms": ms, "timed": nt, "launched": nl}
+    inst.profile(False)
+    layout, wb = inst.layout()
+    inst.close()
+    del flush
+    return total_ms, launches, kern, layout, wb
+
+
+def e2e_form(torch, qisg, w, form, steps, seed):
+    """End to end through the public API with host buffers: couplings and the
+    start state are uploaded from pinned host memory, every step reads the
+    measurement sums back; wall clock around all of it."""
+    from paper_2402_03920_gb300.workloads import random_spins
+    n_sys = w.n_samples * w.n_replicas * w.n_slots
+    J = torch.from_numpy(random_spins((w.n_samples, w.L * w.L, 2), seed)).pin_memory()
+    S = torch.from_numpy(random_spins((w.n_samples, w.n_replicas, w.n_slots, w.L * w.L * w.L_tau),
+                                      seed + 1)).pin_memory()
+    wa = torch.from_numpy(np.tile(np.arange(w.n_slots, dtype=np.int32),
+                                  (w.n_samples, w.n_replicas, 1))).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    inst = make_instance(qisg, w, form, seed)
+    inst.set_couplings(J.numpy())
+    inst.set_state(S.numpy(), wa.numpy(), 0)
+    d2h = 0
+    for _ in range(steps):
+        inst.sweep(SWEEPS_PER_STEP)
+        sA, sB, sq, sq2, nm = inst.measurements()
+        d2h += sA.nbytes + sB.nbytes + sq.nbytes + sq2.nbytes
+    A, B = inst.energies()
+    d2h += A.nbytes + B.nbytes
+    wall = time.perf_counter() - t0
+    inst.close()
+    h2d = J.numel() + S.numel() + 4 * wa.numel()
+    ps = wall * 1e12 / (updates_per_step(w) * steps)
+    return {"value": ps, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps, "n_sys": n_sys}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# Algorithmic integer operations per spin update (32-bit operations), per
+# packing: the shared-draw SAMPLES kernel spends about 40 word-wide logic
+# operations per word plus a quarter Philox call per (replica-group, slot,
+# site); the LANES kernel draws one Philox output per update.
+ALG_OPS = {"samples32": 40 / 32 + 50 / (4 * 32), "samples64": 80 / 64 + 50 / (4 * 64),
+           "lanes": 50 / 4 + 1.5}
+INT_LANES_PER_CLK_PER_SM = 128
+
+
+def roofline(kern, w, layout, wb, n_sm, pk, steps):
+    """Roofline of the half-sweep kernel from its live CUDA-event timing:
+    algorithmic integer operations per launch / average launch time."""
+    from paper_2402_03920_gb300 import qisg
+    sw = kern["sweep"]
+    if not sw["timed"] or not sw["launched"]:
+        return None
+    per_launch_ms = sw["ms"] / sw["timed"]
+    key = f"samples{wb}" if layout == qisg.QISG_LAYOUT_SAMPLES else "lanes"
+    ups_per_launch = updates_per_step(w) * steps / sw["launched"]
+    ops = ALG_OPS[key] * ups_per_launch
+    achieved = ops / (per_launch_ms * 1e-3) / 1e12
+    clk = pk.get("sm_max_mhz", 2070.0)
+    peak = n_sm * INT_LANES_PER_CLK_PER_SM * clk * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "half_sweep",
+            "ops_per_update": ALG_OPS[key], "updates_per_launch": ups_per_launch,
+            "avg_launch_us": per_launch_ms * 1e3}
+
+
+def cpu_baseline(w, budget_s=15.0):
+    """The oracle as it stands on the host cores: nproc samples of the same
+    workload, as many sweeps as fit in about budget_s seconds."""
+    import oracle
+    ncores = os.cpu_count() or 1
+    ladder_k, ladder_kt = oracle.ladder_linear(w.k_lo, w.k_hi, w.n_slots, w.gamma)
+    n_a = min(ncores, w.n_samples)
+    st = oracle.new_state(w.L, w.L_tau, ladder_k, ladder_kt, w.n_replicas, w.seed, 0, n_a)
+    t0 = time.perf_counter()
+    oracle.run(st, 1, 1, w.measure_every, n_threads=ncores)
+    one = time.perf_counter() - t0
+    sweeps = max(1, int(budget_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    oracle.run(st, sweeps, 1, w.measure_every, n_threads=ncores)
+    wall = time.perf_counter() - t0
+    ups = n_a * w.n_replicas * w.n_slots * w.L * w.L * w.L_tau * sweeps
+    return {"value": wall * 1e12 / ups, "unit": UNIT, "cores": min(ncores, n_a), "kind": "oracle",
+            "sample": f"{n_a} samples x {sweeps} sweeps of the workload ({wall:.1f} s)"}
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2402_03920_gb300 import qisg
+    qisg.load()
+    w = workload()
+    seed = w.seed + 1000 * rank
+    forms = [f for f in args.forms.split(",") if f]
+    results = {}
+    clocks = None
+    for form in forms:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as cs:
+            total_ms, launches, kern, layout, wb = time_form(torch, qisg, w, form, args.steps,
+                                                             args.warmup, seed)
+        if form == forms[0]:
+            clocks = cs.summary()
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        results[form] = (total_ms, launches, kern, layout, wb)
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    ups_total = updates_per_step(w) * args.steps * world
+    main = forms[0]
+    total_ms, launches, kern, layout, wb = results[main]
+    value = total_ms * 1e9 / ups_total
+    pk, pk_kind = peaks()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": f"u{wb} bit-packed spins (1 bit/spin), u32 Philox, f64 PT",
+        "data": "synthetic (+-J couplings and start spins from Philox)",
+        "config": {"workload": w.name, "L": w.L, "L_tau": w.L_tau, "n_samples": w.n_samples,
+                   "n_replicas": w.n_replicas, "n_slots": w.n_slots, "k": [w.k_lo, w.k_hi],
+                   "gamma": w.gamma, "sweeps_per_step": SWEEPS_PER_STEP,
+                   "measure_every": w.measure_every, "form": main,
+                   "layout": "SAMPLES" if layout == qisg.QISG_LAYOUT_SAMPLES else "LANES",
+                   "word_bits": wb,
+                   "l2": "flushed between steps (2x L2 buffer written); lattice fits in L2 within a step"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "kernels_ms": {k: v["ms"] for k, v in kern.items()},
+    }
+    for form in forms[1:]:
+        tm, ln, kn, lay, wbb = results[form]
+        line[form] = {"value": tm * 1e9 / ups_total, "unit": UNIT, "ms_per_step": tm / args.steps,
+                      "gpu_launches": ln,
+                      "layout": "SAMPLES" if lay == qisg.QISG_LAYOUT_SAMPLES else "LANES",
+                      "roofline": roofline(kn, w, lay, wbb, n_sm, pk, args.steps)}
+    rl = roofline(kern, w, layout, wb, n_sm, pk, args.steps)
+    if rl is not None:
+        rl["peak_source"] = f"{pk_kind}: {n_sm} SMs x {INT_LANES_PER_CLK_PER_SM} int32 lanes/clk x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"
+    line["roofline"] = rl
+    if not args.no_e2e:
+        line["e2e"] = e2e_form(torch, qisg, w, main, args.steps, seed)
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# --------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    w = workload()
+    ncores = os.cpu_count() or 1
+    k, kt = oracle.ladder_linear(w.k_lo, w.k_hi, w.n_slots, w.gamma)
+    n_a = min(ncores, w.n_samples)
+    st = oracle.new_state(w.L, w.L_tau, k, kt, w.n_replicas, w.seed, 0, n_a)
+    for _ in range(args.warmup):
+        oracle.run(st, 1, 1, w.measure_every, n_threads=ncores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(st, 1, 1, w.measure_every, n_threads=ncores)
+    wall = time.perf_counter() - t0
+    ups = n_a * w.n_replicas * w.n_slots * w.L * w.L * w.L_tau * args.steps
+    value = wall * 1e12 / ups
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "i8 spins, f64",
+            "data": "synthetic (+-J couplings and start spins from Philox)",
+            "config": {"workload": w.name, "L": w.L, "L_tau": w.L_tau, "n_samples": w.n_samples,
+                       "n_replicas": w.n_replicas, "n_slots": w.n_slots,
+                       "step": f"1 sweep of {n_a} samples (a bounded sample of the workload)"},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(ncores, n_a), "kind": "oracle",
+                             "sample": f"{n_a} samples x {args.steps} sweeps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

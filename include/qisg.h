@@ -188,6 +188,24 @@ int qisg_layout(qisg_handle *h, int *layout, int *word_bits);
 /* Kernel launches this handle has issued since creation (diagnostics). */
 int qisg_launch_count(qisg_handle *h, int64_t *n);
 
+/* Kernel kinds for qisg_profile_read. */
+#define QISG_KERNEL_SWEEP   0   /* the red and blue half-sweep kernels            */
+#define QISG_KERNEL_PT      1   /* the PT pass                                    */
+#define QISG_KERNEL_MEASURE 2   /* overlaps and measurement sums                  */
+#define QISG_KERNEL_PERMUTE 3   /* SAMPLES: moving spin bits after a PT pass       */
+
+/* Start (enable = 1, counters reset) or stop (0) timing every launch of the
+ * kernels above with CUDA events recorded on the handle's stream, around the
+ * launch, at most 65536 launches per kind (later launches are counted, not
+ * timed).  Diagnostics for roofline figures; off by default. */
+int qisg_profile(qisg_handle *h, int enable);
+
+/* Total device time (ms) of the timed launches of one kind, how many were
+ * timed and how many were launched since qisg_profile(h, 1).  Synchronises.
+ * EINVAL: unknown kind. */
+int qisg_profile_read(qisg_handle *h, int kind, double *total_ms, int64_t *n_timed,
+                      int64_t *n_launched);
+
 /* Block until the handle's stream is idle; reports any device error flag. */
 int qisg_sync(qisg_handle *h);
 

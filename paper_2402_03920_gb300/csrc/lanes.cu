@@ -375,15 +375,19 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   }
   if (h->per_sample_launch) {
     for (int64_t a = 0; a < h->n_samples; ++a) {
+      const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
       lanes_half_sweep_kernel<Word><<<dim3((unsigned)blocks, 1), kBlock, smem, h->stream>>>(
           p, colour, count_only, a);
+      prof_end(h, QISG_KERNEL_SWEEP, tok);
       h->launches++;
     }
   } else {
     for (int64_t a0 = 0; a0 < h->n_samples; a0 += 65535) {
       const int64_t na = std::min<int64_t>(65535, h->n_samples - a0);
+      const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
       lanes_half_sweep_kernel<Word><<<dim3((unsigned)blocks, (unsigned)na), kBlock, smem, h->stream>>>(
           p, colour, count_only, a0);
+      prof_end(h, QISG_KERNEL_SWEEP, tok);
       h->launches++;
     }
   }
@@ -398,10 +402,12 @@ int measure_t(qisg_handle *h, int force_to_q) {
     const size_t smem = (size_t)n_pairs * 8;
     for (int64_t a0 = 0; a0 < h->n_samples; a0 += 65535) {
       const int64_t na = std::min<int64_t>(65535, h->n_samples - a0);
+      const int tok = prof_begin(h, QISG_KERNEL_MEASURE);
       lanes_overlap_kernel<Word><<<dim3((unsigned)chunks, (unsigned)h->n_slots, (unsigned)na), kBlock,
                                    smem, h->stream>>>(reinterpret_cast<const Word *>(h->spins),
                                                       h->d_walker, h->d_q, a0, h->N, h->n_rep,
                                                       h->n_slots, h->rpw, h->n_groups);
+      prof_end(h, QISG_KERNEL_MEASURE, tok);
       h->launches++;
     }
   }
@@ -448,16 +454,20 @@ int lanes_pt(qisg_handle *h, int explicit_pass) {
   const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
   if (h->per_sample_launch) {
     for (int64_t a = 0; a < h->n_samples; ++a) {
+      const int tok = prof_begin(h, QISG_KERNEL_PT);
       lanes_pt_kernel<<<(unsigned)((h->n_rep + 127) / 128), 128, 0, h->stream>>>(
           h->d_walker, h->d_U, h->d_bases, h->d_t, key, a, 1, h->n_rep, h->n_slots, h->N,
           explicit_pass);
+      prof_end(h, QISG_KERNEL_PT, tok);
       h->launches++;
     }
   } else {
     const int64_t n = h->n_samples * h->n_rep;
+    const int tok = prof_begin(h, QISG_KERNEL_PT);
     lanes_pt_kernel<<<(unsigned)((n + 127) / 128), 128, 0, h->stream>>>(
         h->d_walker, h->d_U, h->d_bases, h->d_t, key, 0, h->n_samples, h->n_rep, h->n_slots, h->N,
         explicit_pass);
+    prof_end(h, QISG_KERNEL_PT, tok);
     h->launches++;
   }
   return cuda_check(cudaGetLastError(), "lanes pt");

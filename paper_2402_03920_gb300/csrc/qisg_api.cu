@@ -30,6 +30,38 @@ int cuda_check(cudaError_t e, const char *what) {
   return QISG_ECUDA;
 }
 
+constexpr int kProfMax = 65536;
+
+int prof_begin(qisg_handle *h, int kind) {
+  if (!h->prof) return -1;
+  h->prof_launched[kind]++;
+  std::vector<cudaEvent_t> &v = h->prof_ev[kind];
+  if ((int)v.size() >= 2 * kProfMax) return -1;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return -1;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return -1;
+  }
+  cudaEventRecord(a, h->stream);
+  v.push_back(a);
+  v.push_back(b);
+  return (int)v.size() - 1;
+}
+
+void prof_end(qisg_handle *h, int kind, int tok) {
+  if (tok < 0) return;
+  cudaEventRecord(h->prof_ev[kind][(size_t)tok], h->stream);
+}
+
+void prof_clear(qisg_handle *h) {
+  for (int k = 0; k < 4; ++k) {
+    for (cudaEvent_t e : h->prof_ev[k]) cudaEventDestroy(e);
+    h->prof_ev[k].clear();
+    h->prof_launched[k] = 0;
+  }
+}
+
 __global__ void advance_kernel(unsigned long long *d_t) { *d_t += 1ull; }
 
 int advance_counter(qisg_handle *h) {
@@ -397,7 +429,7 @@ int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, ui
     if (S[i] != 1 && S[i] != -1) return fail(QISG_ECORRUPT, "spins must be +-1");
   int rc = sync_handle(h);
   if (rc) return rc;
-  rc = h->layout == QISG_LAYOUT_LANES ? lanes_set_spins(h, S) : samples_set_spins(h, S);
+  rc = h->layout == QISG_LAYOUT_LANES ? lanes_set_spins(h, S) : samples_set_spins(h, S, walker_at);
   if (rc) return rc;
   // the permutation (padding lanes keep the identity)
   std::vector<int32_t> wa((size_t)h->n_a_pad * h->n_rep * h->n_slots);
@@ -406,9 +438,6 @@ int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, ui
   rc = cuda_check(cudaMemcpyAsync(h->d_walker, wa.data(), wa.size() * 4, cudaMemcpyHostToDevice, h->stream),
                   "copy walker");
   if (rc) return rc;
-  if (h->layout == QISG_LAYOUT_SAMPLES) {
-    // SAMPLES keeps the spins by slot: the host repacked S by slot above
-  }
   unsigned long long tt = sweep;
   rc = cuda_check(cudaMemcpyAsync(h->d_t, &tt, 8, cudaMemcpyHostToDevice, h->stream), "copy t");
   const size_t n_cs = (size_t)h->n_a_pad * h->n_rep * h->n_slots;
@@ -492,6 +521,34 @@ int qisg_launch_count(qisg_handle *h, int64_t *n) {
   return QISG_OK;
 }
 
+int qisg_profile(qisg_handle *h, int enable) {
+  if (!h) return fail(QISG_EINVAL, "NULL handle");
+  int rc = sync_handle(h);
+  if (rc) return rc;
+  if (enable) prof_clear(h);
+  h->prof = enable != 0;
+  return QISG_OK;
+}
+
+int qisg_profile_read(qisg_handle *h, int kind, double *total_ms, int64_t *n_timed,
+                      int64_t *n_launched) {
+  if (!h || kind < 0 || kind > 3) return fail(QISG_EINVAL, "bad handle or kind");
+  int rc = sync_handle(h);
+  if (rc) return rc;
+  double tot = 0.0;
+  const std::vector<cudaEvent_t> &v = h->prof_ev[kind];
+  for (size_t i = 0; i + 1 < v.size(); i += 2) {
+    float ms = 0.f;
+    rc = cuda_check(cudaEventElapsedTime(&ms, v[i], v[i + 1]), "event elapsed");
+    if (rc) return rc;
+    tot += ms;
+  }
+  if (total_ms) *total_ms = tot;
+  if (n_timed) *n_timed = (int64_t)(v.size() / 2);
+  if (n_launched) *n_launched = h->prof_launched[kind];
+  return QISG_OK;
+}
+
 int qisg_sync(qisg_handle *h) {
   if (!h) return fail(QISG_EINVAL, "NULL handle");
   return sync_handle(h);
@@ -504,6 +561,7 @@ void qisg_destroy(qisg_handle *h) {
                   h->d_sumq, h->d_sumq2, h->d_q, h->d_out, h->d_t, h->d_acc, h->d_err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  prof_clear(h);
   delete h;
 }
 

@@ -117,6 +117,11 @@ struct qisg_handle {
   int *d_err = nullptr;
   size_t device_bytes = 0;
 
+  // launch timing (qisg_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev[4];   // start/stop pairs per kernel kind
+  int64_t prof_launched[4] = {0, 0, 0, 0};
+
   int n_pairs() const { return n_rep * (n_rep - 1) / 2; }
 };
 
@@ -144,11 +149,16 @@ int samples_pt(qisg_handle *h, int explicit_pass);
 int samples_measure(qisg_handle *h, int force_to_q);
 int samples_energies_by_slot(qisg_handle *h);
 int samples_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S);
-int samples_set_spins(qisg_handle *h, const int8_t *S);
+int samples_set_spins(qisg_handle *h, const int8_t *S, const int32_t *walker_at);
 int samples_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J);
 int samples_set_couplings(qisg_handle *h, const int8_t *J);
 
 // common small kernels (qisg_api.cu)
 int advance_counter(qisg_handle *h);
+
+// Launch timing: call prof_begin(h, kind) before and prof_end(h, kind, tok)
+// after a kernel launch on h->stream.
+int prof_begin(qisg_handle *h, int kind);
+void prof_end(qisg_handle *h, int kind, int tok);
 
 }  // namespace qisg

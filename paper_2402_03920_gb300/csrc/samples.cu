@@ -1,15 +1,798 @@
-// SAMPLES packing (placeholder until the multi-sample kernels land).
+// SAMPLES packing: a word of W = 32 or 64 bits holds W disorder samples
+// (lane l = sample a - b*W of sample block b) at one (replica, slot).  This
+// is Ito-Kanada's multi-sample multispin coding (Sec. 2.1.1): all lanes of a
+// word see the same ladder slot, so they share one Metropolis table row and
+// one draw R (the draw is keyed on the 64-sample block a >> 6).  The local
+// energy class (u_s, u_t) of every lane is computed with bit-sliced adders;
+// a mux tree over the class bits selects the per-class reject flags.
+//
+// Because a word is one slot, a PT exchange between slots s and s+1 of a
+// sample (Sec. 2.1) moves that sample's bits between the two slot words; the
+// walker labels are tracked alongside so results are reported by walker.
+//
+// Device arrays (N = L*L*L_tau, n_q = ceil(n_rep / 4), r = 4q + j):
+//   spins  Word [b][s][q][site][4]    bit = 1 <=> spin -1
+//   J      Word [b][x + L*y][2]       bit = 1 <=> J = -1
+//   U      u64 [a][r][s][2]           unsatisfied spatial / tau bonds, by slot
+//   acc    Word [b][r][s]             PT accept masks of the last pass
+#include <algorithm>
+#include <cstring>
+
 #include "qisg_internal.cuh"
 
 namespace qisg {
-static int nyi() { return fail(QISG_EINVAL, "SAMPLES packing not built yet"); }
-int samples_init(qisg_handle *) { return nyi(); }
-int samples_half_sweep(qisg_handle *, int, int) { return nyi(); }
-int samples_pt(qisg_handle *, int) { return nyi(); }
-int samples_measure(qisg_handle *, int) { return nyi(); }
-int samples_energies_by_slot(qisg_handle *) { return nyi(); }
-int samples_get_spins(qisg_handle *, int64_t, int64_t, int8_t *) { return nyi(); }
-int samples_set_spins(qisg_handle *, const int8_t *) { return nyi(); }
-int samples_get_couplings(qisg_handle *, int64_t, int64_t, int8_t *) { return nyi(); }
-int samples_set_couplings(qisg_handle *, const int8_t *) { return nyi(); }
+namespace {
+
+constexpr int kBlock = 256;          // 64 quads of 4 replicas
+constexpr int kQuads = kBlock / 4;
+constexpr int kMaxSlotsPermute = 32;
+constexpr int kKs = 11;              // per-thread planes: u_s sum <= 4 * 256 sites
+constexpr int kKt = 10;              // per-thread planes: u_t sum <= 2 * 256 sites
+constexpr int kMaxSitesPerThread = 256;
+
+template <typename Word>
+__device__ __forceinline__ Word ones_if(bool b) {
+  return b ? ~Word(0) : Word(0);
+}
+
+// sel ? a : b, bitwise
+template <typename Word>
+__device__ __forceinline__ Word mux(Word sel, Word a, Word b) {
+  return (sel & a) | (~sel & b);
+}
+
+template <typename Word>
+__device__ __forceinline__ Word maj3(Word a, Word b, Word c) {
+  return (a & b) | (c & (a ^ b));
+}
+
+// Bit-sliced per-lane counter: plane p holds bit p of every lane's count.
+template <typename Word, int K>
+struct VCount {
+  Word p[K];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < K; ++i) p[i] = 0;
+  }
+  // add x0 + 2 x1 + 4 x2 (per lane)
+  __device__ __forceinline__ void add3(Word x0, Word x1, Word x2) {
+    Word c = p[0] & x0;
+    p[0] ^= x0;
+    Word s = p[1] ^ x1 ^ c;
+    c = maj3(p[1], x1, c);
+    p[1] = s;
+    s = p[2] ^ x2 ^ c;
+    c = maj3(p[2], x2, c);
+    p[2] = s;
+#pragma unroll
+    for (int i = 3; i < K; ++i) {
+      const Word t = p[i] & c;
+      p[i] ^= c;
+      c = t;
+    }
+  }
+  // add x0 + 2 x1
+  __device__ __forceinline__ void add2(Word x0, Word x1) {
+    Word c = p[0] & x0;
+    p[0] ^= x0;
+    const Word s = p[1] ^ x1 ^ c;
+    c = maj3(p[1], x1, c);
+    p[1] = s;
+#pragma unroll
+    for (int i = 2; i < K; ++i) {
+      const Word t = p[i] & c;
+      p[i] ^= c;
+      c = t;
+    }
+  }
+  // add x (one bit per lane)
+  __device__ __forceinline__ void add1(Word x) {
+    Word c = x;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const Word t = p[i] & c;
+      p[i] ^= c;
+      c = t;
+    }
+  }
+};
+
+template <typename Word>
+__device__ __forceinline__ Word shfl_xor_w(Word v, int m) {
+  if (sizeof(Word) == 8) {
+    const unsigned long long u = (unsigned long long)v;
+    const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)u, m);
+    const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(u >> 32), m);
+    return (Word)(((unsigned long long)hi << 32) | lo);
+  }
+  return (Word)__shfl_xor_sync(0xffffffffu, (unsigned)v, m);
+}
+
+template <typename Word>
+__device__ __forceinline__ Word shfl_w(Word v, int src) {
+  if (sizeof(Word) == 8) {
+    const unsigned long long u = (unsigned long long)v;
+    const unsigned lo = __shfl_sync(0xffffffffu, (unsigned)u, src);
+    const unsigned hi = __shfl_sync(0xffffffffu, (unsigned)(u >> 32), src);
+    return (Word)(((unsigned long long)hi << 32) | lo);
+  }
+  return (Word)__shfl_sync(0xffffffffu, (unsigned)v, src);
+}
+
+// Sum a per-thread counter over the warp threads that share (lane % G) and
+// add each of the W lanes' totals into acc[key][lane] (shared memory).
+// K planes per thread; the warp total needs up to K + 5 planes.  Every
+// thread of the warp must call this (full-mask shuffles).
+template <typename Word, int K, int G>
+__device__ __forceinline__ void flush_counter(const VCount<Word, K> &c, int *acc) {
+  constexpr int KT = K + 5;
+  constexpr int W = (int)sizeof(Word) * 8;
+  Word tot[KT];
+#pragma unroll
+  for (int i = 0; i < KT; ++i) tot[i] = i < K ? c.p[i] : Word(0);
+#pragma unroll
+  for (int off = G; off < 32; off <<= 1) {
+    Word carry = 0;
+#pragma unroll
+    for (int i = 0; i < KT; ++i) {
+      const Word o = shfl_xor_w(tot[i], off);
+      const Word s = tot[i] ^ o ^ carry;
+      carry = maj3(tot[i], o, carry);
+      tot[i] = s;
+    }
+  }
+  // thread t extracts lanes l = t / G + m * (32 / G) of key t % G from the
+  // totals held (identically) by every thread with that key
+  const int t = threadIdx.x & 31;
+  const int key = t % G;
+  Word mine[KT];
+#pragma unroll
+  for (int i = 0; i < KT; ++i) mine[i] = shfl_w(tot[i], key);
+  constexpr int per = W * G / 32;
+#pragma unroll
+  for (int m = 0; m < per; ++m) {
+    const int lane = t / G + m * (32 / G);
+    int v = 0;
+#pragma unroll
+    for (int i = 0; i < KT; ++i) v |= (int)((mine[i] >> lane) & 1u) << i;
+    if (v) atomicAdd(&acc[key * W + lane], v);
+  }
+}
+
+template <typename Word>
+struct SamplesArgs {
+  Word *spins;
+  const Word *J;
+  const uint32_t *T;
+  unsigned long long *U;
+  const unsigned long long *d_t;
+  uint2 key;
+  int64_t N, half_N;
+  int L, Lt, n_slots, n_rep, n_q, W;
+  int groups_per_quad;   // site groups (4 sites) each quad handles
+  int blocks_per_set;    // blocks per (b, s, q) word set
+};
+
+// Reject flags of the 9 classes that can reject: rho = all ones iff the
+// class's threshold is not the always-accept sentinel and R >= T.
+template <typename Word>
+__device__ __forceinline__ Word rho(uint32_t R, uint32_t T) {
+  return ones_if<Word>(T != 0xFFFFFFFFu && R >= T);
+}
+
+// One half sweep.  Block: one (b, s, q) word set, 64 quads; quad thread j
+// owns replica r = 4q + j.  Per group of 4 sites every thread of a quad
+// computes one Philox call (for site 4G + j), which serves the four
+// replicas of that site; the results are exchanged in shared memory.
+template <typename Word, bool BLUE>
+__global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<Word> p, int colour,
+                                                                    int count_only) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  __shared__ uint4 rnd[kBlock];
+  __shared__ uint32_t Ts[15];
+  __shared__ int accU[BLUE ? 2 * 4 * W : 1];
+
+  const int64_t set = blockIdx.x / p.blocks_per_set;
+  const int chunk = (int)(blockIdx.x - set * p.blocks_per_set);
+  const int q = (int)(set % p.n_q);
+  const int s = (int)((set / p.n_q) % p.n_slots);
+  const int64_t b = set / ((int64_t)p.n_q * p.n_slots);
+  const int j = threadIdx.x & 3;
+  const int quad = threadIdx.x >> 2;
+  const int r = 4 * q + j;
+
+  if (threadIdx.x < 15) Ts[threadIdx.x] = p.T[s * 15 + threadIdx.x];
+  if (BLUE)
+    for (int i = threadIdx.x; i < 2 * 4 * W; i += blockDim.x) accU[i] = 0;
+  __syncthreads();
+
+  uint32_t T[15];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) T[i] = Ts[i];
+
+  const int L = p.L, Lt = p.Lt;
+  const int64_t plane = (int64_t)L * L;
+  Word *base = p.spins + ((b * p.n_slots + s) * p.n_q + q) * p.N * 4;
+  const Word *Jb = p.J + b * plane * 2;
+  const unsigned long long t = *p.d_t;
+  const uint32_t ctr_z = (uint32_t)s | ((uint32_t)(r >> 2) << 16);
+  const uint32_t ctr_w = (DOM_SWEEP << 28) | (uint32_t)((b * W) >> 6);
+
+  VCount<Word, kKs> cs;
+  VCount<Word, kKt> ct;
+  if (BLUE) {
+    cs.zero();
+    ct.zero();
+  }
+
+  const int64_t n_groups = p.half_N >> 2;
+  for (int gi = 0; gi < p.groups_per_quad; ++gi) {
+    const int64_t G = ((int64_t)chunk * p.groups_per_quad + gi) * kQuads + quad;
+    const bool live = G < n_groups;   // uniform per quad
+    // one Philox per thread: site 4G + j of this colour
+    if (live) {
+      const SiteXYT c = site_of_colour(4 * G + j, L, colour);
+      const int64_t site = c.x + (int64_t)L * c.y + plane * c.tau;
+      rnd[threadIdx.x] = philox(make_uint4((uint32_t)site, (uint32_t)t, ctr_z, ctr_w), p.key);
+    }
+    __syncwarp();
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint4 rv = rnd[(quad << 2) + i];
+        const uint32_t R = pick4(rv, j);
+        const SiteXYT c = site_of_colour(4 * G + i, L, colour);
+        const int xp = c.x + 1 == L ? 0 : c.x + 1, xm = c.x == 0 ? L - 1 : c.x - 1;
+        const int yp = c.y + 1 == L ? 0 : c.y + 1, ym = c.y == 0 ? L - 1 : c.y - 1;
+        const int tp = c.tau + 1 == Lt ? 0 : c.tau + 1, tm = c.tau == 0 ? Lt - 1 : c.tau - 1;
+        const int64_t off_t = plane * c.tau;
+        const int64_t i2 = c.x + (int64_t)L * c.y;
+        const int64_t site = i2 + off_t;
+        const Word sc = base[site * 4 + j];
+        const Word b1 = sc ^ base[(xp + (int64_t)L * c.y + off_t) * 4 + j] ^ Jb[i2 * 2];
+        const Word b2 = sc ^ base[(xm + (int64_t)L * c.y + off_t) * 4 + j] ^ Jb[(xm + (int64_t)L * c.y) * 2];
+        const Word b3 = sc ^ base[(c.x + (int64_t)L * yp + off_t) * 4 + j] ^ Jb[i2 * 2 + 1];
+        const Word b4 = sc ^ base[(c.x + (int64_t)L * ym + off_t) * 4 + j] ^ Jb[(c.x + (int64_t)L * ym) * 2 + 1];
+        const Word t1 = sc ^ base[(i2 + plane * tp) * 4 + j];
+        const Word t2 = sc ^ base[(i2 + plane * tm) * 4 + j];
+        // bit-sliced u_s (3 bits) and u_t (2 bits)
+        const Word s1 = b1 ^ b2 ^ b3;
+        const Word c1 = maj3(b1, b2, b3);
+        const Word us0 = s1 ^ b4;
+        const Word c2 = s1 & b4;
+        const Word us1 = c1 ^ c2;
+        const Word us2 = c1 & c2;
+        const Word ut0 = t1 ^ t2;
+        const Word ut1 = t1 & t2;
+        // reject mask: mux tree over (u_t, u_s) of the per-class flags;
+        // classes with u_s >= 2 and u_t >= 1 always accept
+        Word rej;
+        if (count_only) {
+          rej = ~Word(0);
+        } else {
+          const Word row0 = mux(us2, rho<Word>(R, T[12]),
+                                mux(us1, mux(us0, rho<Word>(R, T[9]), rho<Word>(R, T[6])),
+                                    mux(us0, rho<Word>(R, T[3]), rho<Word>(R, T[0]))));
+          const Word low = ~(us1 | us2);
+          const Word row1 = low & mux(us0, rho<Word>(R, T[4]), rho<Word>(R, T[1]));
+          const Word row2 = low & mux(us0, rho<Word>(R, T[5]), rho<Word>(R, T[2]));
+          rej = mux(ut1, row2, mux(ut0, row1, row0));
+        }
+        const Word flip = ~rej;
+        if (!count_only) base[site * 4 + j] = sc ^ flip;
+        if (BLUE) {
+          // unsatisfied counts after the flip: u -> 4 - u (spatial), 2 - u (tau)
+          const Word vs1 = us1 ^ (flip & us0);
+          const Word vs2 = mux(flip, ~(us0 | us1 | us2), us2);
+          const Word vt1 = mux(flip, ~(ut0 | ut1), ut1);
+          cs.add3(us0, vs1, vs2);
+          ct.add2(ut0, vt1);
+        }
+      }
+    }
+    __syncwarp();
+  }
+
+  if (BLUE) {
+    flush_counter<Word, kKs, 4>(cs, accU);
+    flush_counter<Word, kKt, 4>(ct, accU + 4 * W);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * W; i += blockDim.x) {
+      const int jj = i / W, lane = i - jj * W;
+      const int rr = 4 * q + jj;
+      if (rr >= p.n_rep) continue;
+      const int64_t a = b * W + lane;
+      unsigned long long *u = p.U + ((a * p.n_rep + rr) * p.n_slots + s) * 2;
+      if (accU[i]) atomicAdd(u, (unsigned long long)accU[i]);
+      if (accU[4 * W + i]) atomicAdd(u + 1, (unsigned long long)accU[4 * W + i]);
+    }
+  }
+}
+
+__global__ void zero_u64_kernel(unsigned long long *p, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0;
+}
+
+// PT pass of chain (a, r), energies by slot.  Threads of a warp are 32
+// consecutive samples of one (b, r); the accept flags of pair s become the
+// lane masks acc[b][r][s] through a ballot.
+template <typename Word>
+__global__ void samples_pt_kernel(int32_t *walker, unsigned long long *U, Word *acc,
+                                  const double *bases, const unsigned long long *d_t, uint2 key,
+                                  int64_t n_samples, int n_rep, int n_slots, int64_t n_b,
+                                  int explicit_pass) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= n_b * n_rep * W) return;   // whole warps (W multiple of 32)
+  const int lane = (int)(gid % W);
+  const int r = (int)((gid / W) % n_rep);
+  const int64_t b = gid / ((int64_t)W * n_rep);
+  const int64_t a = b * W + lane;
+  const bool real = a < n_samples;
+  const unsigned long long t = explicit_pass ? *d_t - 1ull : *d_t;
+  int32_t *wa = walker + (a * n_rep + r) * n_slots;
+  unsigned long long *Ua = U + (a * n_rep + r) * n_slots * 2;
+  const double *ap = bases, *am = bases + n_slots, *bp = bases + 2 * n_slots,
+               *bm = bases + 3 * n_slots;
+  Word *accw = acc + (b * n_rep + r) * n_slots;
+  unsigned long long usX = real ? Ua[0] : 0, utX = real ? Ua[1] : 0;
+  for (int s = 0; s + 1 < n_slots; ++s) {
+    bool accept = false;
+    unsigned long long usY = 0, utY = 0;
+    if (real) {
+      usY = Ua[2 * (s + 1)];
+      utY = Ua[2 * (s + 1) + 1];
+      // m = A_Y - A_X with A = 2N - 2 U_s; n likewise with B = N - 2 U_t
+      const long long m = -2 * ((long long)usY - (long long)usX);
+      const long long n = -2 * ((long long)utY - (long long)utX);
+      const double fa = pow_rn(m >= 0 ? ap[s] : am[s], (unsigned long long)(m >= 0 ? m : -m));
+      const double fb = pow_rn(n >= 0 ? bp[s] : bm[s], (unsigned long long)(n >= 0 ? n : -n));
+      const double P = __dmul_rn(fa, fb);
+      const uint4 x = philox(make_uint4((uint32_t)s, (uint32_t)t, (uint32_t)a,
+                                        (DOM_PT << 28) | (uint32_t)(r >> 2)),
+                             key);
+      const double u = __dmul_rn((double)pick4(x, r & 3), 0x1p-32);
+      accept = u < P;
+    }
+    if (accept) {
+      const int32_t X = wa[s];
+      wa[s] = wa[s + 1];
+      wa[s + 1] = X;
+      // the configuration from s+1 now sits at s: its energies move with it,
+      // and the one from s carries on to be compared at s+1
+      Ua[2 * s] = usY;
+      Ua[2 * s + 1] = utY;
+      Ua[2 * (s + 1)] = usX;
+      Ua[2 * (s + 1) + 1] = utX;
+    } else {
+      usX = usY;
+      utX = utY;
+    }
+    const unsigned m32 = __ballot_sync(0xffffffffu, accept);
+    if ((threadIdx.x & 31) == 0) {
+      if (W == 64)
+        reinterpret_cast<unsigned *>(&accw[s])[(lane >> 5)] = m32;
+      else
+        accw[s] = (Word)m32;
+    }
+  }
+}
+
+// Apply the PT pass to the spins: for pair s = 0 .. n_slots-2 in order,
+// exchange the bits of accepting lanes between slot words s and s+1.
+template <typename Word>
+__global__ void __launch_bounds__(kBlock) samples_permute_kernel(Word *spins, const Word *acc, int64_t N,
+                                                                 int n_slots, int n_q, int n_rep,
+                                                                 int blocks_per_set) {
+  __shared__ Word accs[4 * kMaxSlotsPermute];
+  const int64_t set = blockIdx.x / blocks_per_set;     // (b, q)
+  const int chunk = (int)(blockIdx.x - set * blocks_per_set);
+  const int q = (int)(set % n_q);
+  const int64_t b = set / n_q;
+  for (int i = threadIdx.x; i < 4 * n_slots; i += blockDim.x) {
+    const int jj = i / n_slots, s = i - jj * n_slots;
+    const int rr = 4 * q + jj;
+    accs[jj * kMaxSlotsPermute + s] = rr < n_rep ? acc[(b * n_rep + rr) * n_slots + s] : Word(0);
+  }
+  __syncthreads();
+  const int64_t idx = (int64_t)chunk * blockDim.x + threadIdx.x;   // (site, j)
+  if (idx >= N * 4) return;
+  const int jj = (int)(idx & 3);
+  const int64_t stride = (int64_t)n_q * N * 4;
+  Word *w0 = spins + ((b * n_slots) * n_q + q) * N * 4 + idx;
+  Word w[kMaxSlotsPermute];
+#pragma unroll
+  for (int s = 0; s < kMaxSlotsPermute; ++s)
+    if (s < n_slots) w[s] = w0[s * stride];
+#pragma unroll
+  for (int s = 0; s + 1 < kMaxSlotsPermute; ++s)
+    if (s + 1 < n_slots) {
+      const Word x = (w[s] ^ w[s + 1]) & accs[jj * kMaxSlotsPermute + s];
+      w[s] ^= x;
+      w[s + 1] ^= x;
+    }
+#pragma unroll
+  for (int s = 0; s < kMaxSlotsPermute; ++s)
+    if (s < n_slots) w0[s * stride] = w[s];
+}
+
+// Overlaps (Appendix E.1) at slot s for replica pair p: per-lane number of
+// sites where the two configurations differ, accumulated into qcnt[a][s][p].
+template <typename Word>
+__global__ void __launch_bounds__(kBlock) samples_overlap_kernel(const Word *spins, long long *qcnt,
+                                                                 int64_t N, int n_slots, int n_q,
+                                                                 int n_rep, int64_t n_samples,
+                                                                 int sites_per_thread) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  __shared__ int acc[W];
+  const int n_pairs = n_rep * (n_rep - 1) / 2;
+  const int p = blockIdx.y % n_pairs;
+  const int s = (blockIdx.y / n_pairs) % n_slots;
+  const int64_t b = blockIdx.y / ((int64_t)n_pairs * n_slots);
+  int r1 = 0, r2 = 1, k = 0;
+  for (int x = 0; x < n_rep; ++x)
+    for (int y = x + 1; y < n_rep; ++y, ++k)
+      if (k == p) {
+        r1 = x;
+        r2 = y;
+      }
+  for (int i = threadIdx.x; i < W; i += blockDim.x) acc[i] = 0;
+  __syncthreads();
+  const Word *w1 = spins + ((b * n_slots + s) * n_q + (r1 >> 2)) * N * 4 + (r1 & 3);
+  const Word *w2 = spins + ((b * n_slots + s) * n_q + (r2 >> 2)) * N * 4 + (r2 & 3);
+  VCount<Word, 8> c;
+  c.zero();
+  const int64_t start = (int64_t)blockIdx.x * blockDim.x * sites_per_thread + threadIdx.x;
+  for (int k2 = 0; k2 < sites_per_thread; ++k2) {
+    const int64_t site = start + (int64_t)k2 * blockDim.x;
+    if (site < N) c.add1(w1[site * 4] ^ w2[site * 4]);
+  }
+  flush_counter<Word, 8, 1>(c, acc);
+  __syncthreads();
+  for (int i = threadIdx.x; i < W; i += blockDim.x) {
+    const int64_t a = b * W + i;
+    if (a < n_samples && acc[i])
+      atomicAdd(reinterpret_cast<unsigned long long *>(&qcnt[(a * n_slots + s) * n_pairs + p]),
+                (unsigned long long)acc[i]);
+  }
+}
+
+__global__ void samples_finalize_kernel(const unsigned long long *U, long long *qcnt, long long *sumA,
+                                        long long *sumB, long long *sumq, long long *sumq2,
+                                        int64_t n_a, int n_rep, int n_slots, int64_t N,
+                                        int to_q_only) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_a * n_slots) return;
+  const int64_t a = c / n_slots;
+  const int s = (int)(c % n_slots);
+  const int n_pairs = n_rep * (n_rep - 1) / 2;
+  if (to_q_only) {
+    for (int p = 0; p < n_pairs; ++p) {
+      long long *qc = &qcnt[(a * n_slots + s) * n_pairs + p];
+      *qc = N - 2 * *qc;
+    }
+    return;
+  }
+  for (int r = 0; r < n_rep; ++r) {
+    const unsigned long long *u = U + ((a * n_rep + r) * n_slots + s) * 2;
+    sumA[(a * n_rep + r) * n_slots + s] += 2 * N - 2 * (long long)u[0];
+    sumB[(a * n_rep + r) * n_slots + s] += N - 2 * (long long)u[1];
+  }
+  for (int p = 0; p < n_pairs; ++p) {
+    long long *qc = &qcnt[(a * n_slots + s) * n_pairs + p];
+    const long long qv = N - 2 * *qc;
+    sumq[(a * n_slots + s) * n_pairs + p] += qv;
+    sumq2[(a * n_slots + s) * n_pairs + p] += qv * qv;
+    *qc = 0;
+  }
+}
+
+__global__ void samples_by_slot_kernel(const unsigned long long *U, long long *out, int64_t n, int64_t stride,
+                                       int64_t N) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  out[c] = 2 * N - 2 * (long long)U[2 * c];
+  out[stride + c] = N - 2 * (long long)U[2 * c + 1];
+}
+
+template <typename Word>
+__global__ void samples_init_J_kernel(Word *J, int64_t n_b, int L, uint2 key) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // (b, i2, dir)
+  const int64_t plane = (int64_t)L * L;
+  if (c >= n_b * plane * 2) return;
+  const uint32_t dir = (uint32_t)(c & 1);
+  const uint32_t i2 = (uint32_t)((c >> 1) % plane);
+  const int64_t b = (c >> 1) / plane;
+  Word v = 0;
+  for (int l = 0; l < W; ++l) {
+    const uint4 x = philox(make_uint4(i2, dir, (uint32_t)(b * W + l), DOM_J << 28), key);
+    if (!(x.x & 1u)) v |= Word(1) << l;
+  }
+  J[c] = v;
+}
+
+template <typename Word>
+__global__ void samples_init_spins_kernel(Word *spins, int64_t total, int64_t N, int n_slots, int n_q,
+                                          uint2 key) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // [b][s][q][site][j]
+  if (c >= total) return;
+  const int jj = (int)(c & 3);
+  const int64_t site = (c >> 2) % N;
+  const int64_t bsq = (c >> 2) / N;
+  const int q = (int)(bsq % n_q);
+  const int s = (int)((bsq / n_q) % n_slots);
+  const int64_t b = bsq / ((int64_t)n_q * n_slots);
+  const uint32_t r = (uint32_t)(4 * q + jj);
+  Word v = 0;
+  // walker w starts at slot w: the word of slot s holds walker s
+  for (int l = 0; l < W; ++l) {
+    const uint4 x = philox(make_uint4((uint32_t)site, (uint32_t)s, (uint32_t)(b * W + l),
+                                      (DOM_INIT << 28) | r),
+                           key);
+    if (!(x.x & 1u)) v |= Word(1) << l;
+  }
+  spins[c] = v;
+}
+
+// Unpack samples a_lo .. a_lo+n_a-1 by walker into int8 +-1.
+template <typename Word>
+__global__ void samples_extract_kernel(const Word *spins, const int32_t *walker, int8_t *out, int64_t a_lo,
+                                       int64_t n_a, int64_t N, int n_slots, int n_q, int n_rep) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // [ai][r][s][site]
+  if (c >= n_a * n_rep * n_slots * N) return;
+  const int64_t site = c % N;
+  const int s = (int)((c / N) % n_slots);
+  const int r = (int)((c / (N * n_slots)) % n_rep);
+  const int64_t ai = c / (N * n_slots * n_rep);
+  const int64_t a = a_lo + ai;
+  const int64_t b = a / W;
+  const int lane = (int)(a - b * W);
+  const Word v = spins[(((b * n_slots + s) * n_q + (r >> 2)) * N + site) * 4 + (r & 3)];
+  const int w = walker[(a * n_rep + r) * n_slots + s];
+  out[((ai * n_rep + r) * n_slots + w) * N + site] = ((v >> lane) & 1u) ? -1 : 1;
+}
+
+template <typename Word>
+SamplesArgs<Word> make_args(qisg_handle *h) {
+  SamplesArgs<Word> p;
+  p.spins = reinterpret_cast<Word *>(h->spins);
+  p.J = reinterpret_cast<const Word *>(h->J);
+  p.T = h->d_T;
+  p.U = h->d_U;
+  p.d_t = h->d_t;
+  p.key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  p.N = h->N;
+  p.half_N = h->N / 2;
+  p.L = h->L;
+  p.Lt = h->Lt;
+  p.n_slots = h->n_slots;
+  p.n_rep = h->n_rep;
+  p.n_q = h->n_q;
+  p.W = h->W;
+  // site groups of one word set, spread so that the grid fills the GPU:
+  // at least ~4 blocks per SM, at most kMaxSitesPerThread sites per thread
+  const int64_t n_groups = p.half_N / 4;
+  const int64_t sets = h->n_b * h->n_slots * h->n_q;
+  int gpq = (int)std::min<int64_t>(kMaxSitesPerThread / 4, (n_groups + kQuads - 1) / kQuads);
+  const int64_t want_blocks = 4LL * std::max(1, h->n_sm);
+  while (gpq > 1 && sets * ((n_groups + (int64_t)kQuads * gpq - 1) / ((int64_t)kQuads * gpq)) < want_blocks)
+    gpq >>= 1;
+  p.groups_per_quad = std::max(1, gpq);
+  p.blocks_per_set = (int)((n_groups + (int64_t)kQuads * p.groups_per_quad - 1) /
+                           ((int64_t)kQuads * p.groups_per_quad));
+  return p;
+}
+
+template <typename Word>
+int half_sweep_t(qisg_handle *h, int colour, int count_only) {
+  SamplesArgs<Word> p = make_args<Word>(h);
+  const int64_t sets = h->n_b * h->n_slots * h->n_q;
+  const int64_t blocks = sets * p.blocks_per_set;
+  if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+  if (colour == 0) {
+    const int64_t n = h->n_a_pad * h->n_rep * h->n_slots * 2;
+    zero_u64_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, h->stream>>>(h->d_U, n);
+    h->launches++;
+  }
+  const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
+  if (colour == 1)
+    samples_half_sweep_kernel<Word, true><<<(unsigned)blocks, kBlock, 0, h->stream>>>(p, 1, count_only);
+  else
+    samples_half_sweep_kernel<Word, false><<<(unsigned)blocks, kBlock, 0, h->stream>>>(p, 0, count_only);
+  prof_end(h, QISG_KERNEL_SWEEP, tok);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "samples half sweep");
+}
+
+template <typename Word>
+int pt_t(qisg_handle *h, int explicit_pass) {
+  const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  const int64_t n = h->n_b * h->n_rep * h->W;
+  int tok = prof_begin(h, QISG_KERNEL_PT);
+  samples_pt_kernel<Word><<<(unsigned)((n + 127) / 128), 128, 0, h->stream>>>(
+      h->d_walker, h->d_U, reinterpret_cast<Word *>(h->d_acc), h->d_bases, h->d_t, key, h->n_samples,
+      h->n_rep, h->n_slots, h->n_b, explicit_pass);
+  prof_end(h, QISG_KERNEL_PT, tok);
+  h->launches++;
+  int rc = cuda_check(cudaGetLastError(), "samples pt");
+  if (rc) return rc;
+  const int64_t per_set = (h->N * 4 + kBlock - 1) / kBlock;
+  const int64_t blocks = h->n_b * h->n_q * per_set;
+  tok = prof_begin(h, QISG_KERNEL_PERMUTE);
+  samples_permute_kernel<Word><<<(unsigned)blocks, kBlock, 0, h->stream>>>(
+      reinterpret_cast<Word *>(h->spins), reinterpret_cast<const Word *>(h->d_acc), h->N, h->n_slots,
+      h->n_q, h->n_rep, (int)per_set);
+  prof_end(h, QISG_KERNEL_PERMUTE, tok);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "samples permute");
+}
+
+template <typename Word>
+int measure_t(qisg_handle *h, int force_to_q) {
+  const int n_pairs = h->n_pairs();
+  if (n_pairs > 0) {
+    const int spt = 16;
+    const int64_t bx = (h->N + (int64_t)kBlock * spt - 1) / ((int64_t)kBlock * spt);
+    const int64_t by = h->n_b * h->n_slots * n_pairs;
+    if (by > 65535) return fail(QISG_EINVAL, "too many (block, slot, pair) sets for one launch");
+    const int tok = prof_begin(h, QISG_KERNEL_MEASURE);
+    samples_overlap_kernel<Word><<<dim3((unsigned)bx, (unsigned)by), kBlock, 0, h->stream>>>(
+        reinterpret_cast<const Word *>(h->spins), h->d_q, h->N, h->n_slots, h->n_q, h->n_rep,
+        h->n_samples, spt);
+    prof_end(h, QISG_KERNEL_MEASURE, tok);
+    h->launches++;
+  }
+  const int64_t n = h->n_samples * h->n_slots;
+  samples_finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+      h->d_U, h->d_q, h->d_sumA, h->d_sumB, h->d_sumq, h->d_sumq2, h->n_samples, h->n_rep,
+      h->n_slots, h->N, force_to_q);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "samples measure");
+}
+
+template <typename Word>
+int init_t(qisg_handle *h) {
+  const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  const int64_t nJ = h->n_b * h->L * h->L * 2;
+  samples_init_J_kernel<Word><<<(unsigned)((nJ + 255) / 256), 256, 0, h->stream>>>(
+      reinterpret_cast<Word *>(h->J), h->n_b, h->L, key);
+  const int64_t total = h->n_b * h->n_slots * h->n_q * h->N * 4;
+  if ((total + 255) / 256 > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large");
+  samples_init_spins_kernel<Word><<<(unsigned)((total + 255) / 256), 256, 0, h->stream>>>(
+      reinterpret_cast<Word *>(h->spins), total, h->N, h->n_slots, h->n_q, key);
+  h->launches += 2;
+  return cuda_check(cudaGetLastError(), "samples init");
+}
+
+template <typename Word>
+int get_spins_t(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
+  const int64_t n = n_a * h->n_rep * h->n_slots * h->N;
+  if (n == 0) return QISG_OK;
+  int8_t *d = nullptr;
+  int rc = cuda_check(cudaMalloc(&d, (size_t)n), "cudaMalloc");
+  if (rc) return rc;
+  samples_extract_kernel<Word><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+      reinterpret_cast<const Word *>(h->spins), h->d_walker, d, a_lo, n_a, h->N, h->n_slots, h->n_q,
+      h->n_rep);
+  rc = cuda_check(cudaGetLastError(), "extract");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(S, d, (size_t)n, cudaMemcpyDeviceToHost, h->stream), "copy");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  cudaFree(d);
+  return rc;
+}
+
+template <typename Word>
+int set_spins_t(qisg_handle *h, const int8_t *S, const int32_t *walker_at) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  const size_t words = (size_t)h->n_b * h->n_slots * h->n_q * h->N * 4;
+  std::vector<Word> buf(words, Word(0));
+  for (int64_t a = 0; a < h->n_samples; ++a) {
+    const int64_t b = a / W;
+    const Word bit = Word(1) << (a - b * W);
+    for (int r = 0; r < h->n_rep; ++r)
+      for (int s = 0; s < h->n_slots; ++s) {
+        const int w = walker_at[(a * h->n_rep + r) * h->n_slots + s];
+        const int8_t *src = S + ((a * h->n_rep + r) * h->n_slots + w) * h->N;
+        Word *dst = buf.data() + (((b * h->n_slots + s) * h->n_q + (r >> 2)) * h->N) * 4 + (r & 3);
+        for (int64_t i = 0; i < h->N; ++i)
+          if (src[i] == -1) dst[i * 4] |= bit;
+      }
+  }
+  int rc = cuda_check(cudaMemcpyAsync(h->spins, buf.data(), words * sizeof(Word), cudaMemcpyHostToDevice,
+                                      h->stream),
+                      "copy spins");
+  if (rc) return rc;
+  return cuda_check(cudaStreamSynchronize(h->stream), "sync");
+}
+
+template <typename Word>
+int get_couplings_t(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  const int64_t plane = (int64_t)h->L * h->L;
+  std::vector<Word> buf((size_t)h->n_b * plane * 2);
+  int rc = cuda_check(cudaMemcpyAsync(buf.data(), h->J, buf.size() * sizeof(Word), cudaMemcpyDeviceToHost,
+                                      h->stream),
+                      "copy J");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  if (rc) return rc;
+  for (int64_t ai = 0; ai < n_a; ++ai) {
+    const int64_t a = a_lo + ai, b = a / W;
+    const int lane = (int)(a - b * W);
+    for (int64_t i = 0; i < plane; ++i)
+      for (int d = 0; d < 2; ++d)
+        J[(ai * plane + i) * 2 + d] = ((buf[(size_t)((b * plane + i) * 2 + d)] >> lane) & 1u) ? -1 : 1;
+  }
+  return QISG_OK;
+}
+
+template <typename Word>
+int set_couplings_t(qisg_handle *h, const int8_t *J) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  const int64_t plane = (int64_t)h->L * h->L;
+  std::vector<Word> buf((size_t)h->n_b * plane * 2);
+  int rc = cuda_check(cudaMemcpyAsync(buf.data(), h->J, buf.size() * sizeof(Word), cudaMemcpyDeviceToHost,
+                                      h->stream),
+                      "copy J");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  if (rc) return rc;
+  for (int64_t a = 0; a < h->n_samples; ++a) {
+    const int64_t b = a / W;
+    const Word bit = Word(1) << (a - b * W);
+    for (int64_t i = 0; i < plane; ++i)
+      for (int d = 0; d < 2; ++d) {
+        Word &v = buf[(size_t)((b * plane + i) * 2 + d)];
+        v = (J[(a * plane + i) * 2 + d] == -1) ? (v | bit) : (v & ~bit);
+      }
+  }
+  rc = cuda_check(cudaMemcpyAsync(h->J, buf.data(), buf.size() * sizeof(Word), cudaMemcpyHostToDevice,
+                                  h->stream),
+                  "copy J");
+  if (rc) return rc;
+  return cuda_check(cudaStreamSynchronize(h->stream), "sync");
+}
+
+}  // namespace
+
+int samples_init(qisg_handle *h) {
+  if (h->n_slots > kMaxSlotsPermute) return fail(QISG_EINVAL, "SAMPLES packing supports up to 32 slots");
+  return h->W == 64 ? init_t<unsigned long long>(h) : init_t<unsigned int>(h);
+}
+int samples_half_sweep(qisg_handle *h, int colour, int count_only) {
+  return h->W == 64 ? half_sweep_t<unsigned long long>(h, colour, count_only)
+                    : half_sweep_t<unsigned int>(h, colour, count_only);
+}
+int samples_pt(qisg_handle *h, int explicit_pass) {
+  return h->W == 64 ? pt_t<unsigned long long>(h, explicit_pass) : pt_t<unsigned int>(h, explicit_pass);
+}
+int samples_measure(qisg_handle *h, int force_to_q) {
+  return h->W == 64 ? measure_t<unsigned long long>(h, force_to_q) : measure_t<unsigned int>(h, force_to_q);
+}
+int samples_energies_by_slot(qisg_handle *h) {
+  const int64_t n = h->n_samples * h->n_rep * h->n_slots;
+  const int64_t stride = h->n_a_pad * h->n_rep * h->n_slots;
+  samples_by_slot_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->d_U, h->d_out, n, stride, h->N);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "samples energies");
+}
+int samples_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
+  return h->W == 64 ? get_spins_t<unsigned long long>(h, a_lo, n_a, S)
+                    : get_spins_t<unsigned int>(h, a_lo, n_a, S);
+}
+int samples_set_spins(qisg_handle *h, const int8_t *S, const int32_t *walker_at) {
+  return h->W == 64 ? set_spins_t<unsigned long long>(h, S, walker_at)
+                    : set_spins_t<unsigned int>(h, S, walker_at);
+}
+int samples_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J) {
+  return h->W == 64 ? get_couplings_t<unsigned long long>(h, a_lo, n_a, J)
+                    : get_couplings_t<unsigned int>(h, a_lo, n_a, J);
+}
+int samples_set_couplings(qisg_handle *h, const int8_t *J) {
+  return h->W == 64 ? set_couplings_t<unsigned long long>(h, J) : set_couplings_t<unsigned int>(h, J);
+}
+
 }  // namespace qisg

@@ -17,6 +17,7 @@ import numpy as np
 from . import _build_lib
 
 QISG_LAYOUT_AUTO, QISG_LAYOUT_LANES, QISG_LAYOUT_SAMPLES = 0, 1, 2
+KERNEL_SWEEP, KERNEL_PT, KERNEL_MEASURE, KERNEL_PERMUTE = 0, 1, 2, 3
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ECORRUPT", -6: "ESTATE"}
 
 
@@ -78,6 +79,8 @@ def load(build_if_missing: bool = True):
         "qisg_strerror": (ctypes.c_char_p, [I]),
         "qisg_last_error": (ctypes.c_char_p, []),
         "qisg_philox4x32_10": (I, [P, P, P, I64, P]),
+        "qisg_profile": (I, [P, I]),
+        "qisg_profile_read": (I, [P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -94,7 +97,7 @@ def exported_symbols():
             "qisg_get_couplings", "qisg_set_couplings", "qisg_set_state", "qisg_measurements",
             "qisg_slot_means", "qisg_thresholds", "qisg_sweep_count", "qisg_layout",
             "qisg_launch_count", "qisg_sync", "qisg_destroy", "qisg_strerror", "qisg_last_error",
-            "qisg_philox4x32_10"]
+            "qisg_philox4x32_10", "qisg_profile", "qisg_profile_read"]
 
 
 def _check(rc: int):
@@ -264,6 +267,16 @@ class Instance:
         lay, wb = ctypes.c_int(), ctypes.c_int()
         _check(load().qisg_layout(self._h, ctypes.byref(lay), ctypes.byref(wb)))
         return lay.value, wb.value
+
+    def profile(self, enable: bool):
+        _check(load().qisg_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self, kind: int):
+        """(total ms, launches timed, launches) of one kernel kind."""
+        ms, nt, nl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().qisg_profile_read(self._h, kind, ctypes.byref(ms), ctypes.byref(nt),
+                                        ctypes.byref(nl)))
+        return ms.value, nt.value, nl.value
 
     def launch_count(self) -> int:
         n = ctypes.c_int64()

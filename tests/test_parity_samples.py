@@ -1,0 +1,157 @@
+"""GPU parity of the SAMPLES packing (one word = 32 or 64 samples at one
+replica x slot, shared draw) against the CPU oracle and against the LANES
+packing, through the C ABI."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.gpu_util import assert_same_state, make, need_gpu, oracle_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qisg():
+    need_gpu()
+    from paper_2402_03920_gb300 import qisg as q
+    q.load()
+    return q
+
+
+@pytest.mark.parametrize("L,Lt,n_slots,n_rep,W,n_samples", [
+    (4, 8, 8, 4, 32, 32),      # one full 32-sample word
+    (2, 4, 4, 4, 32, 5),       # the enumeration lattice, mostly padding lanes
+    (6, 6, 5, 3, 64, 70),      # two 64-sample words, the second ragged; padded replica
+    (4, 10, 9, 5, 32, 40),     # two replica groups (5 = 4 + 1)
+    (8, 4, 16, 2, 64, 64),
+])
+def test_small_geometries_bit_exact(qisg, L, Lt, n_slots, n_rep, W, n_samples):
+    inst, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 0.9, n_rep, n_samples, 3 + L, word_bits=W,
+                        layout=qisg.QISG_LAYOUT_SAMPLES, measure_every=4)
+    st = oracle_state(ladder, L, Lt, n_rep, 3 + L, 0, n_samples)
+    with inst:
+        assert inst.layout() == (qisg.QISG_LAYOUT_SAMPLES, W)
+        assert_same_state(inst, st, what="start")
+        for n in (1, 3, 28):
+            inst.sweep(n)
+            oracle.run(st, n, pt_every=1, measure_every=4)
+            assert_same_state(inst, st, what=f"L={L} Lt={Lt} W={W} after {st.t}")
+        sA, sB, sq, sq2, nm = inst.measurements()
+        assert nm == st.n_meas
+        assert np.array_equal(sA, st.sumA) and np.array_equal(sB, st.sumB)
+        if n_rep > 1:
+            assert np.array_equal(sq, st.sumq) and np.array_equal(sq2, st.sumq2)
+
+
+def test_samples_equals_lanes(qisg):
+    """Two packings, one trajectory: the result does not depend on how the
+    systems are packed into words."""
+    kw = dict(measure_every=5)
+    a, _ = make(qisg, 8, 16, 0.2, 0.5, 16, 1.0, 4, 33, 12, layout=qisg.QISG_LAYOUT_SAMPLES,
+                word_bits=64, **kw)
+    b, _ = make(qisg, 8, 16, 0.2, 0.5, 16, 1.0, 4, 33, 12, layout=qisg.QISG_LAYOUT_LANES,
+                word_bits=64, **kw)
+    with a, b:
+        a.sweep(40)
+        b.sweep(40)
+        assert np.array_equal(a.permutation(), b.permutation())
+        assert np.array_equal(a.spins(), b.spins())
+        for x, y in zip(a.energies(), b.energies()):
+            assert np.array_equal(x, y)
+        ma, mb = a.measurements(), b.measurements()
+        for x, y in zip(ma, mb):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+        assert np.array_equal(a.overlaps(), b.overlaps())
+
+
+def test_explicit_pt_and_resume(qisg):
+    a, _ = make(qisg, 6, 8, 0.25, 0.45, 6, 1.0, 4, 40, 4, layout=qisg.QISG_LAYOUT_SAMPLES)
+    b, _ = make(qisg, 6, 8, 0.25, 0.45, 6, 1.0, 4, 40, 4, layout=qisg.QISG_LAYOUT_SAMPLES, pt_every=0)
+    with a, b:
+        for _ in range(8):
+            a.sweep(1)
+            b.sweep(1)
+            b.pt_swap()
+        assert np.array_equal(a.spins(), b.spins())
+        assert np.array_equal(a.permutation(), b.permutation())
+        S, wa, t = a.spins(), a.permutation(), a.sweep_count()
+        a.sweep(7)
+        c, _ = make(qisg, 6, 8, 0.25, 0.45, 6, 1.0, 4, 40, 4, layout=qisg.QISG_LAYOUT_SAMPLES)
+        with c:
+            c.set_state(S, wa, t)
+            c.sweep(7)
+            assert np.array_equal(a.spins(), c.spins())
+            assert np.array_equal(a.permutation(), c.permutation())
+
+
+def test_arbitrary_state_against_oracle(qisg):
+    from paper_2402_03920_gb300.workloads import random_permutations, random_spins
+    L, Lt, n_slots, n_rep, n_a = 4, 6, 7, 4, 36
+    inst, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 1.1, n_rep, n_a, 8,
+                        layout=qisg.QISG_LAYOUT_SAMPLES, word_bits=32)
+    J = random_spins((n_a, L * L, 2), 4)
+    S = random_spins((n_a, n_rep, n_slots, L * L * Lt), 5)
+    wa = random_permutations(n_a * n_rep, n_slots, 6).reshape(n_a, n_rep, n_slots)
+    st = oracle_state(ladder, L, Lt, n_rep, 8, 0, n_a)
+    st.J, st.S, st.walker_at, st.t = J.copy(), S.copy(), wa.copy(), 5
+    oracle.refresh_energies(st)
+    with inst:
+        inst.set_couplings(J)
+        inst.set_state(S, wa, 5)
+        assert np.array_equal(inst.couplings(), J)
+        assert_same_state(inst, st, what="after set_state")
+        inst.sweep(12)
+        oracle.run(st, 12)
+        assert_same_state(inst, st, what="after 12 sweeps")
+
+
+def test_production_shape_batched_sampled(qisg):
+    """32 samples, L=16, L_tau=256, 16 slots, in the batched form the
+    benchmark times (SAMPLES, 32-bit words): samples 0 and 31 replayed by
+    the oracle, all samples against the per-instance LANES form."""
+    from paper_2402_03920_gb300.workloads import PRODUCTION as w
+    a, ladder = make(qisg, w.L, w.L_tau, w.k_lo, w.k_hi, w.n_slots, w.gamma, w.n_replicas,
+                     w.n_samples, w.seed, layout=qisg.QISG_LAYOUT_SAMPLES,
+                     measure_every=w.measure_every)
+    b, _ = make(qisg, w.L, w.L_tau, w.k_lo, w.k_hi, w.n_slots, w.gamma, w.n_replicas,
+                w.n_samples, w.seed, word_bits=64, layout=qisg.QISG_LAYOUT_LANES,
+                per_sample_launch=1, measure_every=w.measure_every)
+    with a, b:
+        assert a.layout() == (qisg.QISG_LAYOUT_SAMPLES, 32)
+        a.sweep(6)
+        for s in (0, 31):
+            st = oracle_state(ladder, w.L, w.L_tau, w.n_replicas, w.seed, s, 1)
+            oracle.run(st, 6, measure_every=w.measure_every)
+            assert_same_state(a, st, a_lo=s, what=f"sample {s}")
+        a.sweep(24)
+        b.sweep(30)
+        assert np.array_equal(a.permutation(), b.permutation())
+        assert np.array_equal(a.energies()[0], b.energies()[0])
+        assert np.array_equal(a.energies()[1], b.energies()[1])
+        ma, mb = a.measurements(), b.measurements()
+        for x, y in zip(ma, mb):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_batched_full_size_sampled(qisg):
+    """1024 samples x 4 replicas x 32 slots, L=24, L_tau=512 (4.8 GB of
+    packed spins): 8 samples chosen by a fixed seed are replayed by the
+    oracle for 2 sweeps."""
+    from paper_2402_03920_gb300.workloads import BATCHED as w
+    inst, ladder = make(qisg, w.L, w.L_tau, w.k_lo, w.k_hi, w.n_slots, w.gamma, w.n_replicas,
+                        w.n_samples, w.seed, word_bits=64, layout=qisg.QISG_LAYOUT_SAMPLES)
+    picks = sorted(np.random.default_rng(2024).choice(w.n_samples, size=8, replace=False).tolist())
+    from concurrent.futures import ThreadPoolExecutor
+
+    def replay(s):
+        st = oracle_state(ladder, w.L, w.L_tau, w.n_replicas, w.seed, s, 1)
+        return oracle.run(st, 2, n_threads=1)
+
+    with inst:
+        inst.sweep(2)
+        with ThreadPoolExecutor(max_workers=8) as ex:
+            states = list(ex.map(replay, picks))
+        for s, st in zip(picks, states):
+            assert_same_state(inst, st, a_lo=s, what=f"sample {s}")
