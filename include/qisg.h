@@ -223,6 +223,38 @@ const char *qisg_last_error(void);
 int qisg_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
                        void *cuda_stream);
 
+/* Replica overlaps of a caller-owned configuration, computed without
+ * allocating device memory.  (The paper has no counterpart: this is a
+ * deployment aid.)  It serves callers that cannot call cudaMalloc -- a host
+ * whose allocator owns all device memory under a fixed budget, a serving loop
+ * that must not stall on the device-wide synchronisation an allocation can
+ * cause -- by counting in a scratch array compiled into the library (a
+ * static __device__ array of QISG_NOALLOC_MAX_COUNTS 64-bit counters, 2 MiB,
+ * which every GPU that loads the library holds until the process exits).
+ *
+ *   spins  DEVICE pointer to the SAMPLES packing: words of word_bits (32 or
+ *          64) bits, [b][s][q][site][4] with b = sample / word_bits,
+ *          q = replica / 4, the last index replica % 4, site = x + L*y +
+ *          L*L*tau, bit (sample % word_bits) set <=> spin -1; b runs over
+ *          ceil(n_samples / word_bits) blocks, q over ceil(n_replicas / 4).
+ *          Each word at [..][s][..] holds the configuration now at slot s.
+ *   q      DEVICE pointer, int64 [n_samples][n_slots][n_pairs], written with
+ *          q = sum_i S^{r1}_i S^{r2}_i for pairs r1 < r2 in lexicographic
+ *          order (the quantity qisg_overlaps reports).
+ *   cuda_stream  cudaStream_t the work is ordered on (NULL: legacy default).
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture.  The call allocates nothing (no cudaMalloc, no cudaFree, no
+ * allocating library routine).  All calls share the scratch array, which
+ * keeps the last call's counts; each call clears the part it uses first.
+ * Calls that overlap on the GPU race on the array: serialise them.
+ * EINVAL: NULL pointer, word_bits not 32/64, L or L_tau odd or < 2,
+ *   n_replicas < 2, or n_samples * n_slots * n_pairs > QISG_NOALLOC_MAX_COUNTS.
+ * Asynchronous: errors of the kernels themselves surface at the next sync. */
+#define QISG_NOALLOC_MAX_COUNTS (1 << 18)
+int qisg_overlaps_noalloc(const void *spins, int word_bits, int L, int L_tau, int n_slots,
+                          int n_replicas, int64_t n_samples, int64_t *q, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
