@@ -70,6 +70,18 @@ def updates_per_step(w):
     return w.n_samples * w.n_replicas * w.n_slots * w.L * w.L * w.L_tau * SWEEPS_PER_STEP
 
 
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Weak scaling: every rank simulates its own disorder samples (a seed
+    of its own), the same amount of work per rank."""
+    return base_seed + 1000 * rank
+
+
+def job_value(max_ms_over_ranks: float, updates_per_rank: int, world: int) -> float:
+    """ps per spin update of the whole job: the slowest rank's time over the
+    updates all ranks did."""
+    return max_ms_over_ranks * 1e9 / (updates_per_rank * world)
+
+
 # --------------------------------------------------------------------------
 # clocks during the timed region
 # --------------------------------------------------------------------------
@@ -277,7 +289,7 @@ def run_gpu(args):
     from paper_2402_03920_gb300 import qisg
     qisg.load()
     w = workload()
-    seed = w.seed + 1000 * rank
+    seed = rank_seed(w.seed, rank)
     forms = [f for f in args.forms.split(",") if f]
     results = {}
     clocks = None
@@ -304,7 +316,7 @@ def run_gpu(args):
     ups_total = updates_per_step(w) * args.steps * world
     main = forms[0]
     total_ms, launches, kern, layout, wb = results[main]
-    value = total_ms * 1e9 / ups_total
+    value = job_value(total_ms, updates_per_step(w) * args.steps, world)
     pk, pk_kind = peaks()
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     line = {

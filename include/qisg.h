@@ -206,6 +206,21 @@ int qisg_profile(qisg_handle *h, int enable);
 int qisg_profile_read(qisg_handle *h, int kind, double *total_ms, int64_t *n_timed,
                       int64_t *n_launched);
 
+/* Sweeps are replayed from a CUDA graph of one cycle of lcm(pt_every,
+ * measure_every) sweeps whenever the sweep count is at a multiple of the
+ * cycle (captured once on an internal stream, launched on the handle's
+ * stream).  enable = 0 launches every kernel directly instead.  Results are
+ * the same either way. */
+int qisg_set_graphs(qisg_handle *h, int enable);
+
+/* Choose the SAMPLES sweep tile (site groups per thread quad) by timing
+ * sweeps_per_candidate real sweeps with each candidate on the handle's own
+ * state; the fastest is kept.  The simulation advances by
+ * 7 * (1 + sweeps_per_candidate) sweeps meanwhile (results never depend on
+ * the tile, so the trajectory is the one an untuned run would follow).  chosen:
+ * the tile kept (0 for LANES, which has nothing to tune).  Synchronises. */
+int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen);
+
 /* Block until the handle's stream is idle; reports any device error flag. */
 int qisg_sync(qisg_handle *h);
 

@@ -29,7 +29,8 @@ struct LanesArgs {
   const unsigned long long *d_t;
   uint2 key;
   int64_t N, half_N;
-  int L, Lt, n_slots, n_rep, rpw, n_groups, sites_per_block;
+  FastDiv half_plane_div;
+  int L, Lt, plane, half_plane, n_slots, n_rep, rpw, n_groups, sites_per_block;
 };
 
 template <typename Word>
@@ -51,15 +52,21 @@ __device__ __forceinline__ uint32_t bit_at(Word w, int lane) {
 template <typename Word>
 __global__ void __launch_bounds__(kBlock) lanes_half_sweep_kernel(LanesArgs<Word> p, int colour,
                                                                   int count_only, int64_t a0) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n_slots = p.n_slots, n_rep = p.n_rep, n_groups = p.n_groups;
   const int64_t a = a0 + blockIdx.y;
+  const int plane = p.plane, hp = p.half_plane, L = p.L;
   uint32_t *T_s = reinterpret_cast<uint32_t *>(smem_raw);            // [n_slots*15]
   int *wa_s = reinterpret_cast<int *>(T_s + n_slots * 15);             // [n_rep*n_slots]
   int *e_s = wa_s + n_rep * n_slots;                                   // [n_rep*n_slots*2]
   size_t off = (size_t)(n_slots * 15 + 3 * n_rep * n_slots) * 4;
   off = (off + 7) & ~size_t(7);
   Word *flip_s = reinterpret_cast<Word *>(smem_raw + off);             // [spb*n_groups]
+  off += (size_t)p.sites_per_block * n_groups * sizeof(Word);
+  off = (off + 7) & ~size_t(7);                                        // uint2 alignment
+  uint2 *nb = reinterpret_cast<uint2 *>(smem_raw + off);               // [plane]
+  uint16_t *s2d = reinterpret_cast<uint16_t *>(nb + plane);            // [plane]
+  uint8_t *Js = reinterpret_cast<uint8_t *>(s2d + plane);              // [plane]
 
   for (int i = threadIdx.x; i < n_slots * 15; i += blockDim.x) T_s[i] = p.T[i];
   for (int i = threadIdx.x; i < n_rep * n_slots; i += blockDim.x) {
@@ -68,30 +75,36 @@ __global__ void __launch_bounds__(kBlock) lanes_half_sweep_kernel(LanesArgs<Word
     e_s[2 * i + 1] = 0;
   }
   for (int i = threadIdx.x; i < p.sites_per_block * n_groups; i += blockDim.x) flip_s[i] = 0;
+  for (int i2 = threadIdx.x; i2 < plane; i2 += blockDim.x) {
+    const int y = i2 / L, x = i2 - y * L;
+    const int xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
+    const int yp = y + 1 == L ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
+    nb[i2] = make_uint2((uint32_t)(xp + L * y) | ((uint32_t)(xm + L * y) << 16),
+                        (uint32_t)(x + L * yp) | ((uint32_t)(x + L * ym) << 16));
+    s2d[((x + y) & 1) * hp + (i2 >> 1)] = (uint16_t)i2;
+    Js[i2] = p.J[a * plane + i2];
+  }
   __syncthreads();
 
   const int s = threadIdx.x % n_slots;
   const int jl = threadIdx.x / n_slots;
   const int64_t j = (int64_t)blockIdx.x * p.sites_per_block + jl;
   if (jl < p.sites_per_block && j < p.half_N) {
-    const int L = p.L, Lt = p.Lt;
-    const SiteXYT c = site_of_colour(j, L, colour);
-    const int xp = c.x + 1 == L ? 0 : c.x + 1, xm = c.x == 0 ? L - 1 : c.x - 1;
-    const int yp = c.y + 1 == L ? 0 : c.y + 1, ym = c.y == 0 ? L - 1 : c.y - 1;
-    const int tp = c.tau + 1 == Lt ? 0 : c.tau + 1, tm = c.tau == 0 ? Lt - 1 : c.tau - 1;
-    const int64_t plane = (int64_t)L * L;
-    const int64_t site = c.x + (int64_t)L * c.y + plane * c.tau;
-    const int64_t off_t = plane * c.tau;
-    const int64_t i_xp = xp + (int64_t)L * c.y + off_t, i_xm = xm + (int64_t)L * c.y + off_t;
-    const int64_t i_yp = c.x + (int64_t)L * yp + off_t, i_ym = c.x + (int64_t)L * ym + off_t;
-    const int64_t i_tp = c.x + (int64_t)L * c.y + plane * tp;
-    const int64_t i_tm = c.x + (int64_t)L * c.y + plane * tm;
-    const uint8_t *Ja = p.J + a * plane;
-    const uint8_t j_here = __ldg(Ja + c.x + L * c.y);
+    const uint32_t Lt = (uint32_t)p.Lt;
+    const uint32_t tau = p.half_plane_div.div((uint32_t)j);
+    const uint32_t i2 = s2d[((colour + tau) & 1) * hp + ((uint32_t)j - tau * hp)];
+    const uint2 nv = nb[i2];
+    const uint32_t offt = tau * plane;
+    const uint32_t site = i2 + offt;
+    const uint32_t i_xp = (nv.x & 0xFFFFu) + offt, i_xm = (nv.x >> 16) + offt;
+    const uint32_t i_yp = (nv.y & 0xFFFFu) + offt, i_ym = (nv.y >> 16) + offt;
+    const uint32_t i_tp = i2 + (tau + 1 == Lt ? 0u : offt + plane);
+    const uint32_t i_tm = i2 + (tau == 0 ? (Lt - 1) * plane : offt - plane);
+    const uint8_t j_here = Js[i2];
     const Word Jxp = all_ones_if<Word>(j_here & 1u);
     const Word Jyp = all_ones_if<Word>(j_here & 2u);
-    const Word Jxm = all_ones_if<Word>(__ldg(Ja + xm + L * c.y) & 1u);
-    const Word Jym = all_ones_if<Word>(__ldg(Ja + c.x + L * ym) & 2u);
+    const Word Jxm = all_ones_if<Word>(Js[nv.x >> 16] & 1u);
+    const Word Jym = all_ones_if<Word>(Js[nv.y >> 16] & 2u);
     const unsigned long long t = *p.d_t;
 
     int cur_q = -1;
@@ -156,8 +169,8 @@ __global__ void __launch_bounds__(kBlock) lanes_half_sweep_kernel(LanesArgs<Word
       const int64_t j2 = (int64_t)blockIdx.x * p.sites_per_block + jl2;
       const Word fw = flip_s[i];
       if (j2 < p.half_N && fw) {
-        const SiteXYT c = site_of_colour(j2, p.L, colour);
-        const int64_t site = c.x + (int64_t)p.L * c.y + (int64_t)p.L * p.L * c.tau;
+        const uint32_t tau = p.half_plane_div.div((uint32_t)j2);
+        const uint32_t site = s2d[((colour + tau) & 1) * hp + ((uint32_t)j2 - tau * hp)] + tau * plane;
         p.spins[(a * n_groups + g) * p.N + site] ^= fw;
       }
     }
@@ -177,40 +190,6 @@ __global__ void zero_u64_kernel(unsigned long long *p, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = 0;
-}
-
-// PT pass (Sec. 2.1) of chain (a, r): pairs (s, s+1) in increasing s.  The
-// exchange is accepted iff u < P with P = alpha^|m| beta^|n| (bases chosen
-// by the signs of m = A_Y - A_X, n = B_Y - B_X), u = x * 2^-32.
-__global__ void lanes_pt_kernel(int32_t *walker, const unsigned long long *U, const double *bases,
-                                const unsigned long long *d_t, uint2 key, int64_t a0, int64_t n_a,
-                                int n_rep, int n_slots, int64_t N, int explicit_pass) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= n_a * n_rep) return;
-  const int64_t a = a0 + c / n_rep;
-  const int r = (int)(c % n_rep);
-  const unsigned long long t = explicit_pass ? *d_t - 1ull : *d_t;
-  int32_t *wa = walker + (a * n_rep + r) * n_slots;
-  const unsigned long long *Ua = U + (a * n_rep + r) * n_slots * 2;
-  const double *ap = bases, *am = bases + n_slots, *bp = bases + 2 * n_slots,
-               *bm = bases + 3 * n_slots;
-  for (int s = 0; s + 1 < n_slots; ++s) {
-    const int X = wa[s], Y = wa[s + 1];
-    // A = 2N - 2 U_s, B = N - 2 U_t
-    const long long m = -2 * ((long long)Ua[2 * Y] - (long long)Ua[2 * X]);
-    const long long n = -2 * ((long long)Ua[2 * Y + 1] - (long long)Ua[2 * X + 1]);
-    const double fa = pow_rn(m >= 0 ? ap[s] : am[s], (unsigned long long)(m >= 0 ? m : -m));
-    const double fb = pow_rn(n >= 0 ? bp[s] : bm[s], (unsigned long long)(n >= 0 ? n : -n));
-    const double P = __dmul_rn(fa, fb);
-    const uint4 x = philox(make_uint4((uint32_t)s, (uint32_t)t, (uint32_t)a,
-                                      (DOM_PT << 28) | (uint32_t)(r >> 2)),
-                           key);
-    const double u = __dmul_rn((double)pick4(x, r & 3), 0x1p-32);
-    if (u < P) {
-      wa[s] = Y;
-      wa[s + 1] = X;
-    }
-  }
 }
 
 // Overlaps of the configurations at slot s (Appendix E.1): count the sites
@@ -339,6 +318,16 @@ __global__ void lanes_init_spins_kernel(Word *spins, int64_t n_a, int64_t N, int
 }
 
 template <typename Word>
+size_t lanes_smem_bytes(const qisg_handle *h, int spb) {
+  size_t smem = (size_t)(h->n_slots * 15 + 3 * h->n_rep * h->n_slots) * 4;
+  smem = (smem + 7) & ~size_t(7);
+  smem += (size_t)spb * h->n_groups * sizeof(Word);
+  smem = (smem + 7) & ~size_t(7);
+  smem += (size_t)h->L * h->L * (sizeof(uint2) + sizeof(uint16_t) + 1);
+  return smem;
+}
+
+template <typename Word>
 LanesArgs<Word> make_args(qisg_handle *h) {
   LanesArgs<Word> p;
   p.spins = reinterpret_cast<Word *>(h->spins);
@@ -352,6 +341,9 @@ LanesArgs<Word> make_args(qisg_handle *h) {
   p.half_N = h->N / 2;
   p.L = h->L;
   p.Lt = h->Lt;
+  p.plane = h->L * h->L;
+  p.half_plane = p.plane / 2;
+  p.half_plane_div = FastDiv((uint32_t)p.half_plane);
   p.n_slots = h->n_slots;
   p.n_rep = h->n_rep;
   p.rpw = h->rpw;
@@ -364,15 +356,19 @@ template <typename Word>
 int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   LanesArgs<Word> p = make_args<Word>(h);
   const int64_t blocks = (p.half_N + p.sites_per_block - 1) / p.sites_per_block;
-  size_t smem = (size_t)(h->n_slots * 15 + 3 * h->n_rep * h->n_slots) * 4;
-  smem = (smem + 7) & ~size_t(7);
-  smem += (size_t)p.sites_per_block * h->n_groups * sizeof(Word);
+  const size_t smem = lanes_smem_bytes<Word>(h, p.sites_per_block);
   if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
   if (colour == 0) {
     const int64_t n = h->n_samples * h->n_rep * h->n_slots * 2;
     zero_u64_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, h->stream>>>(h->d_U, n);
     h->launches++;
   }
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    attr_set = true;
+  }
+  if (smem > 227 * 1024) return fail(QISG_EINVAL, "LANES plane tables exceed shared memory");
   if (h->per_sample_launch) {
     for (int64_t a = 0; a < h->n_samples; ++a) {
       const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
@@ -451,26 +447,14 @@ int lanes_half_sweep(qisg_handle *h, int colour, int count_only) {
 }
 
 int lanes_pt(qisg_handle *h, int explicit_pass) {
-  const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
   if (h->per_sample_launch) {
     for (int64_t a = 0; a < h->n_samples; ++a) {
-      const int tok = prof_begin(h, QISG_KERNEL_PT);
-      lanes_pt_kernel<<<(unsigned)((h->n_rep + 127) / 128), 128, 0, h->stream>>>(
-          h->d_walker, h->d_U, h->d_bases, h->d_t, key, a, 1, h->n_rep, h->n_slots, h->N,
-          explicit_pass);
-      prof_end(h, QISG_KERNEL_PT, tok);
-      h->launches++;
+      const int rc = pt_pass(h, explicit_pass, a, 1);
+      if (rc) return rc;
     }
-  } else {
-    const int64_t n = h->n_samples * h->n_rep;
-    const int tok = prof_begin(h, QISG_KERNEL_PT);
-    lanes_pt_kernel<<<(unsigned)((n + 127) / 128), 128, 0, h->stream>>>(
-        h->d_walker, h->d_U, h->d_bases, h->d_t, key, 0, h->n_samples, h->n_rep, h->n_slots, h->N,
-        explicit_pass);
-    prof_end(h, QISG_KERNEL_PT, tok);
-    h->launches++;
+    return QISG_OK;
   }
-  return cuda_check(cudaGetLastError(), "lanes pt");
+  return pt_pass(h, explicit_pass, 0, h->n_samples);
 }
 
 int lanes_measure(qisg_handle *h, int force_to_q) {

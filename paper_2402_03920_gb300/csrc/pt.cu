@@ -1,0 +1,172 @@
+// Parallel-tempering pass (Sec. 2.1), one warp per chain (a, r).
+//
+// Lane s holds the energies of the configuration at slot s and draws the
+// Philox word of pair (s, s+1); the pass over pairs s = 0, 1, ... is then a
+// short uniform loop over warp shuffles: the configuration carried up from
+// pair s-1 meets the original occupant of slot s+1, and the decision fixes
+// the final occupant of slot s.
+//
+//   LANES  : energies are counted by walker; the pass reorders walker_at.
+//   SAMPLES: energies are counted by slot; the pass reorders walker_at and
+//            the slot energies.  A block is the 32 chains of one (sample
+//            block b, replica r, 32-lane half); their accepted pairs are
+//            gathered into the lane masks acc[b][r][s] (bit l: sample b*W+l
+//            exchanged pair (s, s+1)), from which the permute kernel moves
+//            the spin bits.
+#include "qisg_internal.cuh"
+
+namespace qisg {
+namespace {
+
+// Scan of one chain by one warp; returns the accepted-pair bitmask (same in
+// every lane).
+template <bool BY_SLOT>
+__device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua, const PTConst &pc,
+                                             const double *sq, uint2 key, uint32_t t, int64_t a, int r,
+                                             int n_slots) {
+  const int lane = threadIdx.x & 31;
+  int w = 0;
+  long long us = 0, ut = 0;
+  if (lane < n_slots) {
+    w = wa[lane];
+    const int e = BY_SLOT ? lane : w;
+    us = (long long)Ua[2 * e];
+    ut = (long long)Ua[2 * e + 1];
+  }
+  uint32_t x = 0;
+  float lnu = 0.f;
+  if (lane + 1 < n_slots) {
+    x = pick4(philox(make_uint4((uint32_t)lane, t, (uint32_t)a, (DOM_PT << 28) | (uint32_t)(r >> 2)), key), r & 3);
+    lnu = __logf((float)x) - 22.18070977791825f;
+  }
+  // the configuration moving up the ladder and what each slot ends with
+  long long c_us = __shfl_sync(0xffffffffu, us, 0), c_ut = __shfl_sync(0xffffffffu, ut, 0);
+  int c_w = __shfl_sync(0xffffffffu, w, 0);
+  long long f_us = us, f_ut = ut;
+  int f_w = w;
+  uint32_t acc = 0;
+  for (int s = 0; s + 1 < n_slots; ++s) {
+    const long long y_us = __shfl_sync(0xffffffffu, us, s + 1);
+    const long long y_ut = __shfl_sync(0xffffffffu, ut, s + 1);
+    const int y_w = __shfl_sync(0xffffffffu, w, s + 1);
+    const uint32_t xs = __shfl_sync(0xffffffffu, x, s);
+    const float ls = __shfl_sync(0xffffffffu, lnu, s);
+    const long long m = -2 * (y_us - c_us);   // A = 2N - 2 us
+    const long long n = -2 * (y_ut - c_ut);   // B = N - 2 ut
+    const bool ex = pt_decide(pc, sq, s, m, n, xs, ls);
+    if (lane == s) {
+      f_us = ex ? y_us : c_us;
+      f_ut = ex ? y_ut : c_ut;
+      f_w = ex ? y_w : c_w;
+    }
+    if (ex) {
+      acc |= 1u << s;   // the carried configuration moves on to slot s+1
+    } else {
+      c_us = y_us;
+      c_ut = y_ut;
+      c_w = y_w;
+    }
+  }
+  if (lane == n_slots - 1) {
+    f_us = c_us;
+    f_ut = c_ut;
+    f_w = c_w;
+  }
+  if (lane < n_slots) {
+    wa[lane] = f_w;
+    if (BY_SLOT) {
+      Ua[2 * lane] = (unsigned long long)f_us;
+      Ua[2 * lane + 1] = (unsigned long long)f_ut;
+    }
+  }
+  return acc;
+}
+
+// LANES: one warp per chain, chains in (a, r) order.
+__global__ void pt_lanes_kernel(int32_t *walker, unsigned long long *U, const PTConst *ptc, const double *sq,
+                                const unsigned long long *d_t, uint2 key, int64_t a0, int64_t n_chains,
+                                int n_rep, int n_slots, int explicit_pass) {
+  __shared__ PTConst pc;
+  load_ptconst(&pc, ptc);
+  __syncthreads();
+  const int64_t chain = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (chain >= n_chains) return;   // whole warp
+  const int64_t a = a0 + chain / n_rep;
+  const int r = (int)(chain % n_rep);
+  const uint32_t t = (uint32_t)(explicit_pass ? *d_t - 1ull : *d_t);
+  pt_chain<false>(walker + (a * n_rep + r) * n_slots, U + (a * n_rep + r) * n_slots * 2, pc, sq, key, t, a,
+                  r, n_slots);
+}
+
+// SAMPLES: block = 32 warps = samples b*W + h*32 + v (v = warp) of replica r;
+// warp 0 then turns the 32 accept bitmasks into the lane masks (32-bit half
+// h of acc[b][r][s]).
+template <typename Word>
+__global__ void __launch_bounds__(1024) pt_samples_kernel(int32_t *walker, unsigned long long *U, Word *accw,
+                                                          const PTConst *ptc, const double *sq,
+                                                          const unsigned long long *d_t, uint2 key,
+                                                          int64_t n_samples, int n_rep, int n_slots,
+                                                          int explicit_pass) {
+  constexpr int W = (int)sizeof(Word) * 8, halves = W / 32;
+  __shared__ PTConst pc;
+  __shared__ uint32_t bits[32];
+  load_ptconst(&pc, ptc);
+  __syncthreads();
+  const int h = (int)(blockIdx.x % halves);
+  const int r = (int)((blockIdx.x / halves) % n_rep);
+  const int64_t b = blockIdx.x / ((int64_t)halves * n_rep);
+  const int v = threadIdx.x >> 5;
+  const int64_t a = b * W + h * 32 + v;
+  uint32_t acc = 0;
+  if (a < n_samples) {
+    const uint32_t t = (uint32_t)(explicit_pass ? *d_t - 1ull : *d_t);
+    acc = pt_chain<true>(walker + (a * n_rep + r) * n_slots, U + (a * n_rep + r) * n_slots * 2, pc, sq, key,
+                         t, a, r, n_slots);
+  }
+  if ((threadIdx.x & 31) == 0) bits[v] = acc;
+  __syncthreads();
+  if (v == 0) {
+    const uint32_t mine = bits[threadIdx.x];
+    Word *out = accw + (b * n_rep + r) * n_slots;
+    for (int s = 0; s + 1 < n_slots; ++s) {
+      const unsigned m32 = __ballot_sync(0xffffffffu, (mine >> s) & 1u);
+      if (threadIdx.x == 0) {
+        if (W == 64)
+          reinterpret_cast<unsigned *>(&out[s])[h] = m32;
+        else
+          out[s] = (Word)m32;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a) {
+  const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  const int tok = prof_begin(h, QISG_KERNEL_PT);
+  if (h->layout == QISG_LAYOUT_SAMPLES) {
+    const unsigned blocks = (unsigned)(h->n_b * h->n_rep * (h->W / 32));
+    if (h->W == 64)
+      pt_samples_kernel<unsigned long long><<<blocks, 1024, 0, h->stream>>>(
+          h->d_walker, h->d_U, reinterpret_cast<unsigned long long *>(h->d_acc),
+          reinterpret_cast<const PTConst *>(h->d_ptc), h->d_sq, h->d_t, key, h->n_samples, h->n_rep,
+          h->n_slots, explicit_pass);
+    else
+      pt_samples_kernel<unsigned int><<<blocks, 1024, 0, h->stream>>>(
+          h->d_walker, h->d_U, reinterpret_cast<unsigned int *>(h->d_acc),
+          reinterpret_cast<const PTConst *>(h->d_ptc), h->d_sq, h->d_t, key, h->n_samples, h->n_rep,
+          h->n_slots, explicit_pass);
+  } else {
+    const int64_t n_chains = n_a * h->n_rep;
+    constexpr int kWarps = 4;
+    pt_lanes_kernel<<<(unsigned)((n_chains + kWarps - 1) / kWarps), 32 * kWarps, 0, h->stream>>>(
+        h->d_walker, h->d_U, reinterpret_cast<const PTConst *>(h->d_ptc), h->d_sq, h->d_t, key, a0, n_chains,
+        h->n_rep, h->n_slots, explicit_pass);
+  }
+  prof_end(h, QISG_KERNEL_PT, tok);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "pt pass");
+}
+
+}  // namespace qisg

@@ -32,6 +32,18 @@ int cuda_check(cudaError_t e, const char *what) {
 
 constexpr int kProfMax = 65536;
 
+// While the stream is being captured into the sweep graph, an event record
+// must be external to become an event-record node (a plain record is only a
+// capture dependency); outside capture the plain record is the one allowed.
+void prof_record(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, st);
+}
+
 int prof_begin(qisg_handle *h, int kind) {
   if (!h->prof) return -1;
   h->prof_launched[kind]++;
@@ -43,7 +55,7 @@ int prof_begin(qisg_handle *h, int kind) {
     cudaEventDestroy(a);
     return -1;
   }
-  cudaEventRecord(a, h->stream);
+  prof_record(a, h->stream);
   v.push_back(a);
   v.push_back(b);
   return (int)v.size() - 1;
@@ -51,10 +63,12 @@ int prof_begin(qisg_handle *h, int kind) {
 
 void prof_end(qisg_handle *h, int kind, int tok) {
   if (tok < 0) return;
-  cudaEventRecord(h->prof_ev[kind][(size_t)tok], h->stream);
+  prof_record(h->prof_ev[kind][(size_t)tok], h->stream);
 }
 
 void prof_clear(qisg_handle *h) {
+  for (cudaEvent_t e : h->prof_spare) cudaEventDestroy(e);
+  h->prof_spare.clear();
   for (int k = 0; k < 4; ++k) {
     for (cudaEvent_t e : h->prof_ev[k]) cudaEventDestroy(e);
     h->prof_ev[k].clear();
@@ -117,7 +131,7 @@ void build_thresholds(qisg_handle *h) {
 // beta+- = exp(+-(k_tau,s - k_tau,s+1)).
 void build_bases(qisg_handle *h) {
   const int n = h->n_slots;
-  h->bases.assign((size_t)4 * n, 1.0);
+  h->bases.assign((size_t)6 * n, 1.0);
   for (int s = 0; s + 1 < n; ++s) {
     const double dk = h->k[s] - h->k[s + 1];
     const double dkt = h->kt[s] - h->kt[s + 1];
@@ -125,7 +139,21 @@ void build_bases(qisg_handle *h) {
     h->bases[n + s] = std::exp(-dk);
     h->bases[2 * n + s] = std::exp(dkt);
     h->bases[3 * n + s] = std::exp(-dkt);
+    h->bases[4 * n + s] = dk;
+    h->bases[5 * n + s] = dkt;
   }
+  // squaring chains of the four bases of every pair
+  h->sq.assign((size_t)(n > 1 ? n - 1 : 1) * 4 * kSqBits, 1.0);
+  for (int s = 0; s + 1 < n; ++s)
+    for (int w = 0; w < 4; ++w) {
+      double b = h->bases[(size_t)w * n + s];
+      double *c = &h->sq[((size_t)s * 4 + w) * kSqBits];
+      for (int j = 0; j < kSqBits; ++j) {
+        c[j] = b;
+        volatile double sqr = b * b;   // one rounded IEEE multiply, never contracted
+        b = sqr;
+      }
+    }
 }
 
 template <typename T>
@@ -192,7 +220,7 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (n_slots < 1 || !ladder) return fail(QISG_EINVAL, "need at least one ladder slot");
   if (n_replicas < 1 || n_replicas > 1024) return fail(QISG_EINVAL, "n_replicas must be in 1..1024");
   if (n_samples < 1) return fail(QISG_EINVAL, "n_samples must be >= 1");
-  if (n_slots > 4096) return fail(QISG_EINVAL, "n_slots must be <= 4096");
+  if (n_slots > 32) return fail(QISG_EINVAL, "n_slots must be <= 32");
   if ((int64_t)L * L * L_tau > ((int64_t)1 << 31)) return fail(QISG_EINVAL, "lattice too large");
   for (int s = 0; s < n_slots; ++s)
     if (!std::isfinite(ladder[s].k) || !std::isfinite(ladder[s].k_tau) || ladder[s].k < 0 ||
@@ -273,6 +301,8 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc) rc = dalloc(h, &h->J, h->J_bytes);
   if (!rc) rc = dalloc(h, &h->d_T, h->T.size() * 4);
   if (!rc) rc = dalloc(h, &h->d_bases, h->bases.size() * 8);
+  if (!rc) rc = dalloc(h, &h->d_sq, h->sq.size() * 8);
+  if (!rc) rc = dalloc(h, &h->d_ptc, sizeof(PTConst));
   if (!rc) rc = dalloc(h, &h->d_walker, (size_t)n_chain_slots * 4);
   if (!rc) rc = dalloc(h, &h->d_U, (size_t)n_chain_slots * 2 * 8);
   if (!rc) rc = dalloc(h, &h->d_sumA, (size_t)n_chain_slots * 8);
@@ -300,6 +330,18 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc) rc = cuda_check(cudaMemcpyAsync(h->d_bases, h->bases.data(), h->bases.size() * 8,
                                            cudaMemcpyHostToDevice, h->stream),
                            "copy bases");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(h->d_sq, h->sq.data(), h->sq.size() * 8, cudaMemcpyHostToDevice,
+                                           h->stream),
+                           "copy squaring chains");
+  PTConst ptc;
+  std::memset(&ptc, 0, sizeof(ptc));
+  for (int s = 0; s + 1 < n_slots; ++s) {
+    ptc.dkf[s] = (float)h->bases[(size_t)4 * n_slots + s];
+    ptc.dktf[s] = (float)h->bases[(size_t)5 * n_slots + s];
+    for (int w = 0; w < 4; ++w)
+      if (h->bases[(size_t)w * n_slots + s] >= 1.0) ptc.ge1[w] |= 1u << s;
+  }
+  if (!rc) rc = cuda_check(cudaMemcpy(h->d_ptc, &ptc, sizeof(ptc), cudaMemcpyHostToDevice), "copy PT constants");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumA, 0, (size_t)n_chain_slots * 8, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumB, 0, (size_t)n_chain_slots * 8, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumq, 0, qn * 8, h->stream), "memset");
@@ -321,22 +363,236 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   return QISG_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// One sweep t = h->t, enqueued on h->stream: red, blue (+ energies), PT when
+// due, measurement when due, advance of the device counter.
+int one_sweep(qisg_handle *h) {
+  const bool lanes = h->layout == QISG_LAYOUT_LANES;
+  const uint64_t t = h->t;
+  int rc = lanes ? lanes_half_sweep(h, 0, 0) : samples_half_sweep(h, 0, 0);
+  if (!rc) rc = lanes ? lanes_half_sweep(h, 1, 0) : samples_half_sweep(h, 1, 0);
+  if (!rc && h->pt_every > 0 && (t + 1) % (uint64_t)h->pt_every == 0)
+    rc = lanes ? lanes_pt(h, 0) : samples_pt(h, 0);
+  if (!rc && h->measure_every > 0 && (t + 1) % (uint64_t)h->measure_every == 0) {
+    rc = lanes ? lanes_measure(h, 0) : samples_measure(h, 0);
+    h->n_meas++;
+  }
+  if (!rc) rc = advance_counter(h);
+  return rc;
+}
+
+int64_t gcd64(int64_t a, int64_t b) { return b ? gcd64(b, a % b) : a; }
+
+int cycle_length(const qisg_handle *h) {
+  const int64_t p = h->pt_every > 0 ? h->pt_every : 1;
+  const int64_t m = h->measure_every > 0 ? h->measure_every : 1;
+  const int64_t l = p / gcd64(p, m) * m;
+  return (int)(l > 4096 ? 0 : l);   // no graph for very long cycles
+}
+
+void drop_cycle(qisg_handle *h) {
+  if (h->cyc_exec) cudaGraphExecDestroy(h->cyc_exec);
+  if (h->cyc_graph) cudaGraphDestroy(h->cyc_graph);
+  h->cyc_exec = nullptr;
+  h->cyc_graph = nullptr;
+  h->cyc_sweeps = 0;
+  h->cyc_ev_nodes.clear();
+  h->cyc_ev_kind.clear();
+  for (cudaEvent_t e : h->cyc_events) cudaEventDestroy(e);
+  h->cyc_events.clear();
+}
+
+// Capture C sweeps (starting at a multiple of C) into a graph.  The host
+// mirrors (t, measurements, launch counts) are restored afterwards and
+// advanced per replay instead.
+int build_cycle(qisg_handle *h, int C) {
+  drop_cycle(h);
+  int rc = QISG_OK;
+  if (!h->cap_stream)
+    rc = cuda_check(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking), "create capture stream");
+  if (rc) return rc;
+  const uint64_t t0 = h->t;
+  const int64_t meas0 = h->n_meas, launches0 = h->launches;
+  int64_t pl0[4];
+  size_t ev0[4];
+  for (int k = 0; k < 4; ++k) {
+    pl0[k] = h->prof_launched[k];
+    ev0[k] = h->prof_ev[k].size();
+  }
+  cudaStream_t user = h->stream;
+  h->stream = h->cap_stream;
+  rc = cuda_check(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (!rc)
+    for (int i = 0; i < C && !rc; ++i) rc = one_sweep(h);
+  cudaGraph_t g = nullptr;
+  const int rc_end = cuda_check(cudaStreamEndCapture(h->cap_stream, &g), "end capture");
+  h->stream = user;
+  if (!rc) rc = rc_end;
+  h->cyc_launches = h->launches - launches0;
+  h->cyc_meas = h->n_meas - meas0;
+  h->t = t0;
+  h->n_meas = meas0;
+  h->launches = launches0;
+  // events recorded during capture belong to the graph's record nodes
+  std::map<cudaEvent_t, std::pair<int, int>> which;
+  for (int k = 0; k < 4; ++k) {
+    h->cyc_prof_launched[k] = h->prof_launched[k] - pl0[k];
+    h->prof_launched[k] = pl0[k];
+    for (size_t i = ev0[k]; i < h->prof_ev[k].size(); ++i) which[h->prof_ev[k][i]] = {k, (int)((i - ev0[k]) & 1)};
+  }
+  if (!rc) {
+    size_t n_nodes = 0;
+    rc = cuda_check(cudaGraphGetNodes(g, nullptr, &n_nodes), "graph nodes");
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    if (!rc && n_nodes) rc = cuda_check(cudaGraphGetNodes(g, nodes.data(), &n_nodes), "graph nodes");
+    // walk the linear chain from its root so that record nodes keep their order
+    std::vector<cudaGraphNode_t> order;
+    if (!rc) {
+      cudaGraphNode_t cur = nullptr;
+      for (cudaGraphNode_t nd : nodes) {
+        size_t nd_deps = 0;
+        cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &nd_deps);
+        if (nd_deps == 0) cur = nd;
+      }
+      while (cur) {
+        order.push_back(cur);
+        size_t nd_out = 0;
+        cudaGraphNodeGetDependentNodes(cur, nullptr, nullptr, &nd_out);
+        if (nd_out != 1) break;
+        cudaGraphNode_t nxt = nullptr;
+        cudaGraphNodeGetDependentNodes(cur, &nxt, nullptr, &nd_out);
+        cur = nxt;
+      }
+      if (order.size() != n_nodes) rc = fail(QISG_ECUDA, "captured sweep graph is not a chain");
+    }
+    for (size_t i = 0; !rc && i < order.size(); ++i) {
+      cudaGraphNodeType ty;
+      cudaGraphNodeGetType(order[i], &ty);
+      if (ty != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t e = nullptr;
+      cudaGraphEventRecordNodeGetEvent(order[i], &e);
+      auto it = which.find(e);
+      if (it == which.end()) continue;
+      h->cyc_ev_nodes.push_back(order[i]);
+      h->cyc_ev_kind.push_back(it->second);
+    }
+    if (!rc) rc = cuda_check(cudaGraphInstantiate(&h->cyc_exec, g, 0), "instantiate sweep graph");
+  }
+  for (int k = 0; k < 4; ++k) {   // the capture's own events are not timings; the
+    for (size_t i = ev0[k]; i < h->prof_ev[k].size(); ++i)   // graph keeps them until dropped
+      h->cyc_events.push_back(h->prof_ev[k][i]);
+    h->prof_ev[k].resize(ev0[k]);
+  }
+  h->cyc_graph = g;
+  if (rc) {
+    drop_cycle(h);
+    return rc;
+  }
+  h->cyc_sweeps = C;
+  h->cyc_profiled = h->prof;
+  return QISG_OK;
+}
+
+constexpr int kProfMaxPairs = 65536;
+
+int replay_cycle(qisg_handle *h) {
+  if (h->prof) {
+    // fresh events for this replay's record nodes, paired as recorded
+    std::vector<cudaEvent_t> fresh(h->cyc_ev_nodes.size(), nullptr);
+    bool room = true;
+    for (int k = 0; k < 4; ++k)
+      if ((int)h->prof_ev[k].size() >= 2 * kProfMaxPairs) room = false;
+    for (size_t i = 0; i < fresh.size(); ++i) {
+      if (room) cudaEventCreate(&fresh[i]);
+      else cudaEventCreateWithFlags(&fresh[i], cudaEventDisableTiming);
+      const cudaError_t e = cudaGraphExecEventRecordNodeSetEvent(h->cyc_exec, h->cyc_ev_nodes[i], fresh[i]);
+      const int rc = cuda_check(e, ("rebind graph event " + std::to_string(i) + " of " +
+                                    std::to_string(h->cyc_ev_nodes.size())).c_str());
+      if (rc) return rc;
+    }
+    if (room)
+      for (size_t i = 0; i < fresh.size(); ++i) h->prof_ev[h->cyc_ev_kind[i].first].push_back(fresh[i]);
+    else
+      for (cudaEvent_t e : fresh) h->prof_spare.push_back(e);
+    for (int k = 0; k < 4; ++k) h->prof_launched[k] += h->cyc_prof_launched[k];
+  }
+  const int rc = cuda_check(cudaGraphLaunch(h->cyc_exec, h->stream), "launch sweep graph");
+  if (rc) return rc;
+  h->t += (uint64_t)h->cyc_sweeps;
+  h->n_meas += h->cyc_meas;
+  h->launches += h->cyc_launches;
+  return QISG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int qisg_sweep(qisg_handle *h, int64_t n_sweeps) {
   if (!h || n_sweeps < 0) return fail(QISG_EINVAL, "bad handle or n_sweeps < 0");
-  const bool lanes = h->layout == QISG_LAYOUT_LANES;
-  for (int64_t i = 0; i < n_sweeps; ++i) {
-    const uint64_t t = h->t;
-    int rc = lanes ? lanes_half_sweep(h, 0, 0) : samples_half_sweep(h, 0, 0);
-    if (!rc) rc = lanes ? lanes_half_sweep(h, 1, 0) : samples_half_sweep(h, 1, 0);
-    if (!rc && h->pt_every > 0 && (t + 1) % (uint64_t)h->pt_every == 0)
-      rc = lanes ? lanes_pt(h, 0) : samples_pt(h, 0);
-    if (!rc && h->measure_every > 0 && (t + 1) % (uint64_t)h->measure_every == 0) {
-      rc = lanes ? lanes_measure(h, 0) : samples_measure(h, 0);
-      h->n_meas++;
+  const int C = h->use_graphs ? cycle_length(h) : 0;
+  while (n_sweeps > 0) {
+    int rc;
+    if (C > 0 && n_sweeps >= C && h->t % (uint64_t)C == 0) {
+      if (!h->cyc_exec || h->cyc_sweeps != C || h->cyc_profiled != h->prof) {
+        rc = build_cycle(h, C);
+        if (rc) return rc;
+      }
+      rc = replay_cycle(h);
+      n_sweeps -= C;
+    } else {
+      rc = one_sweep(h);
+      n_sweeps -= 1;
     }
-    if (!rc) rc = advance_counter(h);
     if (rc) return rc;
   }
+  return QISG_OK;
+}
+
+int qisg_set_graphs(qisg_handle *h, int enable) {
+  if (!h) return fail(QISG_EINVAL, "NULL handle");
+  h->use_graphs = enable != 0;
+  if (!h->use_graphs) drop_cycle(h);
+  return QISG_OK;
+}
+
+int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
+  if (!h || sweeps_per_candidate < 1) return fail(QISG_EINVAL, "bad handle or sweep count");
+  if (h->layout != QISG_LAYOUT_SAMPLES) {
+    if (chosen) *chosen = 0;
+    return QISG_OK;
+  }
+  int best = 0;
+  float best_ms = 0.f;
+  cudaEvent_t e0, e1;
+  int rc = cuda_check(cudaEventCreate(&e0), "event");
+  if (!rc) rc = cuda_check(cudaEventCreate(&e1), "event");
+  const bool graphs = h->use_graphs;
+  h->use_graphs = false;
+  for (int g = 1; g <= 64 && !rc; g <<= 1) {
+    h->sweep_groups_per_quad = g;
+    rc = one_sweep(h);   // warm the candidate
+    if (!rc) rc = cuda_check(cudaEventRecord(e0, h->stream), "record");
+    for (int i = 0; i < sweeps_per_candidate && !rc; ++i) rc = one_sweep(h);
+    if (!rc) rc = cuda_check(cudaEventRecord(e1, h->stream), "record");
+    if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "sync");
+    float ms = 0.f;
+    if (!rc) rc = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+    if (!rc && (best == 0 || ms < best_ms)) {
+      best = g;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->use_graphs = graphs;
+  if (rc) return rc;
+  h->sweep_groups_per_quad = best;
+  drop_cycle(h);
+  if (chosen) *chosen = best;
   return QISG_OK;
 }
 
@@ -557,11 +813,14 @@ int qisg_sync(qisg_handle *h) {
 void qisg_destroy(qisg_handle *h) {
   if (!h) return;
   if (h->stream || true) cudaStreamSynchronize(h->stream);
-  void *ptrs[] = {h->spins, h->J, h->d_T, h->d_bases, h->d_walker, h->d_U, h->d_sumA, h->d_sumB,
+  void *ptrs[] = {h->spins, h->J, h->d_T, h->d_bases, h->d_sq, h->d_ptc, h->d_walker, h->d_U, h->d_sumA, h->d_sumB,
                   h->d_sumq, h->d_sumq2, h->d_q, h->d_out, h->d_t, h->d_acc, h->d_err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  drop_cycle(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   prof_clear(h);
+  for (cudaEvent_t e : h->prof_spare) cudaEventDestroy(e);
   delete h;
 }
 

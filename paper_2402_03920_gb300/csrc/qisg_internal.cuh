@@ -9,7 +9,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/qisg.h"
@@ -39,16 +41,144 @@ __device__ __forceinline__ uint32_t pick4(const uint4 &v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-// b^e by right-to-left binary powering with round-to-nearest multiplies
-// (no contraction), so host and device agree bit for bit.
-__device__ __forceinline__ double pow_rn(double b, unsigned long long e) {
+// Squaring chain length: exponents |A_Y - A_X| <= 4N < 2^40.
+constexpr int kSqBits = 40;
+
+// b^e by right-to-left binary powering with round-to-nearest multiplies:
+// res = 1; for each bit j of e (low to high) res *= b^(2^j), where the
+// chain b^(2^j) = (b^(2^(j-1)))^2 was squared once on the host with IEEE
+// multiplies.  The multiplies and their operands are exactly those of the
+// textbook loop, so the result is bit-identical to it.
+__device__ __forceinline__ double pow_chain(const double *chain, unsigned long long e) {
   double r = 1.0;
+  int j = 0;
   while (e) {
-    if (e & 1ull) r = __dmul_rn(r, b);
-    b = __dmul_rn(b, b);
+    if (e & 1ull) r = __dmul_rn(r, __ldg(chain + j));
     e >>= 1;
+    ++j;
   }
   return r;
+}
+
+// Unsigned 32-bit division by a run-time invariant d >= 1 through one
+// multiply-high, two shifts and two adds (Granlund and Montgomery, "Division
+// by invariant integers using multiplication", PLDI 1994, Fig. 4.1):
+//   l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+//   q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0),  t = mulhi(m, n).
+struct FastDiv {
+  uint32_t d, m, s1, s2;
+  __host__ __device__ FastDiv() : d(1), m(1), s1(0), s2(0) {}
+  __host__ explicit FastDiv(uint32_t div) : d(div) {
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < div) ++l;
+    m = (uint32_t)(((1ull << 32) * ((1ull << l) - div)) / div + 1ull);
+    s1 = l < 1 ? l : 1;
+    s2 = l > 1 ? l - 1 : 0;
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const {
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+};
+
+// Maximum ladder length of the register-resident PT scan.
+constexpr int kMaxSlotsPT = 32;
+
+// Per-pair constants of the PT shortcut, staged in shared memory by the PT
+// kernels: dk = k_s - k_{s+1} and dkt = k_tau,s - k_tau,s+1 rounded to float,
+// and ge1[w] bit s set when base w (alpha+, alpha-, beta+, beta-) of pair s
+// is >= 1.
+struct PTConst {
+  float dkf[kMaxSlotsPT];
+  float dktf[kMaxSlotsPT];
+  uint32_t ge1[4];
+};
+
+// PT decision for the pair (s, s+1) of chain (a, r) after sweep t (Sec. 2.1):
+// accept iff u < P, P = alpha^|m| beta^|n| with m = A_Y - A_X, n = B_Y - B_X,
+// alpha = exp(+-(k_s - k_{s+1})) and beta = exp(+-(k_tau,s - k_tau,s+1))
+// chosen by the signs of m and n, u = x 2^-32 with x the pair's Philox word.
+//
+// The decision is the one of that exact rule; two shortcuts only skip work:
+//  * when both chosen factors are at least 1 (base >= 1 or exponent 0),
+//    P >= 1 > u: products and squares of numbers >= 1 round to numbers >= 1;
+//  * otherwise ln u (lnu, within 2e-5) is compared in float with
+//    lnP = m dk + n dkt, whose float evaluation is within
+//    (|m dk| + |n dkt|) 2.4e-7 of the double value; the exact power chain
+//    is within (2(|m|+|n|)+1) ulps (< 1e-5 in log for up to 2^31 sites) of
+//    exp of that value.  A margin err = 1e-4 + (|m dk| + |n dkt|) 4.8e-7
+//    covers all of these and the float rounding of the comparison, so
+//    outside it the outcome is the exact rule's.  x = 0, factors that could
+//    leave the normal range (|m dk| or |n dkt| >= 700) and the margin itself
+//    fall through to the exact product.
+// Exact evaluation of the rule (kept out of line: it is rarely taken and
+// inlining it would bloat the scan loop).
+static __device__ __noinline__ bool pt_exact(const double *sq, int s, int ia, int ib, long long m, long long n,
+                                      uint32_t x) {
+  const double fa = pow_chain(sq + ((size_t)s * 4 + ia) * kSqBits, (unsigned long long)(m >= 0 ? m : -m));
+  const double fb = pow_chain(sq + ((size_t)s * 4 + ib) * kSqBits, (unsigned long long)(n >= 0 ? n : -n));
+  const double P = __dmul_rn(fa, fb);
+  const double u = __dmul_rn((double)x, 0x1p-32);
+  return u < P;
+}
+
+__device__ __forceinline__ bool pt_decide(const PTConst &c, const double *sq, int s, long long m,
+                                          long long n, uint32_t x, float lnu) {
+  const int ia = m >= 0 ? 0 : 1, ib = n >= 0 ? 2 : 3;
+  if ((m == 0 || ((c.ge1[ia] >> s) & 1u)) && (n == 0 || ((c.ge1[ib] >> s) & 1u))) return true;
+  if (x != 0u) {
+    const float la = (float)m * c.dkf[s];
+    const float lb = (float)n * c.dktf[s];
+    if (fabsf(la) < 700.f && fabsf(lb) < 700.f) {
+      const float d = lnu - (la + lb);
+      const float err = 1e-4f + (fabsf(la) + fabsf(lb)) * 4.8e-7f;
+      if (d < -err) return true;
+      if (d > err) return false;
+    }
+  }
+  return pt_exact(sq, s, ia, ib, m, n, x);
+}
+
+// One PT pass of chain (a, r) over slot energies held by slot: us[s], ut[s]
+// are the unsatisfied spatial / tau bond counts of the configuration at slot
+// s (A = 2N - 2 us, B = N - 2 ut, so m = -2 (us_Y - us_X)).  Pairs are taken
+// in increasing s; an accepted pair swaps the entries of s and s+1 and sets
+// bit s of the returned mask.  The Philox words of all pairs and their
+// logarithms do not depend on the decisions and are computed up front.
+// The loops are kept rolled: the kernels that run this are a few warps
+// long, and an unrolled scan does not fit the instruction cache.
+__device__ __forceinline__ uint32_t pt_scan(int n_slots, long long *us, long long *ut, const PTConst &c,
+                                            const double *sq, uint2 key, uint32_t t, uint32_t a, int r) {
+  uint32_t xs[kMaxSlotsPT];
+  float lnu[kMaxSlotsPT];
+#pragma unroll 1
+  for (int s = 0; s + 1 < n_slots; ++s) {
+    xs[s] = pick4(philox(make_uint4((uint32_t)s, t, a, (DOM_PT << 28) | (uint32_t)(r >> 2)), key), r & 3);
+    lnu[s] = __logf((float)xs[s]) - 22.18070977791825f;
+  }
+  uint32_t acc = 0;
+#pragma unroll 1
+  for (int s = 0; s + 1 < n_slots; ++s) {
+      const long long m = -2 * (us[s + 1] - us[s]);
+      const long long n = -2 * (ut[s + 1] - ut[s]);
+      if (pt_decide(c, sq, s, m, n, xs[s], lnu[s])) {
+        const long long a1 = us[s], a2 = ut[s];
+        us[s] = us[s + 1];
+        ut[s] = ut[s + 1];
+        us[s + 1] = a1;
+        ut[s + 1] = a2;
+        acc |= 1u << s;
+      }
+  }
+  return acc;
+}
+
+// Stage the PT constants of a handle in shared memory (call with all
+// threads of the block, followed by __syncthreads()).
+__device__ __forceinline__ void load_ptconst(PTConst *dst, const PTConst *src) {
+  const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+  uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(PTConst) / 4); i += blockDim.x) d[i] = s[i];
 }
 
 // Sites of one colour: j in [0, N/2) -> site.  Each (y, tau) row holds L/2
@@ -87,11 +217,16 @@ struct qisg_handle {
   int64_t launches = 0;
   int device = 0;
   int n_sm = 0;
+  // SAMPLES sweep tile: site groups (of 4) per quad, 0 = choose; the grid
+  // aims at sweep_min_blocks_per_sm blocks per SM
+  int sweep_groups_per_quad = 0;
+  int sweep_min_blocks_per_sm = 4;
 
   // host tables (FP64, built once)
   std::vector<double> k, kt;
   std::vector<uint32_t> T;      // [n_slots][5][3]
-  std::vector<double> bases;    // [4][n_slots]: alpha+, alpha-, beta+, beta- of pair s
+  std::vector<double> bases;    // [6][n_slots]: alpha+, alpha-, beta+, beta-, dk, dkt of pair s
+  std::vector<double> sq;       // [n_slots-1][4][kSqBits]: b, b^2, b^4, ... of each base
 
   // LANES geometry: rpw replicas per word, n_groups words per site per sample
   int rpw = 0, n_groups = 0;
@@ -107,13 +242,15 @@ struct qisg_handle {
   size_t J_bytes = 0;
   uint32_t *d_T = nullptr;
   double *d_bases = nullptr;
+  double *d_sq = nullptr;           // [n_slots-1][4][kSqBits] squaring chains of the PT bases
+  void *d_ptc = nullptr;            // PTConst
   int32_t *d_walker = nullptr;      // [a_pad][r][s]
   unsigned long long *d_U = nullptr;  // LANES: [a][r][w][2] by walker; SAMPLES: [a_pad][r][s][2] by slot
   long long *d_sumA = nullptr, *d_sumB = nullptr, *d_sumq = nullptr, *d_sumq2 = nullptr;
   long long *d_q = nullptr;         // overlap scratch [a][s][pair]
   long long *d_out = nullptr;       // output staging [2][a][r][s]
   unsigned long long *d_t = nullptr;  // sweep counter
-  void *d_acc = nullptr;            // SAMPLES: PT accept masks [b][r][s]
+  void *d_acc = nullptr;            // SAMPLES: PT lane masks of the last pass, Word [b][r][s]
   int *d_err = nullptr;
   size_t device_bytes = 0;
 
@@ -121,6 +258,22 @@ struct qisg_handle {
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev[4];   // start/stop pairs per kernel kind
   int64_t prof_launched[4] = {0, 0, 0, 0};
+
+  // CUDA graph of one sweep cycle (lcm of the PT and measurement cadences),
+  // captured on cap_stream and replayed on stream
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t cyc_graph = nullptr;
+  cudaGraphExec_t cyc_exec = nullptr;
+  int cyc_sweeps = 0;
+  int64_t cyc_launches = 0, cyc_meas = 0;
+  int64_t cyc_prof_launched[4] = {0, 0, 0, 0};
+  bool cyc_profiled = false;
+  // event-record nodes of a profiled capture: node, kernel kind, 0 start / 1 stop
+  std::vector<cudaGraphNode_t> cyc_ev_nodes;
+  std::vector<std::pair<int, int>> cyc_ev_kind;
+  std::vector<cudaEvent_t> prof_spare;   // untimed events of replays past the pool
+  std::vector<cudaEvent_t> cyc_events;   // events referenced by the captured graph
 
   int n_pairs() const { return n_rep * (n_rep - 1) / 2; }
 };
@@ -155,6 +308,9 @@ int samples_set_couplings(qisg_handle *h, const int8_t *J);
 
 // common small kernels (qisg_api.cu)
 int advance_counter(qisg_handle *h);
+
+// PT pass of samples a0 .. a0+n_a-1 (pt.cu)
+int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a);
 
 // Launch timing: call prof_begin(h, kind) before and prof_end(h, kind, tok)
 // after a kernel launch on h->stream.

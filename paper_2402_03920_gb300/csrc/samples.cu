@@ -26,9 +26,6 @@ namespace {
 constexpr int kBlock = 256;          // 64 quads of 4 replicas
 constexpr int kQuads = kBlock / 4;
 constexpr int kMaxSlotsPermute = 32;
-constexpr int kKs = 11;              // per-thread planes: u_s sum <= 4 * 256 sites
-constexpr int kKt = 10;              // per-thread planes: u_t sum <= 2 * 256 sites
-constexpr int kMaxSitesPerThread = 256;
 
 template <typename Word>
 __device__ __forceinline__ Word ones_if(bool b) {
@@ -167,30 +164,60 @@ struct SamplesArgs {
   unsigned long long *U;
   const unsigned long long *d_t;
   uint2 key;
+  FastDiv half_plane_div;  // j -> tau for the L*L/2 sites of one colour per plane
   int64_t N, half_N;
-  int L, Lt, n_slots, n_rep, n_q, W;
+  int L, Lt, plane, half_plane, n_slots, n_rep, n_q, W;
   int groups_per_quad;   // site groups (4 sites) each quad handles
   int blocks_per_set;    // blocks per (b, s, q) word set
+  int t_has_zero;        // some threshold of the table is 0 (always reject)
 };
 
-// Reject flags of the 9 classes that can reject: rho = all ones iff the
-// class's threshold is not the always-accept sentinel and R >= T.
+// Shared-memory layout of the half sweep (dynamic).
 template <typename Word>
-__device__ __forceinline__ Word rho(uint32_t R, uint32_t T) {
+struct SweepSmem {
+  static size_t bytes(int plane) {
+    size_t o = sizeof(uint4) * 256 + 16 * 4 + 2 * 4 * 64 * 4;   // rnd, Ts, accU
+    o += 2 * (size_t)plane * sizeof(Word);                        // Jx, Jy
+    o += (size_t)plane * sizeof(uint2);                           // neighbours
+    o += (size_t)plane * sizeof(uint16_t);                        // colour-site table
+    return (o + 15) & ~size_t(15);
+  }
+};
+
+// Reject flag of a class: reject iff T is not the always-accept sentinel
+// and R >= T.  When no threshold of the table is 0 this is one compare,
+// R > Tm1, with Tm1 = T - 1 for finite thresholds and Tm1 = 0xFFFFFFFF (never
+// exceeded) for the sentinel; otherwise both conditions are tested.
+template <typename Word>
+__device__ __forceinline__ Word rho_gt(uint32_t R, uint32_t Tm1) {
+  return ones_if<Word>(R > Tm1);
+}
+template <typename Word>
+__device__ __forceinline__ Word rho_ge(uint32_t R, uint32_t T) {
   return ones_if<Word>(T != 0xFFFFFFFFu && R >= T);
 }
 
 // One half sweep.  Block: one (b, s, q) word set, 64 quads; quad thread j
 // owns replica r = 4q + j.  Per group of 4 sites every thread of a quad
 // computes one Philox call (for site 4G + j), which serves the four
-// replicas of that site; the results are exchanged in shared memory.
-template <typename Word, bool BLUE>
+// replicas of that site; the results are exchanged in shared memory.  The
+// colour-site -> site map, the neighbour table of the L x L plane and the
+// block's couplings are staged in shared memory once per block.
+// G2 = log2(groups per quad) sizes the per-thread energy counters.
+template <typename Word, bool BLUE, int G2>
 __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<Word> p, int colour,
                                                                     int count_only) {
   constexpr int W = (int)sizeof(Word) * 8;
-  __shared__ uint4 rnd[kBlock];
-  __shared__ uint32_t Ts[15];
-  __shared__ int accU[BLUE ? 2 * 4 * W : 1];
+  constexpr int KS = G2 + 5;   // u_s sum <= 4 * 4 * 2^G2 per thread
+  constexpr int KT = G2 + 4;   // u_t sum <= 2 * 4 * 2^G2 per thread
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint4 *rnd = reinterpret_cast<uint4 *>(smem);
+  uint32_t *Ts = reinterpret_cast<uint32_t *>(rnd + 256);
+  int *accU = reinterpret_cast<int *>(Ts + 16);
+  Word *Jx = reinterpret_cast<Word *>(accU + 2 * 4 * 64);
+  Word *Jy = Jx + p.plane;
+  uint2 *nb = reinterpret_cast<uint2 *>(Jy + p.plane);
+  uint16_t *s2d = reinterpret_cast<uint16_t *>(nb + p.plane);
 
   const int64_t set = blockIdx.x / p.blocks_per_set;
   const int chunk = (int)(blockIdx.x - set * p.blocks_per_set);
@@ -200,61 +227,80 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
   const int j = threadIdx.x & 3;
   const int quad = threadIdx.x >> 2;
   const int r = 4 * q + j;
+  const int L = p.L, plane = p.plane, hp = p.half_plane;
 
-  if (threadIdx.x < 15) Ts[threadIdx.x] = p.T[s * 15 + threadIdx.x];
+  if (threadIdx.x < 15) {
+    const uint32_t T = p.T[s * 15 + threadIdx.x];
+    // with no zero threshold: reject iff R > T - 1 (the sentinel stays)
+    Ts[threadIdx.x] = p.t_has_zero ? T : (T == 0xFFFFFFFFu ? T : T - 1u);
+  }
   if (BLUE)
     for (int i = threadIdx.x; i < 2 * 4 * W; i += blockDim.x) accU[i] = 0;
+  const Word *Jb = p.J + b * (int64_t)plane * 2;
+  for (int i2 = threadIdx.x; i2 < plane; i2 += blockDim.x) {
+    const int y = i2 / L, x = i2 - y * L;
+    const int xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
+    const int yp = y + 1 == L ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
+    nb[i2] = make_uint2((uint32_t)(xp + L * y) | ((uint32_t)(xm + L * y) << 16),
+                        (uint32_t)(x + L * yp) | ((uint32_t)(x + L * ym) << 16));
+    Jx[i2] = Jb[2 * i2];
+    Jy[i2] = Jb[2 * i2 + 1];
+    // the k-th site of parity (x + y) & 1 in row-major order is k = i2 / 2
+    s2d[((x + y) & 1) * hp + (i2 >> 1)] = (uint16_t)i2;
+  }
   __syncthreads();
 
   uint32_t T[15];
 #pragma unroll
   for (int i = 0; i < 15; ++i) T[i] = Ts[i];
+  const bool has_zero = p.t_has_zero != 0;
 
-  const int L = p.L, Lt = p.Lt;
-  const int64_t plane = (int64_t)L * L;
-  Word *base = p.spins + ((b * p.n_slots + s) * p.n_q + q) * p.N * 4;
-  const Word *Jb = p.J + b * plane * 2;
+  Word *base = p.spins + ((b * p.n_slots + s) * p.n_q + q) * p.N * 4 + j;
   const unsigned long long t = *p.d_t;
   const uint32_t ctr_z = (uint32_t)s | ((uint32_t)(r >> 2) << 16);
   const uint32_t ctr_w = (DOM_SWEEP << 28) | (uint32_t)((b * W) >> 6);
+  const uint32_t Lt = (uint32_t)p.Lt;
 
-  VCount<Word, kKs> cs;
-  VCount<Word, kKt> ct;
+  VCount<Word, KS> cs;
+  VCount<Word, KT> ct;
   if (BLUE) {
     cs.zero();
     ct.zero();
   }
 
-  const int64_t n_groups = p.half_N >> 2;
+  const uint32_t n_groups = (uint32_t)(p.half_N >> 2);
   for (int gi = 0; gi < p.groups_per_quad; ++gi) {
-    const int64_t G = ((int64_t)chunk * p.groups_per_quad + gi) * kQuads + quad;
+    const uint32_t G = ((uint32_t)chunk * p.groups_per_quad + gi) * kQuads + quad;
     const bool live = G < n_groups;   // uniform per quad
-    // one Philox per thread: site 4G + j of this colour
     if (live) {
-      const SiteXYT c = site_of_colour(4 * G + j, L, colour);
-      const int64_t site = c.x + (int64_t)L * c.y + plane * c.tau;
-      rnd[threadIdx.x] = philox(make_uint4((uint32_t)site, (uint32_t)t, ctr_z, ctr_w), p.key);
+      const uint32_t jj = 4 * G + j;
+      const uint32_t tau = p.half_plane_div.div(jj);
+      const uint32_t k = jj - tau * hp;
+      const uint32_t i2 = s2d[((colour + tau) & 1) * hp + k];
+      rnd[threadIdx.x] = philox(make_uint4(i2 + tau * plane, (uint32_t)t, ctr_z, ctr_w), p.key);
     }
     __syncwarp();
     if (live) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const uint4 rv = rnd[(quad << 2) + i];
-        const uint32_t R = pick4(rv, j);
-        const SiteXYT c = site_of_colour(4 * G + i, L, colour);
-        const int xp = c.x + 1 == L ? 0 : c.x + 1, xm = c.x == 0 ? L - 1 : c.x - 1;
-        const int yp = c.y + 1 == L ? 0 : c.y + 1, ym = c.y == 0 ? L - 1 : c.y - 1;
-        const int tp = c.tau + 1 == Lt ? 0 : c.tau + 1, tm = c.tau == 0 ? Lt - 1 : c.tau - 1;
-        const int64_t off_t = plane * c.tau;
-        const int64_t i2 = c.x + (int64_t)L * c.y;
-        const int64_t site = i2 + off_t;
-        const Word sc = base[site * 4 + j];
-        const Word b1 = sc ^ base[(xp + (int64_t)L * c.y + off_t) * 4 + j] ^ Jb[i2 * 2];
-        const Word b2 = sc ^ base[(xm + (int64_t)L * c.y + off_t) * 4 + j] ^ Jb[(xm + (int64_t)L * c.y) * 2];
-        const Word b3 = sc ^ base[(c.x + (int64_t)L * yp + off_t) * 4 + j] ^ Jb[i2 * 2 + 1];
-        const Word b4 = sc ^ base[(c.x + (int64_t)L * ym + off_t) * 4 + j] ^ Jb[(c.x + (int64_t)L * ym) * 2 + 1];
-        const Word t1 = sc ^ base[(i2 + plane * tp) * 4 + j];
-        const Word t2 = sc ^ base[(i2 + plane * tm) * 4 + j];
+        const uint32_t R = pick4(rnd[(quad << 2) + i], j);
+        const uint32_t jj = 4 * G + i;
+        const uint32_t tau = p.half_plane_div.div(jj);
+        const uint32_t k = jj - tau * hp;
+        const uint32_t i2 = s2d[((colour + tau) & 1) * hp + k];
+        const uint2 nv = nb[i2];
+        const uint32_t off = tau * plane;
+        const uint32_t offp = tau + 1 == Lt ? 0u : off + plane;
+        const uint32_t offm = tau == 0 ? (Lt - 1) * plane : off - plane;
+        const uint32_t site = i2 + off;
+        const uint32_t ixp = nv.x & 0xFFFFu, ixm = nv.x >> 16, iyp = nv.y & 0xFFFFu, iym = nv.y >> 16;
+        const Word sc = base[(size_t)site * 4];
+        const Word b1 = sc ^ base[(size_t)(ixp + off) * 4] ^ Jx[i2];
+        const Word b2 = sc ^ base[(size_t)(ixm + off) * 4] ^ Jx[ixm];
+        const Word b3 = sc ^ base[(size_t)(iyp + off) * 4] ^ Jy[i2];
+        const Word b4 = sc ^ base[(size_t)(iym + off) * 4] ^ Jy[iym];
+        const Word t1 = sc ^ base[(size_t)(i2 + offp) * 4];
+        const Word t2 = sc ^ base[(size_t)(i2 + offm) * 4];
         // bit-sliced u_s (3 bits) and u_t (2 bits)
         const Word s1 = b1 ^ b2 ^ b3;
         const Word c1 = maj3(b1, b2, b3);
@@ -269,17 +315,25 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
         Word rej;
         if (count_only) {
           rej = ~Word(0);
-        } else {
-          const Word row0 = mux(us2, rho<Word>(R, T[12]),
-                                mux(us1, mux(us0, rho<Word>(R, T[9]), rho<Word>(R, T[6])),
-                                    mux(us0, rho<Word>(R, T[3]), rho<Word>(R, T[0]))));
+        } else if (!has_zero) {
+          const Word row0 = mux(us2, rho_gt<Word>(R, T[12]),
+                                mux(us1, mux(us0, rho_gt<Word>(R, T[9]), rho_gt<Word>(R, T[6])),
+                                    mux(us0, rho_gt<Word>(R, T[3]), rho_gt<Word>(R, T[0]))));
           const Word low = ~(us1 | us2);
-          const Word row1 = low & mux(us0, rho<Word>(R, T[4]), rho<Word>(R, T[1]));
-          const Word row2 = low & mux(us0, rho<Word>(R, T[5]), rho<Word>(R, T[2]));
+          const Word row1 = low & mux(us0, rho_gt<Word>(R, T[4]), rho_gt<Word>(R, T[1]));
+          const Word row2 = low & mux(us0, rho_gt<Word>(R, T[5]), rho_gt<Word>(R, T[2]));
+          rej = mux(ut1, row2, mux(ut0, row1, row0));
+        } else {
+          const Word row0 = mux(us2, rho_ge<Word>(R, T[12]),
+                                mux(us1, mux(us0, rho_ge<Word>(R, T[9]), rho_ge<Word>(R, T[6])),
+                                    mux(us0, rho_ge<Word>(R, T[3]), rho_ge<Word>(R, T[0]))));
+          const Word low = ~(us1 | us2);
+          const Word row1 = low & mux(us0, rho_ge<Word>(R, T[4]), rho_ge<Word>(R, T[1]));
+          const Word row2 = low & mux(us0, rho_ge<Word>(R, T[5]), rho_ge<Word>(R, T[2]));
           rej = mux(ut1, row2, mux(ut0, row1, row0));
         }
         const Word flip = ~rej;
-        if (!count_only) base[site * 4 + j] = sc ^ flip;
+        if (!count_only) base[(size_t)site * 4] = sc ^ flip;
         if (BLUE) {
           // unsatisfied counts after the flip: u -> 4 - u (spatial), 2 - u (tau)
           const Word vs1 = us1 ^ (flip & us0);
@@ -294,8 +348,8 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
   }
 
   if (BLUE) {
-    flush_counter<Word, kKs, 4>(cs, accU);
-    flush_counter<Word, kKt, 4>(ct, accU + 4 * W);
+    flush_counter<Word, KS, 4>(cs, accU);
+    flush_counter<Word, KT, 4>(ct, accU + 4 * W);
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * W; i += blockDim.x) {
       const int jj = i / W, lane = i - jj * W;
@@ -315,71 +369,6 @@ __global__ void zero_u64_kernel(unsigned long long *p, int64_t n) {
     p[i] = 0;
 }
 
-// PT pass of chain (a, r), energies by slot.  Threads of a warp are 32
-// consecutive samples of one (b, r); the accept flags of pair s become the
-// lane masks acc[b][r][s] through a ballot.
-template <typename Word>
-__global__ void samples_pt_kernel(int32_t *walker, unsigned long long *U, Word *acc,
-                                  const double *bases, const unsigned long long *d_t, uint2 key,
-                                  int64_t n_samples, int n_rep, int n_slots, int64_t n_b,
-                                  int explicit_pass) {
-  constexpr int W = (int)sizeof(Word) * 8;
-  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= n_b * n_rep * W) return;   // whole warps (W multiple of 32)
-  const int lane = (int)(gid % W);
-  const int r = (int)((gid / W) % n_rep);
-  const int64_t b = gid / ((int64_t)W * n_rep);
-  const int64_t a = b * W + lane;
-  const bool real = a < n_samples;
-  const unsigned long long t = explicit_pass ? *d_t - 1ull : *d_t;
-  int32_t *wa = walker + (a * n_rep + r) * n_slots;
-  unsigned long long *Ua = U + (a * n_rep + r) * n_slots * 2;
-  const double *ap = bases, *am = bases + n_slots, *bp = bases + 2 * n_slots,
-               *bm = bases + 3 * n_slots;
-  Word *accw = acc + (b * n_rep + r) * n_slots;
-  unsigned long long usX = real ? Ua[0] : 0, utX = real ? Ua[1] : 0;
-  for (int s = 0; s + 1 < n_slots; ++s) {
-    bool accept = false;
-    unsigned long long usY = 0, utY = 0;
-    if (real) {
-      usY = Ua[2 * (s + 1)];
-      utY = Ua[2 * (s + 1) + 1];
-      // m = A_Y - A_X with A = 2N - 2 U_s; n likewise with B = N - 2 U_t
-      const long long m = -2 * ((long long)usY - (long long)usX);
-      const long long n = -2 * ((long long)utY - (long long)utX);
-      const double fa = pow_rn(m >= 0 ? ap[s] : am[s], (unsigned long long)(m >= 0 ? m : -m));
-      const double fb = pow_rn(n >= 0 ? bp[s] : bm[s], (unsigned long long)(n >= 0 ? n : -n));
-      const double P = __dmul_rn(fa, fb);
-      const uint4 x = philox(make_uint4((uint32_t)s, (uint32_t)t, (uint32_t)a,
-                                        (DOM_PT << 28) | (uint32_t)(r >> 2)),
-                             key);
-      const double u = __dmul_rn((double)pick4(x, r & 3), 0x1p-32);
-      accept = u < P;
-    }
-    if (accept) {
-      const int32_t X = wa[s];
-      wa[s] = wa[s + 1];
-      wa[s + 1] = X;
-      // the configuration from s+1 now sits at s: its energies move with it,
-      // and the one from s carries on to be compared at s+1
-      Ua[2 * s] = usY;
-      Ua[2 * s + 1] = utY;
-      Ua[2 * (s + 1)] = usX;
-      Ua[2 * (s + 1) + 1] = utX;
-    } else {
-      usX = usY;
-      utX = utY;
-    }
-    const unsigned m32 = __ballot_sync(0xffffffffu, accept);
-    if ((threadIdx.x & 31) == 0) {
-      if (W == 64)
-        reinterpret_cast<unsigned *>(&accw[s])[(lane >> 5)] = m32;
-      else
-        accw[s] = (Word)m32;
-    }
-  }
-}
-
 // Apply the PT pass to the spins: for pair s = 0 .. n_slots-2 in order,
 // exchange the bits of accepting lanes between slot words s and s+1.
 template <typename Word>
@@ -387,16 +376,22 @@ __global__ void __launch_bounds__(kBlock) samples_permute_kernel(Word *spins, co
                                                                  int n_slots, int n_q, int n_rep,
                                                                  int blocks_per_set) {
   __shared__ Word accs[4 * kMaxSlotsPermute];
+  __shared__ int any;
   const int64_t set = blockIdx.x / blocks_per_set;     // (b, q)
   const int chunk = (int)(blockIdx.x - set * blocks_per_set);
   const int q = (int)(set % n_q);
   const int64_t b = set / n_q;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
   for (int i = threadIdx.x; i < 4 * n_slots; i += blockDim.x) {
     const int jj = i / n_slots, s = i - jj * n_slots;
     const int rr = 4 * q + jj;
-    accs[jj * kMaxSlotsPermute + s] = rr < n_rep ? acc[(b * n_rep + rr) * n_slots + s] : Word(0);
+    const Word m = (rr < n_rep && s + 1 < n_slots) ? acc[(b * n_rep + rr) * n_slots + s] : Word(0);
+    accs[jj * kMaxSlotsPermute + s] = m;
+    if (m) any = 1;
   }
   __syncthreads();
+  if (!any) return;   // no exchange in this (b, q): nothing moves
   const int64_t idx = (int64_t)chunk * blockDim.x + threadIdx.x;   // (site, j)
   if (idx >= N * 4) return;
   const int jj = (int)(idx & 3);
@@ -570,22 +565,58 @@ SamplesArgs<Word> make_args(qisg_handle *h) {
   p.half_N = h->N / 2;
   p.L = h->L;
   p.Lt = h->Lt;
+  p.plane = h->L * h->L;
+  p.half_plane = p.plane / 2;
+  p.half_plane_div = FastDiv((uint32_t)p.half_plane);
   p.n_slots = h->n_slots;
   p.n_rep = h->n_rep;
   p.n_q = h->n_q;
   p.W = h->W;
-  // site groups of one word set, spread so that the grid fills the GPU:
-  // at least ~4 blocks per SM, at most kMaxSitesPerThread sites per thread
+  p.t_has_zero = 0;
+  for (uint32_t v : h->T)
+    if (v == 0) p.t_has_zero = 1;
+  // site groups of one word set per quad: a power of two, as large as
+  // possible (cheaper energy flushes) while the grid still gives about
+  // min_blocks_per_sm blocks to every SM
   const int64_t n_groups = p.half_N / 4;
   const int64_t sets = h->n_b * h->n_slots * h->n_q;
-  int gpq = (int)std::min<int64_t>(kMaxSitesPerThread / 4, (n_groups + kQuads - 1) / kQuads);
-  const int64_t want_blocks = 4LL * std::max(1, h->n_sm);
-  while (gpq > 1 && sets * ((n_groups + (int64_t)kQuads * gpq - 1) / ((int64_t)kQuads * gpq)) < want_blocks)
-    gpq >>= 1;
-  p.groups_per_quad = std::max(1, gpq);
-  p.blocks_per_set = (int)((n_groups + (int64_t)kQuads * p.groups_per_quad - 1) /
-                           ((int64_t)kQuads * p.groups_per_quad));
+  int gpq = 64;
+  const int64_t want_blocks = (int64_t)h->sweep_min_blocks_per_sm * std::max(1, h->n_sm);
+  if (h->sweep_groups_per_quad > 0) {
+    gpq = h->sweep_groups_per_quad;
+  } else {
+    while (gpq > 1 && sets * ((n_groups + (int64_t)kQuads * gpq - 1) / ((int64_t)kQuads * gpq)) < want_blocks)
+      gpq >>= 1;
+  }
+  p.groups_per_quad = gpq;
+  p.blocks_per_set = (int)((n_groups + (int64_t)kQuads * gpq - 1) / ((int64_t)kQuads * gpq));
   return p;
+}
+
+template <typename Word, bool BLUE, int G2>
+void launch_sweep(const SamplesArgs<Word> &p, unsigned blocks, size_t smem, cudaStream_t st, int colour,
+                  int count_only) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(samples_half_sweep_kernel<Word, BLUE, G2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr_set = true;
+  }
+  samples_half_sweep_kernel<Word, BLUE, G2><<<blocks, kBlock, smem, st>>>(p, colour, count_only);
+}
+
+template <typename Word, bool BLUE>
+void launch_sweep_g(const SamplesArgs<Word> &p, unsigned blocks, size_t smem, cudaStream_t st, int colour,
+                    int count_only) {
+  switch (p.groups_per_quad) {
+    case 1: launch_sweep<Word, BLUE, 0>(p, blocks, smem, st, colour, count_only); break;
+    case 2: launch_sweep<Word, BLUE, 1>(p, blocks, smem, st, colour, count_only); break;
+    case 4: launch_sweep<Word, BLUE, 2>(p, blocks, smem, st, colour, count_only); break;
+    case 8: launch_sweep<Word, BLUE, 3>(p, blocks, smem, st, colour, count_only); break;
+    case 16: launch_sweep<Word, BLUE, 4>(p, blocks, smem, st, colour, count_only); break;
+    case 32: launch_sweep<Word, BLUE, 5>(p, blocks, smem, st, colour, count_only); break;
+    default: launch_sweep<Word, BLUE, 6>(p, blocks, smem, st, colour, count_only); break;
+  }
 }
 
 template <typename Word>
@@ -599,11 +630,12 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
     zero_u64_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, h->stream>>>(h->d_U, n);
     h->launches++;
   }
+  const size_t smem = SweepSmem<Word>::bytes(p.plane);
   const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
   if (colour == 1)
-    samples_half_sweep_kernel<Word, true><<<(unsigned)blocks, kBlock, 0, h->stream>>>(p, 1, count_only);
+    launch_sweep_g<Word, true>(p, (unsigned)blocks, smem, h->stream, 1, count_only);
   else
-    samples_half_sweep_kernel<Word, false><<<(unsigned)blocks, kBlock, 0, h->stream>>>(p, 0, count_only);
+    launch_sweep<Word, false, 0>(p, (unsigned)blocks, smem, h->stream, 0, count_only);
   prof_end(h, QISG_KERNEL_SWEEP, tok);
   h->launches++;
   return cuda_check(cudaGetLastError(), "samples half sweep");
@@ -611,19 +643,11 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
 
 template <typename Word>
 int pt_t(qisg_handle *h, int explicit_pass) {
-  const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
-  const int64_t n = h->n_b * h->n_rep * h->W;
-  int tok = prof_begin(h, QISG_KERNEL_PT);
-  samples_pt_kernel<Word><<<(unsigned)((n + 127) / 128), 128, 0, h->stream>>>(
-      h->d_walker, h->d_U, reinterpret_cast<Word *>(h->d_acc), h->d_bases, h->d_t, key, h->n_samples,
-      h->n_rep, h->n_slots, h->n_b, explicit_pass);
-  prof_end(h, QISG_KERNEL_PT, tok);
-  h->launches++;
-  int rc = cuda_check(cudaGetLastError(), "samples pt");
+  int rc = pt_pass(h, explicit_pass, 0, h->n_samples);
   if (rc) return rc;
   const int64_t per_set = (h->N * 4 + kBlock - 1) / kBlock;
   const int64_t blocks = h->n_b * h->n_q * per_set;
-  tok = prof_begin(h, QISG_KERNEL_PERMUTE);
+  const int tok = prof_begin(h, QISG_KERNEL_PERMUTE);
   samples_permute_kernel<Word><<<(unsigned)blocks, kBlock, 0, h->stream>>>(
       reinterpret_cast<Word *>(h->spins), reinterpret_cast<const Word *>(h->d_acc), h->N, h->n_slots,
       h->n_q, h->n_rep, (int)per_set);
@@ -760,6 +784,9 @@ int set_couplings_t(qisg_handle *h, const int8_t *J) {
 
 int samples_init(qisg_handle *h) {
   if (h->n_slots > kMaxSlotsPermute) return fail(QISG_EINVAL, "SAMPLES packing supports up to 32 slots");
+  if (h->L > 128) return fail(QISG_EINVAL, "SAMPLES packing supports L <= 128");
+  if (SweepSmem<unsigned long long>::bytes(h->L * h->L) > 227 * 1024)
+    return fail(QISG_EINVAL, "plane tables exceed shared memory");
   return h->W == 64 ? init_t<unsigned long long>(h) : init_t<unsigned int>(h);
 }
 int samples_half_sweep(qisg_handle *h, int colour, int count_only) {

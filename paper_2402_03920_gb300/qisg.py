@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True):
         "qisg_last_error": (ctypes.c_char_p, []),
         "qisg_philox4x32_10": (I, [P, P, P, I64, P]),
         "qisg_profile": (I, [P, I]),
+        "qisg_set_graphs": (I, [P, I]),
+        "qisg_autotune": (I, [P, I, P]),
         "qisg_profile_read": (I, [P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -97,7 +99,8 @@ def exported_symbols():
             "qisg_get_couplings", "qisg_set_couplings", "qisg_set_state", "qisg_measurements",
             "qisg_slot_means", "qisg_thresholds", "qisg_sweep_count", "qisg_layout",
             "qisg_launch_count", "qisg_sync", "qisg_destroy", "qisg_strerror", "qisg_last_error",
-            "qisg_philox4x32_10", "qisg_profile", "qisg_profile_read"]
+            "qisg_philox4x32_10", "qisg_profile", "qisg_profile_read", "qisg_set_graphs",
+            "qisg_autotune"]
 
 
 def _check(rc: int):
@@ -267,6 +270,15 @@ class Instance:
         lay, wb = ctypes.c_int(), ctypes.c_int()
         _check(load().qisg_layout(self._h, ctypes.byref(lay), ctypes.byref(wb)))
         return lay.value, wb.value
+
+    def set_graphs(self, enable: bool):
+        _check(load().qisg_set_graphs(self._h, 1 if enable else 0))
+
+    def autotune(self, sweeps_per_candidate: int = 2) -> int:
+        """Pick the fastest sweep tile on the live state (advances the run)."""
+        g = ctypes.c_int()
+        _check(load().qisg_autotune(self._h, sweeps_per_candidate, ctypes.byref(g)))
+        return g.value
 
     def profile(self, enable: bool):
         _check(load().qisg_profile(self._h, 1 if enable else 0))

@@ -155,3 +155,67 @@ def test_batched_full_size_sampled(qisg):
             states = list(ex.map(replay, picks))
         for s, st in zip(picks, states):
             assert_same_state(inst, st, a_lo=s, what=f"sample {s}")
+
+
+@pytest.mark.parametrize("layout", ["LANES", "SAMPLES"])
+def test_extreme_ladder_exact_paths(qisg, layout):
+    """A ladder from k = 0.05 to k = 12 with k_tau from Gamma = 0.3: the PT
+    exponents reach |m dk| > 700 (the exact power chain, with overflow and
+    underflow) and the Metropolis table holds zero thresholds (flips that
+    are never accepted)."""
+    import numpy as np
+    lay = qisg.QISG_LAYOUT_LANES if layout == "LANES" else qisg.QISG_LAYOUT_SAMPLES
+    ladder = qisg.ladder_linear(0.05, 12.0, 6, 0.3)
+    T = oracle.thresholds(ladder[:, 0], ladder[:, 1])
+    assert (T == 0).any()
+    n_a = 1 if layout == "LANES" else 33
+    cfg = qisg.Config(6, 8, ladder, 4, n_a, 77, layout=lay, measure_every=3)
+    st = oracle_state(ladder, 6, 8, 4, 77, 0, n_a)
+    with qisg.Instance(cfg) as inst:
+        for n in (1, 5, 30):
+            inst.sweep(n)
+            oracle.run(st, n, pt_every=1, measure_every=3)
+            assert_same_state(inst, st, what=f"{layout} after {st.t}")
+        sA = inst.measurements()[0]
+        assert np.array_equal(sA, st.sumA)
+
+
+def test_graph_replay_equals_direct_launches(qisg):
+    """Sweeps replayed from the captured cycle graph (cycle = 5 sweeps here)
+    give the trajectory of direct launches, with live kernel timing."""
+    import numpy as np
+    kw = dict(layout=qisg.QISG_LAYOUT_SAMPLES, measure_every=5, word_bits=32)
+    a, _ = make(qisg, 6, 8, 0.2, 0.5, 8, 1.0, 4, 40, 21, **kw)
+    b, _ = make(qisg, 6, 8, 0.2, 0.5, 8, 1.0, 4, 40, 21, **kw)
+    with a, b:
+        b.set_graphs(False)
+        a.sweep(3)            # not at a cycle boundary: direct launches
+        a.profile(True)
+        a.sweep(17)           # 2 replays + ...
+        ms, timed, launched = a.profile_read(qisg.KERNEL_SWEEP)
+        a.profile(False)
+        a.sweep(5)
+        b.sweep(25)
+        assert launched == 2 * 17 and timed == launched and ms > 0
+        assert a.sweep_count() == b.sweep_count() == 25
+        assert np.array_equal(a.spins(), b.spins())
+        assert np.array_equal(a.permutation(), b.permutation())
+        for x, y in zip(a.measurements(), b.measurements()):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+        assert a.launch_count() == b.launch_count()
+
+
+def test_autotune_keeps_trajectory(qisg):
+    import numpy as np
+    kw = dict(layout=qisg.QISG_LAYOUT_SAMPLES, word_bits=64)
+    a, _ = make(qisg, 8, 16, 0.2, 0.5, 8, 1.0, 4, 64, 5, **kw)
+    b, _ = make(qisg, 8, 16, 0.2, 0.5, 8, 1.0, 4, 64, 5, **kw)
+    with a, b:
+        g = a.autotune(1)
+        assert g in (1, 2, 4, 8, 16, 32, 64)
+        n = a.sweep_count()
+        assert n == 7 * 2
+        a.sweep(6)
+        b.sweep(n + 6)
+        assert np.array_equal(a.spins(), b.spins())
+        assert np.array_equal(a.permutation(), b.permutation())
