@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(kBlock) lanes_half_sweep_kernel(LanesArgs<Word
     e_s[2 * i + 1] = 0;
   }
   for (int i = threadIdx.x; i < p.sites_per_block * n_groups; i += blockDim.x) flip_s[i] = 0;
+  if (colour == 0 && blockIdx.x == 0)   // bond counters of this sample, filled by the blue pass
+    for (int i = threadIdx.x; i < 2 * n_rep * n_slots; i += blockDim.x) p.U[a * n_rep * n_slots * 2 + i] = 0;
   for (int i2 = threadIdx.x; i2 < plane; i2 += blockDim.x) {
     const int y = i2 / L, x = i2 - y * L;
     const int xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
@@ -358,11 +360,6 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   const int64_t blocks = (p.half_N + p.sites_per_block - 1) / p.sites_per_block;
   const size_t smem = lanes_smem_bytes<Word>(h, p.sites_per_block);
   if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
-  if (colour == 0) {
-    const int64_t n = h->n_samples * h->n_rep * h->n_slots * 2;
-    zero_u64_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, h->stream>>>(h->d_U, n);
-    h->launches++;
-  }
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(lanes_half_sweep_kernel<Word>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

@@ -8,9 +8,9 @@
 //
 //   LANES  : energies are counted by walker; the pass reorders walker_at.
 //   SAMPLES: energies are counted by slot; the pass reorders walker_at and
-//            the slot energies.  A block is the 32 chains of one (sample
-//            block b, replica r, 32-lane half); their accepted pairs are
-//            gathered into the lane masks acc[b][r][s] (bit l: sample b*W+l
+//            the slot energies.  A block is the 8 chains of one (sample
+//            block b, replica r, 8-lane octet); their accepted pairs are
+//            OR-ed into the lane masks acc[b][r][s] (bit l: sample b*W+l
 //            exchanged pair (s, s+1)), from which the permute kernel moves
 //            the spin bits.
 #include "qisg_internal.cuh"
@@ -98,25 +98,25 @@ __global__ void pt_lanes_kernel(int32_t *walker, unsigned long long *U, const PT
                   r, n_slots);
 }
 
-// SAMPLES: block = 32 warps = samples b*W + h*32 + v (v = warp) of replica r;
-// warp 0 then turns the 32 accept bitmasks into the lane masks (32-bit half
-// h of acc[b][r][s]).
+// SAMPLES: block = 8 warps = samples b*W + 8*o + v (v = warp) of replica r;
+// thread 0 then ORs the 8 accept bitmasks into the lane masks acc[b][r][s]
+// (cleared by the red pass of the sweep).
 template <typename Word>
-__global__ void __launch_bounds__(1024) pt_samples_kernel(int32_t *walker, unsigned long long *U, Word *accw,
-                                                          const PTConst *ptc, const double *sq,
-                                                          const unsigned long long *d_t, uint2 key,
-                                                          int64_t n_samples, int n_rep, int n_slots,
-                                                          int explicit_pass) {
-  constexpr int W = (int)sizeof(Word) * 8, halves = W / 32;
+__global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsigned long long *U, Word *accw,
+                                                         const PTConst *ptc, const double *sq,
+                                                         const unsigned long long *d_t, uint2 key,
+                                                         int64_t n_samples, int n_rep, int n_slots,
+                                                         int explicit_pass) {
+  constexpr int W = (int)sizeof(Word) * 8, octs = W / 8;
   __shared__ PTConst pc;
-  __shared__ uint32_t bits[32];
+  __shared__ uint32_t bits[8];
   load_ptconst(&pc, ptc);
   __syncthreads();
-  const int h = (int)(blockIdx.x % halves);
-  const int r = (int)((blockIdx.x / halves) % n_rep);
-  const int64_t b = blockIdx.x / ((int64_t)halves * n_rep);
+  const int o = (int)(blockIdx.x % octs);
+  const int r = (int)((blockIdx.x / octs) % n_rep);
+  const int64_t b = blockIdx.x / ((int64_t)octs * n_rep);
   const int v = threadIdx.x >> 5;
-  const int64_t a = b * W + h * 32 + v;
+  const int64_t a = b * W + 8 * o + v;
   uint32_t acc = 0;
   if (a < n_samples) {
     const uint32_t t = (uint32_t)(explicit_pass ? *d_t - 1ull : *d_t);
@@ -125,16 +125,16 @@ __global__ void __launch_bounds__(1024) pt_samples_kernel(int32_t *walker, unsig
   }
   if ((threadIdx.x & 31) == 0) bits[v] = acc;
   __syncthreads();
-  if (v == 0) {
-    const uint32_t mine = bits[threadIdx.x];
+  if (threadIdx.x == 0) {
     Word *out = accw + (b * n_rep + r) * n_slots;
     for (int s = 0; s + 1 < n_slots; ++s) {
-      const unsigned m32 = __ballot_sync(0xffffffffu, (mine >> s) & 1u);
-      if (threadIdx.x == 0) {
-        if (W == 64)
-          reinterpret_cast<unsigned *>(&out[s])[h] = m32;
+      Word m = 0;
+      for (int u = 0; u < 8; ++u) m |= (Word)((bits[u] >> s) & 1u) << (8 * o + u);
+      if (m) {
+        if (sizeof(Word) == 8)
+          atomicOr(reinterpret_cast<unsigned long long *>(&out[s]), (unsigned long long)m);
         else
-          out[s] = (Word)m32;
+          atomicOr(reinterpret_cast<unsigned int *>(&out[s]), (unsigned int)m);
       }
     }
   }
@@ -146,14 +146,14 @@ int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a) {
   const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
   const int tok = prof_begin(h, QISG_KERNEL_PT);
   if (h->layout == QISG_LAYOUT_SAMPLES) {
-    const unsigned blocks = (unsigned)(h->n_b * h->n_rep * (h->W / 32));
+    const unsigned blocks = (unsigned)(h->n_b * h->n_rep * (h->W / 8));
     if (h->W == 64)
-      pt_samples_kernel<unsigned long long><<<blocks, 1024, 0, h->stream>>>(
+      pt_samples_kernel<unsigned long long><<<blocks, 256, 0, h->stream>>>(
           h->d_walker, h->d_U, reinterpret_cast<unsigned long long *>(h->d_acc),
           reinterpret_cast<const PTConst *>(h->d_ptc), h->d_sq, h->d_t, key, h->n_samples, h->n_rep,
           h->n_slots, explicit_pass);
     else
-      pt_samples_kernel<unsigned int><<<blocks, 1024, 0, h->stream>>>(
+      pt_samples_kernel<unsigned int><<<blocks, 256, 0, h->stream>>>(
           h->d_walker, h->d_U, reinterpret_cast<unsigned int *>(h->d_acc),
           reinterpret_cast<const PTConst *>(h->d_ptc), h->d_sq, h->d_t, key, h->n_samples, h->n_rep,
           h->n_slots, explicit_pass);

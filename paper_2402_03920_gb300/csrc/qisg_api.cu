@@ -374,13 +374,25 @@ int one_sweep(qisg_handle *h) {
   const uint64_t t = h->t;
   int rc = lanes ? lanes_half_sweep(h, 0, 0) : samples_half_sweep(h, 0, 0);
   if (!rc) rc = lanes ? lanes_half_sweep(h, 1, 0) : samples_half_sweep(h, 1, 0);
-  if (!rc && h->pt_every > 0 && (t + 1) % (uint64_t)h->pt_every == 0)
-    rc = lanes ? lanes_pt(h, 0) : samples_pt(h, 0);
+  bool advanced = false;
+  if (!rc && h->pt_every > 0 && (t + 1) % (uint64_t)h->pt_every == 0) {
+    if (lanes) {
+      rc = lanes_pt(h, 0);
+    } else {
+      rc = samples_pt(h, 0, 1);   // the permute kernel advances the counter
+      advanced = true;
+    }
+  }
   if (!rc && h->measure_every > 0 && (t + 1) % (uint64_t)h->measure_every == 0) {
     rc = lanes ? lanes_measure(h, 0) : samples_measure(h, 0);
     h->n_meas++;
   }
-  if (!rc) rc = advance_counter(h);
+  if (!rc) {
+    if (advanced)
+      h->t++;
+    else
+      rc = advance_counter(h);
+  }
   return rc;
 }
 
@@ -599,7 +611,7 @@ int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
 int qisg_pt_swap(qisg_handle *h) {
   if (!h) return fail(QISG_EINVAL, "NULL handle");
   if (h->t == 0) return fail(QISG_ESTATE, "no sweep has run yet");
-  return h->layout == QISG_LAYOUT_LANES ? lanes_pt(h, 1) : samples_pt(h, 1);
+  return h->layout == QISG_LAYOUT_LANES ? lanes_pt(h, 1) : samples_pt(h, 1, 0);
 }
 
 int qisg_energies(qisg_handle *h, int64_t *A, int64_t *B) {

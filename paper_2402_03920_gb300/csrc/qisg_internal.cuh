@@ -298,7 +298,7 @@ int lanes_set_couplings(qisg_handle *h, const int8_t *J);
 // SAMPLES kernels (samples.cu)
 int samples_init(qisg_handle *h);
 int samples_half_sweep(qisg_handle *h, int colour, int count_only);
-int samples_pt(qisg_handle *h, int explicit_pass);
+int samples_pt(qisg_handle *h, int explicit_pass, int advance);
 int samples_measure(qisg_handle *h, int force_to_q);
 int samples_energies_by_slot(qisg_handle *h);
 int samples_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S);

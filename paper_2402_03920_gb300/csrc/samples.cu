@@ -170,6 +170,11 @@ struct SamplesArgs {
   int groups_per_quad;   // site groups (4 sites) each quad handles
   int blocks_per_set;    // blocks per (b, s, q) word set
   int t_has_zero;        // some threshold of the table is 0 (always reject)
+  // cleared by the red pass (nothing reads them until the blue pass / PT):
+  unsigned long long *zero_U;   // bond counters, n_zero_U words
+  int64_t n_zero_U;
+  Word *zero_acc;               // PT lane masks, n_zero_acc words
+  int64_t n_zero_acc;
 };
 
 // Shared-memory layout of the half sweep (dynamic).
@@ -236,6 +241,12 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
   }
   if (BLUE)
     for (int i = threadIdx.x; i < 2 * 4 * W; i += blockDim.x) accU[i] = 0;
+  if (!BLUE) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_acc; i += stride)
+      p.zero_acc[i] = 0;
+  }
   const Word *Jb = p.J + b * (int64_t)plane * 2;
   for (int i2 = threadIdx.x; i2 < plane; i2 += blockDim.x) {
     const int y = i2 / L, x = i2 - y * L;
@@ -371,12 +382,16 @@ __global__ void zero_u64_kernel(unsigned long long *p, int64_t n) {
 
 // Apply the PT pass to the spins: for pair s = 0 .. n_slots-2 in order,
 // exchange the bits of accepting lanes between slot words s and s+1.
+// With advance set, block 0 also advances the sweep counter (nothing in this
+// kernel reads it), saving the separate launch at the end of the sweep.
 template <typename Word>
 __global__ void __launch_bounds__(kBlock) samples_permute_kernel(Word *spins, const Word *acc, int64_t N,
                                                                  int n_slots, int n_q, int n_rep,
-                                                                 int blocks_per_set) {
+                                                                 int blocks_per_set,
+                                                                 unsigned long long *advance) {
   __shared__ Word accs[4 * kMaxSlotsPermute];
   __shared__ int any;
+  if (advance && blockIdx.x == 0 && threadIdx.x == 0) *advance += 1ull;
   const int64_t set = blockIdx.x / blocks_per_set;     // (b, q)
   const int chunk = (int)(blockIdx.x - set * blocks_per_set);
   const int q = (int)(set % n_q);
@@ -572,6 +587,10 @@ SamplesArgs<Word> make_args(qisg_handle *h) {
   p.n_rep = h->n_rep;
   p.n_q = h->n_q;
   p.W = h->W;
+  p.zero_U = h->d_U;
+  p.n_zero_U = h->n_a_pad * h->n_rep * h->n_slots * 2;
+  p.zero_acc = reinterpret_cast<Word *>(h->d_acc);
+  p.n_zero_acc = h->n_b * h->n_rep * h->n_slots;
   p.t_has_zero = 0;
   for (uint32_t v : h->T)
     if (v == 0) p.t_has_zero = 1;
@@ -625,11 +644,6 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   const int64_t sets = h->n_b * h->n_slots * h->n_q;
   const int64_t blocks = sets * p.blocks_per_set;
   if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
-  if (colour == 0) {
-    const int64_t n = h->n_a_pad * h->n_rep * h->n_slots * 2;
-    zero_u64_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, h->stream>>>(h->d_U, n);
-    h->launches++;
-  }
   const size_t smem = SweepSmem<Word>::bytes(p.plane);
   const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
   if (colour == 1)
@@ -642,15 +656,19 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
 }
 
 template <typename Word>
-int pt_t(qisg_handle *h, int explicit_pass) {
-  int rc = pt_pass(h, explicit_pass, 0, h->n_samples);
+int pt_t(qisg_handle *h, int explicit_pass, int advance) {
+  int rc = QISG_OK;
+  if (explicit_pass)   // the masks are cleared by the red pass of a sweep only
+    rc = cuda_check(cudaMemsetAsync(h->d_acc, 0, (size_t)h->n_b * h->n_rep * h->n_slots * sizeof(Word), h->stream),
+                    "clear PT masks");
+  if (!rc) rc = pt_pass(h, explicit_pass, 0, h->n_samples);
   if (rc) return rc;
   const int64_t per_set = (h->N * 4 + kBlock - 1) / kBlock;
   const int64_t blocks = h->n_b * h->n_q * per_set;
   const int tok = prof_begin(h, QISG_KERNEL_PERMUTE);
   samples_permute_kernel<Word><<<(unsigned)blocks, kBlock, 0, h->stream>>>(
       reinterpret_cast<Word *>(h->spins), reinterpret_cast<const Word *>(h->d_acc), h->N, h->n_slots,
-      h->n_q, h->n_rep, (int)per_set);
+      h->n_q, h->n_rep, (int)per_set, advance ? h->d_t : nullptr);
   prof_end(h, QISG_KERNEL_PERMUTE, tok);
   h->launches++;
   return cuda_check(cudaGetLastError(), "samples permute");
@@ -793,8 +811,9 @@ int samples_half_sweep(qisg_handle *h, int colour, int count_only) {
   return h->W == 64 ? half_sweep_t<unsigned long long>(h, colour, count_only)
                     : half_sweep_t<unsigned int>(h, colour, count_only);
 }
-int samples_pt(qisg_handle *h, int explicit_pass) {
-  return h->W == 64 ? pt_t<unsigned long long>(h, explicit_pass) : pt_t<unsigned int>(h, explicit_pass);
+int samples_pt(qisg_handle *h, int explicit_pass, int advance) {
+  return h->W == 64 ? pt_t<unsigned long long>(h, explicit_pass, advance)
+                    : pt_t<unsigned int>(h, explicit_pass, advance);
 }
 int samples_measure(qisg_handle *h, int force_to_q) {
   return h->W == 64 ? measure_t<unsigned long long>(h, force_to_q) : measure_t<unsigned int>(h, force_to_q);
