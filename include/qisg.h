@@ -238,6 +238,72 @@ const char *qisg_last_error(void);
 int qisg_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
                        void *cuda_stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched form: many independent single-sample instances of uneven size in  */
+/* one persistent kernel (and the building block of the serving loop).       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct qisg_batch qisg_batch;
+
+/* One instance: an L x L x L_tau prism with its own ladder, n_replicas
+ * replicas, one disorder sample drawn from `seed`, and a sweep target
+ * (0 = no limit).  Its trajectory is that of qisg_create(L, L_tau, ladder,
+ * n_slots, n_replicas, 1, seed) with pt_every = 1. */
+typedef struct {
+    int L, L_tau, n_slots, n_replicas;
+    const qisg_slot *ladder;    /* host array of n_slots (copied at admission) */
+    uint64_t seed;
+    int64_t n_sweeps;
+} qisg_instance_desc;
+
+/* A batch with `capacity` instance slots whose device state lives in one
+ * arena of mem_budget bytes (0: half of the free device memory), work ordered
+ * on cuda_stream.  ENOMEM if the arena cannot be allocated. */
+int qisg_batch_create(qisg_batch **out, int capacity, size_t mem_budget, void *cuda_stream);
+
+/* Admit an instance into a free slot: its state is allocated from the arena
+ * and initialised on the device (Sec. 2.1 start: random spins, walker w at
+ * slot w).  EINVAL: bad descriptor (L even 2..128, L_tau even, 1..32 slots,
+ * 1..64 replicas); ENOMEM: no free slot or the arena has no room -- the
+ * caller keeps the request queued.  Synchronises. */
+int qisg_batch_admit(qisg_batch *b, const qisg_instance_desc *d, int *slot);
+
+/* Free a slot and its arena memory.  Synchronises. */
+int qisg_batch_retire(qisg_batch *b, int slot);
+
+/* Advance every admitted instance by n_sweeps sweeps (an instance stops at
+ * its target).  One cooperative persistent kernel runs all of them: red and
+ * blue half sweeps over a work-list of (instance, site range) tiles, a PT
+ * pass with one warp per (instance, replica) chain, and the counter advance,
+ * separated by grid barriers whose waits are bounded (ETIMEOUT at the next
+ * synchronising call if one gives up).  Asynchronous. */
+int qisg_batch_run(qisg_batch *b, int64_t n_sweeps);
+
+/* Tile rows per work item (1..256) and tile order (0: admission order, 1:
+ * largest instances first).  Results never depend on either. */
+int qisg_batch_set_schedule(qisg_batch *b, int tile_rows, int schedule);
+
+/* Time sweeps_per_candidate sweeps of each (tile rows, order) candidate on the
+ * live batch and keep the fastest; the batch advances meanwhile. */
+int qisg_batch_autotune(qisg_batch *b, int sweeps_per_candidate, int *tile_rows, int *schedule);
+
+/* Sweeps done by a slot and whether it reached its target. */
+int qisg_batch_status(qisg_batch *b, int slot, uint64_t *sweeps_done, int *done);
+
+/* Results of a slot (any pointer may be NULL): A, B by slot int64
+ * [n_replicas][n_slots], walker_at int32 [n_replicas][n_slots], spins by
+ * walker int8 [n_replicas][n_slots][L*L*L_tau].  Synchronises. */
+int qisg_batch_results(qisg_batch *b, int slot, int64_t *A, int64_t *B, int32_t *walker_at, int8_t *S);
+
+/* Free arena bytes, free slots, kernel launches so far. */
+int qisg_batch_info(qisg_batch *b, size_t *free_bytes, int *free_slots, int64_t *launches);
+
+/* Arena bytes an instance would take (0 for an invalid descriptor). */
+size_t qisg_batch_instance_bytes(const qisg_instance_desc *d);
+
+int qisg_batch_sync(qisg_batch *b);
+void qisg_batch_destroy(qisg_batch *b);
+
 /* Replica overlaps of a caller-owned configuration, computed without
  * allocating device memory.  (The paper has no counterpart: this is a
  * deployment aid.)  It serves callers that cannot call cudaMalloc -- a host

@@ -18,70 +18,6 @@
 namespace qisg {
 namespace {
 
-// Scan of one chain by one warp; returns the accepted-pair bitmask (same in
-// every lane).
-template <bool BY_SLOT>
-__device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua, const PTConst &pc,
-                                             const double *sq, uint2 key, uint32_t t, int64_t a, int r,
-                                             int n_slots) {
-  const int lane = threadIdx.x & 31;
-  int w = 0;
-  long long us = 0, ut = 0;
-  if (lane < n_slots) {
-    w = wa[lane];
-    const int e = BY_SLOT ? lane : w;
-    us = (long long)Ua[2 * e];
-    ut = (long long)Ua[2 * e + 1];
-  }
-  uint32_t x = 0;
-  float lnu = 0.f;
-  if (lane + 1 < n_slots) {
-    x = pick4(philox(make_uint4((uint32_t)lane, t, (uint32_t)a, (DOM_PT << 28) | (uint32_t)(r >> 2)), key), r & 3);
-    lnu = __logf((float)x) - 22.18070977791825f;
-  }
-  // the configuration moving up the ladder and what each slot ends with
-  long long c_us = __shfl_sync(0xffffffffu, us, 0), c_ut = __shfl_sync(0xffffffffu, ut, 0);
-  int c_w = __shfl_sync(0xffffffffu, w, 0);
-  long long f_us = us, f_ut = ut;
-  int f_w = w;
-  uint32_t acc = 0;
-  for (int s = 0; s + 1 < n_slots; ++s) {
-    const long long y_us = __shfl_sync(0xffffffffu, us, s + 1);
-    const long long y_ut = __shfl_sync(0xffffffffu, ut, s + 1);
-    const int y_w = __shfl_sync(0xffffffffu, w, s + 1);
-    const uint32_t xs = __shfl_sync(0xffffffffu, x, s);
-    const float ls = __shfl_sync(0xffffffffu, lnu, s);
-    const long long m = -2 * (y_us - c_us);   // A = 2N - 2 us
-    const long long n = -2 * (y_ut - c_ut);   // B = N - 2 ut
-    const bool ex = pt_decide(pc, sq, s, m, n, xs, ls);
-    if (lane == s) {
-      f_us = ex ? y_us : c_us;
-      f_ut = ex ? y_ut : c_ut;
-      f_w = ex ? y_w : c_w;
-    }
-    if (ex) {
-      acc |= 1u << s;   // the carried configuration moves on to slot s+1
-    } else {
-      c_us = y_us;
-      c_ut = y_ut;
-      c_w = y_w;
-    }
-  }
-  if (lane == n_slots - 1) {
-    f_us = c_us;
-    f_ut = c_ut;
-    f_w = c_w;
-  }
-  if (lane < n_slots) {
-    wa[lane] = f_w;
-    if (BY_SLOT) {
-      Ua[2 * lane] = (unsigned long long)f_us;
-      Ua[2 * lane + 1] = (unsigned long long)f_ut;
-    }
-  }
-  return acc;
-}
-
 // LANES: one warp per chain, chains in (a, r) order.
 __global__ void pt_lanes_kernel(int32_t *walker, unsigned long long *U, const PTConst *ptc, const double *sq,
                                 const unsigned long long *d_t, uint2 key, int64_t a0, int64_t n_chains,
@@ -94,7 +30,7 @@ __global__ void pt_lanes_kernel(int32_t *walker, unsigned long long *U, const PT
   const int64_t a = a0 + chain / n_rep;
   const int r = (int)(chain % n_rep);
   const uint32_t t = (uint32_t)(explicit_pass ? *d_t - 1ull : *d_t);
-  pt_chain<false>(walker + (a * n_rep + r) * n_slots, U + (a * n_rep + r) * n_slots * 2, pc, sq, key, t, a,
+  pt_chain<false, false>(walker + (a * n_rep + r) * n_slots, U + (a * n_rep + r) * n_slots * 2, pc, sq, key, t, a,
                   r, n_slots);
 }
 
@@ -120,7 +56,7 @@ __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsign
   uint32_t acc = 0;
   if (a < n_samples) {
     const uint32_t t = (uint32_t)(explicit_pass ? *d_t - 1ull : *d_t);
-    acc = pt_chain<true>(walker + (a * n_rep + r) * n_slots, U + (a * n_rep + r) * n_slots * 2, pc, sq, key,
+    acc = pt_chain<true, false>(walker + (a * n_rep + r) * n_slots, U + (a * n_rep + r) * n_slots * 2, pc, sq, key,
                          t, a, r, n_slots);
   }
   if ((threadIdx.x & 31) == 0) bits[v] = acc;

@@ -173,6 +173,76 @@ __device__ __forceinline__ uint32_t pt_scan(int n_slots, long long *us, long lon
   return acc;
 }
 
+// PT pass of one chain by one warp (Sec. 2.1): lane s holds the energies of
+// the configuration at slot s and draws the Philox word of pair (s, s+1);
+// the pass over pairs is a uniform loop over shuffles in which the
+// configuration carried up from pair s-1 meets the original occupant of
+// slot s+1.  BY_SLOT: energies indexed by slot (else by walker).  CG: read
+// the mutable state through L2 only (needed inside a persistent kernel, whose
+// L1 may hold lines written by other blocks earlier in the launch).  Returns
+// the accepted-pair bitmask (same in every lane).
+template <bool BY_SLOT, bool CG>
+__device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua, const PTConst &pc,
+                                             const double *sq, uint2 key, uint32_t t, int64_t a, int r,
+                                             int n_slots) {
+  const int lane = threadIdx.x & 31;
+  int w = 0;
+  long long us = 0, ut = 0;
+  if (lane < n_slots) {
+    w = CG ? __ldcg(wa + lane) : wa[lane];
+    const int e = BY_SLOT ? lane : w;
+    us = (long long)(CG ? __ldcg(Ua + 2 * e) : Ua[2 * e]);
+    ut = (long long)(CG ? __ldcg(Ua + 2 * e + 1) : Ua[2 * e + 1]);
+  }
+  uint32_t x = 0;
+  float lnu = 0.f;
+  if (lane + 1 < n_slots) {
+    x = pick4(philox(make_uint4((uint32_t)lane, t, (uint32_t)a, (DOM_PT << 28) | (uint32_t)(r >> 2)), key), r & 3);
+    lnu = __logf((float)x) - 22.18070977791825f;
+  }
+  // the configuration moving up the ladder and what each slot ends with
+  long long c_us = __shfl_sync(0xffffffffu, us, 0), c_ut = __shfl_sync(0xffffffffu, ut, 0);
+  int c_w = __shfl_sync(0xffffffffu, w, 0);
+  long long f_us = us, f_ut = ut;
+  int f_w = w;
+  uint32_t acc = 0;
+  for (int s = 0; s + 1 < n_slots; ++s) {
+    const long long y_us = __shfl_sync(0xffffffffu, us, s + 1);
+    const long long y_ut = __shfl_sync(0xffffffffu, ut, s + 1);
+    const int y_w = __shfl_sync(0xffffffffu, w, s + 1);
+    const uint32_t xs = __shfl_sync(0xffffffffu, x, s);
+    const float ls = __shfl_sync(0xffffffffu, lnu, s);
+    const long long m = -2 * (y_us - c_us);   // A = 2N - 2 us
+    const long long n = -2 * (y_ut - c_ut);   // B = N - 2 ut
+    const bool ex = pt_decide(pc, sq, s, m, n, xs, ls);
+    if (lane == s) {
+      f_us = ex ? y_us : c_us;
+      f_ut = ex ? y_ut : c_ut;
+      f_w = ex ? y_w : c_w;
+    }
+    if (ex) {
+      acc |= 1u << s;   // the carried configuration moves on to slot s+1
+    } else {
+      c_us = y_us;
+      c_ut = y_ut;
+      c_w = y_w;
+    }
+  }
+  if (lane == n_slots - 1) {
+    f_us = c_us;
+    f_ut = c_ut;
+    f_w = c_w;
+  }
+  if (lane < n_slots) {
+    wa[lane] = f_w;
+    if (BY_SLOT) {
+      Ua[2 * lane] = (unsigned long long)f_us;
+      Ua[2 * lane + 1] = (unsigned long long)f_ut;
+    }
+  }
+  return acc;
+}
+
 // Stage the PT constants of a handle in shared memory (call with all
 // threads of the block, followed by __syncthreads()).
 __device__ __forceinline__ void load_ptconst(PTConst *dst, const PTConst *src) {

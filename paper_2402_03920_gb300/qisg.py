@@ -82,6 +82,18 @@ def load(build_if_missing: bool = True):
         "qisg_profile": (I, [P, I]),
         "qisg_set_graphs": (I, [P, I]),
         "qisg_autotune": (I, [P, I, P]),
+        "qisg_batch_create": (I, [P, I, ctypes.c_size_t, P]),
+        "qisg_batch_admit": (I, [P, P, P]),
+        "qisg_batch_retire": (I, [P, I]),
+        "qisg_batch_run": (I, [P, I64]),
+        "qisg_batch_set_schedule": (I, [P, I, I]),
+        "qisg_batch_autotune": (I, [P, I, P, P]),
+        "qisg_batch_status": (I, [P, I, P, P]),
+        "qisg_batch_results": (I, [P, I, P, P, P, P]),
+        "qisg_batch_info": (I, [P, P, P, P]),
+        "qisg_batch_instance_bytes": (ctypes.c_size_t, [P]),
+        "qisg_batch_sync": (I, [P]),
+        "qisg_batch_destroy": (None, [P]),
         "qisg_profile_read": (I, [P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -100,7 +112,10 @@ def exported_symbols():
             "qisg_slot_means", "qisg_thresholds", "qisg_sweep_count", "qisg_layout",
             "qisg_launch_count", "qisg_sync", "qisg_destroy", "qisg_strerror", "qisg_last_error",
             "qisg_philox4x32_10", "qisg_profile", "qisg_profile_read", "qisg_set_graphs",
-            "qisg_autotune"]
+            "qisg_autotune", "qisg_batch_create", "qisg_batch_admit", "qisg_batch_retire",
+            "qisg_batch_run", "qisg_batch_set_schedule", "qisg_batch_autotune", "qisg_batch_status",
+            "qisg_batch_results", "qisg_batch_info", "qisg_batch_instance_bytes", "qisg_batch_sync",
+            "qisg_batch_destroy"]
 
 
 def _check(rc: int):
@@ -300,3 +315,104 @@ def philox4x32_10_device(ctr_dev_ptr: int, key_dev_ptr: int, out_dev_ptr: int, n
                          stream: int | None = None):
     """Device Philox on device buffers (pointers from torch tensors)."""
     _check(load().qisg_philox4x32_10(ctr_dev_ptr, key_dev_ptr, out_dev_ptr, n, stream))
+
+
+class InstanceDesc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("L_tau", ctypes.c_int), ("n_slots", ctypes.c_int),
+                ("n_replicas", ctypes.c_int), ("ladder", ctypes.c_void_p),
+                ("seed", ctypes.c_uint64), ("n_sweeps", ctypes.c_int64)]
+
+
+def _desc(L, L_tau, ladder, n_replicas, seed, n_sweeps):
+    lad = np.ascontiguousarray(ladder, dtype=np.float64)
+    d = InstanceDesc(L, L_tau, lad.shape[0], n_replicas, lad.ctypes.data, seed, n_sweeps)
+    return d, lad
+
+
+class Batch:
+    """qisg_batch: independent single-sample instances of uneven size, advanced
+    together by one persistent kernel per qisg_batch_run."""
+
+    def __init__(self, capacity: int, mem_budget: int = 0, stream: int | None = None):
+        lib = load()
+        self._b = ctypes.c_void_p()
+        _check(lib.qisg_batch_create(ctypes.byref(self._b), capacity, mem_budget,
+                                     stream if stream is not None else current_stream_ptr()))
+        self.meta = {}
+
+    def close(self):
+        if getattr(self, "_b", None) and self._b.value:
+            load().qisg_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def instance_bytes(L, L_tau, ladder, n_replicas=4) -> int:
+        d, _lad = _desc(L, L_tau, ladder, n_replicas, 0, 0)
+        return int(load().qisg_batch_instance_bytes(ctypes.byref(d)))
+
+    def admit(self, L, L_tau, ladder, n_replicas, seed, n_sweeps=0) -> int:
+        """Slot of the admitted instance; raises QisgError(ENOMEM) when the
+        arena or the slots are full."""
+        d, lad = _desc(L, L_tau, ladder, n_replicas, seed, n_sweeps)
+        slot = ctypes.c_int()
+        _check(load().qisg_batch_admit(self._b, ctypes.byref(d), ctypes.byref(slot)))
+        self.meta[slot.value] = (L, L_tau, lad.shape[0], n_replicas)
+        return slot.value
+
+    def try_admit(self, *a, **kw):
+        try:
+            return self.admit(*a, **kw)
+        except QisgError as e:
+            if e.code == -2:
+                return None
+            raise
+
+    def retire(self, slot: int):
+        _check(load().qisg_batch_retire(self._b, slot))
+        self.meta.pop(slot, None)
+
+    def run(self, n_sweeps: int):
+        _check(load().qisg_batch_run(self._b, n_sweeps))
+
+    def sync(self):
+        _check(load().qisg_batch_sync(self._b))
+
+    def set_schedule(self, tile_rows: int, schedule: int):
+        _check(load().qisg_batch_set_schedule(self._b, tile_rows, schedule))
+
+    def autotune(self, sweeps_per_candidate: int = 2):
+        r, s = ctypes.c_int(), ctypes.c_int()
+        _check(load().qisg_batch_autotune(self._b, sweeps_per_candidate, ctypes.byref(r), ctypes.byref(s)))
+        return r.value, s.value
+
+    def status(self, slot: int):
+        n, d = ctypes.c_uint64(), ctypes.c_int()
+        _check(load().qisg_batch_status(self._b, slot, ctypes.byref(n), ctypes.byref(d)))
+        return n.value, bool(d.value)
+
+    def results(self, slot: int, spins: bool = False):
+        L, Lt, n_slots, n_rep = self.meta[slot]
+        A = np.zeros((n_rep, n_slots), dtype=np.int64)
+        B = np.zeros_like(A)
+        wa = np.zeros((n_rep, n_slots), dtype=np.int32)
+        S = np.zeros((n_rep, n_slots, L * L * Lt), dtype=np.int8) if spins else None
+        _check(load().qisg_batch_results(self._b, slot, _ptr(A), _ptr(B), _ptr(wa),
+                                         _ptr(S) if spins else None))
+        return A, B, wa, S
+
+    def info(self):
+        fb, fs, ln = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int64()
+        _check(load().qisg_batch_info(self._b, ctypes.byref(fb), ctypes.byref(fs), ctypes.byref(ln)))
+        return fb.value, fs.value, ln.value
