@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--forms", default="batched,per_instance")
+    p.add_argument("--extras", default="uneven,large,serving",
+                   help="other workloads measured beside the headline (empty: none)")
+    p.add_argument("--serving-requests", type=int, default=100)
     return p.parse_args()
 
 
@@ -259,6 +262,98 @@ def roofline(kern, w, layout, wb, n_sm, pk, steps):
             "avg_launch_us": per_launch_ms * 1e3}
 
 
+def uneven_batch_entry(qisg, sweeps=100):
+    """512 instances, L in {8,12,16,20,24}, L_tau in {64..1024}, 8..32 slots,
+    Gamma in [0.8, 1.2], one persistent launch per chunk: ps per update,
+    autotuned schedule against the fixed one."""
+    import torch
+    from paper_2402_03920_gb300.workloads import uneven_batch
+    specs = uneven_batch(512, seed=2024, sweeps=sweeps)
+    out = {}
+    for mode in ("fixed", "autotuned"):
+        with qisg.Batch(512, 0) as b:
+            for sp in specs:
+                b.admit(sp.L, sp.L_tau, qisg.ladder_linear(sp.k_lo, sp.k_hi, sp.n_slots, sp.gamma),
+                        sp.n_replicas, sp.seed)
+            if mode == "autotuned":
+                rows, order = b.autotune(1)
+                out["schedule"] = {"tile_rows": rows, "largest_first": bool(order)}
+            else:
+                b.set_schedule(4, 0)
+            b.run(2)
+            b.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.run(sweeps)
+            e1.record()
+            b.sync()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        ups = sum(sp.L * sp.L * sp.L_tau * sp.n_replicas * sp.n_slots for sp in specs) * sweeps
+        out[mode] = {"value": ms * 1e9 / ups, "unit": UNIT, "ms": ms, "sweeps": sweeps}
+    out["workload"] = "512 uneven instances (L 8..24, L_tau 64..1024, 8..32 slots), one persistent kernel"
+    return out
+
+
+def large_batched_entry(torch, qisg, sweeps=20):
+    """1024 samples x 4 replicas x 32 slots, L=24, L_tau=512 (4.8 GB of
+    spins, far larger than L2): the SAMPLES form, graph replay."""
+    from paper_2402_03920_gb300.workloads import BATCHED as w
+    ladder = qisg.ladder_linear(w.k_lo, w.k_hi, w.n_slots, w.gamma)
+    cfg = qisg.Config(w.L, w.L_tau, ladder, w.n_replicas, w.n_samples, w.seed, word_bits=64,
+                      layout=qisg.QISG_LAYOUT_SAMPLES)
+    with qisg.Instance(cfg) as inst:
+        inst.sweep(2)
+        inst.sync()
+        inst.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        inst.sweep(sweeps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kern = {}
+        for kind, name in ((qisg.KERNEL_SWEEP, "sweep"), (qisg.KERNEL_PT, "pt"),
+                           (qisg.KERNEL_PERMUTE, "permute")):
+            kms, nt, nl = inst.profile_read(kind)
+            kern[name] = {"ms": kms, "timed": nt, "launched": nl}
+        inst.profile(False)
+    N = w.L * w.L * w.L_tau
+    ups = w.n_samples * w.n_replicas * w.n_slots * N * sweeps
+    pk, _ = peaks()
+    sw = kern["sweep"]
+    per_launch = sw["ms"] / max(sw["timed"], 1)
+    # one half sweep moves every spin word once in and half of them out:
+    # 0.25 B per update per sweep split evenly over the two launches
+    bytes_per_launch = 0.25 * ups / sweeps / 2
+    achieved = bytes_per_launch / (per_launch * 1e-3) / 1e9
+    return {"value": ms * 1e9 / ups, "unit": UNIT, "ms": ms, "sweeps": sweeps,
+            "workload": w.name, "kernels_ms": {k: v["ms"] for k, v in kern.items()},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs", 6800.0),
+                         "unit": "GB/s", "frac": achieved / pk.get("hbm_gbs", 6800.0), "traffic": None,
+                         "kernel": "half_sweep", "bytes_per_update": 0.25}}
+
+
+def serving_entry(qisg, n_requests):
+    """Poisson stream of requests (L 8..24, L_tau 32..1024, 8..32 slots,
+    100..5000 sweeps, Gamma in [0.8, 1.2]) through the continuous-batching
+    server: p50/p99 latency and aggregate ps per update."""
+    from paper_2402_03920_gb300.serving import Request, Server
+    from paper_2402_03920_gb300.workloads import poisson_requests
+    specs = poisson_requests(n_requests, rate=200.0, seed=7)
+    reqs = [Request(rid=i, L=sp.L, L_tau=sp.L_tau, n_slots=sp.n_slots, gamma=sp.gamma, sweeps=sp.sweeps,
+                    seed=sp.seed, arrival=sp.arrival) for i, sp in enumerate(specs)]
+    srv = Server(capacity=512, mem_budget=16 << 30, chunk_sweeps=100)
+    try:
+        st = srv.serve(reqs, realtime=True)
+    finally:
+        srv.close()
+    out = st.summary()
+    out.update({"requests": n_requests, "rate_per_s": 200.0, "arrival_seed": 7, "unit": UNIT,
+                "value": out["ps_per_update"]})
+    return out
+
+
 def cpu_baseline(w, budget_s=15.0):
     """The oracle as it stands on the host cores: nproc samples of the same
     workload, as many sweeps as fit in about budget_s seconds."""
@@ -348,6 +443,13 @@ def run_gpu(args):
     line["roofline"] = rl
     if not args.no_e2e:
         line["e2e"] = e2e_form(torch, qisg, w, main, args.steps, seed)
+    extras = [x for x in args.extras.split(",") if x]
+    if "uneven" in extras and world == 1:
+        line["batched_uneven"] = uneven_batch_entry(qisg)
+    if "large" in extras and world == 1:
+        line["batched_large"] = large_batched_entry(torch, qisg)
+    if "serving" in extras and world == 1:
+        line["serving"] = serving_entry(qisg, args.serving_requests)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line))
