@@ -103,7 +103,8 @@ int qisg_ladder_linear(double lo, double hi, int n, double gamma, qisg_slot *out
  *   ladder: host array of n_slots slots (copied).  opts may be NULL.
  * EINVAL: L odd or < 2; L_tau odd or < 2; n_slots < 1; n_replicas < 1;
  *   n_samples < 1; a k or k_tau negative or non-finite; a packing that cannot
- *   hold the systems (LANES needs n_slots <= word bits).
+ *   hold the systems (LANES needs n_slots <= word bits and n_replicas <=
+ *   2 * (word bits / n_slots); SAMPLES needs n_slots <= 32).
  * ENOMEM: allocation failed or the state exceeds opts->mem_budget.        */
 int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, int n_slots,
                 int n_replicas, int64_t n_samples, uint64_t seed, const qisg_opts *opts);
@@ -264,7 +265,7 @@ int qisg_batch_create(qisg_batch **out, int capacity, size_t mem_budget, void *c
 /* Admit an instance into a free slot: its state is allocated from the arena
  * and initialised on the device (Sec. 2.1 start: random spins, walker w at
  * slot w).  EINVAL: bad descriptor (L even 2..128, L_tau even, 1..32 slots,
- * 1..64 replicas); ENOMEM: no free slot or the arena has no room -- the
+ * 1 .. 2*(64/n_slots) replicas); ENOMEM: no free slot or the arena has no room -- the
  * caller keeps the request queued.  Synchronises. */
 int qisg_batch_admit(qisg_batch *b, const qisg_instance_desc *d, int *slot);
 
@@ -279,7 +280,7 @@ int qisg_batch_retire(qisg_batch *b, int slot);
  * synchronising call if one gives up).  Asynchronous. */
 int qisg_batch_run(qisg_batch *b, int64_t n_sweeps);
 
-/* Tile rows per work item (1..256) and tile order (0: admission order, 1:
+/* Tile rows of 256 sites per work item (1..16) and tile order (0: admission order, 1:
  * largest instances first).  Results never depend on either. */
 int qisg_batch_set_schedule(qisg_batch *b, int tile_rows, int schedule);
 

@@ -20,6 +20,7 @@
 #include <map>
 #include <vector>
 
+#include "lanes_core.cuh"
 #include "qisg_internal.cuh"
 
 namespace qisg {
@@ -88,140 +89,29 @@ __device__ bool grid_sync(unsigned *bar, int *err) {
   return *(volatile int *)err == 0;
 }
 
-struct TileSmem {
-  static size_t bytes(int max_plane, int max_slots, int max_rep, int max_spb_groups) {
-    size_t o = (size_t)(max_slots * 15 + 3 * max_rep * max_slots) * 4;
-    o = (o + 7) & ~size_t(7);
-    o += (size_t)max_spb_groups * 8;
-    o = (o + 7) & ~size_t(7);
-    o += (size_t)max_plane * (8 + 2 + 1);
-    return (o + 15) & ~size_t(15);
-  }
-};
-
-// One tile of a half sweep of instance I (LANES arithmetic of lanes.cu, 64-bit
-// words): thread (site row jl, slot s); rows of spb sites until the tile's n
-// sites are done.  Mutable state is read through L2 (__ldcg).
+// One tile of a half sweep of instance I (sample 0, 64-bit LANES words).
+template <bool BLUE>
 __device__ void batch_tile(const InstDev &I, int colour, int j0, int n, unsigned char *smem) {
-  const int n_slots = I.n_slots, n_rep = I.n_rep, n_groups = I.n_groups, plane = I.plane, hp = I.half_plane;
-  uint32_t *T_s = reinterpret_cast<uint32_t *>(smem);
-  int *wa_s = reinterpret_cast<int *>(T_s + n_slots * 15);
-  int *e_s = wa_s + n_rep * n_slots;
-  size_t off = (size_t)(n_slots * 15 + 3 * n_rep * n_slots) * 4;
-  off = (off + 7) & ~size_t(7);
-  unsigned long long *flip_s = reinterpret_cast<unsigned long long *>(smem + off);
-  off += (size_t)I.spb * n_groups * 8;
-  off = (off + 7) & ~size_t(7);
-  uint2 *nb = reinterpret_cast<uint2 *>(smem + off);
-  uint16_t *s2d = reinterpret_cast<uint16_t *>(nb + plane);
-  uint8_t *Js = reinterpret_cast<uint8_t *>(s2d + plane);
-
-  __syncthreads();   // previous tile done with the tables
-  for (int i = threadIdx.x; i < n_slots * 15; i += blockDim.x) T_s[i] = I.T[i];
-  for (int i = threadIdx.x; i < n_rep * n_slots; i += blockDim.x) {
-    wa_s[i] = __ldcg(I.walker + i);
-    e_s[2 * i] = 0;
-    e_s[2 * i + 1] = 0;
-  }
-  for (int i2 = threadIdx.x; i2 < plane; i2 += blockDim.x) {
-    const int L = I.L;
-    const int y = i2 / L, x = i2 - y * L;
-    const int xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
-    const int yp = y + 1 == L ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
-    nb[i2] = make_uint2((uint32_t)(xp + L * y) | ((uint32_t)(xm + L * y) << 16),
-                        (uint32_t)(x + L * yp) | ((uint32_t)(x + L * ym) << 16));
-    s2d[((x + y) & 1) * hp + (i2 >> 1)] = (uint16_t)i2;
-    Js[i2] = I.J[i2];
-  }
-  if (colour == 0 && j0 == 0)   // bond counters, filled by the blue pass
-    for (int i = threadIdx.x; i < 2 * n_rep * n_slots; i += blockDim.x) I.U[i] = 0;
-  const uint32_t t = (uint32_t)__ldcg(&I.t);
-  const int s = threadIdx.x % n_slots;
-  const int jl = threadIdx.x / n_slots;
-  const uint32_t Lt = (uint32_t)I.Lt;
-
-  for (int row = 0; row * I.spb < n; ++row) {
-    for (int i = threadIdx.x; i < I.spb * n_groups; i += blockDim.x) flip_s[i] = 0;
-    __syncthreads();
-    const int jr = row * I.spb + jl;
-    if (jl < I.spb && jr < n) {
-      const uint32_t j = (uint32_t)(j0 + jr);
-      const uint32_t tau = I.hpd.div(j);
-      const uint32_t i2 = s2d[((colour + tau) & 1) * hp + (j - tau * hp)];
-      const uint2 nv = nb[i2];
-      const uint32_t offt = tau * plane;
-      const uint32_t site = i2 + offt;
-      const uint32_t i_xp = (nv.x & 0xFFFFu) + offt, i_xm = (nv.x >> 16) + offt;
-      const uint32_t i_yp = (nv.y & 0xFFFFu) + offt, i_ym = (nv.y >> 16) + offt;
-      const uint32_t i_tp = i2 + (tau + 1 == Lt ? 0u : offt + plane);
-      const uint32_t i_tm = i2 + (tau == 0 ? (Lt - 1) * plane : offt - plane);
-      const uint8_t jh = Js[i2];
-      const unsigned long long Jxp = (jh & 1u) ? ~0ull : 0ull, Jyp = (jh & 2u) ? ~0ull : 0ull;
-      const unsigned long long Jxm = (Js[nv.x >> 16] & 1u) ? ~0ull : 0ull;
-      const unsigned long long Jym = (Js[nv.y >> 16] & 2u) ? ~0ull : 0ull;
-      int cur_q = -1;
-      uint4 R = make_uint4(0, 0, 0, 0);
-      for (int g = 0; g < n_groups; ++g) {
-        const unsigned long long *base = I.spins + (size_t)g * I.N;
-        const unsigned long long sc = __ldcg(base + site);
-        const unsigned long long b1 = sc ^ __ldcg(base + i_xp) ^ Jxp;
-        const unsigned long long b2 = sc ^ __ldcg(base + i_xm) ^ Jxm;
-        const unsigned long long b3 = sc ^ __ldcg(base + i_yp) ^ Jyp;
-        const unsigned long long b4 = sc ^ __ldcg(base + i_ym) ^ Jym;
-        const unsigned long long t1 = sc ^ __ldcg(base + i_tp);
-        const unsigned long long t2 = sc ^ __ldcg(base + i_tm);
-        const unsigned long long s1 = b1 ^ b2 ^ b3;
-        const unsigned long long c1 = (b1 & b2) | (b3 & (b1 ^ b2));
-        const unsigned long long us0 = s1 ^ b4, c2 = s1 & b4;
-        const unsigned long long us1 = c1 ^ c2, us2 = c1 & c2;
-        const unsigned long long ut0 = t1 ^ t2, ut1 = t1 & t2;
-        unsigned long long fw = 0;
-        const int r_lo = g * I.rpw;
-        const int r_hi = min(n_rep, r_lo + I.rpw);
-        for (int r = r_lo; r < r_hi; ++r) {
-          const int q = r >> 2;
-          if (q != cur_q) {   // sample 0: sample block 0
-            R = philox(make_uint4(site, t, (uint32_t)s | ((uint32_t)q << 16), DOM_SWEEP << 28), I.key);
-            cur_q = q;
-          }
-          const int w = wa_s[r * n_slots + s];
-          const int lane = (r - r_lo) * n_slots + w;
-          const int us = (int)(((us0 >> lane) & 1ull) | (((us1 >> lane) & 1ull) << 1) | (((us2 >> lane) & 1ull) << 2));
-          const int ut = (int)(((ut0 >> lane) & 1ull) | (((ut1 >> lane) & 1ull) << 1));
-          const uint32_t thr = T_s[s * 15 + us * 3 + ut];
-          const bool flip = thr == 0xFFFFFFFFu || pick4(R, r & 3) < thr;
-          if (flip) fw |= 1ull << lane;
-          if (colour == 1) {
-            atomicAdd(&e_s[2 * (r * n_slots + s)], flip ? 4 - us : us);
-            atomicAdd(&e_s[2 * (r * n_slots + s) + 1], flip ? 2 - ut : ut);
-          }
-        }
-        if (fw) atomicOr(&flip_s[jl * n_groups + g], fw);
-      }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < I.spb * n_groups; i += blockDim.x) {
-      const int jl2 = i / n_groups, g = i - jl2 * n_groups;
-      const int jr2 = row * I.spb + jl2;
-      const unsigned long long fw = flip_s[i];
-      if (jr2 < n && fw) {
-        const uint32_t j = (uint32_t)(j0 + jr2);
-        const uint32_t tau = I.hpd.div(j);
-        const uint32_t site = s2d[((colour + tau) & 1) * hp + (j - tau * hp)] + tau * plane;
-        unsigned long long *wd = I.spins + (size_t)g * I.N + site;
-        *wd = __ldcg(wd) ^ fw;
-      }
-    }
-    __syncthreads();
-  }
-  if (colour == 1) {
-    for (int i = threadIdx.x; i < n_rep * n_slots; i += blockDim.x) {
-      const int r = i / n_slots;
-      unsigned long long *u = I.U + ((size_t)r * n_slots + wa_s[i]) * 2;
-      if (e_s[2 * i]) atomicAdd(u, (unsigned long long)e_s[2 * i]);
-      if (e_s[2 * i + 1]) atomicAdd(u + 1, (unsigned long long)e_s[2 * i + 1]);
-    }
-  }
+  LanesSample<unsigned long long> S;
+  S.spins = I.spins;
+  S.T = I.T;
+  S.walker = I.walker;
+  S.U = I.U;
+  S.J = I.J;
+  S.key = I.key;
+  S.ctr_w = DOM_SWEEP << 28;   // sample 0: sample block 0
+  S.t = (uint32_t)__ldcg(&I.t);
+  S.hpd = I.hpd;
+  S.L = I.L;
+  S.Lt = I.Lt;
+  S.plane = I.plane;
+  S.half_plane = I.half_plane;
+  S.N = I.N;
+  S.n_slots = I.n_slots;
+  S.n_rep = I.n_rep;
+  S.rpw = I.rpw;
+  S.n_groups = I.n_groups;
+  lanes_tile<unsigned long long, true, BLUE>(S, colour, j0, n, 0, colour == 0 && j0 == 0, smem);
 }
 
 __device__ __forceinline__ bool live(const InstDev &I) { return I.active && __ldcg(&I.remaining) != 0; }
@@ -243,7 +133,10 @@ __global__ void __launch_bounds__(kBatchBlock) batch_kernel(InstDev *insts, int 
         const Tile tl = tiles[k];
         const InstDev &I = insts[tl.inst];
         if (!live(I)) continue;
-        batch_tile(I, colour, tl.j0, tl.n, smem);
+        if (colour == 0)
+          batch_tile<false>(I, 0, tl.j0, tl.n, smem);
+        else
+          batch_tile<true>(I, 1, tl.j0, tl.n, smem);
       }
       if (!grid_sync(bar, err)) return;
     }
@@ -396,7 +289,7 @@ int build_tables(qisg_batch *B) {
   B->max_slots = B->max_rep = B->max_spb_groups = 1;
   for (int i : order) {
     const InstDev &I = B->slots[i].dev;
-    const int per = I.spb * B->tile_rows;
+    const int per = kBatchBlock * B->tile_rows;
     const int half = I.N / 2;
     for (int j0 = 0; j0 < half; j0 += per) tiles.push_back(Tile{i, j0, std::min(per, half - j0)});
     for (int r = 0; r < I.n_rep; ++r) chains.push_back(ChainRef{i, r});
@@ -429,7 +322,7 @@ int build_tables(qisg_batch *B) {
   if (rc) return rc;
   B->n_tiles = (int)tiles.size();
   B->n_chains = (int)chains.size();
-  B->smem = TileSmem::bytes(B->max_plane, B->max_slots, B->max_rep, B->max_spb_groups);
+  B->smem = lanes_tile_smem(B->max_plane, B->max_slots, B->max_rep);
   if (B->smem > 200 * 1024) return fail(QISG_EINVAL, "instance too large for the batch kernel's shared memory");
   cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem);
   int per_sm = 0;
@@ -550,7 +443,8 @@ int check_desc(const qisg_instance_desc *d) {
   if (d->L < 2 || (d->L & 1) || d->L > 128) return fail(QISG_EINVAL, "L must be even, 2..128");
   if (d->L_tau < 2 || (d->L_tau & 1)) return fail(QISG_EINVAL, "L_tau must be even and >= 2");
   if (d->n_slots < 1 || d->n_slots > 32) return fail(QISG_EINVAL, "n_slots must be 1..32");
-  if (d->n_replicas < 1 || d->n_replicas > 64) return fail(QISG_EINVAL, "n_replicas must be 1..64");
+  if (d->n_replicas < 1 || d->n_replicas > 2 * (64 / d->n_slots))
+    return fail(QISG_EINVAL, "n_replicas must be 1 .. 2 * (64 / n_slots)");
   if ((int64_t)d->L * d->L * d->L_tau > ((int64_t)1 << 30)) return fail(QISG_EINVAL, "instance too large");
   if (d->n_sweeps < 0) return fail(QISG_EINVAL, "n_sweeps < 0");
   for (int s = 0; s < d->n_slots; ++s)
@@ -681,7 +575,8 @@ int qisg_batch_run(qisg_batch *B, int64_t n_sweeps) {
 }
 
 int qisg_batch_set_schedule(qisg_batch *B, int tile_rows, int schedule) {
-  if (!B || tile_rows < 1 || tile_rows > 256 || schedule < 0 || schedule > 1) return fail(QISG_EINVAL, "bad schedule");
+  if (!B || tile_rows < 1 || tile_rows > kLanesMaxSitesPerThread || schedule < 0 || schedule > 1)
+    return fail(QISG_EINVAL, "bad schedule");
   B->tile_rows = tile_rows;
   B->schedule = schedule;
   B->dirty = true;

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "lanes_core.cuh"
 #include "qisg_internal.cuh"
 
 namespace qisg {
@@ -43,149 +44,37 @@ __device__ __forceinline__ uint32_t bit_at(Word w, int lane) {
   return (uint32_t)(w >> lane) & 1u;
 }
 
-// One half sweep (colour 0 = red, 1 = blue) of samples a0 + blockIdx.y.
-// Thread (site j of the colour, slot s): one Philox call per group of four
-// replicas serves the four replicas of slot s at this site.  Flips of the
-// lanes of one site are OR-ed in shared memory, then applied once.  In the
-// blue pass the unsatisfied bonds after the flip are counted: every bond
-// has exactly one blue end, so the blue pass counts each bond once.
-template <typename Word>
+// One half sweep (colour 0 = red, 1 = blue) of samples a0 + blockIdx.y:
+// block x is the tile of colour sites [x * tile_sites, (x+1) * tile_sites),
+// one thread per site (lanes_core.cuh).  Block 0 of the red pass clears the
+// sample's bond counters, which the blue pass fills.
+template <typename Word, bool BLUE>
 __global__ void __launch_bounds__(kBlock) lanes_half_sweep_kernel(LanesArgs<Word> p, int colour,
-                                                                  int count_only, int64_t a0) {
+                                                                  int count_only, int64_t a0, int tile_sites) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n_slots = p.n_slots, n_rep = p.n_rep, n_groups = p.n_groups;
   const int64_t a = a0 + blockIdx.y;
-  const int plane = p.plane, hp = p.half_plane, L = p.L;
-  uint32_t *T_s = reinterpret_cast<uint32_t *>(smem_raw);            // [n_slots*15]
-  int *wa_s = reinterpret_cast<int *>(T_s + n_slots * 15);             // [n_rep*n_slots]
-  int *e_s = wa_s + n_rep * n_slots;                                   // [n_rep*n_slots*2]
-  size_t off = (size_t)(n_slots * 15 + 3 * n_rep * n_slots) * 4;
-  off = (off + 7) & ~size_t(7);
-  Word *flip_s = reinterpret_cast<Word *>(smem_raw + off);             // [spb*n_groups]
-  off += (size_t)p.sites_per_block * n_groups * sizeof(Word);
-  off = (off + 7) & ~size_t(7);                                        // uint2 alignment
-  uint2 *nb = reinterpret_cast<uint2 *>(smem_raw + off);               // [plane]
-  uint16_t *s2d = reinterpret_cast<uint16_t *>(nb + plane);            // [plane]
-  uint8_t *Js = reinterpret_cast<uint8_t *>(s2d + plane);              // [plane]
-
-  for (int i = threadIdx.x; i < n_slots * 15; i += blockDim.x) T_s[i] = p.T[i];
-  for (int i = threadIdx.x; i < n_rep * n_slots; i += blockDim.x) {
-    wa_s[i] = p.walker[a * n_rep * n_slots + i];
-    e_s[2 * i] = 0;
-    e_s[2 * i + 1] = 0;
-  }
-  for (int i = threadIdx.x; i < p.sites_per_block * n_groups; i += blockDim.x) flip_s[i] = 0;
-  if (colour == 0 && blockIdx.x == 0)   // bond counters of this sample, filled by the blue pass
-    for (int i = threadIdx.x; i < 2 * n_rep * n_slots; i += blockDim.x) p.U[a * n_rep * n_slots * 2 + i] = 0;
-  for (int i2 = threadIdx.x; i2 < plane; i2 += blockDim.x) {
-    const int y = i2 / L, x = i2 - y * L;
-    const int xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
-    const int yp = y + 1 == L ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
-    nb[i2] = make_uint2((uint32_t)(xp + L * y) | ((uint32_t)(xm + L * y) << 16),
-                        (uint32_t)(x + L * yp) | ((uint32_t)(x + L * ym) << 16));
-    s2d[((x + y) & 1) * hp + (i2 >> 1)] = (uint16_t)i2;
-    Js[i2] = p.J[a * plane + i2];
-  }
-  __syncthreads();
-
-  const int s = threadIdx.x % n_slots;
-  const int jl = threadIdx.x / n_slots;
-  const int64_t j = (int64_t)blockIdx.x * p.sites_per_block + jl;
-  if (jl < p.sites_per_block && j < p.half_N) {
-    const uint32_t Lt = (uint32_t)p.Lt;
-    const uint32_t tau = p.half_plane_div.div((uint32_t)j);
-    const uint32_t i2 = s2d[((colour + tau) & 1) * hp + ((uint32_t)j - tau * hp)];
-    const uint2 nv = nb[i2];
-    const uint32_t offt = tau * plane;
-    const uint32_t site = i2 + offt;
-    const uint32_t i_xp = (nv.x & 0xFFFFu) + offt, i_xm = (nv.x >> 16) + offt;
-    const uint32_t i_yp = (nv.y & 0xFFFFu) + offt, i_ym = (nv.y >> 16) + offt;
-    const uint32_t i_tp = i2 + (tau + 1 == Lt ? 0u : offt + plane);
-    const uint32_t i_tm = i2 + (tau == 0 ? (Lt - 1) * plane : offt - plane);
-    const uint8_t j_here = Js[i2];
-    const Word Jxp = all_ones_if<Word>(j_here & 1u);
-    const Word Jyp = all_ones_if<Word>(j_here & 2u);
-    const Word Jxm = all_ones_if<Word>(Js[nv.x >> 16] & 1u);
-    const Word Jym = all_ones_if<Word>(Js[nv.y >> 16] & 2u);
-    const unsigned long long t = *p.d_t;
-
-    int cur_q = -1;
-    uint4 R = make_uint4(0, 0, 0, 0);
-    for (int g = 0; g < n_groups; ++g) {
-      const Word *base = p.spins + (a * n_groups + g) * p.N;
-      const Word sc = base[site];
-      // unsatisfied-bond bits: J S_i S_j = -1 <=> j ^ s_i ^ s_j = 1
-      const Word b1 = sc ^ base[i_xp] ^ Jxp;
-      const Word b2 = sc ^ base[i_xm] ^ Jxm;
-      const Word b3 = sc ^ base[i_yp] ^ Jyp;
-      const Word b4 = sc ^ base[i_ym] ^ Jym;
-      const Word t1 = sc ^ base[i_tp];
-      const Word t2 = sc ^ base[i_tm];
-      // bit-sliced counts u_s = b1+b2+b3+b4 (3 bits), u_t = t1+t2 (2 bits)
-      const Word s1 = b1 ^ b2 ^ b3;
-      const Word c1 = (b1 & b2) | (b3 & (b1 ^ b2));
-      const Word us0 = s1 ^ b4;
-      const Word c2 = s1 & b4;
-      const Word us1 = c1 ^ c2;
-      const Word us2 = c1 & c2;
-      const Word ut0 = t1 ^ t2;
-      const Word ut1 = t1 & t2;
-
-      Word fw = 0;
-      const int r_lo = g * p.rpw;
-      const int r_hi = min(n_rep, r_lo + p.rpw);
-      for (int r = r_lo; r < r_hi; ++r) {
-        const int q = r >> 2;
-        if (q != cur_q) {
-          R = philox(make_uint4((uint32_t)site, (uint32_t)t, (uint32_t)s | ((uint32_t)q << 16),
-                                (DOM_SWEEP << 28) | (uint32_t)(a >> 6)),
-                     p.key);
-          cur_q = q;
-        }
-        const int w = wa_s[r * n_slots + s];
-        const int lane = (r - r_lo) * n_slots + w;
-        const int us = (int)(bit_at(us0, lane) | (bit_at(us1, lane) << 1) | (bit_at(us2, lane) << 2));
-        const int ut = (int)(bit_at(ut0, lane) | (bit_at(ut1, lane) << 1));
-        const uint32_t thr = T_s[s * 15 + us * 3 + ut];
-        const bool flip = !count_only && (thr == 0xFFFFFFFFu || pick4(R, r & 3) < thr);
-        if (flip) fw |= Word(1) << lane;
-        if (colour == 1) {
-          atomicAdd(&e_s[2 * (r * n_slots + s)], flip ? 4 - us : us);
-          atomicAdd(&e_s[2 * (r * n_slots + s) + 1], flip ? 2 - ut : ut);
-        }
-      }
-      if (fw) {
-        if (sizeof(Word) == 8)
-          atomicOr(reinterpret_cast<unsigned long long *>(&flip_s[jl * n_groups + g]),
-                   (unsigned long long)fw);
-        else
-          atomicOr(reinterpret_cast<unsigned int *>(&flip_s[jl * n_groups + g]), (unsigned int)fw);
-      }
-    }
-  }
-  __syncthreads();
-
-  if (!count_only) {
-    for (int i = threadIdx.x; i < p.sites_per_block * n_groups; i += blockDim.x) {
-      const int jl2 = i / n_groups, g = i - jl2 * n_groups;
-      const int64_t j2 = (int64_t)blockIdx.x * p.sites_per_block + jl2;
-      const Word fw = flip_s[i];
-      if (j2 < p.half_N && fw) {
-        const uint32_t tau = p.half_plane_div.div((uint32_t)j2);
-        const uint32_t site = s2d[((colour + tau) & 1) * hp + ((uint32_t)j2 - tau * hp)] + tau * plane;
-        p.spins[(a * n_groups + g) * p.N + site] ^= fw;
-      }
-    }
-  }
-  if (colour == 1) {
-    for (int i = threadIdx.x; i < n_rep * n_slots; i += blockDim.x) {
-      const int r = i / n_slots;
-      const int w = wa_s[i];
-      unsigned long long *u = p.U + ((a * n_rep + r) * n_slots + w) * 2;
-      if (e_s[2 * i]) atomicAdd(u, (unsigned long long)e_s[2 * i]);
-      if (e_s[2 * i + 1]) atomicAdd(u + 1, (unsigned long long)e_s[2 * i + 1]);
-    }
-  }
+  LanesSample<Word> S;
+  S.spins = p.spins + a * p.n_groups * p.N;
+  S.T = p.T;
+  S.walker = p.walker + a * p.n_rep * p.n_slots;
+  S.U = p.U + a * p.n_rep * p.n_slots * 2;
+  S.J = p.J + a * p.plane;
+  S.key = p.key;
+  S.ctr_w = (DOM_SWEEP << 28) | (uint32_t)(a >> 6);
+  S.t = (uint32_t)*p.d_t;
+  S.hpd = p.half_plane_div;
+  S.L = p.L;
+  S.Lt = p.Lt;
+  S.plane = p.plane;
+  S.half_plane = p.half_plane;
+  S.N = (int)p.N;
+  S.n_slots = p.n_slots;
+  S.n_rep = p.n_rep;
+  S.rpw = p.rpw;
+  S.n_groups = p.n_groups;
+  const int64_t j0 = (int64_t)blockIdx.x * tile_sites;
+  const int n = (int)(p.half_N - j0 < tile_sites ? p.half_N - j0 : tile_sites);
+  lanes_tile<Word, false, BLUE>(S, colour, (int)j0, n, count_only, colour == 0 && blockIdx.x == 0, smem_raw);
 }
 
 __global__ void zero_u64_kernel(unsigned long long *p, int64_t n) {
@@ -320,16 +209,6 @@ __global__ void lanes_init_spins_kernel(Word *spins, int64_t n_a, int64_t N, int
 }
 
 template <typename Word>
-size_t lanes_smem_bytes(const qisg_handle *h, int spb) {
-  size_t smem = (size_t)(h->n_slots * 15 + 3 * h->n_rep * h->n_slots) * 4;
-  smem = (smem + 7) & ~size_t(7);
-  smem += (size_t)spb * h->n_groups * sizeof(Word);
-  smem = (smem + 7) & ~size_t(7);
-  smem += (size_t)h->L * h->L * (sizeof(uint2) + sizeof(uint16_t) + 1);
-  return smem;
-}
-
-template <typename Word>
 LanesArgs<Word> make_args(qisg_handle *h) {
   LanesArgs<Word> p;
   p.spins = reinterpret_cast<Word *>(h->spins);
@@ -357,32 +236,33 @@ LanesArgs<Word> make_args(qisg_handle *h) {
 template <typename Word>
 int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   LanesArgs<Word> p = make_args<Word>(h);
-  const int64_t blocks = (p.half_N + p.sites_per_block - 1) / p.sites_per_block;
-  const size_t smem = lanes_smem_bytes<Word>(h, p.sites_per_block);
+  const size_t smem = lanes_tile_smem(p.plane, h->n_slots, h->n_rep);
+  // tiles of rows x 256 sites (rows <= 16, the counters' limit), as long as
+  // the grid keeps about four blocks per SM
+  const int64_t n_launch_samples = h->per_sample_launch ? 1 : h->n_samples;
+  int rows = 16;
+  while (rows > 1 && ((p.half_N + 256LL * rows - 1) / (256LL * rows)) * n_launch_samples < 4LL * h->n_sm) rows >>= 1;
+  const int tile_sites = 256 * rows;
+  const int64_t blocks = (p.half_N + tile_sites - 1) / tile_sites;
   if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+  if (smem > 227 * 1024) return fail(QISG_EINVAL, "LANES plane tables exceed shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr_set = true;
   }
-  if (smem > 227 * 1024) return fail(QISG_EINVAL, "LANES plane tables exceed shared memory");
-  if (h->per_sample_launch) {
-    for (int64_t a = 0; a < h->n_samples; ++a) {
-      const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
-      lanes_half_sweep_kernel<Word><<<dim3((unsigned)blocks, 1), kBlock, smem, h->stream>>>(
-          p, colour, count_only, a);
-      prof_end(h, QISG_KERNEL_SWEEP, tok);
-      h->launches++;
-    }
-  } else {
-    for (int64_t a0 = 0; a0 < h->n_samples; a0 += 65535) {
-      const int64_t na = std::min<int64_t>(65535, h->n_samples - a0);
-      const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
-      lanes_half_sweep_kernel<Word><<<dim3((unsigned)blocks, (unsigned)na), kBlock, smem, h->stream>>>(
-          p, colour, count_only, a0);
-      prof_end(h, QISG_KERNEL_SWEEP, tok);
-      h->launches++;
-    }
+  for (int64_t a0 = 0; a0 < h->n_samples; a0 += (h->per_sample_launch ? 1 : 65535)) {
+    const int64_t na = h->per_sample_launch ? 1 : std::min<int64_t>(65535, h->n_samples - a0);
+    const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
+    if (colour == 1)
+      lanes_half_sweep_kernel<Word, true><<<dim3((unsigned)blocks, (unsigned)na), kBlock, smem, h->stream>>>(
+          p, 1, count_only, a0, tile_sites);
+    else
+      lanes_half_sweep_kernel<Word, false><<<dim3((unsigned)blocks, (unsigned)na), kBlock, smem, h->stream>>>(
+          p, 0, count_only, a0, tile_sites);
+    prof_end(h, QISG_KERNEL_SWEEP, tok);
+    h->launches++;
   }
   return cuda_check(cudaGetLastError(), "lanes half sweep");
 }

@@ -264,9 +264,9 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
       delete h;
       return fail(QISG_EINVAL, "LANES packing needs n_slots <= word bits");
     }
-    if (n_replicas > 64) {
+    if (n_replicas > 2 * (W / n_slots)) {
       delete h;
-      return fail(QISG_EINVAL, "LANES packing needs n_replicas <= 64");
+      return fail(QISG_EINVAL, "LANES packing needs n_replicas <= 2 * (word bits / n_slots)");
     }
     h->W = W;
     h->rpw = W / n_slots;

@@ -243,6 +243,137 @@ __device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua
   return acc;
 }
 
+// ---- bit-sliced helpers shared by the sweep kernels ----
+
+template <typename Word>
+__device__ __forceinline__ Word ones_if(bool b) {
+  return b ? ~Word(0) : Word(0);
+}
+
+// sel ? a : b, bitwise
+template <typename Word>
+__device__ __forceinline__ Word mux(Word sel, Word a, Word b) {
+  return (sel & a) | (~sel & b);
+}
+
+template <typename Word>
+__device__ __forceinline__ Word maj3(Word a, Word b, Word c) {
+  return (a & b) | (c & (a ^ b));
+}
+
+// Bit-sliced per-lane counter: plane p holds bit p of every lane's count.
+template <typename Word, int K>
+struct VCount {
+  Word p[K];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < K; ++i) p[i] = 0;
+  }
+  // add x0 + 2 x1 + 4 x2 (per lane)
+  __device__ __forceinline__ void add3(Word x0, Word x1, Word x2) {
+    Word c = p[0] & x0;
+    p[0] ^= x0;
+    Word s = p[1] ^ x1 ^ c;
+    c = maj3(p[1], x1, c);
+    p[1] = s;
+    s = p[2] ^ x2 ^ c;
+    c = maj3(p[2], x2, c);
+    p[2] = s;
+#pragma unroll
+    for (int i = 3; i < K; ++i) {
+      const Word t = p[i] & c;
+      p[i] ^= c;
+      c = t;
+    }
+  }
+  // add x0 + 2 x1
+  __device__ __forceinline__ void add2(Word x0, Word x1) {
+    Word c = p[0] & x0;
+    p[0] ^= x0;
+    const Word s = p[1] ^ x1 ^ c;
+    c = maj3(p[1], x1, c);
+    p[1] = s;
+#pragma unroll
+    for (int i = 2; i < K; ++i) {
+      const Word t = p[i] & c;
+      p[i] ^= c;
+      c = t;
+    }
+  }
+  // add x (one bit per lane)
+  __device__ __forceinline__ void add1(Word x) {
+    Word c = x;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const Word t = p[i] & c;
+      p[i] ^= c;
+      c = t;
+    }
+  }
+};
+
+template <typename Word>
+__device__ __forceinline__ Word shfl_xor_w(Word v, int m) {
+  if (sizeof(Word) == 8) {
+    const unsigned long long u = (unsigned long long)v;
+    const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)u, m);
+    const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(u >> 32), m);
+    return (Word)(((unsigned long long)hi << 32) | lo);
+  }
+  return (Word)__shfl_xor_sync(0xffffffffu, (unsigned)v, m);
+}
+
+template <typename Word>
+__device__ __forceinline__ Word shfl_w(Word v, int src) {
+  if (sizeof(Word) == 8) {
+    const unsigned long long u = (unsigned long long)v;
+    const unsigned lo = __shfl_sync(0xffffffffu, (unsigned)u, src);
+    const unsigned hi = __shfl_sync(0xffffffffu, (unsigned)(u >> 32), src);
+    return (Word)(((unsigned long long)hi << 32) | lo);
+  }
+  return (Word)__shfl_sync(0xffffffffu, (unsigned)v, src);
+}
+
+// Sum a per-thread counter over the warp threads that share (lane % G) and
+// add each of the W lanes' totals into acc[key][lane] (shared memory).
+// K planes per thread; the warp total needs up to K + 5 planes.  Every
+// thread of the warp must call this (full-mask shuffles).
+template <typename Word, int K, int G>
+__device__ __forceinline__ void flush_counter(const VCount<Word, K> &c, int *acc) {
+  constexpr int KT = K + 5;
+  constexpr int W = (int)sizeof(Word) * 8;
+  Word tot[KT];
+#pragma unroll
+  for (int i = 0; i < KT; ++i) tot[i] = i < K ? c.p[i] : Word(0);
+#pragma unroll
+  for (int off = G; off < 32; off <<= 1) {
+    Word carry = 0;
+#pragma unroll
+    for (int i = 0; i < KT; ++i) {
+      const Word o = shfl_xor_w(tot[i], off);
+      const Word s = tot[i] ^ o ^ carry;
+      carry = maj3(tot[i], o, carry);
+      tot[i] = s;
+    }
+  }
+  // thread t extracts lanes l = t / G + m * (32 / G) of key t % G from the
+  // totals held (identically) by every thread with that key
+  const int t = threadIdx.x & 31;
+  const int key = t % G;
+  Word mine[KT];
+#pragma unroll
+  for (int i = 0; i < KT; ++i) mine[i] = shfl_w(tot[i], key);
+  constexpr int per = W * G / 32;
+#pragma unroll
+  for (int m = 0; m < per; ++m) {
+    const int lane = t / G + m * (32 / G);
+    int v = 0;
+#pragma unroll
+    for (int i = 0; i < KT; ++i) v |= (int)((mine[i] >> lane) & 1u) << i;
+    if (v) atomicAdd(&acc[key * W + lane], v);
+  }
+}
+
 // Stage the PT constants of a handle in shared memory (call with all
 // threads of the block, followed by __syncthreads()).
 __device__ __forceinline__ void load_ptconst(PTConst *dst, const PTConst *src) {
