@@ -35,10 +35,10 @@ struct SamplesArgs {
   unsigned long long *U;
   const unsigned long long *d_t;
   uint2 key;
-  FastDiv half_plane_div;  // j -> tau for the L*L/2 sites of one colour per plane
   int64_t N, half_N;
   int L, Lt, plane, half_plane, n_slots, n_rep, n_q, W;
-  int groups_per_quad;   // site groups (4 sites) each quad handles
+  int seg_sites;         // G: sites of one colour each quad walks along tau
+  int n_seg;             // (L_tau / 2) / G segments per column
   int blocks_per_set;    // blocks per (b, s, q) word set
   int t_has_zero;        // some threshold of the table is 0 (always reject)
   // cleared by the red pass (nothing reads them until the blue pass / PT):
@@ -46,18 +46,6 @@ struct SamplesArgs {
   int64_t n_zero_U;
   Word *zero_acc;               // PT lane masks, n_zero_acc words
   int64_t n_zero_acc;
-};
-
-// Shared-memory layout of the half sweep (dynamic).
-template <typename Word>
-struct SweepSmem {
-  static size_t bytes(int plane) {
-    size_t o = sizeof(uint4) * 256 + 16 * 4 + 2 * 4 * 64 * 4;   // rnd, Ts, accU
-    o += 2 * (size_t)plane * sizeof(Word);                        // Jx, Jy
-    o += (size_t)plane * sizeof(uint2);                           // neighbours
-    o += (size_t)plane * sizeof(uint16_t);                        // colour-site table
-    return (o + 15) & ~size_t(15);
-  }
 };
 
 // Reject flag of a class: reject iff T is not the always-accept sentinel
@@ -73,27 +61,24 @@ __device__ __forceinline__ Word rho_ge(uint32_t R, uint32_t T) {
   return ones_if<Word>(T != 0xFFFFFFFFu && R >= T);
 }
 
-// One half sweep.  Block: one (b, s, q) word set, 64 quads; quad thread j
-// owns replica r = 4q + j.  Per group of 4 sites every thread of a quad
-// computes one Philox call (for site 4G + j), which serves the four
-// replicas of that site; the results are exchanged in shared memory.  The
-// colour-site -> site map, the neighbour table of the L x L plane and the
-// block's couplings are staged in shared memory once per block.
-// G2 = log2(groups per quad) sizes the per-thread energy counters.
+// One half sweep, column walk.  Block: one (b, s, q) word set; quad thread j
+// owns replica r = 4q + j.  Quad k owns one (x, y) column and a segment of
+// G sites of the colour along tau (tau = tau0, tau0 + 2, ...; tau0 = 2 G seg
+// + ((colour + x + y) & 1)), so the column's couplings and neighbour offsets
+// stay in registers and the word at tau - 1 is the previous step's tau + 1.
+// Per group of 4 steps every thread of a quad computes one Philox call (for
+// step 4g + j), which serves the four replicas of that site; the results are
+// exchanged in shared memory.  G2 = ceil(log2(G / 4)) sizes the per-thread
+// energy counters.
 template <typename Word, bool BLUE, int G2>
 __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<Word> p, int colour,
                                                                     int count_only) {
   constexpr int W = (int)sizeof(Word) * 8;
   constexpr int KS = G2 + 5;   // u_s sum <= 4 * 4 * 2^G2 per thread
   constexpr int KT = G2 + 4;   // u_t sum <= 2 * 4 * 2^G2 per thread
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint4 *rnd = reinterpret_cast<uint4 *>(smem);
-  uint32_t *Ts = reinterpret_cast<uint32_t *>(rnd + 256);
-  int *accU = reinterpret_cast<int *>(Ts + 16);
-  Word *Jx = reinterpret_cast<Word *>(accU + 2 * 4 * 64);
-  Word *Jy = Jx + p.plane;
-  uint2 *nb = reinterpret_cast<uint2 *>(Jy + p.plane);
-  uint16_t *s2d = reinterpret_cast<uint16_t *>(nb + p.plane);
+  __shared__ uint4 rnd[kBlock];
+  __shared__ uint32_t Ts[16];
+  __shared__ int accU[BLUE ? 2 * 4 * 64 : 1];
 
   const int64_t set = blockIdx.x / p.blocks_per_set;
   const int chunk = (int)(blockIdx.x - set * p.blocks_per_set);
@@ -103,7 +88,6 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
   const int j = threadIdx.x & 3;
   const int quad = threadIdx.x >> 2;
   const int r = 4 * q + j;
-  const int L = p.L, plane = p.plane, hp = p.half_plane;
 
   if (threadIdx.x < 15) {
     const uint32_t T = p.T[s * 15 + threadIdx.x];
@@ -118,18 +102,6 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_acc; i += stride)
       p.zero_acc[i] = 0;
   }
-  const Word *Jb = p.J + b * (int64_t)plane * 2;
-  for (int i2 = threadIdx.x; i2 < plane; i2 += blockDim.x) {
-    const int y = i2 / L, x = i2 - y * L;
-    const int xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
-    const int yp = y + 1 == L ? 0 : y + 1, ym = y == 0 ? L - 1 : y - 1;
-    nb[i2] = make_uint2((uint32_t)(xp + L * y) | ((uint32_t)(xm + L * y) << 16),
-                        (uint32_t)(x + L * yp) | ((uint32_t)(x + L * ym) << 16));
-    Jx[i2] = Jb[2 * i2];
-    Jy[i2] = Jb[2 * i2 + 1];
-    // the k-th site of parity (x + y) & 1 in row-major order is k = i2 / 2
-    s2d[((x + y) & 1) * hp + (i2 >> 1)] = (uint16_t)i2;
-  }
   __syncthreads();
 
   uint32_t T[15];
@@ -137,11 +109,29 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
   for (int i = 0; i < 15; ++i) T[i] = Ts[i];
   const bool has_zero = p.t_has_zero != 0;
 
+  const int L = p.L, plane = p.plane, G = p.seg_sites;
+  const uint32_t Lt = (uint32_t)p.Lt;
+  const int64_t gq = (int64_t)chunk * kQuads + quad;
+  const bool live = gq < (int64_t)plane * p.n_seg;   // uniform per quad
+  const int i2 = (int)(gq % plane);
+  const int seg = (int)(gq / plane);
+  const int y = i2 / L, x = i2 - y * L;
+  const uint32_t ixp = (uint32_t)((x + 1 == L ? 0 : x + 1) + L * y), ixm = (uint32_t)((x == 0 ? L - 1 : x - 1) + L * y);
+  const uint32_t iyp = (uint32_t)(x + L * (y + 1 == L ? 0 : y + 1)), iym = (uint32_t)(x + L * (y == 0 ? L - 1 : y - 1));
+  const Word *Jb = p.J + b * (int64_t)plane * 2;
+  Word Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
+  if (live) {
+    Jxp = Jb[2 * i2];
+    Jxm = Jb[2 * ixm];
+    Jyp = Jb[2 * i2 + 1];
+    Jym = Jb[2 * iym + 1];
+  }
+  const uint32_t tau0 = 2u * (uint32_t)G * (uint32_t)seg + (uint32_t)((colour + x + y) & 1);
+
   Word *base = p.spins + ((b * p.n_slots + s) * p.n_q + q) * p.N * 4 + j;
   const unsigned long long t = *p.d_t;
   const uint32_t ctr_z = (uint32_t)s | ((uint32_t)(r >> 2) << 16);
   const uint32_t ctr_w = (DOM_SWEEP << 28) | (uint32_t)((b * W) >> 6);
-  const uint32_t Lt = (uint32_t)p.Lt;
 
   VCount<Word, KS> cs;
   VCount<Word, KT> ct;
@@ -150,39 +140,34 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
     ct.zero();
   }
 
-  const uint32_t n_groups = (uint32_t)(p.half_N >> 2);
-  for (int gi = 0; gi < p.groups_per_quad; ++gi) {
-    const uint32_t G = ((uint32_t)chunk * p.groups_per_quad + gi) * kQuads + quad;
-    const bool live = G < n_groups;   // uniform per quad
-    if (live) {
-      const uint32_t jj = 4 * G + j;
-      const uint32_t tau = p.half_plane_div.div(jj);
-      const uint32_t k = jj - tau * hp;
-      const uint32_t i2 = s2d[((colour + tau) & 1) * hp + k];
-      rnd[threadIdx.x] = philox(make_uint4(i2 + tau * plane, (uint32_t)t, ctr_z, ctr_w), p.key);
+  Word prev_up = 0;   // word at tau + 1 of the previous step = tau - 1 now
+  for (int g4 = 0; 4 * g4 < G; ++g4) {
+    if (live && 4 * g4 + j < G) {
+      const uint32_t tj = tau0 + 2u * (uint32_t)(4 * g4 + j);
+      rnd[threadIdx.x] = philox(make_uint4((uint32_t)i2 + tj * (uint32_t)plane, (uint32_t)t, ctr_z, ctr_w), p.key);
     }
     __syncwarp();
     if (live) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
+        const int k = 4 * g4 + i;
+        if (k >= G) break;
         const uint32_t R = pick4(rnd[(quad << 2) + i], j);
-        const uint32_t jj = 4 * G + i;
-        const uint32_t tau = p.half_plane_div.div(jj);
-        const uint32_t k = jj - tau * hp;
-        const uint32_t i2 = s2d[((colour + tau) & 1) * hp + k];
-        const uint2 nv = nb[i2];
-        const uint32_t off = tau * plane;
+        const uint32_t tau = tau0 + 2u * (uint32_t)k;
+        const uint32_t off = tau * (uint32_t)plane;
         const uint32_t offp = tau + 1 == Lt ? 0u : off + plane;
-        const uint32_t offm = tau == 0 ? (Lt - 1) * plane : off - plane;
-        const uint32_t site = i2 + off;
-        const uint32_t ixp = nv.x & 0xFFFFu, ixm = nv.x >> 16, iyp = nv.y & 0xFFFFu, iym = nv.y >> 16;
+        const uint32_t site = (uint32_t)i2 + off;
         const Word sc = base[(size_t)site * 4];
-        const Word b1 = sc ^ base[(size_t)(ixp + off) * 4] ^ Jx[i2];
-        const Word b2 = sc ^ base[(size_t)(ixm + off) * 4] ^ Jx[ixm];
-        const Word b3 = sc ^ base[(size_t)(iyp + off) * 4] ^ Jy[i2];
-        const Word b4 = sc ^ base[(size_t)(iym + off) * 4] ^ Jy[iym];
-        const Word t1 = sc ^ base[(size_t)(i2 + offp) * 4];
-        const Word t2 = sc ^ base[(size_t)(i2 + offm) * 4];
+        const Word up = base[(size_t)((uint32_t)i2 + offp) * 4];
+        const Word dn = k == 0 ? base[(size_t)((uint32_t)i2 + (tau == 0 ? (Lt - 1) * (uint32_t)plane : off - plane)) * 4]
+                               : prev_up;
+        prev_up = up;
+        const Word b1 = sc ^ base[(size_t)(ixp + off) * 4] ^ Jxp;
+        const Word b2 = sc ^ base[(size_t)(ixm + off) * 4] ^ Jxm;
+        const Word b3 = sc ^ base[(size_t)(iyp + off) * 4] ^ Jyp;
+        const Word b4 = sc ^ base[(size_t)(iym + off) * 4] ^ Jym;
+        const Word t1 = sc ^ up;
+        const Word t2 = sc ^ dn;
         // bit-sliced u_s (3 bits) and u_t (2 bits)
         const Word s1 = b1 ^ b2 ^ b3;
         const Word c1 = maj3(b1, b2, b3);
@@ -453,7 +438,6 @@ SamplesArgs<Word> make_args(qisg_handle *h) {
   p.Lt = h->Lt;
   p.plane = h->L * h->L;
   p.half_plane = p.plane / 2;
-  p.half_plane_div = FastDiv((uint32_t)p.half_plane);
   p.n_slots = h->n_slots;
   p.n_rep = h->n_rep;
   p.n_q = h->n_q;
@@ -465,47 +449,49 @@ SamplesArgs<Word> make_args(qisg_handle *h) {
   p.t_has_zero = 0;
   for (uint32_t v : h->T)
     if (v == 0) p.t_has_zero = 1;
-  // site groups of one word set per quad: a power of two, as large as
-  // possible (cheaper energy flushes) while the grid still gives about
-  // min_blocks_per_sm blocks to every SM
-  const int64_t n_groups = p.half_N / 4;
+  // sites per quad along tau: as many as possible (cheaper energy flushes)
+  // while the grid keeps about sweep_min_blocks_per_sm blocks per SM; G must
+  // divide L_tau / 2
+  const int half_col = h->Lt / 2;
   const int64_t sets = h->n_b * h->n_slots * h->n_q;
-  int gpq = 64;
   const int64_t want_blocks = (int64_t)h->sweep_min_blocks_per_sm * std::max(1, h->n_sm);
-  if (h->sweep_groups_per_quad > 0) {
-    gpq = h->sweep_groups_per_quad;
-  } else {
-    while (gpq > 1 && sets * ((n_groups + (int64_t)kQuads * gpq - 1) / ((int64_t)kQuads * gpq)) < want_blocks)
-      gpq >>= 1;
-  }
-  p.groups_per_quad = gpq;
-  p.blocks_per_set = (int)((n_groups + (int64_t)kQuads * gpq - 1) / ((int64_t)kQuads * gpq));
+  int G = 4 * std::max(1, h->sweep_groups_per_quad > 0 ? h->sweep_groups_per_quad : 64);
+  auto blocks_for = [&](int g) {
+    const int gg = std::min(g, half_col);
+    const int ns = half_col / gg;
+    return sets * (((int64_t)p.plane * ns + kQuads - 1) / kQuads);
+  };
+  if (h->sweep_groups_per_quad <= 0)
+    while (G > 4 && blocks_for(G) < want_blocks) G >>= 1;
+  if (G > half_col) G = half_col;
+  if (half_col % G) G = half_col;   // one segment per column
+  p.seg_sites = G;
+  p.n_seg = half_col / G;
+  p.blocks_per_set = (int)(((int64_t)p.plane * p.n_seg + kQuads - 1) / kQuads);
   return p;
 }
 
 template <typename Word, bool BLUE, int G2>
 void launch_sweep(const SamplesArgs<Word> &p, unsigned blocks, size_t smem, cudaStream_t st, int colour,
                   int count_only) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(samples_half_sweep_kernel<Word, BLUE, G2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         227 * 1024);
-    attr_set = true;
-  }
   samples_half_sweep_kernel<Word, BLUE, G2><<<blocks, kBlock, smem, st>>>(p, colour, count_only);
 }
 
 template <typename Word, bool BLUE>
 void launch_sweep_g(const SamplesArgs<Word> &p, unsigned blocks, size_t smem, cudaStream_t st, int colour,
                     int count_only) {
-  switch (p.groups_per_quad) {
-    case 1: launch_sweep<Word, BLUE, 0>(p, blocks, smem, st, colour, count_only); break;
-    case 2: launch_sweep<Word, BLUE, 1>(p, blocks, smem, st, colour, count_only); break;
-    case 4: launch_sweep<Word, BLUE, 2>(p, blocks, smem, st, colour, count_only); break;
-    case 8: launch_sweep<Word, BLUE, 3>(p, blocks, smem, st, colour, count_only); break;
-    case 16: launch_sweep<Word, BLUE, 4>(p, blocks, smem, st, colour, count_only); break;
-    case 32: launch_sweep<Word, BLUE, 5>(p, blocks, smem, st, colour, count_only); break;
-    default: launch_sweep<Word, BLUE, 6>(p, blocks, smem, st, colour, count_only); break;
+  // counter planes for G sites per thread: G2 = ceil(log2(G / 4))
+  int g2 = 0;
+  while ((4 << g2) < p.seg_sites) ++g2;
+  switch (g2) {
+    case 0: launch_sweep<Word, BLUE, 0>(p, blocks, smem, st, colour, count_only); break;
+    case 1: launch_sweep<Word, BLUE, 1>(p, blocks, smem, st, colour, count_only); break;
+    case 2: launch_sweep<Word, BLUE, 2>(p, blocks, smem, st, colour, count_only); break;
+    case 3: launch_sweep<Word, BLUE, 3>(p, blocks, smem, st, colour, count_only); break;
+    case 4: launch_sweep<Word, BLUE, 4>(p, blocks, smem, st, colour, count_only); break;
+    case 5: launch_sweep<Word, BLUE, 5>(p, blocks, smem, st, colour, count_only); break;
+    case 6: launch_sweep<Word, BLUE, 6>(p, blocks, smem, st, colour, count_only); break;
+    default: launch_sweep<Word, BLUE, 7>(p, blocks, smem, st, colour, count_only); break;
   }
 }
 
@@ -515,7 +501,7 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   const int64_t sets = h->n_b * h->n_slots * h->n_q;
   const int64_t blocks = sets * p.blocks_per_set;
   if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
-  const size_t smem = SweepSmem<Word>::bytes(p.plane);
+  const size_t smem = 0;
   const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
   if (colour == 1)
     launch_sweep_g<Word, true>(p, (unsigned)blocks, smem, h->stream, 1, count_only);
@@ -673,9 +659,7 @@ int set_couplings_t(qisg_handle *h, const int8_t *J) {
 
 int samples_init(qisg_handle *h) {
   if (h->n_slots > kMaxSlotsPermute) return fail(QISG_EINVAL, "SAMPLES packing supports up to 32 slots");
-  if (h->L > 128) return fail(QISG_EINVAL, "SAMPLES packing supports L <= 128");
-  if (SweepSmem<unsigned long long>::bytes(h->L * h->L) > 227 * 1024)
-    return fail(QISG_EINVAL, "plane tables exceed shared memory");
+  if (h->L > 1024) return fail(QISG_EINVAL, "SAMPLES packing supports L <= 1024");
   return h->W == 64 ? init_t<unsigned long long>(h) : init_t<unsigned int>(h);
 }
 int samples_half_sweep(qisg_handle *h, int colour, int count_only) {
