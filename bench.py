@@ -158,17 +158,12 @@ def batched_layout(qisg):
     return int(os.environ.get("QISG_BENCH_LAYOUT", qisg.QISG_LAYOUT_SAMPLES))
 
 
-def time_form(torch, qisg, w, form, steps, warmup, seed):
-    """Device time of `steps` steps (CUDA events on the library's stream,
-    L2 flushed between steps), plus live per-kernel timing."""
-    inst = make_instance(qisg, w, form, seed)
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
-    for _ in range(warmup):
-        inst.sweep(SWEEPS_PER_STEP)
-    inst.sync()
-    torch.cuda.synchronize()
-    launches0 = inst.launch_count()
-    inst.profile(True)
+KINDS = (("sweep", 0), ("pt", 1), ("measure", 2), ("permute", 3))
+
+
+def timed_steps(torch, inst, flush, steps):
+    """Device time (ms) of `steps` steps, CUDA events on the library's stream
+    (torch's current stream), L2 flushed before each step."""
     evs = []
     for _ in range(steps):
         flush.zero_()
@@ -179,14 +174,44 @@ def time_form(torch, qisg, w, form, steps, warmup, seed):
         b.record()
         evs.append((a, b))
     torch.cuda.synchronize()
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    return sum(a.elapsed_time(b) for a, b in evs)
+
+
+def read_profile(inst, names):
+    out = {}
+    for name, kind in KINDS:
+        if name in names:
+            ms, nt, nl = inst.profile_read(kind)
+            out[name] = {"ms": ms, "timed": nt, "launched": nl,
+                         "us_per_launch": 1000.0 * ms / nt if nt else None}
+    return out
+
+
+def time_form(torch, qisg, w, form, steps, warmup, seed):
+    """The timed region: `steps` plain steps (no instrumentation).  Then two
+    more passes of the same steps for the kernel figures: event pairs around
+    the half-sweep launches only (the roofline's launch duration), and event
+    pairs around every launch (the per-kernel breakdown).  An event pair waits
+    for the work before it, so these passes run slower than the plain one."""
+    inst = make_instance(qisg, w, form, seed)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    for _ in range(warmup):
+        inst.sweep(SWEEPS_PER_STEP)
+    inst.sync()
+    torch.cuda.synchronize()
+    launches0 = inst.launch_count()
+    total_ms = timed_steps(torch, inst, flush, steps)
     launches = inst.launch_count() - launches0
-    kern = {}
-    for kind, name in ((qisg.KERNEL_SWEEP, "sweep"), (qisg.KERNEL_PT, "pt"),
-                       (qisg.KERNEL_MEASURE, "measure"), (qisg.KERNEL_PERMUTE, "permute")):
-        ms, nt, nl = inst.profile_read(kind)
-        kern[name] = {"ms": ms, "timed": nt, "launched": nl}
+    inst.profile(True, kinds=[qisg.KERNEL_SWEEP])
+    sweep_pass_ms = timed_steps(torch, inst, flush, steps)
+    kern = read_profile(inst, ("sweep",))
+    inst.profile(True)
+    all_pass_ms = timed_steps(torch, inst, flush, steps)
+    breakdown = read_profile(inst, [k for k, _ in KINDS])
     inst.profile(False)
+    breakdown["pass_ms_per_step"] = all_pass_ms / steps
+    kern["pass_ms_per_step"] = sweep_pass_ms / steps
+    kern["breakdown"] = breakdown
     layout, wb = inst.layout()
     inst.close()
     del flush
@@ -302,21 +327,24 @@ def large_batched_entry(torch, qisg, sweeps=20):
     ladder = qisg.ladder_linear(w.k_lo, w.k_hi, w.n_slots, w.gamma)
     cfg = qisg.Config(w.L, w.L_tau, ladder, w.n_replicas, w.n_samples, w.seed, word_bits=64,
                       layout=qisg.QISG_LAYOUT_SAMPLES)
+    def run(n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        inst.sweep(n)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
     with qisg.Instance(cfg) as inst:
         inst.sweep(2)
         inst.sync()
+        ms = run(sweeps)                      # plain: the value
+        inst.profile(True, kinds=[qisg.KERNEL_SWEEP])
+        run(sweeps)                           # half-sweep launch durations
+        kern = read_profile(inst, ("sweep",))
         inst.profile(True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        inst.sweep(sweeps)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        kern = {}
-        for kind, name in ((qisg.KERNEL_SWEEP, "sweep"), (qisg.KERNEL_PT, "pt"),
-                           (qisg.KERNEL_PERMUTE, "permute")):
-            kms, nt, nl = inst.profile_read(kind)
-            kern[name] = {"ms": kms, "timed": nt, "launched": nl}
+        run(sweeps)                           # breakdown (event pairs on every launch)
+        kern.update({k: v for k, v in read_profile(inst, ("pt", "permute")).items()})
         inst.profile(False)
     N = w.L * w.L * w.L_tau
     ups = w.n_samples * w.n_replicas * w.n_slots * N * sweeps
@@ -328,7 +356,7 @@ def large_batched_entry(torch, qisg, sweeps=20):
     bytes_per_launch = 0.25 * ups / sweeps / 2
     achieved = bytes_per_launch / (per_launch * 1e-3) / 1e9
     return {"value": ms * 1e9 / ups, "unit": UNIT, "ms": ms, "sweeps": sweeps,
-            "workload": w.name, "kernels_ms": {k: v["ms"] for k, v in kern.items()},
+            "workload": w.name, "kernel_us_per_launch": {k: v["us_per_launch"] for k, v in kern.items()},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs", 6800.0),
                          "unit": "GB/s", "frac": achieved / pk.get("hbm_gbs", 6800.0), "traffic": None,
                          "kernel": "half_sweep", "bytes_per_update": 0.25}}
@@ -372,6 +400,17 @@ def cpu_baseline(w, budget_s=15.0):
     ups = n_a * w.n_replicas * w.n_slots * w.L * w.L * w.L_tau * sweeps
     return {"value": wall * 1e12 / ups, "unit": UNIT, "cores": min(ncores, n_a), "kind": "oracle",
             "sample": f"{n_a} samples x {sweeps} sweeps of the workload ({wall:.1f} s)"}
+
+
+def kernel_timing(kern, steps):
+    bd = kern["breakdown"]
+    return {"how": "second and third passes of the same steps with event pairs around the half sweeps "
+                   "(roofline) and around every launch (breakdown); pairs serialise the graph",
+            "sweep_us_per_launch": kern["sweep"]["us_per_launch"],
+            "sweep_pass_ms_per_step": kern["pass_ms_per_step"],
+            "breakdown_us_per_launch": {k: bd[k]["us_per_launch"] for k, _ in KINDS},
+            "breakdown_launches": {k: bd[k]["launched"] for k, _ in KINDS},
+            "breakdown_pass_ms_per_step": bd["pass_ms_per_step"]}
 
 
 def run_gpu(args):
@@ -429,7 +468,7 @@ def run_gpu(args):
                    "l2": "flushed between steps (2x L2 buffer written); lattice fits in L2 within a step"},
         "gpu_launches": launches,
         "clocks": clocks,
-        "kernels_ms": {k: v["ms"] for k, v in kern.items()},
+        "kernel_timing": kernel_timing(kern, args.steps),
     }
     for form in forms[1:]:
         tm, ln, kn, lay, wbb = results[form]

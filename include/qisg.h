@@ -198,7 +198,12 @@ int qisg_launch_count(qisg_handle *h, int64_t *n);
 /* Start (enable = 1, counters reset) or stop (0) timing every launch of the
  * kernels above with CUDA events recorded on the handle's stream, around the
  * launch, at most 65536 launches per kind (later launches are counted, not
- * timed).  Diagnostics for roofline figures; off by default. */
+ * timed).  enable = QISG_PROFILE_ONLY | (1 << kind) | ... times only the
+ * kinds named.  An event pair waits for the work before it, so a timed
+ * launch no longer overlaps its neighbours' launch latency: profiled runs
+ * are slower than plain ones.  Diagnostics for roofline figures; off by
+ * default. */
+#define QISG_PROFILE_ONLY 0x100
 int qisg_profile(qisg_handle *h, int enable);
 
 /* Total device time (ms) of the timed launches of one kind, how many were

@@ -35,8 +35,8 @@ __global__ void pt_lanes_kernel(int32_t *walker, unsigned long long *U, const PT
 }
 
 // SAMPLES: block = 8 warps = samples b*W + 8*o + v (v = warp) of replica r;
-// thread 0 then ORs the 8 accept bitmasks into the lane masks acc[b][r][s]
-// (cleared by the red pass of the sweep).
+// the block then ORs the 8 accept bitmasks into the lane masks acc[b][r][s]
+// (cleared by the red pass of the sweep), one thread per pair.
 template <typename Word>
 __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsigned long long *U, Word *accw,
                                                          const PTConst *ptc, const double *sq,
@@ -61,17 +61,17 @@ __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsign
   }
   if ((threadIdx.x & 31) == 0) bits[v] = acc;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    Word *out = accw + (b * n_rep + r) * n_slots;
-    for (int s = 0; s + 1 < n_slots; ++s) {
-      Word m = 0;
-      for (int u = 0; u < 8; ++u) m |= (Word)((bits[u] >> s) & 1u) << (8 * o + u);
-      if (m) {
-        if (sizeof(Word) == 8)
-          atomicOr(reinterpret_cast<unsigned long long *>(&out[s]), (unsigned long long)m);
-        else
-          atomicOr(reinterpret_cast<unsigned int *>(&out[s]), (unsigned int)m);
-      }
+  const int s = threadIdx.x;   // thread s gathers pair s of the 8 chains
+  if (s + 1 < n_slots) {
+    Word m = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m |= (Word)((bits[u] >> s) & 1u) << (8 * o + u);
+    if (m) {
+      Word *out = accw + (b * n_rep + r) * n_slots;
+      if (sizeof(Word) == 8)
+        atomicOr(reinterpret_cast<unsigned long long *>(&out[s]), (unsigned long long)m);
+      else
+        atomicOr(reinterpret_cast<unsigned int *>(&out[s]), (unsigned int)m);
     }
   }
 }

@@ -45,7 +45,7 @@ void prof_record(cudaEvent_t e, cudaStream_t st) {
 }
 
 int prof_begin(qisg_handle *h, int kind) {
-  if (!h->prof) return -1;
+  if (!((h->prof >> kind) & 1)) return -1;
   h->prof_launched[kind]++;
   std::vector<cudaEvent_t> &v = h->prof_ev[kind];
   if ((int)v.size() >= 2 * kProfMax) return -1;
@@ -794,7 +794,7 @@ int qisg_profile(qisg_handle *h, int enable) {
   int rc = sync_handle(h);
   if (rc) return rc;
   if (enable) prof_clear(h);
-  h->prof = enable != 0;
+  h->prof = !enable ? 0 : (enable & QISG_PROFILE_ONLY) ? (enable & 0xF) : 0xF;
   return QISG_OK;
 }
 

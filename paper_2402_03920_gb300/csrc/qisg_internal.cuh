@@ -173,14 +173,20 @@ __device__ __forceinline__ uint32_t pt_scan(int n_slots, long long *us, long lon
   return acc;
 }
 
-// PT pass of one chain by one warp (Sec. 2.1): lane s holds the energies of
-// the configuration at slot s and draws the Philox word of pair (s, s+1);
-// the pass over pairs is a uniform loop over shuffles in which the
-// configuration carried up from pair s-1 meets the original occupant of
-// slot s+1.  BY_SLOT: energies indexed by slot (else by walker).  CG: read
-// the mutable state through L2 only (needed inside a persistent kernel, whose
-// L1 may hold lines written by other blocks earlier in the launch).  Returns
-// the accepted-pair bitmask (same in every lane).
+// PT pass of one chain by one warp (Sec. 2.1).  Lane s holds the walker and
+// energies of the configuration at slot s and draws the Philox word of pair
+// (s, s+1).  In the sequential pass the configuration that meets the original
+// occupant of slot s+1 at pair s is always one of the original occupants of
+// slots 0..s (it was carried up by accepted exchanges).  So lane s first
+// evaluates the rule for pair s against every candidate 0..s (independent
+// evaluations, bit i of D = accept with candidate i); the pass itself is then
+// a uniform loop of bit lookups: carried c, accept e = bit c of D_s; if e the
+// slot ends with s+1's configuration and c moves on, else it ends with c and
+// s+1 is carried.  Same decisions as the textbook pass, without its serial
+// dependency through the energies.
+// BY_SLOT: energies indexed by slot (else by walker).  CG: read the mutable
+// state through L2 only (persistent kernel).  Returns the accepted-pair
+// bitmask (same in every lane).
 template <bool BY_SLOT, bool CG>
 __device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua, const PTConst &pc,
                                              const double *sq, uint2 key, uint32_t t, int64_t a, int r,
@@ -200,39 +206,34 @@ __device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua
     x = pick4(philox(make_uint4((uint32_t)lane, t, (uint32_t)a, (DOM_PT << 28) | (uint32_t)(r >> 2)), key), r & 3);
     lnu = __logf((float)x) - 22.18070977791825f;
   }
-  // the configuration moving up the ladder and what each slot ends with
-  long long c_us = __shfl_sync(0xffffffffu, us, 0), c_ut = __shfl_sync(0xffffffffu, ut, 0);
-  int c_w = __shfl_sync(0xffffffffu, w, 0);
-  long long f_us = us, f_ut = ut;
-  int f_w = w;
+  // energies of the original occupant of slot s+1 (the Y of pair s)
+  const long long y_us = __shfl_down_sync(0xffffffffu, us, 1);
+  const long long y_ut = __shfl_down_sync(0xffffffffu, ut, 1);
+  uint32_t D = 0;
+  for (int i = 0; i + 1 < n_slots; ++i) {
+    const long long x_us = __shfl_sync(0xffffffffu, us, i);
+    const long long x_ut = __shfl_sync(0xffffffffu, ut, i);
+    if (lane + 1 < n_slots && i <= lane) {
+      const long long m = -2 * (y_us - x_us);   // A = 2N - 2 us
+      const long long n = -2 * (y_ut - x_ut);   // B = N - 2 ut
+      if (pt_decide(pc, sq, lane, m, n, x, lnu)) D |= 1u << i;
+    }
+  }
   uint32_t acc = 0;
-  for (int s = 0; s + 1 < n_slots; ++s) {
-    const long long y_us = __shfl_sync(0xffffffffu, us, s + 1);
-    const long long y_ut = __shfl_sync(0xffffffffu, ut, s + 1);
-    const int y_w = __shfl_sync(0xffffffffu, w, s + 1);
-    const uint32_t xs = __shfl_sync(0xffffffffu, x, s);
-    const float ls = __shfl_sync(0xffffffffu, lnu, s);
-    const long long m = -2 * (y_us - c_us);   // A = 2N - 2 us
-    const long long n = -2 * (y_ut - c_ut);   // B = N - 2 ut
-    const bool ex = pt_decide(pc, sq, s, m, n, xs, ls);
-    if (lane == s) {
-      f_us = ex ? y_us : c_us;
-      f_ut = ex ? y_ut : c_ut;
-      f_w = ex ? y_w : c_w;
-    }
-    if (ex) {
-      acc |= 1u << s;   // the carried configuration moves on to slot s+1
-    } else {
-      c_us = y_us;
-      c_ut = y_ut;
-      c_w = y_w;
-    }
+  int c = 0, mine = lane;   // carried candidate; final occupant index of this lane's slot
+  for (int s2 = 0; s2 + 1 < n_slots; ++s2) {
+    const uint32_t Ds = __shfl_sync(0xffffffffu, D, s2);
+    const bool ex = (Ds >> c) & 1u;
+    if (lane == s2) mine = ex ? s2 + 1 : c;
+    if (ex)
+      acc |= 1u << s2;
+    else
+      c = s2 + 1;
   }
-  if (lane == n_slots - 1) {
-    f_us = c_us;
-    f_ut = c_ut;
-    f_w = c_w;
-  }
+  if (lane == n_slots - 1) mine = c;
+  const int f_w = __shfl_sync(0xffffffffu, w, mine);
+  const long long f_us = __shfl_sync(0xffffffffu, us, mine);
+  const long long f_ut = __shfl_sync(0xffffffffu, ut, mine);
   if (lane < n_slots) {
     wa[lane] = f_w;
     if (BY_SLOT) {
@@ -456,7 +457,7 @@ struct qisg_handle {
   size_t device_bytes = 0;
 
   // launch timing (qisg_profile)
-  bool prof = false;
+  int prof = 0;                    // bit k: time launches of kernel kind k
   std::vector<cudaEvent_t> prof_ev[4];   // start/stop pairs per kernel kind
   int64_t prof_launched[4] = {0, 0, 0, 0};
 

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
   constexpr int W = (int)sizeof(Word) * 8;
   constexpr int KS = G2 + 5;   // u_s sum <= 4 * 4 * 2^G2 per thread
   constexpr int KT = G2 + 4;   // u_t sum <= 2 * 4 * 2^G2 per thread
-  __shared__ uint4 rnd[kBlock];
+  __shared__ uint4 rnd[kBlock];   // one Philox call per thread and group of 4 steps
   __shared__ uint32_t Ts[16];
   __shared__ int accU[BLUE ? 2 * 4 * 64 : 1];
 
@@ -140,11 +140,41 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
     ct.zero();
   }
 
-  Word prev_up = 0;   // word at tau + 1 of the previous step = tau - 1 now
+  // word at tau0 - 1 (the first step's tau - 1); later steps reuse tau + 1
+  Word prev_up = 0;
+  if (live) {
+    const uint32_t off0 = tau0 * (uint32_t)plane;
+    prev_up = base[(size_t)((uint32_t)i2 + (tau0 == 0 ? (Lt - 1) * (uint32_t)plane : off0 - plane)) * 4];
+  }
+  uint32_t *rw = reinterpret_cast<uint32_t *>(rnd);   // [step i][quad][replica j]
   for (int g4 = 0; 4 * g4 < G; ++g4) {
-    if (live && 4 * g4 + j < G) {
-      const uint32_t tj = tau0 + 2u * (uint32_t)(4 * g4 + j);
-      rnd[threadIdx.x] = philox(make_uint4((uint32_t)i2 + tj * (uint32_t)plane, (uint32_t)t, ctr_z, ctr_w), p.key);
+    // every load of the group's 4 steps is issued before any store: the
+    // steps touch disjoint words (centres of this colour, neighbours of the
+    // other), which the compiler cannot prove through one base pointer
+    Word c[4], up[4], nb[4][4];
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = 4 * g4 + i;
+        if (k < G) {
+          const uint32_t tau = tau0 + 2u * (uint32_t)k;
+          const uint32_t off = tau * (uint32_t)plane;
+          const uint32_t offp = tau + 1 == Lt ? 0u : off + plane;
+          c[i] = base[(size_t)((uint32_t)i2 + off) * 4];
+          up[i] = base[(size_t)((uint32_t)i2 + offp) * 4];
+          nb[i][0] = base[(size_t)(ixp + off) * 4];
+          nb[i][1] = base[(size_t)(ixm + off) * 4];
+          nb[i][2] = base[(size_t)(iyp + off) * 4];
+          nb[i][3] = base[(size_t)(iym + off) * 4];
+        } else {
+          c[i] = up[i] = nb[i][0] = nb[i][1] = nb[i][2] = nb[i][3] = 0;
+        }
+      }
+      if (4 * g4 + j < G) {
+        const uint32_t tj = tau0 + 2u * (uint32_t)(4 * g4 + j);
+        const uint4 x = philox(make_uint4((uint32_t)i2 + tj * (uint32_t)plane, (uint32_t)t, ctr_z, ctr_w), p.key);
+        *reinterpret_cast<uint4 *>(rw + ((j * kQuads + quad) << 2)) = x;
+      }
     }
     __syncwarp();
     if (live) {
@@ -152,21 +182,17 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
       for (int i = 0; i < 4; ++i) {
         const int k = 4 * g4 + i;
         if (k >= G) break;
-        const uint32_t R = pick4(rnd[(quad << 2) + i], j);
+        const uint32_t R = rw[((i * kQuads + quad) << 2) + j];
         const uint32_t tau = tau0 + 2u * (uint32_t)k;
-        const uint32_t off = tau * (uint32_t)plane;
-        const uint32_t offp = tau + 1 == Lt ? 0u : off + plane;
-        const uint32_t site = (uint32_t)i2 + off;
-        const Word sc = base[(size_t)site * 4];
-        const Word up = base[(size_t)((uint32_t)i2 + offp) * 4];
-        const Word dn = k == 0 ? base[(size_t)((uint32_t)i2 + (tau == 0 ? (Lt - 1) * (uint32_t)plane : off - plane)) * 4]
-                               : prev_up;
-        prev_up = up;
-        const Word b1 = sc ^ base[(size_t)(ixp + off) * 4] ^ Jxp;
-        const Word b2 = sc ^ base[(size_t)(ixm + off) * 4] ^ Jxm;
-        const Word b3 = sc ^ base[(size_t)(iyp + off) * 4] ^ Jyp;
-        const Word b4 = sc ^ base[(size_t)(iym + off) * 4] ^ Jym;
-        const Word t1 = sc ^ up;
+        const uint32_t site = (uint32_t)i2 + tau * (uint32_t)plane;
+        const Word sc = c[i];
+        const Word dn = prev_up;   // tau - 1 is the previous step's tau + 1
+        prev_up = up[i];
+        const Word b1 = sc ^ nb[i][0] ^ Jxp;
+        const Word b2 = sc ^ nb[i][1] ^ Jxm;
+        const Word b3 = sc ^ nb[i][2] ^ Jyp;
+        const Word b4 = sc ^ nb[i][3] ^ Jym;
+        const Word t1 = sc ^ up[i];
         const Word t2 = sc ^ dn;
         // bit-sliced u_s (3 bits) and u_t (2 bits)
         const Word s1 = b1 ^ b2 ^ b3;
@@ -226,6 +252,226 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
       unsigned long long *u = p.U + ((a * p.n_rep + rr) * p.n_slots + s) * 2;
       if (accU[i]) atomicAdd(u, (unsigned long long)accU[i]);
       if (accU[4 * W + i]) atomicAdd(u + 1, (unsigned long long)accU[4 * W + i]);
+    }
+  }
+}
+
+// ---- W = 32: one thread per (column segment, 4 replicas) ----
+//
+// The 4 replica words of a site are adjacent ([site][4] x 32 bits), so one
+// 16-byte load brings a site's replica quad and one Philox call gives the
+// quad's four draws.  A thread walks G sites of the colour along tau in one
+// (x, y) column, loading the next site while it updates the current one
+// (the steps touch disjoint words: centres of this colour, neighbours of the
+// other).  The 9 thresholds that can reject come from the parameter bank,
+// uniform over the block.  In the blue pass each thread keeps bit-sliced
+// counters per replica; the block then sums them with a tree in shared
+// memory (vertical adds, 32 lanes per operation) instead of warp shuffles.
+constexpr int kBlock4 = 128;
+constexpr int kLog2Block4 = 7;
+
+// Reject thresholds per slot for the classes (u_t = 0: u_s = 0..4),
+// (u_t = 1: u_s = 0, 1), (u_t = 2: u_s = 0, 1), as rho_gt / rho_ge compare
+// them (T - 1 for finite thresholds when no threshold is 0, else T).
+struct SlotThresholds {
+  uint32_t v[kMaxSlotsPT][9];
+};
+
+template <bool HAS_ZERO>
+__device__ __forceinline__ uint32_t reject_mask(uint32_t R, const uint32_t *th, uint32_t us0, uint32_t us1,
+                                                uint32_t us2, uint32_t ut0, uint32_t ut1) {
+#define QISG_F(c) (HAS_ZERO ? rho_ge<uint32_t>(R, th[c]) : rho_gt<uint32_t>(R, th[c]))
+  const uint32_t row0 = mux(us2, QISG_F(4), mux(us1, mux(us0, QISG_F(3), QISG_F(2)), mux(us0, QISG_F(1), QISG_F(0))));
+  const uint32_t low = ~(us1 | us2);
+  const uint32_t row1 = low & mux(us0, QISG_F(6), QISG_F(5));
+  const uint32_t row2 = low & mux(us0, QISG_F(8), QISG_F(7));
+#undef QISG_F
+  return mux(ut1, row2, mux(ut0, row1, row0));
+}
+
+struct Quad4 {
+  uint4 c, up, xp, xm, yp, ym;
+};
+
+__device__ __forceinline__ uint32_t q4(const uint4 &v, int j) {
+  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+// Sum the block's per-thread counters (NC counters of K planes in registers)
+// and add lane l of counter c into out[c * 32 + l]: tree over the 128
+// threads in shared memory, one more plane per level.
+template <int K, int NC>
+__device__ __forceinline__ void block_sum_counters(const VCount<uint32_t, K> *cnt, uint32_t *buf, int *out) {
+  constexpr int KF = K + kLog2Block4;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int i = 0; i < K; ++i) buf[(c * KF + i) * kBlock4 + tid] = cnt[c].p[i];
+  __syncthreads();
+#pragma unroll
+  for (int lvl = 0; lvl < kLog2Block4; ++lvl) {
+    const int half = kBlock4 >> (lvl + 1);
+    for (int w = tid; w < NC * half; w += kBlock4) {
+      const int c = w / half, e = w - c * half;
+      uint32_t *a = buf + (size_t)c * KF * kBlock4 + e;
+      uint32_t carry = 0;
+#pragma unroll
+      for (int i = 0; i < K + lvl; ++i) {
+        const uint32_t x = a[i * kBlock4], y = a[i * kBlock4 + half];
+        a[i * kBlock4] = x ^ y ^ carry;
+        carry = maj3(x, y, carry);
+      }
+      a[(K + lvl) * kBlock4] = carry;
+    }
+    __syncthreads();
+  }
+  for (int w = tid; w < NC * 32; w += kBlock4) {
+    const int c = w >> 5, l = w & 31;
+    int v = 0;
+#pragma unroll
+    for (int i = 0; i < KF; ++i) v |= (int)((buf[(c * KF + i) * kBlock4] >> l) & 1u) << i;
+    out[w] = v;
+  }
+  __syncthreads();   // buf is reused by the caller
+}
+
+template <bool BLUE, int G2>
+__global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uint32_t> p,
+                                                                  const __grid_constant__ SlotThresholds th,
+                                                                  int colour, int count_only) {
+  constexpr int KS = G2 + 5;   // u_s sum <= 4 G per replica and thread
+  constexpr int KT = G2 + 4;   // u_t sum <= 2 G
+  constexpr int KF = KS + kLog2Block4;
+  __shared__ uint32_t buf[BLUE ? 4 * KF * kBlock4 : 1];
+  __shared__ int tot[BLUE ? 2 * 4 * 32 : 1];
+
+  const int64_t set = blockIdx.x / p.blocks_per_set;
+  const int chunk = (int)(blockIdx.x - set * p.blocks_per_set);
+  const int q = (int)(set % p.n_q);
+  const int s = (int)((set / p.n_q) % p.n_slots);
+  const int64_t b = set / ((int64_t)p.n_q * p.n_slots);
+  if (!BLUE) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_acc; i += stride)
+      p.zero_acc[i] = 0;
+  }
+  const uint32_t *T = th.v[s];
+  const bool has_zero = p.t_has_zero != 0;
+  const int L = p.L, plane = p.plane, G = p.seg_sites;
+  const uint32_t Lt = (uint32_t)p.Lt, P = (uint32_t)plane;
+  const int64_t gq = (int64_t)chunk * kBlock4 + threadIdx.x;
+  const bool live = gq < (int64_t)plane * p.n_seg;
+  const int i2 = (int)(gq % plane);
+  const int seg = (int)(gq / plane);
+  const int y = i2 / L, x = i2 - y * L;
+  const int ixp = (x + 1 == L ? 0 : x + 1) + L * y, ixm = (x == 0 ? L - 1 : x - 1) + L * y;
+  const int iyp = x + L * (y + 1 == L ? 0 : y + 1), iym = x + L * (y == 0 ? L - 1 : y - 1);
+  const uint4 *src = reinterpret_cast<const uint4 *>(p.spins) + ((b * p.n_slots + s) * p.n_q + q) * p.N;
+  const uint4 *pc = src + i2, *pxp = src + ixp, *pxm = src + ixm, *pyp = src + iyp, *pym = src + iym;
+  uint4 *wc = reinterpret_cast<uint4 *>(p.spins) + ((b * p.n_slots + s) * p.n_q + q) * p.N + i2;
+  const uint32_t *Jb = p.J + b * (int64_t)plane * 2;
+  uint32_t Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
+  const uint32_t tau0 = 2u * (uint32_t)G * (uint32_t)seg + (uint32_t)((colour + x + y) & 1);
+  const unsigned long long t = *p.d_t;
+  const uint32_t ctr_z = (uint32_t)s | ((uint32_t)q << 16);
+  const uint32_t ctr_w = (DOM_SWEEP << 28) | (uint32_t)((b * 32) >> 6);
+
+  VCount<uint32_t, KS> cs[4];
+  VCount<uint32_t, KT> ct[4];
+  if (BLUE)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      cs[j].zero();
+      ct[j].zero();
+    }
+
+  if (live) {
+    Jxp = Jb[2 * i2];
+    Jxm = Jb[2 * ixm];
+    Jyp = Jb[2 * i2 + 1];
+    Jym = Jb[2 * iym + 1];
+    uint32_t off = tau0 * P;
+    uint4 dn = pc[(size_t)(tau0 == 0 ? (Lt - 1) * P : off - P)];
+    Quad4 cur;
+    cur.c = pc[off];
+    cur.up = pc[(size_t)(tau0 + 1 == Lt ? 0u : off + P)];
+    cur.xp = pxp[off];
+    cur.xm = pxm[off];
+    cur.yp = pyp[off];
+    cur.ym = pym[off];
+    for (int k = 0; k < G; ++k) {
+      const uint32_t tau = tau0 + 2u * (uint32_t)k;
+      Quad4 nxt;
+      if (k + 1 < G) {
+        const uint32_t offn = off + 2 * P;
+        nxt.c = pc[offn];
+        nxt.up = pc[(size_t)(tau + 3 == Lt ? 0u : offn + P)];
+        nxt.xp = pxp[offn];
+        nxt.xm = pxm[offn];
+        nxt.yp = pyp[offn];
+        nxt.ym = pym[offn];
+      }
+      const uint4 R4 = philox(make_uint4((uint32_t)i2 + off, (uint32_t)t, ctr_z, ctr_w), p.key);
+      uint32_t f[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t sc = q4(cur.c, j);
+        const uint32_t b1 = sc ^ q4(cur.xp, j) ^ Jxp;
+        const uint32_t b2 = sc ^ q4(cur.xm, j) ^ Jxm;
+        const uint32_t b3 = sc ^ q4(cur.yp, j) ^ Jyp;
+        const uint32_t b4 = sc ^ q4(cur.ym, j) ^ Jym;
+        const uint32_t t1 = sc ^ q4(cur.up, j);
+        const uint32_t t2 = sc ^ q4(dn, j);
+        const uint32_t s1 = b1 ^ b2 ^ b3;
+        const uint32_t c1 = maj3(b1, b2, b3);
+        const uint32_t us0 = s1 ^ b4;
+        const uint32_t c2 = s1 & b4;
+        const uint32_t us1 = c1 ^ c2;
+        const uint32_t us2 = c1 & c2;
+        const uint32_t ut0 = t1 ^ t2;
+        const uint32_t ut1 = t1 & t2;
+        const uint32_t R = q4(R4, j);
+        uint32_t flip;
+        if (count_only)
+          flip = 0;
+        else if (!has_zero)
+          flip = ~reject_mask<false>(R, T, us0, us1, us2, ut0, ut1);
+        else
+          flip = ~reject_mask<true>(R, T, us0, us1, us2, ut0, ut1);
+        f[j] = flip;
+        if (BLUE) {
+          // unsatisfied counts after the flip: u -> 4 - u (spatial), 2 - u (tau)
+          const uint32_t vs1 = us1 ^ (flip & us0);
+          const uint32_t vs2 = mux(flip, ~(us0 | us1 | us2), us2);
+          const uint32_t vt1 = mux(flip, ~(ut0 | ut1), ut1);
+          cs[j].add3(us0, vs1, vs2);
+          ct[j].add2(ut0, vt1);
+        }
+      }
+      if (!count_only) wc[off] = make_uint4(cur.c.x ^ f[0], cur.c.y ^ f[1], cur.c.z ^ f[2], cur.c.w ^ f[3]);
+      if (k + 1 < G) {
+        dn = cur.up;
+        cur = nxt;
+        off += 2 * P;
+      }
+    }
+  }
+
+  if (BLUE) {
+    block_sum_counters<KS, 4>(cs, buf, tot);
+    block_sum_counters<KT, 4>(ct, buf, tot + 4 * 32);
+    {
+      const int w = threadIdx.x;   // 128 = 4 replicas x 32 lanes
+      const int jj = w >> 5, lane = w & 31;
+      const int rr = 4 * q + jj;
+      const int64_t a = b * 32 + lane;
+      if (rr < p.n_rep) {
+        unsigned long long *u = p.U + ((a * p.n_rep + rr) * p.n_slots + s) * 2;
+        if (tot[w]) atomicAdd(u, (unsigned long long)tot[w]);
+        if (tot[4 * 32 + w]) atomicAdd(u + 1, (unsigned long long)tot[4 * 32 + w]);
+      }
     }
   }
 }
@@ -495,8 +741,65 @@ void launch_sweep_g(const SamplesArgs<Word> &p, unsigned blocks, size_t smem, cu
   }
 }
 
+// W = 32 kernel: one thread per column segment of G sites (G = the tile,
+// or by default as many as keep about half the old kernel's thread count).
+SamplesArgs<uint32_t> make_args4(qisg_handle *h, SlotThresholds &th) {
+  SamplesArgs<uint32_t> p = make_args<uint32_t>(h);
+  const int half_col = h->Lt / 2;
+  const int64_t sets = h->n_b * h->n_slots * h->n_q;
+  const int64_t want_threads = (int64_t)h->sweep_min_blocks_per_sm * std::max(1, h->n_sm) * kBlock / 2;
+  int G = h->sweep_groups_per_quad > 0 ? h->sweep_groups_per_quad : 64;
+  if (h->sweep_groups_per_quad <= 0)
+    while (G > 1 && sets * p.plane * (int64_t)(half_col / std::min(G, half_col)) < want_threads) G >>= 1;
+  if (G > half_col) G = half_col;
+  while (G > 1 && half_col % G) --G;
+  p.seg_sites = G;
+  p.n_seg = half_col / G;
+  p.blocks_per_set = (int)(((int64_t)p.plane * p.n_seg + kBlock4 - 1) / kBlock4);
+  std::memset(&th, 0, sizeof(th));
+  static const int cls[9] = {0, 3, 6, 9, 12, 1, 4, 2, 5};   // us * 3 + ut of the 9 classes
+  for (int sl = 0; sl < h->n_slots; ++sl)
+    for (int c = 0; c < 9; ++c) {
+      const uint32_t T = h->T[(size_t)sl * 15 + cls[c]];
+      th.v[sl][c] = p.t_has_zero ? T : (T == 0xFFFFFFFFu ? T : T - 1u);
+    }
+  return p;
+}
+
+template <bool BLUE>
+void launch_sweep4(const SamplesArgs<uint32_t> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
+                   int colour, int count_only) {
+  if constexpr (!BLUE) {   // the red pass keeps no counters
+    samples_sweep4_kernel<false, 0><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only);
+  } else {
+    int g2 = 0;
+    while ((4 << g2) < p.seg_sites) ++g2;
+    switch (g2) {
+#define QISG_CASE(n) \
+  case n: samples_sweep4_kernel<true, n><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only); break;
+      QISG_CASE(0) QISG_CASE(1) QISG_CASE(2) QISG_CASE(3) QISG_CASE(4)
+      default: samples_sweep4_kernel<true, 5><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only); break;
+#undef QISG_CASE
+    }
+  }
+}
+
 template <typename Word>
 int half_sweep_t(qisg_handle *h, int colour, int count_only) {
+  if (sizeof(Word) == 4) {
+    SlotThresholds th;
+    SamplesArgs<uint32_t> p = make_args4(h, th);
+    const int64_t blocks = h->n_b * h->n_slots * h->n_q * p.blocks_per_set;
+    if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+    const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
+    if (colour == 1)
+      launch_sweep4<true>(p, th, (unsigned)blocks, h->stream, 1, count_only);
+    else
+      launch_sweep4<false>(p, th, (unsigned)blocks, h->stream, 0, count_only);
+    prof_end(h, QISG_KERNEL_SWEEP, tok);
+    h->launches++;
+    return cuda_check(cudaGetLastError(), "samples half sweep");
+  }
   SamplesArgs<Word> p = make_args<Word>(h);
   const int64_t sets = h->n_b * h->n_slots * h->n_q;
   const int64_t blocks = sets * p.blocks_per_set;

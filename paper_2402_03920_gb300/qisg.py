@@ -18,6 +18,7 @@ from . import _build_lib
 
 QISG_LAYOUT_AUTO, QISG_LAYOUT_LANES, QISG_LAYOUT_SAMPLES = 0, 1, 2
 KERNEL_SWEEP, KERNEL_PT, KERNEL_MEASURE, KERNEL_PERMUTE = 0, 1, 2, 3
+PROFILE_ONLY = 0x100
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ECORRUPT", -6: "ESTATE"}
 
 
@@ -295,8 +296,17 @@ class Instance:
         _check(load().qisg_autotune(self._h, sweeps_per_candidate, ctypes.byref(g)))
         return g.value
 
-    def profile(self, enable: bool):
-        _check(load().qisg_profile(self._h, 1 if enable else 0))
+    def profile(self, enable: bool, kinds=None):
+        """Time launches with event pairs; `kinds` limits it to those kernel kinds."""
+        if not enable:
+            code = 0
+        elif kinds is None:
+            code = 1
+        else:
+            code = PROFILE_ONLY
+            for k in kinds:
+                code |= 1 << int(k)
+        _check(load().qisg_profile(self._h, code))
 
     def profile_read(self, kind: int):
         """(total ms, launches timed, launches) of one kernel kind."""
