@@ -54,7 +54,13 @@ def parse():
     p.add_argument("--extras", default="uneven,large,serving",
                    help="other workloads measured beside the headline (empty: none)")
     p.add_argument("--serving-requests", type=int, default=100)
+    p.add_argument("--tiles", default="",
+                   help="pin the sweep schedule 'red,blue,prefetch_red,prefetch_blue' instead of autotuning")
     return p.parse_args()
+
+
+TILES = None    # pinned sweep schedule (from --tiles), else autotuned
+TUNED = {}      # form -> schedule used
 
 
 def dist_env():
@@ -195,6 +201,15 @@ def time_form(torch, qisg, w, form, steps, warmup, seed):
     for the work before it, so these passes run slower than the plain one."""
     inst = make_instance(qisg, w, form, seed)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    # untimed: pick the sweep tiles on the live state (results do not depend
+    # on them), then realign to the graph cycle of measure_every sweeps
+    if TILES is None:
+        inst.autotune(3)
+    else:
+        inst.set_tiles(TILES[:2], TILES[2:])
+    cyc = max(1, w.measure_every)
+    inst.sweep((cyc - inst.sweep_count() % cyc) % cyc)
+    TUNED[form] = inst.tiles()
     for _ in range(warmup):
         inst.sweep(SWEEPS_PER_STEP)
     inst.sync()
@@ -465,6 +480,9 @@ def run_gpu(args):
                    "measure_every": w.measure_every, "form": main,
                    "layout": "SAMPLES" if layout == qisg.QISG_LAYOUT_SAMPLES else "LANES",
                    "word_bits": wb,
+                   "sweep_schedule": {"tiles": list(TUNED.get(main, ((0, 0), (1, 1)))[0]),
+                                      "prefetch": list(TUNED.get(main, ((0, 0), (1, 1)))[1]),
+                                      "how": "pinned" if TILES else "autotuned (untimed)"},
                    "l2": "flushed between steps (2x L2 buffer written); lattice fits in L2 within a step"},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -532,7 +550,12 @@ def run_reference(args):
 
 
 def main():
+    global TILES
     args = parse()
+    if args.tiles:
+        TILES = [int(v) for v in args.tiles.split(",")]
+        if len(TILES) != 4:
+            raise SystemExit("--tiles wants red,blue,prefetch_red,prefetch_blue")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -219,13 +219,25 @@ int qisg_profile_read(qisg_handle *h, int kind, double *total_ms, int64_t *n_tim
  * the same either way. */
 int qisg_set_graphs(qisg_handle *h, int enable);
 
-/* Choose the SAMPLES sweep tile (site groups per thread quad) by timing
- * sweeps_per_candidate real sweeps with each candidate on the handle's own
- * state; the fastest is kept.  The simulation advances by
- * 7 * (1 + sweeps_per_candidate) sweeps meanwhile (results never depend on
- * the tile, so the trajectory is the one an untuned run would follow).  chosen:
- * the tile kept (0 for LANES, which has nothing to tune).  Synchronises. */
+/* Choose the SAMPLES sweep tiles (sites per thread along tau for 32-bit
+ * words, site groups of 4 per thread quad for 64-bit words; 1, 2, ..., 64)
+ * and, for 32-bit words, whether each pass prefetches the next site, by
+ * timing sweeps_per_candidate real sweeps per candidate on the handle's own
+ * state; the red and blue passes are timed and tuned separately.  The
+ * simulation advances by C * (1 + sweeps_per_candidate) sweeps meanwhile,
+ * C = 14 candidates for 32-bit words and 7 for 64-bit words (results never
+ * depend on the tile, so the trajectory is the one an untuned run would
+ * follow).  chosen: the blue pass's tile (0 for LANES, which has nothing to
+ * tune).  Synchronises. */
 int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen);
+
+/* Read or pin the SAMPLES sweep schedule: tile[c] and prefetch[c] of the red
+ * (c = 0) and blue (c = 1) pass, as qisg_autotune chooses them (tile 0 = the
+ * default choice; prefetch is 0 or 1 and only matters for 32-bit words).
+ * Results never depend on the schedule.  EINVAL: tile outside 0..64 or not
+ * a power of two. */
+int qisg_get_tiles(qisg_handle *h, int tile[2], int prefetch[2]);
+int qisg_set_tiles(qisg_handle *h, const int tile[2], const int prefetch[2]);
 
 /* Block until the handle's stream is idle; reports any device error flag. */
 int qisg_sync(qisg_handle *h);

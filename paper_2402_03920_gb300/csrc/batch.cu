@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(kBatchBlock) batch_kernel(InstDev *insts, int 
       const ChainRef cr = chains[c];
       const InstDev &I = insts[cr.inst];
       if (!live(I)) continue;
-      pt_chain<false, true>(I.walker + cr.r * I.n_slots, I.U + (size_t)cr.r * I.n_slots * 2, *I.ptc, I.sq, I.key,
-                            (uint32_t)__ldcg(&I.t), 0, cr.r, I.n_slots);
+      pt_chain<false, true, true>(I.walker + cr.r * I.n_slots, I.U + (size_t)cr.r * I.n_slots * 2, I.ptc, I.sq,
+                                  I.key, (uint32_t)__ldcg(&I.t), 0, cr.r, I.n_slots);
     }
     if (!grid_sync(bar, err)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inst; i += gridDim.x * blockDim.x) {

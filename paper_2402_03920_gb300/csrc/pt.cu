@@ -19,45 +19,42 @@ namespace qisg {
 namespace {
 
 // LANES: one warp per chain, chains in (a, r) order.
+template <bool WIDE>
 __global__ void pt_lanes_kernel(int32_t *walker, unsigned long long *U, const PTConst *ptc, const double *sq,
                                 const unsigned long long *d_t, uint2 key, int64_t a0, int64_t n_chains,
                                 int n_rep, int n_slots, int explicit_pass) {
-  __shared__ PTConst pc;
-  load_ptconst(&pc, ptc);
-  __syncthreads();
   const int64_t chain = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (chain >= n_chains) return;   // whole warp
   const int64_t a = a0 + chain / n_rep;
   const int r = (int)(chain % n_rep);
   const uint32_t t = (uint32_t)(explicit_pass ? *d_t - 1ull : *d_t);
-  pt_chain<false, false>(walker + (a * n_rep + r) * n_slots, U + (a * n_rep + r) * n_slots * 2, pc, sq, key, t, a,
-                  r, n_slots);
+  pt_chain<false, false, WIDE>(walker + (a * n_rep + r) * n_slots, U + (a * n_rep + r) * n_slots * 2, ptc, sq, key,
+                               t, a, r, n_slots);
 }
 
 // SAMPLES: block = 8 warps = samples b*W + 8*o + v (v = warp) of replica r;
 // the block then ORs the 8 accept bitmasks into the lane masks acc[b][r][s]
 // (cleared by the red pass of the sweep), one thread per pair.
-template <typename Word>
+template <typename Word, bool WIDE>
 __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsigned long long *U, Word *accw,
                                                          const PTConst *ptc, const double *sq,
                                                          const unsigned long long *d_t, uint2 key,
                                                          int64_t n_samples, int n_rep, int n_slots,
                                                          int explicit_pass) {
   constexpr int W = (int)sizeof(Word) * 8, octs = W / 8;
-  __shared__ PTConst pc;
   __shared__ uint32_t bits[8];
-  load_ptconst(&pc, ptc);
-  __syncthreads();
-  const int o = (int)(blockIdx.x % octs);
-  const int r = (int)((blockIdx.x / octs) % n_rep);
-  const int64_t b = blockIdx.x / ((int64_t)octs * n_rep);
+  const uint32_t bid = blockIdx.x;
+  const int o = (int)(bid % octs);
+  const uint32_t rest = bid / octs;
+  const uint32_t b = rest / (uint32_t)n_rep;
+  const int r = (int)(rest - b * (uint32_t)n_rep);
   const int v = threadIdx.x >> 5;
-  const int64_t a = b * W + 8 * o + v;
+  const int64_t a = (int64_t)b * W + 8 * o + v;
   uint32_t acc = 0;
   if (a < n_samples) {
     const uint32_t t = (uint32_t)(explicit_pass ? *d_t - 1ull : *d_t);
-    acc = pt_chain<true, false>(walker + (a * n_rep + r) * n_slots, U + (a * n_rep + r) * n_slots * 2, pc, sq, key,
-                         t, a, r, n_slots);
+    acc = pt_chain<true, false, WIDE>(walker + (a * n_rep + r) * n_slots, U + (a * n_rep + r) * n_slots * 2, ptc,
+                                      sq, key, t, a, r, n_slots);
   }
   if ((threadIdx.x & 31) == 0) bits[v] = acc;
   __syncthreads();
@@ -67,7 +64,7 @@ __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsign
 #pragma unroll
     for (int u = 0; u < 8; ++u) m |= (Word)((bits[u] >> s) & 1u) << (8 * o + u);
     if (m) {
-      Word *out = accw + (b * n_rep + r) * n_slots;
+      Word *out = accw + ((int64_t)b * n_rep + r) * n_slots;
       if (sizeof(Word) == 8)
         atomicOr(reinterpret_cast<unsigned long long *>(&out[s]), (unsigned long long)m);
       else
@@ -76,29 +73,39 @@ __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsign
   }
 }
 
+template <typename Word, bool WIDE>
+void launch_pt_samples(qisg_handle *h, uint2 key, int explicit_pass) {
+  const unsigned blocks = (unsigned)(h->n_b * h->n_rep * (h->W / 8));
+  pt_samples_kernel<Word, WIDE><<<blocks, 256, 0, h->stream>>>(
+      h->d_walker, h->d_U, reinterpret_cast<Word *>(h->d_acc), reinterpret_cast<const PTConst *>(h->d_ptc),
+      h->d_sq, h->d_t, key, h->n_samples, h->n_rep, h->n_slots, explicit_pass);
+}
+
 }  // namespace
 
 int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a) {
   const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  const bool wide = 2 * h->N >= (int64_t(1) << 30);   // energy differences beyond 31 bits
   const int tok = prof_begin(h, QISG_KERNEL_PT);
   if (h->layout == QISG_LAYOUT_SAMPLES) {
-    const unsigned blocks = (unsigned)(h->n_b * h->n_rep * (h->W / 8));
-    if (h->W == 64)
-      pt_samples_kernel<unsigned long long><<<blocks, 256, 0, h->stream>>>(
-          h->d_walker, h->d_U, reinterpret_cast<unsigned long long *>(h->d_acc),
-          reinterpret_cast<const PTConst *>(h->d_ptc), h->d_sq, h->d_t, key, h->n_samples, h->n_rep,
-          h->n_slots, explicit_pass);
-    else
-      pt_samples_kernel<unsigned int><<<blocks, 256, 0, h->stream>>>(
-          h->d_walker, h->d_U, reinterpret_cast<unsigned int *>(h->d_acc),
-          reinterpret_cast<const PTConst *>(h->d_ptc), h->d_sq, h->d_t, key, h->n_samples, h->n_rep,
-          h->n_slots, explicit_pass);
+    if (h->W == 64) {
+      if (wide) launch_pt_samples<unsigned long long, true>(h, key, explicit_pass);
+      else launch_pt_samples<unsigned long long, false>(h, key, explicit_pass);
+    } else {
+      if (wide) launch_pt_samples<unsigned int, true>(h, key, explicit_pass);
+      else launch_pt_samples<unsigned int, false>(h, key, explicit_pass);
+    }
   } else {
     const int64_t n_chains = n_a * h->n_rep;
     constexpr int kWarps = 4;
-    pt_lanes_kernel<<<(unsigned)((n_chains + kWarps - 1) / kWarps), 32 * kWarps, 0, h->stream>>>(
-        h->d_walker, h->d_U, reinterpret_cast<const PTConst *>(h->d_ptc), h->d_sq, h->d_t, key, a0, n_chains,
-        h->n_rep, h->n_slots, explicit_pass);
+    const unsigned blocks = (unsigned)((n_chains + kWarps - 1) / kWarps);
+    const PTConst *ptc = reinterpret_cast<const PTConst *>(h->d_ptc);
+    if (wide)
+      pt_lanes_kernel<true><<<blocks, 32 * kWarps, 0, h->stream>>>(h->d_walker, h->d_U, ptc, h->d_sq, h->d_t, key, a0,
+                                                                   n_chains, h->n_rep, h->n_slots, explicit_pass);
+    else
+      pt_lanes_kernel<false><<<blocks, 32 * kWarps, 0, h->stream>>>(h->d_walker, h->d_U, ptc, h->d_sq, h->d_t, key,
+                                                                    a0, n_chains, h->n_rep, h->n_slots, explicit_pass);
   }
   prof_end(h, QISG_KERNEL_PT, tok);
   h->launches++;

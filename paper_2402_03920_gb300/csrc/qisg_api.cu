@@ -369,11 +369,17 @@ namespace {
 
 // One sweep t = h->t, enqueued on h->stream: red, blue (+ energies), PT when
 // due, measurement when due, advance of the device counter.
-int one_sweep(qisg_handle *h) {
+// One sweep (Sec. 2.1): red, blue, PT pass when due, measurement when due.
+// ev: optional events recorded before the red pass, between the passes and
+// after the blue pass (autotuning).
+int one_sweep(qisg_handle *h, cudaEvent_t *ev = nullptr) {
   const bool lanes = h->layout == QISG_LAYOUT_LANES;
   const uint64_t t = h->t;
-  int rc = lanes ? lanes_half_sweep(h, 0, 0) : samples_half_sweep(h, 0, 0);
+  int rc = ev ? cuda_check(cudaEventRecord(ev[0], h->stream), "record") : QISG_OK;
+  if (!rc) rc = lanes ? lanes_half_sweep(h, 0, 0) : samples_half_sweep(h, 0, 0);
+  if (!rc && ev) rc = cuda_check(cudaEventRecord(ev[1], h->stream), "record");
   if (!rc) rc = lanes ? lanes_half_sweep(h, 1, 0) : samples_half_sweep(h, 1, 0);
+  if (!rc && ev) rc = cuda_check(cudaEventRecord(ev[2], h->stream), "record");
   bool advanced = false;
   if (!rc && h->pt_every > 0 && (t + 1) % (uint64_t)h->pt_every == 0) {
     if (lanes) {
@@ -577,34 +583,71 @@ int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
     if (chosen) *chosen = 0;
     return QISG_OK;
   }
-  int best = 0;
-  float best_ms = 0.f;
-  cudaEvent_t e0, e1;
-  int rc = cuda_check(cudaEventCreate(&e0), "event");
-  if (!rc) rc = cuda_check(cudaEventCreate(&e1), "event");
+  // candidates: tiles 1, 2, ..., 64, and for W = 32 each with and without the
+  // prefetch; the red and blue passes are timed apart and tuned apart
+  const int n_tiles = 7, n_cand = h->W == 32 ? 2 * n_tiles : n_tiles;
+  float best_ms[2] = {0.f, 0.f};
+  int best[2] = {0, 0};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  int rc = QISG_OK;
+  for (int i = 0; i < 3 && !rc; ++i) rc = cuda_check(cudaEventCreate(&ev[i]), "event");
   const bool graphs = h->use_graphs;
   h->use_graphs = false;
-  for (int g = 1; g <= 64 && !rc; g <<= 1) {
-    h->sweep_groups_per_quad = g;
+  for (int c = 0; c < n_cand && !rc; ++c) {
+    const int tile = 1 << (c % n_tiles), nopf = c / n_tiles;
+    h->sweep_tile[0] = h->sweep_tile[1] = tile;
+    h->sweep_nopf[0] = h->sweep_nopf[1] = nopf;
     rc = one_sweep(h);   // warm the candidate
-    if (!rc) rc = cuda_check(cudaEventRecord(e0, h->stream), "record");
-    for (int i = 0; i < sweeps_per_candidate && !rc; ++i) rc = one_sweep(h);
-    if (!rc) rc = cuda_check(cudaEventRecord(e1, h->stream), "record");
-    if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "sync");
-    float ms = 0.f;
-    if (!rc) rc = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
-    if (!rc && (best == 0 || ms < best_ms)) {
-      best = g;
-      best_ms = ms;
+    float ms[2] = {0.f, 0.f};
+    for (int i = 0; i < sweeps_per_candidate && !rc; ++i) {
+      rc = one_sweep(h, ev);
+      if (!rc) rc = cuda_check(cudaEventSynchronize(ev[2]), "sync");
+      float a = 0.f, b = 0.f;
+      if (!rc) rc = cuda_check(cudaEventElapsedTime(&a, ev[0], ev[1]), "elapsed");
+      if (!rc) rc = cuda_check(cudaEventElapsedTime(&b, ev[1], ev[2]), "elapsed");
+      ms[0] += a;
+      ms[1] += b;
     }
+    for (int col = 0; col < 2 && !rc; ++col)
+      if (best[col] == 0 || ms[col] < best_ms[col]) {
+        best[col] = c + 1;
+        best_ms[col] = ms[col];
+      }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (int i = 0; i < 3; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
   h->use_graphs = graphs;
   if (rc) return rc;
-  h->sweep_groups_per_quad = best;
+  for (int col = 0; col < 2; ++col) {
+    h->sweep_tile[col] = 1 << ((best[col] - 1) % n_tiles);
+    h->sweep_nopf[col] = (best[col] - 1) / n_tiles;
+  }
   drop_cycle(h);
-  if (chosen) *chosen = best;
+  if (chosen) *chosen = h->sweep_tile[1];
+  return QISG_OK;
+}
+
+int qisg_get_tiles(qisg_handle *h, int tile[2], int prefetch[2]) {
+  if (!h || !tile || !prefetch) return fail(QISG_EINVAL, "NULL argument");
+  for (int c = 0; c < 2; ++c) {
+    tile[c] = h->sweep_tile[c];
+    prefetch[c] = h->sweep_nopf[c] ? 0 : 1;
+  }
+  return QISG_OK;
+}
+
+int qisg_set_tiles(qisg_handle *h, const int tile[2], const int prefetch[2]) {
+  if (!h || !tile || !prefetch) return fail(QISG_EINVAL, "NULL argument");
+  for (int c = 0; c < 2; ++c)
+    if (tile[c] < 0 || tile[c] > 64 || (tile[c] & (tile[c] - 1)) || (prefetch[c] != 0 && prefetch[c] != 1))
+      return fail(QISG_EINVAL, "tile must be 0 or a power of two up to 64, prefetch 0 or 1");
+  int rc = sync_handle(h);
+  if (rc) return rc;
+  for (int c = 0; c < 2; ++c) {
+    h->sweep_tile[c] = tile[c];
+    h->sweep_nopf[c] = prefetch[c] ? 0 : 1;
+  }
+  drop_cycle(h);
   return QISG_OK;
 }
 

@@ -84,8 +84,8 @@ struct FastDiv {
 // Maximum ladder length of the register-resident PT scan.
 constexpr int kMaxSlotsPT = 32;
 
-// Per-pair constants of the PT shortcut, staged in shared memory by the PT
-// kernels: dk = k_s - k_{s+1} and dkt = k_tau,s - k_tau,s+1 rounded to float,
+// Per-pair constants of the PT shortcut, read by lane s of a chain's warp:
+// dk = k_s - k_{s+1} and dkt = k_tau,s - k_tau,s+1 rounded to float,
 // and ge1[w] bit s set when base w (alpha+, alpha-, beta+, beta-) of pair s
 // is >= 1.
 struct PTConst {
@@ -122,105 +122,105 @@ static __device__ __noinline__ bool pt_exact(const double *sq, int s, int ia, in
   return u < P;
 }
 
-__device__ __forceinline__ bool pt_decide(const PTConst &c, const double *sq, int s, long long m,
-                                          long long n, uint32_t x, float lnu) {
-  const int ia = m >= 0 ? 0 : 1, ib = n >= 0 ? 2 : 3;
-  if ((m == 0 || ((c.ge1[ia] >> s) & 1u)) && (n == 0 || ((c.ge1[ib] >> s) & 1u))) return true;
-  if (x != 0u) {
-    const float la = (float)m * c.dkf[s];
-    const float lb = (float)n * c.dktf[s];
-    if (fabsf(la) < 700.f && fabsf(lb) < 700.f) {
-      const float d = lnu - (la + lb);
-      const float err = 1e-4f + (fabsf(la) + fabsf(lb)) * 4.8e-7f;
-      if (d < -err) return true;
-      if (d > err) return false;
-    }
-  }
-  return pt_exact(sq, s, ia, ib, m, n, x);
-}
-
-// One PT pass of chain (a, r) over slot energies held by slot: us[s], ut[s]
-// are the unsatisfied spatial / tau bond counts of the configuration at slot
-// s (A = 2N - 2 us, B = N - 2 ut, so m = -2 (us_Y - us_X)).  Pairs are taken
-// in increasing s; an accepted pair swaps the entries of s and s+1 and sets
-// bit s of the returned mask.  The Philox words of all pairs and their
-// logarithms do not depend on the decisions and are computed up front.
-// The loops are kept rolled: the kernels that run this are a few warps
-// long, and an unrolled scan does not fit the instruction cache.
-__device__ __forceinline__ uint32_t pt_scan(int n_slots, long long *us, long long *ut, const PTConst &c,
-                                            const double *sq, uint2 key, uint32_t t, uint32_t a, int r) {
-  uint32_t xs[kMaxSlotsPT];
-  float lnu[kMaxSlotsPT];
-#pragma unroll 1
-  for (int s = 0; s + 1 < n_slots; ++s) {
-    xs[s] = pick4(philox(make_uint4((uint32_t)s, t, a, (DOM_PT << 28) | (uint32_t)(r >> 2)), key), r & 3);
-    lnu[s] = __logf((float)xs[s]) - 22.18070977791825f;
-  }
-  uint32_t acc = 0;
-#pragma unroll 1
-  for (int s = 0; s + 1 < n_slots; ++s) {
-      const long long m = -2 * (us[s + 1] - us[s]);
-      const long long n = -2 * (ut[s + 1] - ut[s]);
-      if (pt_decide(c, sq, s, m, n, xs[s], lnu[s])) {
-        const long long a1 = us[s], a2 = ut[s];
-        us[s] = us[s + 1];
-        ut[s] = ut[s + 1];
-        us[s + 1] = a1;
-        ut[s + 1] = a2;
-        acc |= 1u << s;
-      }
-  }
-  return acc;
-}
-
 // PT pass of one chain by one warp (Sec. 2.1).  Lane s holds the walker and
-// energies of the configuration at slot s and draws the Philox word of pair
-// (s, s+1).  In the sequential pass the configuration that meets the original
-// occupant of slot s+1 at pair s is always one of the original occupants of
-// slots 0..s (it was carried up by accepted exchanges).  So lane s first
-// evaluates the rule for pair s against every candidate 0..s (independent
-// evaluations, bit i of D = accept with candidate i); the pass itself is then
-// a uniform loop of bit lookups: carried c, accept e = bit c of D_s; if e the
-// slot ends with s+1's configuration and c moves on, else it ends with c and
-// s+1 is carried.  Same decisions as the textbook pass, without its serial
-// dependency through the energies.
+// energies of the configuration at slot s, the constants of pair (s, s+1)
+// and that pair's Philox word.  In the sequential pass the configuration
+// that meets the original occupant of slot s+1 at pair s is always one of
+// the original occupants of slots 0..s (carried up by accepted exchanges).
+// So lane s first decides pair s against every candidate i = 0..s (bit i of
+// D: accept), with the shortcuts above and the exact rule for the few
+// candidates the shortcuts leave open; the pass is then a uniform scan of
+// bit lookups: with c carried, pair s accepts iff bit c of D_s; the slot then
+// ends with s+1's configuration and c moves on, else it ends with c and s+1
+// is carried.  The decisions are those of the textbook pass.
 // BY_SLOT: energies indexed by slot (else by walker).  CG: read the mutable
-// state through L2 only (persistent kernel).  Returns the accepted-pair
-// bitmask (same in every lane).
-template <bool BY_SLOT, bool CG>
-__device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua, const PTConst &pc,
+// state through L2 only (persistent kernel).  WIDE: energies may need more
+// than 30 bits (2N >= 2^30); otherwise differences are taken in 32 bits.
+// Returns the accepted-pair bitmask (same in every lane).
+template <bool CG>
+__device__ __forceinline__ long long ld_energy(const unsigned long long *p) {
+  return (long long)(CG ? __ldcg(p) : *p);
+}
+
+template <bool WIDE>
+struct PTEnergy {
+  using T = long long;
+  __device__ static __forceinline__ T shfl(T v, int src) {
+    const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src);
+    const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)((unsigned long long)v >> 32), src);
+    return (T)(((unsigned long long)hi << 32) | lo);
+  }
+  __device__ static __forceinline__ T diff2(T x, T y) { return 2 * (x - y); }
+};
+template <>
+struct PTEnergy<false> {
+  using T = uint32_t;
+  __device__ static __forceinline__ T shfl(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+  __device__ static __forceinline__ int diff2(T x, T y) { return 2 * (int)(x - y); }
+};
+
+template <bool BY_SLOT, bool CG, bool WIDE>
+__device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua, const PTConst *pc,
                                              const double *sq, uint2 key, uint32_t t, int64_t a, int r,
                                              int n_slots) {
+  using E = PTEnergy<WIDE>;
+  using ET = typename E::T;
   const int lane = threadIdx.x & 31;
+  const bool has_pair = lane + 1 < n_slots;
   int w = 0;
-  long long us = 0, ut = 0;
+  ET us = 0, ut = 0;
   if (lane < n_slots) {
     w = CG ? __ldcg(wa + lane) : wa[lane];
     const int e = BY_SLOT ? lane : w;
-    us = (long long)(CG ? __ldcg(Ua + 2 * e) : Ua[2 * e]);
-    ut = (long long)(CG ? __ldcg(Ua + 2 * e + 1) : Ua[2 * e + 1]);
+    us = (ET)ld_energy<CG>(Ua + 2 * e);
+    ut = (ET)ld_energy<CG>(Ua + 2 * e + 1);
   }
-  uint32_t x = 0;
-  float lnu = 0.f;
-  if (lane + 1 < n_slots) {
+  float dk = 0.f, dkt = 0.f, lnu = 0.f;
+  uint32_t g = 0, x = 0;
+  if (has_pair) {
+    dk = pc->dkf[lane];
+    dkt = pc->dktf[lane];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) g |= ((pc->ge1[k] >> lane) & 1u) << k;
     x = pick4(philox(make_uint4((uint32_t)lane, t, (uint32_t)a, (DOM_PT << 28) | (uint32_t)(r >> 2)), key), r & 3);
     lnu = __logf((float)x) - 22.18070977791825f;
   }
   // energies of the original occupant of slot s+1 (the Y of pair s)
-  const long long y_us = __shfl_down_sync(0xffffffffu, us, 1);
-  const long long y_ut = __shfl_down_sync(0xffffffffu, ut, 1);
-  uint32_t D = 0;
+  const ET y_us = E::shfl(us, (lane + 1) & 31);
+  const ET y_ut = E::shfl(ut, (lane + 1) & 31);
+  uint32_t D = 0, open = 0;
   for (int i = 0; i + 1 < n_slots; ++i) {
-    const long long x_us = __shfl_sync(0xffffffffu, us, i);
-    const long long x_ut = __shfl_sync(0xffffffffu, ut, i);
-    if (lane + 1 < n_slots && i <= lane) {
-      const long long m = -2 * (y_us - x_us);   // A = 2N - 2 us
-      const long long n = -2 * (y_ut - x_ut);   // B = N - 2 ut
-      if (pt_decide(pc, sq, lane, m, n, x, lnu)) D |= 1u << i;
+    const ET x_us = E::shfl(us, i);
+    const ET x_ut = E::shfl(ut, i);
+    if (has_pair && i <= lane) {
+      const auto m = E::diff2(x_us, y_us);   // A_Y - A_X, A = 2N - 2 us
+      const auto n = E::diff2(x_ut, y_ut);   // B_Y - B_X, B = N - 2 ut
+      // both chosen factors >= 1 (base >= 1 or exponent 0): P >= 1 > u
+      bool acc = (m == 0 || ((g >> (m > 0 ? 0 : 1)) & 1u)) && (n == 0 || ((g >> (n > 0 ? 2 : 3)) & 1u));
+      bool und = false;
+      if (!acc) {
+        const float la = (float)m * dk, lb = (float)n * dkt;
+        const bool ok = x != 0u && fabsf(la) < 700.f && fabsf(lb) < 700.f;
+        const float d = lnu - (la + lb);
+        const float err = 1e-4f + (fabsf(la) + fabsf(lb)) * 4.8e-7f;
+        acc = ok && d < -err;
+        und = !acc && !(ok && d > err);
+      }
+      D |= (uint32_t)acc << i;
+      open |= (uint32_t)und << i;
     }
   }
+  while (open) {   // exact rule for the candidates left open (rare)
+    const int i = __ffs(open) - 1;
+    open &= open - 1;
+    const int e = BY_SLOT ? i : (CG ? __ldcg(wa + i) : wa[i]);
+    const long long m = 2 * (ld_energy<CG>(Ua + 2 * e) - (long long)y_us);
+    const long long n = 2 * (ld_energy<CG>(Ua + 2 * e + 1) - (long long)y_ut);
+    if (pt_exact(sq, lane, m >= 0 ? 0 : 1, n >= 0 ? 2 : 3, m, n, x)) D |= 1u << i;
+  }
+  __syncwarp();
   uint32_t acc = 0;
-  int c = 0, mine = lane;   // carried candidate; final occupant index of this lane's slot
+  int c = 0, mine = lane;   // carried candidate; final occupant of this lane's slot
   for (int s2 = 0; s2 + 1 < n_slots; ++s2) {
     const uint32_t Ds = __shfl_sync(0xffffffffu, D, s2);
     const bool ex = (Ds >> c) & 1u;
@@ -232,8 +232,8 @@ __device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua
   }
   if (lane == n_slots - 1) mine = c;
   const int f_w = __shfl_sync(0xffffffffu, w, mine);
-  const long long f_us = __shfl_sync(0xffffffffu, us, mine);
-  const long long f_ut = __shfl_sync(0xffffffffu, ut, mine);
+  const ET f_us = E::shfl(us, mine);
+  const ET f_ut = E::shfl(ut, mine);
   if (lane < n_slots) {
     wa[lane] = f_w;
     if (BY_SLOT) {
@@ -375,13 +375,6 @@ __device__ __forceinline__ void flush_counter(const VCount<Word, K> &c, int *acc
   }
 }
 
-// Stage the PT constants of a handle in shared memory (call with all
-// threads of the block, followed by __syncthreads()).
-__device__ __forceinline__ void load_ptconst(PTConst *dst, const PTConst *src) {
-  const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
-  uint32_t *d = reinterpret_cast<uint32_t *>(dst);
-  for (int i = threadIdx.x; i < (int)(sizeof(PTConst) / 4); i += blockDim.x) d[i] = s[i];
-}
 
 // Sites of one colour: j in [0, N/2) -> site.  Each (y, tau) row holds L/2
 // sites of each colour (L even).
@@ -419,9 +412,13 @@ struct qisg_handle {
   int64_t launches = 0;
   int device = 0;
   int n_sm = 0;
-  // SAMPLES sweep tile: site groups (of 4) per quad, 0 = choose; the grid
-  // aims at sweep_min_blocks_per_sm blocks per SM
-  int sweep_groups_per_quad = 0;
+  // SAMPLES sweep tile per colour (red, blue): sites per thread along tau
+  // (W = 32) or site groups of 4 per thread quad (W = 64), 0 = choose; the
+  // default grid aims at sweep_min_blocks_per_sm blocks of 256 threads per
+  // SM.  sweep_nopf: W = 32 kernel without the next-site prefetch (fewer
+  // registers).  None of these change results.
+  int sweep_tile[2] = {0, 0};
+  int sweep_nopf[2] = {0, 0};
   int sweep_min_blocks_per_sm = 4;
 
   // host tables (FP64, built once)

@@ -41,6 +41,8 @@ struct SamplesArgs {
   int n_seg;             // (L_tau / 2) / G segments per column
   int blocks_per_set;    // blocks per (b, s, q) word set
   int t_has_zero;        // some threshold of the table is 0 (always reject)
+  // division by the invariants of the index decomposition (32-bit indices)
+  FastDiv fd_bps, fd_nq, fd_ns, fd_plane, fd_L;
   // cleared by the red pass (nothing reads them until the blue pass / PT):
   unsigned long long *zero_U;   // bond counters, n_zero_U words
   int64_t n_zero_U;
@@ -80,11 +82,13 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
   __shared__ uint32_t Ts[16];
   __shared__ int accU[BLUE ? 2 * 4 * 64 : 1];
 
-  const int64_t set = blockIdx.x / p.blocks_per_set;
-  const int chunk = (int)(blockIdx.x - set * p.blocks_per_set);
-  const int q = (int)(set % p.n_q);
-  const int s = (int)((set / p.n_q) % p.n_slots);
-  const int64_t b = set / ((int64_t)p.n_q * p.n_slots);
+  const uint32_t bid = blockIdx.x;
+  const uint32_t set = p.fd_bps.div(bid);
+  const uint32_t chunk = bid - set * (uint32_t)p.blocks_per_set;
+  const uint32_t bs = p.fd_nq.div(set);
+  const int q = (int)(set - bs * (uint32_t)p.n_q);
+  const uint32_t b = p.fd_ns.div(bs);
+  const int s = (int)(bs - b * (uint32_t)p.n_slots);
   const int j = threadIdx.x & 3;
   const int quad = threadIdx.x >> 2;
   const int r = 4 * q + j;
@@ -111,11 +115,12 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
 
   const int L = p.L, plane = p.plane, G = p.seg_sites;
   const uint32_t Lt = (uint32_t)p.Lt;
-  const int64_t gq = (int64_t)chunk * kQuads + quad;
-  const bool live = gq < (int64_t)plane * p.n_seg;   // uniform per quad
-  const int i2 = (int)(gq % plane);
-  const int seg = (int)(gq / plane);
-  const int y = i2 / L, x = i2 - y * L;
+  const uint32_t gq = chunk * (uint32_t)kQuads + (uint32_t)quad;
+  const bool live = gq < (uint32_t)plane * (uint32_t)p.n_seg;   // uniform per quad
+  const uint32_t segu = p.fd_plane.div(gq);
+  const int i2 = (int)(gq - segu * (uint32_t)plane);
+  const int seg = (int)segu;
+  const int y = (int)p.fd_L.div((uint32_t)i2), x = i2 - y * L;
   const uint32_t ixp = (uint32_t)((x + 1 == L ? 0 : x + 1) + L * y), ixm = (uint32_t)((x == 0 ? L - 1 : x - 1) + L * y);
   const uint32_t iyp = (uint32_t)(x + L * (y + 1 == L ? 0 : y + 1)), iym = (uint32_t)(x + L * (y == 0 ? L - 1 : y - 1));
   const Word *Jb = p.J + b * (int64_t)plane * 2;
@@ -336,7 +341,7 @@ __device__ __forceinline__ void block_sum_counters(const VCount<uint32_t, K> *cn
   __syncthreads();   // buf is reused by the caller
 }
 
-template <bool BLUE, int G2>
+template <bool BLUE, int G2, bool PF>
 __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uint32_t> p,
                                                                   const __grid_constant__ SlotThresholds th,
                                                                   int colour, int count_only) {
@@ -346,11 +351,14 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
   __shared__ uint32_t buf[BLUE ? 4 * KF * kBlock4 : 1];
   __shared__ int tot[BLUE ? 2 * 4 * 32 : 1];
 
-  const int64_t set = blockIdx.x / p.blocks_per_set;
-  const int chunk = (int)(blockIdx.x - set * p.blocks_per_set);
-  const int q = (int)(set % p.n_q);
-  const int s = (int)((set / p.n_q) % p.n_slots);
-  const int64_t b = set / ((int64_t)p.n_q * p.n_slots);
+  // block -> (b, s, q, chunk) and thread -> (segment, column) in 32 bits
+  const uint32_t bid = blockIdx.x;
+  const uint32_t set = p.fd_bps.div(bid);
+  const uint32_t chunk = bid - set * (uint32_t)p.blocks_per_set;
+  const uint32_t bs = p.fd_nq.div(set);
+  const int q = (int)(set - bs * (uint32_t)p.n_q);
+  const uint32_t b = p.fd_ns.div(bs);
+  const int s = (int)(bs - b * (uint32_t)p.n_slots);
   if (!BLUE) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
@@ -361,11 +369,12 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
   const bool has_zero = p.t_has_zero != 0;
   const int L = p.L, plane = p.plane, G = p.seg_sites;
   const uint32_t Lt = (uint32_t)p.Lt, P = (uint32_t)plane;
-  const int64_t gq = (int64_t)chunk * kBlock4 + threadIdx.x;
-  const bool live = gq < (int64_t)plane * p.n_seg;
-  const int i2 = (int)(gq % plane);
-  const int seg = (int)(gq / plane);
-  const int y = i2 / L, x = i2 - y * L;
+  const uint32_t gq = chunk * (uint32_t)kBlock4 + threadIdx.x;
+  const bool live = gq < P * (uint32_t)p.n_seg;
+  const uint32_t segu = p.fd_plane.div(gq);
+  const int i2 = (int)(gq - segu * P);
+  const int seg = (int)segu;
+  const int y = (int)p.fd_L.div((uint32_t)i2), x = i2 - y * L;
   const int ixp = (x + 1 == L ? 0 : x + 1) + L * y, ixm = (x == 0 ? L - 1 : x - 1) + L * y;
   const int iyp = x + L * (y + 1 == L ? 0 : y + 1), iym = x + L * (y == 0 ? L - 1 : y - 1);
   const uint4 *src = reinterpret_cast<const uint4 *>(p.spins) + ((b * p.n_slots + s) * p.n_q + q) * p.N;
@@ -403,16 +412,17 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
     cur.ym = pym[off];
     for (int k = 0; k < G; ++k) {
       const uint32_t tau = tau0 + 2u * (uint32_t)k;
-      Quad4 nxt;
-      if (k + 1 < G) {
+      auto load_next = [&](Quad4 &nx) {
         const uint32_t offn = off + 2 * P;
-        nxt.c = pc[offn];
-        nxt.up = pc[(size_t)(tau + 3 == Lt ? 0u : offn + P)];
-        nxt.xp = pxp[offn];
-        nxt.xm = pxm[offn];
-        nxt.yp = pyp[offn];
-        nxt.ym = pym[offn];
-      }
+        nx.c = pc[offn];
+        nx.up = pc[(size_t)(tau + 3 == Lt ? 0u : offn + P)];
+        nx.xp = pxp[offn];
+        nx.xm = pxm[offn];
+        nx.yp = pyp[offn];
+        nx.ym = pym[offn];
+      };
+      Quad4 nxt;
+      if (PF && k + 1 < G) load_next(nxt);
       const uint4 R4 = philox(make_uint4((uint32_t)i2 + off, (uint32_t)t, ctr_z, ctr_w), p.key);
       uint32_t f[4];
 #pragma unroll
@@ -453,7 +463,10 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
       if (!count_only) wc[off] = make_uint4(cur.c.x ^ f[0], cur.c.y ^ f[1], cur.c.z ^ f[2], cur.c.w ^ f[3]);
       if (k + 1 < G) {
         dn = cur.up;
-        cur = nxt;
+        if (PF)
+          cur = nxt;
+        else
+          load_next(cur);
         off += 2 * P;
       }
     }
@@ -527,6 +540,47 @@ __global__ void __launch_bounds__(kBlock) samples_permute_kernel(Word *spins, co
     }
 #pragma unroll
   for (int s = 0; s < kMaxSlotsPermute; ++s)
+    if (s < n_slots) w0[s * stride] = w[s];
+}
+
+// W = 32 form of the same: thread per site, the site's 4 replica words as
+// one 16-byte word per slot, NS >= n_slots slot words held in registers.
+template <int NS>
+__global__ void __launch_bounds__(kBlock4) samples_permute4_kernel(uint4 *spins, const uint32_t *acc, int64_t N,
+                                                                    int n_slots, int n_q, int n_rep,
+                                                                    int blocks_per_set,
+                                                                    unsigned long long *advance) {
+  __shared__ uint32_t msk[4][NS];
+  if (advance && blockIdx.x == 0 && threadIdx.x == 0) *advance += 1ull;
+  const int64_t set = blockIdx.x / blocks_per_set;     // (b, q)
+  const int chunk = (int)(blockIdx.x - set * blocks_per_set);
+  const int q = (int)(set % n_q);
+  const int64_t b = set / n_q;
+  for (int i = threadIdx.x; i < 4 * NS; i += blockDim.x) {
+    const int jj = i / NS, s = i - jj * NS;
+    const int rr = 4 * q + jj;
+    msk[jj][s] = (rr < n_rep && s + 1 < n_slots) ? acc[(b * n_rep + rr) * n_slots + s] : 0u;
+  }
+  __syncthreads();
+  const int64_t site = (int64_t)chunk * kBlock4 + threadIdx.x;
+  if (site >= N) return;
+  const int64_t stride = (int64_t)n_q * N;
+  uint4 *w0 = spins + ((b * n_slots) * n_q + q) * N + site;
+  uint4 w[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+    if (s < n_slots) w[s] = w0[s * stride];
+#pragma unroll
+  for (int s = 0; s + 1 < NS; ++s)
+    if (s + 1 < n_slots) {
+      uint32_t x;
+      x = (w[s].x ^ w[s + 1].x) & msk[0][s]; w[s].x ^= x; w[s + 1].x ^= x;
+      x = (w[s].y ^ w[s + 1].y) & msk[1][s]; w[s].y ^= x; w[s + 1].y ^= x;
+      x = (w[s].z ^ w[s + 1].z) & msk[2][s]; w[s].z ^= x; w[s + 1].z ^= x;
+      x = (w[s].w ^ w[s + 1].w) & msk[3][s]; w[s].w ^= x; w[s + 1].w ^= x;
+    }
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
     if (s < n_slots) w0[s * stride] = w[s];
 }
 
@@ -670,7 +724,7 @@ __global__ void samples_extract_kernel(const Word *spins, const int32_t *walker,
 }
 
 template <typename Word>
-SamplesArgs<Word> make_args(qisg_handle *h) {
+SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
   SamplesArgs<Word> p;
   p.spins = reinterpret_cast<Word *>(h->spins);
   p.J = reinterpret_cast<const Word *>(h->J);
@@ -701,19 +755,25 @@ SamplesArgs<Word> make_args(qisg_handle *h) {
   const int half_col = h->Lt / 2;
   const int64_t sets = h->n_b * h->n_slots * h->n_q;
   const int64_t want_blocks = (int64_t)h->sweep_min_blocks_per_sm * std::max(1, h->n_sm);
-  int G = 4 * std::max(1, h->sweep_groups_per_quad > 0 ? h->sweep_groups_per_quad : 64);
+  const int tile = h->sweep_tile[colour];
+  int G = 4 * std::max(1, tile > 0 ? tile : 64);
   auto blocks_for = [&](int g) {
     const int gg = std::min(g, half_col);
     const int ns = half_col / gg;
     return sets * (((int64_t)p.plane * ns + kQuads - 1) / kQuads);
   };
-  if (h->sweep_groups_per_quad <= 0)
+  if (tile <= 0)
     while (G > 4 && blocks_for(G) < want_blocks) G >>= 1;
   if (G > half_col) G = half_col;
   if (half_col % G) G = half_col;   // one segment per column
   p.seg_sites = G;
   p.n_seg = half_col / G;
   p.blocks_per_set = (int)(((int64_t)p.plane * p.n_seg + kQuads - 1) / kQuads);
+  p.fd_bps = FastDiv((uint32_t)p.blocks_per_set);
+  p.fd_nq = FastDiv((uint32_t)p.n_q);
+  p.fd_ns = FastDiv((uint32_t)p.n_slots);
+  p.fd_plane = FastDiv((uint32_t)p.plane);
+  p.fd_L = FastDiv((uint32_t)p.L);
   return p;
 }
 
@@ -743,19 +803,21 @@ void launch_sweep_g(const SamplesArgs<Word> &p, unsigned blocks, size_t smem, cu
 
 // W = 32 kernel: one thread per column segment of G sites (G = the tile,
 // or by default as many as keep about half the old kernel's thread count).
-SamplesArgs<uint32_t> make_args4(qisg_handle *h, SlotThresholds &th) {
-  SamplesArgs<uint32_t> p = make_args<uint32_t>(h);
+SamplesArgs<uint32_t> make_args4(qisg_handle *h, int colour, SlotThresholds &th) {
+  SamplesArgs<uint32_t> p = make_args<uint32_t>(h, colour);
   const int half_col = h->Lt / 2;
   const int64_t sets = h->n_b * h->n_slots * h->n_q;
   const int64_t want_threads = (int64_t)h->sweep_min_blocks_per_sm * std::max(1, h->n_sm) * kBlock / 2;
-  int G = h->sweep_groups_per_quad > 0 ? h->sweep_groups_per_quad : 64;
-  if (h->sweep_groups_per_quad <= 0)
+  const int tile = h->sweep_tile[colour];
+  int G = tile > 0 ? tile : 64;
+  if (tile <= 0)
     while (G > 1 && sets * p.plane * (int64_t)(half_col / std::min(G, half_col)) < want_threads) G >>= 1;
   if (G > half_col) G = half_col;
   while (G > 1 && half_col % G) --G;
   p.seg_sites = G;
   p.n_seg = half_col / G;
   p.blocks_per_set = (int)(((int64_t)p.plane * p.n_seg + kBlock4 - 1) / kBlock4);
+  p.fd_bps = FastDiv((uint32_t)p.blocks_per_set);
   std::memset(&th, 0, sizeof(th));
   static const int cls[9] = {0, 3, 6, 9, 12, 1, 4, 2, 5};   // us * 3 + ut of the 9 classes
   for (int sl = 0; sl < h->n_slots; ++sl)
@@ -766,19 +828,19 @@ SamplesArgs<uint32_t> make_args4(qisg_handle *h, SlotThresholds &th) {
   return p;
 }
 
-template <bool BLUE>
+template <bool BLUE, bool PF>
 void launch_sweep4(const SamplesArgs<uint32_t> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
                    int colour, int count_only) {
   if constexpr (!BLUE) {   // the red pass keeps no counters
-    samples_sweep4_kernel<false, 0><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only);
+    samples_sweep4_kernel<false, 0, PF><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only);
   } else {
     int g2 = 0;
     while ((4 << g2) < p.seg_sites) ++g2;
     switch (g2) {
 #define QISG_CASE(n) \
-  case n: samples_sweep4_kernel<true, n><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only); break;
+  case n: samples_sweep4_kernel<true, n, PF><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only); break;
       QISG_CASE(0) QISG_CASE(1) QISG_CASE(2) QISG_CASE(3) QISG_CASE(4)
-      default: samples_sweep4_kernel<true, 5><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only); break;
+      default: samples_sweep4_kernel<true, 5, PF><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only); break;
 #undef QISG_CASE
     }
   }
@@ -788,22 +850,28 @@ template <typename Word>
 int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   if (sizeof(Word) == 4) {
     SlotThresholds th;
-    SamplesArgs<uint32_t> p = make_args4(h, th);
+    SamplesArgs<uint32_t> p = make_args4(h, colour, th);
     const int64_t blocks = h->n_b * h->n_slots * h->n_q * p.blocks_per_set;
-    if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+    if (blocks > 0x7FFFFFFF || (int64_t)p.blocks_per_set * kBlock4 > 0x7FFFFFFF)
+      return fail(QISG_EINVAL, "lattice too large for one launch");
     const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
-    if (colour == 1)
-      launch_sweep4<true>(p, th, (unsigned)blocks, h->stream, 1, count_only);
-    else
-      launch_sweep4<false>(p, th, (unsigned)blocks, h->stream, 0, count_only);
+    const bool pf = h->sweep_nopf[colour] == 0;
+    if (colour == 1) {
+      if (pf) launch_sweep4<true, true>(p, th, (unsigned)blocks, h->stream, 1, count_only);
+      else launch_sweep4<true, false>(p, th, (unsigned)blocks, h->stream, 1, count_only);
+    } else {
+      if (pf) launch_sweep4<false, true>(p, th, (unsigned)blocks, h->stream, 0, count_only);
+      else launch_sweep4<false, false>(p, th, (unsigned)blocks, h->stream, 0, count_only);
+    }
     prof_end(h, QISG_KERNEL_SWEEP, tok);
     h->launches++;
     return cuda_check(cudaGetLastError(), "samples half sweep");
   }
-  SamplesArgs<Word> p = make_args<Word>(h);
+  SamplesArgs<Word> p = make_args<Word>(h, colour);
   const int64_t sets = h->n_b * h->n_slots * h->n_q;
   const int64_t blocks = sets * p.blocks_per_set;
-  if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+  if (blocks > 0x7FFFFFFF || (int64_t)p.blocks_per_set * kQuads > 0x7FFFFFFF)
+    return fail(QISG_EINVAL, "lattice too large for one launch");
   const size_t smem = 0;
   const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
   if (colour == 1)
@@ -823,12 +891,29 @@ int pt_t(qisg_handle *h, int explicit_pass, int advance) {
                     "clear PT masks");
   if (!rc) rc = pt_pass(h, explicit_pass, 0, h->n_samples);
   if (rc) return rc;
-  const int64_t per_set = (h->N * 4 + kBlock - 1) / kBlock;
-  const int64_t blocks = h->n_b * h->n_q * per_set;
   const int tok = prof_begin(h, QISG_KERNEL_PERMUTE);
-  samples_permute_kernel<Word><<<(unsigned)blocks, kBlock, 0, h->stream>>>(
-      reinterpret_cast<Word *>(h->spins), reinterpret_cast<const Word *>(h->d_acc), h->N, h->n_slots,
-      h->n_q, h->n_rep, (int)per_set, advance ? h->d_t : nullptr);
+  unsigned long long *adv = advance ? h->d_t : nullptr;
+  if (sizeof(Word) == 4) {
+    const int64_t per_set = (h->N + kBlock4 - 1) / kBlock4;
+    const unsigned blocks = (unsigned)(h->n_b * h->n_q * per_set);
+    uint4 *sp = reinterpret_cast<uint4 *>(h->spins);
+    const uint32_t *ac = reinterpret_cast<const uint32_t *>(h->d_acc);
+    if (h->n_slots <= 8)
+      samples_permute4_kernel<8><<<blocks, kBlock4, 0, h->stream>>>(sp, ac, h->N, h->n_slots, h->n_q, h->n_rep,
+                                                                   (int)per_set, adv);
+    else if (h->n_slots <= 16)
+      samples_permute4_kernel<16><<<blocks, kBlock4, 0, h->stream>>>(sp, ac, h->N, h->n_slots, h->n_q, h->n_rep,
+                                                                    (int)per_set, adv);
+    else
+      samples_permute4_kernel<32><<<blocks, kBlock4, 0, h->stream>>>(sp, ac, h->N, h->n_slots, h->n_q, h->n_rep,
+                                                                    (int)per_set, adv);
+  } else {
+    const int64_t per_set = (h->N * 4 + kBlock - 1) / kBlock;
+    const int64_t blocks = h->n_b * h->n_q * per_set;
+    samples_permute_kernel<Word><<<(unsigned)blocks, kBlock, 0, h->stream>>>(
+        reinterpret_cast<Word *>(h->spins), reinterpret_cast<const Word *>(h->d_acc), h->N, h->n_slots,
+        h->n_q, h->n_rep, (int)per_set, adv);
+  }
   prof_end(h, QISG_KERNEL_PERMUTE, tok);
   h->launches++;
   return cuda_check(cudaGetLastError(), "samples permute");

@@ -83,6 +83,8 @@ def load(build_if_missing: bool = True):
         "qisg_profile": (I, [P, I]),
         "qisg_set_graphs": (I, [P, I]),
         "qisg_autotune": (I, [P, I, P]),
+        "qisg_get_tiles": (I, [P, P, P]),
+        "qisg_set_tiles": (I, [P, P, P]),
         "qisg_batch_create": (I, [P, I, ctypes.c_size_t, P]),
         "qisg_batch_admit": (I, [P, P, P]),
         "qisg_batch_retire": (I, [P, I]),
@@ -113,7 +115,7 @@ def exported_symbols():
             "qisg_slot_means", "qisg_thresholds", "qisg_sweep_count", "qisg_layout",
             "qisg_launch_count", "qisg_sync", "qisg_destroy", "qisg_strerror", "qisg_last_error",
             "qisg_philox4x32_10", "qisg_profile", "qisg_profile_read", "qisg_set_graphs",
-            "qisg_autotune", "qisg_batch_create", "qisg_batch_admit", "qisg_batch_retire",
+            "qisg_autotune", "qisg_get_tiles", "qisg_set_tiles", "qisg_batch_create", "qisg_batch_admit", "qisg_batch_retire",
             "qisg_batch_run", "qisg_batch_set_schedule", "qisg_batch_autotune", "qisg_batch_status",
             "qisg_batch_results", "qisg_batch_info", "qisg_batch_instance_bytes", "qisg_batch_sync",
             "qisg_batch_destroy"]
@@ -295,6 +297,16 @@ class Instance:
         g = ctypes.c_int()
         _check(load().qisg_autotune(self._h, sweeps_per_candidate, ctypes.byref(g)))
         return g.value
+
+    def tiles(self):
+        """((red tile, blue tile), (red prefetch, blue prefetch)) of the sweep schedule."""
+        t, pf = (ctypes.c_int * 2)(), (ctypes.c_int * 2)()
+        _check(load().qisg_get_tiles(self._h, t, pf))
+        return (t[0], t[1]), (pf[0], pf[1])
+
+    def set_tiles(self, tiles, prefetch=(1, 1)):
+        t, pf = (ctypes.c_int * 2)(*tiles), (ctypes.c_int * 2)(*prefetch)
+        _check(load().qisg_set_tiles(self._h, t, pf))
 
     def profile(self, enable: bool, kinds=None):
         """Time launches with event pairs; `kinds` limits it to those kernel kinds."""

@@ -205,16 +205,17 @@ def test_graph_replay_equals_direct_launches(qisg):
         assert a.launch_count() == b.launch_count()
 
 
-def test_autotune_keeps_trajectory(qisg):
+@pytest.mark.parametrize("word_bits,n_cand", [(64, 7), (32, 14)])
+def test_autotune_keeps_trajectory(qisg, word_bits, n_cand):
     import numpy as np
-    kw = dict(layout=qisg.QISG_LAYOUT_SAMPLES, word_bits=64)
-    a, _ = make(qisg, 8, 16, 0.2, 0.5, 8, 1.0, 4, 64, 5, **kw)
-    b, _ = make(qisg, 8, 16, 0.2, 0.5, 8, 1.0, 4, 64, 5, **kw)
+    kw = dict(layout=qisg.QISG_LAYOUT_SAMPLES, word_bits=word_bits)
+    a, _ = make(qisg, 8, 16, 0.2, 0.5, 8, 1.0, 4, word_bits, 5, **kw)
+    b, _ = make(qisg, 8, 16, 0.2, 0.5, 8, 1.0, 4, word_bits, 5, **kw)
     with a, b:
         g = a.autotune(1)
         assert g in (1, 2, 4, 8, 16, 32, 64)
         n = a.sweep_count()
-        assert n == 7 * 2
+        assert n == n_cand * 2
         a.sweep(6)
         b.sweep(n + 6)
         assert np.array_equal(a.spins(), b.spins())
