@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsign
                                                          const PTConst *ptc, const double *sq,
                                                          const unsigned long long *d_t, uint2 key,
                                                          int64_t n_samples, int n_rep, int n_slots,
-                                                         int explicit_pass) {
+                                                         int explicit_pass, unsigned long long *adv) {
   constexpr int W = (int)sizeof(Word) * 8, octs = W / 8;
   __shared__ uint32_t bits[8];
   const uint32_t bid = blockIdx.x;
@@ -71,29 +71,39 @@ __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsign
         atomicOr(reinterpret_cast<unsigned int *>(&out[s]), (unsigned int)m);
     }
   }
+  // advance the sweep counter once every block has read it (all reads of
+  // this block precede the barrier above); adv[1] counts arrived blocks
+  if (adv && threadIdx.x == 0) {
+    unsigned int *arrived = reinterpret_cast<unsigned int *>(adv + 1);
+    __threadfence();
+    if (atomicAdd(arrived, 1u) == gridDim.x - 1) {
+      *arrived = 0u;
+      *adv += 1ull;
+    }
+  }
 }
 
 template <typename Word, bool WIDE>
-void launch_pt_samples(qisg_handle *h, uint2 key, int explicit_pass) {
+void launch_pt_samples(qisg_handle *h, uint2 key, int explicit_pass, unsigned long long *adv) {
   const unsigned blocks = (unsigned)(h->n_b * h->n_rep * (h->W / 8));
   pt_samples_kernel<Word, WIDE><<<blocks, 256, 0, h->stream>>>(
       h->d_walker, h->d_U, reinterpret_cast<Word *>(h->d_acc), reinterpret_cast<const PTConst *>(h->d_ptc),
-      h->d_sq, h->d_t, key, h->n_samples, h->n_rep, h->n_slots, explicit_pass);
+      h->d_sq, h->d_t, key, h->n_samples, h->n_rep, h->n_slots, explicit_pass, adv);
 }
 
 }  // namespace
 
-int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a) {
+int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a, unsigned long long *adv) {
   const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
   const bool wide = 2 * h->N >= (int64_t(1) << 30);   // energy differences beyond 31 bits
   const int tok = prof_begin(h, QISG_KERNEL_PT);
   if (h->layout == QISG_LAYOUT_SAMPLES) {
     if (h->W == 64) {
-      if (wide) launch_pt_samples<unsigned long long, true>(h, key, explicit_pass);
-      else launch_pt_samples<unsigned long long, false>(h, key, explicit_pass);
+      if (wide) launch_pt_samples<unsigned long long, true>(h, key, explicit_pass, adv);
+      else launch_pt_samples<unsigned long long, false>(h, key, explicit_pass, adv);
     } else {
-      if (wide) launch_pt_samples<unsigned int, true>(h, key, explicit_pass);
-      else launch_pt_samples<unsigned int, false>(h, key, explicit_pass);
+      if (wide) launch_pt_samples<unsigned int, true>(h, key, explicit_pass, adv);
+      else launch_pt_samples<unsigned int, false>(h, key, explicit_pass, adv);
     }
   } else {
     const int64_t n_chains = n_a * h->n_rep;

@@ -174,6 +174,7 @@ int recompute_energies(qisg_handle *h) {
     if ((rc = lanes_half_sweep(h, 0, 1))) return rc;
     return lanes_half_sweep(h, 1, 1);
   }
+  if ((rc = samples_materialize(h))) return rc;
   if ((rc = samples_half_sweep(h, 0, 1))) return rc;
   return samples_half_sweep(h, 1, 1);
 }
@@ -297,6 +298,8 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
       h->J_bytes = (size_t)h->n_b * L * L * 2 * (h->W / 8);
     }
     rc = dalloc(h, &h->spins, h->spins_bytes);
+    h->fused = layout == QISG_LAYOUT_SAMPLES && h->W == 32;
+    if (!rc && h->fused) rc = dalloc(h, &h->spins_alt, h->spins_bytes);
   }
   if (!rc) rc = dalloc(h, &h->J, h->J_bytes);
   if (!rc) rc = dalloc(h, &h->d_T, h->T.size() * 4);
@@ -312,7 +315,7 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc) rc = dalloc(h, &h->d_sumq2, qn * 8);
   if (!rc) rc = dalloc(h, &h->d_q, qn * 8);
   if (!rc) rc = dalloc(h, &h->d_out, (size_t)2 * n_chain_slots * 8 + qn * 8);
-  if (!rc) rc = dalloc(h, &h->d_t, 8);
+  if (!rc) rc = dalloc(h, &h->d_t, 16);
   if (!rc) rc = dalloc(h, &h->d_err, 4);
   if (!rc && layout == QISG_LAYOUT_SAMPLES)
     rc = dalloc(h, &h->d_acc, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8));
@@ -347,7 +350,7 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumq, 0, qn * 8, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumq2, 0, qn * 8, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_q, 0, qn * 8, h->stream), "memset");
-  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_t, 0, 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_t, 0, 16, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_err, 0, 4, h->stream), "memset");
   if (!rc && h->d_acc)
     rc = cuda_check(cudaMemsetAsync(h->d_acc, 0, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8), h->stream),
@@ -407,7 +410,8 @@ int64_t gcd64(int64_t a, int64_t b) { return b ? gcd64(b, a % b) : a; }
 int cycle_length(const qisg_handle *h) {
   const int64_t p = h->pt_every > 0 ? h->pt_every : 1;
   const int64_t m = h->measure_every > 0 ? h->measure_every : 1;
-  const int64_t l = p / gcd64(p, m) * m;
+  int64_t l = p / gcd64(p, m) * m;
+  if (h->fused && (l & 1)) l *= 2;   // every red pass swaps the lattice buffers
   return (int)(l > 4096 ? 0 : l);   // no graph for very long cycles
 }
 
@@ -434,6 +438,8 @@ int build_cycle(qisg_handle *h, int C) {
   if (rc) return rc;
   const uint64_t t0 = h->t;
   const int64_t meas0 = h->n_meas, launches0 = h->launches;
+  const bool pending0 = h->perm_pending;
+  void *const spins0 = h->spins;
   int64_t pl0[4];
   size_t ev0[4];
   for (int k = 0; k < 4; ++k) {
@@ -451,6 +457,9 @@ int build_cycle(qisg_handle *h, int C) {
   if (!rc) rc = rc_end;
   h->cyc_launches = h->launches - launches0;
   h->cyc_meas = h->n_meas - meas0;
+  h->cyc_pending = h->perm_pending;
+  h->perm_pending = pending0;
+  if (!rc && h->spins != spins0) rc = fail(QISG_ECUDA, "sweep cycle does not return to its lattice buffer");
   h->t = t0;
   h->n_meas = meas0;
   h->launches = launches0;
@@ -541,6 +550,7 @@ int replay_cycle(qisg_handle *h) {
   if (rc) return rc;
   h->t += (uint64_t)h->cyc_sweeps;
   h->n_meas += h->cyc_meas;
+  h->perm_pending = h->cyc_pending;
   h->launches += h->cyc_launches;
   return QISG_OK;
 }
@@ -868,7 +878,7 @@ int qisg_sync(qisg_handle *h) {
 void qisg_destroy(qisg_handle *h) {
   if (!h) return;
   if (h->stream || true) cudaStreamSynchronize(h->stream);
-  void *ptrs[] = {h->spins, h->J, h->d_T, h->d_bases, h->d_sq, h->d_ptc, h->d_walker, h->d_U, h->d_sumA, h->d_sumB,
+  void *ptrs[] = {h->spins, h->spins_alt, h->J, h->d_T, h->d_bases, h->d_sq, h->d_ptc, h->d_walker, h->d_U, h->d_sumA, h->d_sumB,
                   h->d_sumq, h->d_sumq2, h->d_q, h->d_out, h->d_t, h->d_acc, h->d_err};
   for (void *p : ptrs)
     if (p) cudaFree(p);

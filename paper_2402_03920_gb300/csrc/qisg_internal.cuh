@@ -437,6 +437,13 @@ struct qisg_handle {
   // device memory
   void *spins = nullptr;
   size_t spins_bytes = 0;
+  // SAMPLES, W = 32: the red pass applies the last PT pass's exchanges while
+  // it copies the lattice into the other buffer (spins and spins_alt swap
+  // after every red pass); perm_pending: the stored lattice still lacks the
+  // exchanges of the last PT pass (its masks are in d_acc)
+  bool fused = false;
+  void *spins_alt = nullptr;
+  bool perm_pending = false;
   void *J = nullptr;
   size_t J_bytes = 0;
   uint32_t *d_T = nullptr;
@@ -448,7 +455,7 @@ struct qisg_handle {
   long long *d_sumA = nullptr, *d_sumB = nullptr, *d_sumq = nullptr, *d_sumq2 = nullptr;
   long long *d_q = nullptr;         // overlap scratch [a][s][pair]
   long long *d_out = nullptr;       // output staging [2][a][r][s]
-  unsigned long long *d_t = nullptr;  // sweep counter
+  unsigned long long *d_t = nullptr;  // sweep counter; d_t[1]: PT blocks that read it (fused mode)
   void *d_acc = nullptr;            // SAMPLES: PT lane masks of the last pass, Word [b][r][s]
   int *d_err = nullptr;
   size_t device_bytes = 0;
@@ -468,6 +475,7 @@ struct qisg_handle {
   int64_t cyc_launches = 0, cyc_meas = 0;
   int64_t cyc_prof_launched[4] = {0, 0, 0, 0};
   bool cyc_profiled = false;
+  bool cyc_pending = false;         // perm_pending after one replay
   // event-record nodes of a profiled capture: node, kernel kind, 0 start / 1 stop
   std::vector<cudaGraphNode_t> cyc_ev_nodes;
   std::vector<std::pair<int, int>> cyc_ev_kind;
@@ -498,6 +506,7 @@ int lanes_set_couplings(qisg_handle *h, const int8_t *J);
 int samples_init(qisg_handle *h);
 int samples_half_sweep(qisg_handle *h, int colour, int count_only);
 int samples_pt(qisg_handle *h, int explicit_pass, int advance);
+int samples_materialize(qisg_handle *h);
 int samples_measure(qisg_handle *h, int force_to_q);
 int samples_energies_by_slot(qisg_handle *h);
 int samples_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S);
@@ -509,7 +518,8 @@ int samples_set_couplings(qisg_handle *h, const int8_t *J);
 int advance_counter(qisg_handle *h);
 
 // PT pass of samples a0 .. a0+n_a-1 (pt.cu)
-int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a);
+// adv: SAMPLES only, advance the sweep counter after the pass (nullptr: no)
+int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a, unsigned long long *adv = nullptr);
 
 // Launch timing: call prof_begin(h, kind) before and prof_end(h, kind, tok)
 // after a kernel launch on h->stream.

@@ -41,6 +41,7 @@ struct SamplesArgs {
   int n_seg;             // (L_tau / 2) / G segments per column
   int blocks_per_set;    // blocks per (b, s, q) word set
   int t_has_zero;        // some threshold of the table is 0 (always reject)
+  uint32_t one, all_ones;   // 1 and 0xFFFFFFFF as runtime values (flag_imad)
   // division by the invariants of the index decomposition (32-bit indices)
   FastDiv fd_bps, fd_nq, fd_ns, fd_plane, fd_L;
   // cleared by the red pass (nothing reads them until the blue pass / PT):
@@ -276,16 +277,33 @@ constexpr int kBlock4 = 128;
 constexpr int kLog2Block4 = 7;
 
 // Reject thresholds per slot for the classes (u_t = 0: u_s = 0..4),
-// (u_t = 1: u_s = 0, 1), (u_t = 2: u_s = 0, 1), as rho_gt / rho_ge compare
-// them (T - 1 for finite thresholds when no threshold is 0, else T).
+// (u_t = 1: u_s = 0, 1), (u_t = 2: u_s = 0, 1), in the form reject_mask
+// reads them.
 struct SlotThresholds {
   uint32_t v[kMaxSlotsPT][9];
 };
 
+// Reject flag on the integer multiply-add pipe (leaving the logic pipe to
+// the bit-sliced arithmetic): with K = ~(T - 1) (K = 0 for the sentinel),
+// R + K >= 2^32 iff R > T - 1, so the high word of the 64-bit R * 1 + K is
+// the flag and its product with 0xFFFFFFFF the mask.  one and all_ones are
+// the runtime values 1 and 0xFFFFFFFF (kernel parameters, so the compiler
+// keeps the multiplies).
+__device__ __forceinline__ uint32_t flag_imad(uint32_t R, uint32_t K, uint32_t one, uint32_t all_ones) {
+  unsigned long long v;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(v) : "r"(R), "r"(one), "l"((unsigned long long)K));
+  uint32_t m;
+  asm("mul.lo.u32 %0, %1, %2;" : "=r"(m) : "r"((uint32_t)(v >> 32)), "r"(all_ones));
+  return m;
+}
+
+// HAS_ZERO: th holds T and the flags are T != sentinel && R >= T; else th
+// holds K = ~(T - 1) (0 for the sentinel) for flag_imad.
 template <bool HAS_ZERO>
 __device__ __forceinline__ uint32_t reject_mask(uint32_t R, const uint32_t *th, uint32_t us0, uint32_t us1,
-                                                uint32_t us2, uint32_t ut0, uint32_t ut1) {
-#define QISG_F(c) (HAS_ZERO ? rho_ge<uint32_t>(R, th[c]) : rho_gt<uint32_t>(R, th[c]))
+                                                uint32_t us2, uint32_t ut0, uint32_t ut1, uint32_t one,
+                                                uint32_t all_ones) {
+#define QISG_F(c) (HAS_ZERO ? rho_ge<uint32_t>(R, th[c]) : flag_imad(R, th[c], one, all_ones))
   const uint32_t row0 = mux(us2, QISG_F(4), mux(us1, mux(us0, QISG_F(3), QISG_F(2)), mux(us0, QISG_F(1), QISG_F(0))));
   const uint32_t low = ~(us1 | us2);
   const uint32_t row1 = low & mux(us0, QISG_F(6), QISG_F(5));
@@ -300,6 +318,280 @@ struct Quad4 {
 
 __device__ __forceinline__ uint32_t q4(const uint4 &v, int j) {
   return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+// Red pass with the pending PT exchanges folded in (W = 32).  After a PT pass
+// (Sec. 2.1) the stored lattice still holds every slot's words as they were
+// before the exchanges; the accepted pairs of each (sample block, replica)
+// are the lane masks acc[b][r][s].  A thread owns one red site of one
+// replica and streams the slot words s = 0, 1, ... of the seven sites it
+// needs (the site, its two tau and four spatial neighbours), carrying up the
+// word that the sequential pass moves through pair s (masked exchange of
+// the carried word with slot s+1's), so slot s's words are final when the
+// thread reaches s.  It updates the red site of slot s from them and writes
+// it, with its blue partner at tau + 1 (every blue site is the partner of
+// exactly one red site, the one below it), to the other lattice buffer; the
+// blue pass then works on that buffer in place.  The four replica threads of
+// a site share one Philox call per slot, made by one of them per group of
+// four slots and exchanged in shared memory.
+struct FusedRedArgs {
+  const uint32_t *src;
+  uint32_t *dst;
+  const uint32_t *J;
+  const uint32_t *acc;
+  const unsigned long long *d_t;
+  unsigned long long *zero_U;
+  int64_t n_zero_U;
+  uint2 key;
+  int64_t N;
+  int L, Lt, plane, n_slots, n_q, n_rep, blocks_per_set, t_has_zero;
+  uint32_t one, all_ones;
+  FastDiv fd_bps, fd_nq, fd_plane, fd_L;
+};
+
+__global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedRedArgs p,
+                                                                     const __grid_constant__ SlotThresholds th) {
+  __shared__ uint32_t msk[4][kMaxSlotsPT];
+  __shared__ uint4 rnd[kBlock4];   // per warp: [slot in group][quad][replica]
+  const uint32_t bid = blockIdx.x;
+  const uint32_t set = p.fd_bps.div(bid);   // (b, q)
+  const uint32_t chunk = bid - set * (uint32_t)p.blocks_per_set;
+  const uint32_t b = p.fd_nq.div(set);
+  const int q = (int)(set - b * (uint32_t)p.n_q);
+  const int n = p.n_slots;
+  {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
+  }
+  for (int i = threadIdx.x; i < 4 * kMaxSlotsPT; i += blockDim.x) {
+    const int jj = i / kMaxSlotsPT, sl = i - jj * kMaxSlotsPT;
+    const int rr = 4 * q + jj;
+    msk[jj][sl] = (rr < p.n_rep && sl + 1 < n) ? p.acc[((int64_t)b * p.n_rep + rr) * n + sl] : 0u;
+  }
+  __syncthreads();
+
+  const uint32_t tid = chunk * (uint32_t)kBlock4 + threadIdx.x;
+  const int j = (int)(tid & 3u);
+  const uint32_t quad = tid >> 2;
+  const uint32_t P = (uint32_t)p.plane, Lt = (uint32_t)p.Lt, L = (uint32_t)p.L;
+  const bool live = quad < P * (Lt / 2);
+  const uint32_t seg = p.fd_plane.div(quad);
+  const uint32_t i2 = quad - seg * P;
+  const uint32_t y = p.fd_L.div(i2), x = i2 - y * L;
+  const uint32_t tau = 2 * seg + ((x + y) & 1u);
+  const uint32_t ixp = (x + 1 == L ? 0 : x + 1) + L * y, ixm = (x == 0 ? L - 1 : x - 1) + L * y;
+  const uint32_t iyp = x + L * (y + 1 == L ? 0 : y + 1), iym = x + L * (y == 0 ? L - 1 : y - 1);
+  const uint32_t off = tau * P;
+  // the seven sites: centre, tau + 1 (blue partner), tau - 1, x+, x-, y+, y-
+  uint32_t z[7];
+  z[0] = i2 + off;
+  z[1] = i2 + (tau + 1 == Lt ? 0u : off + P);
+  z[2] = i2 + (tau == 0 ? (Lt - 1) * P : off - P);
+  z[3] = ixp + off;
+  z[4] = ixm + off;
+  z[5] = iyp + off;
+  z[6] = iym + off;
+  // word of site zz at slot sl: slot base (uniform over the block) + 4 zz + j
+  // (layout [b][s][q][site][4])
+  const int64_t base = (((int64_t)b * n * p.n_q + q) * p.N) * 4;
+  const int64_t SS = (int64_t)p.n_q * p.N * 4;
+  uint32_t zo[7];
+  const uint32_t *Jb = p.J + (int64_t)b * P * 2;
+  uint32_t Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
+  const unsigned long long t = *p.d_t;
+  const uint32_t ctr_w = (DOM_SWEEP << 28) | ((b * 32u) >> 6);
+  const bool has_zero = p.t_has_zero != 0;
+  uint32_t cw[7], n1[7];   // carried words at the current slot; words of the next slot
+#pragma unroll
+  for (int k = 0; k < 7; ++k) zo[k] = 4 * z[k] + (uint32_t)j;
+  const uint32_t *sb = p.src + base;
+  uint32_t *db = p.dst + base;
+  if (live) {
+    Jxp = Jb[2 * i2];
+    Jxm = Jb[2 * ixm];
+    Jyp = Jb[2 * i2 + 1];
+    Jym = Jb[2 * iym + 1];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) cw[k] = sb[zo[k]];
+    if (n > 1)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) n1[k] = sb[SS + zo[k]];
+  }
+  uint32_t *rw = reinterpret_cast<uint32_t *>(rnd) + (threadIdx.x >> 5) * 128;
+  const int ql = (int)((threadIdx.x & 31) >> 2);
+  for (int g = 0; 4 * g < n; ++g) {
+    if (live && 4 * g + j < n) {
+      const uint4 r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)(4 * g + j) | ((uint32_t)q << 16), ctr_w),
+                              p.key);
+      *reinterpret_cast<uint4 *>(rw + ((j * 8 + ql) << 2)) = r4;
+    }
+    __syncwarp();
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int sl = 4 * g + i;
+        if (sl >= n) break;
+        // words of slot sl after the exchanges of pairs 0 .. sl
+        uint32_t fw[7];
+        if (sl + 1 < n) {
+          uint32_t n2[7] = {0, 0, 0, 0, 0, 0, 0};
+          if (sl + 2 < n) {
+            const uint32_t *ps = sb + (int64_t)(sl + 2) * SS;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) n2[k] = ps[zo[k]];
+          }
+          const uint32_t m = msk[j][sl];
+#pragma unroll
+          for (int k = 0; k < 7; ++k) {
+            const uint32_t xx = (cw[k] ^ n1[k]) & m;
+            fw[k] = cw[k] ^ xx;
+            cw[k] = n1[k] ^ xx;
+            n1[k] = n2[k];
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 7; ++k) fw[k] = cw[k];
+        }
+        const uint32_t R = rw[((i * 8 + ql) << 2) + j];
+        const uint32_t *T = th.v[sl];
+        const uint32_t sc = fw[0];
+        const uint32_t b1 = sc ^ fw[3] ^ Jxp;
+        const uint32_t b2 = sc ^ fw[4] ^ Jxm;
+        const uint32_t b3 = sc ^ fw[5] ^ Jyp;
+        const uint32_t b4 = sc ^ fw[6] ^ Jym;
+        const uint32_t t1 = sc ^ fw[1];
+        const uint32_t t2 = sc ^ fw[2];
+        const uint32_t s1 = b1 ^ b2 ^ b3;
+        const uint32_t c1 = maj3(b1, b2, b3);
+        const uint32_t us0 = s1 ^ b4;
+        const uint32_t c2 = s1 & b4;
+        const uint32_t us1 = c1 ^ c2;
+        const uint32_t us2 = c1 & c2;
+        const uint32_t ut0 = t1 ^ t2;
+        const uint32_t ut1 = t1 & t2;
+        const uint32_t rej = has_zero ? reject_mask<true>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones)
+                                      : reject_mask<false>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
+        uint32_t *pd = db + (int64_t)sl * SS;
+        pd[zo[0]] = sc ^ ~rej;
+        pd[zo[1]] = fw[1];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// The same pass with one thread per red site and replica quad: 16-byte slot
+// words (the site's four replica words), one Philox call per slot for the
+// four draws.  Fewer threads, fewer instructions per word; the autotuner
+// picks between the two forms (results are identical).
+__global__ void __launch_bounds__(kBlock4) samples_red_fused4_kernel(const FusedRedArgs p,
+                                                                      const __grid_constant__ SlotThresholds th) {
+  __shared__ __align__(16) uint32_t msk[kMaxSlotsPT][4];
+  const uint32_t bid = blockIdx.x;
+  const uint32_t set = p.fd_bps.div(bid);   // (b, q)
+  const uint32_t chunk = bid - set * (uint32_t)p.blocks_per_set;
+  const uint32_t b = p.fd_nq.div(set);
+  const int q = (int)(set - b * (uint32_t)p.n_q);
+  const int n = p.n_slots;
+  {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
+  }
+  for (int i = threadIdx.x; i < 4 * kMaxSlotsPT; i += blockDim.x) {
+    const int sl = i >> 2, jj = i & 3;
+    const int rr = 4 * q + jj;
+    msk[sl][jj] = (rr < p.n_rep && sl + 1 < n) ? p.acc[((int64_t)b * p.n_rep + rr) * n + sl] : 0u;
+  }
+  __syncthreads();
+
+  const uint32_t quad = chunk * (uint32_t)kBlock4 + threadIdx.x;   // red site of the (b, q) set
+  const uint32_t P = (uint32_t)p.plane, Lt = (uint32_t)p.Lt, L = (uint32_t)p.L;
+  if (quad >= P * (Lt / 2)) return;
+  const uint32_t seg = p.fd_plane.div(quad);
+  const uint32_t i2 = quad - seg * P;
+  const uint32_t y = p.fd_L.div(i2), x = i2 - y * L;
+  const uint32_t tau = 2 * seg + ((x + y) & 1u);
+  const uint32_t ixp = (x + 1 == L ? 0 : x + 1) + L * y, ixm = (x == 0 ? L - 1 : x - 1) + L * y;
+  const uint32_t iyp = x + L * (y + 1 == L ? 0 : y + 1), iym = x + L * (y == 0 ? L - 1 : y - 1);
+  const uint32_t off = tau * P;
+  uint32_t z[7];
+  z[0] = i2 + off;
+  z[1] = i2 + (tau + 1 == Lt ? 0u : off + P);
+  z[2] = i2 + (tau == 0 ? (Lt - 1) * P : off - P);
+  z[3] = ixp + off;
+  z[4] = ixm + off;
+  z[5] = iyp + off;
+  z[6] = iym + off;
+  // 16-byte word of site zz at slot sl: slot base (uniform) + zz
+  const int64_t base = ((int64_t)b * n * p.n_q + q) * p.N;
+  const int64_t SS = (int64_t)p.n_q * p.N;
+  const uint4 *sb = reinterpret_cast<const uint4 *>(p.src) + base;
+  uint4 *db = reinterpret_cast<uint4 *>(p.dst) + base;
+  const uint32_t *Jb = p.J + (int64_t)b * P * 2;
+  const uint32_t Jxp = Jb[2 * i2], Jxm = Jb[2 * ixm], Jyp = Jb[2 * i2 + 1], Jym = Jb[2 * iym + 1];
+  const unsigned long long t = *p.d_t;
+  const uint32_t ctr_w = (DOM_SWEEP << 28) | ((b * 32u) >> 6);
+  const bool has_zero = p.t_has_zero != 0;
+  uint4 cw[7], n1[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) cw[k] = sb[z[k]];
+  if (n > 1)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) n1[k] = sb[SS + z[k]];
+  for (int sl = 0; sl < n; ++sl) {
+    uint4 fw[7];
+    if (sl + 1 < n) {
+      uint4 n2[7];
+      if (sl + 2 < n) {
+        const uint4 *ps = sb + (int64_t)(sl + 2) * SS;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) n2[k] = ps[z[k]];
+      }
+      const uint4 m = *reinterpret_cast<const uint4 *>(msk[sl]);
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        uint4 xx;
+        xx.x = (cw[k].x ^ n1[k].x) & m.x;
+        xx.y = (cw[k].y ^ n1[k].y) & m.y;
+        xx.z = (cw[k].z ^ n1[k].z) & m.z;
+        xx.w = (cw[k].w ^ n1[k].w) & m.w;
+        fw[k] = make_uint4(cw[k].x ^ xx.x, cw[k].y ^ xx.y, cw[k].z ^ xx.z, cw[k].w ^ xx.w);
+        cw[k] = make_uint4(n1[k].x ^ xx.x, n1[k].y ^ xx.y, n1[k].z ^ xx.z, n1[k].w ^ xx.w);
+        if (sl + 2 < n) n1[k] = n2[k];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) fw[k] = cw[k];
+    }
+    const uint4 R4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)sl | ((uint32_t)q << 16), ctr_w), p.key);
+    const uint32_t *T = th.v[sl];
+    uint32_t f[4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const uint32_t sc = q4(fw[0], jj);
+      const uint32_t b1 = sc ^ q4(fw[3], jj) ^ Jxp;
+      const uint32_t b2 = sc ^ q4(fw[4], jj) ^ Jxm;
+      const uint32_t b3 = sc ^ q4(fw[5], jj) ^ Jyp;
+      const uint32_t b4 = sc ^ q4(fw[6], jj) ^ Jym;
+      const uint32_t t1 = sc ^ q4(fw[1], jj);
+      const uint32_t t2 = sc ^ q4(fw[2], jj);
+      const uint32_t s1 = b1 ^ b2 ^ b3;
+      const uint32_t c1 = maj3(b1, b2, b3);
+      const uint32_t us0 = s1 ^ b4;
+      const uint32_t c2 = s1 & b4;
+      const uint32_t us1 = c1 ^ c2;
+      const uint32_t us2 = c1 & c2;
+      const uint32_t ut0 = t1 ^ t2;
+      const uint32_t ut1 = t1 & t2;
+      const uint32_t R = q4(R4, jj);
+      const uint32_t rej = has_zero ? reject_mask<true>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones)
+                                    : reject_mask<false>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
+      f[jj] = ~rej;
+    }
+    uint4 *pd = db + (int64_t)sl * SS;
+    pd[z[0]] = make_uint4(fw[0].x ^ f[0], fw[0].y ^ f[1], fw[0].z ^ f[2], fw[0].w ^ f[3]);
+    pd[z[1]] = fw[1];
+  }
 }
 
 // Sum the block's per-thread counters (NC counters of K planes in registers)
@@ -359,7 +651,7 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
   const int q = (int)(set - bs * (uint32_t)p.n_q);
   const uint32_t b = p.fd_ns.div(bs);
   const int s = (int)(bs - b * (uint32_t)p.n_slots);
-  if (!BLUE) {
+  {   // counters / masks the host asked this pass to clear (nothing reads them before the next pass)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_acc; i += stride)
@@ -447,9 +739,9 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
         if (count_only)
           flip = 0;
         else if (!has_zero)
-          flip = ~reject_mask<false>(R, T, us0, us1, us2, ut0, ut1);
+          flip = ~reject_mask<false>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
         else
-          flip = ~reject_mask<true>(R, T, us0, us1, us2, ut0, ut1);
+          flip = ~reject_mask<true>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
         f[j] = flip;
         if (BLUE) {
           // unsatisfied counts after the flip: u -> 4 - u (spatial), 2 - u (tau)
@@ -749,6 +1041,8 @@ SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
   p.t_has_zero = 0;
   for (uint32_t v : h->T)
     if (v == 0) p.t_has_zero = 1;
+  p.one = 1u;
+  p.all_ones = 0xFFFFFFFFu;
   // sites per quad along tau: as many as possible (cheaper energy flushes)
   // while the grid keeps about sweep_min_blocks_per_sm blocks per SM; G must
   // divide L_tau / 2
@@ -823,7 +1117,7 @@ SamplesArgs<uint32_t> make_args4(qisg_handle *h, int colour, SlotThresholds &th)
   for (int sl = 0; sl < h->n_slots; ++sl)
     for (int c = 0; c < 9; ++c) {
       const uint32_t T = h->T[(size_t)sl * 15 + cls[c]];
-      th.v[sl][c] = p.t_has_zero ? T : (T == 0xFFFFFFFFu ? T : T - 1u);
+      th.v[sl][c] = p.t_has_zero ? T : (T == 0xFFFFFFFFu ? 0u : ~(T - 1u));
     }
   return p;
 }
@@ -846,11 +1140,63 @@ void launch_sweep4(const SamplesArgs<uint32_t> &p, const SlotThresholds &th, uns
   }
 }
 
+int fused_red(qisg_handle *h) {
+  SlotThresholds th;
+  const SamplesArgs<uint32_t> a = make_args4(h, 0, th);
+  FusedRedArgs p;
+  p.src = reinterpret_cast<const uint32_t *>(h->spins);
+  p.dst = reinterpret_cast<uint32_t *>(h->spins_alt);
+  p.J = reinterpret_cast<const uint32_t *>(h->J);
+  p.acc = reinterpret_cast<const uint32_t *>(h->d_acc);
+  p.d_t = h->d_t;
+  p.zero_U = h->d_U;
+  p.n_zero_U = a.n_zero_U;
+  p.key = a.key;
+  p.N = h->N;
+  p.L = h->L;
+  p.Lt = h->Lt;
+  p.plane = a.plane;
+  p.n_slots = h->n_slots;
+  p.n_q = h->n_q;
+  p.n_rep = h->n_rep;
+  p.t_has_zero = a.t_has_zero;
+  p.one = 1u;
+  p.all_ones = 0xFFFFFFFFu;
+  // red tile 1: a thread per (site, replica); otherwise a thread per (site, replica quad)
+  const bool per_replica = h->sweep_tile[0] == 1;
+  const int64_t threads_per_set = (int64_t)a.plane * (h->Lt / 2) * (per_replica ? 4 : 1);
+  if (threads_per_set + kBlock4 > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+  p.blocks_per_set = (int)((threads_per_set + kBlock4 - 1) / kBlock4);
+  p.fd_bps = FastDiv((uint32_t)p.blocks_per_set);
+  p.fd_nq = FastDiv((uint32_t)h->n_q);
+  p.fd_plane = FastDiv((uint32_t)a.plane);
+  p.fd_L = FastDiv((uint32_t)h->L);
+  const int64_t blocks = h->n_b * h->n_q * p.blocks_per_set;
+  if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+  const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
+  if (per_replica)
+    samples_red_fused_kernel<<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+  else
+    samples_red_fused4_kernel<<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+  prof_end(h, QISG_KERNEL_SWEEP, tok);
+  h->launches++;
+  std::swap(h->spins, h->spins_alt);
+  h->perm_pending = false;
+  return cuda_check(cudaGetLastError(), "samples red pass");
+}
+
 template <typename Word>
 int half_sweep_t(qisg_handle *h, int colour, int count_only) {
+  if (sizeof(Word) == 4 && h->fused && colour == 0 && !count_only) return fused_red(h);
   if (sizeof(Word) == 4) {
     SlotThresholds th;
     SamplesArgs<uint32_t> p = make_args4(h, colour, th);
+    if (h->fused && colour == 1) {   // the fused red pass read the masks: clear them here
+      p.n_zero_U = 0;
+    } else if (colour == 1) {
+      p.n_zero_U = 0;
+      p.n_zero_acc = 0;
+    }
     const int64_t blocks = h->n_b * h->n_slots * h->n_q * p.blocks_per_set;
     if (blocks > 0x7FFFFFFF || (int64_t)p.blocks_per_set * kBlock4 > 0x7FFFFFFF)
       return fail(QISG_EINVAL, "lattice too large for one launch");
@@ -884,13 +1230,38 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
 }
 
 template <typename Word>
+int clear_masks(qisg_handle *h) {
+  return cuda_check(cudaMemsetAsync(h->d_acc, 0, (size_t)h->n_b * h->n_rep * h->n_slots * sizeof(Word), h->stream),
+                    "clear PT masks");
+}
+
+template <typename Word>
+int permute_t(qisg_handle *h, int advance);
+
+// PT pass.  Fused mode (W = 32), sweep pass: the exchanges stay pending in
+// the masks for the next red pass, and the PT kernel advances the sweep
+// counter.  Otherwise (and for an explicit pass) the lattice is permuted now.
+template <typename Word>
 int pt_t(qisg_handle *h, int explicit_pass, int advance) {
   int rc = QISG_OK;
-  if (explicit_pass)   // the masks are cleared by the red pass of a sweep only
-    rc = cuda_check(cudaMemsetAsync(h->d_acc, 0, (size_t)h->n_b * h->n_rep * h->n_slots * sizeof(Word), h->stream),
-                    "clear PT masks");
-  if (!rc) rc = pt_pass(h, explicit_pass, 0, h->n_samples);
+  if (explicit_pass || h->perm_pending) {   // masks still set: apply them first
+    rc = samples_materialize(h);
+    if (!rc) rc = clear_masks<Word>(h);
+  }
   if (rc) return rc;
+  if (h->fused && !explicit_pass) {
+    rc = pt_pass(h, 0, 0, h->n_samples, advance ? h->d_t : nullptr);
+    if (!rc) h->perm_pending = true;
+    return rc;
+  }
+  rc = pt_pass(h, explicit_pass, 0, h->n_samples, nullptr);
+  if (!rc) rc = permute_t<Word>(h, advance);
+  if (!rc && h->fused) rc = clear_masks<Word>(h);
+  return rc;
+}
+
+template <typename Word>
+int permute_t(qisg_handle *h, int advance) {
   const int tok = prof_begin(h, QISG_KERNEL_PERMUTE);
   unsigned long long *adv = advance ? h->d_t : nullptr;
   if (sizeof(Word) == 4) {
@@ -921,6 +1292,8 @@ int pt_t(qisg_handle *h, int explicit_pass, int advance) {
 
 template <typename Word>
 int measure_t(qisg_handle *h, int force_to_q) {
+  int rc0 = samples_materialize(h);
+  if (rc0) return rc0;
   const int n_pairs = h->n_pairs();
   if (n_pairs > 0) {
     const int spt = 16;
@@ -960,8 +1333,10 @@ template <typename Word>
 int get_spins_t(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
   const int64_t n = n_a * h->n_rep * h->n_slots * h->N;
   if (n == 0) return QISG_OK;
+  int rc = samples_materialize(h);
+  if (rc) return rc;
   int8_t *d = nullptr;
-  int rc = cuda_check(cudaMalloc(&d, (size_t)n), "cudaMalloc");
+  rc = cuda_check(cudaMalloc(&d, (size_t)n), "cudaMalloc");
   if (rc) return rc;
   samples_extract_kernel<Word><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
       reinterpret_cast<const Word *>(h->spins), h->d_walker, d, a_lo, n_a, h->N, h->n_slots, h->n_q,
@@ -976,6 +1351,11 @@ int get_spins_t(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
 template <typename Word>
 int set_spins_t(qisg_handle *h, const int8_t *S, const int32_t *walker_at) {
   constexpr int W = (int)sizeof(Word) * 8;
+  if (h->perm_pending) {   // the new state replaces the one the masks refer to
+    const int rc = clear_masks<Word>(h);
+    if (rc) return rc;
+    h->perm_pending = false;
+  }
   const size_t words = (size_t)h->n_b * h->n_slots * h->n_q * h->N * 4;
   std::vector<Word> buf(words, Word(0));
   for (int64_t a = 0; a < h->n_samples; ++a) {
@@ -1049,6 +1429,13 @@ int samples_init(qisg_handle *h) {
   if (h->n_slots > kMaxSlotsPermute) return fail(QISG_EINVAL, "SAMPLES packing supports up to 32 slots");
   if (h->L > 1024) return fail(QISG_EINVAL, "SAMPLES packing supports L <= 1024");
   return h->W == 64 ? init_t<unsigned long long>(h) : init_t<unsigned int>(h);
+}
+int samples_materialize(qisg_handle *h) {
+  if (!h->fused || !h->perm_pending) return QISG_OK;
+  int rc = permute_t<unsigned int>(h, 0);
+  if (!rc) rc = clear_masks<unsigned int>(h);
+  if (!rc) h->perm_pending = false;
+  return rc;
 }
 int samples_half_sweep(qisg_handle *h, int colour, int count_only) {
   return h->W == 64 ? half_sweep_t<unsigned long long>(h, colour, count_only)
