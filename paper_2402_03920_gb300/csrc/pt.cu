@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsign
   const int64_t a = (int64_t)b * W + 8 * o + v;
   uint32_t acc = 0;
   if (a < n_samples) {
-    const uint32_t t = (uint32_t)(explicit_pass ? *d_t - 1ull : *d_t);
+    const uint32_t t = (uint32_t)(adv ? adv[1] : explicit_pass ? *d_t - 1ull : *d_t);
     acc = pt_chain<true, false, WIDE>(walker + (a * n_rep + r) * n_slots, U + (a * n_rep + r) * n_slots * 2, ptc,
                                       sq, key, t, a, r, n_slots);
   }
@@ -71,16 +71,9 @@ __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsign
         atomicOr(reinterpret_cast<unsigned int *>(&out[s]), (unsigned int)m);
     }
   }
-  // advance the sweep counter once every block has read it (all reads of
-  // this block precede the barrier above); adv[1] counts arrived blocks
-  if (adv && threadIdx.x == 0) {
-    unsigned int *arrived = reinterpret_cast<unsigned int *>(adv + 1);
-    __threadfence();
-    if (atomicAdd(arrived, 1u) == gridDim.x - 1) {
-      *arrived = 0u;
-      *adv += 1ull;
-    }
-  }
+  // advance: the pass read t from adv[1] (the blue pass's copy); no block
+  // reads adv[0], so block 0 sets it to t + 1 for the next sweep
+  if (adv && blockIdx.x == 0 && threadIdx.x == 0) adv[0] = adv[1] + 1ull;
 }
 
 template <typename Word, bool WIDE>

@@ -455,7 +455,7 @@ struct qisg_handle {
   long long *d_sumA = nullptr, *d_sumB = nullptr, *d_sumq = nullptr, *d_sumq2 = nullptr;
   long long *d_q = nullptr;         // overlap scratch [a][s][pair]
   long long *d_out = nullptr;       // output staging [2][a][r][s]
-  unsigned long long *d_t = nullptr;  // sweep counter; d_t[1]: PT blocks that read it (fused mode)
+  unsigned long long *d_t = nullptr;  // sweep counter; d_t[1]: its copy for the PT pass (fused mode)
   void *d_acc = nullptr;            // SAMPLES: PT lane masks of the last pass, Word [b][r][s]
   int *d_err = nullptr;
   size_t device_bytes = 0;

@@ -42,6 +42,7 @@ struct SamplesArgs {
   int blocks_per_set;    // blocks per (b, s, q) word set
   int t_has_zero;        // some threshold of the table is 0 (always reject)
   uint32_t one, all_ones;   // 1 and 0xFFFFFFFF as runtime values (flag_imad)
+  unsigned long long *t_copy;   // blue pass, fused mode: copy t here for the PT pass
   // division by the invariants of the index decomposition (32-bit indices)
   FastDiv fd_bps, fd_nq, fd_ns, fd_plane, fd_L;
   // cleared by the red pass (nothing reads them until the blue pass / PT):
@@ -676,6 +677,7 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
   uint32_t Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
   const uint32_t tau0 = 2u * (uint32_t)G * (uint32_t)seg + (uint32_t)((colour + x + y) & 1);
   const unsigned long long t = *p.d_t;
+  if (p.t_copy && bid == 0 && threadIdx.x == 0) *p.t_copy = t;
   const uint32_t ctr_z = (uint32_t)s | ((uint32_t)q << 16);
   const uint32_t ctr_w = (DOM_SWEEP << 28) | (uint32_t)((b * 32) >> 6);
 
@@ -1068,6 +1070,7 @@ SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
   p.fd_ns = FastDiv((uint32_t)p.n_slots);
   p.fd_plane = FastDiv((uint32_t)p.plane);
   p.fd_L = FastDiv((uint32_t)p.L);
+  p.t_copy = nullptr;
   return p;
 }
 
@@ -1193,6 +1196,7 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
     SamplesArgs<uint32_t> p = make_args4(h, colour, th);
     if (h->fused && colour == 1) {   // the fused red pass read the masks: clear them here
       p.n_zero_U = 0;
+      if (!count_only) p.t_copy = h->d_t + 1;
     } else if (colour == 1) {
       p.n_zero_U = 0;
       p.n_zero_acc = 0;
