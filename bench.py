@@ -55,7 +55,7 @@ def parse():
                    help="other workloads measured beside the headline (empty: none)")
     p.add_argument("--serving-requests", type=int, default=100)
     p.add_argument("--tiles", default="",
-                   help="pin the sweep schedule 'red,blue,prefetch_red,prefetch_blue' instead of autotuning")
+                   help="pin the sweep schedule 'red_tile,blue_tile,red_variant,blue_variant' instead of autotuning")
     return p.parse_args()
 
 
@@ -480,8 +480,8 @@ def run_gpu(args):
                    "measure_every": w.measure_every, "form": main,
                    "layout": "SAMPLES" if layout == qisg.QISG_LAYOUT_SAMPLES else "LANES",
                    "word_bits": wb,
-                   "sweep_schedule": {"tiles": list(TUNED.get(main, ((0, 0), (1, 1)))[0]),
-                                      "prefetch": list(TUNED.get(main, ((0, 0), (1, 1)))[1]),
+                   "sweep_schedule": {"tiles": list(TUNED.get(main, ((0, 0), (0, 0)))[0]),
+                                      "variants": list(TUNED.get(main, ((0, 0), (0, 0)))[1]),
                                       "how": "pinned" if TILES else "autotuned (untimed)"},
                    "l2": "flushed between steps (2x L2 buffer written); lattice fits in L2 within a step"},
         "gpu_launches": launches,
@@ -555,7 +555,7 @@ def main():
     if args.tiles:
         TILES = [int(v) for v in args.tiles.split(",")]
         if len(TILES) != 4:
-            raise SystemExit("--tiles wants red,blue,prefetch_red,prefetch_blue")
+            raise SystemExit("--tiles wants red_tile,blue_tile,red_variant,blue_variant")
     if args.impl == "reference":
         run_reference(args)
     else:

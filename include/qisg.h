@@ -219,25 +219,27 @@ int qisg_profile_read(qisg_handle *h, int kind, double *total_ms, int64_t *n_tim
  * the same either way. */
 int qisg_set_graphs(qisg_handle *h, int enable);
 
-/* Choose the SAMPLES sweep tiles (sites per thread along tau for 32-bit
- * words, site groups of 4 per thread quad for 64-bit words; 1, 2, ..., 64)
- * and, for 32-bit words, whether each pass prefetches the next site, by
- * timing sweeps_per_candidate real sweeps per candidate on the handle's own
- * state; the red and blue passes are timed and tuned separately.  The
- * simulation advances by C * (1 + sweeps_per_candidate) sweeps meanwhile,
- * C = 14 candidates for 32-bit words and 7 for 64-bit words (results never
- * depend on the tile, so the trajectory is the one an untuned run would
- * follow).  chosen: the blue pass's tile (0 for LANES, which has nothing to
- * tune).  Synchronises. */
+/* Choose the SAMPLES sweep schedule by timing sweeps_per_candidate real
+ * sweeps per candidate on the handle's own state; the red and blue passes are
+ * timed and tuned separately.  Candidates: tiles 1, 2, ..., 64 and, for
+ * 32-bit words, both kernel variants of each.  The tile is, for 64-bit words,
+ * the site groups of 4 each thread walks along tau; for 32-bit words it
+ * selects the red pass's threads per site (1: four, 2: two, else one) and the
+ * blue pass's sites per thread (variant 0, a thread per replica quad) or site
+ * groups of 4 per thread (variant 1, a thread per replica).  The simulation
+ * advances by C * (1 + sweeps_per_candidate) sweeps meanwhile, C = 14
+ * candidates for 32-bit words and 7 for 64-bit words (results never depend on
+ * the schedule, so the trajectory is the one an untuned run would follow).
+ * chosen: the blue pass's tile (0 for LANES, which has nothing to tune).
+ * Synchronises. */
 int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen);
 
-/* Read or pin the SAMPLES sweep schedule: tile[c] and prefetch[c] of the red
- * (c = 0) and blue (c = 1) pass, as qisg_autotune chooses them (tile 0 = the
- * default choice; prefetch is 0 or 1 and only matters for 32-bit words).
- * Results never depend on the schedule.  EINVAL: tile outside 0..64 or not
- * a power of two. */
-int qisg_get_tiles(qisg_handle *h, int tile[2], int prefetch[2]);
-int qisg_set_tiles(qisg_handle *h, const int tile[2], const int prefetch[2]);
+/* Read or pin the SAMPLES sweep schedule: tile[c] and variant[c] of the red
+ * (c = 0) and blue (c = 1) pass as qisg_autotune chooses them (tile 0 = the
+ * default; variant 0 or 1).  Results never depend on the schedule.  EINVAL:
+ * tile outside 0..64 or not a power of two, variant not 0 or 1. */
+int qisg_get_tiles(qisg_handle *h, int tile[2], int variant[2]);
+int qisg_set_tiles(qisg_handle *h, const int tile[2], const int variant[2]);
 
 /* Block until the handle's stream is idle; reports any device error flag. */
 int qisg_sync(qisg_handle *h);

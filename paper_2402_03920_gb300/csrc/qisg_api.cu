@@ -593,8 +593,8 @@ int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
     if (chosen) *chosen = 0;
     return QISG_OK;
   }
-  // candidates: tiles 1, 2, ..., 64, and for W = 32 each with and without the
-  // prefetch; the red and blue passes are timed apart and tuned apart
+  // candidates: tiles 1, 2, ..., 64, and for W = 32 each with both kernel
+  // variants; the red and blue passes are timed apart and tuned apart
   const int n_tiles = 7, n_cand = h->W == 32 ? 2 * n_tiles : n_tiles;
   float best_ms[2] = {0.f, 0.f};
   int best[2] = {0, 0};
@@ -604,9 +604,9 @@ int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
   const bool graphs = h->use_graphs;
   h->use_graphs = false;
   for (int c = 0; c < n_cand && !rc; ++c) {
-    const int tile = 1 << (c % n_tiles), nopf = c / n_tiles;
+    const int tile = 1 << (c % n_tiles), variant = c / n_tiles;
     h->sweep_tile[0] = h->sweep_tile[1] = tile;
-    h->sweep_nopf[0] = h->sweep_nopf[1] = nopf;
+    h->sweep_variant[0] = h->sweep_variant[1] = variant;
     rc = one_sweep(h);   // warm the candidate
     float ms[2] = {0.f, 0.f};
     for (int i = 0; i < sweeps_per_candidate && !rc; ++i) {
@@ -630,32 +630,32 @@ int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
   if (rc) return rc;
   for (int col = 0; col < 2; ++col) {
     h->sweep_tile[col] = 1 << ((best[col] - 1) % n_tiles);
-    h->sweep_nopf[col] = (best[col] - 1) / n_tiles;
+    h->sweep_variant[col] = (best[col] - 1) / n_tiles;
   }
   drop_cycle(h);
   if (chosen) *chosen = h->sweep_tile[1];
   return QISG_OK;
 }
 
-int qisg_get_tiles(qisg_handle *h, int tile[2], int prefetch[2]) {
-  if (!h || !tile || !prefetch) return fail(QISG_EINVAL, "NULL argument");
+int qisg_get_tiles(qisg_handle *h, int tile[2], int variant[2]) {
+  if (!h || !tile || !variant) return fail(QISG_EINVAL, "NULL argument");
   for (int c = 0; c < 2; ++c) {
     tile[c] = h->sweep_tile[c];
-    prefetch[c] = h->sweep_nopf[c] ? 0 : 1;
+    variant[c] = h->sweep_variant[c];
   }
   return QISG_OK;
 }
 
-int qisg_set_tiles(qisg_handle *h, const int tile[2], const int prefetch[2]) {
-  if (!h || !tile || !prefetch) return fail(QISG_EINVAL, "NULL argument");
+int qisg_set_tiles(qisg_handle *h, const int tile[2], const int variant[2]) {
+  if (!h || !tile || !variant) return fail(QISG_EINVAL, "NULL argument");
   for (int c = 0; c < 2; ++c)
-    if (tile[c] < 0 || tile[c] > 64 || (tile[c] & (tile[c] - 1)) || (prefetch[c] != 0 && prefetch[c] != 1))
-      return fail(QISG_EINVAL, "tile must be 0 or a power of two up to 64, prefetch 0 or 1");
+    if (tile[c] < 0 || tile[c] > 64 || (tile[c] & (tile[c] - 1)) || (variant[c] != 0 && variant[c] != 1))
+      return fail(QISG_EINVAL, "tile must be 0 or a power of two up to 64, variant 0 or 1");
   int rc = sync_handle(h);
   if (rc) return rc;
   for (int c = 0; c < 2; ++c) {
     h->sweep_tile[c] = tile[c];
-    h->sweep_nopf[c] = prefetch[c] ? 0 : 1;
+    h->sweep_variant[c] = variant[c];
   }
   drop_cycle(h);
   return QISG_OK;

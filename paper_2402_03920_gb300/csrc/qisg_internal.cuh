@@ -412,13 +412,15 @@ struct qisg_handle {
   int64_t launches = 0;
   int device = 0;
   int n_sm = 0;
-  // SAMPLES sweep tile per colour (red, blue): sites per thread along tau
-  // (W = 32) or site groups of 4 per thread quad (W = 64), 0 = choose; the
-  // default grid aims at sweep_min_blocks_per_sm blocks of 256 threads per
-  // SM.  sweep_nopf: W = 32 kernel without the next-site prefetch (fewer
-  // registers).  None of these change results.
+  // SAMPLES sweep schedule per colour (red, blue); none of it changes results.
+  // tile: W = 64 and the W = 32 column walk: site groups of 4 per thread
+  // quad; W = 32 replica-quad kernel: sites per thread along tau; W = 32
+  // red pass: threads per site (1: four, 2: two, else one); 0 = default.
+  // variant (W = 32 blue pass): 0 the replica-quad kernel, 1 the column walk.
+  // The default grid aims at sweep_min_blocks_per_sm blocks of 256 threads
+  // per SM.
   int sweep_tile[2] = {0, 0};
-  int sweep_nopf[2] = {0, 0};
+  int sweep_variant[2] = {0, 0};
   int sweep_min_blocks_per_sm = 4;
 
   // host tables (FP64, built once)

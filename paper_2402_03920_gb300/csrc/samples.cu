@@ -65,6 +65,102 @@ __device__ __forceinline__ Word rho_ge(uint32_t R, uint32_t T) {
   return ones_if<Word>(T != 0xFFFFFFFFu && R >= T);
 }
 
+// Reject thresholds per slot for the classes (u_t = 0: u_s = 0..4),
+// (u_t = 1: u_s = 0, 1), (u_t = 2: u_s = 0, 1), in the form reject_mask
+// reads them.
+struct SlotThresholds {
+  uint32_t v[kMaxSlotsPT][9];
+};
+
+// Reject flag on the integer multiply-add pipe (leaving the logic pipe to
+// the bit-sliced arithmetic): with K = ~(T - 1) (K = 0 for the sentinel),
+// R + K >= 2^32 iff R > T - 1, so the high word of the 64-bit R * 1 + K is
+// the flag and its product with 0xFFFFFFFF the mask.  one and all_ones are
+// the runtime values 1 and 0xFFFFFFFF (kernel parameters, so the compiler
+// keeps the multiplies).
+__device__ __forceinline__ uint32_t flag_imad(uint32_t R, uint32_t K, uint32_t one, uint32_t all_ones) {
+  unsigned long long v;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(v) : "r"(R), "r"(one), "l"((unsigned long long)K));
+  uint32_t m;
+  asm("mul.lo.u32 %0, %1, %2;" : "=r"(m) : "r"((uint32_t)(v >> 32)), "r"(all_ones));
+  return m;
+}
+
+// HAS_ZERO: th holds T and the flags are T != sentinel && R >= T; else th
+// holds K = ~(T - 1) (0 for the sentinel) for flag_imad.
+template <bool HAS_ZERO>
+__device__ __forceinline__ uint32_t reject_mask(uint32_t R, const uint32_t *th, uint32_t us0, uint32_t us1,
+                                                uint32_t us2, uint32_t ut0, uint32_t ut1, uint32_t one,
+                                                uint32_t all_ones) {
+#define QISG_F(c) (HAS_ZERO ? rho_ge<uint32_t>(R, th[c]) : flag_imad(R, th[c], one, all_ones))
+  const uint32_t row0 = mux(us2, QISG_F(4), mux(us1, mux(us0, QISG_F(3), QISG_F(2)), mux(us0, QISG_F(1), QISG_F(0))));
+  const uint32_t low = ~(us1 | us2);
+  const uint32_t row1 = low & mux(us0, QISG_F(6), QISG_F(5));
+  const uint32_t row2 = low & mux(us0, QISG_F(8), QISG_F(7));
+#undef QISG_F
+  return mux(ut1, row2, mux(ut0, row1, row0));
+}
+
+// Per-replica-class sum of the block's counters: thread (quad, j) holds
+// counter c of replica j; the 64 quads' counters of each replica are summed
+// by a tree in shared memory (vertical adds, W lanes per operation) and lane
+// l of replica j's total is added to out[j * W + l].
+template <typename Word, int K>
+__device__ __forceinline__ void quad_sum_counters(const VCount<Word, K> &c, Word *buf, int *out) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  constexpr int NQ = kQuads, LOG = 6;   // 64 quads per block
+  constexpr int KF = K + LOG;
+  static_assert((1 << LOG) == NQ, "quads per block");
+  const int j = threadIdx.x & 3, quad = threadIdx.x >> 2;
+#pragma unroll
+  for (int i = 0; i < K; ++i) buf[(j * KF + i) * NQ + quad] = c.p[i];
+  __syncthreads();
+#pragma unroll
+  for (int lvl = 0; lvl < LOG; ++lvl) {
+    const int half = NQ >> (lvl + 1);
+    for (int w = threadIdx.x; w < 4 * half; w += blockDim.x) {
+      const int g = w / half, e = w - g * half;
+      Word *a = buf + (size_t)g * KF * NQ + e;
+      Word carry = 0;
+#pragma unroll
+      for (int i = 0; i < K + lvl; ++i) {
+        const Word x = a[i * NQ], y = a[i * NQ + half];
+        a[i * NQ] = x ^ y ^ carry;
+        carry = maj3(x, y, carry);
+      }
+      a[(K + lvl) * NQ] = carry;
+    }
+    __syncthreads();
+  }
+  for (int w = threadIdx.x; w < 4 * W; w += blockDim.x) {
+    const int g = w / W, l = w - g * W;
+    int v = 0;
+#pragma unroll
+    for (int i = 0; i < KF; ++i) v |= (int)((buf[(g * KF + i) * NQ] >> l) & 1u) << i;
+    out[w] = v;
+  }
+  __syncthreads();   // buf is reused by the caller
+}
+
+// Reject mask of one word for class planes (us, ut): the flags are 32-bit
+// masks (flag_imad), widened for 64-bit words.
+template <typename Word, bool HAS_ZERO>
+__device__ __forceinline__ Word reject_word(uint32_t R, const uint32_t *th, Word us0, Word us1, Word us2, Word ut0,
+                                            Word ut1, uint32_t one, uint32_t all_ones) {
+  auto f = [&](int c) -> Word {
+    const uint32_t m = HAS_ZERO ? (uint32_t)rho_ge<uint32_t>(R, th[c]) : flag_imad(R, th[c], one, all_ones);
+    if constexpr (sizeof(Word) == 8)
+      return ((Word)m << 32) | (Word)m;
+    else
+      return (Word)m;
+  };
+  const Word row0 = mux(us2, f(4), mux(us1, mux(us0, f(3), f(2)), mux(us0, f(1), f(0))));
+  const Word low = ~(us1 | us2);
+  const Word row1 = low & mux(us0, f(6), f(5));
+  const Word row2 = low & mux(us0, f(8), f(7));
+  return mux(ut1, row2, mux(ut0, row1, row0));
+}
+
 // One half sweep, column walk.  Block: one (b, s, q) word set; quad thread j
 // owns replica r = 4q + j.  Quad k owns one (x, y) column and a segment of
 // G sites of the colour along tau (tau = tau0, tau0 + 2, ...; tau0 = 2 G seg
@@ -72,17 +168,19 @@ __device__ __forceinline__ Word rho_ge(uint32_t R, uint32_t T) {
 // stay in registers and the word at tau - 1 is the previous step's tau + 1.
 // Per group of 4 steps every thread of a quad computes one Philox call (for
 // step 4g + j), which serves the four replicas of that site; the results are
-// exchanged in shared memory.  G2 = ceil(log2(G / 4)) sizes the per-thread
-// energy counters.
+// exchanged in shared memory.  The thresholds of the slot come from the
+// parameter bank.  G2 = ceil(log2(G / 4)) sizes the per-thread energy
+// counters, summed per replica by a tree in shared memory.
 template <typename Word, bool BLUE, int G2>
-__global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<Word> p, int colour,
-                                                                    int count_only) {
+__global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<Word> p,
+                                                                    const __grid_constant__ SlotThresholds th,
+                                                                    int colour, int count_only) {
   constexpr int W = (int)sizeof(Word) * 8;
   constexpr int KS = G2 + 5;   // u_s sum <= 4 * 4 * 2^G2 per thread
   constexpr int KT = G2 + 4;   // u_t sum <= 2 * 4 * 2^G2 per thread
   __shared__ uint4 rnd[kBlock];   // one Philox call per thread and group of 4 steps
-  __shared__ uint32_t Ts[16];
-  __shared__ int accU[BLUE ? 2 * 4 * 64 : 1];
+  __shared__ Word buf[BLUE ? 4 * (KS + 6) * kQuads : 1];
+  __shared__ int accU[BLUE ? 2 * 4 * W : 1];
 
   const uint32_t bid = blockIdx.x;
   const uint32_t set = p.fd_bps.div(bid);
@@ -94,25 +192,13 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
   const int j = threadIdx.x & 3;
   const int quad = threadIdx.x >> 2;
   const int r = 4 * q + j;
-
-  if (threadIdx.x < 15) {
-    const uint32_t T = p.T[s * 15 + threadIdx.x];
-    // with no zero threshold: reject iff R > T - 1 (the sentinel stays)
-    Ts[threadIdx.x] = p.t_has_zero ? T : (T == 0xFFFFFFFFu ? T : T - 1u);
-  }
-  if (BLUE)
-    for (int i = threadIdx.x; i < 2 * 4 * W; i += blockDim.x) accU[i] = 0;
-  if (!BLUE) {
+  {   // counters / masks the host asked this pass to clear
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_acc; i += stride)
       p.zero_acc[i] = 0;
   }
-  __syncthreads();
-
-  uint32_t T[15];
-#pragma unroll
-  for (int i = 0; i < 15; ++i) T[i] = Ts[i];
+  const uint32_t *T = th.v[s];
   const bool has_zero = p.t_has_zero != 0;
 
   const int L = p.L, plane = p.plane, G = p.seg_sites;
@@ -137,6 +223,7 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
 
   Word *base = p.spins + ((b * p.n_slots + s) * p.n_q + q) * p.N * 4 + j;
   const unsigned long long t = *p.d_t;
+  if (p.t_copy && bid == 0 && threadIdx.x == 0) *p.t_copy = t;
   const uint32_t ctr_z = (uint32_t)s | ((uint32_t)(r >> 2) << 16);
   const uint32_t ctr_w = (DOM_SWEEP << 28) | (uint32_t)((b * W) >> 6);
 
@@ -213,25 +300,12 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
         // reject mask: mux tree over (u_t, u_s) of the per-class flags;
         // classes with u_s >= 2 and u_t >= 1 always accept
         Word rej;
-        if (count_only) {
+        if (count_only)
           rej = ~Word(0);
-        } else if (!has_zero) {
-          const Word row0 = mux(us2, rho_gt<Word>(R, T[12]),
-                                mux(us1, mux(us0, rho_gt<Word>(R, T[9]), rho_gt<Word>(R, T[6])),
-                                    mux(us0, rho_gt<Word>(R, T[3]), rho_gt<Word>(R, T[0]))));
-          const Word low = ~(us1 | us2);
-          const Word row1 = low & mux(us0, rho_gt<Word>(R, T[4]), rho_gt<Word>(R, T[1]));
-          const Word row2 = low & mux(us0, rho_gt<Word>(R, T[5]), rho_gt<Word>(R, T[2]));
-          rej = mux(ut1, row2, mux(ut0, row1, row0));
-        } else {
-          const Word row0 = mux(us2, rho_ge<Word>(R, T[12]),
-                                mux(us1, mux(us0, rho_ge<Word>(R, T[9]), rho_ge<Word>(R, T[6])),
-                                    mux(us0, rho_ge<Word>(R, T[3]), rho_ge<Word>(R, T[0]))));
-          const Word low = ~(us1 | us2);
-          const Word row1 = low & mux(us0, rho_ge<Word>(R, T[4]), rho_ge<Word>(R, T[1]));
-          const Word row2 = low & mux(us0, rho_ge<Word>(R, T[5]), rho_ge<Word>(R, T[2]));
-          rej = mux(ut1, row2, mux(ut0, row1, row0));
-        }
+        else if (!has_zero)
+          rej = reject_word<Word, false>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
+        else
+          rej = reject_word<Word, true>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
         const Word flip = ~rej;
         if (!count_only) base[(size_t)site * 4] = sc ^ flip;
         if (BLUE) {
@@ -248,9 +322,8 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
   }
 
   if (BLUE) {
-    flush_counter<Word, KS, 4>(cs, accU);
-    flush_counter<Word, KT, 4>(ct, accU + 4 * W);
-    __syncthreads();
+    quad_sum_counters<Word, KS>(cs, buf, accU);
+    quad_sum_counters<Word, KT>(ct, buf, accU + 4 * W);
     for (int i = threadIdx.x; i < 4 * W; i += blockDim.x) {
       const int jj = i / W, lane = i - jj * W;
       const int rr = 4 * q + jj;
@@ -276,42 +349,6 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
 // memory (vertical adds, 32 lanes per operation) instead of warp shuffles.
 constexpr int kBlock4 = 128;
 constexpr int kLog2Block4 = 7;
-
-// Reject thresholds per slot for the classes (u_t = 0: u_s = 0..4),
-// (u_t = 1: u_s = 0, 1), (u_t = 2: u_s = 0, 1), in the form reject_mask
-// reads them.
-struct SlotThresholds {
-  uint32_t v[kMaxSlotsPT][9];
-};
-
-// Reject flag on the integer multiply-add pipe (leaving the logic pipe to
-// the bit-sliced arithmetic): with K = ~(T - 1) (K = 0 for the sentinel),
-// R + K >= 2^32 iff R > T - 1, so the high word of the 64-bit R * 1 + K is
-// the flag and its product with 0xFFFFFFFF the mask.  one and all_ones are
-// the runtime values 1 and 0xFFFFFFFF (kernel parameters, so the compiler
-// keeps the multiplies).
-__device__ __forceinline__ uint32_t flag_imad(uint32_t R, uint32_t K, uint32_t one, uint32_t all_ones) {
-  unsigned long long v;
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(v) : "r"(R), "r"(one), "l"((unsigned long long)K));
-  uint32_t m;
-  asm("mul.lo.u32 %0, %1, %2;" : "=r"(m) : "r"((uint32_t)(v >> 32)), "r"(all_ones));
-  return m;
-}
-
-// HAS_ZERO: th holds T and the flags are T != sentinel && R >= T; else th
-// holds K = ~(T - 1) (0 for the sentinel) for flag_imad.
-template <bool HAS_ZERO>
-__device__ __forceinline__ uint32_t reject_mask(uint32_t R, const uint32_t *th, uint32_t us0, uint32_t us1,
-                                                uint32_t us2, uint32_t ut0, uint32_t ut1, uint32_t one,
-                                                uint32_t all_ones) {
-#define QISG_F(c) (HAS_ZERO ? rho_ge<uint32_t>(R, th[c]) : flag_imad(R, th[c], one, all_ones))
-  const uint32_t row0 = mux(us2, QISG_F(4), mux(us1, mux(us0, QISG_F(3), QISG_F(2)), mux(us0, QISG_F(1), QISG_F(0))));
-  const uint32_t low = ~(us1 | us2);
-  const uint32_t row1 = low & mux(us0, QISG_F(6), QISG_F(5));
-  const uint32_t row2 = low & mux(us0, QISG_F(8), QISG_F(7));
-#undef QISG_F
-  return mux(ut1, row2, mux(ut0, row1, row0));
-}
 
 struct Quad4 {
   uint4 c, up, xp, xm, yp, ym;
@@ -481,12 +518,34 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedR
   }
 }
 
-// The same pass with one thread per red site and replica quad: 16-byte slot
-// words (the site's four replica words), one Philox call per slot for the
-// four draws.  Fewer threads, fewer instructions per word; the autotuner
-// picks between the two forms (results are identical).
-__global__ void __launch_bounds__(kBlock4) samples_red_fused4_kernel(const FusedRedArgs p,
+// The same pass with one thread per red site and RP of its four replicas
+// (RP = 4: the site's 16-byte replica quad; RP = 2: two threads per site,
+// 8 bytes each, sharing the Philox calls of the quad's draws through a
+// shuffle: the even thread draws even slots, the odd thread odd ones).
+// Fewer threads and instructions per word than the per-replica form; the
+// autotuner picks the form (results are identical).
+template <int RP>
+__device__ __forceinline__ void ld_rp(uint32_t (&d)[RP], const uint32_t *p) {
+  if constexpr (RP == 4) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(p);
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+  } else {
+    const uint2 v = *reinterpret_cast<const uint2 *>(p);
+    d[0] = v.x; d[1] = v.y;
+  }
+}
+template <int RP>
+__device__ __forceinline__ void st_rp(uint32_t *p, const uint32_t (&d)[RP]) {
+  if constexpr (RP == 4)
+    *reinterpret_cast<uint4 *>(p) = make_uint4(d[0], d[1], d[2], d[3]);
+  else
+    *reinterpret_cast<uint2 *>(p) = make_uint2(d[0], d[1]);
+}
+
+template <int RP>
+__global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const FusedRedArgs p,
                                                                       const __grid_constant__ SlotThresholds th) {
+  constexpr int TPS = 4 / RP;   // threads per site
   __shared__ __align__(16) uint32_t msk[kMaxSlotsPT][4];
   const uint32_t bid = blockIdx.x;
   const uint32_t set = p.fd_bps.div(bid);   // (b, q)
@@ -505,9 +564,11 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused4_kernel(const Fused
   }
   __syncthreads();
 
-  const uint32_t quad = chunk * (uint32_t)kBlock4 + threadIdx.x;   // red site of the (b, q) set
+  const uint32_t tid = chunk * (uint32_t)kBlock4 + threadIdx.x;
+  const int h = TPS == 1 ? 0 : (int)(tid & 1u);   // which replica pair (RP = 2)
+  const uint32_t quad = tid / TPS;                // red site of the (b, q) set
   const uint32_t P = (uint32_t)p.plane, Lt = (uint32_t)p.Lt, L = (uint32_t)p.L;
-  if (quad >= P * (Lt / 2)) return;
+  const bool live = quad < P * (Lt / 2);          // uniform per site (pairs share a site)
   const uint32_t seg = p.fd_plane.div(quad);
   const uint32_t i2 = quad - seg * P;
   const uint32_t y = p.fd_L.div(i2), x = i2 - y * L;
@@ -515,67 +576,109 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused4_kernel(const Fused
   const uint32_t ixp = (x + 1 == L ? 0 : x + 1) + L * y, ixm = (x == 0 ? L - 1 : x - 1) + L * y;
   const uint32_t iyp = x + L * (y + 1 == L ? 0 : y + 1), iym = x + L * (y == 0 ? L - 1 : y - 1);
   const uint32_t off = tau * P;
-  uint32_t z[7];
-  z[0] = i2 + off;
-  z[1] = i2 + (tau + 1 == Lt ? 0u : off + P);
-  z[2] = i2 + (tau == 0 ? (Lt - 1) * P : off - P);
-  z[3] = ixp + off;
-  z[4] = ixm + off;
-  z[5] = iyp + off;
-  z[6] = iym + off;
-  // 16-byte word of site zz at slot sl: slot base (uniform) + zz
-  const int64_t base = ((int64_t)b * n * p.n_q + q) * p.N;
-  const int64_t SS = (int64_t)p.n_q * p.N;
-  const uint4 *sb = reinterpret_cast<const uint4 *>(p.src) + base;
-  uint4 *db = reinterpret_cast<uint4 *>(p.dst) + base;
+  uint32_t zo[7];   // word offsets (u32 units) of the seven sites' replica groups
+  {
+    uint32_t z[7];
+    z[0] = i2 + off;
+    z[1] = i2 + (tau + 1 == Lt ? 0u : off + P);
+    z[2] = i2 + (tau == 0 ? (Lt - 1) * P : off - P);
+    z[3] = ixp + off;
+    z[4] = ixm + off;
+    z[5] = iyp + off;
+    z[6] = iym + off;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) zo[k] = 4 * z[k] + (uint32_t)(RP * h);
+  }
+  const int64_t base = (((int64_t)b * n * p.n_q + q) * p.N) * 4;
+  const int64_t SS = (int64_t)p.n_q * p.N * 4;
+  const uint32_t *sb = p.src + base;
+  uint32_t *db = p.dst + base;
   const uint32_t *Jb = p.J + (int64_t)b * P * 2;
-  const uint32_t Jxp = Jb[2 * i2], Jxm = Jb[2 * ixm], Jyp = Jb[2 * i2 + 1], Jym = Jb[2 * iym + 1];
+  uint32_t Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
   const unsigned long long t = *p.d_t;
   const uint32_t ctr_w = (DOM_SWEEP << 28) | ((b * 32u) >> 6);
+  const uint32_t site = i2 + off;
   const bool has_zero = p.t_has_zero != 0;
-  uint4 cw[7], n1[7];
+  uint32_t cw[7][RP], n1[7][RP];
+  if (live) {
+    Jxp = Jb[2 * i2];
+    Jxm = Jb[2 * ixm];
+    Jyp = Jb[2 * i2 + 1];
+    Jym = Jb[2 * iym + 1];
 #pragma unroll
-  for (int k = 0; k < 7; ++k) cw[k] = sb[z[k]];
-  if (n > 1)
+    for (int k = 0; k < 7; ++k) ld_rp<RP>(cw[k], sb + zo[k]);
+    if (n > 1)
 #pragma unroll
-    for (int k = 0; k < 7; ++k) n1[k] = sb[SS + z[k]];
+      for (int k = 0; k < 7; ++k) ld_rp<RP>(n1[k], sb + SS + zo[k]);
+  }
+  uint4 R4 = make_uint4(0, 0, 0, 0);
   for (int sl = 0; sl < n; ++sl) {
-    uint4 fw[7];
+    // the draws of slot sl (RP = 2: the pair's calls alternate over slots)
+    if constexpr (RP == 4) {
+      if (live) R4 = philox(make_uint4(site, (uint32_t)t, (uint32_t)sl | ((uint32_t)q << 16), ctr_w), p.key);
+    } else {
+      if ((sl & 1) == 0) {
+        const int sm = sl + h;   // this thread's call covers slot sl + h
+        if (live && sm < n) R4 = philox(make_uint4(site, (uint32_t)t, (uint32_t)sm | ((uint32_t)q << 16), ctr_w), p.key);
+      }
+    }
+    uint32_t Rj[RP];
+    if constexpr (RP == 4) {
+      Rj[0] = R4.x; Rj[1] = R4.y; Rj[2] = R4.z; Rj[3] = R4.w;
+    } else {
+      // slot sl's call is held by thread (sl & 1) of the pair; thread h needs
+      // its components 2h, 2h + 1
+      const int owner = sl & 1;
+      const uint32_t give0 = (owner == h) ? (h ? R4.x : R4.z) : 0u;   // partner's components
+      const uint32_t give1 = (owner == h) ? (h ? R4.y : R4.w) : 0u;
+      const uint32_t got0 = __shfl_xor_sync(0xffffffffu, give0, 1);
+      const uint32_t got1 = __shfl_xor_sync(0xffffffffu, give1, 1);
+      if (owner == h) {
+        Rj[0] = h ? R4.z : R4.x;
+        Rj[1] = h ? R4.w : R4.y;
+      } else {
+        Rj[0] = got0;
+        Rj[1] = got1;
+      }
+    }
+    if (!live) continue;
+    uint32_t fw[7][RP];
     if (sl + 1 < n) {
-      uint4 n2[7];
+      uint32_t n2[7][RP];
       if (sl + 2 < n) {
-        const uint4 *ps = sb + (int64_t)(sl + 2) * SS;
+        const uint32_t *ps = sb + (int64_t)(sl + 2) * SS;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) n2[k] = ps[z[k]];
+        for (int k = 0; k < 7; ++k) ld_rp<RP>(n2[k], ps + zo[k]);
       }
-      const uint4 m = *reinterpret_cast<const uint4 *>(msk[sl]);
+      uint32_t m[RP];
 #pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        uint4 xx;
-        xx.x = (cw[k].x ^ n1[k].x) & m.x;
-        xx.y = (cw[k].y ^ n1[k].y) & m.y;
-        xx.z = (cw[k].z ^ n1[k].z) & m.z;
-        xx.w = (cw[k].w ^ n1[k].w) & m.w;
-        fw[k] = make_uint4(cw[k].x ^ xx.x, cw[k].y ^ xx.y, cw[k].z ^ xx.z, cw[k].w ^ xx.w);
-        cw[k] = make_uint4(n1[k].x ^ xx.x, n1[k].y ^ xx.y, n1[k].z ^ xx.z, n1[k].w ^ xx.w);
-        if (sl + 2 < n) n1[k] = n2[k];
-      }
+      for (int jj = 0; jj < RP; ++jj) m[jj] = msk[sl][RP * h + jj];
+#pragma unroll
+      for (int k = 0; k < 7; ++k)
+#pragma unroll
+        for (int jj = 0; jj < RP; ++jj) {
+          const uint32_t xx = (cw[k][jj] ^ n1[k][jj]) & m[jj];
+          fw[k][jj] = cw[k][jj] ^ xx;
+          cw[k][jj] = n1[k][jj] ^ xx;
+          if (sl + 2 < n) n1[k][jj] = n2[k][jj];
+        }
     } else {
 #pragma unroll
-      for (int k = 0; k < 7; ++k) fw[k] = cw[k];
-    }
-    const uint4 R4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)sl | ((uint32_t)q << 16), ctr_w), p.key);
-    const uint32_t *T = th.v[sl];
-    uint32_t f[4];
+      for (int k = 0; k < 7; ++k)
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const uint32_t sc = q4(fw[0], jj);
-      const uint32_t b1 = sc ^ q4(fw[3], jj) ^ Jxp;
-      const uint32_t b2 = sc ^ q4(fw[4], jj) ^ Jxm;
-      const uint32_t b3 = sc ^ q4(fw[5], jj) ^ Jyp;
-      const uint32_t b4 = sc ^ q4(fw[6], jj) ^ Jym;
-      const uint32_t t1 = sc ^ q4(fw[1], jj);
-      const uint32_t t2 = sc ^ q4(fw[2], jj);
+        for (int jj = 0; jj < RP; ++jj) fw[k][jj] = cw[k][jj];
+    }
+    const uint32_t *T = th.v[sl];
+    uint32_t out[RP];
+#pragma unroll
+    for (int jj = 0; jj < RP; ++jj) {
+      const uint32_t sc = fw[0][jj];
+      const uint32_t b1 = sc ^ fw[3][jj] ^ Jxp;
+      const uint32_t b2 = sc ^ fw[4][jj] ^ Jxm;
+      const uint32_t b3 = sc ^ fw[5][jj] ^ Jyp;
+      const uint32_t b4 = sc ^ fw[6][jj] ^ Jym;
+      const uint32_t t1 = sc ^ fw[1][jj];
+      const uint32_t t2 = sc ^ fw[2][jj];
       const uint32_t s1 = b1 ^ b2 ^ b3;
       const uint32_t c1 = maj3(b1, b2, b3);
       const uint32_t us0 = s1 ^ b4;
@@ -584,23 +687,23 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused4_kernel(const Fused
       const uint32_t us2 = c1 & c2;
       const uint32_t ut0 = t1 ^ t2;
       const uint32_t ut1 = t1 & t2;
-      const uint32_t R = q4(R4, jj);
-      const uint32_t rej = has_zero ? reject_mask<true>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones)
-                                    : reject_mask<false>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
-      f[jj] = ~rej;
+      const uint32_t rej = has_zero ? reject_mask<true>(Rj[jj], T, us0, us1, us2, ut0, ut1, p.one, p.all_ones)
+                                    : reject_mask<false>(Rj[jj], T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
+      out[jj] = sc ^ ~rej;
     }
-    uint4 *pd = db + (int64_t)sl * SS;
-    pd[z[0]] = make_uint4(fw[0].x ^ f[0], fw[0].y ^ f[1], fw[0].z ^ f[2], fw[0].w ^ f[3]);
-    pd[z[1]] = fw[1];
+    uint32_t *pd = db + (int64_t)sl * SS;
+    st_rp<RP>(pd + zo[0], out);
+    st_rp<RP>(pd + zo[1], fw[1]);
   }
 }
 
 // Sum the block's per-thread counters (NC counters of K planes in registers)
 // and add lane l of counter c into out[c * 32 + l]: tree over the 128
 // threads in shared memory, one more plane per level.
-template <int K, int NC>
-__device__ __forceinline__ void block_sum_counters(const VCount<uint32_t, K> *cnt, uint32_t *buf, int *out) {
+template <int K, int NC, typename Word = uint32_t>
+__device__ __forceinline__ void block_sum_counters(const VCount<Word, K> *cnt, Word *buf, int *out) {
   constexpr int KF = K + kLog2Block4;
+  constexpr int W = (int)sizeof(Word) * 8;
   const int tid = threadIdx.x;
 #pragma unroll
   for (int c = 0; c < NC; ++c)
@@ -612,11 +715,11 @@ __device__ __forceinline__ void block_sum_counters(const VCount<uint32_t, K> *cn
     const int half = kBlock4 >> (lvl + 1);
     for (int w = tid; w < NC * half; w += kBlock4) {
       const int c = w / half, e = w - c * half;
-      uint32_t *a = buf + (size_t)c * KF * kBlock4 + e;
-      uint32_t carry = 0;
+      Word *a = buf + (size_t)c * KF * kBlock4 + e;
+      Word carry = 0;
 #pragma unroll
       for (int i = 0; i < K + lvl; ++i) {
-        const uint32_t x = a[i * kBlock4], y = a[i * kBlock4 + half];
+        const Word x = a[i * kBlock4], y = a[i * kBlock4 + half];
         a[i * kBlock4] = x ^ y ^ carry;
         carry = maj3(x, y, carry);
       }
@@ -624,8 +727,8 @@ __device__ __forceinline__ void block_sum_counters(const VCount<uint32_t, K> *cn
     }
     __syncthreads();
   }
-  for (int w = tid; w < NC * 32; w += kBlock4) {
-    const int c = w >> 5, l = w & 31;
+  for (int w = tid; w < NC * W; w += kBlock4) {
+    const int c = w / W, l = w - c * W;
     int v = 0;
 #pragma unroll
     for (int i = 0; i < KF; ++i) v |= (int)((buf[(c * KF + i) * kBlock4] >> l) & 1u) << i;
@@ -878,6 +981,98 @@ __global__ void __launch_bounds__(kBlock4) samples_permute4_kernel(uint4 *spins,
     if (s < n_slots) w0[s * stride] = w[s];
 }
 
+// Overlaps (Appendix E.1) of every replica pair at one slot, for up to 4
+// replicas (one replica quad): a thread reads the quad of G sites of one
+// (b, s) once and counts, per pair, the sites where the two configurations
+// differ (per lane, bit-sliced); the block sums its threads' counters (tree
+// in shared memory, in two batches of three pairs) and adds lane a's counts
+// into qcnt[a][s][p].  Pairs p in the order (0,1), (0,2), (0,3), (1,2),
+// (1,3), (2,3) restricted to the replicas present.
+template <typename Word, int K>
+__global__ void __launch_bounds__(kBlock4) samples_overlap4_kernel(const Word *spins, long long *qcnt, int64_t N,
+                                                                    int n_slots, int n_rep, int64_t n_samples,
+                                                                    int sites_per_thread, int blocks_per_set) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  constexpr int KF = K + kLog2Block4;
+  __shared__ Word buf[3 * KF * kBlock4];
+  __shared__ int tot[6 * W];
+  const int64_t set = blockIdx.x / blocks_per_set;   // (b, s)
+  const int chunk = (int)(blockIdx.x - set * blocks_per_set);
+  const int s = (int)(set % n_slots);
+  const int64_t b = set / n_slots;
+  const Word *w0 = spins + (b * n_slots + s) * N * 4;   // n_q = 1
+  VCount<Word, K> c[6];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) c[p].zero();
+  const int64_t start = (int64_t)chunk * kBlock4 * sites_per_thread + threadIdx.x;
+  for (int k = 0; k < sites_per_thread; ++k) {
+    const int64_t site = start + (int64_t)k * kBlock4;
+    if (site >= N) break;
+    Word r[4];
+    if constexpr (sizeof(Word) == 4) {
+      const uint4 v = reinterpret_cast<const uint4 *>(w0)[site];
+      r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+    } else {
+      const ulonglong2 v0 = reinterpret_cast<const ulonglong2 *>(w0)[2 * site];
+      const ulonglong2 v1 = reinterpret_cast<const ulonglong2 *>(w0)[2 * site + 1];
+      r[0] = v0.x; r[1] = v0.y; r[2] = v1.x; r[3] = v1.y;
+    }
+    c[0].add1(r[0] ^ r[1]);
+    c[1].add1(r[0] ^ r[2]);
+    c[2].add1(r[0] ^ r[3]);
+    c[3].add1(r[1] ^ r[2]);
+    c[4].add1(r[1] ^ r[3]);
+    c[5].add1(r[2] ^ r[3]);
+  }
+  block_sum_counters<K, 3, Word>(c, buf, tot);
+  block_sum_counters<K, 3, Word>(c + 3, buf, tot + 3 * W);
+  // the pair index of (x, y) among the replicas present
+  const int n_pairs = n_rep * (n_rep - 1) / 2;
+  for (int w = threadIdx.x; w < 6 * W; w += blockDim.x) {
+    const int pp = w / W, lane = (int)(w - pp * W);
+    const int x = pp < 3 ? 0 : pp < 5 ? 1 : 2;
+    const int y = pp < 3 ? pp + 1 : pp < 5 ? pp - 1 : 3;
+    if (y >= n_rep || !tot[w]) continue;
+    const int p = x * n_rep - x * (x + 1) / 2 + (y - x - 1);
+    const int64_t a = b * W + lane;
+    if (a < n_samples) atomicAdd(reinterpret_cast<unsigned long long *>(&qcnt[(a * n_slots + s) * n_pairs + p]),
+                                 (unsigned long long)tot[w]);
+  }
+}
+
+// Measurement sums (Appendix E.1): one thread per (sample, slot) and item,
+// items = the replicas' (A, B) then the pairs' q = N - 2 (differing sites);
+// to_q_only only converts the counts to q.
+__global__ void samples_finalize2_kernel(const unsigned long long *__restrict__ U, long long *__restrict__ qcnt,
+                                         long long *__restrict__ sumA, long long *__restrict__ sumB,
+                                         long long *__restrict__ sumq, long long *__restrict__ sumq2, int64_t n_a,
+                                         int n_rep, int n_slots, int64_t N, int to_q_only) {
+  const int n_pairs = n_rep * (n_rep - 1) / 2;
+  const int items = n_rep + n_pairs;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n_a * n_slots * items) return;
+  const int it = (int)(g % items);
+  const int64_t as = g / items;   // a * n_slots + s
+  const int64_t a = as / n_slots;
+  const int s = (int)(as - a * n_slots);
+  if (it < n_rep) {
+    if (to_q_only) return;
+    const int64_t c = (a * n_rep + it) * n_slots + s;
+    sumA[c] += 2 * N - 2 * (long long)U[2 * c];
+    sumB[c] += N - 2 * (long long)U[2 * c + 1];
+    return;
+  }
+  long long *qc = &qcnt[as * n_pairs + (it - n_rep)];
+  const long long qv = N - 2 * *qc;
+  if (to_q_only) {
+    *qc = qv;
+    return;
+  }
+  sumq[as * n_pairs + (it - n_rep)] += qv;
+  sumq2[as * n_pairs + (it - n_rep)] += qv * qv;
+  *qc = 0;
+}
+
 // Overlaps (Appendix E.1) at slot s for replica pair p: per-lane number of
 // sites where the two configurations differ, accumulated into qcnt[a][s][p].
 template <typename Word>
@@ -916,36 +1111,6 @@ __global__ void __launch_bounds__(kBlock) samples_overlap_kernel(const Word *spi
     if (a < n_samples && acc[i])
       atomicAdd(reinterpret_cast<unsigned long long *>(&qcnt[(a * n_slots + s) * n_pairs + p]),
                 (unsigned long long)acc[i]);
-  }
-}
-
-__global__ void samples_finalize_kernel(const unsigned long long *U, long long *qcnt, long long *sumA,
-                                        long long *sumB, long long *sumq, long long *sumq2,
-                                        int64_t n_a, int n_rep, int n_slots, int64_t N,
-                                        int to_q_only) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= n_a * n_slots) return;
-  const int64_t a = c / n_slots;
-  const int s = (int)(c % n_slots);
-  const int n_pairs = n_rep * (n_rep - 1) / 2;
-  if (to_q_only) {
-    for (int p = 0; p < n_pairs; ++p) {
-      long long *qc = &qcnt[(a * n_slots + s) * n_pairs + p];
-      *qc = N - 2 * *qc;
-    }
-    return;
-  }
-  for (int r = 0; r < n_rep; ++r) {
-    const unsigned long long *u = U + ((a * n_rep + r) * n_slots + s) * 2;
-    sumA[(a * n_rep + r) * n_slots + s] += 2 * N - 2 * (long long)u[0];
-    sumB[(a * n_rep + r) * n_slots + s] += N - 2 * (long long)u[1];
-  }
-  for (int p = 0; p < n_pairs; ++p) {
-    long long *qc = &qcnt[(a * n_slots + s) * n_pairs + p];
-    const long long qv = N - 2 * *qc;
-    sumq[(a * n_slots + s) * n_pairs + p] += qv;
-    sumq2[(a * n_slots + s) * n_pairs + p] += qv * qv;
-    *qc = 0;
   }
 }
 
@@ -1075,27 +1240,39 @@ SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
 }
 
 template <typename Word, bool BLUE, int G2>
-void launch_sweep(const SamplesArgs<Word> &p, unsigned blocks, size_t smem, cudaStream_t st, int colour,
-                  int count_only) {
-  samples_half_sweep_kernel<Word, BLUE, G2><<<blocks, kBlock, smem, st>>>(p, colour, count_only);
+void launch_sweep(const SamplesArgs<Word> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
+                  int colour, int count_only) {
+  samples_half_sweep_kernel<Word, BLUE, G2><<<blocks, kBlock, 0, st>>>(p, th, colour, count_only);
 }
 
 template <typename Word, bool BLUE>
-void launch_sweep_g(const SamplesArgs<Word> &p, unsigned blocks, size_t smem, cudaStream_t st, int colour,
-                    int count_only) {
+void launch_sweep_g(const SamplesArgs<Word> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
+                    int colour, int count_only) {
   // counter planes for G sites per thread: G2 = ceil(log2(G / 4))
   int g2 = 0;
   while ((4 << g2) < p.seg_sites) ++g2;
   switch (g2) {
-    case 0: launch_sweep<Word, BLUE, 0>(p, blocks, smem, st, colour, count_only); break;
-    case 1: launch_sweep<Word, BLUE, 1>(p, blocks, smem, st, colour, count_only); break;
-    case 2: launch_sweep<Word, BLUE, 2>(p, blocks, smem, st, colour, count_only); break;
-    case 3: launch_sweep<Word, BLUE, 3>(p, blocks, smem, st, colour, count_only); break;
-    case 4: launch_sweep<Word, BLUE, 4>(p, blocks, smem, st, colour, count_only); break;
-    case 5: launch_sweep<Word, BLUE, 5>(p, blocks, smem, st, colour, count_only); break;
-    case 6: launch_sweep<Word, BLUE, 6>(p, blocks, smem, st, colour, count_only); break;
-    default: launch_sweep<Word, BLUE, 7>(p, blocks, smem, st, colour, count_only); break;
+    case 0: launch_sweep<Word, BLUE, 0>(p, th, blocks, st, colour, count_only); break;
+    case 1: launch_sweep<Word, BLUE, 1>(p, th, blocks, st, colour, count_only); break;
+    case 2: launch_sweep<Word, BLUE, 2>(p, th, blocks, st, colour, count_only); break;
+    case 3: launch_sweep<Word, BLUE, 3>(p, th, blocks, st, colour, count_only); break;
+    case 4: launch_sweep<Word, BLUE, 4>(p, th, blocks, st, colour, count_only); break;
+    case 5: launch_sweep<Word, BLUE, 5>(p, th, blocks, st, colour, count_only); break;
+    case 6: launch_sweep<Word, BLUE, 6>(p, th, blocks, st, colour, count_only); break;
+    default: launch_sweep<Word, BLUE, 7>(p, th, blocks, st, colour, count_only); break;
   }
+}
+
+// The 9 rejecting classes' thresholds of every slot in the form reject_mask
+// and reject_word read them.
+void fill_thresholds(const qisg_handle *h, int has_zero, SlotThresholds &th) {
+  std::memset(&th, 0, sizeof(th));
+  static const int cls[9] = {0, 3, 6, 9, 12, 1, 4, 2, 5};   // us * 3 + ut of the 9 classes
+  for (int sl = 0; sl < h->n_slots; ++sl)
+    for (int c = 0; c < 9; ++c) {
+      const uint32_t T = h->T[(size_t)sl * 15 + cls[c]];
+      th.v[sl][c] = has_zero ? T : (T == 0xFFFFFFFFu ? 0u : ~(T - 1u));
+    }
 }
 
 // W = 32 kernel: one thread per column segment of G sites (G = the tile,
@@ -1115,13 +1292,7 @@ SamplesArgs<uint32_t> make_args4(qisg_handle *h, int colour, SlotThresholds &th)
   p.n_seg = half_col / G;
   p.blocks_per_set = (int)(((int64_t)p.plane * p.n_seg + kBlock4 - 1) / kBlock4);
   p.fd_bps = FastDiv((uint32_t)p.blocks_per_set);
-  std::memset(&th, 0, sizeof(th));
-  static const int cls[9] = {0, 3, 6, 9, 12, 1, 4, 2, 5};   // us * 3 + ut of the 9 classes
-  for (int sl = 0; sl < h->n_slots; ++sl)
-    for (int c = 0; c < 9; ++c) {
-      const uint32_t T = h->T[(size_t)sl * 15 + cls[c]];
-      th.v[sl][c] = p.t_has_zero ? T : (T == 0xFFFFFFFFu ? 0u : ~(T - 1u));
-    }
+  fill_thresholds(h, p.t_has_zero, th);
   return p;
 }
 
@@ -1165,9 +1336,10 @@ int fused_red(qisg_handle *h) {
   p.t_has_zero = a.t_has_zero;
   p.one = 1u;
   p.all_ones = 0xFFFFFFFFu;
-  // red tile 1: a thread per (site, replica); otherwise a thread per (site, replica quad)
-  const bool per_replica = h->sweep_tile[0] == 1;
-  const int64_t threads_per_set = (int64_t)a.plane * (h->Lt / 2) * (per_replica ? 4 : 1);
+  // red tile 1: a thread per (site, replica); 2: per (site, replica pair);
+  // otherwise per (site, replica quad)
+  const int tpsite = h->sweep_tile[0] == 1 ? 4 : h->sweep_tile[0] == 2 ? 2 : 1;
+  const int64_t threads_per_set = (int64_t)a.plane * (h->Lt / 2) * tpsite;
   if (threads_per_set + kBlock4 > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
   p.blocks_per_set = (int)((threads_per_set + kBlock4 - 1) / kBlock4);
   p.fd_bps = FastDiv((uint32_t)p.blocks_per_set);
@@ -1177,10 +1349,12 @@ int fused_red(qisg_handle *h) {
   const int64_t blocks = h->n_b * h->n_q * p.blocks_per_set;
   if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
   const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
-  if (per_replica)
+  if (tpsite == 4)
     samples_red_fused_kernel<<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+  else if (tpsite == 2)
+    samples_red_fusedq_kernel<2><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
   else
-    samples_red_fused4_kernel<<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+    samples_red_fusedq_kernel<4><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
   prof_end(h, QISG_KERNEL_SWEEP, tok);
   h->launches++;
   std::swap(h->spins, h->spins_alt);
@@ -1191,7 +1365,10 @@ int fused_red(qisg_handle *h) {
 template <typename Word>
 int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   if (sizeof(Word) == 4 && h->fused && colour == 0 && !count_only) return fused_red(h);
-  if (sizeof(Word) == 4) {
+  // W = 32, blue variant 0 (and the counting red pass): a thread per
+  // (column segment, replica quad); otherwise the column walk, a thread per
+  // (column segment, replica)
+  if (sizeof(Word) == 4 && !(colour == 1 && h->sweep_variant[1] == 1)) {
     SlotThresholds th;
     SamplesArgs<uint32_t> p = make_args4(h, colour, th);
     if (h->fused && colour == 1) {   // the fused red pass read the masks: clear them here
@@ -1205,29 +1382,34 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
     if (blocks > 0x7FFFFFFF || (int64_t)p.blocks_per_set * kBlock4 > 0x7FFFFFFF)
       return fail(QISG_EINVAL, "lattice too large for one launch");
     const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
-    const bool pf = h->sweep_nopf[colour] == 0;
-    if (colour == 1) {
-      if (pf) launch_sweep4<true, true>(p, th, (unsigned)blocks, h->stream, 1, count_only);
-      else launch_sweep4<true, false>(p, th, (unsigned)blocks, h->stream, 1, count_only);
-    } else {
-      if (pf) launch_sweep4<false, true>(p, th, (unsigned)blocks, h->stream, 0, count_only);
-      else launch_sweep4<false, false>(p, th, (unsigned)blocks, h->stream, 0, count_only);
-    }
+    if (colour == 1)
+      launch_sweep4<true, false>(p, th, (unsigned)blocks, h->stream, 1, count_only);
+    else
+      launch_sweep4<false, false>(p, th, (unsigned)blocks, h->stream, 0, count_only);
     prof_end(h, QISG_KERNEL_SWEEP, tok);
     h->launches++;
     return cuda_check(cudaGetLastError(), "samples half sweep");
   }
   SamplesArgs<Word> p = make_args<Word>(h, colour);
+  SlotThresholds th;
+  fill_thresholds(h, p.t_has_zero, th);
+  if (colour == 1) {
+    p.n_zero_U = 0;
+    if (h->fused) {   // masks read by the fused red pass: clear them here
+      if (!count_only) p.t_copy = h->d_t + 1;
+    } else {
+      p.n_zero_acc = 0;
+    }
+  }
   const int64_t sets = h->n_b * h->n_slots * h->n_q;
   const int64_t blocks = sets * p.blocks_per_set;
   if (blocks > 0x7FFFFFFF || (int64_t)p.blocks_per_set * kQuads > 0x7FFFFFFF)
     return fail(QISG_EINVAL, "lattice too large for one launch");
-  const size_t smem = 0;
   const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
   if (colour == 1)
-    launch_sweep_g<Word, true>(p, (unsigned)blocks, smem, h->stream, 1, count_only);
+    launch_sweep_g<Word, true>(p, th, (unsigned)blocks, h->stream, 1, count_only);
   else
-    launch_sweep<Word, false, 0>(p, (unsigned)blocks, smem, h->stream, 0, count_only);
+    launch_sweep<Word, false, 0>(p, th, (unsigned)blocks, h->stream, 0, count_only);
   prof_end(h, QISG_KERNEL_SWEEP, tok);
   h->launches++;
   return cuda_check(cudaGetLastError(), "samples half sweep");
@@ -1299,7 +1481,18 @@ int measure_t(qisg_handle *h, int force_to_q) {
   int rc0 = samples_materialize(h);
   if (rc0) return rc0;
   const int n_pairs = h->n_pairs();
-  if (n_pairs > 0) {
+  if (n_pairs > 0 && h->n_q == 1) {
+    constexpr int spt = 16, K = 5;   // 16 sites per thread: counts <= 16 need 5 planes
+    const int64_t per_set = (h->N + (int64_t)kBlock4 * spt - 1) / ((int64_t)kBlock4 * spt);
+    const int64_t blocks = h->n_b * h->n_slots * per_set;
+    if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+    const int tok = prof_begin(h, QISG_KERNEL_MEASURE);
+    samples_overlap4_kernel<Word, K><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(
+        reinterpret_cast<const Word *>(h->spins), h->d_q, h->N, h->n_slots, h->n_rep, h->n_samples, spt,
+        (int)per_set);
+    prof_end(h, QISG_KERNEL_MEASURE, tok);
+    h->launches++;
+  } else if (n_pairs > 0) {
     const int spt = 16;
     const int64_t bx = (h->N + (int64_t)kBlock * spt - 1) / ((int64_t)kBlock * spt);
     const int64_t by = h->n_b * h->n_slots * n_pairs;
@@ -1311,8 +1504,8 @@ int measure_t(qisg_handle *h, int force_to_q) {
     prof_end(h, QISG_KERNEL_MEASURE, tok);
     h->launches++;
   }
-  const int64_t n = h->n_samples * h->n_slots;
-  samples_finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+  const int64_t n = h->n_samples * h->n_slots * (h->n_rep + n_pairs);
+  samples_finalize2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
       h->d_U, h->d_q, h->d_sumA, h->d_sumB, h->d_sumq, h->d_sumq2, h->n_samples, h->n_rep,
       h->n_slots, h->N, force_to_q);
   h->launches++;

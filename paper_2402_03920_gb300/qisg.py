@@ -299,13 +299,13 @@ class Instance:
         return g.value
 
     def tiles(self):
-        """((red tile, blue tile), (red prefetch, blue prefetch)) of the sweep schedule."""
+        """((red tile, blue tile), (red variant, blue variant)) of the sweep schedule."""
         t, pf = (ctypes.c_int * 2)(), (ctypes.c_int * 2)()
         _check(load().qisg_get_tiles(self._h, t, pf))
         return (t[0], t[1]), (pf[0], pf[1])
 
-    def set_tiles(self, tiles, prefetch=(1, 1)):
-        t, pf = (ctypes.c_int * 2)(*tiles), (ctypes.c_int * 2)(*prefetch)
+    def set_tiles(self, tiles, variants=(0, 0)):
+        t, pf = (ctypes.c_int * 2)(*tiles), (ctypes.c_int * 2)(*variants)
         _check(load().qisg_set_tiles(self._h, t, pf))
 
     def profile(self, enable: bool, kinds=None):
