@@ -298,7 +298,7 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
       h->J_bytes = (size_t)h->n_b * L * L * 2 * (h->W / 8);
     }
     rc = dalloc(h, &h->spins, h->spins_bytes);
-    h->fused = layout == QISG_LAYOUT_SAMPLES && h->W == 32;
+    h->fused = layout == QISG_LAYOUT_SAMPLES;
     if (!rc && h->fused) rc = dalloc(h, &h->spins_alt, h->spins_bytes);
   }
   if (!rc) rc = dalloc(h, &h->J, h->J_bytes);

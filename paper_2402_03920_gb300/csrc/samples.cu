@@ -372,11 +372,12 @@ __device__ __forceinline__ uint32_t q4(const uint4 &v, int j) {
 // blue pass then works on that buffer in place.  The four replica threads of
 // a site share one Philox call per slot, made by one of them per group of
 // four slots and exchanged in shared memory.
-struct FusedRedArgs {
-  const uint32_t *src;
-  uint32_t *dst;
-  const uint32_t *J;
-  const uint32_t *acc;
+template <typename Word>
+struct FusedRedArgsT {
+  const Word *src;
+  Word *dst;
+  const Word *J;
+  const Word *acc;
   const unsigned long long *d_t;
   unsigned long long *zero_U;
   int64_t n_zero_U;
@@ -386,6 +387,7 @@ struct FusedRedArgs {
   uint32_t one, all_ones;
   FastDiv fd_bps, fd_nq, fd_plane, fd_L;
 };
+using FusedRedArgs = FusedRedArgsT<uint32_t>;
 
 __global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedRedArgs p,
                                                                      const __grid_constant__ SlotThresholds th) {
@@ -524,29 +526,44 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedR
 // shuffle: the even thread draws even slots, the odd thread odd ones).
 // Fewer threads and instructions per word than the per-replica form; the
 // autotuner picks the form (results are identical).
-template <int RP>
-__device__ __forceinline__ void ld_rp(uint32_t (&d)[RP], const uint32_t *p) {
-  if constexpr (RP == 4) {
+template <typename Word, int RP>
+__device__ __forceinline__ void ld_rp(Word (&d)[RP], const Word *p) {
+  if constexpr (RP * sizeof(Word) == 16) {
     const uint4 v = *reinterpret_cast<const uint4 *>(p);
-    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
-  } else {
+    memcpy(d, &v, 16);
+  } else if constexpr (RP * sizeof(Word) == 8) {
     const uint2 v = *reinterpret_cast<const uint2 *>(p);
-    d[0] = v.x; d[1] = v.y;
+    memcpy(d, &v, 8);
+  } else {
+    d[0] = *p;
   }
 }
-template <int RP>
-__device__ __forceinline__ void st_rp(uint32_t *p, const uint32_t (&d)[RP]) {
-  if constexpr (RP == 4)
-    *reinterpret_cast<uint4 *>(p) = make_uint4(d[0], d[1], d[2], d[3]);
-  else
-    *reinterpret_cast<uint2 *>(p) = make_uint2(d[0], d[1]);
+template <typename Word, int RP>
+__device__ __forceinline__ void st_rp(Word *p, const Word (&d)[RP]) {
+  if constexpr (RP * sizeof(Word) == 16) {
+    uint4 v;
+    memcpy(&v, d, 16);
+    *reinterpret_cast<uint4 *>(p) = v;
+  } else if constexpr (RP * sizeof(Word) == 8) {
+    uint2 v;
+    memcpy(&v, d, 8);
+    *reinterpret_cast<uint2 *>(p) = v;
+  } else {
+    *p = d[0];
+  }
 }
 
-template <int RP>
-__global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const FusedRedArgs p,
+// Red pass with the pending PT exchanges (as above) for either word width,
+// one thread per red site and RP of its four replicas (TPS = 4 / RP threads
+// per site, consecutive lanes).  The site's Philox calls (one per slot, four
+// draws) are spread over its threads: thread h makes the call of slot
+// TPS g + h and the draws are passed on by shuffles.
+template <typename Word, int RP>
+__global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const FusedRedArgsT<Word> p,
                                                                       const __grid_constant__ SlotThresholds th) {
-  constexpr int TPS = 4 / RP;   // threads per site
-  __shared__ __align__(16) uint32_t msk[kMaxSlotsPT][4];
+  constexpr int TPS = 4 / RP;
+  constexpr int W = (int)sizeof(Word) * 8;
+  __shared__ __align__(16) Word msk[kMaxSlotsPT][4];
   const uint32_t bid = blockIdx.x;
   const uint32_t set = p.fd_bps.div(bid);   // (b, q)
   const uint32_t chunk = bid - set * (uint32_t)p.blocks_per_set;
@@ -560,15 +577,15 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const Fused
   for (int i = threadIdx.x; i < 4 * kMaxSlotsPT; i += blockDim.x) {
     const int sl = i >> 2, jj = i & 3;
     const int rr = 4 * q + jj;
-    msk[sl][jj] = (rr < p.n_rep && sl + 1 < n) ? p.acc[((int64_t)b * p.n_rep + rr) * n + sl] : 0u;
+    msk[sl][jj] = (rr < p.n_rep && sl + 1 < n) ? p.acc[((int64_t)b * p.n_rep + rr) * n + sl] : Word(0);
   }
   __syncthreads();
 
   const uint32_t tid = chunk * (uint32_t)kBlock4 + threadIdx.x;
-  const int h = TPS == 1 ? 0 : (int)(tid & 1u);   // which replica pair (RP = 2)
+  const int h = (int)(tid % TPS);                 // which replica group of the site
   const uint32_t quad = tid / TPS;                // red site of the (b, q) set
   const uint32_t P = (uint32_t)p.plane, Lt = (uint32_t)p.Lt, L = (uint32_t)p.L;
-  const bool live = quad < P * (Lt / 2);          // uniform per site (pairs share a site)
+  const bool live = quad < P * (Lt / 2);          // uniform over a site's threads
   const uint32_t seg = p.fd_plane.div(quad);
   const uint32_t i2 = quad - seg * P;
   const uint32_t y = p.fd_L.div(i2), x = i2 - y * L;
@@ -576,7 +593,7 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const Fused
   const uint32_t ixp = (x + 1 == L ? 0 : x + 1) + L * y, ixm = (x == 0 ? L - 1 : x - 1) + L * y;
   const uint32_t iyp = x + L * (y + 1 == L ? 0 : y + 1), iym = x + L * (y == 0 ? L - 1 : y - 1);
   const uint32_t off = tau * P;
-  uint32_t zo[7];   // word offsets (u32 units) of the seven sites' replica groups
+  uint32_t zo[7];   // word offsets of the seven sites' replica groups
   {
     uint32_t z[7];
     z[0] = i2 + off;
@@ -591,73 +608,69 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const Fused
   }
   const int64_t base = (((int64_t)b * n * p.n_q + q) * p.N) * 4;
   const int64_t SS = (int64_t)p.n_q * p.N * 4;
-  const uint32_t *sb = p.src + base;
-  uint32_t *db = p.dst + base;
-  const uint32_t *Jb = p.J + (int64_t)b * P * 2;
-  uint32_t Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
+  const Word *sb = p.src + base;
+  Word *db = p.dst + base;
+  const Word *Jb = p.J + (int64_t)b * P * 2;
+  Word Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
   const unsigned long long t = *p.d_t;
-  const uint32_t ctr_w = (DOM_SWEEP << 28) | ((b * 32u) >> 6);
+  const uint32_t ctr_w = (DOM_SWEEP << 28) | ((b * (uint32_t)W) >> 6);
   const uint32_t site = i2 + off;
   const bool has_zero = p.t_has_zero != 0;
-  uint32_t cw[7][RP], n1[7][RP];
+  const int lane = (int)(threadIdx.x & 31), lane0 = lane & ~(TPS - 1);
+  Word cw[7][RP], n1[7][RP];
   if (live) {
     Jxp = Jb[2 * i2];
     Jxm = Jb[2 * ixm];
     Jyp = Jb[2 * i2 + 1];
     Jym = Jb[2 * iym + 1];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) ld_rp<RP>(cw[k], sb + zo[k]);
+    for (int k = 0; k < 7; ++k) ld_rp<Word, RP>(cw[k], sb + zo[k]);
     if (n > 1)
 #pragma unroll
-      for (int k = 0; k < 7; ++k) ld_rp<RP>(n1[k], sb + SS + zo[k]);
+      for (int k = 0; k < 7; ++k) ld_rp<Word, RP>(n1[k], sb + SS + zo[k]);
   }
   uint4 R4 = make_uint4(0, 0, 0, 0);
   for (int sl = 0; sl < n; ++sl) {
-    // the draws of slot sl (RP = 2: the pair's calls alternate over slots)
-    if constexpr (RP == 4) {
-      if (live) R4 = philox(make_uint4(site, (uint32_t)t, (uint32_t)sl | ((uint32_t)q << 16), ctr_w), p.key);
-    } else {
-      if ((sl & 1) == 0) {
-        const int sm = sl + h;   // this thread's call covers slot sl + h
-        if (live && sm < n) R4 = philox(make_uint4(site, (uint32_t)t, (uint32_t)sm | ((uint32_t)q << 16), ctr_w), p.key);
-      }
+    const int i = sl % TPS;   // thread i of the site holds slot sl's call
+    if (i == 0) {
+      const int sm = sl + h;
+      if (live && sm < n) R4 = philox(make_uint4(site, (uint32_t)t, (uint32_t)sm | ((uint32_t)q << 16), ctr_w), p.key);
     }
     uint32_t Rj[RP];
-    if constexpr (RP == 4) {
+    if constexpr (TPS == 1) {
       Rj[0] = R4.x; Rj[1] = R4.y; Rj[2] = R4.z; Rj[3] = R4.w;
-    } else {
-      // slot sl's call is held by thread (sl & 1) of the pair; thread h needs
-      // its components 2h, 2h + 1
-      const int owner = sl & 1;
-      const uint32_t give0 = (owner == h) ? (h ? R4.x : R4.z) : 0u;   // partner's components
-      const uint32_t give1 = (owner == h) ? (h ? R4.y : R4.w) : 0u;
+    } else if constexpr (TPS == 2) {
+      // the owner passes the partner's two components
+      const uint32_t give0 = (i == h) ? (h ? R4.x : R4.z) : 0u;
+      const uint32_t give1 = (i == h) ? (h ? R4.y : R4.w) : 0u;
       const uint32_t got0 = __shfl_xor_sync(0xffffffffu, give0, 1);
       const uint32_t got1 = __shfl_xor_sync(0xffffffffu, give1, 1);
-      if (owner == h) {
-        Rj[0] = h ? R4.z : R4.x;
-        Rj[1] = h ? R4.w : R4.y;
-      } else {
-        Rj[0] = got0;
-        Rj[1] = got1;
-      }
+      Rj[0] = (i == h) ? (h ? R4.z : R4.x) : got0;
+      Rj[1] = (i == h) ? (h ? R4.w : R4.y) : got1;
+    } else {
+      const uint32_t v0 = __shfl_sync(0xffffffffu, R4.x, lane0 + i);
+      const uint32_t v1 = __shfl_sync(0xffffffffu, R4.y, lane0 + i);
+      const uint32_t v2 = __shfl_sync(0xffffffffu, R4.z, lane0 + i);
+      const uint32_t v3 = __shfl_sync(0xffffffffu, R4.w, lane0 + i);
+      Rj[0] = h == 0 ? v0 : h == 1 ? v1 : h == 2 ? v2 : v3;
     }
     if (!live) continue;
-    uint32_t fw[7][RP];
+    Word fw[7][RP];
     if (sl + 1 < n) {
-      uint32_t n2[7][RP];
+      Word n2[7][RP];
       if (sl + 2 < n) {
-        const uint32_t *ps = sb + (int64_t)(sl + 2) * SS;
+        const Word *ps = sb + (int64_t)(sl + 2) * SS;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) ld_rp<RP>(n2[k], ps + zo[k]);
+        for (int k = 0; k < 7; ++k) ld_rp<Word, RP>(n2[k], ps + zo[k]);
       }
-      uint32_t m[RP];
+      Word m[RP];
 #pragma unroll
       for (int jj = 0; jj < RP; ++jj) m[jj] = msk[sl][RP * h + jj];
 #pragma unroll
       for (int k = 0; k < 7; ++k)
 #pragma unroll
         for (int jj = 0; jj < RP; ++jj) {
-          const uint32_t xx = (cw[k][jj] ^ n1[k][jj]) & m[jj];
+          const Word xx = (cw[k][jj] ^ n1[k][jj]) & m[jj];
           fw[k][jj] = cw[k][jj] ^ xx;
           cw[k][jj] = n1[k][jj] ^ xx;
           if (sl + 2 < n) n1[k][jj] = n2[k][jj];
@@ -669,31 +682,31 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const Fused
         for (int jj = 0; jj < RP; ++jj) fw[k][jj] = cw[k][jj];
     }
     const uint32_t *T = th.v[sl];
-    uint32_t out[RP];
+    Word out[RP];
 #pragma unroll
     for (int jj = 0; jj < RP; ++jj) {
-      const uint32_t sc = fw[0][jj];
-      const uint32_t b1 = sc ^ fw[3][jj] ^ Jxp;
-      const uint32_t b2 = sc ^ fw[4][jj] ^ Jxm;
-      const uint32_t b3 = sc ^ fw[5][jj] ^ Jyp;
-      const uint32_t b4 = sc ^ fw[6][jj] ^ Jym;
-      const uint32_t t1 = sc ^ fw[1][jj];
-      const uint32_t t2 = sc ^ fw[2][jj];
-      const uint32_t s1 = b1 ^ b2 ^ b3;
-      const uint32_t c1 = maj3(b1, b2, b3);
-      const uint32_t us0 = s1 ^ b4;
-      const uint32_t c2 = s1 & b4;
-      const uint32_t us1 = c1 ^ c2;
-      const uint32_t us2 = c1 & c2;
-      const uint32_t ut0 = t1 ^ t2;
-      const uint32_t ut1 = t1 & t2;
-      const uint32_t rej = has_zero ? reject_mask<true>(Rj[jj], T, us0, us1, us2, ut0, ut1, p.one, p.all_ones)
-                                    : reject_mask<false>(Rj[jj], T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
+      const Word sc = fw[0][jj];
+      const Word b1 = sc ^ fw[3][jj] ^ Jxp;
+      const Word b2 = sc ^ fw[4][jj] ^ Jxm;
+      const Word b3 = sc ^ fw[5][jj] ^ Jyp;
+      const Word b4 = sc ^ fw[6][jj] ^ Jym;
+      const Word t1 = sc ^ fw[1][jj];
+      const Word t2 = sc ^ fw[2][jj];
+      const Word s1 = b1 ^ b2 ^ b3;
+      const Word c1 = maj3(b1, b2, b3);
+      const Word us0 = s1 ^ b4;
+      const Word c2 = s1 & b4;
+      const Word us1 = c1 ^ c2;
+      const Word us2 = c1 & c2;
+      const Word ut0 = t1 ^ t2;
+      const Word ut1 = t1 & t2;
+      const Word rej = has_zero ? reject_word<Word, true>(Rj[jj], T, us0, us1, us2, ut0, ut1, p.one, p.all_ones)
+                                : reject_word<Word, false>(Rj[jj], T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
       out[jj] = sc ^ ~rej;
     }
-    uint32_t *pd = db + (int64_t)sl * SS;
-    st_rp<RP>(pd + zo[0], out);
-    st_rp<RP>(pd + zo[1], fw[1]);
+    Word *pd = db + (int64_t)sl * SS;
+    st_rp<Word, RP>(pd + zo[0], out);
+    st_rp<Word, RP>(pd + zo[1], fw[1]);
   }
 }
 
@@ -1314,14 +1327,16 @@ void launch_sweep4(const SamplesArgs<uint32_t> &p, const SlotThresholds &th, uns
   }
 }
 
+template <typename Word>
 int fused_red(qisg_handle *h) {
   SlotThresholds th;
-  const SamplesArgs<uint32_t> a = make_args4(h, 0, th);
-  FusedRedArgs p;
-  p.src = reinterpret_cast<const uint32_t *>(h->spins);
-  p.dst = reinterpret_cast<uint32_t *>(h->spins_alt);
-  p.J = reinterpret_cast<const uint32_t *>(h->J);
-  p.acc = reinterpret_cast<const uint32_t *>(h->d_acc);
+  const SamplesArgs<Word> a = make_args<Word>(h, 0);
+  fill_thresholds(h, a.t_has_zero, th);
+  FusedRedArgsT<Word> p;
+  p.src = reinterpret_cast<const Word *>(h->spins);
+  p.dst = reinterpret_cast<Word *>(h->spins_alt);
+  p.J = reinterpret_cast<const Word *>(h->J);
+  p.acc = reinterpret_cast<const Word *>(h->d_acc);
   p.d_t = h->d_t;
   p.zero_U = h->d_U;
   p.n_zero_U = a.n_zero_U;
@@ -1336,9 +1351,10 @@ int fused_red(qisg_handle *h) {
   p.t_has_zero = a.t_has_zero;
   p.one = 1u;
   p.all_ones = 0xFFFFFFFFu;
-  // red tile 1: a thread per (site, replica); 2: per (site, replica pair);
-  // otherwise per (site, replica quad)
-  const int tpsite = h->sweep_tile[0] == 1 ? 4 : h->sweep_tile[0] == 2 ? 2 : 1;
+  // threads per site from the red tile: 1 -> four, 2 -> two, else one
+  // (64-bit words: at most two replicas per thread)
+  int tpsite = h->sweep_tile[0] == 1 ? 4 : h->sweep_tile[0] == 2 ? 2 : 1;
+  if (sizeof(Word) == 8 && tpsite == 1) tpsite = 2;
   const int64_t threads_per_set = (int64_t)a.plane * (h->Lt / 2) * tpsite;
   if (threads_per_set + kBlock4 > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
   p.blocks_per_set = (int)((threads_per_set + kBlock4 - 1) / kBlock4);
@@ -1349,12 +1365,20 @@ int fused_red(qisg_handle *h) {
   const int64_t blocks = h->n_b * h->n_q * p.blocks_per_set;
   if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
   const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
-  if (tpsite == 4)
-    samples_red_fused_kernel<<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
-  else if (tpsite == 2)
-    samples_red_fusedq_kernel<2><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
-  else
-    samples_red_fusedq_kernel<4><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+  if constexpr (sizeof(Word) == 4) {
+    const FusedRedArgs &p32 = p;
+    if (tpsite == 4)
+      samples_red_fused_kernel<<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p32, th);
+    else if (tpsite == 2)
+      samples_red_fusedq_kernel<uint32_t, 2><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+    else
+      samples_red_fusedq_kernel<uint32_t, 4><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+  } else {
+    if (tpsite == 4)
+      samples_red_fusedq_kernel<Word, 1><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+    else
+      samples_red_fusedq_kernel<Word, 2><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+  }
   prof_end(h, QISG_KERNEL_SWEEP, tok);
   h->launches++;
   std::swap(h->spins, h->spins_alt);
@@ -1364,7 +1388,7 @@ int fused_red(qisg_handle *h) {
 
 template <typename Word>
 int half_sweep_t(qisg_handle *h, int colour, int count_only) {
-  if (sizeof(Word) == 4 && h->fused && colour == 0 && !count_only) return fused_red(h);
+  if (h->fused && colour == 0 && !count_only) return fused_red<Word>(h);
   // W = 32, blue variant 0 (and the counting red pass): a thread per
   // (column segment, replica quad); otherwise the column walk, a thread per
   // (column segment, replica)
@@ -1629,8 +1653,8 @@ int samples_init(qisg_handle *h) {
 }
 int samples_materialize(qisg_handle *h) {
   if (!h->fused || !h->perm_pending) return QISG_OK;
-  int rc = permute_t<unsigned int>(h, 0);
-  if (!rc) rc = clear_masks<unsigned int>(h);
+  int rc = h->W == 64 ? permute_t<unsigned long long>(h, 0) : permute_t<unsigned int>(h, 0);
+  if (!rc) rc = h->W == 64 ? clear_masks<unsigned long long>(h) : clear_masks<unsigned int>(h);
   if (!rc) h->perm_pending = false;
   return rc;
 }
