@@ -476,21 +476,24 @@ int build_cycle(qisg_handle *h, int C) {
     std::vector<cudaGraphNode_t> nodes(n_nodes);
     if (!rc && n_nodes) rc = cuda_check(cudaGraphGetNodes(g, nodes.data(), &n_nodes), "graph nodes");
     // walk the linear chain from its root so that record nodes keep their order
+    // (edges may carry programmatic-launch data, so every query takes edge data)
     std::vector<cudaGraphNode_t> order;
     if (!rc) {
       cudaGraphNode_t cur = nullptr;
       for (cudaGraphNode_t nd : nodes) {
         size_t nd_deps = 0;
-        cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &nd_deps);
+        rc = cuda_check(cudaGraphNodeGetDependencies(nd, nullptr, nullptr, &nd_deps), "graph node dependencies");
+        if (rc) break;
         if (nd_deps == 0) cur = nd;
       }
-      while (cur) {
+      while (!rc && cur) {
         order.push_back(cur);
         size_t nd_out = 0;
-        cudaGraphNodeGetDependentNodes(cur, nullptr, nullptr, &nd_out);
-        if (nd_out != 1) break;
+        rc = cuda_check(cudaGraphNodeGetDependentNodes(cur, nullptr, nullptr, &nd_out), "graph node dependents");
+        if (rc || nd_out != 1) break;
         cudaGraphNode_t nxt = nullptr;
-        cudaGraphNodeGetDependentNodes(cur, &nxt, nullptr, &nd_out);
+        cudaGraphEdgeData ed;
+        rc = cuda_check(cudaGraphNodeGetDependentNodes(cur, &nxt, &ed, &nd_out), "graph node dependents");
         cur = nxt;
       }
       if (order.size() != n_nodes) rc = fail(QISG_ECUDA, "captured sweep graph is not a chain");
