@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--forms", default="batched,per_instance")
-    p.add_argument("--extras", default="uneven,large,serving",
+    p.add_argument("--extras", default="uneven,large,paper,serving",
                    help="other workloads measured beside the headline (empty: none)")
     p.add_argument("--serving-requests", type=int, default=100)
     p.add_argument("--tiles", default="",
@@ -385,6 +385,39 @@ def large_batched_entry(torch, qisg, sweeps=20):
                                  "frac": hbm_achieved / pk.get("hbm_gbs", 6800.0), "bytes_per_update": 0.25}}}
 
 
+def paper_shape_entry(torch, qisg, sweeps=10):
+    """The lattice shapes of the paper's performance figures (Sec. 4: L=16,
+    L_tau=8192 and L=24; 0.466 and 0.735 ps/spin-update on four A100s for one
+    system and its k ladder) with equal couplings k_tau = k, run as the
+    batched form: 32 samples x 4 replicas x 16 slots, k linear in [0.2, 0.5],
+    PT every sweep.  L=24 is run at L_tau=2048 (the paper's production
+    L_tau; the figure's L_tau is not given)."""
+    out = {}
+    n_slots = 16
+    ks = np.linspace(0.2, 0.5, n_slots)
+    ladder = np.stack([ks, ks], axis=1)   # equal coupling
+    for L, Lt in ((16, 8192), (24, 2048)):
+        cfg = qisg.Config(L, Lt, ladder, 4, 32, 1, word_bits=32, layout=qisg.QISG_LAYOUT_SAMPLES)
+        with qisg.Instance(cfg) as inst:
+            inst.autotune(1)
+            inst.sweep(2)
+            inst.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            inst.sweep(sweeps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            tiles = inst.tiles()
+        ups = 32 * 4 * n_slots * L * L * Lt * sweeps
+        out[f"L{L}_Ltau{Lt}"] = {"value": ms * 1e9 / ups, "unit": UNIT, "ms_per_sweep": ms / sweeps,
+                                  "schedule": {"tiles": list(tiles[0]), "variants": list(tiles[1])}}
+    out["workload"] = ("paper's lattice shapes, equal coupling k_tau = k, 32 samples x 4 replicas x 16 slots, "
+                       "k in [0.2, 0.5], PT every sweep")
+    out["paper_4xA100_ps"] = {"L16_Ltau8192": 0.466, "L24": 0.735}
+    return out
+
+
 def serving_entry(qisg, n_requests):
     """Poisson stream of requests (L 8..24, L_tau 32..1024, 8..32 slots,
     100..5000 sweeps, Gamma in [0.8, 1.2]) through the continuous-batching
@@ -513,6 +546,8 @@ def run_gpu(args):
         line["batched_uneven"] = uneven_batch_entry(qisg)
     if "large" in extras and world == 1:
         line["batched_large"] = large_batched_entry(torch, qisg)
+    if "paper" in extras and world == 1:
+        line["paper_shape"] = paper_shape_entry(torch, qisg)
     if "serving" in extras and world == 1:
         line["serving"] = serving_entry(qisg, args.serving_requests)
     if not args.no_cpu_baseline and world == 1:
