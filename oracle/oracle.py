@@ -62,9 +62,9 @@ def _load():
             lib.orc_init_spins.argtypes = [i32, i32, i32, i32, i64, i64, u64, P]
             lib.orc_init_spins.restype = None
             lib.orc_run.argtypes = [i32, i32, i32, i32, i64, i64, u64, P, P, i32, i32,
-                                    P, P, P, u64, i64, P, P, P, P, P, P, P, i32]
+                                    P, P, P, u64, i64, P, P, P, P, P, P, P, i32, i32]
             lib.orc_run.restype = i32
-            lib.orc_energies.argtypes = [i32, i32, i32, i32, i64, P, P, P, P]
+            lib.orc_energies.argtypes = [i32, i32, i32, i32, i64, P, P, P, P, i32]
             lib.orc_energies.restype = None
             lib.orc_pt_only.argtypes = [i32, i32, i64, u64, P, P, u64, P, P, P]
             lib.orc_pt_only.restype = None
@@ -129,13 +129,14 @@ def init_spins(L: int, Ltau: int, n_slots: int, n_rep: int, a_lo: int, n_a: int,
     return S
 
 
-def energies(L: int, Ltau: int, J: np.ndarray, S: np.ndarray):
-    """A, B (by walker) of configurations S[n_a][n_rep][n_slots][N]."""
+def energies(L: int, Ltau: int, J: np.ndarray, S: np.ndarray, tau_ap: bool = False):
+    """A, B (by walker) of configurations S[n_a][n_rep][n_slots][N];
+    tau_ap: antiperiodic along tau."""
     n_a, n_rep, n_slots, _ = S.shape
     A = np.zeros((n_a, n_rep, n_slots), dtype=np.int64)
     B = np.zeros_like(A)
     _load().orc_energies(L, Ltau, n_slots, n_rep, n_a, _ptr(np.ascontiguousarray(J)),
-                         _ptr(np.ascontiguousarray(S)), _ptr(A), _ptr(B))
+                         _ptr(np.ascontiguousarray(S)), _ptr(A), _ptr(B), int(bool(tau_ap)))
     return A, B
 
 
@@ -173,6 +174,7 @@ class OracleState:
     sumq: np.ndarray = None  # [n_a][n_slots][n_pairs]
     sumq2: np.ndarray = None
     n_meas: int = 0
+    tau_ap: bool = False     # antiperiodic along tau
 
     @property
     def n_slots(self) -> int:
@@ -183,14 +185,14 @@ class OracleState:
         return self.L * self.L * self.Ltau
 
 
-def new_state(L, Ltau, k, ktau, n_rep, seed, a_lo=0, n_a=1) -> OracleState:
+def new_state(L, Ltau, k, ktau, n_rep, seed, a_lo=0, n_a=1, tau_ap=False) -> OracleState:
     k = np.ascontiguousarray(k, dtype=np.float64)
     kt = np.ascontiguousarray(ktau, dtype=np.float64)
     n_slots = len(k)
     J = init_couplings(L, a_lo, n_a, seed)
     S = init_spins(L, Ltau, n_slots, n_rep, a_lo, n_a, seed)
     wa = np.tile(np.arange(n_slots, dtype=np.int32), (n_a, n_rep, 1)).copy()
-    st = OracleState(L, Ltau, k, kt, n_rep, a_lo, n_a, seed, J, S, wa)
+    st = OracleState(L, Ltau, k, kt, n_rep, a_lo, n_a, seed, J, S, wa, tau_ap=bool(tau_ap))
     alloc_obs(st)
     refresh_energies(st)
     return st
@@ -198,7 +200,7 @@ def new_state(L, Ltau, k, ktau, n_rep, seed, a_lo=0, n_a=1) -> OracleState:
 
 def refresh_energies(st: OracleState) -> None:
     """Set st.A, st.B (by slot) from the current configurations."""
-    Aw, Bw = energies(st.L, st.Ltau, st.J, st.S)
+    Aw, Bw = energies(st.L, st.Ltau, st.J, st.S, st.tau_ap)
     idx = st.walker_at.astype(np.int64)
     st.A = np.take_along_axis(Aw, idx, axis=2)
     st.B = np.take_along_axis(Bw, idx, axis=2)
@@ -224,7 +226,7 @@ def run(st: OracleState, n_sweeps: int, pt_every: int = 1, measure_every: int = 
                      _ptr(st.k), _ptr(st.ktau), pt_every, measure_every,
                      _ptr(st.J), _ptr(st.S), _ptr(st.walker_at), st.t, n_sweeps,
                      _ptr(st.A), _ptr(st.B), _ptr(st.sumA), _ptr(st.sumB),
-                     _ptr(st.sumq), _ptr(st.sumq2), ctypes.byref(n_meas), n_threads)
+                     _ptr(st.sumq), _ptr(st.sumq2), ctypes.byref(n_meas), n_threads, int(st.tau_ap))
     if rc != 0:
         raise MemoryError("oracle run failed")
     st.t += n_sweeps

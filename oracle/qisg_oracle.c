@@ -8,7 +8,9 @@
  *
  * What it computes (the paper's notation):
  *   - the Trotter-Suzuki classical model of Eq. (2)-(3) (Sec. 1): spins
- *     S_{x,tau} = +-1 on an L x L x L_tau prism, periodic in x, y and tau,
+ *     S_{x,tau} = +-1 on an L x L x L_tau prism, periodic in x and y and
+ *     periodic or antiperiodic in tau (Sec. 1: S_{x,L_tau} = +-S_{x,0}, so the
+ *     antiperiodic wrap bond enters Eq. (3) as -S_{x,L_tau-1} S_{x,0}),
  *     with spatial bonds k*J_xy (J = +-1) and imaginary-time bonds k_tau.
  *     The paper's single coupling k is generalised to a (k, k_tau) pair per
  *     ladder slot, exp(-2 k_tau) = tanh(k Gamma); k_tau = k recovers the
@@ -193,13 +195,15 @@ void orc_init_spins(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64
 
 typedef struct {
     int L, Ltau, n_slots, n_rep;
+    int tau_ap;                         /* 1: antiperiodic along tau */
     uint64_t seed;
     const uint32_t *T;                  /* [n_slots][5][3] */
     const double *ap, *am, *bp, *bm;    /* [n_slots-1] */
 } orc_model;
 
 /* A = sum over spatial bonds of J S S, B = sum over imaginary-time bonds of
- * S S (Eq. (3) splits -E into these two sums). */
+ * S S (Eq. (3) splits -E into these two sums); with antiperiodic tau the
+ * bond from tau = L_tau-1 to tau = 0 counts -S S. */
 static void energies_of(const orc_model *m, const int8_t *J, const int8_t *S,
                         int64_t *A, int64_t *B)
 {
@@ -215,7 +219,7 @@ static void energies_of(const orc_model *m, const int8_t *J, const int8_t *S,
                 int i2 = x + L * y;
                 a += J[i2 * 2 + 0] * S[i] * S[ix];
                 a += J[i2 * 2 + 1] * S[i] * S[iy];
-                b += S[i] * S[it];
+                b += (m->tau_ap && t == Lt - 1 ? -1 : 1) * S[i] * S[it];
             }
     *A = a;
     *B = b;
@@ -232,13 +236,16 @@ static void half_sweep(const orc_model *m, int64_t a, const int8_t *J, int8_t *S
     for (tau = 0; tau < Lt; ++tau)
         for (y = 0; y < L; ++y)
             for (x = 0; x < L; ++x) {
-                int xp, xm, yp, ym, tp, tm, i2;
+                int xp, xm, yp, ym, tp, tm, i2, gp, gm;
                 int64_t site;
                 if (((x + y + tau) & 1) != colour) continue;
                 site = x + (int64_t)L * y + (int64_t)L * L * tau;
                 xp = (x + 1) % L; xm = (x + L - 1) % L;
                 yp = (y + 1) % L; ym = (y + L - 1) % L;
                 tp = (tau + 1) % Lt; tm = (tau + Lt - 1) % Lt;
+                /* sign of the tau bonds: -1 on the antiperiodic wrap bond */
+                gp = (m->tau_ap && tau == Lt - 1) ? -1 : 1;
+                gm = (m->tau_ap && tau == 0) ? -1 : 1;
                 i2 = x + L * y;
                 for (r = 0; r < n_rep; ++r)
                     for (s = 0; s < n_slots; ++s) {
@@ -251,8 +258,8 @@ static void half_sweep(const orc_model *m, int64_t a, const int8_t *J, int8_t *S
                         us += (J[(xm + L * y) * 2 + 0] * si * Sw[xm + L * y + (int64_t)L * L * tau] == -1);
                         us += (J[i2 * 2 + 1] * si * Sw[x + L * yp + (int64_t)L * L * tau] == -1);
                         us += (J[(x + L * ym) * 2 + 1] * si * Sw[x + L * ym + (int64_t)L * L * tau] == -1);
-                        ut += (si * Sw[x + L * y + (int64_t)L * L * tp] == -1);
-                        ut += (si * Sw[x + L * y + (int64_t)L * L * tm] == -1);
+                        ut += (gp * si * Sw[x + L * y + (int64_t)L * L * tp] == -1);
+                        ut += (gm * si * Sw[x + L * y + (int64_t)L * L * tm] == -1);
                         thr = m->T[(s * 5 + us) * 3 + ut];
                         R = philox_word((uint32_t)site, (uint32_t)t,
                                         (uint32_t)s | ((uint32_t)(r >> 2) << 16),
@@ -304,13 +311,14 @@ static void pt_pass(const orc_model *m, int64_t a, int r, uint64_t t,
  *   sumA,sumB [n_a][n_rep][n_slots] by slot       in/out: measurement sums
  *   sumq,sumq2[n_a][n_slots][n_rep(n_rep-1)/2]    in/out: overlap sums
  *   n_meas                                        in/out: measurements taken
- * Observables may be NULL when measure_every == 0.
+ * Observables may be NULL when measure_every == 0.  tau_ap: antiperiodic
+ * boundary along tau (0: periodic).
  */
 int orc_run(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64_t n_a, uint64_t seed,
             const double *k, const double *ktau, int pt_every, int measure_every,
             const int8_t *J, int8_t *S, int32_t *walker_at, uint64_t t0, int64_t n_sweeps,
             int64_t *A, int64_t *B, int64_t *sumA, int64_t *sumB, int64_t *sumq, int64_t *sumq2,
-            int64_t *n_meas, int n_threads)
+            int64_t *n_meas, int n_threads, int tau_ap)
 {
     orc_model m;
     uint32_t *T;
@@ -327,6 +335,7 @@ int orc_run(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64_t n_a, 
     orc_thresholds(n_slots, k, ktau, T);
     orc_pt_bases(n_slots, k, ktau, ap, am, bp, bm);
     m.L = L; m.Ltau = Ltau; m.n_slots = n_slots; m.n_rep = n_rep; m.seed = seed;
+    m.tau_ap = tau_ap;
     m.T = T; m.ap = ap; m.am = am; m.bp = bp; m.bm = bm;
 
 #ifdef _OPENMP
@@ -401,11 +410,11 @@ int orc_run(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64_t n_a, 
 
 /* Energies A, B (by walker) of given configurations: [n_a][n_rep][n_slots]. */
 void orc_energies(int L, int Ltau, int n_slots, int n_rep, int64_t n_a, const int8_t *J,
-                  const int8_t *S, int64_t *A, int64_t *B)
+                  const int8_t *S, int64_t *A, int64_t *B, int tau_ap)
 {
     orc_model m;
     int64_t N = (int64_t)L * L * Ltau, c;
-    m.L = L; m.Ltau = Ltau; m.n_slots = n_slots; m.n_rep = n_rep;
+    m.L = L; m.Ltau = Ltau; m.n_slots = n_slots; m.n_rep = n_rep; m.tau_ap = tau_ap;
     for (c = 0; c < n_a * n_rep * n_slots; ++c)
         energies_of(&m, J + (c / (n_rep * n_slots)) * L * L * 2, S + c * N, &A[c], &B[c]);
 }

@@ -8,7 +8,8 @@ oracle or the CUDA library.
   (periodic), weight exp(k A + k_tau B) -- Eq. (2)-(3) with a separate
   imaginary-time coupling.
 * ``chain_B``: closed form for k = 0, where every spatial site carries an
-  independent periodic Ising chain of L_tau spins with coupling k_tau.
+  independent Ising ring of L_tau spins with coupling k_tau, periodic or
+  antiperiodic (one bond of opposite sign).
 """
 from __future__ import annotations
 
@@ -21,25 +22,28 @@ def _all_configs(n: int) -> np.ndarray:
     return (1 - 2 * bits).astype(np.int8)       # bit 1 -> spin -1
 
 
-def AB_of_configs(S: np.ndarray, J: np.ndarray, L: int, Ltau: int):
+def AB_of_configs(S: np.ndarray, J: np.ndarray, L: int, Ltau: int, tau_ap: bool = False):
     """A and B of a batch of configurations S[m][N] (site = x + L y + L^2 tau);
-    J[L*L][2] with dir 0 = +x, dir 1 = +y."""
+    J[L*L][2] with dir 0 = +x, dir 1 = +y.  tau_ap: S_{x,L_tau} = -S_{x,0}."""
     m = S.shape[0]
     V = S.reshape(m, Ltau, L, L).astype(np.int64)            # [m][tau][y][x]
     Jx = J[:, 0].reshape(L, L).astype(np.int64)              # [y][x]
     Jy = J[:, 1].reshape(L, L).astype(np.int64)
     A = (Jx[None, None] * V * np.roll(V, -1, axis=3)).sum(axis=(1, 2, 3))
     A += (Jy[None, None] * V * np.roll(V, -1, axis=2)).sum(axis=(1, 2, 3))
-    B = (V * np.roll(V, -1, axis=1)).sum(axis=(1, 2, 3))
+    up = np.roll(V, -1, axis=1)
+    if tau_ap:
+        up[:, Ltau - 1] = -up[:, Ltau - 1]
+    B = (V * up).sum(axis=(1, 2, 3))
     return A, B
 
 
-def enumerate_AB(J: np.ndarray, L: int, Ltau: int, k: float, ktau: float):
+def enumerate_AB(J: np.ndarray, L: int, Ltau: int, k: float, ktau: float, tau_ap: bool = False):
     """Exact <A>, <B>, <A^2>, <B^2> at (k, k_tau) by enumeration (N <= 20)."""
     n = L * L * Ltau
     assert n <= 20
     S = _all_configs(n)
-    A, B = AB_of_configs(S, J, L, Ltau)
+    A, B = AB_of_configs(S, J, L, Ltau, tau_ap)
     logw = k * A.astype(np.float64) + ktau * B.astype(np.float64)
     logw -= logw.max()
     w = np.exp(logw)
@@ -60,13 +64,16 @@ def layer_A(J: np.ndarray, L: int, k: float) -> float:
     return float((w * A).sum() / w.sum())
 
 
-def chain_B(L: int, Ltau: int, ktau: float) -> float:
-    """<B> for k = 0: L^2 independent periodic chains of Ltau spins,
-    Z = (2 cosh K)^n + (2 sinh K)^n, <sum S S_{+1}> = d ln Z / dK."""
+def chain_B(L: int, Ltau: int, ktau: float, tau_ap: bool = False) -> float:
+    """<B> for k = 0: L^2 independent rings of Ltau spins; the transfer
+    matrix has eigenvalues 2 cosh K and 2 sinh K, and the bond of opposite
+    sign of the antiperiodic ring flips the sign of the second:
+    Z = (2 cosh K)^n +- (2 sinh K)^n, <B> = d ln Z / dK (per ring)."""
     n = Ltau
     c, s = np.cosh(ktau), np.sinh(ktau)
+    sg = -1.0 if tau_ap else 1.0
     # divide numerator and denominator by (2 cosh K)^n
     t = np.tanh(ktau)
-    num = n * (s / c + t ** (n - 1))
-    den = 1.0 + t ** n
+    num = n * (s / c + sg * t ** (n - 1))
+    den = 1.0 + sg * t ** n
     return float(L * L * num / den)

@@ -431,3 +431,70 @@ def test_overlap_identity():
                 d = int((S[r1, wa[r1, s]] != S[r2, wa[r2, s]]).sum())
                 assert st.sumq[0, s, p] == st.N - 2 * d
             p += 1
+
+
+# --------------------------------------------------------------------------
+# Antiperiodic boundary along tau (Sec. 1: S_{x,L_tau} = -S_{x,0})
+# --------------------------------------------------------------------------
+
+def test_exact_ring_closed_form_both_boundaries():
+    """The enumeration helper against the transfer-matrix closed form of an
+    Ising ring (k = 0 leaves independent rings): Z = (2 cosh K)^n +-
+    (2 sinh K)^n, the minus sign for one bond of opposite sign."""
+    J = np.ones((1, 2), dtype=np.int8)
+    for ap in (False, True):
+        for n in (4, 5, 6):
+            for K in (0.3, 0.7, 1.1):
+                _, xB, _, _ = exact.enumerate_AB(J, 1, n, 0.0, K, tau_ap=ap)
+                assert abs(xB - exact.chain_B(1, n, K, tau_ap=ap)) < 1e-9 * n
+
+
+def test_energies_antiperiodic_match_roll_formula():
+    rng = np.random.default_rng(5)
+    L, Lt = 4, 6
+    J = (1 - 2 * rng.integers(0, 2, size=(2, L * L, 2))).astype(np.int8)
+    S = (1 - 2 * rng.integers(0, 2, size=(2, 3, 4, L * L * Lt))).astype(np.int8)
+    A, B = oracle.energies(L, Lt, J, S, tau_ap=True)
+    Ap, Bp = oracle.energies(L, Lt, J, S, tau_ap=False)
+    for a in range(2):
+        A2, B2 = exact.AB_of_configs(S[a].reshape(-1, L * L * Lt), J[a], L, Lt, tau_ap=True)
+        assert np.array_equal(A[a].ravel(), A2)
+        assert np.array_equal(B[a].ravel(), B2)
+    # only the wrap bond changes sign: B_ap = B_p - 2 sum_x S_{x,L_tau-1} S_{x,0}
+    V = S.reshape(2, 3, 4, Lt, L * L).astype(np.int64)
+    wrap = (V[:, :, :, Lt - 1] * V[:, :, :, 0]).sum(axis=-1)
+    assert np.array_equal(B, Bp - 2 * wrap)
+    assert np.array_equal(A, Ap)
+
+
+@pytest.mark.parametrize("seed", [2])
+def test_enumeration_L2_Ltau4_antiperiodic(seed):
+    """L=2, L_tau=4 antiperiodic: MC <A>, <B> per slot match exact
+    enumeration with the wrap bond of opposite sign (within 4 sigma)."""
+    L, Lt = 2, 4
+    k, kt = oracle.ladder_linear(0.25, 0.45, 4, 1.0)
+    st = oracle.new_state(L, Lt, k, kt, n_rep=8, seed=seed, tau_ap=True)
+    J = st.J[0]
+    assert _spatially_free_sites(J) == []
+    oracle.run(st, 200)
+    mA, eA, mB, eB = _mc_means(st, 60, 400)
+    for s in range(len(k)):
+        xA, xB, _, _ = exact.enumerate_AB(J, L, Lt, k[s], kt[s], tau_ap=True)
+        pA, pB, _, _ = exact.enumerate_AB(J, L, Lt, k[s], kt[s], tau_ap=False)
+        assert abs(mA[s] - xA) < 4 * eA[s] + 1e-9, (s, mA[s], xA, eA[s])
+        assert abs(mB[s] - xB) < 4 * eB[s] + 1e-9, (s, mB[s], xB, eB[s])
+        assert abs(xB - pB) > 8 * eB[s]   # the boundary is visible in <B>
+
+
+def test_k_tau_zero_antiperiodic_same_spins():
+    """k_tau = 0: the table ignores u_t, so the antiperiodic run follows the
+    periodic spin trajectory bit for bit; only B differs (the wrap bond)."""
+    L, Lt = 4, 6
+    ks = np.array([0.2, 0.45, 0.8])
+    st = oracle.new_state(L, Lt, ks, np.zeros(3), n_rep=4, seed=19)
+    ap = oracle.new_state(L, Lt, ks, np.zeros(3), n_rep=4, seed=19, tau_ap=True)
+    oracle.run(st, 30)
+    oracle.run(ap, 30)
+    assert np.array_equal(st.S, ap.S) and np.array_equal(st.walker_at, ap.walker_at)
+    assert np.array_equal(st.A, ap.A)
+    assert not np.array_equal(st.B, ap.B)
