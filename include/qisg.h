@@ -80,10 +80,13 @@ typedef struct {
     int layout;             /* QISG_LAYOUT_*                                       */
     int per_sample_launch;  /* LANES only: 1 = one kernel launch per sample per
                                half sweep (the plain per-instance form)            */
+    int tau_antiperiodic;   /* 1 = antiperiodic boundary along tau (Sec. 1: the
+                               bond from tau = L_tau-1 to tau = 0 counts -S S in
+                               B); 0 = periodic                                    */
 } qisg_opts;
 
 /* Fill *opts with defaults: word_bits 0, NULL stream, no budget, pt_every 1,
- * measure_every 0, layout AUTO, per_sample_launch 0. */
+ * measure_every 0, layout AUTO, per_sample_launch 0, tau_antiperiodic 0. */
 void qisg_opts_default(qisg_opts *opts);
 
 /* Linear ladder (k_s = lo + (hi-lo) s/(n-1), both ends included; k_s = lo for

@@ -111,6 +111,7 @@ __device__ void batch_tile(const InstDev &I, int colour, int j0, int n, unsigned
   S.n_rep = I.n_rep;
   S.rpw = I.rpw;
   S.n_groups = I.n_groups;
+  S.tau_ap = 0;   // batched instances are periodic along tau
   lanes_tile<unsigned long long, true, BLUE>(S, colour, j0, n, 0, colour == 0 && j0 == 0, smem);
 }
 

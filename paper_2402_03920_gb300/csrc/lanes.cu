@@ -32,6 +32,7 @@ struct LanesArgs {
   int64_t N, half_N;
   FastDiv half_plane_div;
   int L, Lt, plane, half_plane, n_slots, n_rep, rpw, n_groups, sites_per_block;
+  int tau_ap;
 };
 
 template <typename Word>
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(kBlock) lanes_half_sweep_kernel(LanesArgs<Word
   S.n_rep = p.n_rep;
   S.rpw = p.rpw;
   S.n_groups = p.n_groups;
+  S.tau_ap = p.tau_ap;
   const int64_t j0 = (int64_t)blockIdx.x * tile_sites;
   const int n = (int)(p.half_N - j0 < tile_sites ? p.half_N - j0 : tile_sites);
   lanes_tile<Word, false, BLUE>(S, colour, (int)j0, n, count_only, colour == 0 && blockIdx.x == 0, smem_raw);
@@ -230,6 +232,7 @@ LanesArgs<Word> make_args(qisg_handle *h) {
   p.rpw = h->rpw;
   p.n_groups = h->n_groups;
   p.sites_per_block = kBlock / h->n_slots;
+  p.tau_ap = h->tau_ap;
   return p;
 }
 

@@ -33,6 +33,7 @@ struct LanesSample {
   uint32_t t;                    // sweep index
   FastDiv hpd;
   int L, Lt, plane, half_plane, N, n_slots, n_rep, rpw, n_groups;
+  int tau_ap;                    // antiperiodic along tau: the wrap tau bond flips sign
 };
 
 // Shared memory of one tile: T, walker labels, lane -> (r, w) and the plane
@@ -111,6 +112,8 @@ __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n
       const uint32_t i_yp = (nv.y & 0xFFFFu) + offt, i_ym = (nv.y >> 16) + offt;
       const uint32_t i_tp = i2 + (tau + 1 == Lt ? 0u : offt + plane);
       const uint32_t i_tm = i2 + (tau == 0 ? (Lt - 1) * plane : offt - plane);
+      // the antiperiodic wrap bond is unsatisfied when its spins agree
+      const Word gtp = ones_if<Word>(S.tau_ap && tau + 1 == Lt), gtm = ones_if<Word>(S.tau_ap && tau == 0);
       const uint8_t jh = Js[i2];
       const Word Jxp = ones_if<Word>(jh & 1u), Jyp = ones_if<Word>(jh & 2u);
       const Word Jxm = ones_if<Word>(Js[nv.x >> 16] & 1u);
@@ -127,8 +130,8 @@ __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n
           const Word b2 = c ^ ld_word<CG>(w + i_xm) ^ Jxm;
           const Word b3 = c ^ ld_word<CG>(w + i_yp) ^ Jyp;
           const Word b4 = c ^ ld_word<CG>(w + i_ym) ^ Jym;
-          const Word t1 = c ^ ld_word<CG>(w + i_tp);
-          const Word t2 = c ^ ld_word<CG>(w + i_tm);
+          const Word t1 = c ^ ld_word<CG>(w + i_tp) ^ gtp;
+          const Word t2 = c ^ ld_word<CG>(w + i_tm) ^ gtm;
           const Word s1 = b1 ^ b2 ^ b3, c1 = maj3(b1, b2, b3);
           sc[g] = c;
           P0[g] = s1 ^ b4;

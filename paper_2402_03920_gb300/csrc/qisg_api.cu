@@ -234,6 +234,7 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
     return fail(QISG_EINVAL, "word_bits must be 0, 32 or 64");
   if (o.pt_every < 0 || o.measure_every < 0) return fail(QISG_EINVAL, "negative cadence");
   if (o.layout < 0 || o.layout > 2) return fail(QISG_EINVAL, "unknown layout");
+  if (o.tau_antiperiodic != 0 && o.tau_antiperiodic != 1) return fail(QISG_EINVAL, "tau_antiperiodic must be 0 or 1");
 
   qisg_handle *h = new (std::nothrow) qisg_handle();
   if (!h) return fail(QISG_ENOMEM, "host allocation");
@@ -249,6 +250,7 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   h->stream = reinterpret_cast<cudaStream_t>(o.cuda_stream);
   h->mem_budget = o.mem_budget;
   h->per_sample_launch = o.per_sample_launch;
+  h->tau_ap = o.tau_antiperiodic;
   h->k.resize(n_slots);
   h->kt.resize(n_slots);
   for (int s = 0; s < n_slots; ++s) {

@@ -405,6 +405,7 @@ struct qisg_handle {
   uint64_t seed = 0;
   int pt_every = 1, measure_every = 0;
   int layout = QISG_LAYOUT_LANES, W = 64, per_sample_launch = 0;
+  int tau_ap = 0;   // antiperiodic along tau: the wrap tau bond has the opposite sign
   cudaStream_t stream = nullptr;
   size_t mem_budget = 0;
   uint64_t t = 0;          // sweeps done (host mirror of *d_t)

@@ -43,6 +43,7 @@ struct SamplesArgs {
   int t_has_zero;        // some threshold of the table is 0 (always reject)
   uint32_t one, all_ones;   // 1 and 0xFFFFFFFF as runtime values (flag_imad)
   unsigned long long *t_copy;   // blue pass, fused mode: copy t here for the PT pass
+  int tau_ap;                   // antiperiodic along tau: the wrap tau bond flips sign
   // division by the invariants of the index decomposition (32-bit indices)
   FastDiv fd_bps, fd_nq, fd_ns, fd_plane, fd_L;
   // cleared by the red pass (nothing reads them until the blue pass / PT):
@@ -286,8 +287,9 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
         const Word b2 = sc ^ nb[i][1] ^ Jxm;
         const Word b3 = sc ^ nb[i][2] ^ Jyp;
         const Word b4 = sc ^ nb[i][3] ^ Jym;
-        const Word t1 = sc ^ up[i];
-        const Word t2 = sc ^ dn;
+        // the antiperiodic wrap bond is unsatisfied when its spins agree
+        const Word t1 = sc ^ up[i] ^ ones_if<Word>(p.tau_ap && tau + 1 == Lt);
+        const Word t2 = sc ^ dn ^ ones_if<Word>(p.tau_ap && tau == 0);
         // bit-sliced u_s (3 bits) and u_t (2 bits)
         const Word s1 = b1 ^ b2 ^ b3;
         const Word c1 = maj3(b1, b2, b3);
@@ -385,6 +387,7 @@ struct FusedRedArgsT {
   int64_t N;
   int L, Lt, plane, n_slots, n_q, n_rep, blocks_per_set, t_has_zero;
   uint32_t one, all_ones;
+  int tau_ap;
   FastDiv fd_bps, fd_nq, fd_plane, fd_L;
 };
 using FusedRedArgs = FusedRedArgsT<uint32_t>;
@@ -422,6 +425,8 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedR
   const uint32_t ixp = (x + 1 == L ? 0 : x + 1) + L * y, ixm = (x == 0 ? L - 1 : x - 1) + L * y;
   const uint32_t iyp = x + L * (y + 1 == L ? 0 : y + 1), iym = x + L * (y == 0 ? L - 1 : y - 1);
   const uint32_t off = tau * P;
+  // the antiperiodic wrap bond is unsatisfied when its spins agree
+  const uint32_t gtp = ones_if<uint32_t>(p.tau_ap && tau + 1 == Lt), gtm = ones_if<uint32_t>(p.tau_ap && tau == 0);
   // the seven sites: centre, tau + 1 (blue partner), tau - 1, x+, x-, y+, y-
   uint32_t z[7];
   z[0] = i2 + off;
@@ -499,8 +504,8 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedR
         const uint32_t b2 = sc ^ fw[4] ^ Jxm;
         const uint32_t b3 = sc ^ fw[5] ^ Jyp;
         const uint32_t b4 = sc ^ fw[6] ^ Jym;
-        const uint32_t t1 = sc ^ fw[1];
-        const uint32_t t2 = sc ^ fw[2];
+        const uint32_t t1 = sc ^ fw[1] ^ gtp;
+        const uint32_t t2 = sc ^ fw[2] ^ gtm;
         const uint32_t s1 = b1 ^ b2 ^ b3;
         const uint32_t c1 = maj3(b1, b2, b3);
         const uint32_t us0 = s1 ^ b4;
@@ -593,6 +598,8 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const Fused
   const uint32_t ixp = (x + 1 == L ? 0 : x + 1) + L * y, ixm = (x == 0 ? L - 1 : x - 1) + L * y;
   const uint32_t iyp = x + L * (y + 1 == L ? 0 : y + 1), iym = x + L * (y == 0 ? L - 1 : y - 1);
   const uint32_t off = tau * P;
+  // the antiperiodic wrap bond is unsatisfied when its spins agree
+  const Word gtp = ones_if<Word>(p.tau_ap && tau + 1 == Lt), gtm = ones_if<Word>(p.tau_ap && tau == 0);
   uint32_t zo[7];   // word offsets of the seven sites' replica groups
   {
     uint32_t z[7];
@@ -690,8 +697,8 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const Fused
       const Word b2 = sc ^ fw[4][jj] ^ Jxm;
       const Word b3 = sc ^ fw[5][jj] ^ Jyp;
       const Word b4 = sc ^ fw[6][jj] ^ Jym;
-      const Word t1 = sc ^ fw[1][jj];
-      const Word t2 = sc ^ fw[2][jj];
+      const Word t1 = sc ^ fw[1][jj] ^ gtp;
+      const Word t2 = sc ^ fw[2][jj] ^ gtm;
       const Word s1 = b1 ^ b2 ^ b3;
       const Word c1 = maj3(b1, b2, b3);
       const Word us0 = s1 ^ b4;
@@ -834,6 +841,8 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
       Quad4 nxt;
       if (PF && k + 1 < G) load_next(nxt);
       const uint4 R4 = philox(make_uint4((uint32_t)i2 + off, (uint32_t)t, ctr_z, ctr_w), p.key);
+      // the antiperiodic wrap bond is unsatisfied when its spins agree
+      const uint32_t gtp = ones_if<uint32_t>(p.tau_ap && tau + 1 == Lt), gtm = ones_if<uint32_t>(p.tau_ap && tau == 0);
       uint32_t f[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -842,8 +851,8 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
         const uint32_t b2 = sc ^ q4(cur.xm, j) ^ Jxm;
         const uint32_t b3 = sc ^ q4(cur.yp, j) ^ Jyp;
         const uint32_t b4 = sc ^ q4(cur.ym, j) ^ Jym;
-        const uint32_t t1 = sc ^ q4(cur.up, j);
-        const uint32_t t2 = sc ^ q4(dn, j);
+        const uint32_t t1 = sc ^ q4(cur.up, j) ^ gtp;
+        const uint32_t t2 = sc ^ q4(dn, j) ^ gtm;
         const uint32_t s1 = b1 ^ b2 ^ b3;
         const uint32_t c1 = maj3(b1, b2, b3);
         const uint32_t us0 = s1 ^ b4;
@@ -1249,6 +1258,7 @@ SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
   p.fd_plane = FastDiv((uint32_t)p.plane);
   p.fd_L = FastDiv((uint32_t)p.L);
   p.t_copy = nullptr;
+  p.tau_ap = h->tau_ap;
   return p;
 }
 
@@ -1351,6 +1361,7 @@ int fused_red(qisg_handle *h) {
   p.t_has_zero = a.t_has_zero;
   p.one = 1u;
   p.all_ones = 0xFFFFFFFFu;
+  p.tau_ap = h->tau_ap;
   // threads per site from the red tile: 1 -> four, 2 -> two, else one
   // (64-bit words: at most two replicas per thread)
   int tpsite = h->sweep_tile[0] == 1 ? 4 : h->sweep_tile[0] == 2 ? 2 : 1;

@@ -36,7 +36,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("word_bits", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("mem_budget", ctypes.c_size_t), ("pt_every", ctypes.c_int),
                 ("measure_every", ctypes.c_int), ("layout", ctypes.c_int),
-                ("per_sample_launch", ctypes.c_int)]
+                ("per_sample_launch", ctypes.c_int), ("tau_antiperiodic", ctypes.c_int)]
 
 
 _lib = None
@@ -164,6 +164,7 @@ class Config:
     measure_every: int = 0
     layout: int = QISG_LAYOUT_AUTO
     per_sample_launch: int = 0
+    tau_antiperiodic: int = 0
     mem_budget: int = 0
 
 
@@ -187,6 +188,7 @@ class Instance:
         opts.measure_every = cfg.measure_every
         opts.layout = cfg.layout
         opts.per_sample_launch = cfg.per_sample_launch
+        opts.tau_antiperiodic = cfg.tau_antiperiodic
         self._h = ctypes.c_void_p()
         _check(lib.qisg_create(ctypes.byref(self._h), cfg.L, cfg.L_tau, _ptr(ladder), self.n_slots,
                                cfg.n_replicas, cfg.n_samples, cfg.seed, ctypes.byref(opts)))

@@ -21,8 +21,9 @@ def make(qisg, L, Lt, lo, hi, n_slots, gamma, n_rep, n_samples, seed, **kw):
     return qisg.Instance(cfg), ladder
 
 
-def oracle_state(ladder, L, Lt, n_rep, seed, a_lo=0, n_a=1):
-    return oracle.new_state(L, Lt, ladder[:, 0], ladder[:, 1], n_rep, seed, a_lo=a_lo, n_a=n_a)
+def oracle_state(ladder, L, Lt, n_rep, seed, a_lo=0, n_a=1, tau_ap=False):
+    return oracle.new_state(L, Lt, ladder[:, 0], ladder[:, 1], n_rep, seed, a_lo=a_lo, n_a=n_a,
+                            tau_ap=tau_ap)
 
 
 def assert_same_state(inst, st, a_lo=0, what=""):

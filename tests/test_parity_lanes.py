@@ -187,3 +187,22 @@ def test_production_shape_sampled(qisg):
             st = oracle_state(ladder, w.L, w.L_tau, w.n_replicas, w.seed, a, 1)
             oracle.run(st, 6, measure_every=w.measure_every)
             assert_same_state(inst, st, a_lo=a, what=f"sample {a}")
+
+
+@pytest.mark.parametrize("W,per_sample", [(64, 0), (32, 1)])
+def test_antiperiodic_tau_bit_exact(qisg, W, per_sample):
+    """Antiperiodic boundary along tau in the LANES packing against the oracle."""
+    L, Lt, n_slots, n_rep, n_samples = 4, 6, 8, 4 if W == 64 else 2, 3
+    inst, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 0.9, n_rep, n_samples, 29, word_bits=W,
+                        layout=qisg.QISG_LAYOUT_LANES, measure_every=3, per_sample_launch=per_sample,
+                        tau_antiperiodic=1)
+    st = oracle_state(ladder, L, Lt, n_rep, 29, 0, n_samples, tau_ap=True)
+    with inst:
+        assert_same_state(inst, st, what="start")
+        for n in (1, 5, 12):
+            inst.sweep(n)
+            oracle.run(st, n, pt_every=1, measure_every=3)
+            assert_same_state(inst, st, what=f"W={W} after {st.t}")
+        sA, sB, sq, sq2, nm = inst.measurements()
+        assert nm == st.n_meas
+        assert np.array_equal(sA, st.sumA) and np.array_equal(sB, st.sumB)

@@ -220,3 +220,25 @@ def test_autotune_keeps_trajectory(qisg, word_bits, n_cand):
         b.sweep(n + 6)
         assert np.array_equal(a.spins(), b.spins())
         assert np.array_equal(a.permutation(), b.permutation())
+
+
+@pytest.mark.parametrize("W,tiles", [(32, ((1, 4), (0, 0))), (32, ((2, 2), (0, 1))), (32, ((4, 1), (0, 0))),
+                                     (64, ((0, 0), (0, 0))), (64, ((1, 1), (0, 0)))])
+def test_antiperiodic_tau_bit_exact(qisg, W, tiles):
+    """Antiperiodic boundary along tau (the wrap tau bond counts -S S): every
+    red and blue kernel form against the oracle with the same boundary."""
+    L, Lt, n_slots, n_rep, n_samples = 4, 6, 5, 4, W
+    inst, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 0.9, n_rep, n_samples, 23, word_bits=W,
+                        layout=qisg.QISG_LAYOUT_SAMPLES, measure_every=3, tau_antiperiodic=1)
+    st = oracle_state(ladder, L, Lt, n_rep, 23, 0, n_samples, tau_ap=True)
+    with inst:
+        inst.set_tiles(*tiles)
+        assert_same_state(inst, st, what="start")
+        for n in (1, 5, 12):
+            inst.sweep(n)
+            oracle.run(st, n, pt_every=1, measure_every=3)
+            assert_same_state(inst, st, what=f"W={W} tiles={tiles} after {st.t}")
+        sA, sB, sq, sq2, nm = inst.measurements()
+        assert nm == st.n_meas
+        assert np.array_equal(sA, st.sumA) and np.array_equal(sB, st.sumB)
+        assert np.array_equal(sq, st.sumq) and np.array_equal(sq2, st.sumq2)
