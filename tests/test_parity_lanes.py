@@ -206,3 +206,22 @@ def test_antiperiodic_tau_bit_exact(qisg, W, per_sample):
         sA, sB, sq, sq2, nm = inst.measurements()
         assert nm == st.n_meas
         assert np.array_equal(sA, st.sumA) and np.array_equal(sB, st.sumB)
+
+
+@pytest.mark.parametrize("W,L,Lt,n_slots,n_rep,pt_every,measure_every", [
+    (32, 4, 4, 1, 1, 1, 2),      # one slot, one replica
+    (64, 4, 2, 8, 8, 1, 3),      # L_tau = 2, a full 64-lane word
+    (32, 6, 6, 8, 2, 3, 1),      # PT every 3rd sweep
+])
+def test_edge_cases_bit_exact(qisg, W, L, Lt, n_slots, n_rep, pt_every, measure_every):
+    inst, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 0.9, n_rep, 2, 37 + L, word_bits=W,
+                        layout=qisg.QISG_LAYOUT_LANES, pt_every=pt_every, measure_every=measure_every)
+    st = oracle_state(ladder, L, Lt, n_rep, 37 + L, 0, 2)
+    with inst:
+        for n in (1, 7, 24):
+            inst.sweep(n)
+            oracle.run(st, n, pt_every=pt_every, measure_every=measure_every)
+            assert_same_state(inst, st, what=f"after {st.t}")
+        sA, sB, sq, sq2, nm = inst.measurements()
+        assert nm == st.n_meas
+        assert np.array_equal(sA, st.sumA) and np.array_equal(sB, st.sumB)

@@ -242,3 +242,30 @@ def test_antiperiodic_tau_bit_exact(qisg, W, tiles):
         assert nm == st.n_meas
         assert np.array_equal(sA, st.sumA) and np.array_equal(sB, st.sumB)
         assert np.array_equal(sq, st.sumq) and np.array_equal(sq2, st.sumq2)
+
+
+@pytest.mark.parametrize("W,L,Lt,n_slots,n_rep,n_samples,pt_every,measure_every", [
+    (32, 4, 4, 1, 1, 32, 1, 2),      # one slot (no PT pair), one replica (no overlap pair)
+    (64, 4, 6, 32, 4, 64, 1, 5),     # the largest ladder (32 slots)
+    (32, 4, 2, 6, 4, 32, 1, 3),      # L_tau = 2: both tau bonds join the same pair of sites
+    (32, 6, 8, 6, 4, 20, 3, 1),      # PT every 3rd sweep, odd graph cycle (doubled for the two buffers)
+    (64, 4, 8, 6, 3, 64, 0, 4),      # no PT at all
+    (32, 2, 4, 3, 2, 7, 2, 3),       # the smallest lattice, ragged lanes
+])
+def test_edge_cases_bit_exact(qisg, W, L, Lt, n_slots, n_rep, n_samples, pt_every, measure_every):
+    inst, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 0.9, n_rep, n_samples, 31 + L, word_bits=W,
+                        layout=qisg.QISG_LAYOUT_SAMPLES, pt_every=pt_every, measure_every=measure_every)
+    st = oracle_state(ladder, L, Lt, n_rep, 31 + L, 0, n_samples)
+    with inst:
+        inst.sweep(0)                     # a no-op
+        assert inst.sweep_count() == 0
+        assert_same_state(inst, st, what="start")
+        for n in (1, 7, 24):
+            inst.sweep(n)
+            oracle.run(st, n, pt_every=pt_every, measure_every=measure_every)
+            assert_same_state(inst, st, what=f"after {st.t}")
+        sA, sB, sq, sq2, nm = inst.measurements()
+        assert nm == st.n_meas
+        assert np.array_equal(sA, st.sumA) and np.array_equal(sB, st.sumB)
+        if n_rep > 1:
+            assert np.array_equal(sq, st.sumq) and np.array_equal(sq2, st.sumq2)
