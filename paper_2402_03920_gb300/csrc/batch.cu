@@ -119,13 +119,13 @@ __device__ __forceinline__ bool live(const InstDev &I) { return I.active && __ld
 
 // The persistent kernel: n_sweeps x (red tiles | barrier | blue tiles |
 // barrier | PT chains | barrier | advance | barrier).  Block b takes the
-// contiguous tile range [b n_tiles / grid, (b+1) n_tiles / grid).
+// contiguous tile range [bstart[b], bstart[b+1]) (ranges of about equal cost).
 __global__ void __launch_bounds__(kBatchBlock) batch_kernel(InstDev *insts, int n_inst, const Tile *tiles,
-                                                            int n_tiles, const ChainRef *chains, int n_chains,
-                                                            int n_sweeps, unsigned *bar, int *err) {
+                                                            int n_tiles, const int *bstart, const ChainRef *chains,
+                                                            int n_chains, int n_sweeps, unsigned *bar, int *err) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int64_t lo = (int64_t)blockIdx.x * n_tiles / gridDim.x;
-  const int64_t hi = (int64_t)(blockIdx.x + 1) * n_tiles / gridDim.x;
+  const int64_t lo = bstart[blockIdx.x];
+  const int64_t hi = bstart[blockIdx.x + 1];
   const int warps = (gridDim.x * blockDim.x) >> 5;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   for (int sw = 0; sw < n_sweeps; ++sw) {
@@ -257,6 +257,8 @@ struct qisg_batch {
   qisg::InstDev *d_inst = nullptr;
   qisg::Tile *d_tiles = nullptr;
   size_t tiles_cap = 0;
+  int *d_bstart = nullptr;   // first tile of each block (grid + 1 entries)
+  size_t bstart_cap = 0;
   int n_tiles = 0;
   qisg::ChainRef *d_chains = nullptr;
   size_t chains_cap = 0;
@@ -332,6 +334,35 @@ int build_tables(qisg_batch *B) {
   if (rc) return rc;
   if (per_sm < 1) return fail(QISG_EINVAL, "batch kernel does not fit on an SM");
   B->grid = per_sm * B->n_sm;
+  // contiguous tile ranges of about equal cost per block (a tile costs its
+  // sites times its lanes, plus a fixed share for its set-up), so that blocks
+  // reach the grid barriers together
+  std::vector<int> bstart((size_t)B->grid + 1, (int)tiles.size());
+  {
+    std::vector<double> cum(tiles.size() + 1, 0.0);
+    for (size_t k = 0; k < tiles.size(); ++k) {
+      const InstDev &I = B->slots[tiles[k].inst].dev;
+      cum[k + 1] = cum[k] + (double)tiles[k].n * (double)(I.n_rep * I.n_slots + 32) + 4096.0;
+    }
+    size_t k = 0;
+    for (int b = 0; b <= B->grid; ++b) {
+      const double target = cum.back() * (double)b / (double)B->grid;
+      while (k < tiles.size() && cum[k] < target) ++k;
+      bstart[(size_t)b] = (int)k;
+    }
+    bstart[(size_t)B->grid] = (int)tiles.size();
+  }
+  if (bstart.size() > B->bstart_cap) {
+    if (B->d_bstart) cudaFree(B->d_bstart);
+    B->d_bstart = nullptr;
+    B->bstart_cap = std::max<size_t>(bstart.size(), 2 * B->bstart_cap);
+    rc = cuda_check(cudaMalloc(&B->d_bstart, B->bstart_cap * sizeof(int)), "block table");
+    if (rc) return rc;
+  }
+  rc = cuda_check(cudaMemcpyAsync(B->d_bstart, bstart.data(), bstart.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                  B->stream),
+                  "copy block table");
+  if (rc) return rc;
   B->dirty = false;
   return QISG_OK;
 }
@@ -556,8 +587,8 @@ int qisg_batch_run(qisg_batch *B, int64_t n_sweeps) {
   int64_t left = n_sweeps;
   while (left > 0 && !rc) {
     int ns = (int)std::min<int64_t>(left, chunk);
-    void *args[] = {&B->d_inst, &B->capacity, &B->d_tiles, &B->n_tiles, &B->d_chains, &B->n_chains, &ns,
-                    &B->d_bar, &B->d_err};
+    void *args[] = {&B->d_inst, &B->capacity, &B->d_tiles, &B->n_tiles, &B->d_bstart, &B->d_chains, &B->n_chains,
+                    &ns, &B->d_bar, &B->d_err};
     rc = cuda_check(cudaMemsetAsync(B->d_bar, 0, 2 * sizeof(unsigned), B->stream), "reset barrier");
     if (rc) break;
     rc = cuda_check(cudaLaunchCooperativeKernel((const void *)batch_kernel, dim3((unsigned)B->grid),
@@ -697,6 +728,7 @@ void qisg_batch_destroy(qisg_batch *B) {
   if (B->arena) cudaFree(B->arena);
   if (B->d_inst) cudaFree(B->d_inst);
   if (B->d_tiles) cudaFree(B->d_tiles);
+  if (B->d_bstart) cudaFree(B->d_bstart);
   if (B->d_chains) cudaFree(B->d_chains);
   if (B->d_bar) cudaFree(B->d_bar);
   if (B->d_err) cudaFree(B->d_err);
