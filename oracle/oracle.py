@@ -1,7 +1,8 @@
 """ctypes driver for the plain-C oracle (test infrastructure only).
 
 Every function here marshals numpy arrays into ``qisg_oracle.c`` and back;
-the arithmetic of the method lives in the C file, whose comments cite the
+the arithmetic of the method lives in the C file (except the daemon rule's
+cumulative tables, written out below in decimal arithmetic), whose comments cite the
 paper passage each step follows (Sec. 1 Eq. (2)-(3), Sec. 2.1, Sec. 2.1.1,
 Appendix E.1).  ``build()`` compiles it with gcc; nothing of the product
 package is imported.
@@ -9,6 +10,7 @@ package is imported.
 from __future__ import annotations
 
 import ctypes
+import decimal
 import os
 import subprocess
 import threading
@@ -62,7 +64,7 @@ def _load():
             lib.orc_init_spins.argtypes = [i32, i32, i32, i32, i64, i64, u64, P]
             lib.orc_init_spins.restype = None
             lib.orc_run.argtypes = [i32, i32, i32, i32, i64, i64, u64, P, P, i32, i32,
-                                    P, P, P, u64, i64, P, P, P, P, P, P, P, i32, i32]
+                                    P, P, P, u64, i64, P, P, P, P, P, P, P, i32, i32, P]
             lib.orc_run.restype = i32
             lib.orc_energies.argtypes = [i32, i32, i32, i32, i64, P, P, P, P, i32]
             lib.orc_energies.restype = None
@@ -70,6 +72,16 @@ def _load():
             lib.orc_pt_only.restype = None
             lib.orc_pow_by_squaring.argtypes = [f64, u64]
             lib.orc_pow_by_squaring.restype = f64
+            lib.orc_xoroshiro128pp_step.argtypes = [P]
+            lib.orc_xoroshiro128pp_step.restype = None
+            lib.orc_daemon_nstar.argtypes = [P, u64]
+            lib.orc_daemon_nstar.restype = ctypes.c_uint32
+            lib.orc_daemon_bword.argtypes = [u64, i64, i32, i32, ctypes.c_uint32, u64, i32, P]
+            lib.orc_daemon_bword.restype = ctypes.c_uint32
+            lib.orc_daemon_level.argtypes = [i32, i32, i32]
+            lib.orc_daemon_level.restype = i32
+            lib.orc_daemon_flip.argtypes = [i32, i32]
+            lib.orc_daemon_flip.restype = i32
             _lib = lib
     return _lib
 
@@ -114,6 +126,60 @@ def pt_bases(k, ktau):
 
 def pow_by_squaring(b: float, e: int) -> float:
     return _load().orc_pow_by_squaring(float(b), int(e))
+
+
+# --------------------------------------------------------------------------
+# Daemon rule (Sec. 2.1.1, Appendices C and D)
+# --------------------------------------------------------------------------
+
+def daemon_cumulative(k: float) -> np.ndarray:
+    """cumulative(n), n = 0..254, of Sec. 2.1.1 for coupling k: the 64-bit
+    truncation of 2^64 sum_{m <= n} P[m], P[m] = p^pop(m) (1-p)^(8-pop(m)),
+    p = e^{-4k}.  The paper evaluates the sum in 128-bit floating point; here
+    it is evaluated with 80 significant decimal digits (the exact value's
+    truncation, which 128-bit arithmetic also gives unless the sum lies
+    within about 2^-49 of an integer)."""
+    with decimal.localcontext() as ctx:
+        ctx.prec = 80
+        p = (decimal.Decimal(-4) * decimal.Decimal(float(k))).exp()
+        q = 1 - p
+        scale = decimal.Decimal(2) ** 64
+        acc = decimal.Decimal(0)
+        out = np.zeros(255, dtype=np.uint64)
+        for n in range(255):
+            c = bin(n).count("1")
+            acc += (p ** c) * (q ** (8 - c))
+            out[n] = int((acc * scale).to_integral_value(rounding=decimal.ROUND_FLOOR))
+    return out
+
+
+def daemon_tables(k) -> np.ndarray:
+    """[n_slots][255] cumulative tables of a ladder."""
+    return np.ascontiguousarray(np.stack([daemon_cumulative(float(v)) for v in k]), dtype=np.uint64)
+
+
+def xoroshiro128pp_step(s0: int, s1: int):
+    st = np.array([s0, s1], dtype=np.uint64)
+    _load().orc_xoroshiro128pp_step(_ptr(st))
+    return int(st[0]), int(st[1])
+
+
+def daemon_nstar(cum: np.ndarray, R: int) -> int:
+    return int(_load().orc_daemon_nstar(_ptr(np.ascontiguousarray(cum, dtype=np.uint64)), int(R)))
+
+
+def daemon_bword(seed: int, a: int, r: int, s: int, wsite: int, t: int, which: int,
+                 cum: np.ndarray) -> int:
+    return int(_load().orc_daemon_bword(seed, a, r, s, wsite, t, which,
+                                        _ptr(np.ascontiguousarray(cum, dtype=np.uint64))))
+
+
+def daemon_level(b4: int, b8: int, b12: int) -> int:
+    return int(_load().orc_daemon_level(b4, b8, b12))
+
+
+def daemon_flip(u: int, d: int) -> bool:
+    return bool(_load().orc_daemon_flip(u, d))
 
 
 def init_couplings(L: int, a_lo: int, n_a: int, seed: int) -> np.ndarray:
@@ -175,6 +241,7 @@ class OracleState:
     sumq2: np.ndarray = None
     n_meas: int = 0
     tau_ap: bool = False     # antiperiodic along tau
+    cum: np.ndarray = None   # daemon rule: [n_slots][255] cumulative tables; None: thresholds
 
     @property
     def n_slots(self) -> int:
@@ -185,14 +252,20 @@ class OracleState:
         return self.L * self.L * self.Ltau
 
 
-def new_state(L, Ltau, k, ktau, n_rep, seed, a_lo=0, n_a=1, tau_ap=False) -> OracleState:
+def new_state(L, Ltau, k, ktau, n_rep, seed, a_lo=0, n_a=1, tau_ap=False,
+              daemon=False) -> OracleState:
+    """daemon: the paper's multi-site daemon rule (needs k_tau = k and
+    L_tau a multiple of 64) instead of the threshold table."""
     k = np.ascontiguousarray(k, dtype=np.float64)
     kt = np.ascontiguousarray(ktau, dtype=np.float64)
     n_slots = len(k)
+    if daemon and (not np.array_equal(k, kt) or Ltau % 64 != 0):
+        raise ValueError("the daemon rule needs k_tau = k and L_tau a multiple of 64")
     J = init_couplings(L, a_lo, n_a, seed)
     S = init_spins(L, Ltau, n_slots, n_rep, a_lo, n_a, seed)
     wa = np.tile(np.arange(n_slots, dtype=np.int32), (n_a, n_rep, 1)).copy()
-    st = OracleState(L, Ltau, k, kt, n_rep, a_lo, n_a, seed, J, S, wa, tau_ap=bool(tau_ap))
+    st = OracleState(L, Ltau, k, kt, n_rep, a_lo, n_a, seed, J, S, wa, tau_ap=bool(tau_ap),
+                     cum=daemon_tables(k) if daemon else None)
     alloc_obs(st)
     refresh_energies(st)
     return st
@@ -226,7 +299,10 @@ def run(st: OracleState, n_sweeps: int, pt_every: int = 1, measure_every: int = 
                      _ptr(st.k), _ptr(st.ktau), pt_every, measure_every,
                      _ptr(st.J), _ptr(st.S), _ptr(st.walker_at), st.t, n_sweeps,
                      _ptr(st.A), _ptr(st.B), _ptr(st.sumA), _ptr(st.sumB),
-                     _ptr(st.sumq), _ptr(st.sumq2), ctypes.byref(n_meas), n_threads, int(st.tau_ap))
+                     _ptr(st.sumq), _ptr(st.sumq2), ctypes.byref(n_meas), n_threads, int(st.tau_ap),
+                     _ptr(st.cum) if st.cum is not None else None)
+    if rc == -2:
+        raise ValueError("the daemon rule needs k_tau = k, L_tau % 64 == 0 and fewer than 2^24 samples")
     if rc != 0:
         raise MemoryError("oracle run failed")
     st.t += n_sweeps

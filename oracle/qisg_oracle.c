@@ -23,6 +23,18 @@
  *   - observables: integer energies and the replica overlap (Appendix E.1).
  *   - Philox4x32-10 (Sec. 2.1.1), the counter-based generator of Salmon et
  *     al. (SC'11), written here from its published definition.
+ *   - the paper's own update rule (Sec. 2.1 and 2.1.1, Appendices C and D),
+ *     for equal couplings k_tau = k: multi-site coding puts 32 tau-sites of
+ *     one system in a word (site (x, y, tau) is bit
+ *     tau / M of word (x, y, tau mod M), M = L_tau / 32), and a flip is taken
+ *     iff u + d >= 3, with u the number of unsatisfied bonds of the site
+ *     (0..6) and d the site's two-bit Ito-Kanada daemon.  The daemon is the
+ *     number of leading ones in the bits (b4, b8, b12) of three words whose
+ *     bits are independent and set with probability e^{-4k}; each byte of
+ *     such a word is the inverse-cumulative image of a 64-bit "50/50" word
+ *     whose upper half comes from Philox4x32-10 and lower half from one
+ *     xoroshiro128++ state step (Blackman and Vigna, 2019) of the same
+ *     Philox output.
  *
  * Storage is one int8 spin per (sample, replica, walker, site); every loop
  * runs in plain order.  Floating point is IEEE double with no contraction
@@ -38,7 +50,7 @@
 #endif
 
 /* Philox counter domains: one per kind of draw. */
-enum { ORC_DOM_J = 1, ORC_DOM_INIT = 2, ORC_DOM_SWEEP = 3, ORC_DOM_PT = 4 };
+enum { ORC_DOM_J = 1, ORC_DOM_INIT = 2, ORC_DOM_SWEEP = 3, ORC_DOM_PT = 4, ORC_DOM_DAEMON = 5 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Sec. 2.1.1; Salmon, Moraes, Dror, Shaw, SC'11).            */
@@ -190,6 +202,83 @@ void orc_init_spins(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64
 }
 
 /* ------------------------------------------------------------------------ */
+/* Daemon bits (Sec. 2.1.1, Appendices C and D).                             */
+/* ------------------------------------------------------------------------ */
+
+/* One state step of xoroshiro128++ (Blackman and Vigna, "Scrambled linear
+ * pseudorandom number generators", 2019): with t = s1 xor s0, the new state
+ * is (rotl(s0, 49) xor t xor (t << 21), rotl(t, 28)).  The "++" output
+ * scrambler is not part of the state step. */
+static uint64_t rotl64(uint64_t v, int k) { return (v << k) | (v >> (64 - k)); }
+
+void orc_xoroshiro128pp_step(uint64_t st[2])
+{
+    uint64_t s0 = st[0];
+    uint64_t tt = st[1] ^ s0;
+    st[0] = rotl64(s0, 49) ^ tt ^ (tt << 21);
+    st[1] = rotl64(tt, 28);
+}
+
+/* n* of a 64-bit word R under the cumulative table cum[0..254] of one k
+ * (Sec. 2.1.1): the n with cumulative(n-1) <= R < cumulative(n), where
+ * cumulative(-1) is below every word and cumulative(255) = 2^64 - 1 (R =
+ * 2^64 - 1 gives 255).  Since the table is non-decreasing this is the number
+ * of n in 0..254 with cum[n] <= R. */
+uint32_t orc_daemon_nstar(const uint64_t *cum, uint64_t R)
+{
+    uint32_t c = 0;
+    int n;
+    for (n = 0; n < 255; ++n) c += (cum[n] <= R);
+    return c;
+}
+
+/* Daemon word `which` (0: b4, 1: b8, 2: b12) of word-site wsite of system
+ * (a, r, slot s) in sweep t.  One Philox4x32-10 call gives the upper halves
+ * x_0..x_3 of four 64-bit words; the same 128 bits, read as the xoroshiro
+ * state (x_0 | x_1 << 32, x_2 | x_3 << 32), take one state step, whose four
+ * 32-bit quarters (same order) are the lower halves.  Byte i of the word is
+ * n* of 64-bit word i. */
+uint32_t orc_daemon_bword(uint64_t seed, int64_t a, int r, int s, uint32_t wsite, uint64_t t,
+                          int which, const uint64_t *cum)
+{
+    uint32_t ctr[4], key[2], x[4], lo[4], b = 0;
+    uint64_t st[2];
+    int i;
+    ctr[0] = wsite;
+    ctr[1] = (uint32_t)t;
+    ctr[2] = (uint32_t)s | ((uint32_t)r << 16);
+    ctr[3] = ((uint32_t)ORC_DOM_DAEMON << 28) | ((uint32_t)which << 24) | (uint32_t)a;
+    key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32);
+    orc_philox4x32_10(ctr, key, x);
+    st[0] = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+    st[1] = (uint64_t)x[2] | ((uint64_t)x[3] << 32);
+    orc_xoroshiro128pp_step(st);
+    lo[0] = (uint32_t)st[0]; lo[1] = (uint32_t)(st[0] >> 32);
+    lo[2] = (uint32_t)st[1]; lo[3] = (uint32_t)(st[1] >> 32);
+    for (i = 0; i < 4; ++i)
+        b |= orc_daemon_nstar(cum, ((uint64_t)x[i] << 32) | lo[i]) << (8 * i);
+    return b;
+}
+
+/* The daemon's level d in 0..3 from one bit of each of b4, b8, b12
+ * (Appendix C): after b8 &= b4 and b12 &= b8 the four reachable patterns
+ * 000, 100, 110, 111 stand for d = 0, 1, 2, 3, i.e. d is the number of
+ * leading ones of (b4, b8, b12). */
+int orc_daemon_level(int b4, int b8, int b12)
+{
+    if (!b4) return 0;
+    if (!b8) return 1;
+    if (!b12) return 2;
+    return 3;
+}
+
+/* Metropolis with the daemon at equal couplings (Sec. 2.1, Ito and Kanada):
+ * flipping a site with u unsatisfied bonds out of 6 changes the energy of
+ * Eq. (3) by 12 - 4u, and the daemon pays for it iff u + d >= 3, which has
+ * probability min(1, e^{-4k(3-u)}). */
+int orc_daemon_flip(int u, int d) { return u + d >= 3; }
+
+/* ------------------------------------------------------------------------ */
 /* The Markov chain.                                                         */
 /* ------------------------------------------------------------------------ */
 
@@ -199,6 +288,7 @@ typedef struct {
     uint64_t seed;
     const uint32_t *T;                  /* [n_slots][5][3] */
     const double *ap, *am, *bp, *bm;    /* [n_slots-1] */
+    const uint64_t *cum;                /* daemon rule: [n_slots][255]; NULL: thresholds */
 } orc_model;
 
 /* A = sum over spatial bonds of J S S, B = sum over imaginary-time bonds of
@@ -260,6 +350,19 @@ static void half_sweep(const orc_model *m, int64_t a, const int8_t *J, int8_t *S
                         us += (J[(x + L * ym) * 2 + 1] * si * Sw[x + L * ym + (int64_t)L * L * tau] == -1);
                         ut += (gp * si * Sw[x + L * y + (int64_t)L * L * tp] == -1);
                         ut += (gm * si * Sw[x + L * y + (int64_t)L * L * tm] == -1);
+                        if (m->cum) {
+                            /* daemon rule: site (x, y, tau) is bit j = tau / M of
+                             * word-site x + L y + L^2 (tau mod M), M = L_tau / 32 */
+                            int M = Lt / 32, j = tau / M, d;
+                            uint32_t ws = (uint32_t)(x + L * y + (int64_t)L * L * (tau % M));
+                            const uint64_t *cs = m->cum + (int64_t)s * 255;
+                            uint32_t b4 = orc_daemon_bword(m->seed, a, r, s, ws, t, 0, cs);
+                            uint32_t b8 = orc_daemon_bword(m->seed, a, r, s, ws, t, 1, cs);
+                            uint32_t b12 = orc_daemon_bword(m->seed, a, r, s, ws, t, 2, cs);
+                            d = orc_daemon_level((b4 >> j) & 1, (b8 >> j) & 1, (b12 >> j) & 1);
+                            if (orc_daemon_flip(us + ut, d)) Sw[site] = (int8_t)(-si);
+                            continue;
+                        }
                         thr = m->T[(s * 5 + us) * 3 + ut];
                         R = philox_word((uint32_t)site, (uint32_t)t,
                                         (uint32_t)s | ((uint32_t)(r >> 2) << 16),
@@ -312,13 +415,15 @@ static void pt_pass(const orc_model *m, int64_t a, int r, uint64_t t,
  *   sumq,sumq2[n_a][n_slots][n_rep(n_rep-1)/2]    in/out: overlap sums
  *   n_meas                                        in/out: measurements taken
  * Observables may be NULL when measure_every == 0.  tau_ap: antiperiodic
- * boundary along tau (0: periodic).
+ * boundary along tau (0: periodic).  daemon_cum: NULL for the threshold
+ * rule; else the daemon rule with the cumulative tables [n_slots][255] of
+ * Sec. 2.1.1 (needs k_tau = k for every slot and L_tau a multiple of 64).
  */
 int orc_run(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64_t n_a, uint64_t seed,
             const double *k, const double *ktau, int pt_every, int measure_every,
             const int8_t *J, int8_t *S, int32_t *walker_at, uint64_t t0, int64_t n_sweeps,
             int64_t *A, int64_t *B, int64_t *sumA, int64_t *sumB, int64_t *sumq, int64_t *sumq2,
-            int64_t *n_meas, int n_threads, int tau_ap)
+            int64_t *n_meas, int n_threads, int tau_ap, const uint64_t *daemon_cum)
 {
     orc_model m;
     uint32_t *T;
@@ -337,6 +442,15 @@ int orc_run(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64_t n_a, 
     m.L = L; m.Ltau = Ltau; m.n_slots = n_slots; m.n_rep = n_rep; m.seed = seed;
     m.tau_ap = tau_ap;
     m.T = T; m.ap = ap; m.am = am; m.bp = bp; m.bm = bm;
+    m.cum = daemon_cum;
+    if (daemon_cum) {
+        int s;
+        if (Ltau % 64 != 0 || a_lo + n_a > ((int64_t)1 << 24) || n_rep > 4096) {
+            free(T); free(ap); return -2;
+        }
+        for (s = 0; s < n_slots; ++s)
+            if (k[s] != ktau[s]) { free(T); free(ap); return -2; }
+    }
 
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -415,6 +529,7 @@ void orc_energies(int L, int Ltau, int n_slots, int n_rep, int64_t n_a, const in
     orc_model m;
     int64_t N = (int64_t)L * L * Ltau, c;
     m.L = L; m.Ltau = Ltau; m.n_slots = n_slots; m.n_rep = n_rep; m.tau_ap = tau_ap;
+    m.cum = NULL;
     for (c = 0; c < n_a * n_rep * n_slots; ++c)
         energies_of(&m, J + (c / (n_rep * n_slots)) * L * L * 2, S + c * N, &A[c], &B[c]);
 }
@@ -428,6 +543,7 @@ void orc_pt_only(int n_slots, int n_rep, int64_t a, uint64_t seed, const double 
     double *ap = (double *)malloc(sizeof(double) * 4 * (size_t)(n_slots > 1 ? n_slots : 2));
     int r;
     m.n_slots = n_slots; m.n_rep = n_rep; m.seed = seed;
+    m.cum = NULL;
     m.ap = ap; m.am = ap + n_slots; m.bp = ap + 2 * n_slots; m.bm = ap + 3 * n_slots;
     orc_pt_bases(n_slots, k, ktau, ap, ap + n_slots, ap + 2 * n_slots, ap + 3 * n_slots);
     for (r = 0; r < n_rep; ++r)
