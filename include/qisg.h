@@ -58,10 +58,25 @@ extern "C" {
  * SAMPLES: a word holds 32 or 64 SAMPLES at one (replica, slot); the draw of
  *   a (replica, slot, site, sweep) is shared by the 64 samples of a sample
  *   block, as in Ito-Kanada's multi-sample coding (Sec. 2.1.1); PT moves the
- *   spin bits of each sample between slot words.                           */
+ *   spin bits of each sample between slot words.
+ * SITES: the paper's own multi-site coding with its update rule (Sec. 2.1,
+ *   Sec. 2.1.1, Appendices C and D): a 32-bit word holds 32 imaginary-time
+ *   sites of ONE system (site (x, y, tau) is bit tau / M of word-site
+ *   x + L y + L^2 (tau mod M), M = L_tau / 32), and a site with u of its 6
+ *   bonds unsatisfied flips iff u + d >= 3, d its two-bit daemon, whose
+ *   bits come from Philox4x32-10 + one xoroshiro128++ state step + the
+ *   inverse-cumulative bytes of Sec. 2.1.1 (the words b4, b8, b12 of
+ *   word-site ws of system (a, r, slot s) in sweep t: Philox counter
+ *   {ws, t, s | r << 16, 5 << 28 | which << 24 | a}, which = 0, 1, 2).  This
+ *   is a different Markov chain from the threshold rule of LANES and
+ *   SAMPLES (the same distribution, another random stream).  Needs word_bits
+ *   0 or 32, k_tau = k <= 16 at every slot (the rule prices a flip with one
+ *   coupling), L_tau a multiple of 64 and n_samples < 2^24; never chosen by
+ *   AUTO.  PT swaps the slot labels, as in LANES.                          */
 #define QISG_LAYOUT_AUTO    0
 #define QISG_LAYOUT_LANES   1
 #define QISG_LAYOUT_SAMPLES 2
+#define QISG_LAYOUT_SITES   3
 
 typedef struct qisg_handle qisg_handle;
 
@@ -94,6 +109,16 @@ void qisg_opts_default(qisg_opts *opts);
  * of Sec. 1's relation between k and Gamma.  out: caller array of n slots.
  * EINVAL: n < 1, gamma <= 0, lo <= 0 or a non-finite k_tau. */
 int qisg_ladder_linear(double lo, double hi, int n, double gamma, qisg_slot *out);
+
+/* The tables of the SITES daemon rule for coupling k (Sec. 2.1.1, Appendix
+ * D), computed on the host: cum[0..254] = cumulative(n), the truncation of
+ * 2^64 sum_{m <= n} p^pop(m) (1-p)^(8-pop(m)) with p = e^{-4k} (fixed point
+ * with 126 fractional bits; the paper uses 128-bit floats); lut (NULL =
+ * skip): 2^lut_bits entries, entry h = n_min | (n_max - n_min) << 8, where
+ * [n_min, n_max] holds n* of every 64-bit word whose top lut_bits bits are
+ * h.  The caller owns both arrays (255 and 2^lut_bits entries).  EINVAL:
+ * k outside [0, 16], cum NULL, lut_bits outside 1..16. */
+int qisg_daemon_tables(double k, int lut_bits, uint64_t *cum, uint16_t *lut);
 
 /* Create an instance: n_samples disorder samples (J = +-1, p = 1/2), each
  * with n_replicas independent replicas of an n_slots PT ladder, on an

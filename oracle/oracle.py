@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import decimal
+import math
 import os
 import subprocess
 import threading
@@ -82,6 +83,8 @@ def _load():
             lib.orc_daemon_level.restype = i32
             lib.orc_daemon_flip.argtypes = [i32, i32]
             lib.orc_daemon_flip.restype = i32
+            lib.orc_daemon_sweep_system.argtypes = [i32, i32, u64, i64, i32, i32, u64, i32, P, P, P]
+            lib.orc_daemon_sweep_system.restype = None
             _lib = lib
     return _lib
 
@@ -136,21 +139,22 @@ def daemon_cumulative(k: float) -> np.ndarray:
     """cumulative(n), n = 0..254, of Sec. 2.1.1 for coupling k: the 64-bit
     truncation of 2^64 sum_{m <= n} P[m], P[m] = p^pop(m) (1-p)^(8-pop(m)),
     p = e^{-4k}.  The paper evaluates the sum in 128-bit floating point; here
-    it is evaluated with 80 significant decimal digits (the exact value's
+    it is evaluated in decimal arithmetic with 80 significant digits beyond
+    those that p^8 = e^{-32k} needs next to 1 (the exact value's
     truncation, which 128-bit arithmetic also gives unless the sum lies
     within about 2^-49 of an integer)."""
     with decimal.localcontext() as ctx:
-        ctx.prec = 80
+        ctx.prec = 80 + int(32.0 * float(k) / math.log(10.0)) + 1
         p = (decimal.Decimal(-4) * decimal.Decimal(float(k))).exp()
         q = 1 - p
         scale = decimal.Decimal(2) ** 64
         acc = decimal.Decimal(0)
-        out = np.zeros(255, dtype=np.uint64)
+        out = []
         for n in range(255):
             c = bin(n).count("1")
             acc += (p ** c) * (q ** (8 - c))
-            out[n] = int((acc * scale).to_integral_value(rounding=decimal.ROUND_FLOOR))
-    return out
+            out.append(int((acc * scale).to_integral_value(rounding=decimal.ROUND_FLOOR)))
+    return np.array(out, dtype=np.uint64)
 
 
 def daemon_tables(k) -> np.ndarray:
@@ -180,6 +184,16 @@ def daemon_level(b4: int, b8: int, b12: int) -> int:
 
 def daemon_flip(u: int, d: int) -> bool:
     return bool(_load().orc_daemon_flip(u, d))
+
+
+def daemon_sweep_system(L: int, Ltau: int, seed: int, a: int, r: int, s: int, t: int, J_a: np.ndarray,
+                        S: np.ndarray, cum: np.ndarray, tau_ap: bool = False) -> None:
+    """One daemon-rule sweep t of one system (sample a, replica r, slot s)
+    in place: S [N] int8, J_a [L*L][2] of sample a, cum [n_slots][255]."""
+    assert S.dtype == np.int8 and S.flags["C_CONTIGUOUS"]
+    _load().orc_daemon_sweep_system(L, Ltau, seed, a, r, s, t, int(bool(tau_ap)),
+                                    _ptr(np.ascontiguousarray(J_a, dtype=np.int8)), _ptr(S),
+                                    _ptr(np.ascontiguousarray(cum, dtype=np.uint64)))
 
 
 def init_couplings(L: int, a_lo: int, n_a: int, seed: int) -> np.ndarray:

@@ -315,6 +315,52 @@ static void energies_of(const orc_model *m, const int8_t *J, const int8_t *S,
     *B = b;
 }
 
+/* Metropolis update of site (x, y, tau) of the system (a, r, walker at slot
+ * s) whose spins are Sw, in sweep t: u_s, u_t = unsatisfied spatial and
+ * tau bonds; with the threshold rule the flip is taken iff T == 0xFFFFFFFF
+ * or R < T[s][u_s][u_t]; with the daemon rule iff u_s + u_t + d >= 3. */
+static void site_update(const orc_model *m, int64_t a, int r, int s, const int8_t *J, int8_t *Sw,
+                        int x, int y, int tau, uint64_t t)
+{
+    int L = m->L, Lt = m->Ltau;
+    int xp = (x + 1) % L, xm = (x + L - 1) % L;
+    int yp = (y + 1) % L, ym = (y + L - 1) % L;
+    int tp = (tau + 1) % Lt, tm = (tau + Lt - 1) % Lt;
+    /* sign of the tau bonds: -1 on the antiperiodic wrap bond */
+    int gp = (m->tau_ap && tau == Lt - 1) ? -1 : 1;
+    int gm = (m->tau_ap && tau == 0) ? -1 : 1;
+    int i2 = x + L * y;
+    int64_t site = x + (int64_t)L * y + (int64_t)L * L * tau;
+    int si = Sw[site];
+    int us = 0, ut = 0;
+    uint32_t thr, R;
+    us += (J[i2 * 2 + 0] * si * Sw[xp + L * y + (int64_t)L * L * tau] == -1);
+    us += (J[(xm + L * y) * 2 + 0] * si * Sw[xm + L * y + (int64_t)L * L * tau] == -1);
+    us += (J[i2 * 2 + 1] * si * Sw[x + L * yp + (int64_t)L * L * tau] == -1);
+    us += (J[(x + L * ym) * 2 + 1] * si * Sw[x + L * ym + (int64_t)L * L * tau] == -1);
+    ut += (gp * si * Sw[x + L * y + (int64_t)L * L * tp] == -1);
+    ut += (gm * si * Sw[x + L * y + (int64_t)L * L * tm] == -1);
+    if (m->cum) {
+        /* daemon rule: site (x, y, tau) is bit j = tau / M of word-site
+         * x + L y + L^2 (tau mod M), M = L_tau / 32 */
+        int M = Lt / 32, j = tau / M, d;
+        uint32_t ws = (uint32_t)(x + L * y + (int64_t)L * L * (tau % M));
+        const uint64_t *cs = m->cum + (int64_t)s * 255;
+        uint32_t b4 = orc_daemon_bword(m->seed, a, r, s, ws, t, 0, cs);
+        uint32_t b8 = orc_daemon_bword(m->seed, a, r, s, ws, t, 1, cs);
+        uint32_t b12 = orc_daemon_bword(m->seed, a, r, s, ws, t, 2, cs);
+        d = orc_daemon_level((b4 >> j) & 1, (b8 >> j) & 1, (b12 >> j) & 1);
+        if (orc_daemon_flip(us + ut, d)) Sw[site] = (int8_t)(-si);
+        return;
+    }
+    thr = m->T[(s * 5 + us) * 3 + ut];
+    R = philox_word((uint32_t)site, (uint32_t)t,
+                    (uint32_t)s | ((uint32_t)(r >> 2) << 16),
+                    ((uint32_t)ORC_DOM_SWEEP << 28) | (uint32_t)(a >> 6),
+                    m->seed, r & 3);
+    if (thr == 0xFFFFFFFFu || R < thr) Sw[site] = (int8_t)(-si);
+}
+
 /* One half sweep of one sample a: every site of the given colour, every
  * replica r and slot s, for the walker w currently at slot s. */
 static void half_sweep(const orc_model *m, int64_t a, const int8_t *J, int8_t *S_a,
@@ -326,51 +372,32 @@ static void half_sweep(const orc_model *m, int64_t a, const int8_t *J, int8_t *S
     for (tau = 0; tau < Lt; ++tau)
         for (y = 0; y < L; ++y)
             for (x = 0; x < L; ++x) {
-                int xp, xm, yp, ym, tp, tm, i2, gp, gm;
-                int64_t site;
                 if (((x + y + tau) & 1) != colour) continue;
-                site = x + (int64_t)L * y + (int64_t)L * L * tau;
-                xp = (x + 1) % L; xm = (x + L - 1) % L;
-                yp = (y + 1) % L; ym = (y + L - 1) % L;
-                tp = (tau + 1) % Lt; tm = (tau + Lt - 1) % Lt;
-                /* sign of the tau bonds: -1 on the antiperiodic wrap bond */
-                gp = (m->tau_ap && tau == Lt - 1) ? -1 : 1;
-                gm = (m->tau_ap && tau == 0) ? -1 : 1;
-                i2 = x + L * y;
                 for (r = 0; r < n_rep; ++r)
                     for (s = 0; s < n_slots; ++s) {
                         int w = walker_at_a[r * n_slots + s];
-                        int8_t *Sw = S_a + ((int64_t)r * n_slots + w) * N;
-                        int si = Sw[site];
-                        int us = 0, ut = 0;
-                        uint32_t thr, R;
-                        us += (J[i2 * 2 + 0] * si * Sw[xp + L * y + (int64_t)L * L * tau] == -1);
-                        us += (J[(xm + L * y) * 2 + 0] * si * Sw[xm + L * y + (int64_t)L * L * tau] == -1);
-                        us += (J[i2 * 2 + 1] * si * Sw[x + L * yp + (int64_t)L * L * tau] == -1);
-                        us += (J[(x + L * ym) * 2 + 1] * si * Sw[x + L * ym + (int64_t)L * L * tau] == -1);
-                        ut += (gp * si * Sw[x + L * y + (int64_t)L * L * tp] == -1);
-                        ut += (gm * si * Sw[x + L * y + (int64_t)L * L * tm] == -1);
-                        if (m->cum) {
-                            /* daemon rule: site (x, y, tau) is bit j = tau / M of
-                             * word-site x + L y + L^2 (tau mod M), M = L_tau / 32 */
-                            int M = Lt / 32, j = tau / M, d;
-                            uint32_t ws = (uint32_t)(x + L * y + (int64_t)L * L * (tau % M));
-                            const uint64_t *cs = m->cum + (int64_t)s * 255;
-                            uint32_t b4 = orc_daemon_bword(m->seed, a, r, s, ws, t, 0, cs);
-                            uint32_t b8 = orc_daemon_bword(m->seed, a, r, s, ws, t, 1, cs);
-                            uint32_t b12 = orc_daemon_bword(m->seed, a, r, s, ws, t, 2, cs);
-                            d = orc_daemon_level((b4 >> j) & 1, (b8 >> j) & 1, (b12 >> j) & 1);
-                            if (orc_daemon_flip(us + ut, d)) Sw[site] = (int8_t)(-si);
-                            continue;
-                        }
-                        thr = m->T[(s * 5 + us) * 3 + ut];
-                        R = philox_word((uint32_t)site, (uint32_t)t,
-                                        (uint32_t)s | ((uint32_t)(r >> 2) << 16),
-                                        ((uint32_t)ORC_DOM_SWEEP << 28) | (uint32_t)(a >> 6),
-                                        m->seed, r & 3);
-                        if (thr == 0xFFFFFFFFu || R < thr) Sw[site] = (int8_t)(-si);
+                        site_update(m, a, r, s, J, S_a + ((int64_t)r * n_slots + w) * N, x, y, tau, t);
                     }
             }
+}
+
+/* One sweep (red, then blue) of ONE system of the daemon rule: sample a,
+ * replica r, slot s, spins S [N] in place, couplings J [L*L][2] of sample
+ * a, cumulative tables cum [n_slots][255].  The daemon rule's update of a
+ * system depends on no other system, so this is the same sweep the full
+ * chain applies to it (for the tests at sizes where a full run is too slow). */
+void orc_daemon_sweep_system(int L, int Ltau, uint64_t seed, int64_t a, int r, int s, uint64_t t,
+                             int tau_ap, const int8_t *J, int8_t *S, const uint64_t *cum)
+{
+    orc_model m;
+    int x, y, tau, colour;
+    memset(&m, 0, sizeof(m));
+    m.L = L; m.Ltau = Ltau; m.seed = seed; m.tau_ap = tau_ap; m.cum = cum;
+    for (colour = 0; colour < 2; ++colour)
+        for (tau = 0; tau < Ltau; ++tau)
+            for (y = 0; y < L; ++y)
+                for (x = 0; x < L; ++x)
+                    if (((x + y + tau) & 1) == colour) site_update(&m, a, r, s, J, S, x, y, tau, t);
 }
 
 /* One PT pass of chain (a, r) after sweep t: pairs (s, s+1) in increasing s.

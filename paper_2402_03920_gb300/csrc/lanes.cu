@@ -302,11 +302,28 @@ int lane_of(const qisg_handle *h, int r, int w, int *g) {
 
 }  // namespace
 
-int lanes_init(qisg_handle *h) {
+int lanes_init_couplings(qisg_handle *h) {
   const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
   const int64_t nJ = h->n_samples * h->L * h->L;
   lanes_init_J_kernel<<<(unsigned)((nJ + 255) / 256), 256, 0, h->stream>>>(
       reinterpret_cast<uint8_t *>(h->J), h->n_samples, h->L, key);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "init couplings");
+}
+
+int lanes_finalize(qisg_handle *h, int force_to_q) {
+  const int64_t n = h->n_samples * h->n_slots;
+  lanes_finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+      h->d_walker, h->d_U, h->d_q, h->d_sumA, h->d_sumB, h->d_sumq, h->d_sumq2, h->n_samples,
+      h->n_rep, h->n_slots, h->N, force_to_q);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "finalize measurement");
+}
+
+int lanes_init(qisg_handle *h) {
+  const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  int rc = lanes_init_couplings(h);
+  if (rc) return rc;
   const int64_t nS = h->n_samples * h->n_groups * h->N;
   if ((nS + 255) / 256 > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large");
   if (h->W == 64)
@@ -317,7 +334,7 @@ int lanes_init(qisg_handle *h) {
     lanes_init_spins_kernel<unsigned int><<<(unsigned)((nS + 255) / 256), 256, 0, h->stream>>>(
         reinterpret_cast<unsigned int *>(h->spins), h->n_samples, h->N, h->n_rep, h->n_slots,
         h->rpw, h->n_groups, key);
-  h->launches += 2;
+  h->launches += 1;
   return cuda_check(cudaGetLastError(), "lanes init");
 }
 

@@ -174,6 +174,10 @@ int recompute_energies(qisg_handle *h) {
     if ((rc = lanes_half_sweep(h, 0, 1))) return rc;
     return lanes_half_sweep(h, 1, 1);
   }
+  if (h->layout == QISG_LAYOUT_SITES) {
+    if ((rc = sites_half_sweep(h, 0, 1))) return rc;
+    return sites_half_sweep(h, 1, 1);
+  }
   if ((rc = samples_materialize(h))) return rc;
   if ((rc = samples_half_sweep(h, 0, 1))) return rc;
   return samples_half_sweep(h, 1, 1);
@@ -233,7 +237,16 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (o.word_bits != 0 && o.word_bits != 32 && o.word_bits != 64)
     return fail(QISG_EINVAL, "word_bits must be 0, 32 or 64");
   if (o.pt_every < 0 || o.measure_every < 0) return fail(QISG_EINVAL, "negative cadence");
-  if (o.layout < 0 || o.layout > 2) return fail(QISG_EINVAL, "unknown layout");
+  if (o.layout < 0 || o.layout > 3) return fail(QISG_EINVAL, "unknown layout");
+  if (o.layout == QISG_LAYOUT_SITES) {
+    if (o.word_bits != 0 && o.word_bits != 32)
+      return fail(QISG_EINVAL, "the SITES packing holds 32 tau-sites per 32-bit word");
+    if (L_tau % 64 != 0) return fail(QISG_EINVAL, "the SITES packing needs L_tau to be a multiple of 64");
+    if (n_samples >= ((int64_t)1 << 24)) return fail(QISG_EINVAL, "the SITES packing takes fewer than 2^24 samples");
+    for (int s = 0; s < n_slots; ++s)
+      if (ladder[s].k != ladder[s].k_tau || ladder[s].k > 16.0)
+        return fail(QISG_EINVAL, "the daemon rule needs k_tau = k <= 16 at every slot");
+  }
   if (o.tau_antiperiodic != 0 && o.tau_antiperiodic != 1) return fail(QISG_EINVAL, "tau_antiperiodic must be 0 or 1");
 
   qisg_handle *h = new (std::nothrow) qisg_handle();
@@ -260,7 +273,10 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   int layout = o.layout;
   if (layout == QISG_LAYOUT_AUTO) layout = n_samples >= 32 ? QISG_LAYOUT_SAMPLES : QISG_LAYOUT_LANES;
   h->layout = layout;
-  if (layout == QISG_LAYOUT_LANES) {
+  if (layout == QISG_LAYOUT_SITES) {
+    h->W = 32;
+    h->n_a_pad = n_samples;
+  } else if (layout == QISG_LAYOUT_LANES) {
     int W = o.word_bits;
     if (W == 0) W = (n_slots * n_replicas <= 32) ? 32 : 64;
     if (n_slots > W) {
@@ -295,6 +311,9 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
     if (layout == QISG_LAYOUT_LANES) {
       h->spins_bytes = (size_t)n_samples * h->n_groups * h->N * (h->W / 8);
       h->J_bytes = (size_t)n_samples * L * L;
+    } else if (layout == QISG_LAYOUT_SITES) {
+      h->spins_bytes = (size_t)n_samples * n_replicas * n_slots * (h->N / 8);
+      h->J_bytes = (size_t)n_samples * L * L;
     } else {
       h->spins_bytes = (size_t)h->n_b * n_slots * h->n_q * h->N * 4 * (h->W / 8);
       h->J_bytes = (size_t)h->n_b * L * L * 2 * (h->W / 8);
@@ -321,6 +340,8 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc) rc = dalloc(h, &h->d_err, 4);
   if (!rc && layout == QISG_LAYOUT_SAMPLES)
     rc = dalloc(h, &h->d_acc, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8));
+  if (!rc && layout == QISG_LAYOUT_SITES) rc = dalloc(h, &h->d_dcum, (size_t)n_slots * 256 * 8);
+  if (!rc && layout == QISG_LAYOUT_SITES) rc = dalloc(h, &h->d_dlut, ((size_t)n_slots << kDaemonLutBits) * 2);
   if (rc) {
     qisg_destroy(h);
     return rc;
@@ -357,7 +378,7 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc && h->d_acc)
     rc = cuda_check(cudaMemsetAsync(h->d_acc, 0, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8), h->stream),
                     "memset");
-  if (!rc) rc = (layout == QISG_LAYOUT_LANES) ? lanes_init(h) : samples_init(h);
+  if (!rc) rc = (layout == QISG_LAYOUT_LANES) ? lanes_init(h) : (layout == QISG_LAYOUT_SITES) ? sites_init(h) : samples_init(h);
   if (!rc) rc = recompute_energies(h);
   if (!rc) rc = sync_handle(h);
   if (rc) {
@@ -378,12 +399,13 @@ namespace {
 // ev: optional events recorded before the red pass, between the passes and
 // after the blue pass (autotuning).
 int one_sweep(qisg_handle *h, cudaEvent_t *ev = nullptr) {
-  const bool lanes = h->layout == QISG_LAYOUT_LANES;
+  const bool lanes = h->layout != QISG_LAYOUT_SAMPLES;   // walker-major: LANES and SITES
+  const bool sites = h->layout == QISG_LAYOUT_SITES;
   const uint64_t t = h->t;
   int rc = ev ? cuda_check(cudaEventRecord(ev[0], h->stream), "record") : QISG_OK;
-  if (!rc) rc = lanes ? lanes_half_sweep(h, 0, 0) : samples_half_sweep(h, 0, 0);
+  if (!rc) rc = sites ? sites_half_sweep(h, 0, 0) : lanes ? lanes_half_sweep(h, 0, 0) : samples_half_sweep(h, 0, 0);
   if (!rc && ev) rc = cuda_check(cudaEventRecord(ev[1], h->stream), "record");
-  if (!rc) rc = lanes ? lanes_half_sweep(h, 1, 0) : samples_half_sweep(h, 1, 0);
+  if (!rc) rc = sites ? sites_half_sweep(h, 1, 0) : lanes ? lanes_half_sweep(h, 1, 0) : samples_half_sweep(h, 1, 0);
   if (!rc && ev) rc = cuda_check(cudaEventRecord(ev[2], h->stream), "record");
   bool advanced = false;
   if (!rc && h->pt_every > 0 && (t + 1) % (uint64_t)h->pt_every == 0) {
@@ -395,7 +417,7 @@ int one_sweep(qisg_handle *h, cudaEvent_t *ev = nullptr) {
     }
   }
   if (!rc && h->measure_every > 0 && (t + 1) % (uint64_t)h->measure_every == 0) {
-    rc = lanes ? lanes_measure(h, 0) : samples_measure(h, 0);
+    rc = sites ? sites_measure(h, 0) : lanes ? lanes_measure(h, 0) : samples_measure(h, 0);
     h->n_meas++;
   }
   if (!rc) {
@@ -669,12 +691,12 @@ int qisg_set_tiles(qisg_handle *h, const int tile[2], const int variant[2]) {
 int qisg_pt_swap(qisg_handle *h) {
   if (!h) return fail(QISG_EINVAL, "NULL handle");
   if (h->t == 0) return fail(QISG_ESTATE, "no sweep has run yet");
-  return h->layout == QISG_LAYOUT_LANES ? lanes_pt(h, 1) : samples_pt(h, 1, 0);
+  return h->layout != QISG_LAYOUT_SAMPLES ? lanes_pt(h, 1) : samples_pt(h, 1, 0);
 }
 
 int qisg_energies(qisg_handle *h, int64_t *A, int64_t *B) {
   if (!h || !A || !B) return fail(QISG_EINVAL, "NULL argument");
-  int rc = h->layout == QISG_LAYOUT_LANES ? lanes_energies_by_slot(h) : samples_energies_by_slot(h);
+  int rc = h->layout != QISG_LAYOUT_SAMPLES ? lanes_energies_by_slot(h) : samples_energies_by_slot(h);
   if (rc) return rc;
   const size_t n = (size_t)h->n_samples * h->n_rep * h->n_slots;
   const size_t stride = (size_t)h->n_a_pad * h->n_rep * h->n_slots;
@@ -689,7 +711,9 @@ int qisg_overlaps(qisg_handle *h, int64_t *q) {
   if (!h || !q) return fail(QISG_EINVAL, "NULL argument");
   const int n_pairs = h->n_pairs();
   if (n_pairs == 0) return QISG_OK;
-  int rc = h->layout == QISG_LAYOUT_LANES ? lanes_measure(h, 1) : samples_measure(h, 1);
+  int rc = h->layout == QISG_LAYOUT_LANES ? lanes_measure(h, 1)
+           : h->layout == QISG_LAYOUT_SITES ? sites_measure(h, 1)
+                                             : samples_measure(h, 1);
   if (rc) return rc;
   const size_t n = (size_t)h->n_samples * h->n_slots * n_pairs;
   rc = cuda_check(cudaMemcpyAsync(q, h->d_q, n * 8, cudaMemcpyDeviceToHost, h->stream), "copy q");
@@ -713,8 +737,9 @@ int qisg_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
   if (a_lo < 0 || n_a < 0 || a_lo + n_a > h->n_samples) return fail(QISG_EINVAL, "sample range");
   int rc = sync_handle(h);
   if (rc) return rc;
-  return h->layout == QISG_LAYOUT_LANES ? lanes_get_spins(h, a_lo, n_a, S)
-                                        : samples_get_spins(h, a_lo, n_a, S);
+  return h->layout == QISG_LAYOUT_LANES   ? lanes_get_spins(h, a_lo, n_a, S)
+         : h->layout == QISG_LAYOUT_SITES ? sites_get_spins(h, a_lo, n_a, S)
+                                          : samples_get_spins(h, a_lo, n_a, S);
 }
 
 int qisg_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J) {
@@ -722,8 +747,8 @@ int qisg_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J) {
   if (a_lo < 0 || n_a < 0 || a_lo + n_a > h->n_samples) return fail(QISG_EINVAL, "sample range");
   int rc = sync_handle(h);
   if (rc) return rc;
-  return h->layout == QISG_LAYOUT_LANES ? lanes_get_couplings(h, a_lo, n_a, J)
-                                        : samples_get_couplings(h, a_lo, n_a, J);
+  return h->layout != QISG_LAYOUT_SAMPLES ? lanes_get_couplings(h, a_lo, n_a, J)
+                                          : samples_get_couplings(h, a_lo, n_a, J);
 }
 
 int qisg_set_couplings(qisg_handle *h, const int8_t *J) {
@@ -732,7 +757,7 @@ int qisg_set_couplings(qisg_handle *h, const int8_t *J) {
   for (int64_t i = 0; i < n; ++i)
     if (J[i] != 1 && J[i] != -1) return fail(QISG_EINVAL, "couplings must be +-1");
   int rc = sync_handle(h);
-  if (!rc) rc = h->layout == QISG_LAYOUT_LANES ? lanes_set_couplings(h, J) : samples_set_couplings(h, J);
+  if (!rc) rc = h->layout != QISG_LAYOUT_SAMPLES ? lanes_set_couplings(h, J) : samples_set_couplings(h, J);
   if (!rc) rc = recompute_energies(h);
   if (!rc) rc = sync_handle(h);
   return rc;
@@ -755,7 +780,9 @@ int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, ui
     if (S[i] != 1 && S[i] != -1) return fail(QISG_ECORRUPT, "spins must be +-1");
   int rc = sync_handle(h);
   if (rc) return rc;
-  rc = h->layout == QISG_LAYOUT_LANES ? lanes_set_spins(h, S) : samples_set_spins(h, S, walker_at);
+  rc = h->layout == QISG_LAYOUT_LANES   ? lanes_set_spins(h, S)
+       : h->layout == QISG_LAYOUT_SITES ? sites_set_spins(h, S)
+                                        : samples_set_spins(h, S, walker_at);
   if (rc) return rc;
   // the permutation (padding lanes keep the identity)
   std::vector<int32_t> wa((size_t)h->n_a_pad * h->n_rep * h->n_slots);
@@ -884,7 +911,7 @@ void qisg_destroy(qisg_handle *h) {
   if (!h) return;
   if (h->stream || true) cudaStreamSynchronize(h->stream);
   void *ptrs[] = {h->spins, h->spins_alt, h->J, h->d_T, h->d_bases, h->d_sq, h->d_ptc, h->d_walker, h->d_U, h->d_sumA, h->d_sumB,
-                  h->d_sumq, h->d_sumq2, h->d_q, h->d_out, h->d_t, h->d_acc, h->d_err};
+                  h->d_sumq, h->d_sumq2, h->d_q, h->d_out, h->d_t, h->d_acc, h->d_err, h->d_dcum, h->d_dlut};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   drop_cycle(h);

@@ -19,7 +19,10 @@
 namespace qisg {
 
 // Philox counter domains: one per kind of draw.
-enum : uint32_t { DOM_J = 1, DOM_INIT = 2, DOM_SWEEP = 3, DOM_PT = 4 };
+enum : uint32_t { DOM_J = 1, DOM_INIT = 2, DOM_SWEEP = 3, DOM_PT = 4, DOM_DAEMON = 5 };
+
+// Index bits of the SITES daemon tables (the words' top bits -> candidate bins).
+constexpr int kDaemonLutBits = 12;
 
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
@@ -460,6 +463,8 @@ struct qisg_handle {
   long long *d_out = nullptr;       // output staging [2][a][r][s]
   unsigned long long *d_t = nullptr;  // sweep counter; d_t[1]: its copy for the PT pass (fused mode)
   void *d_acc = nullptr;            // SAMPLES: PT lane masks of the last pass, Word [b][r][s]
+  unsigned long long *d_dcum = nullptr;   // SITES: cumulative tables [n_slots][256]
+  uint16_t *d_dlut = nullptr;             // SITES: prefix index [n_slots][2^kDaemonLutBits]
   int *d_err = nullptr;
   size_t device_bytes = 0;
 
@@ -504,6 +509,16 @@ int lanes_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S);
 int lanes_set_spins(qisg_handle *h, const int8_t *S);
 int lanes_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J);
 int lanes_set_couplings(qisg_handle *h, const int8_t *J);
+int lanes_init_couplings(qisg_handle *h);
+int lanes_finalize(qisg_handle *h, int force_to_q);
+
+// SITES packing (sites.cu): the paper's multi-site coding with daemon bits.
+int sites_init(qisg_handle *h);
+int sites_half_sweep(qisg_handle *h, int colour, int count_only);
+int sites_measure(qisg_handle *h, int force_to_q);
+int sites_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S);
+int sites_set_spins(qisg_handle *h, const int8_t *S);
+void daemon_cumulative(double k, uint64_t *cum);
 
 // SAMPLES kernels (samples.cu)
 int samples_init(qisg_handle *h);

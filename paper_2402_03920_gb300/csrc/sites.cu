@@ -1,0 +1,493 @@
+// SITES packing: the paper's own multi-site coding with its daemon-bit
+// Metropolis rule (Sec. 2.1 and 2.1.1, Appendices C and D), for equal
+// couplings k_tau = k.  A 32-bit word holds 32 imaginary-time sites of ONE
+// system: with M = L_tau / 32, site (x, y, tau) is bit tau / M of word-site
+// x + L y + L^2 (tau mod M).  M is even, so all bits of a word have the
+// colour (x + y + tau) mod 2 of their word-site, and the six neighbours of a
+// word are whole words: four spatial ones at the same tau, and the words at
+// tau +- 1, rotated by one bit where the word stream wraps (tau mod M = M-1
+// upwards, 0 downwards), with the antiperiodic sign on the bit that crosses
+// tau = L_tau - 1 -> 0.
+//
+// The update of a word: u = number of unsatisfied bonds of each bit (6 bond
+// masks, a bit-sliced 6-input counter), d = the bit's daemon level, and the
+// bit flips iff u + d >= 3 (a flip costs 4k(3 - u); P(d >= n) = e^{-4kn}).
+// d >= n is "the first n of the daemon words b4, b8, b12 have the bit set",
+// so the flip mask is
+//   f = [u >= 3] | b4 & ([u = 2] | b8 & ([u = 1] | b12 & [u = 0])).
+// Each daemon word comes from one Philox4x32-10 call (the upper halves of
+// four 64-bit "50/50" words) and one xoroshiro128++ state step of the same
+// 128 bits (the lower halves); byte i of the word is n* of 64-bit word i,
+// the bin of the word in the cumulative table of the walker's slot.  n* is
+// found from an index of the top kLutBits bits (the bins that the prefix's
+// range of words can fall in, [n_min, n_min + span]) and at most span
+// comparisons against the cumulative table, both staged in shared memory.
+//
+// Device arrays (systems walker-major; PT exchanges slot labels only):
+//   spins  u32 [a][r][w][L^2 M]       bit = 1 <=> spin -1
+//   J      uint8 [a][x + L*y]          bit0: J(+x) = -1, bit1: J(+y) = -1
+//   U      u64 [a][r][w][2]            unsatisfied spatial / tau bonds of walker w
+//   cum    u64 [n_slots][256]          cumulative(0..254) of Sec. 2.1.1; [255] = 2^64-1
+//   lut    u16 [n_slots][2^kLutBits]   n_min | span << 8 of each prefix
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "qisg_internal.cuh"
+
+namespace qisg {
+namespace {
+
+constexpr int kBlock = 256;
+
+struct SitesArgs {
+  uint32_t *spins;
+  const uint8_t *J;
+  const int32_t *walker;
+  const unsigned long long *cum;
+  const uint16_t *lut;
+  unsigned long long *U;
+  const unsigned long long *d_t;
+  uint2 key;
+  FastDiv half_plane_div, half_L_div;
+  int L, M, plane, half_plane, n_words, half_words;
+  int n_slots, n_rep;
+  int blocks_per_sys, words_per_thread;
+  int tau_ap;
+};
+
+// xoroshiro128++ state step (Blackman and Vigna, 2019) on the 128 bits of a
+// Philox output, state (x | y << 32, z | w << 32); returns the new state's
+// four 32-bit quarters in the same order.
+__device__ __forceinline__ uint4 xoroshiro_step(uint4 x) {
+  const unsigned long long s0 = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
+  const unsigned long long s1 = (unsigned long long)x.z | ((unsigned long long)x.w << 32);
+  const unsigned long long tt = s1 ^ s0;
+  const unsigned long long n0 = ((s0 << 49) | (s0 >> 15)) ^ tt ^ (tt << 21);
+  const unsigned long long n1 = (tt << 28) | (tt >> 36);
+  return make_uint4((uint32_t)n0, (uint32_t)(n0 >> 32), (uint32_t)n1, (uint32_t)(n1 >> 32));
+}
+
+// n* of the 64-bit word hi:lo (Sec. 2.1.1) from the prefix index and the
+// cumulative table of one slot (shared memory).
+__device__ __forceinline__ uint32_t nstar(uint32_t hi, uint32_t lo, const uint16_t *lut,
+                                          const unsigned long long *cum) {
+  const uint32_t e = lut[hi >> (32 - kDaemonLutBits)];
+  uint32_t n = e & 0xFFu;
+  const uint32_t end = n + (e >> 8);
+  const unsigned long long R = ((unsigned long long)hi << 32) | lo;
+  for (uint32_t q = n; q < end; ++q) n += (R >= cum[q]) ? 1u : 0u;
+  return n;
+}
+
+// Daemon word `which` (0: b4, 1: b8, 2: b12) of word-site ws of system
+// (a, r, slot s) in sweep t.
+__device__ __forceinline__ uint32_t daemon_word(uint32_t ws, uint32_t t, uint32_t c2, uint32_t c3, uint2 key,
+                                                const uint16_t *lut, const unsigned long long *cum) {
+  const uint4 x = philox(make_uint4(ws, t, c2, c3), key);
+  const uint4 lo = xoroshiro_step(x);
+  return nstar(x.x, lo.x, lut, cum) | (nstar(x.y, lo.y, lut, cum) << 8) | (nstar(x.z, lo.z, lut, cum) << 16) |
+         (nstar(x.w, lo.w, lut, cum) << 24);
+}
+
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
+
+// One half sweep (colour 0 = red, 1 = blue).  Block x serves system
+// x / blocks_per_sys (sys = (a n_rep + r) n_slots + w) and the colour words
+// [chunk * 256 * wpt, (chunk + 1) * 256 * wpt) of it, thread i taking words
+// chunk * 256 * wpt + i + 256 j.  The blue pass counts, per system, the
+// unsatisfied bonds of its words after the update: every bond has exactly
+// one blue end, so this is each bond once.  Chunk 0 of the red pass clears
+// the system's counters.  count_only: no update (energies of the stored
+// state).
+template <bool BLUE>
+__global__ void __launch_bounds__(kBlock) sites_half_sweep_kernel(SitesArgs p, int count_only) {
+  __shared__ unsigned long long cum_s[256];
+  __shared__ __align__(16) uint16_t lut_s[1 << kDaemonLutBits];
+  __shared__ unsigned long long red_s[2][kBlock / 32];
+  const int64_t sys = blockIdx.x / p.blocks_per_sys;
+  const int chunk = (int)(blockIdx.x - sys * p.blocks_per_sys);
+  const int w = (int)(sys % p.n_slots);
+  const int64_t ar = sys / p.n_slots;   // a * n_rep + r
+  const int r = (int)(ar % p.n_rep);
+  const int64_t a = ar / p.n_rep;
+  const int colour = BLUE ? 1 : 0;
+  if (!BLUE && chunk == 0 && threadIdx.x < 2) p.U[sys * 2 + threadIdx.x] = 0;
+  if (!BLUE && count_only) return;
+  // slot of walker w: lane l of every warp reads walker_at[a][r][l]
+  const int lane = threadIdx.x & 31;
+  const int32_t wl = lane < p.n_slots ? __ldg(p.walker + ar * p.n_slots + lane) : -1;
+  const int s = max(__ffs(__ballot_sync(0xFFFFFFFFu, wl == w)) - 1, 0);   // rows are permutations
+  // stage the slot's tables
+  {
+    const unsigned long long *cg = p.cum + (size_t)s * 256;
+    for (int i = threadIdx.x; i < 256; i += kBlock) cum_s[i] = __ldg(cg + i);
+    const uint4 *lg = reinterpret_cast<const uint4 *>(p.lut + ((size_t)s << kDaemonLutBits));
+    uint4 *ls = reinterpret_cast<uint4 *>(lut_s);
+    for (int i = threadIdx.x; i < (1 << kDaemonLutBits) / 8; i += kBlock) ls[i] = __ldg(lg + i);
+  }
+  __syncthreads();
+  uint32_t *S = p.spins + sys * p.n_words;
+  const uint8_t *J = p.J + a * p.plane;
+  const uint32_t t = (uint32_t)*p.d_t;
+  const uint32_t c2 = (uint32_t)s | ((uint32_t)r << 16);
+  const uint32_t c3 = (DOM_DAEMON << 28) | (uint32_t)a;
+  const uint32_t ap_up = p.tau_ap ? 0x80000000u : 0u, ap_dn = p.tau_ap ? 1u : 0u;
+  unsigned long long us_cnt = 0, ut_cnt = 0;
+  const int base = chunk * kBlock * p.words_per_thread + threadIdx.x;
+  for (int j = 0; j < p.words_per_thread; ++j) {
+    const int idx = base + j * kBlock;
+    if (idx >= p.half_words) break;
+    // idx -> (tau', y, x) of the colour's words
+    const uint32_t tq = p.half_plane_div.div((uint32_t)idx);
+    const uint32_t rem = (uint32_t)idx - tq * (uint32_t)p.half_plane;
+    const uint32_t y = p.half_L_div.div(rem);
+    const uint32_t xh = rem - y * (uint32_t)(p.L >> 1);
+    const uint32_t x = 2 * xh + ((y + tq + (uint32_t)colour) & 1u);
+    const int L = p.L;
+    const int ws = (int)(x + (uint32_t)L * y + (uint32_t)p.plane * tq);
+    const int xp = (x == (uint32_t)(L - 1)) ? ws - (L - 1) : ws + 1;
+    const int xm = (x == 0) ? ws + (L - 1) : ws - 1;
+    const int yp = (y == (uint32_t)(L - 1)) ? ws - (L - 1) * L : ws + L;
+    const int ym = (y == 0) ? ws + (L - 1) * L : ws - L;
+    const bool top = tq == (uint32_t)(p.M - 1), bottom = tq == 0;
+    const int tp = top ? ws - (p.M - 1) * p.plane : ws + p.plane;
+    const int tm = bottom ? ws + (p.M - 1) * p.plane : ws - p.plane;
+    const uint32_t c = S[ws];
+    uint32_t nup = S[tp], ndn = S[tm];
+    if (top) nup = __funnelshift_r(nup, nup, 1) ^ ap_up;   // bit j <- bit j+1 of tau' = 0
+    if (bottom) ndn = __funnelshift_l(ndn, ndn, 1) ^ ap_dn;   // bit j <- bit j-1 of tau' = M-1
+    const int i2 = (int)(x + (uint32_t)L * y);
+    const uint32_t jc = __ldg(J + i2);
+    const uint32_t jxm = __ldg(J + (x == 0 ? i2 + L - 1 : i2 - 1));
+    const uint32_t jym = __ldg(J + (y == 0 ? i2 + (L - 1) * L : i2 - L));
+    // unsatisfied bond masks: J S S' = -1 <=> bit(S) ^ bit(S') ^ bit(J) = 1
+    uint32_t e1 = c ^ S[xp] ^ (0u - (jc & 1u));
+    uint32_t e2 = c ^ S[xm] ^ (0u - (jxm & 1u));
+    uint32_t e3 = c ^ S[yp] ^ (0u - ((jc >> 1) & 1u));
+    uint32_t e4 = c ^ S[ym] ^ (0u - ((jym >> 1) & 1u));
+    uint32_t e5 = c ^ nup;
+    uint32_t e6 = c ^ ndn;
+    uint32_t f = 0;
+    if (!count_only) {
+      // u = u0 + 2 u1 + 4 u2, bit-sliced over the 32 sites
+      const uint32_t s1 = e1 ^ e2 ^ e3, k1 = maj3(e1, e2, e3);
+      const uint32_t s2 = e4 ^ e5 ^ e6, k2 = maj3(e4, e5, e6);
+      const uint32_t u0 = s1 ^ s2, h = s1 & s2;
+      const uint32_t u1 = k1 ^ k2 ^ h, u2 = maj3(k1, k2, h);
+      const uint32_t ge3 = u2 | (u1 & u0);
+      const uint32_t eq2 = ~u2 & u1 & ~u0, eq1 = ~u2 & ~u1 & u0, eq0 = ~(u2 | u1 | u0);
+      const uint32_t b4 = daemon_word((uint32_t)ws, t, c2, c3, p.key, lut_s, cum_s);
+      const uint32_t b8 = daemon_word((uint32_t)ws, t, c2, c3 | (1u << 24), p.key, lut_s, cum_s);
+      const uint32_t b12 = daemon_word((uint32_t)ws, t, c2, c3 | (2u << 24), p.key, lut_s, cum_s);
+      f = ge3 | (b4 & (eq2 | (b8 & (eq1 | (b12 & eq0)))));
+      S[ws] = c ^ f;
+    }
+    if (BLUE) {
+      us_cnt += __popc(e1 ^ f) + __popc(e2 ^ f) + __popc(e3 ^ f) + __popc(e4 ^ f);
+      ut_cnt += __popc(e5 ^ f) + __popc(e6 ^ f);
+    }
+  }
+  if (BLUE) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      us_cnt += __shfl_xor_sync(0xFFFFFFFFu, us_cnt, o);
+      ut_cnt += __shfl_xor_sync(0xFFFFFFFFu, ut_cnt, o);
+    }
+    if (lane == 0) {
+      red_s[0][threadIdx.x >> 5] = us_cnt;
+      red_s[1][threadIdx.x >> 5] = ut_cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      unsigned long long v = 0;
+      for (int i = 0; i < kBlock / 32; ++i) v += red_s[threadIdx.x][i];
+      if (v) atomicAdd(p.U + sys * 2 + threadIdx.x, v);
+    }
+  }
+}
+
+// Overlaps of the configurations at slot s (Appendix E.1): count the sites
+// where the replicas r1 < r2 differ (popcount of the XOR of their words);
+// q = N - 2 * count.  Grid (chunks, n_slots, n_a).
+__global__ void __launch_bounds__(kBlock) sites_overlap_kernel(const uint32_t *spins, const int32_t *walker,
+                                                               long long *qcnt, int64_t a0, int n_words,
+                                                               int n_rep, int n_slots) {
+  extern __shared__ long long q_s[];  // [n_pairs]
+  const int n_pairs = n_rep * (n_rep - 1) / 2;
+  const int s = blockIdx.y;
+  const int64_t a = a0 + blockIdx.z;
+  for (int i = threadIdx.x; i < n_pairs; i += blockDim.x) q_s[i] = 0;
+  __syncthreads();
+  const int32_t *wa = walker + a * n_rep * n_slots;
+  int p = 0;
+  for (int r1 = 0; r1 < n_rep; ++r1) {
+    const uint32_t *S1 = spins + ((a * n_rep + r1) * n_slots + wa[r1 * n_slots + s]) * (int64_t)n_words;
+    for (int r2 = r1 + 1; r2 < n_rep; ++r2, ++p) {
+      const uint32_t *S2 = spins + ((a * n_rep + r2) * n_slots + wa[r2 * n_slots + s]) * (int64_t)n_words;
+      unsigned cnt = 0;
+      for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_words; i += gridDim.x * blockDim.x)
+        cnt += __popc(S1[i] ^ S2[i]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+      if ((threadIdx.x & 31) == 0 && cnt)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&q_s[p]), (unsigned long long)cnt);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_pairs; i += blockDim.x)
+    if (q_s[i])
+      atomicAdd(reinterpret_cast<unsigned long long *>(&qcnt[(a * n_slots + s) * n_pairs + i]),
+                (unsigned long long)q_s[i]);
+}
+
+// Start spins from Philox domain DOM_INIT: one thread per word, 32 draws.
+__global__ void sites_init_spins_kernel(uint32_t *spins, int64_t n_sys, int n_words, int L, int M, int n_rep,
+                                        int n_slots, uint2 key) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_sys * n_words) return;
+  const int ws = (int)(c % n_words);
+  const int64_t sys = c / n_words;
+  const int w = (int)(sys % n_slots);
+  const int64_t ar = sys / n_slots;
+  const int r = (int)(ar % n_rep);
+  const int64_t a = ar / n_rep;
+  const int plane = L * L;
+  const int tq = ws / plane, i2 = ws - tq * plane;
+  uint32_t v = 0;
+  for (int j = 0; j < 32; ++j) {
+    const uint32_t site = (uint32_t)(i2 + plane * (tq + j * M));
+    const uint4 x = philox(make_uint4(site, (uint32_t)w, (uint32_t)a, (DOM_INIT << 28) | (uint32_t)r), key);
+    if (!(x.x & 1u)) v |= 1u << j;   // spin -1
+  }
+  spins[c] = v;
+}
+
+SitesArgs make_args(qisg_handle *h) {
+  SitesArgs p;
+  p.spins = reinterpret_cast<uint32_t *>(h->spins);
+  p.J = reinterpret_cast<const uint8_t *>(h->J);
+  p.walker = h->d_walker;
+  p.cum = h->d_dcum;
+  p.lut = h->d_dlut;
+  p.U = h->d_U;
+  p.d_t = h->d_t;
+  p.key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  p.L = h->L;
+  p.M = h->Lt / 32;
+  p.plane = h->L * h->L;
+  p.half_plane = p.plane / 2;
+  p.n_words = p.plane * p.M;
+  p.half_words = p.n_words / 2;
+  p.half_plane_div = FastDiv((uint32_t)p.half_plane);
+  p.half_L_div = FastDiv((uint32_t)(h->L / 2));
+  p.n_slots = h->n_slots;
+  p.n_rep = h->n_rep;
+  p.tau_ap = h->tau_ap;
+  // words per thread: up to 8, while the grid keeps 8 blocks per SM
+  const int64_t n_sys = h->n_samples * h->n_rep * h->n_slots;
+  int wpt = h->sweep_tile[0] > 0 ? h->sweep_tile[0] : 8;
+  while (wpt > 1 && n_sys * ((p.half_words + kBlock * wpt - 1) / (kBlock * wpt)) < 8LL * h->n_sm) wpt >>= 1;
+  p.words_per_thread = wpt;
+  p.blocks_per_sys = (p.half_words + kBlock * wpt - 1) / (kBlock * wpt);
+  return p;
+}
+
+// Fixed-point numbers in [0, 2) with 126 fractional bits.
+using u128 = unsigned __int128;
+constexpr int kFrac = 126;
+const u128 kOne = (u128)1 << kFrac;
+
+// floor(a b / 2^126) for a, b < 2^127, through 64-bit limbs.
+u128 mulq(u128 a, u128 b) {
+  const uint64_t a0 = (uint64_t)a, a1 = (uint64_t)(a >> 64), b0 = (uint64_t)b, b1 = (uint64_t)(b >> 64);
+  const u128 p00 = (u128)a0 * b0, p01 = (u128)a0 * b1, p10 = (u128)a1 * b0, p11 = (u128)a1 * b1;
+  const u128 mid = (p00 >> 64) + (uint64_t)p01 + (uint64_t)p10;
+  const u128 hi = p11 + (p01 >> 64) + (p10 >> 64) + (mid >> 64);   // bits 128..255
+  const u128 lo = (mid << 64) | (uint64_t)p00;                       // bits 0..127
+  return (hi << (128 - kFrac)) | (lo >> kFrac);
+}
+
+// e^{-x} for 0 <= x <= 64 in fixed point: x = y 2^m with y < 1/16 (exact),
+// e^{-y} by its Taylor series (terms to y^30/30!), then m squarings.
+u128 exp_neg(double x) {
+  int m = 0;
+  while (x / std::ldexp(1.0, m) >= 1.0 / 16) ++m;
+  const double y = x / std::ldexp(1.0, m);   // exact: a power-of-two scaling
+  int ex = 0;
+  const double fr = std::frexp(y, &ex);     // y = fr 2^ex, fr in [0.5, 1)
+  const uint64_t mant = (uint64_t)std::ldexp(fr, 53);
+  const int sh = kFrac + ex - 53;
+  const u128 yq = y == 0.0 ? 0 : (sh >= 0 ? (u128)mant << sh : (u128)(mant >> (-sh)));
+  u128 term = kOne, pos = kOne, neg = 0;
+  for (int i = 1; i <= 30; ++i) {
+    term = mulq(term, yq) / (u128)i;
+    if (i & 1) neg += term;
+    else pos += term;
+  }
+  u128 r = pos - neg;
+  for (int i = 0; i < m; ++i) r = mulq(r, r);
+  return r;
+}
+
+}  // namespace
+
+// cumulative(0..254) of Sec. 2.1.1 for coupling k (0 <= k <= 16):
+// floor(2^64 sum_{m <= n} p^pop(m) (1-p)^(8-pop(m))), p = e^{-4k}, in
+// fixed point with 126 fractional bits (the paper uses 128-bit floats).
+void daemon_cumulative(double k, uint64_t *cum) {
+  const u128 p = exp_neg(4.0 * k);
+  const u128 q = kOne - p;
+  u128 pw[9], qw[9];
+  pw[0] = qw[0] = kOne;
+  for (int c = 1; c <= 8; ++c) {
+    pw[c] = mulq(pw[c - 1], p);
+    qw[c] = mulq(qw[c - 1], q);
+  }
+  u128 acc = 0;
+  for (int n = 0; n < 255; ++n) {
+    const int c = __builtin_popcount((unsigned)n);
+    acc += mulq(pw[c], qw[8 - c]);
+    cum[n] = (uint64_t)(acc >> (kFrac - 64));
+  }
+}
+
+// Prefix index of one cumulative table: entry h covers the words
+// [h 2^(64-bits), (h+1) 2^(64-bits)), whose n* lie in [n_min, n_max];
+// entry = n_min | (n_max - n_min) << 8.
+void daemon_lut(const uint64_t *cum, int bits, uint16_t *lut) {
+  auto ns = [&](uint64_t R) {
+    uint32_t c = 0;
+    while (c < 255 && cum[c] <= R) ++c;   // cum is non-decreasing
+    return c;
+  };
+  for (uint64_t h = 0; h < (1ull << bits); ++h) {
+    const uint64_t lo = h << (64 - bits), hi = lo + ((~0ull) >> bits);
+    const uint32_t a = ns(lo), b = ns(hi);
+    lut[h] = (uint16_t)(a | ((b - a) << 8));
+  }
+}
+
+int sites_build_tables(qisg_handle *h) {
+  const int n = h->n_slots, nl = 1 << kDaemonLutBits;
+  std::vector<unsigned long long> cum((size_t)n * 256);
+  std::vector<uint16_t> lut((size_t)n * nl);
+  for (int s = 0; s < n; ++s) {
+    uint64_t c[256];
+    daemon_cumulative(h->k[s], c);
+    c[255] = ~0ull;
+    for (int i = 0; i < 256; ++i) cum[(size_t)s * 256 + i] = c[i];
+    daemon_lut(c, kDaemonLutBits, lut.data() + (size_t)s * nl);
+  }
+  int rc = cuda_check(cudaMemcpyAsync(h->d_dcum, cum.data(), cum.size() * 8, cudaMemcpyHostToDevice, h->stream),
+                      "copy cumulative tables");
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync(h->d_dlut, lut.data(), lut.size() * 2, cudaMemcpyHostToDevice, h->stream),
+                    "copy prefix index");
+  // the host vectors must outlive the copies
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  return rc;
+}
+
+int sites_init(qisg_handle *h) {
+  int rc = sites_build_tables(h);
+  if (rc) return rc;
+  const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  rc = lanes_init_couplings(h);
+  if (rc) return rc;
+  const int n_words = h->L * h->L * (h->Lt / 32);
+  const int64_t n_sys = h->n_samples * h->n_rep * h->n_slots;
+  const int64_t nS = n_sys * n_words;
+  if ((nS + 255) / 256 > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large");
+  sites_init_spins_kernel<<<(unsigned)((nS + 255) / 256), 256, 0, h->stream>>>(
+      reinterpret_cast<uint32_t *>(h->spins), n_sys, n_words, h->L, h->Lt / 32, h->n_rep, h->n_slots, key);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "sites init");
+}
+
+int sites_half_sweep(qisg_handle *h, int colour, int count_only) {
+  const SitesArgs p = make_args(h);
+  const int64_t n_sys = h->n_samples * h->n_rep * h->n_slots;
+  const int64_t blocks = n_sys * p.blocks_per_sys;
+  if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+  const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
+  if (colour == 1)
+    sites_half_sweep_kernel<true><<<(unsigned)blocks, kBlock, 0, h->stream>>>(p, count_only);
+  else
+    sites_half_sweep_kernel<false><<<(unsigned)blocks, kBlock, 0, h->stream>>>(p, count_only);
+  prof_end(h, QISG_KERNEL_SWEEP, tok);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "sites half sweep");
+}
+
+int sites_measure(qisg_handle *h, int force_to_q) {
+  const int n_pairs = h->n_pairs();
+  if (n_pairs > 0) {
+    const int n_words = h->L * h->L * (h->Lt / 32);
+    const int64_t chunks = std::min<int64_t>((n_words + kBlock - 1) / kBlock, 64);
+    const size_t smem = (size_t)n_pairs * 8;
+    for (int64_t a0 = 0; a0 < h->n_samples; a0 += 65535) {
+      const int64_t na = std::min<int64_t>(65535, h->n_samples - a0);
+      const int tok = prof_begin(h, QISG_KERNEL_MEASURE);
+      sites_overlap_kernel<<<dim3((unsigned)chunks, (unsigned)h->n_slots, (unsigned)na), kBlock, smem,
+                             h->stream>>>(reinterpret_cast<const uint32_t *>(h->spins), h->d_walker, h->d_q, a0,
+                                          n_words, h->n_rep, h->n_slots);
+      prof_end(h, QISG_KERNEL_MEASURE, tok);
+      h->launches++;
+    }
+    int rc = cuda_check(cudaGetLastError(), "sites overlaps");
+    if (rc) return rc;
+  }
+  return lanes_finalize(h, force_to_q);
+}
+
+int sites_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
+  const int M = h->Lt / 32, plane = h->L * h->L, n_words = plane * M;
+  const size_t per_a = (size_t)h->n_rep * h->n_slots * n_words;
+  std::vector<uint32_t> buf(per_a * n_a);
+  int rc = cuda_check(cudaMemcpyAsync(buf.data(), reinterpret_cast<const uint32_t *>(h->spins) + a_lo * per_a,
+                                      buf.size() * 4, cudaMemcpyDeviceToHost, h->stream),
+                      "copy spins");
+  if (rc) return rc;
+  rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  if (rc) return rc;
+  for (size_t sys = 0; sys < (size_t)n_a * h->n_rep * h->n_slots; ++sys) {
+    const uint32_t *src = buf.data() + sys * n_words;
+    int8_t *dst = S + sys * h->N;
+    for (int64_t site = 0; site < h->N; ++site) {
+      const int64_t tau = site / plane, i2 = site % plane;
+      const uint32_t v = src[i2 + plane * (tau % M)];
+      dst[site] = ((v >> (tau / M)) & 1u) ? -1 : 1;
+    }
+  }
+  return QISG_OK;
+}
+
+int sites_set_spins(qisg_handle *h, const int8_t *S) {
+  const int M = h->Lt / 32, plane = h->L * h->L, n_words = plane * M;
+  const size_t n_sys = (size_t)h->n_samples * h->n_rep * h->n_slots;
+  std::vector<uint32_t> buf(n_sys * n_words, 0u);
+  for (size_t sys = 0; sys < n_sys; ++sys) {
+    const int8_t *src = S + sys * h->N;
+    uint32_t *dst = buf.data() + sys * n_words;
+    for (int64_t site = 0; site < h->N; ++site)
+      if (src[site] == -1) {
+        const int64_t tau = site / plane, i2 = site % plane;
+        dst[i2 + plane * (tau % M)] |= 1u << (tau / M);
+      }
+  }
+  int rc = cuda_check(cudaMemcpyAsync(h->spins, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice, h->stream),
+                      "copy spins");
+  if (rc) return rc;
+  return cuda_check(cudaStreamSynchronize(h->stream), "sync");
+}
+
+}  // namespace qisg
+
+extern "C" int qisg_daemon_tables(double k, int lut_bits, uint64_t *cum, uint16_t *lut) {
+  if (!cum || !(k >= 0.0) || !(k <= 16.0)) return qisg::fail(QISG_EINVAL, "need 0 <= k <= 16 and a table");
+  if (lut && (lut_bits < 1 || lut_bits > 16)) return qisg::fail(QISG_EINVAL, "lut_bits must be in 1..16");
+  qisg::daemon_cumulative(k, cum);
+  if (lut) qisg::daemon_lut(cum, lut_bits, lut);
+  return QISG_OK;
+}

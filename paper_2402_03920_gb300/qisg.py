@@ -16,7 +16,7 @@ import numpy as np
 
 from . import _build_lib
 
-QISG_LAYOUT_AUTO, QISG_LAYOUT_LANES, QISG_LAYOUT_SAMPLES = 0, 1, 2
+QISG_LAYOUT_AUTO, QISG_LAYOUT_LANES, QISG_LAYOUT_SAMPLES, QISG_LAYOUT_SITES = 0, 1, 2, 3
 KERNEL_SWEEP, KERNEL_PT, KERNEL_MEASURE, KERNEL_PERMUTE = 0, 1, 2, 3
 PROFILE_ONLY = 0x100
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ECORRUPT", -6: "ESTATE"}
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
         "qisg_batch_sync": (I, [P]),
         "qisg_batch_destroy": (None, [P]),
         "qisg_profile_read": (I, [P, I, P, P, P]),
+        "qisg_daemon_tables": (I, [D, I, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -118,7 +119,7 @@ def exported_symbols():
             "qisg_autotune", "qisg_get_tiles", "qisg_set_tiles", "qisg_batch_create", "qisg_batch_admit", "qisg_batch_retire",
             "qisg_batch_run", "qisg_batch_set_schedule", "qisg_batch_autotune", "qisg_batch_status",
             "qisg_batch_results", "qisg_batch_info", "qisg_batch_instance_bytes", "qisg_batch_sync",
-            "qisg_batch_destroy"]
+            "qisg_batch_destroy", "qisg_daemon_tables"]
 
 
 def _check(rc: int):
@@ -138,6 +139,22 @@ def ladder_linear(lo: float, hi: float, n: int, gamma: float) -> np.ndarray:
     arr = (Slot * n)()
     _check(load().qisg_ladder_linear(lo, hi, n, gamma, ctypes.cast(arr, ctypes.c_void_p)))
     return np.array([[s.k, s.k_tau] for s in arr], dtype=np.float64)
+
+
+def daemon_tables(k: float, lut_bits: int = 12):
+    """cumulative(0..254) (uint64) and the prefix index (uint16, 2^lut_bits
+    entries) of the SITES daemon rule for coupling k."""
+    cum = np.zeros(255, dtype=np.uint64)
+    lut = np.zeros(1 << lut_bits, dtype=np.uint16)
+    _check(load().qisg_daemon_tables(float(k), int(lut_bits), _ptr(cum), _ptr(lut)))
+    return cum, lut
+
+
+def ladder_equal(lo: float, hi: float, n: int) -> np.ndarray:
+    """[n][2] ladder with k_tau = k (the paper's single coupling, Sec. 1),
+    k linear in [lo, hi]: the ladders the SITES daemon rule takes."""
+    k = np.array([lo] if n == 1 else [lo + (hi - lo) * s / (n - 1) for s in range(n)], dtype=np.float64)
+    return np.stack([k, k], axis=1)
 
 
 def current_stream_ptr() -> int | None:

@@ -94,7 +94,7 @@ def _bin_probs(cum):
     return [Fraction(c[n + 1] - c[n], TWO64) for n in range(256)]
 
 
-@pytest.mark.parametrize("k", [0.1, 0.29, 0.5, 1.3])
+@pytest.mark.parametrize("k", [0.0, 0.1, 0.29, 0.5, 1.3, 16.0])
 def test_daemon_cumulative_is_product_of_bernoulli_bits(k):
     """Each of the 8 bits of n* is 1 with probability e^{-4k}, pairs are
     independent, and P(n) = p^pop(n) (1-p)^(8-pop(n)), all within the
@@ -285,3 +285,21 @@ def test_transfer_matrix_matches_enumeration():
             a, b, _, _ = exact.enumerate_AB(J, L, Lt, k, kt)
             ta, tb = exact.transfer_AB(J, L, Lt, k, kt)
             assert abs(a - ta) < 1e-9 and abs(b - tb) < 1e-9
+
+
+def test_one_system_sweep_is_the_chain_sweep():
+    """The oracle's one-system sweep (used where the full chain is too slow)
+    applies to a system exactly what the full run does to it (no PT)."""
+    L, Lt = 4, 128
+    k = np.array([0.25, 0.4, 0.55])
+    for tau_ap in (False, True):
+        st = oracle.new_state(L, Lt, k, k.copy(), n_rep=2, seed=8, n_a=2, tau_ap=tau_ap, daemon=True)
+        S0 = st.S.copy()
+        oracle.run(st, 2, pt_every=0)
+        for a in range(2):
+            for r in range(2):
+                for w in range(3):
+                    S = np.ascontiguousarray(S0[a, r, w])
+                    for t in range(2):
+                        oracle.daemon_sweep_system(L, Lt, 8, a, r, w, t, st.J[a], S, st.cum, tau_ap)
+                    assert np.array_equal(S, st.S[a, r, w]), (tau_ap, a, r, w)
