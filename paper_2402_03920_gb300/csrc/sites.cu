@@ -19,16 +19,24 @@
 // four 64-bit "50/50" words) and one xoroshiro128++ state step of the same
 // 128 bits (the lower halves); byte i of the word is n* of 64-bit word i,
 // the bin of the word in the cumulative table of the walker's slot.  n* is
-// found from an index of the top kLutBits bits (the bins that the prefix's
-// range of words can fall in, [n_min, n_min + span]) and at most span
-// comparisons against the cumulative table, both staged in shared memory.
+// found from an index of the top kDaemonLutBits bits, staged in shared
+// memory: the words with a given prefix fall in the bins [n_min, n_min +
+// span], so n* = n_min + #{q in [n_min, n_min + span): cumulative(q) <= word}.
+// With span <= 1 the entry holds the upper half of the one cut point and
+// n* = n_min + [upper half of the word > it]; with span >= 2 the upper
+// halves of the span cut points are compared one by one.  Only when an
+// upper half equals a cut point's does the lower half matter: then the
+// whole daemon word is redone with the full 64-bit words (the xoroshiro
+// step is only computed there).
 //
 // Device arrays (systems walker-major; PT exchanges slot labels only):
 //   spins  u32 [a][r][w][L^2 M]       bit = 1 <=> spin -1
 //   J      uint8 [a][x + L*y]          bit0: J(+x) = -1, bit1: J(+y) = -1
 //   U      u64 [a][r][w][2]            unsatisfied spatial / tau bonds of walker w
 //   cum    u64 [n_slots][256]          cumulative(0..254) of Sec. 2.1.1; [255] = 2^64-1
-//   lut    u16 [n_slots][2^kLutBits]   n_min | span << 8 of each prefix
+//   lut    uint2 [n_slots][2^kDaemonLutBits]
+//                                      {n_min | span << 8, upper half of cumulative(n_min)
+//                                       when span = 1, else 2^32 - 1}
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -45,7 +53,7 @@ struct SitesArgs {
   const uint8_t *J;
   const int32_t *walker;
   const unsigned long long *cum;
-  const uint16_t *lut;
+  const uint2 *lut;
   unsigned long long *U;
   const unsigned long long *d_t;
   uint2 key;
@@ -68,26 +76,65 @@ __device__ __forceinline__ uint4 xoroshiro_step(uint4 x) {
   return make_uint4((uint32_t)n0, (uint32_t)(n0 >> 32), (uint32_t)n1, (uint32_t)(n1 >> 32));
 }
 
-// n* of the 64-bit word hi:lo (Sec. 2.1.1) from the prefix index and the
-// cumulative table of one slot (shared memory).
-__device__ __forceinline__ uint32_t nstar(uint32_t hi, uint32_t lo, const uint16_t *lut,
-                                          const unsigned long long *cum) {
-  const uint32_t e = lut[hi >> (32 - kDaemonLutBits)];
+// Philox4x32-10 with 32 x 32 -> 64-bit products (the same function as
+// philox(): each round's high and low halves come from one wide multiply).
+__device__ __forceinline__ uint4 philox_wide(uint4 c, uint2 k) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const unsigned long long p0 = (unsigned long long)kPhiloxM0 * c.x;
+    const unsigned long long p1 = (unsigned long long)kPhiloxM1 * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y, (uint32_t)p0);
+    k.x += kPhiloxW0;
+    k.y += kPhiloxW1;
+  }
+  return c;
+}
+
+// Exact n* of 64-bit word i of a daemon word (the rare path): the lower
+// half from the xoroshiro step of the Philox output x, then the count of
+// the cut points at or below the word among the prefix's candidates.
+static __device__ __noinline__ uint32_t nstar_exact(uint4 x, int i, const uint2 *lut,
+                                                    const unsigned long long *cum) {
+  const uint4 lo = xoroshiro_step(x);
+  const uint32_t hi = pick4(x, i), l = pick4(lo, i);
+  const unsigned long long R = ((unsigned long long)hi << 32) | l;
+  const uint32_t e = lut[hi >> (32 - kDaemonLutBits)].x;
   uint32_t n = e & 0xFFu;
   const uint32_t end = n + (e >> 8);
-  const unsigned long long R = ((unsigned long long)hi << 32) | lo;
   for (uint32_t q = n; q < end; ++q) n += (R >= cum[q]) ? 1u : 0u;
   return n;
 }
 
+// n* of a 64-bit word from its upper half hi, or *tie when the upper
+// halves of the word and a candidate cut point are equal.
+__device__ __forceinline__ uint32_t nstar_hi(uint32_t hi, const uint2 *lut, const uint32_t *cut_hi, bool *tie) {
+  const uint2 e = lut[hi >> (32 - kDaemonLutBits)];
+  uint32_t n = (e.x & 0xFFu) + (hi > e.y ? 1u : 0u);
+  *tie |= hi == e.y;
+  if (e.x >= 0x200u) {   // span >= 2 (e.y is all ones there)
+    const uint32_t n0 = e.x & 0xFFu, end = n0 + (e.x >> 8);
+    for (uint32_t q = n0; q < end; ++q) {
+      const uint32_t c = cut_hi[q];
+      n += hi > c ? 1u : 0u;
+      *tie |= hi == c;
+    }
+  }
+  return n;
+}
+
 // Daemon word `which` (0: b4, 1: b8, 2: b12) of word-site ws of system
-// (a, r, slot s) in sweep t.
+// (a, r, slot s) in sweep t: byte i is n* of the 64-bit word whose upper
+// half is Philox output i.
 __device__ __forceinline__ uint32_t daemon_word(uint32_t ws, uint32_t t, uint32_t c2, uint32_t c3, uint2 key,
-                                                const uint16_t *lut, const unsigned long long *cum) {
-  const uint4 x = philox(make_uint4(ws, t, c2, c3), key);
-  const uint4 lo = xoroshiro_step(x);
-  return nstar(x.x, lo.x, lut, cum) | (nstar(x.y, lo.y, lut, cum) << 8) | (nstar(x.z, lo.z, lut, cum) << 16) |
-         (nstar(x.w, lo.w, lut, cum) << 24);
+                                                const uint2 *lut, const uint32_t *cut_hi,
+                                                const unsigned long long *cum) {
+  const uint4 x = philox_wide(make_uint4(ws, t, c2, c3), key);
+  bool tie = false;
+  const uint32_t b = nstar_hi(x.x, lut, cut_hi, &tie) | (nstar_hi(x.y, lut, cut_hi, &tie) << 8) |
+                     (nstar_hi(x.z, lut, cut_hi, &tie) << 16) | (nstar_hi(x.w, lut, cut_hi, &tie) << 24);
+  if (!tie) return b;
+  return nstar_exact(x, 0, lut, cum) | (nstar_exact(x, 1, lut, cum) << 8) | (nstar_exact(x, 2, lut, cum) << 16) |
+         (nstar_exact(x, 3, lut, cum) << 24);
 }
 
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
@@ -103,7 +150,8 @@ __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { r
 template <bool BLUE>
 __global__ void __launch_bounds__(kBlock) sites_half_sweep_kernel(SitesArgs p, int count_only) {
   __shared__ unsigned long long cum_s[256];
-  __shared__ __align__(16) uint16_t lut_s[1 << kDaemonLutBits];
+  __shared__ uint32_t cut_hi_s[256];
+  extern __shared__ __align__(16) uint2 lut_s[];   // [2^kDaemonLutBits]
   __shared__ unsigned long long red_s[2][kBlock / 32];
   const int64_t sys = blockIdx.x / p.blocks_per_sys;
   const int chunk = (int)(blockIdx.x - sys * p.blocks_per_sys);
@@ -121,10 +169,14 @@ __global__ void __launch_bounds__(kBlock) sites_half_sweep_kernel(SitesArgs p, i
   // stage the slot's tables
   {
     const unsigned long long *cg = p.cum + (size_t)s * 256;
-    for (int i = threadIdx.x; i < 256; i += kBlock) cum_s[i] = __ldg(cg + i);
+    for (int i = threadIdx.x; i < 256; i += kBlock) {
+      const unsigned long long v = __ldg(cg + i);
+      cum_s[i] = v;
+      cut_hi_s[i] = (uint32_t)(v >> 32);
+    }
     const uint4 *lg = reinterpret_cast<const uint4 *>(p.lut + ((size_t)s << kDaemonLutBits));
     uint4 *ls = reinterpret_cast<uint4 *>(lut_s);
-    for (int i = threadIdx.x; i < (1 << kDaemonLutBits) / 8; i += kBlock) ls[i] = __ldg(lg + i);
+    for (int i = threadIdx.x; i < (1 << kDaemonLutBits) / 2; i += kBlock) ls[i] = __ldg(lg + i);
   }
   __syncthreads();
   uint32_t *S = p.spins + sys * p.n_words;
@@ -177,9 +229,9 @@ __global__ void __launch_bounds__(kBlock) sites_half_sweep_kernel(SitesArgs p, i
       const uint32_t u1 = k1 ^ k2 ^ h, u2 = maj3(k1, k2, h);
       const uint32_t ge3 = u2 | (u1 & u0);
       const uint32_t eq2 = ~u2 & u1 & ~u0, eq1 = ~u2 & ~u1 & u0, eq0 = ~(u2 | u1 | u0);
-      const uint32_t b4 = daemon_word((uint32_t)ws, t, c2, c3, p.key, lut_s, cum_s);
-      const uint32_t b8 = daemon_word((uint32_t)ws, t, c2, c3 | (1u << 24), p.key, lut_s, cum_s);
-      const uint32_t b12 = daemon_word((uint32_t)ws, t, c2, c3 | (2u << 24), p.key, lut_s, cum_s);
+      const uint32_t b4 = daemon_word((uint32_t)ws, t, c2, c3, p.key, lut_s, cut_hi_s, cum_s);
+      const uint32_t b8 = daemon_word((uint32_t)ws, t, c2, c3 | (1u << 24), p.key, lut_s, cut_hi_s, cum_s);
+      const uint32_t b12 = daemon_word((uint32_t)ws, t, c2, c3 | (2u << 24), p.key, lut_s, cut_hi_s, cum_s);
       f = ge3 | (b4 & (eq2 | (b8 & (eq1 | (b12 & eq0)))));
       S[ws] = c ^ f;
     }
@@ -355,7 +407,7 @@ void daemon_cumulative(double k, uint64_t *cum) {
 // Prefix index of one cumulative table: entry h covers the words
 // [h 2^(64-bits), (h+1) 2^(64-bits)), whose n* lie in [n_min, n_max];
 // entry = n_min | (n_max - n_min) << 8.
-void daemon_lut(const uint64_t *cum, int bits, uint16_t *lut) {
+void daemon_lut(const uint64_t *cum, int bits, uint16_t *lut, uint32_t *cut_hi = nullptr) {
   auto ns = [&](uint64_t R) {
     uint32_t c = 0;
     while (c < 255 && cum[c] <= R) ++c;   // cum is non-decreasing
@@ -365,24 +417,29 @@ void daemon_lut(const uint64_t *cum, int bits, uint16_t *lut) {
     const uint64_t lo = h << (64 - bits), hi = lo + ((~0ull) >> bits);
     const uint32_t a = ns(lo), b = ns(hi);
     lut[h] = (uint16_t)(a | ((b - a) << 8));
+    // upper half of the one cut point inside the cell, else all ones
+    if (cut_hi) cut_hi[h] = (b - a == 1) ? (uint32_t)(cum[a] >> 32) : 0xFFFFFFFFu;
   }
 }
 
 int sites_build_tables(qisg_handle *h) {
   const int n = h->n_slots, nl = 1 << kDaemonLutBits;
   std::vector<unsigned long long> cum((size_t)n * 256);
-  std::vector<uint16_t> lut((size_t)n * nl);
+  std::vector<uint2> lut((size_t)n * nl);
+  std::vector<uint16_t> l16((size_t)nl);
+  std::vector<uint32_t> chi((size_t)nl);
   for (int s = 0; s < n; ++s) {
     uint64_t c[256];
     daemon_cumulative(h->k[s], c);
     c[255] = ~0ull;
     for (int i = 0; i < 256; ++i) cum[(size_t)s * 256 + i] = c[i];
-    daemon_lut(c, kDaemonLutBits, lut.data() + (size_t)s * nl);
+    daemon_lut(c, kDaemonLutBits, l16.data(), chi.data());
+    for (int i = 0; i < nl; ++i) lut[(size_t)s * nl + i] = make_uint2(l16[(size_t)i], chi[(size_t)i]);
   }
   int rc = cuda_check(cudaMemcpyAsync(h->d_dcum, cum.data(), cum.size() * 8, cudaMemcpyHostToDevice, h->stream),
                       "copy cumulative tables");
   if (!rc)
-    rc = cuda_check(cudaMemcpyAsync(h->d_dlut, lut.data(), lut.size() * 2, cudaMemcpyHostToDevice, h->stream),
+    rc = cuda_check(cudaMemcpyAsync(h->d_dlut, lut.data(), lut.size() * 8, cudaMemcpyHostToDevice, h->stream),
                     "copy prefix index");
   // the host vectors must outlive the copies
   if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
@@ -410,11 +467,18 @@ int sites_half_sweep(qisg_handle *h, int colour, int count_only) {
   const int64_t n_sys = h->n_samples * h->n_rep * h->n_slots;
   const int64_t blocks = n_sys * p.blocks_per_sys;
   if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+  constexpr size_t smem = sizeof(uint2) << kDaemonLutBits;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(sites_half_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(sites_half_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
   const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
   if (colour == 1)
-    sites_half_sweep_kernel<true><<<(unsigned)blocks, kBlock, 0, h->stream>>>(p, count_only);
+    sites_half_sweep_kernel<true><<<(unsigned)blocks, kBlock, smem, h->stream>>>(p, count_only);
   else
-    sites_half_sweep_kernel<false><<<(unsigned)blocks, kBlock, 0, h->stream>>>(p, count_only);
+    sites_half_sweep_kernel<false><<<(unsigned)blocks, kBlock, smem, h->stream>>>(p, count_only);
   prof_end(h, QISG_KERNEL_SWEEP, tok);
   h->launches++;
   return cuda_check(cudaGetLastError(), "sites half sweep");
