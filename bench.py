@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--forms", default="batched,per_instance")
-    p.add_argument("--extras", default="uneven,large,paper,serving",
+    p.add_argument("--extras", default="uneven,large,paper,daemon,serving",
                    help="other workloads measured beside the headline (empty: none)")
     p.add_argument("--serving-requests", type=int, default=100)
     p.add_argument("--tiles", default="",
@@ -418,6 +418,35 @@ def paper_shape_entry(torch, qisg, sweeps=10):
     return out
 
 
+def daemon_entry(torch, qisg, sweeps=10):
+    """The paper's own update rule and packing (SITES: 32 tau-sites of one
+    system per word, Ito-Kanada daemon bits from Philox + xoroshiro128++ +
+    the inverse-cumulative bytes) at the lattice shapes of its performance
+    figures, equal couplings: 16 samples x 4 replicas x 16 slots, k linear in
+    [0.2, 0.5], PT every sweep.  L=24 at L_tau=2048 as above."""
+    out = {}
+    n_a, n_r, n_slots = 16, 4, 16
+    ks = np.linspace(0.2, 0.5, n_slots)
+    ladder = np.stack([ks, ks], axis=1)
+    for L, Lt in ((16, 8192), (24, 2048)):
+        cfg = qisg.Config(L, Lt, ladder, n_r, n_a, 1, layout=qisg.QISG_LAYOUT_SITES)
+        with qisg.Instance(cfg) as inst:
+            inst.sweep(3)
+            inst.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            inst.sweep(sweeps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        ups = n_a * n_r * n_slots * L * L * Lt * sweeps
+        out[f"L{L}_Ltau{Lt}"] = {"value": ms * 1e9 / ups, "unit": UNIT, "ms_per_sweep": ms / sweeps}
+    out["workload"] = ("SITES packing with the daemon-bit rule, equal coupling k_tau = k, 16 samples x 4 replicas "
+                       "x 16 slots, k in [0.2, 0.5], PT every sweep")
+    out["paper_4xA100_ps"] = {"L16_Ltau8192": 0.466, "L24": 0.735, "per_A100_L16": 1.864}
+    return out
+
+
 def serving_entry(qisg, n_requests):
     """Poisson stream of requests (L 8..24, L_tau 32..1024, 8..32 slots,
     100..5000 sweeps, Gamma in [0.8, 1.2]) through the continuous-batching
@@ -548,6 +577,8 @@ def run_gpu(args):
         line["batched_large"] = large_batched_entry(torch, qisg)
     if "paper" in extras and world == 1:
         line["paper_shape"] = paper_shape_entry(torch, qisg)
+    if "daemon" in extras and world == 1:
+        line["paper_rule"] = daemon_entry(torch, qisg)
     if "serving" in extras and world == 1:
         line["serving"] = serving_entry(qisg, args.serving_requests)
     if not args.no_cpu_baseline and world == 1:
