@@ -229,9 +229,15 @@ __global__ void __launch_bounds__(kBlock) sites_half_sweep_kernel(SitesArgs p, i
       const uint32_t u1 = k1 ^ k2 ^ h, u2 = maj3(k1, k2, h);
       const uint32_t ge3 = u2 | (u1 & u0);
       const uint32_t eq2 = ~u2 & u1 & ~u0, eq1 = ~u2 & ~u1 & u0, eq0 = ~(u2 | u1 | u0);
-      const uint32_t b4 = daemon_word((uint32_t)ws, t, c2, c3, p.key, lut_s, cut_hi_s, cum_s);
-      const uint32_t b8 = daemon_word((uint32_t)ws, t, c2, c3 | (1u << 24), p.key, lut_s, cut_hi_s, cum_s);
-      const uint32_t b12 = daemon_word((uint32_t)ws, t, c2, c3 | (2u << 24), p.key, lut_s, cut_hi_s, cum_s);
+      // b4, b8, b12 in a rolled loop (one copy of the lookup code)
+      uint32_t b4 = 0, b8 = 0, b12 = 0;
+#pragma unroll 1
+      for (uint32_t which = 0; which < 3; ++which) {
+        const uint32_t dw = daemon_word((uint32_t)ws, t, c2, c3 | (which << 24), p.key, lut_s, cut_hi_s, cum_s);
+        b4 = b8;
+        b8 = b12;
+        b12 = dw;
+      }
       f = ge3 | (b4 & (eq2 | (b8 & (eq1 | (b12 & eq0)))));
       S[ws] = c ^ f;
     }
