@@ -27,6 +27,7 @@ namespace qisg {
 namespace {
 
 constexpr int kBatchBlock = 256;
+static_assert(kBatchBlock <= kLanesMaxThreads, "the LANES class-code buffer holds kLanesMaxThreads threads");
 constexpr long long kBarrierTimeoutNs = 5000000000ll;   // 5 s per wait
 
 struct InstDev {

@@ -19,6 +19,7 @@ namespace qisg {
 namespace {
 
 constexpr int kBlock = 256;
+static_assert(kBlock <= kLanesMaxThreads, "the LANES class-code buffer holds kLanesMaxThreads threads");
 
 template <typename Word>
 struct LanesArgs {

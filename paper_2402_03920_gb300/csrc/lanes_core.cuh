@@ -6,8 +6,12 @@
 // counts u_s (4 spatial bonds) and u_t (2 tau bonds) of every lane, and then
 // visits every (slot s, replica r): the walker w at slot s of replica r is
 // lane (r, w), whose draw R (one Philox call per (slot, replica quad, site,
-// sweep)) is compared with the threshold T[s][u_s][u_t] (Sec. 2.1).  The flip
-// mask of the site is built in registers and applied once.  In the blue pass
+// sweep)) is compared with the threshold T[s][u_s][u_t] (Sec. 2.1).  Before
+// that visit the thread spreads the five count planes into a byte per lane
+// in shared memory (the 5-bit class code u_s + 8 u_t, four lanes per word),
+// so a lane's class is one load and its threshold one more, from a 32-entry
+// row per slot.  The flip mask of the site is built in registers and
+// applied once.  In the blue pass
 // the unsatisfied bonds after the flip are accumulated per lane in bit-sliced
 // counters and flushed per tile (every bond has exactly one blue end).
 #pragma once
@@ -20,6 +24,8 @@ constexpr int kLanesMaxGroups = 2;    // word groups per site held in registers
 constexpr int kLanesKs = 7;           // u_s counter planes: <= 4 x 16 sites per thread
 constexpr int kLanesKt = 6;           // u_t counter planes: <= 2 x 16 sites per thread
 constexpr int kLanesMaxSitesPerThread = 16;
+constexpr int kLanesMaxThreads = 256;                    // block size the class-code buffer is sized for
+constexpr int kLanesCodeWords = kLanesMaxGroups * 16;    // per thread: 2 groups x 64 lanes, 4 per word
 
 template <typename Word>
 struct LanesSample {
@@ -36,15 +42,19 @@ struct LanesSample {
   int tau_ap;                    // antiperiodic along tau: the wrap tau bond flips sign
 };
 
-// Shared memory of one tile: T, walker labels, lane -> (r, w) and the plane
-// tables.
+// Shared memory of one tile: the thresholds by class code, walker labels,
+// counter sums, the per-thread class codes and the plane tables.
 __host__ __device__ inline size_t lanes_tile_smem(int plane, int n_slots, int n_rep) {
-  size_t o = (size_t)(n_slots * 15 + n_rep * n_slots) * 4;   // T_s, wa_s
+  size_t o = (size_t)(n_slots * 32 + n_rep * n_slots) * 4;   // T5_s, wa_s
   o += (size_t)2 * kLanesMaxGroups * 64 * 4;                  // acc_s, acc_t
+  o += (size_t)kLanesCodeWords * kLanesMaxThreads * 4;
   o = (o + 7) & ~size_t(7);
   o += (size_t)plane * (8 + 2 + 1);                           // nb, s2d, Js
   return (o + 15) & ~size_t(15);
 }
+
+// Bits 0..3 of x moved to bits 0, 8, 16, 24.
+__device__ __forceinline__ uint32_t spread4(uint32_t x) { return ((x & 0xFu) * 0x00204081u) & 0x01010101u; }
 
 template <bool CG, typename Word>
 __device__ __forceinline__ Word ld_word(const Word *p) {
@@ -59,18 +69,23 @@ __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n
                            unsigned char *smem) {
   constexpr int W = (int)sizeof(Word) * 8;
   const int n_slots = S.n_slots, n_rep = S.n_rep, plane = S.plane, hp = S.half_plane;
-  uint32_t *T_s = reinterpret_cast<uint32_t *>(smem);
-  int *wa_s = reinterpret_cast<int *>(T_s + n_slots * 15);
+  uint32_t *T5_s = reinterpret_cast<uint32_t *>(smem);   // [slot][code], code = u_s + 8 u_t
+  int *wa_s = reinterpret_cast<int *>(T5_s + n_slots * 32);
   int *acc_s = wa_s + n_rep * n_slots;                 // [group][lane]
   int *acc_t = acc_s + kLanesMaxGroups * 64;
-  size_t off = (size_t)(n_slots * 15 + n_rep * n_slots) * 4 + (size_t)2 * kLanesMaxGroups * 64 * 4;
+  uint32_t *code_s = reinterpret_cast<uint32_t *>(acc_t + kLanesMaxGroups * 64);   // [word][thread]
+  size_t off = (size_t)(n_slots * 32 + n_rep * n_slots) * 4 + (size_t)2 * kLanesMaxGroups * 64 * 4 +
+               (size_t)kLanesCodeWords * kLanesMaxThreads * 4;
   off = (off + 7) & ~size_t(7);
   uint2 *nb = reinterpret_cast<uint2 *>(smem + off);
   uint16_t *s2d = reinterpret_cast<uint16_t *>(nb + plane);
   uint8_t *Js = reinterpret_cast<uint8_t *>(s2d + plane);
 
   __syncthreads();   // a previous tile is done with shared memory
-  for (int i = threadIdx.x; i < n_slots * 15; i += blockDim.x) T_s[i] = S.T[i];
+  for (int i = threadIdx.x; i < n_slots * 32; i += blockDim.x) {
+    const int sl = i >> 5, us = i & 7, ut = (i >> 3) & 3;
+    T5_s[i] = (us <= 4 && ut <= 2) ? S.T[sl * 15 + us * 3 + ut] : 0xFFFFFFFFu;
+  }
   for (int i = threadIdx.x; i < n_rep * n_slots; i += blockDim.x) wa_s[i] = CG ? __ldcg(S.walker + i) : S.walker[i];
   if (BLUE)
     for (int i = threadIdx.x; i < 2 * kLanesMaxGroups * 64; i += blockDim.x) acc_s[i] = 0;
@@ -143,8 +158,28 @@ __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n
         }
       }
       if (!count_only) {
+        // class codes of every lane, a byte each: word g*16 + l/4 of this
+        // thread holds lanes l .. l+3 of group g
+        uint32_t *cw = code_s + threadIdx.x;
+#pragma unroll
+        for (int g = 0; g < kLanesMaxGroups; ++g)
+          if (g < NG) {
+#pragma unroll
+            for (int h = 0; h < W / 32; ++h) {
+              const uint32_t a0 = (uint32_t)(P0[g] >> (32 * h)), a1 = (uint32_t)(P1[g] >> (32 * h));
+              const uint32_t a2 = (uint32_t)(P2[g] >> (32 * h)), a3 = (uint32_t)(Q0[g] >> (32 * h));
+              const uint32_t a4 = (uint32_t)(Q1[g] >> (32 * h));
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const uint32_t c = spread4(a0 >> (4 * i)) | (spread4(a1 >> (4 * i)) << 1) |
+                                   (spread4(a2 >> (4 * i)) << 2) | (spread4(a3 >> (4 * i)) << 3) |
+                                   (spread4(a4 >> (4 * i)) << 4);
+                cw[(g * 16 + h * 8 + i) * kLanesMaxThreads] = c;
+              }
+            }
+          }
         for (int s = 0; s < n_slots; ++s) {
-          const uint32_t *Trow = T_s + s * 15;
+          const uint32_t *Trow = T5_s + s * 32;
           for (int q = 0; 4 * q < n_rep; ++q) {
             const uint4 R4 = philox(make_uint4(site, S.t, (uint32_t)s | ((uint32_t)q << 16), S.ctr_w), S.key);
 #pragma unroll
@@ -153,11 +188,8 @@ __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n
               if (r >= n_rep) break;
               const int g = r >= S.rpw ? 1 : 0;   // n_groups <= 2
               const int lane = (r - g * S.rpw) * n_slots + wa_s[r * n_slots + s];
-              const Word p0 = g ? P0[1] : P0[0], p1 = g ? P1[1] : P1[0], p2 = g ? P2[1] : P2[0];
-              const Word q0 = g ? Q0[1] : Q0[0], q1 = g ? Q1[1] : Q1[0];
-              const int us = (int)(((p0 >> lane) & 1u) | (((p1 >> lane) & 1u) << 1) | (((p2 >> lane) & 1u) << 2));
-              const int ut = (int)(((q0 >> lane) & 1u) | (((q1 >> lane) & 1u) << 1));
-              const uint32_t thr = Trow[us * 3 + ut];
+              const uint32_t word = cw[(g * 16 + (lane >> 2)) * kLanesMaxThreads];
+              const uint32_t thr = Trow[(word >> (8 * (lane & 3))) & 31u];
               if (thr == 0xFFFFFFFFu || pick4(R4, jj) < thr) {
                 if (g) fw[1] |= Word(1) << lane;
                 else fw[0] |= Word(1) << lane;
