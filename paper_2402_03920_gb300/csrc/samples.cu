@@ -1204,6 +1204,26 @@ __global__ void samples_extract_kernel(const Word *spins, const int32_t *walker,
   out[((ai * n_rep + r) * n_slots + w) * N + site] = ((v >> lane) & 1u) ? -1 : 1;
 }
 
+// Pack the int8 +-1 spins of replica r of the samples of word group b
+// (staged [a - b W][walker][site], n_a of them) into the lattice: a thread
+// per (slot, site) word, lane a - b W, walker from the device labels.
+template <typename Word>
+__global__ void samples_pack_kernel(Word *spins, const int8_t *stage, const int32_t *walker, int64_t b, int r,
+                                    int n_a, int64_t N, int n_slots, int n_q, int n_rep) {
+  constexpr int W = (int)sizeof(Word) * 8;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // [s][site]
+  if (c >= (int64_t)n_slots * N) return;
+  const int s = (int)(c / N);
+  const int64_t site = c - (int64_t)s * N;
+  Word v = 0;
+  for (int al = 0; al < n_a; ++al) {
+    const int64_t a = b * W + al;
+    const int w = walker[(a * n_rep + r) * n_slots + s];
+    if (stage[((int64_t)al * n_slots + w) * N + site] == -1) v |= Word(1) << al;
+  }
+  spins[(((b * n_slots + s) * n_q + (r >> 2)) * N + site) * 4 + (r & 3)] = v;
+}
+
 template <typename Word>
 SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
   SamplesArgs<Word> p;
@@ -1588,25 +1608,36 @@ int set_spins_t(qisg_handle *h, const int8_t *S, const int32_t *walker_at) {
     if (rc) return rc;
     h->perm_pending = false;
   }
-  const size_t words = (size_t)h->n_b * h->n_slots * h->n_q * h->N * 4;
-  std::vector<Word> buf(words, Word(0));
-  for (int64_t a = 0; a < h->n_samples; ++a) {
-    const int64_t b = a / W;
-    const Word bit = Word(1) << (a - b * W);
-    for (int r = 0; r < h->n_rep; ++r)
-      for (int s = 0; s < h->n_slots; ++s) {
-        const int w = walker_at[(a * h->n_rep + r) * h->n_slots + s];
-        const int8_t *src = S + ((a * h->n_rep + r) * h->n_slots + w) * h->N;
-        Word *dst = buf.data() + (((b * h->n_slots + s) * h->n_q + (r >> 2)) * h->N) * 4 + (r & 3);
-        for (int64_t i = 0; i < h->N; ++i)
-          if (src[i] == -1) dst[i * 4] |= bit;
-      }
-  }
-  int rc = cuda_check(cudaMemcpyAsync(h->spins, buf.data(), words * sizeof(Word), cudaMemcpyHostToDevice,
-                                      h->stream),
-                      "copy spins");
+  // the walker labels are on the device already (qisg_set_state uploads
+  // them first); the spins go up one (word group, replica) at a time into a
+  // staging buffer and are packed there
+  (void)walker_at;
+  const int64_t row = (int64_t)h->n_slots * h->N;   // bytes of one (sample, replica)
+  int8_t *stage = nullptr;
+  int rc = cuda_check(cudaMalloc(&stage, (size_t)W * row), "cudaMalloc");
   if (rc) return rc;
-  return cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  if ((size_t)h->n_q * 4 > (size_t)h->n_rep) {   // padding replicas of the last quad stay 0
+    rc = cuda_check(cudaMemsetAsync(h->spins, 0, (size_t)h->n_b * h->n_slots * h->n_q * h->N * 4 * sizeof(Word),
+                                    h->stream),
+                    "memset");
+  }
+  for (int64_t b = 0; b < h->n_b && !rc; ++b) {
+    const int n_a = (int)std::min<int64_t>(W, h->n_samples - b * W);
+    for (int r = 0; r < h->n_rep && !rc; ++r) {
+      rc = cuda_check(cudaMemcpy2DAsync(stage, (size_t)row, S + ((b * W) * h->n_rep + r) * row,
+                                        (size_t)(h->n_rep * row), (size_t)row, (size_t)n_a, cudaMemcpyHostToDevice,
+                                        h->stream),
+                      "copy spins");
+      if (rc) break;
+      samples_pack_kernel<Word><<<(unsigned)((row + 255) / 256), 256, 0, h->stream>>>(
+          reinterpret_cast<Word *>(h->spins), stage, h->d_walker, b, r, n_a, h->N, h->n_slots, h->n_q, h->n_rep);
+      h->launches++;
+      rc = cuda_check(cudaGetLastError(), "pack spins");
+    }
+  }
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  cudaFree(stage);
+  return rc;
 }
 
 template <typename Word>
