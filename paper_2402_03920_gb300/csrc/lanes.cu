@@ -80,12 +80,6 @@ __global__ void __launch_bounds__(kBlock) lanes_half_sweep_kernel(LanesArgs<Word
   lanes_tile<Word, false, BLUE>(S, colour, (int)j0, n, count_only, colour == 0 && blockIdx.x == 0, smem_raw);
 }
 
-__global__ void zero_u64_kernel(unsigned long long *p, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = 0;
-}
-
 // Overlaps of the configurations at slot s (Appendix E.1): count the sites
 // where the replicas r1 < r2 differ; q = N - 2 * count.  Grid (chunks,
 // n_slots, n_a); accumulates counts into qcnt[a][s][pair].
@@ -211,6 +205,41 @@ __global__ void lanes_init_spins_kernel(Word *spins, int64_t n_a, int64_t N, int
   spins[c] = v;
 }
 
+// int8 +-1 spins [ai][r][w][site] of samples a_lo .. a_lo+n_a-1 from the
+// lattice: a thread per spin.
+template <typename Word>
+__global__ void lanes_extract_kernel(const Word *spins, int8_t *out, int64_t a_lo, int64_t n_a, int64_t N, int n_rep,
+                                     int n_slots, int rpw, int n_groups) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_a * n_rep * n_slots * N) return;
+  const int64_t site = c % N, rw = c / N;
+  const int w = (int)(rw % n_slots);
+  const int64_t ar = rw / n_slots;
+  const int r = (int)(ar % n_rep);
+  const int64_t ai = ar / n_rep;
+  const int g = r / rpw, lane = (r - g * rpw) * n_slots + w;
+  const Word v = spins[((a_lo + ai) * n_groups + g) * N + site];
+  out[c] = ((v >> lane) & 1u) ? -1 : 1;
+}
+
+// The lattice words of samples a0 .. a0+n_a-1 from int8 +-1 spins staged as
+// [ai][r][w][site]: a thread per (sample, word group, site) word.
+template <typename Word>
+__global__ void lanes_pack_kernel(Word *spins, const int8_t *stage, int64_t a0, int64_t n_a, int64_t N, int n_rep,
+                                  int n_slots, int rpw, int n_groups) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_a * n_groups * N) return;
+  const int64_t site = c % N, ag = c / N;
+  const int g = (int)(ag % n_groups);
+  const int64_t ai = ag / n_groups;
+  const int r_lo = g * rpw, r_hi = min(n_rep, r_lo + rpw);
+  Word v = 0;
+  for (int r = r_lo; r < r_hi; ++r)
+    for (int w = 0; w < n_slots; ++w)
+      if (stage[((ai * n_rep + r) * n_slots + w) * N + site] == -1) v |= Word(1) << ((r - r_lo) * n_slots + w);
+  spins[((a0 + ai) * n_groups + g) * N + site] = v;
+}
+
 template <typename Word>
 LanesArgs<Word> make_args(qisg_handle *h) {
   LanesArgs<Word> p;
@@ -296,10 +325,6 @@ int measure_t(qisg_handle *h, int force_to_q) {
   return cuda_check(cudaGetLastError(), "lanes measure");
 }
 
-int lane_of(const qisg_handle *h, int r, int w, int *g) {
-  *g = r / h->rpw;
-  return (r - *g * h->rpw) * h->n_slots + w;
-}
 
 }  // namespace
 
@@ -368,69 +393,59 @@ int lanes_energies_by_slot(qisg_handle *h) {
   return cuda_check(cudaGetLastError(), "lanes energies");
 }
 
+// Samples per staging chunk of the spin transfers (at most 256 MB of int8).
+int64_t spin_chunk(const qisg_handle *h) {
+  const int64_t per_a = (int64_t)h->n_rep * h->n_slots * h->N;
+  return std::max<int64_t>(1, ((int64_t)256 << 20) / per_a);
+}
+
+template <typename Word>
+int get_spins_t(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
+  const int64_t per_a = (int64_t)h->n_rep * h->n_slots * h->N, chunk = std::min(n_a, spin_chunk(h));
+  if (n_a == 0) return QISG_OK;
+  int8_t *stage = nullptr;
+  int rc = cuda_check(cudaMalloc(&stage, (size_t)(chunk * per_a)), "cudaMalloc");
+  for (int64_t a0 = 0; a0 < n_a && !rc; a0 += chunk) {
+    const int64_t na = std::min(chunk, n_a - a0), n = na * per_a;
+    lanes_extract_kernel<Word><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+        reinterpret_cast<const Word *>(h->spins), stage, a_lo + a0, na, h->N, h->n_rep, h->n_slots, h->rpw,
+        h->n_groups);
+    h->launches++;
+    rc = cuda_check(cudaGetLastError(), "unpack spins");
+    if (!rc)
+      rc = cuda_check(cudaMemcpyAsync(S + a0 * per_a, stage, (size_t)n, cudaMemcpyDeviceToHost, h->stream), "copy");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  }
+  if (stage) cudaFree(stage);
+  return rc;
+}
+
+template <typename Word>
+int set_spins_t(qisg_handle *h, const int8_t *S) {
+  const int64_t per_a = (int64_t)h->n_rep * h->n_slots * h->N, chunk = std::min(h->n_samples, spin_chunk(h));
+  int8_t *stage = nullptr;
+  int rc = cuda_check(cudaMalloc(&stage, (size_t)(chunk * per_a)), "cudaMalloc");
+  for (int64_t a0 = 0; a0 < h->n_samples && !rc; a0 += chunk) {
+    const int64_t na = std::min(chunk, h->n_samples - a0), n = na * h->n_groups * h->N;
+    rc = cuda_check(cudaMemcpyAsync(stage, S + a0 * per_a, (size_t)(na * per_a), cudaMemcpyHostToDevice, h->stream),
+                    "copy spins");
+    if (rc) break;
+    lanes_pack_kernel<Word><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+        reinterpret_cast<Word *>(h->spins), stage, a0, na, h->N, h->n_rep, h->n_slots, h->rpw, h->n_groups);
+    h->launches++;
+    rc = cuda_check(cudaGetLastError(), "pack spins");
+  }
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  if (stage) cudaFree(stage);
+  return rc;
+}
+
 int lanes_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
-  const size_t wb = h->W / 8;
-  const size_t per_a = (size_t)h->n_groups * h->N * wb;
-  std::vector<unsigned char> buf(per_a * n_a);
-  int rc = cuda_check(cudaMemcpyAsync(buf.data(), (const unsigned char *)h->spins + a_lo * per_a,
-                                      buf.size(), cudaMemcpyDeviceToHost, h->stream),
-                      "copy spins");
-  if (rc) return rc;
-  rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
-  if (rc) return rc;
-  for (int64_t ai = 0; ai < n_a; ++ai)
-    for (int r = 0; r < h->n_rep; ++r)
-      for (int w = 0; w < h->n_slots; ++w) {
-        int g;
-        const int lane = lane_of(h, r, w, &g);
-        int8_t *dst = S + ((ai * h->n_rep + r) * h->n_slots + w) * h->N;
-        const unsigned char *src = buf.data() + ai * per_a + (size_t)g * h->N * wb;
-        for (int64_t i = 0; i < h->N; ++i) {
-          uint64_t v;
-          if (wb == 8) {
-            std::memcpy(&v, src + i * 8, 8);
-          } else {
-            uint32_t v32;
-            std::memcpy(&v32, src + i * 4, 4);
-            v = v32;
-          }
-          dst[i] = ((v >> lane) & 1u) ? -1 : 1;
-        }
-      }
-  return QISG_OK;
+  return h->W == 64 ? get_spins_t<unsigned long long>(h, a_lo, n_a, S) : get_spins_t<unsigned int>(h, a_lo, n_a, S);
 }
 
 int lanes_set_spins(qisg_handle *h, const int8_t *S) {
-  const size_t wb = h->W / 8;
-  const size_t per_a = (size_t)h->n_groups * h->N * wb;
-  std::vector<unsigned char> buf(per_a * h->n_samples, 0);
-  for (int64_t a = 0; a < h->n_samples; ++a)
-    for (int r = 0; r < h->n_rep; ++r)
-      for (int w = 0; w < h->n_slots; ++w) {
-        int g;
-        const int lane = lane_of(h, r, w, &g);
-        const int8_t *src = S + ((a * h->n_rep + r) * h->n_slots + w) * h->N;
-        unsigned char *dst = buf.data() + a * per_a + (size_t)g * h->N * wb;
-        for (int64_t i = 0; i < h->N; ++i) {
-          if (src[i] != -1) continue;
-          if (wb == 8) {
-            uint64_t v;
-            std::memcpy(&v, dst + i * 8, 8);
-            v |= 1ull << lane;
-            std::memcpy(dst + i * 8, &v, 8);
-          } else {
-            uint32_t v;
-            std::memcpy(&v, dst + i * 4, 4);
-            v |= 1u << lane;
-            std::memcpy(dst + i * 4, &v, 4);
-          }
-        }
-      }
-  int rc = cuda_check(cudaMemcpyAsync(h->spins, buf.data(), buf.size(), cudaMemcpyHostToDevice,
-                                      h->stream),
-                      "copy spins");
-  if (rc) return rc;
-  return cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  return h->W == 64 ? set_spins_t<unsigned long long>(h, S) : set_spins_t<unsigned int>(h, S);
 }
 
 int lanes_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J) {

@@ -321,6 +321,32 @@ __global__ void sites_init_spins_kernel(uint32_t *spins, int64_t n_sys, int n_wo
   spins[c] = v;
 }
 
+// int8 +-1 spins [sys][site] of systems sys0 .. sys0+n_sys-1 from the
+// lattice (site (x, y, tau) is bit tau / M of word x + L y + L^2 (tau mod M)).
+__global__ void sites_extract_kernel(const uint32_t *spins, int8_t *out, int64_t sys0, int64_t n_sys, int plane,
+                                     int M, int n_words, int64_t N) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_sys * N) return;
+  const int64_t sys = c / N, site = c - sys * N;
+  const int tau = (int)(site / plane), i2 = (int)(site - (int64_t)tau * plane);
+  const uint32_t v = spins[(sys0 + sys) * n_words + i2 + plane * (tau % M)];
+  out[c] = ((v >> (tau / M)) & 1u) ? -1 : 1;
+}
+
+// The words of systems sys0 .. sys0+n_sys-1 from int8 +-1 spins staged as
+// [sys][site]: a thread per word, 32 spins along tau.
+__global__ void sites_pack_kernel(uint32_t *spins, const int8_t *stage, int64_t sys0, int64_t n_sys, int plane, int M,
+                                  int n_words, int64_t N) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= n_sys * n_words) return;
+  const int64_t sys = c / n_words;
+  const int ws = (int)(c - sys * n_words), tq = ws / plane, i2 = ws - tq * plane;
+  uint32_t v = 0;
+  for (int j = 0; j < 32; ++j)
+    if (stage[sys * N + i2 + (int64_t)plane * (tq + j * M)] == -1) v |= 1u << j;
+  spins[(sys0 + sys) * n_words + ws] = v;
+}
+
 SitesArgs make_args(qisg_handle *h) {
   SitesArgs p;
   p.spins = reinterpret_cast<uint32_t *>(h->spins);
@@ -513,43 +539,45 @@ int sites_measure(qisg_handle *h, int force_to_q) {
 
 int sites_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
   const int M = h->Lt / 32, plane = h->L * h->L, n_words = plane * M;
-  const size_t per_a = (size_t)h->n_rep * h->n_slots * n_words;
-  std::vector<uint32_t> buf(per_a * n_a);
-  int rc = cuda_check(cudaMemcpyAsync(buf.data(), reinterpret_cast<const uint32_t *>(h->spins) + a_lo * per_a,
-                                      buf.size() * 4, cudaMemcpyDeviceToHost, h->stream),
-                      "copy spins");
-  if (rc) return rc;
-  rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
-  if (rc) return rc;
-  for (size_t sys = 0; sys < (size_t)n_a * h->n_rep * h->n_slots; ++sys) {
-    const uint32_t *src = buf.data() + sys * n_words;
-    int8_t *dst = S + sys * h->N;
-    for (int64_t site = 0; site < h->N; ++site) {
-      const int64_t tau = site / plane, i2 = site % plane;
-      const uint32_t v = src[i2 + plane * (tau % M)];
-      dst[site] = ((v >> (tau / M)) & 1u) ? -1 : 1;
-    }
+  const int64_t per_sys = h->N, n_sys = n_a * h->n_rep * h->n_slots, sys_lo = a_lo * h->n_rep * h->n_slots;
+  if (n_sys == 0) return QISG_OK;
+  const int64_t chunk = std::min<int64_t>(n_sys, std::max<int64_t>(1, ((int64_t)256 << 20) / per_sys));
+  int8_t *stage = nullptr;
+  int rc = cuda_check(cudaMalloc(&stage, (size_t)(chunk * per_sys)), "cudaMalloc");
+  for (int64_t s0 = 0; s0 < n_sys && !rc; s0 += chunk) {
+    const int64_t ns = std::min(chunk, n_sys - s0), n = ns * per_sys;
+    sites_extract_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+        reinterpret_cast<const uint32_t *>(h->spins), stage, sys_lo + s0, ns, plane, M, n_words, h->N);
+    h->launches++;
+    rc = cuda_check(cudaGetLastError(), "unpack spins");
+    if (!rc)
+      rc = cuda_check(cudaMemcpyAsync(S + s0 * per_sys, stage, (size_t)n, cudaMemcpyDeviceToHost, h->stream), "copy");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
   }
-  return QISG_OK;
+  if (stage) cudaFree(stage);
+  return rc;
 }
 
 int sites_set_spins(qisg_handle *h, const int8_t *S) {
   const int M = h->Lt / 32, plane = h->L * h->L, n_words = plane * M;
-  const size_t n_sys = (size_t)h->n_samples * h->n_rep * h->n_slots;
-  std::vector<uint32_t> buf(n_sys * n_words, 0u);
-  for (size_t sys = 0; sys < n_sys; ++sys) {
-    const int8_t *src = S + sys * h->N;
-    uint32_t *dst = buf.data() + sys * n_words;
-    for (int64_t site = 0; site < h->N; ++site)
-      if (src[site] == -1) {
-        const int64_t tau = site / plane, i2 = site % plane;
-        dst[i2 + plane * (tau % M)] |= 1u << (tau / M);
-      }
+  const int64_t per_sys = h->N, n_sys = h->n_samples * h->n_rep * h->n_slots;
+  const int64_t chunk = std::min<int64_t>(n_sys, std::max<int64_t>(1, ((int64_t)256 << 20) / per_sys));
+  int8_t *stage = nullptr;
+  int rc = cuda_check(cudaMalloc(&stage, (size_t)(chunk * per_sys)), "cudaMalloc");
+  for (int64_t s0 = 0; s0 < n_sys && !rc; s0 += chunk) {
+    const int64_t ns = std::min(chunk, n_sys - s0), n = ns * n_words;
+    rc = cuda_check(cudaMemcpyAsync(stage, S + s0 * per_sys, (size_t)(ns * per_sys), cudaMemcpyHostToDevice,
+                                    h->stream),
+                    "copy spins");
+    if (rc) break;
+    sites_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(reinterpret_cast<uint32_t *>(h->spins),
+                                                                          stage, s0, ns, plane, M, n_words, h->N);
+    h->launches++;
+    rc = cuda_check(cudaGetLastError(), "pack spins");
   }
-  int rc = cuda_check(cudaMemcpyAsync(h->spins, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice, h->stream),
-                      "copy spins");
-  if (rc) return rc;
-  return cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  if (stage) cudaFree(stage);
+  return rc;
 }
 
 }  // namespace qisg
