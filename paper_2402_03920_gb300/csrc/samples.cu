@@ -908,11 +908,6 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
   }
 }
 
-__global__ void zero_u64_kernel(unsigned long long *p, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = 0;
-}
 
 // Apply the PT pass to the spins: for pair s = 0 .. n_slots-2 in order,
 // exchange the bits of accepting lanes between slot words s and s+1.
