@@ -341,7 +341,7 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc && layout == QISG_LAYOUT_SAMPLES)
     rc = dalloc(h, &h->d_acc, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8));
   if (!rc && layout == QISG_LAYOUT_SITES) rc = dalloc(h, &h->d_dcum, (size_t)n_slots * 256 * 8);
-  if (!rc && layout == QISG_LAYOUT_SITES) rc = dalloc(h, &h->d_dlut, ((size_t)n_slots << kDaemonLutBits) * 8);
+  if (!rc && layout == QISG_LAYOUT_SITES) rc = dalloc(h, &h->d_dlut, ((size_t)n_slots << kDaemonLutBits) * 9);
   if (rc) {
     qisg_destroy(h);
     return rc;

@@ -464,7 +464,7 @@ struct qisg_handle {
   unsigned long long *d_t = nullptr;  // sweep counter; d_t[1]: its copy for the PT pass (fused mode)
   void *d_acc = nullptr;            // SAMPLES: PT lane masks of the last pass, Word [b][r][s]
   unsigned long long *d_dcum = nullptr;   // SITES: cumulative tables [n_slots][256]
-  uint2 *d_dlut = nullptr;                // SITES: prefix index [n_slots][2^kDaemonLutBits]
+  uint2 *d_dlut = nullptr;                // SITES: prefix index [n_slots][2^kDaemonLutBits], then the spans (bytes)
   int *d_err = nullptr;
   size_t device_bytes = 0;
 

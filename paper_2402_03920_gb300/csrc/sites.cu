@@ -25,9 +25,11 @@
 // With span <= 1 the entry holds the upper half of the one cut point and
 // n* = n_min + [upper half of the word > it]; with span >= 2 the upper
 // halves of the span cut points are compared one by one.  Only when an
-// upper half equals a cut point's does the lower half matter: then the
-// whole daemon word is redone with the full 64-bit words (the xoroshiro
-// step is only computed there).
+// upper half equals a cut point's does the lower half matter (a running
+// product of the XORs of the upper halves then becomes 0): the whole daemon
+// word is redone with the full 64-bit words, and the xoroshiro step is only
+// computed there.  The bytes are assembled by multiply-adds with run-time
+// factors, which keeps that work off the logic pipe.
 //
 // Device arrays (systems walker-major; PT exchanges slot labels only):
 //   spins  u32 [a][r][w][L^2 M]       bit = 1 <=> spin -1
@@ -35,8 +37,9 @@
 //   U      u64 [a][r][w][2]            unsatisfied spatial / tau bonds of walker w
 //   cum    u64 [n_slots][256]          cumulative(0..254) of Sec. 2.1.1; [255] = 2^64-1
 //   lut    uint2 [n_slots][2^kDaemonLutBits]
-//                                      {n_min | span << 8, upper half of cumulative(n_min)
-//                                       when span = 1, else 2^32 - 1}
+//                                      {n_min, | 2^31 when span >= 2; upper half of
+//                                       cumulative(n_min) when span = 1, else 2^32 - 1}
+//   span   uint8 [n_slots][2^kDaemonLutBits] (after lut)   span of each prefix
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -54,9 +57,11 @@ struct SitesArgs {
   const int32_t *walker;
   const unsigned long long *cum;
   const uint2 *lut;
+  const uint8_t *span;
   unsigned long long *U;
   const unsigned long long *d_t;
   uint2 key;
+  uint32_t m8, m16, m24;       // 2^8, 2^16, 2^24 at run time (byte assembly by multiply-adds)
   FastDiv half_plane_div, half_L_div;
   int L, M, plane, half_plane, n_words, half_words;
   int n_slots, n_rep;
@@ -93,30 +98,36 @@ __device__ __forceinline__ uint4 philox_wide(uint4 c, uint2 k) {
 // Exact n* of 64-bit word i of a daemon word (the rare path): the lower
 // half from the xoroshiro step of the Philox output x, then the count of
 // the cut points at or below the word among the prefix's candidates.
-static __device__ __noinline__ uint32_t nstar_exact(uint4 x, int i, const uint2 *lut,
+static __device__ __noinline__ uint32_t nstar_exact(uint4 x, int i, const uint2 *lut, const uint8_t *span,
                                                     const unsigned long long *cum) {
   const uint4 lo = xoroshiro_step(x);
   const uint32_t hi = pick4(x, i), l = pick4(lo, i);
   const unsigned long long R = ((unsigned long long)hi << 32) | l;
-  const uint32_t e = lut[hi >> (32 - kDaemonLutBits)].x;
-  uint32_t n = e & 0xFFu;
-  const uint32_t end = n + (e >> 8);
+  const uint32_t h = hi >> (32 - kDaemonLutBits);
+  uint32_t n = lut[h].x & 0xFFu;
+  const uint32_t end = n + span[h];
   for (uint32_t q = n; q < end; ++q) n += (R >= cum[q]) ? 1u : 0u;
   return n;
 }
 
-// n* of a 64-bit word from its upper half hi, or *tie when the upper
-// halves of the word and a candidate cut point are equal.
-__device__ __forceinline__ uint32_t nstar_hi(uint32_t hi, const uint2 *lut, const uint32_t *cut_hi, bool *tie) {
-  const uint2 e = lut[hi >> (32 - kDaemonLutBits)];
-  uint32_t n = (e.x & 0xFFu) + (hi > e.y ? 1u : 0u);
-  *tie |= hi == e.y;
-  if (e.x >= 0x200u) {   // span >= 2 (e.y is all ones there)
-    const uint32_t n0 = e.x & 0xFFu, end = n0 + (e.x >> 8);
+// n* of a 64-bit word from its upper half hi (entry e: e.x = n_min, bit 31
+// set when the cell holds two or more cut points; e.y = upper half of the
+// one cut point, else all ones).  *prod collects hi ^ (cut's upper half):
+// it becomes 0 when they tie (the lower halves then decide; a zero product
+// without a tie only sends the word to the exact path).
+__device__ __forceinline__ uint32_t nstar_hi(uint32_t hi, const uint2 *lut, const uint32_t *cut_hi,
+                                             const uint8_t *span, uint32_t *prod) {
+  const uint32_t h = hi >> (32 - kDaemonLutBits);
+  const uint2 e = lut[h];
+  uint32_t n = e.x + (hi > e.y ? 1u : 0u);
+  *prod *= hi ^ e.y;
+  if ((int)e.x < 0) {   // two or more cut points: compare their upper halves
+    const uint32_t n0 = e.x & 0xFFu, end = n0 + span[h];
+    n = n0;
     for (uint32_t q = n0; q < end; ++q) {
       const uint32_t c = cut_hi[q];
       n += hi > c ? 1u : 0u;
-      *tie |= hi == c;
+      *prod *= hi ^ c;
     }
   }
   return n;
@@ -126,15 +137,16 @@ __device__ __forceinline__ uint32_t nstar_hi(uint32_t hi, const uint2 *lut, cons
 // (a, r, slot s) in sweep t: byte i is n* of the 64-bit word whose upper
 // half is Philox output i.
 __device__ __forceinline__ uint32_t daemon_word(uint32_t ws, uint32_t t, uint32_t c2, uint32_t c3, uint2 key,
-                                                const uint2 *lut, const uint32_t *cut_hi,
-                                                const unsigned long long *cum) {
+                                                const uint2 *lut, const uint32_t *cut_hi, const uint8_t *span,
+                                                const unsigned long long *cum, uint32_t m8, uint32_t m16,
+                                                uint32_t m24) {
   const uint4 x = philox_wide(make_uint4(ws, t, c2, c3), key);
-  bool tie = false;
-  const uint32_t b = nstar_hi(x.x, lut, cut_hi, &tie) | (nstar_hi(x.y, lut, cut_hi, &tie) << 8) |
-                     (nstar_hi(x.z, lut, cut_hi, &tie) << 16) | (nstar_hi(x.w, lut, cut_hi, &tie) << 24);
-  if (!tie) return b;
-  return nstar_exact(x, 0, lut, cum) | (nstar_exact(x, 1, lut, cum) << 8) | (nstar_exact(x, 2, lut, cum) << 16) |
-         (nstar_exact(x, 3, lut, cum) << 24);
+  uint32_t prod = 1;
+  const uint32_t b = nstar_hi(x.x, lut, cut_hi, span, &prod) + nstar_hi(x.y, lut, cut_hi, span, &prod) * m8 +
+                     nstar_hi(x.z, lut, cut_hi, span, &prod) * m16 + nstar_hi(x.w, lut, cut_hi, span, &prod) * m24;
+  if (prod != 0) return b;
+  return nstar_exact(x, 0, lut, span, cum) | (nstar_exact(x, 1, lut, span, cum) << 8) |
+         (nstar_exact(x, 2, lut, span, cum) << 16) | (nstar_exact(x, 3, lut, span, cum) << 24);
 }
 
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
@@ -151,6 +163,7 @@ template <bool BLUE>
 __global__ void __launch_bounds__(kBlock) sites_half_sweep_kernel(SitesArgs p, int count_only) {
   __shared__ unsigned long long cum_s[256];
   __shared__ uint32_t cut_hi_s[256];
+  __shared__ __align__(16) uint8_t span_s[1 << kDaemonLutBits];
   extern __shared__ __align__(16) uint2 lut_s[];   // [2^kDaemonLutBits]
   __shared__ unsigned long long red_s[2][kBlock / 32];
   const int64_t sys = blockIdx.x / p.blocks_per_sys;
@@ -177,6 +190,9 @@ __global__ void __launch_bounds__(kBlock) sites_half_sweep_kernel(SitesArgs p, i
     const uint4 *lg = reinterpret_cast<const uint4 *>(p.lut + ((size_t)s << kDaemonLutBits));
     uint4 *ls = reinterpret_cast<uint4 *>(lut_s);
     for (int i = threadIdx.x; i < (1 << kDaemonLutBits) / 2; i += kBlock) ls[i] = __ldg(lg + i);
+    const uint4 *sg = reinterpret_cast<const uint4 *>(p.span + ((size_t)s << kDaemonLutBits));
+    uint4 *ss = reinterpret_cast<uint4 *>(span_s);
+    for (int i = threadIdx.x; i < (1 << kDaemonLutBits) / 16; i += kBlock) ss[i] = __ldg(sg + i);
   }
   __syncthreads();
   uint32_t *S = p.spins + sys * p.n_words;
@@ -233,7 +249,8 @@ __global__ void __launch_bounds__(kBlock) sites_half_sweep_kernel(SitesArgs p, i
       uint32_t b4 = 0, b8 = 0, b12 = 0;
 #pragma unroll 1
       for (uint32_t which = 0; which < 3; ++which) {
-        const uint32_t dw = daemon_word((uint32_t)ws, t, c2, c3 | (which << 24), p.key, lut_s, cut_hi_s, cum_s);
+        const uint32_t dw = daemon_word((uint32_t)ws, t, c2, c3 | (which << 24), p.key, lut_s, cut_hi_s, span_s, cum_s,
+                                        p.m8, p.m16, p.m24);
         b4 = b8;
         b8 = b12;
         b12 = dw;
@@ -354,9 +371,13 @@ SitesArgs make_args(qisg_handle *h) {
   p.walker = h->d_walker;
   p.cum = h->d_dcum;
   p.lut = h->d_dlut;
+  p.span = reinterpret_cast<const uint8_t *>(h->d_dlut + ((size_t)h->n_slots << kDaemonLutBits));
   p.U = h->d_U;
   p.d_t = h->d_t;
   p.key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  p.m8 = 1u << 8;
+  p.m16 = 1u << 16;
+  p.m24 = 1u << 24;
   p.L = h->L;
   p.M = h->Lt / 32;
   p.plane = h->L * h->L;
@@ -458,6 +479,7 @@ int sites_build_tables(qisg_handle *h) {
   const int n = h->n_slots, nl = 1 << kDaemonLutBits;
   std::vector<unsigned long long> cum((size_t)n * 256);
   std::vector<uint2> lut((size_t)n * nl);
+  std::vector<uint8_t> span((size_t)n * nl);
   std::vector<uint16_t> l16((size_t)nl);
   std::vector<uint32_t> chi((size_t)nl);
   for (int s = 0; s < n; ++s) {
@@ -466,13 +488,21 @@ int sites_build_tables(qisg_handle *h) {
     c[255] = ~0ull;
     for (int i = 0; i < 256; ++i) cum[(size_t)s * 256 + i] = c[i];
     daemon_lut(c, kDaemonLutBits, l16.data(), chi.data());
-    for (int i = 0; i < nl; ++i) lut[(size_t)s * nl + i] = make_uint2(l16[(size_t)i], chi[(size_t)i]);
+    for (int i = 0; i < nl; ++i) {
+      const uint32_t nmin = l16[(size_t)i] & 0xFFu, sp = l16[(size_t)i] >> 8;
+      lut[(size_t)s * nl + i] = make_uint2(nmin | (sp >= 2 ? 0x80000000u : 0u), chi[(size_t)i]);
+      span[(size_t)s * nl + i] = (uint8_t)sp;
+    }
   }
   int rc = cuda_check(cudaMemcpyAsync(h->d_dcum, cum.data(), cum.size() * 8, cudaMemcpyHostToDevice, h->stream),
                       "copy cumulative tables");
   if (!rc)
     rc = cuda_check(cudaMemcpyAsync(h->d_dlut, lut.data(), lut.size() * 8, cudaMemcpyHostToDevice, h->stream),
                     "copy prefix index");
+  if (!rc)
+    rc = cuda_check(cudaMemcpyAsync(h->d_dlut + lut.size(), span.data(), span.size(), cudaMemcpyHostToDevice,
+                                    h->stream),
+                    "copy prefix spans");
   // the host vectors must outlive the copies
   if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
   return rc;
