@@ -113,7 +113,10 @@ __device__ void batch_tile(const InstDev &I, int colour, int j0, int n, unsigned
   S.rpw = I.rpw;
   S.n_groups = I.n_groups;
   S.tau_ap = 0;   // batched instances are periodic along tau
-  lanes_tile<unsigned long long, true, BLUE>(S, colour, j0, n, 0, colour == 0 && j0 == 0, smem);
+  if (I.n_rep == 4)   // the common case (every uneven-batch and serving instance): loops unrolled
+    lanes_tile<unsigned long long, true, BLUE, 4>(S, colour, j0, n, 0, colour == 0 && j0 == 0, smem);
+  else
+    lanes_tile<unsigned long long, true, BLUE>(S, colour, j0, n, 0, colour == 0 && j0 == 0, smem);
 }
 
 __device__ __forceinline__ bool live(const InstDev &I) { return I.active && __ldcg(&I.remaining) != 0; }

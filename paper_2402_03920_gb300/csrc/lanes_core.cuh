@@ -62,13 +62,15 @@ __device__ __forceinline__ Word ld_word(const Word *p) {
 }
 
 // Sites [j0, j0 + n) of one colour; every thread of the block must call it.
+// NREP > 0: the sample has exactly NREP replicas (a compile-time count lets
+// the per-slot replica loop unroll without bound checks).
 // CG: read mutable state through L2 only (inside a persistent kernel).
 // zero_U: clear this sample's bond counters first (red pass, one tile).
-template <typename Word, bool CG, bool BLUE>
+template <typename Word, bool CG, bool BLUE, int NREP = 0>
 __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n, int count_only, bool zero_U,
                            unsigned char *smem) {
   constexpr int W = (int)sizeof(Word) * 8;
-  const int n_slots = S.n_slots, n_rep = S.n_rep, plane = S.plane, hp = S.half_plane;
+  const int n_slots = S.n_slots, n_rep = NREP > 0 ? NREP : S.n_rep, plane = S.plane, hp = S.half_plane;
   uint32_t *T5_s = reinterpret_cast<uint32_t *>(smem);   // [slot][code], code = u_s + 8 u_t
   int *wa_s = reinterpret_cast<int *>(T5_s + n_slots * 32);
   int *acc_s = wa_s + n_rep * n_slots;                 // [group][lane]

@@ -26,16 +26,17 @@ def _oracle_instance(L, Lt, ladder, n_rep, seed, sweeps):
 
 
 def test_uneven_batch_bit_exact(qisg):
-    """Six instances of different L, L_tau, ladder length and Gamma in one
-    batch: every one matches its own oracle run after 1, 4 and 25 sweeps."""
+    """Six instances of different L, L_tau, ladder length, Gamma and replica
+    count (the 4-replica tile and the general one) in one batch: every one
+    matches its own oracle run after 1, 4 and 25 sweeps."""
     rng = np.random.default_rng(3)
     specs = []
-    for i in range(6):
+    for i, n_rep in enumerate((4, 1, 3, 2, 4, 3)):
         L = int(rng.choice([2, 4, 6, 8]))
         Lt = int(rng.choice([4, 8, 16]))
         n_slots = int(rng.integers(3, 33))
         gamma = float(rng.uniform(0.8, 1.2))
-        specs.append((L, Lt, qisg.ladder_linear(0.2, 0.5, n_slots, gamma), 4, 100 + i))
+        specs.append((L, Lt, qisg.ladder_linear(0.2, 0.5, n_slots, gamma), n_rep, 100 + i))
     with qisg.Batch(8, 64 << 20) as b:
         slots = [b.admit(L, Lt, lad, nr, seed) for (L, Lt, lad, nr, seed) in specs]
         done = 0
