@@ -50,7 +50,7 @@ __device__ __forceinline__ uint32_t bit_at(Word w, int lane) {
 // block x is the tile of colour sites [x * tile_sites, (x+1) * tile_sites),
 // one thread per site (lanes_core.cuh).  Block 0 of the red pass clears the
 // sample's bond counters, which the blue pass fills.
-template <typename Word, bool BLUE, int NREP>
+template <typename Word, bool BLUE, int NREP, int NGC>
 __global__ void __launch_bounds__(kBlock) lanes_half_sweep_kernel(LanesArgs<Word> p, int colour,
                                                                   int count_only, int64_t a0, int tile_sites) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kBlock) lanes_half_sweep_kernel(LanesArgs<Word
   S.tau_ap = p.tau_ap;
   const int64_t j0 = (int64_t)blockIdx.x * tile_sites;
   const int n = (int)(p.half_N - j0 < tile_sites ? p.half_N - j0 : tile_sites);
-  lanes_tile<Word, false, BLUE, NREP>(S, colour, (int)j0, n, count_only, colour == 0 && blockIdx.x == 0, smem_raw);
+  lanes_tile<Word, false, BLUE, NREP, NGC>(S, colour, (int)j0, n, count_only, colour == 0 && blockIdx.x == 0, smem_raw);
 }
 
 // Overlaps of the configurations at slot s (Appendix E.1): count the sites
@@ -281,26 +281,35 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   if (smem > 227 * 1024) return fail(QISG_EINVAL, "LANES plane tables exceed shared memory");
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, false, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, true, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, false, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, true, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, false, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(lanes_half_sweep_kernel<Word, true, 4, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr_set = true;
   }
   for (int64_t a0 = 0; a0 < h->n_samples; a0 += (h->per_sample_launch ? 1 : 65535)) {
     const int64_t na = h->per_sample_launch ? 1 : std::min<int64_t>(65535, h->n_samples - a0);
     const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
     const dim3 grid((unsigned)blocks, (unsigned)na);
-    if (h->n_rep == 4) {   // loops unrolled for the common replica count
+    // compile-time replica count (loops unrolled) and word-group count (fewer
+    // registers) for the common cases
+    if (h->n_rep == 4 && h->n_groups == 1) {
       if (colour == 1)
-        lanes_half_sweep_kernel<Word, true, 4><<<grid, kBlock, smem, h->stream>>>(p, 1, count_only, a0, tile_sites);
+        lanes_half_sweep_kernel<Word, true, 4, 1><<<grid, kBlock, smem, h->stream>>>(p, 1, count_only, a0, tile_sites);
       else
-        lanes_half_sweep_kernel<Word, false, 4><<<grid, kBlock, smem, h->stream>>>(p, 0, count_only, a0, tile_sites);
+        lanes_half_sweep_kernel<Word, false, 4, 1><<<grid, kBlock, smem, h->stream>>>(p, 0, count_only, a0, tile_sites);
+    } else if (h->n_rep == 4) {
+      if (colour == 1)
+        lanes_half_sweep_kernel<Word, true, 4, 0><<<grid, kBlock, smem, h->stream>>>(p, 1, count_only, a0, tile_sites);
+      else
+        lanes_half_sweep_kernel<Word, false, 4, 0><<<grid, kBlock, smem, h->stream>>>(p, 0, count_only, a0, tile_sites);
     } else {
       if (colour == 1)
-        lanes_half_sweep_kernel<Word, true, 0><<<grid, kBlock, smem, h->stream>>>(p, 1, count_only, a0, tile_sites);
+        lanes_half_sweep_kernel<Word, true, 0, 0><<<grid, kBlock, smem, h->stream>>>(p, 1, count_only, a0, tile_sites);
       else
-        lanes_half_sweep_kernel<Word, false, 0><<<grid, kBlock, smem, h->stream>>>(p, 0, count_only, a0, tile_sites);
+        lanes_half_sweep_kernel<Word, false, 0, 0><<<grid, kBlock, smem, h->stream>>>(p, 0, count_only, a0, tile_sites);
     }
     prof_end(h, QISG_KERNEL_SWEEP, tok);
     h->launches++;

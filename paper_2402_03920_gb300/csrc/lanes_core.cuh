@@ -63,10 +63,11 @@ __device__ __forceinline__ Word ld_word(const Word *p) {
 
 // Sites [j0, j0 + n) of one colour; every thread of the block must call it.
 // NREP > 0: the sample has exactly NREP replicas (a compile-time count lets
-// the per-slot replica loop unroll without bound checks).
+// the per-slot replica loop unroll without bound checks).  NGC > 0: exactly
+// NGC word groups per site (registers for those only).
 // CG: read mutable state through L2 only (inside a persistent kernel).
 // zero_U: clear this sample's bond counters first (red pass, one tile).
-template <typename Word, bool CG, bool BLUE, int NREP = 0>
+template <typename Word, bool CG, bool BLUE, int NREP = 0, int NGC = 0>
 __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n, int count_only, bool zero_U,
                            unsigned char *smem) {
   constexpr int W = (int)sizeof(Word) * 8;
@@ -105,13 +106,14 @@ __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n
     for (int i = threadIdx.x; i < 2 * n_rep * n_slots; i += blockDim.x) S.U[i] = 0;
   __syncthreads();
 
-  const int NG = S.n_groups;   // 1 or 2
+  constexpr int MG = NGC > 0 ? NGC : kLanesMaxGroups;   // word groups held in registers
+  const int NG = NGC > 0 ? NGC : S.n_groups;             // 1 or 2
   const uint32_t Lt = (uint32_t)S.Lt;
-  VCount<Word, kLanesKs> cs[kLanesMaxGroups];
-  VCount<Word, kLanesKt> ct[kLanesMaxGroups];
+  VCount<Word, kLanesKs> cs[MG];
+  VCount<Word, kLanesKt> ct[MG];
   if (BLUE)
 #pragma unroll
-    for (int g = 0; g < kLanesMaxGroups; ++g) {
+    for (int g = 0; g < MG; ++g) {
       cs[g].zero();
       ct[g].zero();
     }
@@ -135,10 +137,9 @@ __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n
       const Word Jxp = ones_if<Word>(jh & 1u), Jyp = ones_if<Word>(jh & 2u);
       const Word Jxm = ones_if<Word>(Js[nv.x >> 16] & 1u);
       const Word Jym = ones_if<Word>(Js[nv.y >> 16] & 2u);
-      Word sc[kLanesMaxGroups], P0[kLanesMaxGroups], P1[kLanesMaxGroups], P2[kLanesMaxGroups],
-          Q0[kLanesMaxGroups], Q1[kLanesMaxGroups], fw[kLanesMaxGroups];
+      Word sc[MG], P0[MG], P1[MG], P2[MG], Q0[MG], Q1[MG], fw[MG];
 #pragma unroll
-      for (int g = 0; g < kLanesMaxGroups; ++g) {
+      for (int g = 0; g < MG; ++g) {
         sc[g] = P0[g] = P1[g] = P2[g] = Q0[g] = Q1[g] = fw[g] = 0;
         if (g < NG) {
           const Word *w = S.spins + (size_t)g * S.N;
@@ -164,7 +165,7 @@ __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n
         // thread holds lanes l .. l+3 of group g
         uint32_t *cw = code_s + threadIdx.x;
 #pragma unroll
-        for (int g = 0; g < kLanesMaxGroups; ++g)
+        for (int g = 0; g < MG; ++g)
           if (g < NG) {
 #pragma unroll
             for (int h = 0; h < W / 32; ++h) {
@@ -188,19 +189,19 @@ __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n
             for (int jj = 0; jj < 4; ++jj) {
               const int r = 4 * q + jj;
               if (r >= n_rep) break;
-              const int g = r >= S.rpw ? 1 : 0;   // n_groups <= 2
+              const int g = (MG > 1 && r >= S.rpw) ? 1 : 0;   // n_groups <= 2
               const int lane = (r - g * S.rpw) * n_slots + wa_s[r * n_slots + s];
               const uint32_t word = cw[(g * 16 + (lane >> 2)) * kLanesMaxThreads];
               const uint32_t thr = Trow[(word >> (8 * (lane & 3))) & 31u];
               if (thr == 0xFFFFFFFFu || pick4(R4, jj) < thr) {
-                if (g) fw[1] |= Word(1) << lane;
+                if (MG > 1 && g) fw[MG - 1] |= Word(1) << lane;
                 else fw[0] |= Word(1) << lane;
               }
             }
           }
         }
 #pragma unroll
-        for (int g = 0; g < kLanesMaxGroups; ++g)
+        for (int g = 0; g < MG; ++g)
           if (g < NG && fw[g]) {
             Word *w = S.spins + (size_t)g * S.N + site;
             *w = sc[g] ^ fw[g];
@@ -208,7 +209,7 @@ __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n
       }
       if (BLUE) {
 #pragma unroll
-        for (int g = 0; g < kLanesMaxGroups; ++g)
+        for (int g = 0; g < MG; ++g)
           if (g < NG) {
             // unsatisfied counts after the flip: u -> 4 - u (spatial), 2 - u (tau)
             const Word f = fw[g];
@@ -223,7 +224,7 @@ __device__ void lanes_tile(const LanesSample<Word> &S, int colour, int j0, int n
   }
   if (BLUE) {
 #pragma unroll
-    for (int g = 0; g < kLanesMaxGroups; ++g)
+    for (int g = 0; g < MG; ++g)
       if (g < NG) {   // uniform across the block
         flush_counter<Word, kLanesKs, 1>(cs[g], acc_s + g * W);
         flush_counter<Word, kLanesKt, 1>(ct[g], acc_t + g * W);
