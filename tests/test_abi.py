@@ -63,3 +63,28 @@ def test_host_only_entry_points_without_gpu():
     rc = lib.qisg_create(ctypes.byref(h), 8, 31, sl.ctypes.data_as(ctypes.c_void_p), 16, 4, 1, 1, None)
     assert rc == -1
     assert lib.qisg_strerror(-4) == b"bounded device wait expired"
+
+
+def test_daemon_tables_host_without_gpu():
+    """The daemon rule's host tables (fixed point, 126 fractional bits) equal
+    the oracle's (decimal arithmetic) bit for bit, and a SITES handle with
+    unequal couplings or an unfit L_tau is refused before any device work."""
+    import numpy as np
+    from paper_2402_03920_gb300 import qisg
+    import oracle
+    for k in (0.0, 0.05, 0.2, 0.29, 0.4137, 0.5, 1.7, 16.0):
+        cum, _ = qisg.daemon_tables(k, 12)
+        assert np.array_equal(cum, oracle.daemon_cumulative(k)), k
+    lib = qisg.load()
+    h = ctypes.c_void_p()
+    opts = qisg.Opts()
+    lib.qisg_opts_default(ctypes.byref(opts))
+    opts.layout = qisg.QISG_LAYOUT_SITES
+    unequal = np.ascontiguousarray(qisg.ladder_linear(0.2, 0.5, 4, 1.0))
+    equal = np.ascontiguousarray(qisg.ladder_equal(0.2, 0.5, 4))
+    rc = lib.qisg_create(ctypes.byref(h), 4, 64, unequal.ctypes.data_as(ctypes.c_void_p), 4, 2, 1, 1,
+                         ctypes.byref(opts))
+    assert rc == -1
+    rc = lib.qisg_create(ctypes.byref(h), 4, 96, equal.ctypes.data_as(ctypes.c_void_p), 4, 2, 1, 1,
+                         ctypes.byref(opts))
+    assert rc == -1
