@@ -7,8 +7,9 @@ oracle or the CUDA library.
   and B = sum_tau S S over all 2^N configurations of an L x L x L_tau prism
   (periodic), weight exp(k A + k_tau B) -- Eq. (2)-(3) with a separate
   imaginary-time coupling.
-* ``transfer_AB``: the same averages for a periodic prism of any L_tau by
-  the transfer matrix along tau (L <= 3), checked against ``enumerate_AB``.
+* ``transfer_AB``: the same averages for a prism of any L_tau, periodic or
+  antiperiodic, by the transfer matrix along tau (L <= 3), checked against
+  ``enumerate_AB``.
 * ``chain_B``: closed form for k = 0, where every spatial site carries an
   independent Ising ring of L_tau spins with coupling k_tau, periodic or
   antiperiodic (one bond of opposite sign).
@@ -81,32 +82,36 @@ def chain_B(L: int, Ltau: int, ktau: float, tau_ap: bool = False) -> float:
     return float(L * L * num / den)
 
 
-def transfer_AB(J: np.ndarray, L: int, Ltau: int, k: float, ktau: float):
-    """Exact <A>, <B> of a periodic L x L x L_tau prism by the transfer matrix
-    along tau (L <= 3): with D = diag(exp(k A_layer)) and
-    C[s, s'] = exp(k_tau s.s'), the slice-to-slice matrix is
-    T = D^1/2 C D^1/2 and Z = Tr T^L_tau, so
-    <A> = L_tau Tr(diag(A_layer) T^L_tau) / Z and
-    <B> = L_tau Tr(D^1/2 (C o G) D^1/2 T^(L_tau - 1)) / Z with G[s, s'] = s.s'."""
+def transfer_AB(J: np.ndarray, L: int, Ltau: int, k: float, ktau: float, tau_ap: bool = False):
+    """Exact <A>, <B> of an L x L x L_tau prism by the transfer matrix along
+    tau (L <= 3): with D = diag(exp(k A_layer)) and C[s, s'] = exp(k_tau
+    s.s'), the slice-to-slice matrix is T = D^1/2 C D^1/2 and Z = Tr T^L_tau;
+    antiperiodic (tau_ap): the bond L_tau-1 -> 0 has the opposite sign, its
+    matrix T~ = D^1/2 C~ D^1/2 with C~[s, s'] = exp(-k_tau s.s'), and
+    Z = Tr T^(L_tau - 1) T~.  Flipping every spin of one slice moves that
+    twist and leaves A_layer unchanged, so every slice and every tau bond
+    contributes alike:
+    <A> = L_tau Tr(diag(A_layer) P) / Z with P the closed product, and
+    <B> = L_tau Tr(D^1/2 (C o G) D^1/2 T^(L_tau - 2) T~) / Z (T~ = T when
+    periodic), G[s, s'] = s.s'."""
     n = L * L
-    assert n <= 9
+    assert n <= 9 and Ltau >= 2
     S = _all_configs(n).astype(np.float64)                      # [2^n][n]
     A_layer, _ = AB_of_configs(_all_configs(n), J, L, 1)
     A_layer = A_layer.astype(np.float64)
     G = S @ S.T
-    C = np.exp(ktau * G)
     d = np.exp(0.5 * k * (A_layer - A_layer.max()))
-    T = d[:, None] * C * d[None, :]
-    lam, V = np.linalg.eigh(T)
-    top = lam.max()
-    lam_n = lam / top
 
-    def power(m):
-        return (V * lam_n ** m) @ V.T
+    def mat(sign):
+        return d[:, None] * np.exp(sign * ktau * G) * d[None, :]
 
-    Tn = power(Ltau)
-    Z = np.trace(Tn)
-    mA = Ltau * np.trace(A_layer[:, None] * Tn) / Z
-    TB = (d[:, None] * (C * G) * d[None, :]) / top
-    mB = Ltau * np.trace(TB @ power(Ltau - 1)) / Z
+    T = mat(1.0)
+    Tw = mat(-1.0) if tau_ap else T
+    top = np.linalg.eigvalsh(T).max()
+    Tn, Twn = T / top, Tw / top
+    P = np.linalg.matrix_power(Tn, Ltau - 1) @ Twn
+    Z = np.trace(P)
+    mA = Ltau * np.trace(A_layer[:, None] * P) / Z
+    TB = (d[:, None] * (np.exp(ktau * G) * G) * d[None, :]) / top
+    mB = Ltau * np.trace(TB @ np.linalg.matrix_power(Tn, Ltau - 2) @ Twn) / Z
     return float(mA), float(mB)

@@ -282,9 +282,38 @@ def test_transfer_matrix_matches_enumeration():
     for L, Lt in ((2, 3), (2, 4)):
         J = (1 - 2 * rng.integers(0, 2, size=(L * L, 2))).astype(np.int8)
         for k, kt in ((0.3, 0.3), (0.2, 0.8)):
-            a, b, _, _ = exact.enumerate_AB(J, L, Lt, k, kt)
-            ta, tb = exact.transfer_AB(J, L, Lt, k, kt)
-            assert abs(a - ta) < 1e-9 and abs(b - tb) < 1e-9
+            for ap in (False, True):
+                a, b, _, _ = exact.enumerate_AB(J, L, Lt, k, kt, ap)
+                ta, tb = exact.transfer_AB(J, L, Lt, k, kt, ap)
+                assert abs(a - ta) < 1e-9 and abs(b - tb) < 1e-9, (L, Lt, k, kt, ap)
+
+
+def test_daemon_chain_antiperiodic_matches_transfer_matrix_L2():
+    """L=2, L_tau=64, antiperiodic along tau, k in {0.6, 0.8}: MC <A>, <B>
+    match the antiperiodic transfer-matrix values within 4 sigma, and <B> at
+    k = 0.8 excludes the periodic value (about 8 apart at this size)."""
+    L, Lt = 2, 64
+    k = np.array([0.6, 0.8])
+    st = oracle.new_state(L, Lt, k, k.copy(), n_rep=8, seed=2, daemon=True, tau_ap=True)
+    J = st.J[0]
+    assert _spatially_free_sites(J) == []
+    oracle.run(st, 300)
+    means_A, means_B = [], []
+    for _ in range(30):
+        sA0, sB0, m0 = st.sumA.copy(), st.sumB.copy(), st.n_meas
+        oracle.run(st, 40, pt_every=1, measure_every=1)
+        dm = st.n_meas - m0
+        means_A.append((st.sumA - sA0).sum(axis=(0, 1)) / (dm * st.n_rep))
+        means_B.append((st.sumB - sB0).sum(axis=(0, 1)) / (dm * st.n_rep))
+    mA, mB = np.array(means_A), np.array(means_B)
+    eA = mA.std(0, ddof=1) / math.sqrt(len(mA))
+    eB = mB.std(0, ddof=1) / math.sqrt(len(mB))
+    for s in range(2):
+        xA, xB = exact.transfer_AB(J, L, Lt, k[s], k[s], True)
+        assert abs(mA.mean(0)[s] - xA) < 4 * eA[s] + 1e-9, (s, mA.mean(0)[s], xA, eA[s])
+        assert abs(mB.mean(0)[s] - xB) < 4 * eB[s] + 1e-9, (s, mB.mean(0)[s], xB, eB[s])
+    _, pB = exact.transfer_AB(J, L, Lt, k[1], k[1], False)
+    assert abs(mB.mean(0)[1] - pB) > 20 * eB[1]
 
 
 def test_one_system_sweep_is_the_chain_sweep():
