@@ -498,3 +498,24 @@ def test_k_tau_zero_antiperiodic_same_spins():
     assert np.array_equal(st.S, ap.S) and np.array_equal(st.walker_at, ap.walker_at)
     assert np.array_equal(st.A, ap.A)
     assert not np.array_equal(st.B, ap.B)
+
+
+@pytest.mark.parametrize("tau_ap", [False, True])
+def test_long_tau_chain_matches_transfer_matrix(tau_ap):
+    """L=2, L_tau=32 with separate couplings (k, k_tau) of a Gamma = 0.9
+    ladder and PT: MC <A>, <B> per slot match the transfer-matrix values of
+    the same boundary within 4 sigma, and at the first slot <B> excludes the
+    other boundary's value (about 5 apart at this size)."""
+    L, Lt = 2, 32
+    k, kt = oracle.ladder_linear(0.3, 0.6, 2, 0.9)
+    st = oracle.new_state(L, Lt, k, kt, n_rep=8, seed=2, tau_ap=tau_ap)
+    J = st.J[0]
+    assert _spatially_free_sites(J) == []
+    oracle.run(st, 300)
+    mA, eA, mB, eB = _mc_means(st, 30, 40)
+    for s in range(2):
+        xA, xB = exact.transfer_AB(J, L, Lt, k[s], kt[s], tau_ap)
+        assert abs(mA[s] - xA) < 4 * eA[s] + 1e-9, (s, mA[s], xA, eA[s])
+        assert abs(mB[s] - xB) < 4 * eB[s] + 1e-9, (s, mB[s], xB, eB[s])
+    _, oB = exact.transfer_AB(J, L, Lt, k[0], kt[0], not tau_ap)
+    assert abs(mB[0] - oB) > 8 * eB[0]
