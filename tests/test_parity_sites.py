@@ -145,27 +145,29 @@ def test_sites_rejects_what_the_rule_cannot_run(qisg):
         _make(qisg, 4, 64, _ladder(0.2, 0.5, 4), 1, 1, 1, word_bits=64)
 
 
-@pytest.mark.parametrize("L,Lt,n_samples,n_rep,n_slots", [(16, 8192, 1, 4, 16), (24, 2048, 1, 4, 16)])
+@pytest.mark.parametrize("L,Lt,n_samples,n_rep,n_slots", [(16, 8192, 16, 4, 16), (24, 2048, 16, 4, 16)])
 def test_sites_paper_shape_sampled_systems(qisg, L, Lt, n_samples, n_rep, n_slots):
-    """The paper's lattice shapes in the launch configuration the benchmark
-    times: after 3 sweeps without PT, sweep 3 of two sampled systems is
-    redone by the oracle from the device state and compared bit for bit;
-    the device energies of every system equal the oracle's recount."""
+    """The paper's lattice shapes in the configuration and launch shape the
+    benchmark times (16 samples x 4 replicas x 16 slots): after 3 sweeps
+    without PT, sweep 3 of two systems of one sampled disorder sample is
+    redone by the oracle from the device state and compared bit for bit; the
+    device energies of that sample's 64 systems equal the oracle's recount."""
     ladder = _ladder(0.2, 0.5, n_slots)
     seed = 17
+    a = 9
     inst = _make(qisg, L, Lt, ladder, n_rep, n_samples, seed, pt_every=0)
     cum = oracle.daemon_tables(ladder[:, 0])
     with inst:
         inst.sweep(3)
-        S3 = inst.spins()
-        J = inst.couplings()
+        S3 = inst.spins(a, 1)
+        J = inst.couplings(a, 1)
         inst.sweep(1)
-        S4 = inst.spins()
+        S4 = inst.spins(a, 1)
         A, B = inst.energies()
-    J = J.reshape(n_samples, L * L, 2)
+    J = J.reshape(1, L * L, 2)
     for (r, w) in ((0, 0), (n_rep - 1, n_slots - 1)):
         S = np.ascontiguousarray(S3[0, r, w])
-        oracle.daemon_sweep_system(L, Lt, seed, 0, r, w, 3, J[0], S, cum)   # no PT: walker w at slot w
+        oracle.daemon_sweep_system(L, Lt, seed, a, r, w, 3, J[0], S, cum)   # no PT: walker w at slot w
         assert np.array_equal(S, S4[0, r, w]), (r, w)
     Ao, Bo = oracle.energies(L, Lt, J, S4)
-    assert np.array_equal(A, Ao) and np.array_equal(B, Bo)
+    assert np.array_equal(A[a:a + 1], Ao) and np.array_equal(B[a:a + 1], Bo)
