@@ -100,3 +100,27 @@ def test_batch_equals_handles_and_schedule_invariance(qisg):
             for slot, (S, wa, A) in zip(slots, refs):
                 A2, _, wa2, S2 = b.results(slot, spins=True)
                 assert np.array_equal(S2, S) and np.array_equal(wa2, wa) and np.array_equal(A2, A)
+
+
+@pytest.mark.parametrize("rows,order", [(16, 0), (4, 1)])
+def test_uneven_batch_full_size_sampled(qisg, rows, order):
+    """The benchmark's batch (512 uneven instances, one persistent kernel) in
+    two tile schedules: after 2 sweeps, the two smallest instances and the
+    largest one are replayed by the oracle and compared bit for bit."""
+    from paper_2402_03920_gb300.workloads import uneven_batch
+    specs = uneven_batch(512, seed=2024, sweeps=100)
+    size = [sp.L * sp.L * sp.L_tau * sp.n_slots * sp.n_replicas for sp in specs]
+    picks = sorted(range(len(specs)), key=lambda i: size[i])[:2] + [int(np.argmax(size))]
+    with qisg.Batch(512, 0) as b:
+        slots = [b.admit(sp.L, sp.L_tau, qisg.ladder_linear(sp.k_lo, sp.k_hi, sp.n_slots, sp.gamma), sp.n_replicas,
+                         sp.seed) for sp in specs]
+        b.set_schedule(rows, order)
+        b.run(2)
+        for i in picks:
+            sp = specs[i]
+            lad = qisg.ladder_linear(sp.k_lo, sp.k_hi, sp.n_slots, sp.gamma)
+            st = _oracle_instance(sp.L, sp.L_tau, lad, sp.n_replicas, sp.seed, 2)
+            A, B, wa, S = b.results(slots[i], spins=True)
+            assert np.array_equal(wa, st.walker_at[0]), i
+            assert np.array_equal(S, st.S[0]), i
+            assert np.array_equal(A, st.A[0]) and np.array_equal(B, st.B[0]), i
