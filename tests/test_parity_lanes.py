@@ -150,13 +150,15 @@ def test_resume_is_bit_exact(qisg):
             assert np.array_equal(a.energies()[0], b2.energies()[0])
 
 
-def test_arbitrary_state_and_couplings_against_oracle(qisg):
-    """Random couplings, spins and permutation set through the ABI, then run
-    on both sides (the path the gauge and flip symmetries exercise)."""
+@pytest.mark.parametrize("W,n_slots,n_rep", [(0, 6, 4), (32, 16, 4), (64, 20, 5)])
+def test_arbitrary_state_and_couplings_against_oracle(qisg, W, n_slots, n_rep):
+    """Random couplings, spins and permutation set through the ABI (packed on
+    the device), then run on both sides (the path the gauge and flip
+    symmetries exercise); one and two word groups per site."""
     from paper_2402_03920_gb300.workloads import random_permutations, random_spins
-    L, Lt, n_slots, n_rep, n_a = 6, 8, 6, 4, 2
+    L, Lt, n_a = 6, 8, 2
     inst, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 1.1, n_rep, n_a, 5,
-                        layout=qisg.QISG_LAYOUT_LANES)
+                        layout=qisg.QISG_LAYOUT_LANES, word_bits=W)
     J = random_spins((n_a, L * L, 2), 1)
     S = random_spins((n_a, n_rep, n_slots, L * L * Lt), 2)
     wa = random_permutations(n_a * n_rep, n_slots, 3).reshape(n_a, n_rep, n_slots)

@@ -86,11 +86,15 @@ def test_explicit_pt_and_resume(qisg):
             assert np.array_equal(a.permutation(), c.permutation())
 
 
-def test_arbitrary_state_against_oracle(qisg):
+@pytest.mark.parametrize("W,n_rep,n_a", [(32, 4, 36), (64, 3, 70), (32, 5, 33)])
+def test_arbitrary_state_against_oracle(qisg, W, n_rep, n_a):
+    """Random couplings, spins and permutation through qisg_set_state (packed
+    on the device), including a ragged last word group and replica counts
+    that leave padding replicas in the last quad."""
     from paper_2402_03920_gb300.workloads import random_permutations, random_spins
-    L, Lt, n_slots, n_rep, n_a = 4, 6, 7, 4, 36
+    L, Lt, n_slots = 4, 6, 7
     inst, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 1.1, n_rep, n_a, 8,
-                        layout=qisg.QISG_LAYOUT_SAMPLES, word_bits=32)
+                        layout=qisg.QISG_LAYOUT_SAMPLES, word_bits=W)
     J = random_spins((n_a, L * L, 2), 4)
     S = random_spins((n_a, n_rep, n_slots, L * L * Lt), 5)
     wa = random_permutations(n_a * n_rep, n_slots, 6).reshape(n_a, n_rep, n_slots)
