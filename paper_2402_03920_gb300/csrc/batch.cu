@@ -533,9 +533,13 @@ int qisg_batch_create(qisg_batch **out, int capacity, size_t mem_budget, void *c
   if (!rc) rc = cuda_check(cudaMalloc(&B->d_inst, sizeof(InstDev) * (size_t)capacity), "descriptors");
   if (!rc) rc = cuda_check(cudaMalloc(&B->d_bar, 2 * sizeof(unsigned)), "barrier");
   if (!rc) rc = cuda_check(cudaMalloc(&B->d_err, sizeof(int)), "error flag");
-  if (!rc) rc = cuda_check(cudaMemset(B->d_bar, 0, 2 * sizeof(unsigned)), "barrier");
-  if (!rc) rc = cuda_check(cudaMemset(B->d_err, 0, sizeof(int)), "error flag");
-  if (!rc) rc = cuda_check(cudaMemset(B->d_inst, 0, sizeof(InstDev) * (size_t)capacity), "descriptors");
+  // on the batch's stream (it may be non-blocking, so a default-stream memset
+  // would not be ordered before the first launch)
+  if (!rc) rc = cuda_check(cudaMemsetAsync(B->d_bar, 0, 2 * sizeof(unsigned), B->stream), "barrier");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(B->d_err, 0, sizeof(int), B->stream), "error flag");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(B->d_inst, 0, sizeof(InstDev) * (size_t)capacity, B->stream),
+                           "descriptors");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(B->stream), "stream synchronize");
   if (rc) {
     qisg_batch_destroy(B);
     return rc;

@@ -367,7 +367,8 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
     for (int w = 0; w < 4; ++w)
       if (h->bases[(size_t)w * n_slots + s] >= 1.0) ptc.ge1[w] |= 1u << s;
   }
-  if (!rc) rc = cuda_check(cudaMemcpy(h->d_ptc, &ptc, sizeof(ptc), cudaMemcpyHostToDevice), "copy PT constants");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(h->d_ptc, &ptc, sizeof(ptc), cudaMemcpyHostToDevice, h->stream),
+                           "copy PT constants");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumA, 0, (size_t)n_chain_slots * 8, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumB, 0, (size_t)n_chain_slots * 8, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumq, 0, qn * 8, h->stream), "memset");
@@ -912,7 +913,7 @@ int qisg_sync(qisg_handle *h) {
 
 void qisg_destroy(qisg_handle *h) {
   if (!h) return;
-  if (h->stream || true) cudaStreamSynchronize(h->stream);
+  cudaStreamSynchronize(h->stream);
   void *ptrs[] = {h->spins, h->spins_alt, h->J, h->d_T, h->d_bases, h->d_sq, h->d_ptc, h->d_walker, h->d_U, h->d_sumA, h->d_sumB,
                   h->d_sumq, h->d_sumq2, h->d_q, h->d_out, h->d_t, h->d_acc, h->d_err, h->d_dcum, h->d_dlut};
   for (void *p : ptrs)
@@ -920,7 +921,6 @@ void qisg_destroy(qisg_handle *h) {
   drop_cycle(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   prof_clear(h);
-  for (cudaEvent_t e : h->prof_spare) cudaEventDestroy(e);
   delete h;
 }
 
