@@ -1579,21 +1579,27 @@ int init_t(qisg_handle *h) {
   return cuda_check(cudaGetLastError(), "samples init");
 }
 
+// Unpacked in chunks of samples (at most 256 MB of int8 staged at a time).
 template <typename Word>
 int get_spins_t(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
-  const int64_t n = n_a * h->n_rep * h->n_slots * h->N;
-  if (n == 0) return QISG_OK;
+  if (n_a == 0) return QISG_OK;
+  const int64_t per_a = (int64_t)h->n_rep * h->n_slots * h->N;
+  const int64_t chunk = std::min(n_a, std::max<int64_t>(1, ((int64_t)256 << 20) / per_a));
   int rc = samples_materialize(h);
   if (rc) return rc;
   int8_t *d = nullptr;
-  rc = cuda_check(cudaMalloc(&d, (size_t)n), "cudaMalloc");
+  rc = cuda_check(cudaMalloc(&d, (size_t)(chunk * per_a)), "cudaMalloc");
   if (rc) return rc;
-  samples_extract_kernel<Word><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
-      reinterpret_cast<const Word *>(h->spins), h->d_walker, d, a_lo, n_a, h->N, h->n_slots, h->n_q,
-      h->n_rep);
-  rc = cuda_check(cudaGetLastError(), "extract");
-  if (!rc) rc = cuda_check(cudaMemcpyAsync(S, d, (size_t)n, cudaMemcpyDeviceToHost, h->stream), "copy");
-  if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  for (int64_t a0 = 0; a0 < n_a && !rc; a0 += chunk) {
+    const int64_t na = std::min(chunk, n_a - a0), n = na * per_a;
+    samples_extract_kernel<Word><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+        reinterpret_cast<const Word *>(h->spins), h->d_walker, d, a_lo + a0, na, h->N, h->n_slots, h->n_q,
+        h->n_rep);
+    h->launches++;
+    rc = cuda_check(cudaGetLastError(), "extract");
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(S + a0 * per_a, d, (size_t)n, cudaMemcpyDeviceToHost, h->stream), "copy");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  }
   cudaFree(d);
   return rc;
 }
