@@ -61,7 +61,8 @@ class Stats:
     chunks: int = 0
     latencies: list = field(default_factory=list)
     max_active: int = 0
-    refused_for_memory: int = 0
+    refused_for_memory: int = 0     # admission attempts deferred because the arena was full
+    rejected: list = field(default_factory=list)   # rids that cannot fit even in an empty batch
 
     def summary(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
@@ -70,7 +71,8 @@ class Stats:
                 "ps_per_update": self.wall * 1e12 / max(self.updates, 1),
                 "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)),
-                "max_active": self.max_active, "refused_for_memory": self.refused_for_memory}
+                "max_active": self.max_active, "refused_for_memory": self.refused_for_memory,
+                "rejected": len(self.rejected)}
 
 
 def updates_of(req: Request) -> int:
@@ -78,12 +80,17 @@ def updates_of(req: Request) -> int:
 
 
 class Server:
-    """One resident batch, admission by memory, continuous batching."""
+    """One resident batch, admission by memory, continuous batching.
+
+    ``batch`` defaults to a new ``qisg.Batch(capacity, mem_budget, stream)``;
+    any object with the same admit/run/status/results/retire calls can stand
+    in for it (the scheduling logic is tested that way on the host)."""
 
     def __init__(self, capacity: int = 256, mem_budget: int = 8 << 30, chunk_sweeps: int = 50,
-                 keep_spins: bool = False, stream: int | None = None):
-        self.batch = qisg.Batch(capacity, mem_budget, stream)
+                 keep_spins: bool = False, stream: int | None = None, batch=None):
+        self.batch = batch if batch is not None else qisg.Batch(capacity, mem_budget, stream)
         self.chunk = chunk_sweeps
+        self._t0 = time.perf_counter()
         self.keep_spins = keep_spins
         self.queue: list[Request] = []
         self.active: dict[int, tuple[Request, float]] = {}   # slot -> (request, admitted at)
@@ -101,6 +108,12 @@ class Server:
             req = self.queue[0]
             lad = qisg.ladder_linear(req.k_lo, req.k_hi, req.n_slots, req.gamma)
             slot = self.batch.try_admit(req.L, req.L_tau, lad, req.n_replicas, req.seed, req.sweeps)
+            if slot is None and not self.active:
+                # refused by an empty batch: it never fits, and waiting would
+                # block the queue for good
+                self.queue.pop(0)
+                self.stats.rejected.append(req.rid)
+                continue
             if slot is None:
                 self.stats.refused_for_memory += 1
                 break          # wait for memory to free up (FIFO)
@@ -128,19 +141,21 @@ class Server:
             self.batch.run(self.chunk)
             self.batch.sync()
             self.stats.chunks += 1
-        self._retire(now_fn())
+        self._retire(self.clock())
+
+    def clock(self) -> float:
+        """Seconds since the start of the current ``serve`` run."""
+        return time.perf_counter() - self._t0
 
     def serve(self, requests: list[Request], realtime: bool = True, max_wall: float = 3600.0) -> Stats:
         """Feed requests at their arrival times (seconds from start) and run
         until all are done.  With realtime=False every request is available at
         once (offline batch)."""
         pending = sorted(requests, key=lambda r: r.arrival)
-        t0 = time.perf_counter()
-        global _T0
-        _T0 = t0
+        self._t0 = time.perf_counter()
         i = 0
         while i < len(pending) or self.queue or self.active:
-            now = time.perf_counter() - t0
+            now = self.clock()
             while i < len(pending) and (not realtime or pending[i].arrival <= now):
                 r = pending[i]
                 if not realtime:
@@ -155,12 +170,5 @@ class Server:
             self.step(now)
             if now > max_wall:
                 raise TimeoutError("serving run exceeded its wall-clock budget")
-        self.stats.wall = time.perf_counter() - t0
+        self.stats.wall = self.clock()
         return self.stats
-
-
-_T0 = time.perf_counter()
-
-
-def now_fn() -> float:
-    return time.perf_counter() - _T0
