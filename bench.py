@@ -75,6 +75,13 @@ def workload():
     return PRODUCTION
 
 
+def base_config(w) -> dict:
+    """The workload's description, shared by both arms' JSON lines."""
+    return {"workload": w.name, "L": w.L, "L_tau": w.L_tau, "n_samples": w.n_samples,
+            "n_replicas": w.n_replicas, "n_slots": w.n_slots, "k": [w.k_lo, w.k_hi], "gamma": w.gamma,
+            "measure_every": w.measure_every}
+
+
 def updates_per_step(w):
     return w.n_samples * w.n_replicas * w.n_slots * w.L * w.L * w.L_tau * SWEEPS_PER_STEP
 
@@ -542,12 +549,10 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": f"u{wb} bit-packed spins (1 bit/spin), u32 Philox, f64 PT",
+        "dtype": f"u{wb}",
         "data": "synthetic (+-J couplings and start spins from Philox)",
-        "config": {"workload": w.name, "L": w.L, "L_tau": w.L_tau, "n_samples": w.n_samples,
-                   "n_replicas": w.n_replicas, "n_slots": w.n_slots, "k": [w.k_lo, w.k_hi],
-                   "gamma": w.gamma, "sweeps_per_step": SWEEPS_PER_STEP,
-                   "measure_every": w.measure_every, "form": main,
+        "config": {**base_config(w), "sweeps_per_step": SWEEPS_PER_STEP, "form": main,
+                   "arith": f"u{wb} words of bit-packed spins (1 bit/spin), u32 Philox draws, f64 PT",
                    "layout": "SAMPLES" if layout == qisg.QISG_LAYOUT_SAMPLES else "LANES",
                    "word_bits": wb,
                    "sweep_schedule": {"tiles": list(TUNED.get(main, ((0, 0), (0, 0)))[0]),
@@ -611,10 +616,9 @@ def run_reference(args):
     value = wall * 1e12 / ups
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "i8 spins, f64",
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "i8",
             "data": "synthetic (+-J couplings and start spins from Philox)",
-            "config": {"workload": w.name, "L": w.L, "L_tau": w.L_tau, "n_samples": w.n_samples,
-                       "n_replicas": w.n_replicas, "n_slots": w.n_slots,
+            "config": {**base_config(w), "arith": "one int8 spin per byte, u32 Philox draws, f64 PT",
                        "step": f"1 sweep of {n_a} samples (a bounded sample of the workload)"},
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(ncores, n_a), "kind": "oracle",
