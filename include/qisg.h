@@ -169,7 +169,10 @@ int qisg_permutation(qisg_handle *h, int32_t *walker_at);
 
 /* Unpacked +-1 spins of samples a_lo .. a_lo+n_a-1, by walker:
  * S[a - a_lo][r][w][site], host int8, n_a*n_replicas*n_slots*L*L*L_tau
- * bytes.  EINVAL: the sample range is outside [0, n_samples).  Synchronises. */
+ * bytes.  EINVAL: the sample range is outside [0, n_samples).  Synchronises.
+ * Unpacked on the device through a temporary staging buffer of at most
+ * 256 MB (or one sample's spins, if larger), allocated outside the memory
+ * budget and freed before returning; ENOMEM if it cannot be allocated.    */
 int qisg_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S);
 
 /* Couplings of samples a_lo .. a_lo+n_a-1: J[a - a_lo][x + L*y][dir], int8
@@ -186,7 +189,11 @@ int qisg_set_couplings(qisg_handle *h, const int8_t *J);
  * and the sweep counter.  Measurement sums are cleared; energies are
  * recomputed.  Because every draw is a function of the counters, resuming
  * from a saved state is bit-exact with the uninterrupted run.
- * ECORRUPT: a row of walker_at is not a permutation or a spin is not +-1. */
+ * ECORRUPT: a row of walker_at is not a permutation or a spin is not +-1.
+ * Packed on the device through a temporary staging buffer (at most 256 MB,
+ * or one sample's spins if larger; in the SAMPLES packing one word group's
+ * samples of one replica, word_bits * n_slots * N bytes), allocated outside
+ * the memory budget and freed before returning.                           */
 int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, uint64_t sweep);
 
 /* Measurement sums since creation (or the last qisg_set_state), by slot:
