@@ -150,6 +150,23 @@ def daemon_tables(k: float, lut_bits: int = 12):
     return cum, lut
 
 
+def _sized(arr, dtype, n: int, what: str) -> np.ndarray:
+    """Contiguous copy (or view) of `arr` as `dtype`, which must hold exactly
+    n elements: the library reads that many from the pointer."""
+    a = np.ascontiguousarray(arr, dtype=dtype)
+    if a.size != n:
+        raise ValueError(f"{what}: expected {n} elements, got {a.size}")
+    return a
+
+
+def _ladder_array(ladder) -> np.ndarray:
+    """The ladder as contiguous float64 [n_slots][2] (k, k_tau) rows."""
+    lad = np.ascontiguousarray(ladder, dtype=np.float64)
+    if lad.ndim != 2 or lad.shape[1] != 2 or lad.shape[0] < 1:
+        raise ValueError(f"ladder: expected [n_slots][2] (k, k_tau) rows, got shape {lad.shape}")
+    return lad
+
+
 def ladder_equal(lo: float, hi: float, n: int) -> np.ndarray:
     """[n][2] ladder with k_tau = k (the paper's single coupling, Sec. 1),
     k linear in [lo, hi]: the ladders the SITES daemon rule takes."""
@@ -191,7 +208,7 @@ class Instance:
     def __init__(self, cfg: Config, stream: int | None = None):
         lib = load()
         self.cfg = cfg
-        ladder = np.ascontiguousarray(cfg.ladder, dtype=np.float64)
+        ladder = _ladder_array(cfg.ladder)
         self.n_slots = ladder.shape[0]
         self.L, self.L_tau = cfg.L, cfg.L_tau
         self.N = cfg.L * cfg.L * cfg.L_tau
@@ -272,11 +289,14 @@ class Instance:
         return J
 
     def set_couplings(self, J: np.ndarray):
-        _check(load().qisg_set_couplings(self._h, _ptr(np.ascontiguousarray(J, dtype=np.int8))))
+        J = _sized(J, np.int8, self.n_samples * self.L * self.L * 2, "J [n_samples][L*L][2]")
+        _check(load().qisg_set_couplings(self._h, _ptr(J)))
 
     def set_state(self, S: np.ndarray, walker_at: np.ndarray, sweep: int):
-        _check(load().qisg_set_state(self._h, _ptr(np.ascontiguousarray(S, dtype=np.int8)),
-                                     _ptr(np.ascontiguousarray(walker_at, dtype=np.int32)), sweep))
+        n_cs = self.n_samples * self.n_rep * self.n_slots
+        S = _sized(S, np.int8, n_cs * self.N, "S [n_samples][n_replicas][n_slots][N]")
+        wa = _sized(walker_at, np.int32, n_cs, "walker_at [n_samples][n_replicas][n_slots]")
+        _check(load().qisg_set_state(self._h, _ptr(S), _ptr(wa), sweep))
 
     def measurements(self):
         ncs = (self.n_samples, self.n_rep, self.n_slots)
@@ -365,7 +385,7 @@ class InstanceDesc(ctypes.Structure):
 
 
 def _desc(L, L_tau, ladder, n_replicas, seed, n_sweeps):
-    lad = np.ascontiguousarray(ladder, dtype=np.float64)
+    lad = _ladder_array(ladder)
     d = InstanceDesc(L, L_tau, lad.shape[0], n_replicas, lad.ctypes.data, seed, n_sweeps)
     return d, lad
 

@@ -6,6 +6,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -88,3 +89,17 @@ def test_daemon_tables_host_without_gpu():
     rc = lib.qisg_create(ctypes.byref(h), 4, 96, equal.ctypes.data_as(ctypes.c_void_p), 4, 2, 1, 1,
                          ctypes.byref(opts))
     assert rc == -1
+
+
+def test_binding_rejects_misshapen_host_arrays():
+    """The library reads exactly the documented number of elements from each
+    host pointer, so the binding refuses arrays of another size or shape
+    before the call."""
+    from paper_2402_03920_gb300 import qisg
+    assert qisg._sized(np.ones((2, 3), np.int64), np.int8, 6, "x").dtype == np.int8
+    with pytest.raises(ValueError):
+        qisg._sized(np.ones(5, np.int8), np.int8, 6, "x")
+    assert qisg._ladder_array([[0.2, 0.3], [0.4, 0.5]]).shape == (2, 2)
+    for bad in ([0.2, 0.3], np.zeros((2, 3)), np.zeros((0, 2))):
+        with pytest.raises(ValueError):
+            qisg._ladder_array(bad)
