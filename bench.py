@@ -309,6 +309,13 @@ def roofline(kern, w, layout, wb, n_sm, pk, steps):
             "avg_launch_us": per_launch_ms * 1e3}
 
 
+def alu_peak_source(n_sm, pk, pk_kind) -> str:
+    """How the ALU peak is made: unit counts times the maximum SM clock (the
+    clock read from MEASURED_PEAKS.json, or the fallback figure)."""
+    return (f"derived: {n_sm} SMs x {INT_LANES_PER_CLK_PER_SM} int32 lanes/clk x "
+            f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz (max SM clock, {pk_kind})")
+
+
 def uneven_batch_entry(qisg, sweeps=100):
     """512 instances, L in {8,12,16,20,24}, L_tau in {64..1024}, 8..32 slots,
     Gamma in [0.8, 1.2], one persistent launch per chunk: ps per update,
@@ -571,7 +578,7 @@ def run_gpu(args):
                       "roofline": roofline(kn, w, lay, wbb, n_sm, pk, args.steps)}
     rl = roofline(kern, w, layout, wb, n_sm, pk, args.steps)
     if rl is not None:
-        rl["peak_source"] = f"{pk_kind}: {n_sm} SMs x {INT_LANES_PER_CLK_PER_SM} int32 lanes/clk x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"
+        rl["peak_source"] = alu_peak_source(n_sm, pk, pk_kind)
     line["roofline"] = rl
     if not args.no_e2e:
         line["e2e"] = e2e_form(torch, qisg, w, main, args.steps, seed)
