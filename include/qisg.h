@@ -160,7 +160,12 @@ int qisg_energies(qisg_handle *h, int64_t *A, int64_t *B);
 /* Replica overlaps of the configurations now at each slot (Appendix E.1):
  * q[a][s][p] = sum_i S^{r1}_i S^{r2}_i over pairs p = (r1 < r2) in
  * lexicographic order.  q: host int64 [n_samples][n_slots][n_pairs],
- * n_pairs = n_replicas (n_replicas-1) / 2.  Synchronises.                  */
+ * n_pairs = n_replicas (n_replicas-1) / 2.  Synchronises.
+ * Limits: the LANES and SITES overlap kernels keep one 8-byte counter per
+ * pair in shared memory (48 KB), so they take n_replicas <= 111; beyond
+ * that this call and the cadenced measurement return QISG_ECUDA.  The
+ * SAMPLES packing takes up to 65535 (word group, slot, pair) sets (EINVAL
+ * beyond).                                                               */
 int qisg_overlaps(qisg_handle *h, int64_t *q);
 
 /* PT permutation: walker_at[a][r][s] = walker now at slot s.  Host int32
