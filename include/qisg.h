@@ -60,7 +60,7 @@ extern "C" {
  *   block, as in Ito-Kanada's multi-sample coding (Sec. 2.1.1); PT moves the
  *   spin bits of each sample between slot words.
  * SITES: the paper's own multi-site coding with its update rule (Sec. 2.1,
- *   Sec. 2.1.1, Appendices C and D): a 32-bit word holds 32 imaginary-time
+ *   Sec. 2.1.1, Appendices B and C): a 32-bit word holds 32 imaginary-time
  *   sites of ONE system (site (x, y, tau) is bit tau / M of word-site
  *   x + L y + L^2 (tau mod M), M = L_tau / 32), and a site with u of its 6
  *   bonds unsatisfied flips iff u + d >= 3, d its two-bit daemon, whose
@@ -111,7 +111,7 @@ void qisg_opts_default(qisg_opts *opts);
 int qisg_ladder_linear(double lo, double hi, int n, double gamma, qisg_slot *out);
 
 /* The tables of the SITES daemon rule for coupling k (Sec. 2.1.1, Appendix
- * D), computed on the host: cum[0..254] = cumulative(n), the truncation of
+ * C), computed on the host: cum[0..254] = cumulative(n), the truncation of
  * 2^64 sum_{m <= n} p^pop(m) (1-p)^(8-pop(m)) with p = e^{-4k} (fixed point
  * with 126 fractional bits; the paper uses 128-bit floats); lut (NULL =
  * skip): 2^lut_bits entries, entry h = n_min | (n_max - n_min) << 8, where

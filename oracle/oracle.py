@@ -132,7 +132,7 @@ def pow_by_squaring(b: float, e: int) -> float:
 
 
 # --------------------------------------------------------------------------
-# Daemon rule (Sec. 2.1.1, Appendices C and D)
+# Daemon rule (Sec. 2.1.1, Appendices B and C)
 # --------------------------------------------------------------------------
 
 def daemon_cumulative(k: float) -> np.ndarray:

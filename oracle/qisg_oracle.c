@@ -23,7 +23,7 @@
  *   - observables: integer energies and the replica overlap (Appendix E.1).
  *   - Philox4x32-10 (Sec. 2.1.1), the counter-based generator of Salmon et
  *     al. (SC'11), written here from its published definition.
- *   - the paper's own update rule (Sec. 2.1 and 2.1.1, Appendices C and D),
+ *   - the paper's own update rule (Sec. 2.1 and 2.1.1, Appendices B and C),
  *     for equal couplings k_tau = k: multi-site coding puts 32 tau-sites of
  *     one system in a word (site (x, y, tau) is bit
  *     tau / M of word (x, y, tau mod M), M = L_tau / 32), and a flip is taken
@@ -202,7 +202,7 @@ void orc_init_spins(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64
 }
 
 /* ------------------------------------------------------------------------ */
-/* Daemon bits (Sec. 2.1.1, Appendices C and D).                             */
+/* Daemon bits (Sec. 2.1.1, Appendices B and C).                             */
 /* ------------------------------------------------------------------------ */
 
 /* One state step of xoroshiro128++ (Blackman and Vigna, "Scrambled linear
@@ -261,7 +261,7 @@ uint32_t orc_daemon_bword(uint64_t seed, int64_t a, int r, int s, uint32_t wsite
 }
 
 /* The daemon's level d in 0..3 from one bit of each of b4, b8, b12
- * (Appendix C): after b8 &= b4 and b12 &= b8 the four reachable patterns
+ * (Appendix B): after b8 &= b4 and b12 &= b8 the four reachable patterns
  * 000, 100, 110, 111 stand for d = 0, 1, 2, 3, i.e. d is the number of
  * leading ones of (b4, b8, b12). */
 int orc_daemon_level(int b4, int b8, int b12)

@@ -1,5 +1,5 @@
 // SITES packing: the paper's own multi-site coding with its daemon-bit
-// Metropolis rule (Sec. 2.1 and 2.1.1, Appendices C and D), for equal
+// Metropolis rule (Sec. 2.1 and 2.1.1, Appendices B and C), for equal
 // couplings k_tau = k.  A 32-bit word holds 32 imaginary-time sites of ONE
 // system: with M = L_tau / 32, site (x, y, tau) is bit tau / M of word-site
 // x + L y + L^2 (tau mod M).  M is even, so all bits of a word have the

@@ -1,4 +1,4 @@
-"""Pins of the oracle's daemon rule (Sec. 2.1.1, Appendices C and D) against
+"""Pins of the oracle's daemon rule (Sec. 2.1.1, Appendices B and C) against
 things other than itself (no GPU): the truth table the paper prints, the
 closed-form probabilities of the inverse-cumulative bytes, the full period of
 the xoroshiro128 state step, the Metropolis probabilities of Eq. (3) at equal
@@ -22,7 +22,7 @@ TWO64 = 1 << 64
 
 
 # --------------------------------------------------------------------------
-# Appendix C: the daemon's truth table
+# Appendix B: the daemon's truth table
 # --------------------------------------------------------------------------
 
 def _truth_rows():

@@ -1,5 +1,5 @@
 """GPU parity of the SITES packing (the paper's multi-site coding with its
-daemon-bit rule, Sec. 2.1.1 and Appendices C-D) against the CPU oracle,
+daemon-bit rule, Sec. 2.1.1 and Appendices B-C) against the CPU oracle,
 through the C ABI: the host tables, full runs bit for bit, resume, and at the
 paper's lattice shape one sweep of sampled systems."""
 from __future__ import annotations
