@@ -171,7 +171,7 @@ def batched_layout(qisg):
     return int(os.environ.get("QISG_BENCH_LAYOUT", qisg.QISG_LAYOUT_SAMPLES))
 
 
-KINDS = (("sweep", 0), ("pt", 1), ("measure", 2), ("permute", 3))
+KINDS = (("red", 5), ("blue", 4), ("pt", 1), ("measure", 2), ("permute", 3))
 
 
 def timed_steps(torch, inst, flush, steps):
@@ -201,11 +201,11 @@ def read_profile(inst, names):
 
 
 def time_form(torch, qisg, w, form, steps, warmup, seed):
-    """The timed region: `steps` plain steps (no instrumentation).  Then two
-    more passes of the same steps for the kernel figures: event pairs around
-    the half-sweep launches only (the roofline's launch duration), and event
-    pairs around every launch (the per-kernel breakdown).  An event pair waits
-    for the work before it, so these passes run slower than the plain one."""
+    """The timed region: `steps` plain steps (no instrumentation).  Then a
+    second pass of the same steps with CUDA event pairs around every launch,
+    which gives each kernel kind's share of the device time (an event pair
+    waits for the work before it, so that pass runs slower than the plain
+    one and its absolute durations are not used)."""
     inst = make_instance(qisg, w, form, seed)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
     # untimed: pick the sweep tiles on the live state (results do not depend
@@ -224,16 +224,11 @@ def time_form(torch, qisg, w, form, steps, warmup, seed):
     launches0 = inst.launch_count()
     total_ms = timed_steps(torch, inst, flush, steps)
     launches = inst.launch_count() - launches0
-    inst.profile(True, kinds=[qisg.KERNEL_SWEEP])
-    sweep_pass_ms = timed_steps(torch, inst, flush, steps)
-    kern = read_profile(inst, ("sweep",))
     inst.profile(True)
-    all_pass_ms = timed_steps(torch, inst, flush, steps)
-    breakdown = read_profile(inst, [k for k, _ in KINDS])
+    pass_ms = timed_steps(torch, inst, flush, steps)
+    kern = read_profile(inst, [k for k, _ in KINDS])
     inst.profile(False)
-    breakdown["pass_ms_per_step"] = all_pass_ms / steps
-    kern["pass_ms_per_step"] = sweep_pass_ms / steps
-    kern["breakdown"] = breakdown
+    kern["pass_ms_per_step"] = pass_ms / steps
     layout, wb = inst.layout()
     inst.close()
     del flush
@@ -289,24 +284,100 @@ ALG_OPS = {"samples32": 40 / 32 + 50 / (4 * 32), "samples64": 80 / 64 + 50 / (4 
 INT_LANES_PER_CLK_PER_SM = 128
 
 
-def roofline(kern, w, layout, wb, n_sm, pk, steps):
-    """Roofline of the half-sweep kernel from its live CUDA-event timing:
-    algorithmic integer operations per launch / average launch time."""
+def kernel_shares(kern):
+    """Each kernel kind's share of the device time of the event-pair pass."""
+    tot = sum(kern[k]["ms"] for k, _ in KINDS if k in kern)
+    return {k: (kern[k]["ms"] / tot if tot > 0 else 0.0) for k, _ in KINDS if k in kern}
+
+
+def kernel_names(layout, wb, tiles):
+    """The CUDA kernels behind the red and blue kinds for this schedule."""
     from paper_2402_03920_gb300 import qisg
-    sw = kern["sweep"]
-    if not sw["timed"] or not sw["launched"]:
+    if layout != qisg.QISG_LAYOUT_SAMPLES:
+        return {"red": "lanes_half_sweep_kernel", "blue": "lanes_half_sweep_kernel"}
+    (t_red, _t_blue), (_v_red, v_blue) = tiles
+    if wb == 32:
+        red = {1: "samples_red_fused_kernel", 2: "samples_red_fusedq_kernel<2>"}.get(t_red, "samples_red_fusedq_kernel<4>")
+        blue = "samples_sweep4_kernel" if v_blue == 0 else "samples_half_sweep_kernel"
+    else:
+        red = blue = "samples_half_sweep_kernel"
+    return {"red": red, "blue": blue}
+
+
+def source_digest() -> str:
+    """sha256 (16 hex) of the kernel sources: DRAM traffic taken from an ncu
+    capture is used only while the kernels are the ones captured."""
+    import hashlib
+    hsh = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2402_03920_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                hsh.update(f.read())
+    return hsh.hexdigest()[:16]
+
+
+def captured_traffic(kernel: str, workload_name: str):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload_name` from
+    the ncu summary profiles/dram_traffic.md (rows: | kernel | workload |
+    bytes per launch | source digest | ...), or None when absent or taken
+    from other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    try:
+        rows = open(path).read().splitlines()
+    except OSError:
         return None
-    per_launch_ms = sw["ms"] / sw["timed"]
-    key = f"samples{wb}" if layout == qisg.QISG_LAYOUT_SAMPLES else "lanes"
-    ups_per_launch = updates_per_step(w) * steps / sw["launched"]
-    ops = ALG_OPS[key] * ups_per_launch
-    achieved = ops / (per_launch_ms * 1e-3) / 1e12
+    digest = source_digest()
+    for row in rows:
+        cells = [c.strip().strip("`") for c in row.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel and cells[1] == workload_name and cells[3] == digest:
+            try:
+                return float(cells[2])
+            except ValueError:
+                return None
+    return None
+
+
+def roofline(kern, ups_per_step, key, n_sm, pk, steps, ms_per_step, names, wname):
+    """ALU roofline of the red and the blue half-sweep kernels.  A kernel's
+    average launch duration is the plain (timed) step time times its share
+    of the event-pair pass, over its launches per step, so that launches x
+    duration never exceeds the timed step; achieved = algorithmic integer
+    operations per launch / that duration.  Returns (dominant, by kernel)."""
+    shares = kernel_shares(kern)
     clk = pk.get("sm_max_mhz", 2070.0)
     peak = n_sm * INT_LANES_PER_CLK_PER_SM * clk * 1e6 / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "half_sweep",
-            "ops_per_update": ALG_OPS[key], "updates_per_launch": ups_per_launch,
-            "avg_launch_us": per_launch_ms * 1e3}
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    out = {}
+    for kind in ("red", "blue"):
+        k = kern.get(kind)
+        if not k or not k["launched"]:
+            continue
+        per_step = k["launched"] / steps
+        dur_ms = ms_per_step * shares[kind] / per_step
+        ups_per_launch = ups_per_step / per_step
+        ops = ALG_OPS[key] * ups_per_launch
+        achieved = ops / (dur_ms * 1e-3) / 1e12
+        alg_bytes = 0.25 * ups_per_launch / 2   # half of one read and one write of every spin per sweep
+        out[kind] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": captured_traffic(names[kind], wname),
+                     "kernel": names[kind], "ops_per_update": ALG_OPS[key], "updates_per_launch": ups_per_launch,
+                     "avg_launch_us": dur_ms * 1e3, "share": shares[kind], "launches_per_step": per_step,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "hbm": {"achieved": alg_bytes / (dur_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": alg_bytes / (dur_ms * 1e-3) / 1e9 / hbm_peak},
+                     "timing": "plain step time x share of the event-pair pass / launches per step"}
+    if not out:
+        return None, {}
+    dom = max(out, key=lambda k: out[k]["share"])
+    return out[dom], out
+
+
+def form_roofline(kern, w, layout, wb, n_sm, pk, steps, ms_per_step, tiles):
+    from paper_2402_03920_gb300 import qisg
+    key = f"samples{wb}" if layout == qisg.QISG_LAYOUT_SAMPLES else "lanes"
+    return roofline(kern, updates_per_step(w), key, n_sm, pk, steps, ms_per_step,
+                    kernel_names(layout, wb, tiles), w.name)
 
 
 def alu_peak_source(n_sm, pk, pk_kind) -> str:
@@ -351,11 +422,14 @@ def uneven_batch_entry(qisg, sweeps=100):
 
 def large_batched_entry(torch, qisg, sweeps=20):
     """1024 samples x 4 replicas x 32 slots, L=24, L_tau=512 (4.8 GB of
-    spins, far larger than L2): the SAMPLES form, graph replay."""
+    spins, far larger than L2): the SAMPLES form, graph replay.  Kernel
+    figures as for the headline: plain time x each kernel's share of an
+    event-pair pass."""
     from paper_2402_03920_gb300.workloads import BATCHED as w
     ladder = qisg.ladder_linear(w.k_lo, w.k_hi, w.n_slots, w.gamma)
     cfg = qisg.Config(w.L, w.L_tau, ladder, w.n_replicas, w.n_samples, w.seed, word_bits=64,
                       layout=qisg.QISG_LAYOUT_SAMPLES)
+
     def run(n):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -368,35 +442,20 @@ def large_batched_entry(torch, qisg, sweeps=20):
         inst.sweep(2)
         inst.sync()
         ms = run(sweeps)                      # plain: the value
-        inst.profile(True, kinds=[qisg.KERNEL_SWEEP])
-        run(sweeps)                           # half-sweep launch durations
-        kern = read_profile(inst, ("sweep",))
         inst.profile(True)
-        run(sweeps)                           # breakdown (event pairs on every launch)
-        kern.update({k: v for k, v in read_profile(inst, ("pt", "permute")).items()})
+        run(sweeps)                           # shares (event pairs on every launch)
+        kern = read_profile(inst, [k for k, _ in KINDS])
         inst.profile(False)
+        tiles = inst.tiles()
+        layout, wb = inst.layout()
     N = w.L * w.L * w.L_tau
-    ups = w.n_samples * w.n_replicas * w.n_slots * N * sweeps
+    ups_per_sweep = w.n_samples * w.n_replicas * w.n_slots * N
     pk, _ = peaks()
-    sw = kern["sweep"]
-    per_launch = sw["ms"] / max(sw["timed"], 1)
-    ups_per_launch = ups / sweeps / 2
-    # the half sweeps are integer-ALU bound here too; the HBM figure (one read
-    # and one write of every spin per sweep, split over the two passes) says
-    # how far the lattice traffic is from the copy bandwidth
-    ops = ALG_OPS["samples64"] * ups_per_launch
-    alu_achieved = ops / (per_launch * 1e-3) / 1e12
-    import torch as _t
-    n_sm = _t.cuda.get_device_properties(0).multi_processor_count
-    alu_peak = n_sm * INT_LANES_PER_CLK_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    hbm_achieved = 0.25 * ups_per_launch / (per_launch * 1e-3) / 1e9
-    return {"value": ms * 1e9 / ups, "unit": UNIT, "ms": ms, "sweeps": sweeps,
-            "workload": w.name, "kernel_us_per_launch": {k: v["us_per_launch"] for k, v in kern.items()},
-            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
-                         "frac": alu_achieved / alu_peak, "traffic": None, "kernel": "half_sweep",
-                         "ops_per_update": ALG_OPS["samples64"],
-                         "hbm": {"achieved": hbm_achieved, "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                                 "frac": hbm_achieved / pk.get("hbm_gbs", 6800.0), "bytes_per_update": 0.25}}}
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    rl, rl_all = roofline(kern, ups_per_sweep, "samples64", n_sm, pk, sweeps, ms / sweeps,
+                          kernel_names(layout, wb, tiles), w.name)
+    return {"value": ms * 1e9 / (ups_per_sweep * sweeps), "unit": UNIT, "ms": ms, "sweeps": sweeps,
+            "workload": w.name, "share": kernel_shares(kern), "roofline": rl, "roofline_by_kernel": rl_all}
 
 
 def paper_shape_entry(torch, qisg, sweeps=10):
@@ -502,14 +561,12 @@ def cpu_baseline(w, budget_s=15.0):
 
 
 def kernel_timing(kern, steps):
-    bd = kern["breakdown"]
-    return {"how": "second and third passes of the same steps with event pairs around the half sweeps "
-                   "(roofline) and around every launch (breakdown); pairs serialise the graph",
-            "sweep_us_per_launch": kern["sweep"]["us_per_launch"],
-            "sweep_pass_ms_per_step": kern["pass_ms_per_step"],
-            "breakdown_us_per_launch": {k: bd[k]["us_per_launch"] for k, _ in KINDS},
-            "breakdown_launches": {k: bd[k]["launched"] for k, _ in KINDS},
-            "breakdown_pass_ms_per_step": bd["pass_ms_per_step"]}
+    return {"how": "second pass of the same steps with event pairs around every launch (pairs serialise "
+                   "the graph); only the shares of its device time are used",
+            "share": kernel_shares(kern),
+            "pair_us_per_launch": {k: kern[k]["us_per_launch"] for k, _ in KINDS},
+            "launches_per_step": {k: kern[k]["launched"] / steps for k, _ in KINDS},
+            "pair_pass_ms_per_step": kern["pass_ms_per_step"]}
 
 
 def run_gpu(args):
@@ -570,16 +627,12 @@ def run_gpu(args):
         "clocks": clocks,
         "kernel_timing": kernel_timing(kern, args.steps),
     }
-    for form in forms[1:]:
-        tm, ln, kn, lay, wbb = results[form]
-        line[form] = {"value": tm * 1e9 / ups_total, "unit": UNIT, "ms_per_step": tm / args.steps,
-                      "gpu_launches": ln,
-                      "layout": "SAMPLES" if lay == qisg.QISG_LAYOUT_SAMPLES else "LANES",
-                      "roofline": roofline(kn, w, lay, wbb, n_sm, pk, args.steps)}
-    rl = roofline(kern, w, layout, wb, n_sm, pk, args.steps)
+    rl, rl_all = form_roofline(kern, w, layout, wb, n_sm, pk, args.steps, total_ms / args.steps,
+                               TUNED.get(main, ((0, 0), (0, 0))))
     if rl is not None:
         rl["peak_source"] = alu_peak_source(n_sm, pk, pk_kind)
     line["roofline"] = rl
+    line["roofline_by_kernel"] = rl_all
     if not args.no_e2e:
         line["e2e"] = e2e_form(torch, qisg, w, main, args.steps, seed)
     extras = [x for x in args.extras.split(",") if x]
@@ -595,6 +648,16 @@ def run_gpu(args):
         line["serving"] = serving_entry(qisg, args.serving_requests)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w)
+    # the other forms last, so that a tail of the line keeps them
+    for form in forms[1:]:
+        tm, ln, kn, lay, wbb = results[form]
+        f_rl, _ = form_roofline(kn, w, lay, wbb, n_sm, pk, args.steps, tm / args.steps,
+                                TUNED.get(form, ((0, 0), (0, 0))))
+        line[form] = {"value": tm * 1e9 / ups_total, "unit": UNIT, "ms_per_step": tm / args.steps,
+                      "gpu_launches": ln,
+                      "layout": "SAMPLES" if lay == qisg.QISG_LAYOUT_SAMPLES else "LANES",
+                      "roofline_frac": f_rl["frac"] if f_rl else None,
+                      "vs_value": (tm * 1e9 / ups_total) / value}
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

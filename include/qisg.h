@@ -201,6 +201,28 @@ int qisg_set_couplings(qisg_handle *h, const int8_t *J);
  * the memory budget and freed before returning.                           */
 int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, uint64_t sweep);
 
+/* Test entry: one explicit PT pass (Sec. 2.1) of every chain through the
+ * handle's own PT kernel, on integer energies given by the caller instead of
+ * the ones counted from its configurations -- so that tests can place the
+ * acceptance test u < P wherever they choose (at, just inside and just
+ * outside the kernel's float shortcut margin) and compare the permutation
+ * with an independent evaluation of the rule.
+ *   U          host int64 [n_samples][n_replicas][n_slots][2]: the
+ *              unsatisfied spatial and tau bond counts (u_s, u_t) of the
+ *              configuration of walker w (last-but-one index), i.e.
+ *              A = 2N - 2 u_s and B = N - 2 u_t; only differences enter.
+ *   walker_at  host int32 [n_samples][n_replicas][n_slots]: in, the
+ *              permutation before the pass; out, the one after it.
+ *   t          the pass draws the numbers of a PT pass after sweep t.
+ *   wide       0: energy differences in the width the lattice size selects
+ *              (32 bits when 2N < 2^30), 1: 64-bit differences.
+ * Afterwards the handle's energies and permutation no longer describe its
+ * configurations: qisg_sweep and qisg_pt_swap return ESTATE until
+ * qisg_set_state.  Synchronises.
+ * EINVAL: a count outside [0, 2^38) (or [0, 2^29) with 32-bit differences),
+ *   more than 32 slots; ECORRUPT: a row of walker_at is not a permutation. */
+int qisg_pt_given(qisg_handle *h, const int64_t *U, int32_t *walker_at, uint64_t t, int wide);
+
 /* Measurement sums since creation (or the last qisg_set_state), by slot:
  *   sumA, sumB  [n_samples][n_replicas][n_slots]  sums of A and B
  *   sumq, sumq2 [n_samples][n_slots][n_pairs]     sums of q and q^2
@@ -234,6 +256,8 @@ int qisg_launch_count(qisg_handle *h, int64_t *n);
 #define QISG_KERNEL_PT      1   /* the PT pass                                    */
 #define QISG_KERNEL_MEASURE 2   /* overlaps and measurement sums                  */
 #define QISG_KERNEL_PERMUTE 3   /* SAMPLES: moving spin bits after a PT pass       */
+#define QISG_KERNEL_BLUE    4   /* read only: the blue half sweeps (in SWEEP too)  */
+#define QISG_KERNEL_RED     5   /* read only: the red half sweeps (in SWEEP too)   */
 
 /* Start (enable = 1, counters reset) or stop (0) timing every launch of the
  * kernels above with CUDA events recorded on the handle's stream, around the
@@ -247,8 +271,9 @@ int qisg_launch_count(qisg_handle *h, int64_t *n);
 int qisg_profile(qisg_handle *h, int enable);
 
 /* Total device time (ms) of the timed launches of one kind, how many were
- * timed and how many were launched since qisg_profile(h, 1).  Synchronises.
- * EINVAL: unknown kind. */
+ * timed and how many were launched since qisg_profile(h, 1); kinds BLUE and
+ * RED split QISG_KERNEL_SWEEP by colour.  Synchronises.  EINVAL: unknown
+ * kind. */
 int qisg_profile_read(qisg_handle *h, int kind, double *total_ms, int64_t *n_timed,
                       int64_t *n_launched);
 
@@ -343,6 +368,14 @@ int qisg_batch_run(qisg_batch *b, int64_t n_sweeps);
  * largest instances first).  Results never depend on either. */
 int qisg_batch_set_schedule(qisg_batch *b, int tile_rows, int schedule);
 
+/* Bound of each grid-barrier wait of the batch kernel, in nanoseconds (0:
+ * the default, 5 s).  A wait that runs out sets the batch's error flag and
+ * every block of the launch returns; the next synchronising call on the
+ * batch returns ETIMEOUT, and the batch's state is then undefined (destroy
+ * it).  For tests of that path and for callers that want a tighter watchdog.
+ * EINVAL: wait_ns < 0. */
+int qisg_batch_set_wait_limit(qisg_batch *b, int64_t wait_ns);
+
 /* Time sweeps_per_candidate sweeps of each (tile rows, order) candidate on the
  * live batch and keep the fastest; the batch advances meanwhile. */
 int qisg_batch_autotune(qisg_batch *b, int sweeps_per_candidate, int *tile_rows, int *schedule);
@@ -383,14 +416,19 @@ void qisg_batch_destroy(qisg_batch *b);
  *          q = sum_i S^{r1}_i S^{r2}_i for pairs r1 < r2 in lexicographic
  *          order (the quantity qisg_overlaps reports).
  *   cuda_stream  cudaStream_t the work is ordered on (NULL: legacy default).
- * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture.  The call allocates nothing (no cudaMalloc, no cudaFree, no
- * allocating library routine).  All calls share the scratch array, which
- * keeps the last call's counts; each call clears the part it uses first.
- * Calls that overlap on the GPU race on the array: serialise them.
- * EINVAL: NULL pointer, word_bits not 32/64, L or L_tau odd or < 2,
- *   n_replicas < 2, or n_samples * n_slots * n_pairs > QISG_NOALLOC_MAX_COUNTS.
+ * The scratch array's device address is looked up (cudaGetSymbolAddress)
+ * on the first call made with a given device and CUDA context current, and
+ * cached per (device, context); a call whose stream is being captured uses
+ * the cache only, so make the first call on each device and context before
+ * any stream capture (ESTATE otherwise).  The call allocates nothing (no
+ * cudaMalloc, no cudaFree, no allocating library routine).  All calls share
+ * the scratch array, which keeps the last call's counts; each call clears the
+ * part it uses first.  Calls that overlap on the GPU race on the array:
+ * serialise them.
+ * EINVAL (checked before any device work): NULL pointer; word_bits not
+ *   32/64; spins not aligned to its word or q to 8 bytes; L or L_tau odd or
+ *   < 2; more than 2^31 sites; n_slots < 1, n_replicas < 2 or n_samples < 1;
+ *   n_samples * n_slots * n_pairs > QISG_NOALLOC_MAX_COUNTS.
  * Asynchronous: errors of the kernels themselves surface at the next sync. */
 #define QISG_NOALLOC_MAX_COUNTS (1 << 18)
 int qisg_overlaps_noalloc(const void *spins, int word_bits, int L, int L_tau, int n_slots,

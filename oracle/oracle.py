@@ -54,6 +54,8 @@ def _load():
             i32, i64, u64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
             lib.orc_philox4x32_10.argtypes = [P, P, P]
             lib.orc_philox4x32_10.restype = None
+            lib.orc_philox4x32_10_many.argtypes = [i64, P, P, P]
+            lib.orc_philox4x32_10_many.restype = None
             lib.orc_ladder_linear.argtypes = [f64, f64, i32, f64, P, P]
             lib.orc_ladder_linear.restype = None
             lib.orc_thresholds.argtypes = [i32, P, P, P]
@@ -100,6 +102,15 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     k = np.ascontiguousarray(key, dtype=np.uint32)
     out = np.zeros(4, dtype=np.uint32)
     _load().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def philox4x32_10_many(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of counters ctr [n][4] under one key (2 x uint32)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros_like(c)
+    _load().orc_philox4x32_10_many(len(c), _ptr(c), _ptr(k), _ptr(out))
     return out
 
 

@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kBatchBlock = 256;
 static_assert(kBatchBlock <= kLanesMaxThreads, "the LANES class-code buffer holds kLanesMaxThreads threads");
-constexpr long long kBarrierTimeoutNs = 5000000000ll;   // 5 s per wait
+constexpr long long kBarrierTimeoutNs = 5000000000ll;   // 5 s per wait (default)
 
 struct InstDev {
   unsigned long long *spins;   // [g][site]
@@ -61,9 +61,9 @@ __device__ __forceinline__ unsigned long long gtime() {
 }
 
 // Grid-wide barrier with a bounded wait: bar[0] arrivals, bar[1] generation.
-// A wait that exceeds kBarrierTimeoutNs sets *err and gives up; every block
-// checks *err after each barrier and leaves, so the launch always ends.
-__device__ bool grid_sync(unsigned *bar, int *err) {
+// A wait that exceeds wait_ns sets *err and gives up; every block checks
+// *err after each barrier and leaves, so the launch always ends.
+__device__ bool grid_sync(unsigned *bar, int *err, long long wait_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned *gen = bar + 1;
@@ -77,7 +77,7 @@ __device__ bool grid_sync(unsigned *bar, int *err) {
       const unsigned long long t0 = gtime();
       while (*gen == g) {
         if (*(volatile int *)err) break;
-        if (gtime() - t0 > (unsigned long long)kBarrierTimeoutNs) {
+        if (gtime() - t0 > (unsigned long long)wait_ns) {
           atomicExch(err, 1);
           break;
         }
@@ -130,7 +130,8 @@ __device__ __forceinline__ bool live(const InstDev &I) { return I.active && __ld
 // 512-instance uneven batch, where two blocks per SM fit without the bound).
 __global__ void __launch_bounds__(kBatchBlock, 3) batch_kernel(InstDev *insts, int n_inst, const Tile *tiles,
                                                             int n_tiles, const int *bstart, const ChainRef *chains,
-                                                            int n_chains, int n_sweeps, unsigned *bar, int *err) {
+                                                            int n_chains, int n_sweeps, unsigned *bar, int *err,
+                                                            long long wait_ns) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t lo = bstart[blockIdx.x];
   const int64_t hi = bstart[blockIdx.x + 1];
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) batch_kernel(InstDev *insts, i
         else
           batch_tile<true>(I, 1, tl.j0, tl.n, smem);
       }
-      if (!grid_sync(bar, err)) return;
+      if (!grid_sync(bar, err, wait_ns)) return;
     }
     for (int c = gwarp; c < n_chains; c += warps) {
       const ChainRef cr = chains[c];
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) batch_kernel(InstDev *insts, i
       pt_chain<false, true, true>(I.walker + cr.r * I.n_slots, I.U + (size_t)cr.r * I.n_slots * 2, I.ptc, I.sq,
                                   I.key, (uint32_t)__ldcg(&I.t), 0, cr.r, I.n_slots);
     }
-    if (!grid_sync(bar, err)) return;
+    if (!grid_sync(bar, err, wait_ns)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inst; i += gridDim.x * blockDim.x) {
       InstDev &I = insts[i];
       const long long rem = __ldcg(&I.remaining);
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) batch_kernel(InstDev *insts, i
         if (rem > 0) I.remaining = rem - 1;
       }
     }
-    if (!grid_sync(bar, err)) return;
+    if (!grid_sync(bar, err, wait_ns)) return;
   }
 }
 
@@ -280,6 +281,7 @@ struct qisg_batch {
   size_t smem = 0;
   int max_plane = 4, max_slots = 1, max_rep = 1, max_spb_groups = 1;
   int64_t launches = 0;
+  long long wait_ns = qisg::kBarrierTimeoutNs;   // bound of each grid-barrier wait
 };
 
 using namespace qisg;
@@ -600,7 +602,7 @@ int qisg_batch_run(qisg_batch *B, int64_t n_sweeps) {
   while (left > 0 && !rc) {
     int ns = (int)std::min<int64_t>(left, chunk);
     void *args[] = {&B->d_inst, &B->capacity, &B->d_tiles, &B->n_tiles, &B->d_bstart, &B->d_chains, &B->n_chains,
-                    &ns, &B->d_bar, &B->d_err};
+                    &ns, &B->d_bar, &B->d_err, &B->wait_ns};
     rc = cuda_check(cudaMemsetAsync(B->d_bar, 0, 2 * sizeof(unsigned), B->stream), "reset barrier");
     if (rc) break;
     rc = cuda_check(cudaLaunchCooperativeKernel((const void *)batch_kernel, dim3((unsigned)B->grid),
@@ -616,6 +618,12 @@ int qisg_batch_run(qisg_batch *B, int64_t n_sweeps) {
     left -= ns;
   }
   return rc;
+}
+
+int qisg_batch_set_wait_limit(qisg_batch *B, int64_t wait_ns) {
+  if (!B || wait_ns < 0) return fail(QISG_EINVAL, "bad batch or wait_ns < 0");
+  B->wait_ns = wait_ns == 0 ? kBarrierTimeoutNs : (long long)wait_ns;
+  return QISG_OK;
 }
 
 int qisg_batch_set_schedule(qisg_batch *B, int tile_rows, int schedule) {

@@ -291,7 +291,7 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   }
   for (int64_t a0 = 0; a0 < h->n_samples; a0 += (h->per_sample_launch ? 1 : 65535)) {
     const int64_t na = h->per_sample_launch ? 1 : std::min<int64_t>(65535, h->n_samples - a0);
-    const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
+    const int tok = prof_begin(h, sweep_kind(colour));
     const dim3 grid((unsigned)blocks, (unsigned)na);
     // compile-time replica count (loops unrolled) and word-group count (fewer
     // registers) for the common cases
@@ -311,7 +311,7 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
       else
         lanes_half_sweep_kernel<Word, false, 0, 0><<<grid, kBlock, smem, h->stream>>>(p, 0, count_only, a0, tile_sites);
     }
-    prof_end(h, QISG_KERNEL_SWEEP, tok);
+    prof_end(h, sweep_kind(colour), tok);
     h->launches++;
   }
   return cuda_check(cudaGetLastError(), "lanes half sweep");

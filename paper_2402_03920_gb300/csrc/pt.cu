@@ -86,9 +86,9 @@ void launch_pt_samples(qisg_handle *h, uint2 key, int explicit_pass, unsigned lo
 
 }  // namespace
 
-int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a, unsigned long long *adv) {
+int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a, unsigned long long *adv, bool force_wide) {
   const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
-  const bool wide = 2 * h->N >= (int64_t(1) << 30);   // energy differences beyond 31 bits
+  const bool wide = force_wide || 2 * h->N >= (int64_t(1) << 30);   // energy differences beyond 31 bits
   const int tok = prof_begin(h, QISG_KERNEL_PT);
   if (h->layout == QISG_LAYOUT_SAMPLES) {
     if (h->W == 64) {

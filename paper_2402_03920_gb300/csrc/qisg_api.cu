@@ -69,7 +69,7 @@ void prof_end(qisg_handle *h, int kind, int tok) {
 void prof_clear(qisg_handle *h) {
   for (cudaEvent_t e : h->prof_spare) cudaEventDestroy(e);
   h->prof_spare.clear();
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kProfKinds; ++k) {
     for (cudaEvent_t e : h->prof_ev[k]) cudaEventDestroy(e);
     h->prof_ev[k].clear();
     h->prof_launched[k] = 0;
@@ -465,9 +465,9 @@ int build_cycle(qisg_handle *h, int C) {
   const int64_t meas0 = h->n_meas, launches0 = h->launches;
   const bool pending0 = h->perm_pending;
   void *const spins0 = h->spins;
-  int64_t pl0[4];
-  size_t ev0[4];
-  for (int k = 0; k < 4; ++k) {
+  int64_t pl0[kProfKinds];
+  size_t ev0[kProfKinds];
+  for (int k = 0; k < kProfKinds; ++k) {
     pl0[k] = h->prof_launched[k];
     ev0[k] = h->prof_ev[k].size();
   }
@@ -490,7 +490,7 @@ int build_cycle(qisg_handle *h, int C) {
   h->launches = launches0;
   // events recorded during capture belong to the graph's record nodes
   std::map<cudaEvent_t, std::pair<int, int>> which;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kProfKinds; ++k) {
     h->cyc_prof_launched[k] = h->prof_launched[k] - pl0[k];
     h->prof_launched[k] = pl0[k];
     for (size_t i = ev0[k]; i < h->prof_ev[k].size(); ++i) which[h->prof_ev[k][i]] = {k, (int)((i - ev0[k]) & 1)};
@@ -536,7 +536,7 @@ int build_cycle(qisg_handle *h, int C) {
     }
     if (!rc) rc = cuda_check(cudaGraphInstantiate(&h->cyc_exec, g, 0), "instantiate sweep graph");
   }
-  for (int k = 0; k < 4; ++k) {   // the capture's own events are not timings; the
+  for (int k = 0; k < kProfKinds; ++k) {   // the capture's own events are not timings; the
     for (size_t i = ev0[k]; i < h->prof_ev[k].size(); ++i)   // graph keeps them until dropped
       h->cyc_events.push_back(h->prof_ev[k][i]);
     h->prof_ev[k].resize(ev0[k]);
@@ -558,7 +558,7 @@ int replay_cycle(qisg_handle *h) {
     // fresh events for this replay's record nodes, paired as recorded
     std::vector<cudaEvent_t> fresh(h->cyc_ev_nodes.size(), nullptr);
     bool room = true;
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < kProfKinds; ++k)
       if ((int)h->prof_ev[k].size() >= 2 * kProfMaxPairs) room = false;
     for (size_t i = 0; i < fresh.size(); ++i) {
       if (room) cudaEventCreate(&fresh[i]);
@@ -572,7 +572,7 @@ int replay_cycle(qisg_handle *h) {
       for (size_t i = 0; i < fresh.size(); ++i) h->prof_ev[h->cyc_ev_kind[i].first].push_back(fresh[i]);
     else
       for (cudaEvent_t e : fresh) h->prof_spare.push_back(e);
-    for (int k = 0; k < 4; ++k) h->prof_launched[k] += h->cyc_prof_launched[k];
+    for (int k = 0; k < kProfKinds; ++k) h->prof_launched[k] += h->cyc_prof_launched[k];
   }
   const int rc = cuda_check(cudaGraphLaunch(h->cyc_exec, h->stream), "launch sweep graph");
   if (rc) return rc;
@@ -589,6 +589,7 @@ extern "C" {
 
 int qisg_sweep(qisg_handle *h, int64_t n_sweeps) {
   if (!h || n_sweeps < 0) return fail(QISG_EINVAL, "bad handle or n_sweeps < 0");
+  if (h->needs_state) return fail(QISG_ESTATE, "energies were replaced by qisg_pt_given: call qisg_set_state");
   const int C = h->use_graphs ? cycle_length(h) : 0;
   while (n_sweeps > 0) {
     int rc;
@@ -691,6 +692,7 @@ int qisg_set_tiles(qisg_handle *h, const int tile[2], const int variant[2]) {
 
 int qisg_pt_swap(qisg_handle *h) {
   if (!h) return fail(QISG_EINVAL, "NULL handle");
+  if (h->needs_state) return fail(QISG_ESTATE, "energies were replaced by qisg_pt_given: call qisg_set_state");
   if (h->t == 0) return fail(QISG_ESTATE, "no sweep has run yet");
   return h->layout != QISG_LAYOUT_SAMPLES ? lanes_pt(h, 1) : samples_pt(h, 1, 0);
 }
@@ -809,7 +811,59 @@ int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, ui
   if (!rc) {
     h->t = sweep;
     h->n_meas = 0;
+    h->needs_state = false;
   }
+  return rc;
+}
+
+int qisg_pt_given(qisg_handle *h, const int64_t *U, int32_t *walker_at, uint64_t t, int wide) {
+  if (!h || !U || !walker_at) return fail(QISG_EINVAL, "NULL argument");
+  if (wide != 0 && wide != 1) return fail(QISG_EINVAL, "wide must be 0 or 1");
+  if (h->n_slots > kMaxSlotsPT) return fail(QISG_EINVAL, "ladder longer than the PT kernel takes");
+  const bool w64 = wide || 2 * h->N >= (int64_t(1) << 30);
+  const int64_t lim = w64 ? (int64_t(1) << 38) : (int64_t(1) << 29);
+  const int64_t rows = h->n_samples * h->n_rep;
+  const int64_t n_u = rows * h->n_slots * 2;
+  for (int64_t i = 0; i < n_u; ++i)
+    if (U[i] < 0 || U[i] >= lim) return fail(QISG_EINVAL, "bond count outside the energy width");
+  std::vector<char> seen((size_t)h->n_slots);
+  for (int64_t c = 0; c < rows; ++c) {
+    std::fill(seen.begin(), seen.end(), 0);
+    for (int s = 0; s < h->n_slots; ++s) {
+      const int32_t w = walker_at[c * h->n_slots + s];
+      if (w < 0 || w >= h->n_slots || seen[(size_t)w]) return fail(QISG_ECORRUPT, "walker_at row is not a permutation");
+      seen[(size_t)w] = 1;
+    }
+  }
+  int rc = sync_handle(h);
+  if (rc) return rc;
+  const size_t n_cs = (size_t)h->n_a_pad * h->n_rep * h->n_slots;
+  std::vector<int32_t> wa(n_cs);
+  for (size_t i = 0; i < n_cs; ++i) wa[i] = (int32_t)(i % h->n_slots);
+  std::memcpy(wa.data(), walker_at, (size_t)rows * h->n_slots * 4);
+  // LANES and SITES count by walker, SAMPLES by slot
+  std::vector<unsigned long long> u(n_cs * 2, 0ull);
+  const bool by_slot = h->layout == QISG_LAYOUT_SAMPLES;
+  for (int64_t c = 0; c < rows; ++c)
+    for (int s = 0; s < h->n_slots; ++s) {
+      const int64_t src = c * h->n_slots + (by_slot ? wa[(size_t)(c * h->n_slots + s)] : s);
+      u[(size_t)(c * h->n_slots + s) * 2] = (unsigned long long)U[src * 2];
+      u[(size_t)(c * h->n_slots + s) * 2 + 1] = (unsigned long long)U[src * 2 + 1];
+    }
+  h->needs_state = true;
+  h->perm_pending = false;
+  drop_cycle(h);
+  unsigned long long tt[2] = {t + 1ull, t + 1ull};   // an explicit pass reads the sweep it follows as t + 1 - 1
+  rc = cuda_check(cudaMemcpyAsync(h->d_walker, wa.data(), n_cs * 4, cudaMemcpyHostToDevice, h->stream), "copy walker");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(h->d_U, u.data(), u.size() * 8, cudaMemcpyHostToDevice, h->stream), "copy U");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(h->d_t, tt, 16, cudaMemcpyHostToDevice, h->stream), "copy t");
+  if (!rc && h->d_acc)
+    rc = cuda_check(cudaMemsetAsync(h->d_acc, 0, (size_t)h->n_b * h->n_rep * h->n_slots * (h->W / 8), h->stream),
+                    "clear PT masks");
+  if (!rc) rc = pt_pass(h, 1, 0, h->n_samples, nullptr, wide != 0);
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(walker_at, h->d_walker, (size_t)rows * h->n_slots * 4,
+                                           cudaMemcpyDeviceToHost, h->stream), "copy walker");
+  if (!rc) rc = sync_handle(h);
   return rc;
 }
 
@@ -883,26 +937,38 @@ int qisg_profile(qisg_handle *h, int enable) {
   int rc = sync_handle(h);
   if (rc) return rc;
   if (enable) prof_clear(h);
-  h->prof = !enable ? 0 : (enable & QISG_PROFILE_ONLY) ? (enable & 0xF) : 0xF;
+  // bit 0 (the half sweeps) times both internal sweep kinds
+  const int bits = (enable & QISG_PROFILE_ONLY) ? (enable & 0xF) : 0xF;
+  h->prof = !enable ? 0 : bits | ((bits & 1) << kProfBlue);
   return QISG_OK;
 }
 
 int qisg_profile_read(qisg_handle *h, int kind, double *total_ms, int64_t *n_timed,
                       int64_t *n_launched) {
-  if (!h || kind < 0 || kind > 3) return fail(QISG_EINVAL, "bad handle or kind");
+  if (!h || kind < 0 || kind > QISG_KERNEL_RED) return fail(QISG_EINVAL, "bad handle or kind");
   int rc = sync_handle(h);
   if (rc) return rc;
+  // public kind -> internal kinds: SWEEP = red + blue, RED = internal SWEEP
+  int parts[2] = {kind, -1};
+  if (kind == QISG_KERNEL_SWEEP) parts[1] = kProfBlue;
+  if (kind == QISG_KERNEL_RED) parts[0] = QISG_KERNEL_SWEEP;
   double tot = 0.0;
-  const std::vector<cudaEvent_t> &v = h->prof_ev[kind];
-  for (size_t i = 0; i + 1 < v.size(); i += 2) {
-    float ms = 0.f;
-    rc = cuda_check(cudaEventElapsedTime(&ms, v[i], v[i + 1]), "event elapsed");
-    if (rc) return rc;
-    tot += ms;
+  int64_t timed = 0, launched = 0;
+  for (int k : parts) {
+    if (k < 0) continue;
+    const std::vector<cudaEvent_t> &v = h->prof_ev[k];
+    for (size_t i = 0; i + 1 < v.size(); i += 2) {
+      float ms = 0.f;
+      rc = cuda_check(cudaEventElapsedTime(&ms, v[i], v[i + 1]), "event elapsed");
+      if (rc) return rc;
+      tot += ms;
+    }
+    timed += (int64_t)(v.size() / 2);
+    launched += h->prof_launched[k];
   }
   if (total_ms) *total_ms = tot;
-  if (n_timed) *n_timed = (int64_t)(v.size() / 2);
-  if (n_launched) *n_launched = h->prof_launched[kind];
+  if (n_timed) *n_timed = timed;
+  if (n_launched) *n_launched = launched;
   return QISG_OK;
 }
 

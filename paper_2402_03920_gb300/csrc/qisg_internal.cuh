@@ -409,6 +409,9 @@ struct qisg_handle {
   int pt_every = 1, measure_every = 0;
   int layout = QISG_LAYOUT_LANES, W = 64, per_sample_launch = 0;
   int tau_ap = 0;   // antiperiodic along tau: the wrap tau bond has the opposite sign
+  // set by qisg_pt_given: energies and permutation no longer describe the
+  // configurations; sweeps are refused until qisg_set_state
+  bool needs_state = false;
   cudaStream_t stream = nullptr;
   size_t mem_budget = 0;
   uint64_t t = 0;          // sweeps done (host mirror of *d_t)
@@ -470,8 +473,8 @@ struct qisg_handle {
 
   // launch timing (qisg_profile)
   int prof = 0;                    // bit k: time launches of kernel kind k
-  std::vector<cudaEvent_t> prof_ev[4];   // start/stop pairs per kernel kind
-  int64_t prof_launched[4] = {0, 0, 0, 0};
+  std::vector<cudaEvent_t> prof_ev[5];   // start/stop pairs per internal kernel kind
+  int64_t prof_launched[5] = {0, 0, 0, 0, 0};
 
   // CUDA graph of one sweep cycle (lcm of the PT and measurement cadences),
   // captured on cap_stream and replayed on stream
@@ -481,7 +484,7 @@ struct qisg_handle {
   cudaGraphExec_t cyc_exec = nullptr;
   int cyc_sweeps = 0;
   int64_t cyc_launches = 0, cyc_meas = 0;
-  int64_t cyc_prof_launched[4] = {0, 0, 0, 0};
+  int64_t cyc_prof_launched[5] = {0, 0, 0, 0, 0};
   bool cyc_profiled = false;
   bool cyc_pending = false;         // perm_pending after one replay
   // event-record nodes of a profiled capture: node, kernel kind, 0 start / 1 stop
@@ -537,10 +540,16 @@ int advance_counter(qisg_handle *h);
 
 // PT pass of samples a0 .. a0+n_a-1 (pt.cu)
 // adv: SAMPLES only, advance the sweep counter after the pass (nullptr: no)
-int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a, unsigned long long *adv = nullptr);
+// force_wide: take 64-bit energy differences whatever the lattice size
+int pt_pass(qisg_handle *h, int explicit_pass, int64_t a0, int64_t n_a, unsigned long long *adv = nullptr,
+            bool force_wide = false);
 
 // Launch timing: call prof_begin(h, kind) before and prof_end(h, kind, tok)
-// after a kernel launch on h->stream.
+// after a kernel launch on h->stream.  Internal kinds: QISG_KERNEL_SWEEP
+// holds the red half sweeps, kProfBlue the blue ones (qisg_profile_read
+// reports QISG_KERNEL_SWEEP as their sum).
+constexpr int kProfBlue = 4, kProfKinds = 5;
+inline int sweep_kind(int colour) { return colour ? kProfBlue : QISG_KERNEL_SWEEP; }
 int prof_begin(qisg_handle *h, int kind);
 void prof_end(qisg_handle *h, int kind, int tok);
 

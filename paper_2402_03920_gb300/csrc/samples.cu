@@ -1431,7 +1431,7 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
     const int64_t blocks = h->n_b * h->n_slots * h->n_q * p.blocks_per_set;
     if (blocks > 0x7FFFFFFF || (int64_t)p.blocks_per_set * kBlock4 > 0x7FFFFFFF)
       return fail(QISG_EINVAL, "lattice too large for one launch");
-    const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
+    const int tok = prof_begin(h, sweep_kind(colour));
     // the blue pass loads the next site of its walk while it updates the
     // current one (measured: 4% off the production sweep, with the tuner then
     // taking walks of 4 sites)
@@ -1439,7 +1439,7 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
       launch_sweep4<true, true>(p, th, (unsigned)blocks, h->stream, 1, count_only);
     else
       launch_sweep4<false, false>(p, th, (unsigned)blocks, h->stream, 0, count_only);
-    prof_end(h, QISG_KERNEL_SWEEP, tok);
+    prof_end(h, sweep_kind(colour), tok);
     h->launches++;
     return cuda_check(cudaGetLastError(), "samples half sweep");
   }
@@ -1458,12 +1458,12 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   const int64_t blocks = sets * p.blocks_per_set;
   if (blocks > 0x7FFFFFFF || (int64_t)p.blocks_per_set * kQuads > 0x7FFFFFFF)
     return fail(QISG_EINVAL, "lattice too large for one launch");
-  const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
+  const int tok = prof_begin(h, sweep_kind(colour));
   if (colour == 1)
     launch_sweep_g<Word, true>(p, th, (unsigned)blocks, h->stream, 1, count_only);
   else
     launch_sweep<Word, false, 0>(p, th, (unsigned)blocks, h->stream, 0, count_only);
-  prof_end(h, QISG_KERNEL_SWEEP, tok);
+  prof_end(h, sweep_kind(colour), tok);
   h->launches++;
   return cuda_check(cudaGetLastError(), "samples half sweep");
 }

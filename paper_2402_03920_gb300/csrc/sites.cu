@@ -536,12 +536,12 @@ int sites_half_sweep(qisg_handle *h, int colour, int count_only) {
     cudaFuncSetAttribute(sites_half_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr_set = true;
   }
-  const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
+  const int tok = prof_begin(h, sweep_kind(colour));
   if (colour == 1)
     sites_half_sweep_kernel<true><<<(unsigned)blocks, kBlock, smem, h->stream>>>(p, count_only);
   else
     sites_half_sweep_kernel<false><<<(unsigned)blocks, kBlock, smem, h->stream>>>(p, count_only);
-  prof_end(h, QISG_KERNEL_SWEEP, tok);
+  prof_end(h, sweep_kind(colour), tok);
   h->launches++;
   return cuda_check(cudaGetLastError(), "sites half sweep");
 }

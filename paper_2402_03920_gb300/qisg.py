@@ -17,7 +17,7 @@ import numpy as np
 from . import _build_lib
 
 QISG_LAYOUT_AUTO, QISG_LAYOUT_LANES, QISG_LAYOUT_SAMPLES, QISG_LAYOUT_SITES = 0, 1, 2, 3
-KERNEL_SWEEP, KERNEL_PT, KERNEL_MEASURE, KERNEL_PERMUTE = 0, 1, 2, 3
+KERNEL_SWEEP, KERNEL_PT, KERNEL_MEASURE, KERNEL_PERMUTE, KERNEL_BLUE, KERNEL_RED = 0, 1, 2, 3, 4, 5
 PROFILE_ONLY = 0x100
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ECORRUPT", -6: "ESTATE"}
 
@@ -69,6 +69,7 @@ def load(build_if_missing: bool = True):
         "qisg_get_couplings": (I, [P, I64, I64, P]),
         "qisg_set_couplings": (I, [P, P]),
         "qisg_set_state": (I, [P, P, P, U64]),
+        "qisg_pt_given": (I, [P, P, P, U64, I]),
         "qisg_measurements": (I, [P, P, P, P, P, P]),
         "qisg_slot_means": (I, [P, P, P, P]),
         "qisg_thresholds": (I, [P, P]),
@@ -90,6 +91,7 @@ def load(build_if_missing: bool = True):
         "qisg_batch_retire": (I, [P, I]),
         "qisg_batch_run": (I, [P, I64]),
         "qisg_batch_set_schedule": (I, [P, I, I]),
+        "qisg_batch_set_wait_limit": (I, [P, I64]),
         "qisg_batch_autotune": (I, [P, I, P, P]),
         "qisg_batch_status": (I, [P, I, P, P]),
         "qisg_batch_results": (I, [P, I, P, P, P, P]),
@@ -99,6 +101,7 @@ def load(build_if_missing: bool = True):
         "qisg_batch_destroy": (None, [P]),
         "qisg_profile_read": (I, [P, I, P, P, P]),
         "qisg_daemon_tables": (I, [D, I, P, P]),
+        "qisg_overlaps_noalloc": (I, [P, I, I, I, I, I, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -112,14 +115,15 @@ def exported_symbols():
     """Names the binding expects the library to export."""
     return ["qisg_opts_default", "qisg_ladder_linear", "qisg_create", "qisg_sweep", "qisg_pt_swap",
             "qisg_energies", "qisg_overlaps", "qisg_permutation", "qisg_get_spins",
-            "qisg_get_couplings", "qisg_set_couplings", "qisg_set_state", "qisg_measurements",
+            "qisg_get_couplings", "qisg_set_couplings", "qisg_set_state", "qisg_pt_given", "qisg_measurements",
             "qisg_slot_means", "qisg_thresholds", "qisg_sweep_count", "qisg_layout",
             "qisg_launch_count", "qisg_sync", "qisg_destroy", "qisg_strerror", "qisg_last_error",
             "qisg_philox4x32_10", "qisg_profile", "qisg_profile_read", "qisg_set_graphs",
             "qisg_autotune", "qisg_get_tiles", "qisg_set_tiles", "qisg_batch_create", "qisg_batch_admit", "qisg_batch_retire",
-            "qisg_batch_run", "qisg_batch_set_schedule", "qisg_batch_autotune", "qisg_batch_status",
+            "qisg_batch_run", "qisg_batch_set_schedule", "qisg_batch_set_wait_limit", "qisg_batch_autotune",
+            "qisg_batch_status",
             "qisg_batch_results", "qisg_batch_info", "qisg_batch_instance_bytes", "qisg_batch_sync",
-            "qisg_batch_destroy", "qisg_daemon_tables"]
+            "qisg_batch_destroy", "qisg_daemon_tables", "qisg_overlaps_noalloc"]
 
 
 def _check(rc: int):
@@ -298,6 +302,16 @@ class Instance:
         wa = _sized(walker_at, np.int32, n_cs, "walker_at [n_samples][n_replicas][n_slots]")
         _check(load().qisg_set_state(self._h, _ptr(S), _ptr(wa), sweep))
 
+    def pt_given(self, U: np.ndarray, walker_at: np.ndarray, t: int, wide: bool = False) -> np.ndarray:
+        """One PT pass of the handle's PT kernel on given bond counts U
+        [n_samples][n_replicas][n_slots walkers][2]; returns the permutation
+        after the pass (test entry: the handle then needs set_state)."""
+        n_cs = self.n_samples * self.n_rep * self.n_slots
+        U = _sized(U, np.int64, n_cs * 2, "U [n_samples][n_replicas][n_slots][2]")
+        wa = _sized(walker_at, np.int32, n_cs, "walker_at [n_samples][n_replicas][n_slots]").copy()
+        _check(load().qisg_pt_given(self._h, _ptr(U), _ptr(wa), t, int(bool(wide))))
+        return wa.reshape(self.n_samples, self.n_rep, self.n_slots)
+
     def measurements(self):
         ncs = (self.n_samples, self.n_rep, self.n_slots)
         nq = (self.n_samples, self.n_slots, max(self.n_pairs, 1))
@@ -452,6 +466,10 @@ class Batch:
 
     def set_schedule(self, tile_rows: int, schedule: int):
         _check(load().qisg_batch_set_schedule(self._b, tile_rows, schedule))
+
+    def set_wait_limit(self, wait_ns: int):
+        """Bound of each grid-barrier wait (0: the default)."""
+        _check(load().qisg_batch_set_wait_limit(self._b, wait_ns))
 
     def autotune(self, sweeps_per_candidate: int = 2):
         r, s = ctypes.c_int(), ctypes.c_int()

@@ -102,25 +102,69 @@ def test_batch_equals_handles_and_schedule_invariance(qisg):
                 assert np.array_equal(S2, S) and np.array_equal(wa2, wa) and np.array_equal(A2, A)
 
 
+_UNEVEN_REPLAYS = {}
+
+
 @pytest.mark.parametrize("rows,order", [(16, 0), (4, 1)])
 def test_uneven_batch_full_size_sampled(qisg, rows, order):
     """The benchmark's batch (512 uneven instances, one persistent kernel) in
-    two tile schedules: after 2 sweeps, the two smallest instances and the
-    largest one are replayed by the oracle and compared bit for bit."""
+    two tile schedules: after 20 sweeps, instances covering every L and
+    every L_tau of the mix (the smallest of each) and the largest one are
+    replayed by the oracle and compared bit for bit."""
+    from concurrent.futures import ThreadPoolExecutor
     from paper_2402_03920_gb300.workloads import uneven_batch
     specs = uneven_batch(512, seed=2024, sweeps=100)
     size = [sp.L * sp.L * sp.L_tau * sp.n_slots * sp.n_replicas for sp in specs]
-    picks = sorted(range(len(specs)), key=lambda i: size[i])[:2] + [int(np.argmax(size))]
+    picks = {int(np.argmax(size))}
+    for key in ("L", "L_tau"):
+        for v in sorted({getattr(sp, key) for sp in specs}):
+            picks.add(min((i for i, sp in enumerate(specs) if getattr(sp, key) == v), key=lambda i: size[i]))
+    picks = sorted(picks)
+    assert {specs[i].L for i in picks} == {8, 12, 16, 20, 24}
+    assert {specs[i].L_tau for i in picks} == {64, 128, 256, 512, 1024}
+    n = 20
+
+    def replay(i):
+        if i not in _UNEVEN_REPLAYS:   # the same replay serves both schedules
+            sp = specs[i]
+            lad = qisg.ladder_linear(sp.k_lo, sp.k_hi, sp.n_slots, sp.gamma)
+            st = oracle.new_state(sp.L, sp.L_tau, lad[:, 0], lad[:, 1], sp.n_replicas, sp.seed)
+            _UNEVEN_REPLAYS[i] = oracle.run(st, n, n_threads=1)
+        return _UNEVEN_REPLAYS[i]
+
     with qisg.Batch(512, 0) as b:
         slots = [b.admit(sp.L, sp.L_tau, qisg.ladder_linear(sp.k_lo, sp.k_hi, sp.n_slots, sp.gamma), sp.n_replicas,
                          sp.seed) for sp in specs]
         b.set_schedule(rows, order)
-        b.run(2)
-        for i in picks:
-            sp = specs[i]
-            lad = qisg.ladder_linear(sp.k_lo, sp.k_hi, sp.n_slots, sp.gamma)
-            st = _oracle_instance(sp.L, sp.L_tau, lad, sp.n_replicas, sp.seed, 2)
+        b.run(n)
+        with ThreadPoolExecutor(max_workers=len(picks)) as ex:
+            states = list(ex.map(replay, picks))
+        for i, st in zip(picks, states):
             A, B, wa, S = b.results(slots[i], spins=True)
             assert np.array_equal(wa, st.walker_at[0]), i
             assert np.array_equal(S, st.S[0]), i
             assert np.array_equal(A, st.A[0]) and np.array_equal(B, st.B[0]), i
+
+
+def test_barrier_wait_runs_out(qisg):
+    """A grid-barrier wait bounded to 1 ns runs out (the blocks of the
+    persistent launch never reach a barrier together that fast): the launch
+    ends and the next synchronising call reports ETIMEOUT.  A fresh batch
+    then runs normally and matches the oracle.  Nothing here waits unbounded
+    or faults: the kernel gives up and returns."""
+    lad = qisg.ladder_linear(0.2, 0.5, 16, 1.0)
+    with qisg.Batch(8, 256 << 20) as b:
+        for i in range(6):
+            b.admit(16, 64, lad, 4, 40 + i)
+        b.set_wait_limit(1)
+        b.run(50)
+        with pytest.raises(qisg.QisgError) as e:
+            b.sync()
+        assert e.value.code == -4
+    with qisg.Batch(2, 64 << 20) as b:
+        s = b.admit(8, 16, lad, 4, 41)
+        b.run(6)
+        b.sync()
+        A, B, wa, S = b.results(s, spins=True)
+        st = _oracle_instance(8, 16, lad, 4, 41, 6)
+        assert np.array_equal(S, st.S[0]) and np.array_equal(wa, st.walker_at[0])

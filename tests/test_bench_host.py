@@ -17,27 +17,56 @@ def test_job_value_is_slowest_rank_over_all_updates():
     assert bench.rank_seed(7, 0) == 7 and bench.rank_seed(7, 3) != bench.rank_seed(7, 2)
 
 
-def test_roofline_from_event_timing():
+def test_roofline_from_plain_time_and_shares():
+    """Per-kernel durations come from the plain step time split by each
+    kind's share of the event-pair pass, so launches x duration fits in the
+    timed step; red and blue are reported apart, the larger share first."""
     from paper_2402_03920_gb300 import qisg
     w = bench.workload()
     steps = 4
-    launches = 2 * bench.SWEEPS_PER_STEP * steps          # red and blue per sweep
-    kern = {"sweep": {"timed": launches, "launched": launches, "ms": launches * 0.02}}   # 20 us each
+    per_kind = bench.SWEEPS_PER_STEP * steps                 # one red and one blue launch per sweep
+    # event-pair pass: red 30 us, blue 50 us, PT 20 us per launch (shares 0.3, 0.5, 0.2)
+    kern = {"red": {"timed": per_kind, "launched": per_kind, "ms": per_kind * 0.03},
+            "blue": {"timed": per_kind, "launched": per_kind, "ms": per_kind * 0.05},
+            "pt": {"timed": per_kind, "launched": per_kind, "ms": per_kind * 0.02}}
     pk = {"sm_max_mhz": 2000.0}
-    rl = bench.roofline(kern, w, qisg.QISG_LAYOUT_SAMPLES, 32, 100, pk, steps)
-    ups = bench.updates_per_step(w) * steps / launches
+    ms_per_step = 0.4                                        # plain: 40 us per sweep
+    rl, by = bench.form_roofline(kern, w, qisg.QISG_LAYOUT_SAMPLES, 32, 100, pk, steps, ms_per_step,
+                                 ((1, 4), (0, 0)))
+    assert rl is by["blue"] and rl["share"] == pytest.approx(0.5)
+    assert by["red"]["avg_launch_us"] == pytest.approx(12.0) and rl["avg_launch_us"] == pytest.approx(20.0)
+    for k in by.values():   # launches x duration within the plain step
+        assert k["launches_per_step"] * k["avg_launch_us"] <= 1000 * ms_per_step + 1e-9
+    ups = bench.updates_per_step(w) / bench.SWEEPS_PER_STEP
     assert rl["updates_per_launch"] == pytest.approx(ups)
-    assert rl["avg_launch_us"] == pytest.approx(20.0)
     assert rl["achieved"] == pytest.approx(bench.ALG_OPS["samples32"] * ups / 20e-6 / 1e12)
     assert rl["peak"] == pytest.approx(100 * bench.INT_LANES_PER_CLK_PER_SM * 2000e6 / 1e12)
     assert rl["frac"] == pytest.approx(rl["achieved"] / rl["peak"])
     assert rl["bound"] == "alu" and rl["unit"] == "Tops/s"
+    assert rl["kernel"] == "samples_sweep4_kernel" and by["red"]["kernel"] == "samples_red_fused_kernel"
     assert "derived" in bench.alu_peak_source(100, pk, "measured")
     # the algorithmic cost per update: 40 word operations per word plus a
     # quarter Philox call (about 50 operations) per replica quad's word
     assert bench.ALG_OPS["samples32"] == pytest.approx(40 / 32 + 50 / 128)
-    kern["sweep"]["timed"] = 0
-    assert bench.roofline(kern, w, qisg.QISG_LAYOUT_SAMPLES, 32, 100, pk, steps) is None
+    kern["red"]["launched"] = kern["blue"]["launched"] = 0
+    assert bench.form_roofline(kern, w, qisg.QISG_LAYOUT_SAMPLES, 32, 100, pk, steps, ms_per_step,
+                               ((1, 4), (0, 0)))[0] is None
+
+
+def test_traffic_only_from_matching_kernel_sources(tmp_path, monkeypatch):
+    """DRAM traffic from an ncu summary is taken only for the kernel sources
+    it was captured on."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    digest = bench.source_digest()
+    (prof / "dram_traffic.md").write_text(
+        "| kernel | workload | bytes per launch | source digest |\n|---|---|---|---|\n"
+        f"| `k1` | wl | 1234.5 | {digest} |\n| `k2` | wl | 99 | 0000000000000000 |\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_digest", lambda: digest)
+    assert bench.captured_traffic("k1", "wl") == pytest.approx(1234.5)
+    assert bench.captured_traffic("k2", "wl") is None
+    assert bench.captured_traffic("k1", "other") is None
 
 
 class _Done:

@@ -113,8 +113,11 @@ def test_arbitrary_state_against_oracle(qisg, W, n_rep, n_a):
 
 def test_production_shape_batched_sampled(qisg):
     """32 samples, L=16, L_tau=256, 16 slots, in the batched form the
-    benchmark times (SAMPLES, 32-bit words): samples 0 and 31 replayed by
-    the oracle, all samples against the per-instance LANES form."""
+    benchmark times (SAMPLES, 32-bit words, measurements every 10 sweeps):
+    samples 0 and 31 replayed by the oracle after 6 and after 30 sweeps
+    (spins, energies, permutation and their measurement sums), and all
+    samples against the per-instance LANES form."""
+    from concurrent.futures import ThreadPoolExecutor
     from paper_2402_03920_gb300.workloads import PRODUCTION as w
     a, ladder = make(qisg, w.L, w.L_tau, w.k_lo, w.k_hi, w.n_slots, w.gamma, w.n_replicas,
                      w.n_samples, w.seed, layout=qisg.QISG_LAYOUT_SAMPLES,
@@ -122,14 +125,23 @@ def test_production_shape_batched_sampled(qisg):
     b, _ = make(qisg, w.L, w.L_tau, w.k_lo, w.k_hi, w.n_slots, w.gamma, w.n_replicas,
                 w.n_samples, w.seed, word_bits=64, layout=qisg.QISG_LAYOUT_LANES,
                 per_sample_launch=1, measure_every=w.measure_every)
+    states = {s: oracle_state(ladder, w.L, w.L_tau, w.n_replicas, w.seed, s, 1) for s in (0, 31)}
+
+    def advance(item, n):
+        return oracle.run(item, n, measure_every=w.measure_every, n_threads=1)
+
     with a, b:
         assert a.layout() == (qisg.QISG_LAYOUT_SAMPLES, 32)
-        a.sweep(6)
-        for s in (0, 31):
-            st = oracle_state(ladder, w.L, w.L_tau, w.n_replicas, w.seed, s, 1)
-            oracle.run(st, 6, measure_every=w.measure_every)
-            assert_same_state(a, st, a_lo=s, what=f"sample {s}")
-        a.sweep(24)
+        for n in (6, 24):
+            a.sweep(n)
+            with ThreadPoolExecutor(max_workers=2) as ex:
+                list(ex.map(lambda st: advance(st, n), states.values()))
+            sA, sB, sq, sq2, nm = a.measurements()
+            for s, st in states.items():
+                assert_same_state(a, st, a_lo=s, what=f"sample {s} after {st.t}")
+                assert nm == st.n_meas
+                assert np.array_equal(sA[s], st.sumA[0]) and np.array_equal(sB[s], st.sumB[0])
+                assert np.array_equal(sq[s], st.sumq[0]) and np.array_equal(sq2[s], st.sumq2[0])
         b.sweep(30)
         assert np.array_equal(a.permutation(), b.permutation())
         assert np.array_equal(a.energies()[0], b.energies()[0])
@@ -141,8 +153,9 @@ def test_production_shape_batched_sampled(qisg):
 
 def test_batched_full_size_sampled(qisg):
     """1024 samples x 4 replicas x 32 slots, L=24, L_tau=512 (4.8 GB of
-    packed spins): 8 samples chosen by a fixed seed are replayed by the
-    oracle for 2 sweeps."""
+    packed spins), in the launch form the benchmark times: 8 samples chosen
+    by a fixed seed are replayed by the oracle for the benchmark's 20
+    sweeps."""
     from paper_2402_03920_gb300.workloads import BATCHED as w
     inst, ladder = make(qisg, w.L, w.L_tau, w.k_lo, w.k_hi, w.n_slots, w.gamma, w.n_replicas,
                         w.n_samples, w.seed, word_bits=64, layout=qisg.QISG_LAYOUT_SAMPLES)
@@ -151,10 +164,10 @@ def test_batched_full_size_sampled(qisg):
 
     def replay(s):
         st = oracle_state(ladder, w.L, w.L_tau, w.n_replicas, w.seed, s, 1)
-        return oracle.run(st, 2, n_threads=1)
+        return oracle.run(st, 20, n_threads=1)
 
     with inst:
-        inst.sweep(2)
+        inst.sweep(20)
         with ThreadPoolExecutor(max_workers=8) as ex:
             states = list(ex.map(replay, picks))
         for s, st in zip(picks, states):

@@ -55,3 +55,50 @@ def test_alone_equals_mix_and_oracle():
         st = oracle.new_state(r.L, r.L_tau, lad[:, 0], lad[:, 1], r.n_replicas, r.seed)
         oracle.run(st, r.sweeps)
         assert np.array_equal(res.spins, st.S[0]) and np.array_equal(res.walker_at, st.walker_at[0]), r.rid
+
+
+def test_full_size_stream_sampled_replay():
+    """A Poisson stream of the full request distribution (L 8..24, L_tau
+    32..1024, 8..32 slots, Gamma in [0.8, 1.2]) through the serving loop,
+    with each request's sweep count capped by an update budget so that the
+    oracle can replay it; 16 completed requests, chosen by a fixed seed and
+    always including the largest L and the largest L_tau, are replayed by
+    the oracle (one host core each) and compared bit for bit."""
+    need_gpu()
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2402_03920_gb300 import qisg
+    from paper_2402_03920_gb300.serving import Request, Server
+    from paper_2402_03920_gb300.workloads import poisson_requests
+    budget = 1.2e9   # spin updates per replayed request
+    reqs = []
+    for i, sp in enumerate(poisson_requests(64, rate=400.0, seed=11)):
+        per_sweep = sp.L * sp.L * sp.L_tau * sp.n_slots * sp.n_replicas
+        sweeps = int(min(sp.sweeps, max(12, budget // per_sweep)))
+        reqs.append(Request(rid=i, L=sp.L, L_tau=sp.L_tau, n_slots=sp.n_slots, gamma=sp.gamma, sweeps=sweeps,
+                            seed=sp.seed, arrival=sp.arrival))
+    srv = Server(capacity=64, mem_budget=4 << 30, chunk_sweeps=25, keep_spins=True)
+    try:
+        stats = srv.serve(reqs, realtime=True)
+    finally:
+        srv.close()
+    assert stats.completed == len(reqs) and stats.max_active > 1
+    rng = np.random.default_rng(16)
+    big_L = max(range(len(reqs)), key=lambda i: (reqs[i].L, reqs[i].L_tau))
+    big_T = max(range(len(reqs)), key=lambda i: (reqs[i].L_tau, reqs[i].L))
+    rest = [i for i in range(len(reqs)) if i not in (big_L, big_T)]
+    picks = sorted({big_L, big_T, *rng.choice(rest, size=14, replace=False).tolist()})
+    assert reqs[big_L].L == 24 and reqs[big_T].L_tau == 1024
+
+    def replay(i):
+        r = reqs[i]
+        lad = qisg.ladder_linear(r.k_lo, r.k_hi, r.n_slots, r.gamma)
+        st = oracle.new_state(r.L, r.L_tau, lad[:, 0], lad[:, 1], r.n_replicas, r.seed)
+        return oracle.run(st, r.sweeps, n_threads=1)
+
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        states = list(ex.map(replay, picks))
+    for i, st in zip(picks, states):
+        res = srv.results[reqs[i].rid]
+        assert np.array_equal(res.walker_at, st.walker_at[0]), i
+        assert np.array_equal(res.spins, st.S[0]), i
+        assert np.array_equal(res.A, st.A[0]) and np.array_equal(res.B, st.B[0]), i
