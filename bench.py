@@ -355,10 +355,10 @@ def roofline(kern, ups_per_step, key, n_sm, pk, steps, ms_per_step, names, wname
             continue
         per_step = k["launched"] / steps
         dur_ms = ms_per_step * shares[kind] / per_step
-        ups_per_launch = ups_per_step / per_step
+        ups_per_launch = ups_per_step / 2 / per_step   # a half sweep updates the sites of one colour
         ops = ALG_OPS[key] * ups_per_launch
         achieved = ops / (dur_ms * 1e-3) / 1e12
-        alg_bytes = 0.25 * ups_per_launch / 2   # half of one read and one write of every spin per sweep
+        alg_bytes = 0.25 * ups_per_launch   # one read and one write of each updated spin
         out[kind] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                      "frac": achieved / peak, "traffic": captured_traffic(names[kind], wname),
                      "kernel": names[kind], "ops_per_update": ALG_OPS[key], "updates_per_launch": ups_per_launch,

@@ -98,10 +98,17 @@ typedef struct {
     int tau_antiperiodic;   /* 1 = antiperiodic boundary along tau (Sec. 1: the
                                bond from tau = L_tau-1 to tau = 0 counts -S S in
                                B); 0 = periodic                                    */
+    int history_len;        /* PT walk history (Appendix A's history_betas): keep
+                               the slot of every walker at the last history_len
+                               measurements; 0 = none                              */
+    int maxit;              /* measurements per block average (Appendix A); 0 =
+                               none                                                */
+    int blocks_len;         /* block sums kept when maxit > 0 (>= 1)               */
 } qisg_opts;
 
 /* Fill *opts with defaults: word_bits 0, NULL stream, no budget, pt_every 1,
- * measure_every 0, layout AUTO, per_sample_launch 0, tau_antiperiodic 0. */
+ * measure_every 0, layout AUTO, per_sample_launch 0, tau_antiperiodic 0,
+ * no walk history, no block sums. */
 void qisg_opts_default(qisg_opts *opts);
 
 /* Linear ladder (k_s = lo + (hi-lo) s/(n-1), both ends included; k_s = lo for
@@ -223,6 +230,56 @@ int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, ui
  *   more than 32 slots; ECORRUPT: a row of walker_at is not a permutation. */
 int qisg_pt_given(qisg_handle *h, const int64_t *U, int32_t *walker_at, uint64_t t, int wide);
 
+/* Checkpoint files.  The paper writes the configurations at every block of
+ * measurements and they serve as backups to restart from (Sec. 2.1,
+ * Appendix A); here a checkpoint holds everything a bit-exact resume needs,
+ * with a CRC over all of it.  Byte layout (little-endian integers):
+ *   offset 0    "QISGCKP1"; u32 version = 1; u32 header bytes = 128
+ *          16   i32 L, L_tau, n_slots, n_replicas; i64 n_samples; u64 seed;
+ *               u64 sweep; i64 n_meas; i32 pt_every, measure_every,
+ *               tau_antiperiodic, rule (0 threshold table, 1 daemon bits);
+ *               zeros up to byte 128
+ *   then        the ladder, n_slots x (f64 k, f64 k_tau) (IEEE bits)
+ *               couplings int8 [n_samples][L*L][2], +-1
+ *               spins by walker, one bit each (1 <=> -1), bit i of the
+ *                 sequence [n_samples][n_replicas][n_slots][N] at bit
+ *                 i % 8 of byte i / 8, padded with zero bits to a byte
+ *               walker_at i32 [n_samples][n_replicas][n_slots]
+ *               measurement sums i64: sumA, sumB [n_samples][n_replicas]
+ *                 [n_slots]; sumq, sumq2 [n_samples][n_slots][n_pairs]
+ *   last        u32 CRC-32 (IEEE 802.3: reflected polynomial 0xEDB88320,
+ *               initial value and final complement 0xFFFFFFFF) of every
+ *               byte before it
+ * The walk history and block sums are not stored: after a load they hold
+ * the measurements taken from then on. */
+typedef struct {
+    int L, L_tau, n_slots, n_replicas;
+    int64_t n_samples;
+    uint64_t seed, sweep;
+    int64_t n_meas;
+    int pt_every, measure_every, tau_antiperiodic, rule;
+} qisg_checkpoint_info;
+
+/* Write the handle's state to `path` (through path.tmp, renamed when
+ * complete).  The spins are read back in chunks of at most 256 MB.
+ * Synchronises.  EINVAL: the file cannot be written. */
+int qisg_checkpoint_save(qisg_handle *h, const char *path);
+
+/* Check a checkpoint file on the host only (no device work): header, sizes
+ * and CRC; fills *info (may be NULL).  ECORRUPT: bad magic or version,
+ * inconsistent sizes, truncated or extended file, CRC mismatch; EINVAL: the
+ * file cannot be opened. */
+int qisg_checkpoint_verify(const char *path, qisg_checkpoint_info *info);
+
+/* Resume from a checkpoint: the file is checked first (ECORRUPT as above,
+ * before the handle is touched), must describe this handle's problem (same
+ * lattice, ladder bits, replicas, samples, seed, cadences, boundary and
+ * rule; EINVAL otherwise; any packing or word width), and then replaces the
+ * couplings, spins, permutation, sweep counter and measurement sums, so the
+ * run continues bit for bit as if uninterrupted.  Unpacks the spins into a
+ * host buffer of one byte per spin.  Synchronises. */
+int qisg_checkpoint_load(qisg_handle *h, const char *path);
+
 /* Measurement sums since creation (or the last qisg_set_state), by slot:
  *   sumA, sumB  [n_samples][n_replicas][n_slots]  sums of A and B
  *   sumq, sumq2 [n_samples][n_slots][n_pairs]     sums of q and q^2
@@ -236,6 +293,31 @@ int qisg_measurements(qisg_handle *h, int64_t *sumA, int64_t *sumB, int64_t *sum
  * the integer sums are added in the fixed order sample, replica (pair).
  * Host double arrays of n_slots.  ESTATE: no measurement yet.             */
 int qisg_slot_means(qisg_handle *h, double *e_s, double *e_t, double *q2);
+
+/* PT walk history (Appendix A: at every measurement the state of the
+ * parallel-tempering random walk, i.e. the value of k of every system copy,
+ * is collected in history_betas for the equilibration test):
+ * slot_of[i][a][r][w] = the ladder slot of walker w of chain (a, r) at
+ * measurement first + i (measurements counted from creation or the last
+ * qisg_set_state / qisg_checkpoint_load).  Host uint8
+ * [n][n_samples][n_replicas][n_slots].  Synchronises.
+ * ESTATE: history_len = 0, or a requested measurement is not (yet, or no
+ * longer) among the last history_len.                                       */
+int qisg_walk_history(qisg_handle *h, int64_t first, int64_t n, uint8_t *slot_of);
+
+/* Block sums (Appendix A: maxit consecutive energy measurements are
+ * averaged and written out): sumA[i][a][r][s] and sumB[i][a][r][s], by slot,
+ * over the measurements first_block*maxit ... of blocks first .. first+n-1.
+ * Host int64 [n][n_samples][n_replicas][n_slots].  Only complete blocks
+ * among the last blocks_len are available (ESTATE otherwise, or when
+ * maxit = 0).  Synchronises.                                                */
+int qisg_block_sums(qisg_handle *h, int64_t first, int64_t n, int64_t *sumA, int64_t *sumB);
+
+/* FP64 block averages per slot: e_s[i][s] = <A>/(2N), e_t[i][s] = <B>/N over
+ * the samples, replicas and maxit measurements of block first + i, the
+ * integer sums added in the fixed order sample, replica.  Host double
+ * [n][n_slots].  Errors as qisg_block_sums.                                 */
+int qisg_block_means(qisg_handle *h, int64_t first, int64_t n, double *e_s, double *e_t);
 
 /* The uint32 Metropolis table in use: T[s][u_s][u_t] (u_s unsatisfied
  * spatial bonds 0..4, u_t unsatisfied tau bonds 0..2); a spin flips iff
@@ -331,14 +413,17 @@ int qisg_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, 
 typedef struct qisg_batch qisg_batch;
 
 /* One instance: an L x L x L_tau prism with its own ladder, n_replicas
- * replicas, one disorder sample drawn from `seed`, and a sweep target
- * (0 = no limit).  Its trajectory is that of qisg_create(L, L_tau, ladder,
- * n_slots, n_replicas, 1, seed) with pt_every = 1. */
+ * replicas, one disorder sample drawn from `seed`, a sweep target (0 = no
+ * limit) and its boundary along tau (tau_antiperiodic 1: the bond from
+ * tau = L_tau-1 to tau = 0 counts -S S, Sec. 1; 0: periodic).  Its
+ * trajectory is that of qisg_create(L, L_tau, ladder, n_slots, n_replicas,
+ * 1, seed) with pt_every = 1 and the same tau_antiperiodic. */
 typedef struct {
     int L, L_tau, n_slots, n_replicas;
     const qisg_slot *ladder;    /* host array of n_slots (copied at admission) */
     uint64_t seed;
     int64_t n_sweeps;
+    int tau_antiperiodic;
 } qisg_instance_desc;
 
 /* A batch with `capacity` instance slots whose device state lives in one
@@ -349,7 +434,7 @@ int qisg_batch_create(qisg_batch **out, int capacity, size_t mem_budget, void *c
 /* Admit an instance into a free slot: its state is allocated from the arena
  * and initialised on the device (Sec. 2.1 start: random spins, walker w at
  * slot w).  EINVAL: bad descriptor (L even 2..128, L_tau even, 1..32 slots,
- * 1 .. 2*(64/n_slots) replicas); ENOMEM: no free slot or the arena has no room -- the
+ * 1 .. 2*(64/n_slots) replicas, tau_antiperiodic 0 or 1); ENOMEM: no free slot or the arena has no room -- the
  * caller keeps the request queued.  Synchronises. */
 int qisg_batch_admit(qisg_batch *b, const qisg_instance_desc *d, int *slot);
 

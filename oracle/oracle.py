@@ -67,7 +67,8 @@ def _load():
             lib.orc_init_spins.argtypes = [i32, i32, i32, i32, i64, i64, u64, P]
             lib.orc_init_spins.restype = None
             lib.orc_run.argtypes = [i32, i32, i32, i32, i64, i64, u64, P, P, i32, i32,
-                                    P, P, P, u64, i64, P, P, P, P, P, P, P, i32, i32, P]
+                                    P, P, P, u64, i64, P, P, P, P, P, P, P, i32, i32, P,
+                                    P, i32, P, P]
             lib.orc_run.restype = i32
             lib.orc_energies.argtypes = [i32, i32, i32, i32, i64, P, P, P, P, i32]
             lib.orc_energies.restype = None
@@ -267,6 +268,11 @@ class OracleState:
     n_meas: int = 0
     tau_ap: bool = False     # antiperiodic along tau
     cum: np.ndarray = None   # daemon rule: [n_slots][255] cumulative tables; None: thresholds
+    keep_history: bool = False   # record the PT walk at every measurement (history_betas)
+    maxit: int = 0               # measurements per block sum (0: none)
+    hist: np.ndarray = None      # [n_meas][n_a][n_rep][n_slots] uint8: slot of every walker
+    blkA: np.ndarray = None      # [n_blocks][n_a][n_rep][n_slots] by slot: block sums
+    blkB: np.ndarray = None
 
     @property
     def n_slots(self) -> int:
@@ -315,17 +321,39 @@ def alloc_obs(st: OracleState) -> None:
     st.sumq2 = np.zeros_like(st.sumq)
 
 
+def _grow(arr, rows: int, shape_tail, dtype):
+    """arr with at least `rows` leading rows (new rows zero)."""
+    if arr is not None and arr.shape[0] >= rows:
+        return arr
+    out = np.zeros((max(rows, 1),) + tuple(shape_tail), dtype=dtype)
+    if arr is not None:
+        out[: arr.shape[0]] = arr
+    return out
+
+
 def run(st: OracleState, n_sweeps: int, pt_every: int = 1, measure_every: int = 0,
         n_threads: int = 0) -> OracleState:
     """Advance the state by n_sweeps sweeps (in place)."""
     lib = _load()
     n_meas = ctypes.c_int64(st.n_meas)
+    new_meas = 0
+    if measure_every > 0:
+        new_meas = (st.t + n_sweeps) // measure_every - st.t // measure_every
+    tail = (st.n_a, st.n_rep, st.n_slots)
+    if st.keep_history:
+        st.hist = _grow(st.hist, st.n_meas + new_meas, tail, np.uint8)
+    if st.maxit > 0:
+        nb = -(-(st.n_meas + new_meas) // st.maxit)
+        st.blkA = _grow(st.blkA, nb, tail, np.int64)
+        st.blkB = _grow(st.blkB, nb, tail, np.int64)
     rc = lib.orc_run(st.L, st.Ltau, st.n_slots, st.n_rep, st.a_lo, st.n_a, st.seed,
                      _ptr(st.k), _ptr(st.ktau), pt_every, measure_every,
                      _ptr(st.J), _ptr(st.S), _ptr(st.walker_at), st.t, n_sweeps,
                      _ptr(st.A), _ptr(st.B), _ptr(st.sumA), _ptr(st.sumB),
                      _ptr(st.sumq), _ptr(st.sumq2), ctypes.byref(n_meas), n_threads, int(st.tau_ap),
-                     _ptr(st.cum) if st.cum is not None else None)
+                     _ptr(st.cum) if st.cum is not None else None,
+                     _ptr(st.hist) if st.keep_history else None, int(st.maxit),
+                     _ptr(st.blkA) if st.maxit > 0 else None, _ptr(st.blkB) if st.maxit > 0 else None)
     if rc == -2:
         raise ValueError("the daemon rule needs k_tau = k, L_tau % 64 == 0 and fewer than 2^24 samples")
     if rc != 0:

@@ -452,12 +452,21 @@ static void pt_pass(const orc_model *m, int64_t a, int r, uint64_t t,
  * boundary along tau (0: periodic).  daemon_cum: NULL for the threshold
  * rule; else the daemon rule with the cumulative tables [n_slots][255] of
  * Sec. 2.1.1 (needs k_tau = k for every slot and L_tau a multiple of 64).
+ *
+ * Records of Appendix A, indexed by the measurement number m (counted from
+ * *n_meas on entry, which is the number of measurements already taken):
+ *   hist      [m][n_a][n_rep][n_slots]  (NULL: not kept) history_betas: the
+ *             slot, i.e. the ladder value k, of every walker (system copy)
+ *   blkA/B    [m / maxit][n_a][n_rep][n_slots] by slot (NULL or maxit 0: not
+ *             kept): sums of A and B over the maxit consecutive
+ *             measurements of each block, whose averages are written out
  */
 int orc_run(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64_t n_a, uint64_t seed,
             const double *k, const double *ktau, int pt_every, int measure_every,
             const int8_t *J, int8_t *S, int32_t *walker_at, uint64_t t0, int64_t n_sweeps,
             int64_t *A, int64_t *B, int64_t *sumA, int64_t *sumB, int64_t *sumq, int64_t *sumq2,
-            int64_t *n_meas, int n_threads, int tau_ap, const uint64_t *daemon_cum)
+            int64_t *n_meas, int n_threads, int tau_ap, const uint64_t *daemon_cum,
+            uint8_t *hist, int maxit, int64_t *blkA, int64_t *blkB)
 {
     orc_model m;
     uint32_t *T;
@@ -466,6 +475,7 @@ int orc_run(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64_t n_a, 
     int n_pairs = n_rep * (n_rep - 1) / 2;
     int64_t ai;
     int64_t meas_total = 0;
+    const int64_t meas0 = n_meas ? *n_meas : 0;
 
     T = (uint32_t *)malloc(sizeof(uint32_t) * 15 * (size_t)n_slots);
     ap = (double *)malloc(sizeof(double) * 4 * (size_t)(n_slots > 1 ? n_slots : 2));
@@ -532,6 +542,24 @@ int orc_run(int L, int Ltau, int n_slots, int n_rep, int64_t a_lo, int64_t n_a, 
                             sumq[(ai * n_slots + s) * n_pairs + p] += q;
                             sumq2[(ai * n_slots + s) * n_pairs + p] += q * q;
                         }
+                }
+                {
+                    const int64_t mi = meas0 + local_meas;
+                    if (hist)   /* the PT walk: where every walker is now */
+                        for (r = 0; r < n_rep; ++r)
+                            for (s = 0; s < n_slots; ++s)
+                                hist[((mi * n_a + ai) * n_rep + r) * n_slots + wa[r * n_slots + s]] = (uint8_t)s;
+                    if (blkA && blkB && maxit > 0) {   /* block sums of maxit measurements */
+                        const int64_t bi = mi / maxit;
+                        const int first = mi % maxit == 0;
+                        for (r = 0; r < n_rep; ++r)
+                            for (s = 0; s < n_slots; ++s) {
+                                const int64_t idx = ((bi * n_a + ai) * n_rep + r) * n_slots + s;
+                                w = wa[r * n_slots + s];
+                                blkA[idx] = (first ? 0 : blkA[idx]) + Aw[r * n_slots + w];
+                                blkB[idx] = (first ? 0 : blkB[idx]) + Bw[r * n_slots + w];
+                            }
+                    }
                 }
                 ++local_meas;
             }

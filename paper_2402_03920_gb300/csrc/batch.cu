@@ -43,6 +43,7 @@ struct InstDev {
   uint2 key;
   FastDiv hpd;
   int L, Lt, plane, half_plane, n_slots, n_rep, rpw, n_groups, spb, N;
+  int tau_ap;   // antiperiodic along tau: the wrap tau bond flips sign
   int active;
 };
 
@@ -112,7 +113,7 @@ __device__ void batch_tile(const InstDev &I, int colour, int j0, int n, unsigned
   S.n_rep = I.n_rep;
   S.rpw = I.rpw;
   S.n_groups = I.n_groups;
-  S.tau_ap = 0;   // batched instances are periodic along tau
+  S.tau_ap = I.tau_ap;
   if (I.n_rep == 4)   // the common case (every uneven-batch and serving instance): loops unrolled
     lanes_tile<unsigned long long, true, BLUE, 4>(S, colour, j0, n, 0, colour == 0 && j0 == 0, smem);
   else
@@ -458,6 +459,7 @@ int setup_slot(qisg_batch *B, int i) {
   I.n_groups = n_groups;
   I.spb = kBatchBlock / n;
   I.N = (int)N;
+  I.tau_ap = d.tau_antiperiodic;
   I.active = 1;
   S.done = 0;
   int rc = cuda_check(cudaMemcpyAsync(base + o_T, T.data(), T.size() * 4, cudaMemcpyHostToDevice, B->stream), "T");
@@ -489,6 +491,7 @@ int check_desc(const qisg_instance_desc *d) {
     return fail(QISG_EINVAL, "n_replicas must be 1 .. 2 * (64 / n_slots)");
   if ((int64_t)d->L * d->L * d->L_tau > ((int64_t)1 << 30)) return fail(QISG_EINVAL, "instance too large");
   if (d->n_sweeps < 0) return fail(QISG_EINVAL, "n_sweeps < 0");
+  if (d->tau_antiperiodic != 0 && d->tau_antiperiodic != 1) return fail(QISG_EINVAL, "tau_antiperiodic must be 0 or 1");
   for (int s = 0; s < d->n_slots; ++s)
     if (!std::isfinite(d->ladder[s].k) || !std::isfinite(d->ladder[s].k_tau) || d->ladder[s].k < 0 ||
         d->ladder[s].k_tau < 0)

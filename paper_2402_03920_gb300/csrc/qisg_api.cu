@@ -195,6 +195,10 @@ int sync_handle(qisg_handle *h) {
 
 }  // namespace
 
+namespace qisg {
+int handle_sync(qisg_handle *h) { return sync_handle(h); }
+}  // namespace qisg
+
 extern "C" {
 
 void qisg_opts_default(qisg_opts *o) {
@@ -248,6 +252,8 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
         return fail(QISG_EINVAL, "the daemon rule needs k_tau = k <= 16 at every slot");
   }
   if (o.tau_antiperiodic != 0 && o.tau_antiperiodic != 1) return fail(QISG_EINVAL, "tau_antiperiodic must be 0 or 1");
+  if (o.history_len < 0 || o.maxit < 0 || o.blocks_len < 0) return fail(QISG_EINVAL, "negative record length");
+  if (o.maxit > 0 && o.blocks_len < 1) return fail(QISG_EINVAL, "maxit > 0 needs blocks_len >= 1");
 
   qisg_handle *h = new (std::nothrow) qisg_handle();
   if (!h) return fail(QISG_ENOMEM, "host allocation");
@@ -264,6 +270,9 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   h->mem_budget = o.mem_budget;
   h->per_sample_launch = o.per_sample_launch;
   h->tau_ap = o.tau_antiperiodic;
+  h->hist_len = o.history_len;
+  h->maxit = o.maxit;
+  h->blk_len = o.maxit > 0 ? o.blocks_len : 0;
   h->k.resize(n_slots);
   h->kt.resize(n_slots);
   for (int s = 0; s < n_slots; ++s) {
@@ -338,6 +347,11 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc) rc = dalloc(h, &h->d_out, (size_t)2 * n_chain_slots * 8 + qn * 8);
   if (!rc) rc = dalloc(h, &h->d_t, 16);
   if (!rc) rc = dalloc(h, &h->d_err, 4);
+  if (!rc) rc = dalloc(h, &h->d_meas, 8);
+  const size_t n_rows = (size_t)n_samples * n_replicas * n_slots;
+  if (!rc && h->hist_len) rc = dalloc(h, &h->d_hist, (size_t)h->hist_len * n_rows);
+  if (!rc && h->blk_len) rc = dalloc(h, &h->d_blkA, (size_t)h->blk_len * n_rows * 8);
+  if (!rc && h->blk_len) rc = dalloc(h, &h->d_blkB, (size_t)h->blk_len * n_rows * 8);
   if (!rc && layout == QISG_LAYOUT_SAMPLES)
     rc = dalloc(h, &h->d_acc, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8));
   if (!rc && layout == QISG_LAYOUT_SITES) rc = dalloc(h, &h->d_dcum, (size_t)n_slots * 256 * 8);
@@ -376,6 +390,7 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_q, 0, qn * 8, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_t, 0, 16, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_err, 0, 4, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_meas, 0, 8, h->stream), "memset");
   if (!rc && h->d_acc)
     rc = cuda_check(cudaMemsetAsync(h->d_acc, 0, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8), h->stream),
                     "memset");
@@ -419,6 +434,7 @@ int one_sweep(qisg_handle *h, cudaEvent_t *ev = nullptr) {
   }
   if (!rc && h->measure_every > 0 && (t + 1) % (uint64_t)h->measure_every == 0) {
     rc = sites ? sites_measure(h, 0) : lanes ? lanes_measure(h, 0) : samples_measure(h, 0);
+    if (!rc && (h->hist_len || h->maxit)) rc = record_measurement(h);
     h->n_meas++;
   }
   if (!rc) {
@@ -806,11 +822,13 @@ int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, ui
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumq, 0, qn * 8, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_sumq2, 0, qn * 8, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_q, 0, qn * 8, h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_meas, 0, 8, h->stream), "memset");
   if (!rc) rc = recompute_energies(h);
   if (!rc) rc = sync_handle(h);
   if (!rc) {
     h->t = sweep;
     h->n_meas = 0;
+    h->rec_base = 0;
     h->needs_state = false;
   }
   return rc;
@@ -981,7 +999,8 @@ void qisg_destroy(qisg_handle *h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   void *ptrs[] = {h->spins, h->spins_alt, h->J, h->d_T, h->d_bases, h->d_sq, h->d_ptc, h->d_walker, h->d_U, h->d_sumA, h->d_sumB,
-                  h->d_sumq, h->d_sumq2, h->d_q, h->d_out, h->d_t, h->d_acc, h->d_err, h->d_dcum, h->d_dlut};
+                  h->d_sumq, h->d_sumq2, h->d_q, h->d_out, h->d_t, h->d_acc, h->d_err, h->d_dcum, h->d_dlut,
+                  h->d_meas, h->d_hist, h->d_blkA, h->d_blkB};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   drop_cycle(h);

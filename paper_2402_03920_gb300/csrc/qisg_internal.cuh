@@ -469,6 +469,12 @@ struct qisg_handle {
   unsigned long long *d_dcum = nullptr;   // SITES: cumulative tables [n_slots][256]
   uint2 *d_dlut = nullptr;                // SITES: prefix index [n_slots][2^kDaemonLutBits], then the spans (bytes)
   int *d_err = nullptr;
+  // records at every measurement (Appendix A): PT walk history and maxit block sums
+  int hist_len = 0, maxit = 0, blk_len = 0;
+  unsigned long long *d_meas = nullptr;   // measurements taken (device copy of n_meas)
+  uint8_t *d_hist = nullptr;              // [hist_len][n_samples][n_rep][n_slots]: slot of each walker
+  long long *d_blkA = nullptr, *d_blkB = nullptr;   // [blk_len][n_samples][n_rep][n_slots] by slot
+  int64_t rec_base = 0;                   // first measurement the rings hold (checkpoint loads start later)
   size_t device_bytes = 0;
 
   // launch timing (qisg_profile)
@@ -537,6 +543,11 @@ int samples_set_couplings(qisg_handle *h, const int8_t *J);
 
 // common small kernels (qisg_api.cu)
 int advance_counter(qisg_handle *h);
+// synchronise the handle's stream and report a device error flag
+int handle_sync(qisg_handle *h);
+
+// records of a measurement: walk history and block sums (records.cu)
+int record_measurement(qisg_handle *h);
 
 // PT pass of samples a0 .. a0+n_a-1 (pt.cu)
 // adv: SAMPLES only, advance the sweep counter after the pass (nullptr: no)

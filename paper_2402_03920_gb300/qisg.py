@@ -36,7 +36,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("word_bits", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("mem_budget", ctypes.c_size_t), ("pt_every", ctypes.c_int),
                 ("measure_every", ctypes.c_int), ("layout", ctypes.c_int),
-                ("per_sample_launch", ctypes.c_int), ("tau_antiperiodic", ctypes.c_int)]
+                ("per_sample_launch", ctypes.c_int), ("tau_antiperiodic", ctypes.c_int),
+                ("history_len", ctypes.c_int), ("maxit", ctypes.c_int), ("blocks_len", ctypes.c_int)]
 
 
 _lib = None
@@ -73,6 +74,12 @@ def load(build_if_missing: bool = True):
         "qisg_measurements": (I, [P, P, P, P, P, P]),
         "qisg_slot_means": (I, [P, P, P, P]),
         "qisg_thresholds": (I, [P, P]),
+        "qisg_walk_history": (I, [P, I64, I64, P]),
+        "qisg_checkpoint_save": (I, [P, ctypes.c_char_p]),
+        "qisg_checkpoint_load": (I, [P, ctypes.c_char_p]),
+        "qisg_checkpoint_verify": (I, [ctypes.c_char_p, P]),
+        "qisg_block_sums": (I, [P, I64, I64, P, P]),
+        "qisg_block_means": (I, [P, I64, I64, P, P]),
         "qisg_sweep_count": (I, [P, P]),
         "qisg_layout": (I, [P, P, P]),
         "qisg_launch_count": (I, [P, P]),
@@ -116,7 +123,9 @@ def exported_symbols():
     return ["qisg_opts_default", "qisg_ladder_linear", "qisg_create", "qisg_sweep", "qisg_pt_swap",
             "qisg_energies", "qisg_overlaps", "qisg_permutation", "qisg_get_spins",
             "qisg_get_couplings", "qisg_set_couplings", "qisg_set_state", "qisg_pt_given", "qisg_measurements",
-            "qisg_slot_means", "qisg_thresholds", "qisg_sweep_count", "qisg_layout",
+            "qisg_slot_means", "qisg_walk_history", "qisg_block_sums", "qisg_block_means",
+            "qisg_checkpoint_save", "qisg_checkpoint_load", "qisg_checkpoint_verify",
+            "qisg_thresholds", "qisg_sweep_count", "qisg_layout",
             "qisg_launch_count", "qisg_sync", "qisg_destroy", "qisg_strerror", "qisg_last_error",
             "qisg_philox4x32_10", "qisg_profile", "qisg_profile_read", "qisg_set_graphs",
             "qisg_autotune", "qisg_get_tiles", "qisg_set_tiles", "qisg_batch_create", "qisg_batch_admit", "qisg_batch_retire",
@@ -204,6 +213,9 @@ class Config:
     per_sample_launch: int = 0
     tau_antiperiodic: int = 0
     mem_budget: int = 0
+    history_len: int = 0
+    maxit: int = 0
+    blocks_len: int = 0
 
 
 class Instance:
@@ -227,6 +239,9 @@ class Instance:
         opts.layout = cfg.layout
         opts.per_sample_launch = cfg.per_sample_launch
         opts.tau_antiperiodic = cfg.tau_antiperiodic
+        opts.history_len = cfg.history_len
+        opts.maxit = cfg.maxit
+        opts.blocks_len = cfg.blocks_len
         self._h = ctypes.c_void_p()
         _check(lib.qisg_create(ctypes.byref(self._h), cfg.L, cfg.L_tau, _ptr(ladder), self.n_slots,
                                cfg.n_replicas, cfg.n_samples, cfg.seed, ctypes.byref(opts)))
@@ -327,6 +342,33 @@ class Instance:
         _check(load().qisg_slot_means(self._h, _ptr(e_s), _ptr(e_t), _ptr(q2)))
         return e_s, e_t, q2
 
+    def checkpoint_save(self, path: str):
+        _check(load().qisg_checkpoint_save(self._h, os.fsencode(path)))
+
+    def checkpoint_load(self, path: str):
+        _check(load().qisg_checkpoint_load(self._h, os.fsencode(path)))
+
+    def walk_history(self, first: int, n: int) -> np.ndarray:
+        """Slot of every walker at measurements first .. first+n-1:
+        [n][n_samples][n_replicas][n_slots] uint8."""
+        out = np.zeros((n, self.n_samples, self.n_rep, self.n_slots), dtype=np.uint8)
+        _check(load().qisg_walk_history(self._h, first, n, _ptr(out)))
+        return out
+
+    def block_sums(self, first: int, n: int):
+        """Sums of A and B over blocks first .. first+n-1 of maxit
+        measurements: two int64 [n][n_samples][n_replicas][n_slots]."""
+        A = np.zeros((n, self.n_samples, self.n_rep, self.n_slots), dtype=np.int64)
+        B = np.zeros_like(A)
+        _check(load().qisg_block_sums(self._h, first, n, _ptr(A), _ptr(B)))
+        return A, B
+
+    def block_means(self, first: int, n: int):
+        e_s = np.zeros((n, self.n_slots))
+        e_t = np.zeros((n, self.n_slots))
+        _check(load().qisg_block_means(self._h, first, n, _ptr(e_s), _ptr(e_t)))
+        return e_s, e_t
+
     def thresholds(self) -> np.ndarray:
         T = np.zeros((self.n_slots, 5, 3), dtype=np.uint32)
         _check(load().qisg_thresholds(self._h, _ptr(T)))
@@ -392,15 +434,29 @@ def philox4x32_10_device(ctr_dev_ptr: int, key_dev_ptr: int, out_dev_ptr: int, n
     _check(load().qisg_philox4x32_10(ctr_dev_ptr, key_dev_ptr, out_dev_ptr, n, stream))
 
 
+class CheckpointInfo(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("L_tau", ctypes.c_int), ("n_slots", ctypes.c_int),
+                ("n_replicas", ctypes.c_int), ("n_samples", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("sweep", ctypes.c_uint64), ("n_meas", ctypes.c_int64), ("pt_every", ctypes.c_int),
+                ("measure_every", ctypes.c_int), ("tau_antiperiodic", ctypes.c_int), ("rule", ctypes.c_int)]
+
+
+def checkpoint_verify(path: str) -> dict:
+    """Header of a checkpoint file after its size and CRC checks (host only)."""
+    info = CheckpointInfo()
+    _check(load().qisg_checkpoint_verify(os.fsencode(path), ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in CheckpointInfo._fields_}
+
+
 class InstanceDesc(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("L_tau", ctypes.c_int), ("n_slots", ctypes.c_int),
                 ("n_replicas", ctypes.c_int), ("ladder", ctypes.c_void_p),
-                ("seed", ctypes.c_uint64), ("n_sweeps", ctypes.c_int64)]
+                ("seed", ctypes.c_uint64), ("n_sweeps", ctypes.c_int64), ("tau_antiperiodic", ctypes.c_int)]
 
 
-def _desc(L, L_tau, ladder, n_replicas, seed, n_sweeps):
+def _desc(L, L_tau, ladder, n_replicas, seed, n_sweeps, tau_antiperiodic=0):
     lad = _ladder_array(ladder)
-    d = InstanceDesc(L, L_tau, lad.shape[0], n_replicas, lad.ctypes.data, seed, n_sweeps)
+    d = InstanceDesc(L, L_tau, lad.shape[0], n_replicas, lad.ctypes.data, seed, n_sweeps, int(tau_antiperiodic))
     return d, lad
 
 
@@ -437,10 +493,10 @@ class Batch:
         d, _lad = _desc(L, L_tau, ladder, n_replicas, 0, 0)
         return int(load().qisg_batch_instance_bytes(ctypes.byref(d)))
 
-    def admit(self, L, L_tau, ladder, n_replicas, seed, n_sweeps=0) -> int:
+    def admit(self, L, L_tau, ladder, n_replicas, seed, n_sweeps=0, tau_antiperiodic=0) -> int:
         """Slot of the admitted instance; raises QisgError(ENOMEM) when the
         arena or the slots are full."""
-        d, lad = _desc(L, L_tau, ladder, n_replicas, seed, n_sweeps)
+        d, lad = _desc(L, L_tau, ladder, n_replicas, seed, n_sweeps, tau_antiperiodic)
         slot = ctypes.c_int()
         _check(load().qisg_batch_admit(self._b, ctypes.byref(d), ctypes.byref(slot)))
         self.meta[slot.value] = (L, L_tau, lad.shape[0], n_replicas)

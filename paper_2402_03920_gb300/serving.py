@@ -35,6 +35,7 @@ class Request:
     n_replicas: int = 4
     k_lo: float = 0.2
     k_hi: float = 0.5
+    tau_antiperiodic: int = 0      # boundary along tau (Sec. 1)
 
 
 @dataclass
@@ -107,7 +108,8 @@ class Server:
         while self.queue:
             req = self.queue[0]
             lad = qisg.ladder_linear(req.k_lo, req.k_hi, req.n_slots, req.gamma)
-            slot = self.batch.try_admit(req.L, req.L_tau, lad, req.n_replicas, req.seed, req.sweeps)
+            slot = self.batch.try_admit(req.L, req.L_tau, lad, req.n_replicas, req.seed, req.sweeps,
+                                        req.tau_antiperiodic)
             if slot is None and not self.active:
                 # refused by an empty batch: it never fits, and waiting would
                 # block the queue for good

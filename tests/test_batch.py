@@ -168,3 +168,21 @@ def test_barrier_wait_runs_out(qisg):
         A, B, wa, S = b.results(s, spins=True)
         st = _oracle_instance(8, 16, lad, 4, 41, 6)
         assert np.array_equal(S, st.S[0]) and np.array_equal(wa, st.walker_at[0])
+
+
+def test_antiperiodic_instances_in_the_mix(qisg):
+    """Instances with the antiperiodic boundary along tau (Sec. 1) next to
+    periodic ones in one persistent launch: each matches the oracle with its
+    own boundary."""
+    specs = [(6, 8, 7, 1.0, 71, 1), (8, 16, 12, 0.9, 72, 0), (4, 32, 20, 1.1, 73, 1), (6, 4, 5, 1.2, 74, 1)]
+    with qisg.Batch(4, 64 << 20) as b:
+        slots = [b.admit(L, Lt, qisg.ladder_linear(0.2, 0.5, ns, g), 4, seed, tau_antiperiodic=ap)
+                 for (L, Lt, ns, g, seed, ap) in specs]
+        b.run(17)
+        for slot, (L, Lt, ns, g, seed, ap) in zip(slots, specs):
+            lad = qisg.ladder_linear(0.2, 0.5, ns, g)
+            st = oracle.new_state(L, Lt, lad[:, 0], lad[:, 1], 4, seed, tau_ap=bool(ap))
+            oracle.run(st, 17)
+            A, B, wa, S = b.results(slot, spins=True)
+            assert np.array_equal(S, st.S[0]) and np.array_equal(wa, st.walker_at[0]), slot
+            assert np.array_equal(A, st.A[0]) and np.array_equal(B, st.B[0]), slot

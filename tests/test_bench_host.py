@@ -37,8 +37,9 @@ def test_roofline_from_plain_time_and_shares():
     assert by["red"]["avg_launch_us"] == pytest.approx(12.0) and rl["avg_launch_us"] == pytest.approx(20.0)
     for k in by.values():   # launches x duration within the plain step
         assert k["launches_per_step"] * k["avg_launch_us"] <= 1000 * ms_per_step + 1e-9
-    ups = bench.updates_per_step(w) / bench.SWEEPS_PER_STEP
+    ups = bench.updates_per_step(w) / bench.SWEEPS_PER_STEP / 2      # one colour's sites per launch
     assert rl["updates_per_launch"] == pytest.approx(ups)
+    assert rl["algorithmic_bytes_per_launch"] == pytest.approx(0.25 * ups)
     assert rl["achieved"] == pytest.approx(bench.ALG_OPS["samples32"] * ups / 20e-6 / 1e12)
     assert rl["peak"] == pytest.approx(100 * bench.INT_LANES_PER_CLK_PER_SM * 2000e6 / 1e12)
     assert rl["frac"] == pytest.approx(rl["achieved"] / rl["peak"])

@@ -27,7 +27,7 @@ class FakeBatch:
     def nbytes(self, L, L_tau, n_slots, n_rep):
         return L * L * L_tau * n_slots * n_rep + self.HEADER
 
-    def try_admit(self, L, L_tau, ladder, n_rep, seed, n_sweeps):
+    def try_admit(self, L, L_tau, ladder, n_rep, seed, n_sweeps, tau_antiperiodic=0):
         b = self.nbytes(L, L_tau, ladder.shape[0], n_rep)
         free = [k for k in range(self.capacity) if k not in self.slots]
         if not free or self.used + b > self.budget:
