@@ -366,6 +366,22 @@ int qisg_profile_read(qisg_handle *h, int kind, double *total_ms, int64_t *n_tim
  * the same either way. */
 int qisg_set_graphs(qisg_handle *h, int enable);
 
+/* The persistent form of the batched sweep (SAMPLES packing, 32-bit words,
+ * PT every sweep; Sec. 2.1's red / blue / PT cycle): enable = 1 runs every
+ * stretch of sweeps up to the next measurement (or 64 sweeps when nothing
+ * is measured) as ONE cooperative kernel launch -- fused red pass with the
+ * pending PT exchanges, grid barrier, blue pass with the bond counts,
+ * barrier, PT pass, barrier, per sweep -- and replays those launches (and
+ * the measurements) from a captured CUDA graph.  The trajectory is the
+ * same as with separate launches.  Each grid-barrier wait is bounded by
+ * wait_ns nanoseconds (0: the default, 5 s); a wait that runs out ends the
+ * launch and the next synchronising call returns ETIMEOUT (the handle's
+ * state is then undefined: destroy it).  qisg_autotune then chooses the red
+ * pass's threads per site and the sites each blue thread walks along tau
+ * for this form.  EINVAL: another packing or word width, pt_every != 1,
+ * 2N >= 2^30, or wait_ns < 0.  Synchronises. */
+int qisg_set_persistent(qisg_handle *h, int enable, int64_t wait_ns);
+
 /* Choose the SAMPLES sweep schedule by timing sweeps_per_candidate real
  * sweeps per candidate on the handle's own state; the red and blue passes are
  * timed and tuned separately.  Candidates: tiles 1, 2, ..., 64 and, for

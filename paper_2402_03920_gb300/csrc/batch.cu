@@ -28,7 +28,6 @@ namespace {
 
 constexpr int kBatchBlock = 256;
 static_assert(kBatchBlock <= kLanesMaxThreads, "the LANES class-code buffer holds kLanesMaxThreads threads");
-constexpr long long kBarrierTimeoutNs = 5000000000ll;   // 5 s per wait (default)
 
 struct InstDev {
   unsigned long long *spins;   // [g][site]
@@ -54,42 +53,6 @@ struct Tile {
 struct ChainRef {
   int inst, r;
 };
-
-__device__ __forceinline__ unsigned long long gtime() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier with a bounded wait: bar[0] arrivals, bar[1] generation.
-// A wait that exceeds wait_ns sets *err and gives up; every block checks
-// *err after each barrier and leaves, so the launch always ends.
-__device__ bool grid_sync(unsigned *bar, int *err, long long wait_ns) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned *gen = bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const unsigned long long t0 = gtime();
-      while (*gen == g) {
-        if (*(volatile int *)err) break;
-        if (gtime() - t0 > (unsigned long long)wait_ns) {
-          atomicExch(err, 1);
-          break;
-        }
-        __nanosleep(128);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return *(volatile int *)err == 0;
-}
 
 // One tile of a half sweep of instance I (sample 0, 64-bit LANES words).
 template <bool BLUE>
@@ -149,7 +112,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) batch_kernel(InstDev *insts, i
         else
           batch_tile<true>(I, 1, tl.j0, tl.n, smem);
       }
-      if (!grid_sync(bar, err, wait_ns)) return;
+      if (!grid_barrier(bar, err, wait_ns)) return;
     }
     for (int c = gwarp; c < n_chains; c += warps) {
       const ChainRef cr = chains[c];
@@ -158,7 +121,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) batch_kernel(InstDev *insts, i
       pt_chain<false, true, true>(I.walker + cr.r * I.n_slots, I.U + (size_t)cr.r * I.n_slots * 2, I.ptc, I.sq,
                                   I.key, (uint32_t)__ldcg(&I.t), 0, cr.r, I.n_slots);
     }
-    if (!grid_sync(bar, err, wait_ns)) return;
+    if (!grid_barrier(bar, err, wait_ns)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_inst; i += gridDim.x * blockDim.x) {
       InstDev &I = insts[i];
       const long long rem = __ldcg(&I.remaining);
@@ -167,7 +130,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) batch_kernel(InstDev *insts, i
         if (rem > 0) I.remaining = rem - 1;
       }
     }
-    if (!grid_sync(bar, err, wait_ns)) return;
+    if (!grid_barrier(bar, err, wait_ns)) return;
   }
 }
 

@@ -354,6 +354,7 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc && h->blk_len) rc = dalloc(h, &h->d_blkB, (size_t)h->blk_len * n_rows * 8);
   if (!rc && layout == QISG_LAYOUT_SAMPLES)
     rc = dalloc(h, &h->d_acc, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8));
+  if (!rc && layout == QISG_LAYOUT_SAMPLES) rc = dalloc(h, &h->d_bar, 2 * sizeof(unsigned));
   if (!rc && layout == QISG_LAYOUT_SITES) rc = dalloc(h, &h->d_dcum, (size_t)n_slots * 256 * 8);
   if (!rc && layout == QISG_LAYOUT_SITES) rc = dalloc(h, &h->d_dlut, ((size_t)n_slots << kDaemonLutBits) * 9);
   if (rc) {
@@ -448,7 +449,31 @@ int one_sweep(qisg_handle *h, cudaEvent_t *ev = nullptr) {
 
 int64_t gcd64(int64_t a, int64_t b) { return b ? gcd64(b, a % b) : a; }
 
+// Persistent form: sweeps per launch when nothing is measured.
+constexpr int kPersistChunk = 64;
+
+// k sweeps in the persistent form (the caller keeps a due measurement at
+// the end of the run, never inside it), then the measurement if due.
+int persistent_chunk(qisg_handle *h, int k) {
+  int rc = samples_persistent(h, k);
+  if (rc) return rc;
+  h->t += (uint64_t)k;
+  if (h->measure_every > 0 && h->t % (uint64_t)h->measure_every == 0) {
+    rc = samples_measure(h, 0);
+    if (!rc && (h->hist_len || h->maxit)) rc = record_measurement(h);
+    h->n_meas++;
+  }
+  return rc;
+}
+
+// Sweeps per persistent launch: up to the next measurement.
+int persistent_run(const qisg_handle *h) { return h->measure_every > 0 ? h->measure_every : kPersistChunk; }
+
 int cycle_length(const qisg_handle *h) {
+  if (h->persistent) {   // whole launches; an even count returns to the lattice buffer
+    const int r = persistent_run(h);
+    return (r & 1) ? 2 * r : r;
+  }
   const int64_t p = h->pt_every > 0 ? h->pt_every : 1;
   const int64_t m = h->measure_every > 0 ? h->measure_every : 1;
   int64_t l = p / gcd64(p, m) * m;
@@ -490,7 +515,9 @@ int build_cycle(qisg_handle *h, int C) {
   cudaStream_t user = h->stream;
   h->stream = h->cap_stream;
   rc = cuda_check(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-  if (!rc)
+  if (!rc && h->persistent)
+    for (int i = 0; i < C && !rc; i += persistent_run(h)) rc = persistent_chunk(h, persistent_run(h));
+  else if (!rc)
     for (int i = 0; i < C && !rc; ++i) rc = one_sweep(h);
   cudaGraph_t g = nullptr;
   const int rc_end = cuda_check(cudaStreamEndCapture(h->cap_stream, &g), "end capture");
@@ -616,6 +643,11 @@ int qisg_sweep(qisg_handle *h, int64_t n_sweeps) {
       }
       rc = replay_cycle(h);
       n_sweeps -= C;
+    } else if (h->persistent) {   // up to the next measurement (or a full run)
+      const int r = persistent_run(h);
+      const int k = (int)std::min<int64_t>(n_sweeps, r - (int64_t)(h->t % (uint64_t)r));
+      rc = persistent_chunk(h, k);
+      n_sweeps -= k;
     } else {
       rc = one_sweep(h);
       n_sweeps -= 1;
@@ -623,6 +655,66 @@ int qisg_sweep(qisg_handle *h, int64_t n_sweeps) {
     if (rc) return rc;
   }
   return QISG_OK;
+}
+
+int qisg_set_persistent(qisg_handle *h, int enable, int64_t wait_ns) {
+  if (!h || wait_ns < 0) return fail(QISG_EINVAL, "bad handle or wait_ns < 0");
+  if (enable && !samples_persistent_ok(h))
+    return fail(QISG_EINVAL, "the persistent form needs the SAMPLES packing, 32-bit words, PT every sweep");
+  int rc = sync_handle(h);
+  if (rc) return rc;
+  h->persistent = enable != 0;
+  h->wait_ns = wait_ns == 0 ? kBarrierTimeoutNs : (long long)wait_ns;
+  drop_cycle(h);
+  return QISG_OK;
+}
+
+// Persistent form: time whole runs of sweeps for every (red tile, blue tile)
+// pair -- the red pass's threads per site and the number of sites each blue
+// thread walks along tau -- on the handle's own state; keep the fastest.
+static int autotune_persistent(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
+  const int red_tiles[3] = {1, 2, 4}, blue_tiles[6] = {1, 2, 4, 8, 16, 32};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = cuda_check(cudaEventCreate(&e0), "event");
+  if (!rc) rc = cuda_check(cudaEventCreate(&e1), "event");
+  float best = -1.f;
+  int best_r = 4, best_b = 8;
+  auto run = [&](int n) {
+    int r = QISG_OK;
+    while (n > 0 && !r) {
+      const int rr = persistent_run(h);
+      const int k = (int)std::min<int64_t>(n, rr - (int64_t)(h->t % (uint64_t)rr));
+      r = persistent_chunk(h, k);
+      n -= k;
+    }
+    return r;
+  };
+  for (int i = 0; i < 3 && !rc; ++i)
+    for (int j = 0; j < 6 && !rc; ++j) {
+      h->sweep_tile[0] = red_tiles[i];
+      h->sweep_tile[1] = blue_tiles[j];
+      h->sweep_variant[0] = h->sweep_variant[1] = 0;
+      rc = run(1);   // warm the candidate
+      if (!rc) rc = cuda_check(cudaEventRecord(e0, h->stream), "record");
+      if (!rc) rc = run(sweeps_per_candidate);
+      if (!rc) rc = cuda_check(cudaEventRecord(e1, h->stream), "record");
+      if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "sync");
+      float ms = 0.f;
+      if (!rc) rc = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+      if (!rc && (best < 0.f || ms < best)) {
+        best = ms;
+        best_r = red_tiles[i];
+        best_b = blue_tiles[j];
+      }
+    }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc) return rc;
+  h->sweep_tile[0] = best_r;
+  h->sweep_tile[1] = best_b;
+  drop_cycle(h);
+  if (chosen) *chosen = best_b;
+  return sync_handle(h);
 }
 
 int qisg_set_graphs(qisg_handle *h, int enable) {
@@ -638,6 +730,7 @@ int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
     if (chosen) *chosen = 0;
     return QISG_OK;
   }
+  if (h->persistent) return autotune_persistent(h, sweeps_per_candidate, chosen);
   // candidates: tiles 1, 2, ..., 64, and for W = 32 each with both kernel
   // variants; the red and blue passes are timed apart and tuned apart
   const int n_tiles = 7, n_cand = h->W == 32 ? 2 * n_tiles : n_tiles;
@@ -1000,7 +1093,7 @@ void qisg_destroy(qisg_handle *h) {
   cudaStreamSynchronize(h->stream);
   void *ptrs[] = {h->spins, h->spins_alt, h->J, h->d_T, h->d_bases, h->d_sq, h->d_ptc, h->d_walker, h->d_U, h->d_sumA, h->d_sumB,
                   h->d_sumq, h->d_sumq2, h->d_q, h->d_out, h->d_t, h->d_acc, h->d_err, h->d_dcum, h->d_dlut,
-                  h->d_meas, h->d_hist, h->d_blkA, h->d_blkB};
+                  h->d_meas, h->d_hist, h->d_blkA, h->d_blkB, h->d_bar};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   drop_cycle(h);

@@ -247,6 +247,58 @@ __device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua
   return acc;
 }
 
+// ---- persistent kernels ----
+
+constexpr long long kBarrierTimeoutNs = 5000000000ll;   // default bound of a grid-barrier wait: 5 s
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch with a bounded wait: bar[0]
+// counts arrivals, bar[1] is the generation.  A wait that exceeds wait_ns
+// sets *err and gives up; every block checks *err after each barrier and
+// leaves (returns false), so the launch always ends.  bar must be zero at
+// launch.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, long long wait_ns) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = gtime();
+      while (*gen == g) {
+        if (*(volatile int *)err) break;
+        if (gtime() - t0 > (unsigned long long)wait_ns) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int *)err == 0;
+}
+
+// Load through L2 only (CG) where other blocks of the same persistent launch
+// wrote the data in an earlier phase (L1 is not coherent across SMs).
+template <bool CG, typename T>
+__device__ __forceinline__ T ld_g(const T *p) {
+  if constexpr (CG)
+    return __ldcg(p);
+  else
+    return *p;
+}
+
 // ---- bit-sliced helpers shared by the sweep kernels ----
 
 template <typename Word>
@@ -412,6 +464,11 @@ struct qisg_handle {
   // set by qisg_pt_given: energies and permutation no longer describe the
   // configurations; sweeps are refused until qisg_set_state
   bool needs_state = false;
+  // persistent form (SAMPLES, 32-bit words, PT every sweep): one cooperative
+  // launch per run of sweeps between measurements
+  bool persistent = false;
+  unsigned *d_bar = nullptr;        // grid barrier of the persistent kernel
+  long long wait_ns = 5000000000ll; // bound of each barrier wait
   cudaStream_t stream = nullptr;
   size_t mem_budget = 0;
   uint64_t t = 0;          // sweeps done (host mirror of *d_t)
@@ -540,6 +597,9 @@ int samples_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S);
 int samples_set_spins(qisg_handle *h, const int8_t *S, const int32_t *walker_at);
 int samples_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J);
 int samples_set_couplings(qisg_handle *h, const int8_t *J);
+// persistent form: n sweeps (red, blue, PT) in one cooperative launch
+bool samples_persistent_ok(const qisg_handle *h);
+int samples_persistent(qisg_handle *h, int n_sweeps);
 
 // common small kernels (qisg_api.cu)
 int advance_counter(qisg_handle *h);

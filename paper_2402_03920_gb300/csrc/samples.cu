@@ -531,16 +531,16 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedR
 // shuffle: the even thread draws even slots, the odd thread odd ones).
 // Fewer threads and instructions per word than the per-replica form; the
 // autotuner picks the form (results are identical).
-template <typename Word, int RP>
+template <typename Word, int RP, bool CG = false>
 __device__ __forceinline__ void ld_rp(Word (&d)[RP], const Word *p) {
   if constexpr (RP * sizeof(Word) == 16) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(p);
+    const uint4 v = ld_g<CG>(reinterpret_cast<const uint4 *>(p));
     memcpy(d, &v, 16);
   } else if constexpr (RP * sizeof(Word) == 8) {
-    const uint2 v = *reinterpret_cast<const uint2 *>(p);
+    const uint2 v = ld_g<CG>(reinterpret_cast<const uint2 *>(p));
     memcpy(d, &v, 8);
   } else {
-    d[0] = *p;
+    d[0] = ld_g<CG>(p);
   }
 }
 template <typename Word, int RP>
@@ -563,26 +563,24 @@ __device__ __forceinline__ void st_rp(Word *p, const Word (&d)[RP]) {
 // per site, consecutive lanes).  The site's Philox calls (one per slot, four
 // draws) are spread over its threads: thread h makes the call of slot
 // TPS g + h and the draws are passed on by shuffles.
-template <typename Word, int RP>
-__global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const FusedRedArgsT<Word> p,
-                                                                      const __grid_constant__ SlotThresholds th) {
+// Body of the pass for (virtual) block bid of sweep t; CG: read what other
+// blocks of a persistent launch wrote (spins, masks) through L2 only.
+template <typename Word, int RP, bool CG>
+__device__ __forceinline__ void red_fusedq_body(const FusedRedArgsT<Word> &p, const SlotThresholds &th, uint32_t bid,
+                                                unsigned long long t) {
   constexpr int TPS = 4 / RP;
   constexpr int W = (int)sizeof(Word) * 8;
   __shared__ __align__(16) Word msk[kMaxSlotsPT][4];
-  const uint32_t bid = blockIdx.x;
   const uint32_t set = p.fd_bps.div(bid);   // (b, q)
   const uint32_t chunk = bid - set * (uint32_t)p.blocks_per_set;
   const uint32_t b = p.fd_nq.div(set);
   const int q = (int)(set - b * (uint32_t)p.n_q);
   const int n = p.n_slots;
-  {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
-  }
+  __syncthreads();   // msk of the previous (virtual) block is no longer read
   for (int i = threadIdx.x; i < 4 * kMaxSlotsPT; i += blockDim.x) {
     const int sl = i >> 2, jj = i & 3;
     const int rr = 4 * q + jj;
-    msk[sl][jj] = (rr < p.n_rep && sl + 1 < n) ? p.acc[((int64_t)b * p.n_rep + rr) * n + sl] : Word(0);
+    msk[sl][jj] = (rr < p.n_rep && sl + 1 < n) ? ld_g<CG>(p.acc + ((int64_t)b * p.n_rep + rr) * n + sl) : Word(0);
   }
   __syncthreads();
 
@@ -619,7 +617,6 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const Fused
   Word *db = p.dst + base;
   const Word *Jb = p.J + (int64_t)b * P * 2;
   Word Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
-  const unsigned long long t = *p.d_t;
   const uint32_t ctr_w = (DOM_SWEEP << 28) | ((b * (uint32_t)W) >> 6);
   const uint32_t site = i2 + off;
   const bool has_zero = p.t_has_zero != 0;
@@ -631,10 +628,10 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const Fused
     Jyp = Jb[2 * i2 + 1];
     Jym = Jb[2 * iym + 1];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) ld_rp<Word, RP>(cw[k], sb + zo[k]);
+    for (int k = 0; k < 7; ++k) ld_rp<Word, RP, CG>(cw[k], sb + zo[k]);
     if (n > 1)
 #pragma unroll
-      for (int k = 0; k < 7; ++k) ld_rp<Word, RP>(n1[k], sb + SS + zo[k]);
+      for (int k = 0; k < 7; ++k) ld_rp<Word, RP, CG>(n1[k], sb + SS + zo[k]);
   }
   uint4 R4 = make_uint4(0, 0, 0, 0);
   for (int sl = 0; sl < n; ++sl) {
@@ -668,7 +665,7 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const Fused
       if (sl + 2 < n) {
         const Word *ps = sb + (int64_t)(sl + 2) * SS;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) ld_rp<Word, RP>(n2[k], ps + zo[k]);
+        for (int k = 0; k < 7; ++k) ld_rp<Word, RP, CG>(n2[k], ps + zo[k]);
       }
       Word m[RP];
 #pragma unroll
@@ -717,6 +714,16 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const Fused
   }
 }
 
+template <typename Word, int RP>
+__global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const FusedRedArgsT<Word> p,
+                                                                      const __grid_constant__ SlotThresholds th) {
+  {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
+  }
+  red_fusedq_body<Word, RP, false>(p, th, blockIdx.x, *p.d_t);
+}
+
 // Sum the block's per-thread counters (NC counters of K planes in registers)
 // and add lane l of counter c into out[c * 32 + l]: tree over the 128
 // threads in shared memory, one more plane per level.
@@ -757,10 +764,11 @@ __device__ __forceinline__ void block_sum_counters(const VCount<Word, K> *cnt, W
   __syncthreads();   // buf is reused by the caller
 }
 
-template <bool BLUE, int G2, bool PF>
-__global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uint32_t> p,
-                                                                  const __grid_constant__ SlotThresholds th,
-                                                                  int colour, int count_only) {
+// Body of the pass for (virtual) block bid of sweep t; CG: read the spins
+// through L2 only (a persistent launch, where other blocks wrote them).
+template <bool BLUE, int G2, bool PF, bool CG>
+__device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, const SlotThresholds &th, uint32_t bid,
+                                            unsigned long long t, int colour, int count_only) {
   constexpr int KS = G2 + 5;   // u_s sum <= 4 G per replica and thread
   constexpr int KT = G2 + 4;   // u_t sum <= 2 G
   constexpr int KF = KS + kLog2Block4;
@@ -768,19 +776,12 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
   __shared__ int tot[BLUE ? 2 * 4 * 32 : 1];
 
   // block -> (b, s, q, chunk) and thread -> (segment, column) in 32 bits
-  const uint32_t bid = blockIdx.x;
   const uint32_t set = p.fd_bps.div(bid);
   const uint32_t chunk = bid - set * (uint32_t)p.blocks_per_set;
   const uint32_t bs = p.fd_nq.div(set);
   const int q = (int)(set - bs * (uint32_t)p.n_q);
   const uint32_t b = p.fd_ns.div(bs);
   const int s = (int)(bs - b * (uint32_t)p.n_slots);
-  {   // counters / masks the host asked this pass to clear (nothing reads them before the next pass)
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_acc; i += stride)
-      p.zero_acc[i] = 0;
-  }
   const uint32_t *T = th.v[s];
   const bool has_zero = p.t_has_zero != 0;
   const int L = p.L, plane = p.plane, G = p.seg_sites;
@@ -799,8 +800,6 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
   const uint32_t *Jb = p.J + b * (int64_t)plane * 2;
   uint32_t Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
   const uint32_t tau0 = 2u * (uint32_t)G * (uint32_t)seg + (uint32_t)((colour + x + y) & 1);
-  const unsigned long long t = *p.d_t;
-  if (p.t_copy && bid == 0 && threadIdx.x == 0) *p.t_copy = t;
   const uint32_t ctr_z = (uint32_t)s | ((uint32_t)q << 16);
   const uint32_t ctr_w = (DOM_SWEEP << 28) | (uint32_t)((b * 32) >> 6);
 
@@ -819,24 +818,24 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
     Jyp = Jb[2 * i2 + 1];
     Jym = Jb[2 * iym + 1];
     uint32_t off = tau0 * P;
-    uint4 dn = pc[(size_t)(tau0 == 0 ? (Lt - 1) * P : off - P)];
+    uint4 dn = ld_g<CG>(pc + (size_t)(tau0 == 0 ? (Lt - 1) * P : off - P));
     Quad4 cur;
-    cur.c = pc[off];
-    cur.up = pc[(size_t)(tau0 + 1 == Lt ? 0u : off + P)];
-    cur.xp = pxp[off];
-    cur.xm = pxm[off];
-    cur.yp = pyp[off];
-    cur.ym = pym[off];
+    cur.c = ld_g<CG>(pc + off);
+    cur.up = ld_g<CG>(pc + (size_t)(tau0 + 1 == Lt ? 0u : off + P));
+    cur.xp = ld_g<CG>(pxp + off);
+    cur.xm = ld_g<CG>(pxm + off);
+    cur.yp = ld_g<CG>(pyp + off);
+    cur.ym = ld_g<CG>(pym + off);
     for (int k = 0; k < G; ++k) {
       const uint32_t tau = tau0 + 2u * (uint32_t)k;
       auto load_next = [&](Quad4 &nx) {
         const uint32_t offn = off + 2 * P;
-        nx.c = pc[offn];
-        nx.up = pc[(size_t)(tau + 3 == Lt ? 0u : offn + P)];
-        nx.xp = pxp[offn];
-        nx.xm = pxm[offn];
-        nx.yp = pyp[offn];
-        nx.ym = pym[offn];
+        nx.c = ld_g<CG>(pc + offn);
+        nx.up = ld_g<CG>(pc + (size_t)(tau + 3 == Lt ? 0u : offn + P));
+        nx.xp = ld_g<CG>(pxp + offn);
+        nx.xm = ld_g<CG>(pxm + offn);
+        nx.yp = ld_g<CG>(pyp + offn);
+        nx.ym = ld_g<CG>(pym + offn);
       };
       Quad4 nxt;
       if (PF && k + 1 < G) load_next(nxt);
@@ -906,6 +905,22 @@ __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uin
       }
     }
   }
+}
+
+
+template <bool BLUE, int G2, bool PF>
+__global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uint32_t> p,
+                                                                  const __grid_constant__ SlotThresholds th,
+                                                                  int colour, int count_only) {
+  {   // counters / masks the host asked this pass to clear (nothing reads them before the next pass)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_acc; i += stride)
+      p.zero_acc[i] = 0;
+  }
+  const unsigned long long t = *p.d_t;
+  if (p.t_copy && blockIdx.x == 0 && threadIdx.x == 0) *p.t_copy = t;
+  sweep4_body<BLUE, G2, PF, false>(p, th, blockIdx.x, t, colour, count_only);
 }
 
 
@@ -1219,6 +1234,77 @@ __global__ void samples_pack_kernel(Word *spins, const int8_t *stage, const int3
   spins[(((b * n_slots + s) * n_q + (r >> 2)) * N + site) * 4 + (r & 3)] = v;
 }
 
+// ---- persistent form: red | blue | PT for a run of sweeps in one launch ----
+//
+// One cooperative launch runs n sweeps of the 32-bit SAMPLES packing.  Per
+// sweep: the fused red pass (the pending PT exchanges applied, the red sites
+// updated, the lattice copied into the other buffer; the bond counters
+// cleared), a grid barrier, the blue pass in place (bond counters; the PT
+// masks cleared, the red pass having read them), a barrier, the PT pass (a
+// warp per chain, accepted pairs OR-ed into the masks the next red pass
+// applies), a barrier.  Blocks take the passes' blocks in turn (block b does
+// b, b + grid, ...), so a pass's work split is the one its own kernel has;
+// anything another block wrote earlier in the launch is read through L2.
+// The barriers' waits are bounded (error flag -> QISG_ETIMEOUT).
+struct PersistArgs {
+  FusedRedArgsT<uint32_t> red;    // src/dst set per sweep from buf
+  SamplesArgs<uint32_t> blue;     // spins set per sweep
+  uint32_t *buf[2];               // the two lattice buffers; buf[0] holds the lattice at launch
+  int red_blocks, blue_blocks;
+  int32_t *walker;                // [a_pad][r][s]
+  unsigned long long *U;          // [a_pad][r][s][2] by slot
+  uint32_t *acc;                  // PT lane masks [b][r][s]
+  const PTConst *ptc;
+  const double *sq;
+  uint2 key;
+  int64_t n_samples;
+  int n_rep, n_slots;
+  int64_t n_U, n_acc;             // words the red / blue phase clears
+  unsigned long long *d_t;        // sweeps done; advanced by n at the end
+  int n_sweeps;
+  unsigned *bar;
+  int *err;
+  long long wait_ns;
+};
+
+template <int RP, int G2>
+__global__ void __launch_bounds__(kBlock4, 3) samples_persistent_kernel(const PersistArgs a,
+                                                                      const __grid_constant__ SlotThresholds th) {
+  const unsigned long long t0 = __ldcg(a.d_t);
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+  const int gwarp = (int)(gtid >> 5);
+  const int lane = threadIdx.x & 31;
+  const int64_t n_chains = a.n_samples * a.n_rep;
+  for (int sw = 0; sw < a.n_sweeps; ++sw) {
+    const unsigned long long t = t0 + (unsigned long long)sw;
+    const int cur = sw & 1;
+    FusedRedArgsT<uint32_t> rp = a.red;
+    rp.src = a.buf[cur];
+    rp.dst = a.buf[cur ^ 1];
+    for (int64_t i = gtid; i < a.n_U; i += gstride) a.U[i] = 0;
+    for (int vb = blockIdx.x; vb < a.red_blocks; vb += gridDim.x) red_fusedq_body<uint32_t, RP, true>(rp, th, vb, t);
+    if (!grid_barrier(a.bar, a.err, a.wait_ns)) return;
+    for (int64_t i = gtid; i < a.n_acc; i += gstride) a.acc[i] = 0;
+    SamplesArgs<uint32_t> bp = a.blue;
+    bp.spins = a.buf[cur ^ 1];
+    for (int vb = blockIdx.x; vb < a.blue_blocks; vb += gridDim.x)
+      sweep4_body<true, G2, true, true>(bp, th, vb, t, 1, 0);
+    if (!grid_barrier(a.bar, a.err, a.wait_ns)) return;
+    for (int64_t c = gwarp; c < n_chains; c += warps) {   // whole warps: c is uniform over the warp
+      const int64_t sa = c / a.n_rep;
+      const int r = (int)(c - sa * a.n_rep);
+      const uint32_t acc = pt_chain<true, true, false>(a.walker + c * a.n_slots, a.U + c * a.n_slots * 2, a.ptc,
+                                                       a.sq, a.key, (uint32_t)t, sa, r, a.n_slots);
+      if (lane + 1 < a.n_slots && ((acc >> lane) & 1u))
+        atomicOr(a.acc + ((sa >> 5) * a.n_rep + r) * a.n_slots + lane, 1u << (sa & 31));
+    }
+    if (!grid_barrier(a.bar, a.err, a.wait_ns)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.d_t = t0 + (unsigned long long)a.n_sweeps;
+}
+
 template <typename Word>
 SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
   SamplesArgs<Word> p;
@@ -1352,12 +1438,13 @@ void launch_sweep4(const SamplesArgs<uint32_t> &p, const SlotThresholds &th, uns
   }
 }
 
+// Arguments of the fused red pass (and its threads per site, from the red
+// tile: 1 -> four, 2 -> two, else one; 64-bit words: at most two replicas
+// per thread) and its block count.
 template <typename Word>
-int fused_red(qisg_handle *h) {
-  SlotThresholds th;
+int make_red_args(qisg_handle *h, SlotThresholds &th, FusedRedArgsT<Word> &p, int &tpsite, int64_t &blocks) {
   const SamplesArgs<Word> a = make_args<Word>(h, 0);
   fill_thresholds(h, a.t_has_zero, th);
-  FusedRedArgsT<Word> p;
   p.src = reinterpret_cast<const Word *>(h->spins);
   p.dst = reinterpret_cast<Word *>(h->spins_alt);
   p.J = reinterpret_cast<const Word *>(h->J);
@@ -1377,9 +1464,7 @@ int fused_red(qisg_handle *h) {
   p.one = 1u;
   p.all_ones = 0xFFFFFFFFu;
   p.tau_ap = h->tau_ap;
-  // threads per site from the red tile: 1 -> four, 2 -> two, else one
-  // (64-bit words: at most two replicas per thread)
-  int tpsite = h->sweep_tile[0] == 1 ? 4 : h->sweep_tile[0] == 2 ? 2 : 1;
+  tpsite = h->sweep_tile[0] == 1 ? 4 : h->sweep_tile[0] == 2 ? 2 : 1;
   if (sizeof(Word) == 8 && tpsite == 1) tpsite = 2;
   const int64_t threads_per_set = (int64_t)a.plane * (h->Lt / 2) * tpsite;
   if (threads_per_set + kBlock4 > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
@@ -1388,8 +1473,19 @@ int fused_red(qisg_handle *h) {
   p.fd_nq = FastDiv((uint32_t)h->n_q);
   p.fd_plane = FastDiv((uint32_t)a.plane);
   p.fd_L = FastDiv((uint32_t)h->L);
-  const int64_t blocks = h->n_b * h->n_q * p.blocks_per_set;
+  blocks = h->n_b * h->n_q * p.blocks_per_set;
   if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+  return QISG_OK;
+}
+
+template <typename Word>
+int fused_red(qisg_handle *h) {
+  SlotThresholds th;
+  FusedRedArgsT<Word> p;
+  int tpsite = 1;
+  int64_t blocks = 0;
+  const int rc = make_red_args<Word>(h, th, p, tpsite, blocks);
+  if (rc) return rc;
   const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
   if constexpr (sizeof(Word) == 4) {
     const FusedRedArgs &p32 = p;
@@ -1708,6 +1804,85 @@ int samples_half_sweep(qisg_handle *h, int colour, int count_only) {
   return h->W == 64 ? half_sweep_t<unsigned long long>(h, colour, count_only)
                     : half_sweep_t<unsigned int>(h, colour, count_only);
 }
+bool samples_persistent_ok(const qisg_handle *h) {
+  return h->layout == QISG_LAYOUT_SAMPLES && h->W == 32 && h->fused && h->pt_every == 1 &&
+         2 * h->N < (int64_t(1) << 30) && h->n_slots <= kMaxSlotsPT && h->d_bar != nullptr;
+}
+
+int samples_persistent(qisg_handle *h, int n_sweeps) {
+  if (!samples_persistent_ok(h)) return fail(QISG_EINVAL, "persistent form: needs SAMPLES, 32-bit words, PT every sweep");
+  if (n_sweeps <= 0) return QISG_OK;
+  PersistArgs a;
+  SlotThresholds th, th_blue;
+  int tpsite = 1;
+  int64_t red_blocks = 0;
+  int rc = make_red_args<uint32_t>(h, th, a.red, tpsite, red_blocks);
+  if (rc) return rc;
+  a.red.n_zero_U = 0;
+  a.blue = make_args4(h, 1, th_blue);
+  a.blue.n_zero_U = 0;
+  a.blue.n_zero_acc = 0;
+  a.blue.t_copy = nullptr;
+  const int64_t blue_blocks = h->n_b * h->n_slots * h->n_q * a.blue.blocks_per_set;
+  if (blue_blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
+  int g2 = 0;
+  while ((4 << g2) < a.blue.seg_sites) ++g2;
+  if (g2 > 3) return fail(QISG_EINVAL, "persistent form: blue tile above 32 sites");
+  a.buf[0] = reinterpret_cast<uint32_t *>(h->spins);
+  a.buf[1] = reinterpret_cast<uint32_t *>(h->spins_alt);
+  a.red_blocks = (int)red_blocks;
+  a.blue_blocks = (int)blue_blocks;
+  a.walker = h->d_walker;
+  a.U = h->d_U;
+  a.acc = reinterpret_cast<uint32_t *>(h->d_acc);
+  a.ptc = reinterpret_cast<const PTConst *>(h->d_ptc);
+  a.sq = h->d_sq;
+  a.key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+  a.n_samples = h->n_samples;
+  a.n_rep = h->n_rep;
+  a.n_slots = h->n_slots;
+  a.n_U = h->n_a_pad * h->n_rep * h->n_slots * 2;
+  a.n_acc = h->n_b * h->n_rep * h->n_slots;
+  a.d_t = h->d_t;
+  a.n_sweeps = n_sweeps;
+  a.bar = h->d_bar;
+  a.err = h->d_err;
+  a.wait_ns = h->wait_ns;
+  const int rp = tpsite == 4 ? 1 : tpsite == 2 ? 2 : 4;
+  const void *fn = nullptr;
+#define QISG_PK(R, G) \
+  if (rp == R && g2 == G) fn = (const void *)samples_persistent_kernel<R, G>;
+  QISG_PK(1, 0) QISG_PK(1, 1) QISG_PK(1, 2) QISG_PK(1, 3) QISG_PK(2, 0) QISG_PK(2, 1) QISG_PK(2, 2) QISG_PK(2, 3)
+  QISG_PK(4, 0) QISG_PK(4, 1) QISG_PK(4, 2) QISG_PK(4, 3)
+#undef QISG_PK
+  int per_sm = 0;
+  rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock4, 0), "occupancy");
+  if (rc) return rc;
+  if (per_sm < 1) return fail(QISG_ECUDA, "persistent kernel does not fit on an SM");
+  const int grid = per_sm * std::max(1, h->n_sm);
+  rc = cuda_check(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream), "reset barrier");
+  if (rc) return rc;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBlock4);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = h->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void *args[] = {(void *)&a, (void *)&th};
+  const int tok = prof_begin(h, QISG_KERNEL_SWEEP);
+  rc = cuda_check(cudaLaunchKernelExC(&cfg, fn, args), "persistent sweep kernel");
+  prof_end(h, QISG_KERNEL_SWEEP, tok);
+  if (rc) return rc;
+  h->launches++;
+  if (n_sweeps & 1) std::swap(h->spins, h->spins_alt);
+  h->perm_pending = true;
+  return QISG_OK;
+}
+
 int samples_pt(qisg_handle *h, int explicit_pass, int advance) {
   return h->W == 64 ? pt_t<unsigned long long>(h, explicit_pass, advance)
                     : pt_t<unsigned int>(h, explicit_pass, advance);
