@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--forms", default="batched,per_instance")
-    p.add_argument("--extras", default="uneven,large,paper,daemon,serving",
+    p.add_argument("--extras", default="uneven,large,paper,daemon,serving,transfer,tau",
                    help="other workloads measured beside the headline (empty: none)")
     p.add_argument("--serving-requests", type=int, default=100)
     p.add_argument("--tiles", default="",
@@ -579,6 +579,57 @@ def serving_entry(qisg, n_requests):
     return out
 
 
+def transfer_entry(torch, qisg, reps=50):
+    """The exact-diagonalisation code's transfer-matrix product (Sec. 2.2) at
+    the largest lattice one GPU holds, L = 5 (even sector, 2^24 doubles):
+    time per product and its HBM roofline.  Algorithmic bytes: one read of
+    the input and one write of the output (16 B per element); the kernels
+    make three passes over the vector (rounds fused in shared-memory
+    tiles)."""
+    L, k = 5, 0.29
+    rng = np.random.default_rng(5)
+    J = np.where(rng.random((L * L, 2)) < 0.5, 1, -1).astype(np.int8)
+    n = 1 << (L * L - 1)
+    v = torch.randn(n, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(v)
+    for _ in range(3):
+        qisg.transfer_matvec(v.data_ptr(), out.data_ptr(), L, k, k, J, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        qisg.transfer_matvec(v.data_ptr(), out.data_ptr(), L, k, k, J, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    pk, _ = peaks()
+    alg = 16.0 * n
+    hbm = pk.get("hbm_gbs", 6800.0)
+    return {"workload": "EDQSG transfer-matrix product, L=5 even sector (2^24 doubles)", "ms_per_product": ms,
+            "unit": "ms", "passes": 3,
+            "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": alg / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": alg, "traffic": None,
+                         "note": "three passes move 6 x 8 B per element; the algorithmic 16 B counts input and output"}}
+
+
+def tau_entry(torch, qisg):
+    """Imaginary-time observables (Appendix E.1) of the production workload's
+    configurations (32 samples x 4 replicas x 16 slots, L=16, L_tau=256):
+    time of one qisg_tau_observables call over all of them."""
+    w = workload()
+    ladder = qisg.ladder_linear(w.k_lo, w.k_hi, w.n_slots, w.gamma)
+    cfg = qisg.Config(w.L, w.L_tau, ladder, w.n_replicas, w.n_samples, w.seed, layout=qisg.QISG_LAYOUT_SAMPLES)
+    with qisg.Instance(cfg) as inst:
+        inst.sweep(10)
+        inst.tau_observables(0, 1)
+        t0 = time.perf_counter()
+        inst.tau_observables()
+        wall = time.perf_counter() - t0
+    pairs = w.n_samples * w.n_replicas * w.n_slots * w.L_tau * w.L_tau
+    return {"workload": w.name, "s_per_call": wall, "configurations": w.n_samples * w.n_replicas * w.n_slots,
+            "ns_per_tau_pair": wall * 1e9 / pairs}
+
+
 def cpu_baseline(w, budget_s=15.0):
     """The oracle as it stands on the host cores: nproc samples of the same
     workload, as many sweeps as fit in about budget_s seconds."""
@@ -685,6 +736,10 @@ def run_gpu(args):
         line["paper_rule"] = daemon_entry(torch, qisg)
     if "serving" in extras and world == 1:
         line["serving"] = serving_entry(qisg, args.serving_requests)
+    if "transfer" in extras and world == 1:
+        line["transfer"] = transfer_entry(torch, qisg)
+    if "tau" in extras and world == 1:
+        line["tau_observables"] = tau_entry(torch, qisg)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w)
     # the other forms last, so that a tail of the line keeps them

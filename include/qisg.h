@@ -319,6 +319,28 @@ int qisg_block_sums(qisg_handle *h, int64_t first, int64_t n, int64_t *sumA, int
  * [n][n_slots].  Errors as qisg_block_sums.                                 */
 int qisg_block_means(qisg_handle *h, int64_t first, int64_t n, double *e_s, double *e_t);
 
+/* Imaginary-time observables (Appendix E.1: the tau-resolved overlaps
+ * Q_2(tau), Q_4(tau), F(tau) and the Euclidean correlation C(tau) of the
+ * analysis programs), computed on the configurations now at each slot.
+ * With q~_x(tau_1, tau) = S_{x,tau_1} S_{x,tau_1+tau} (tau_1 + tau taken
+ * modulo L_tau, as the paper does for both boundaries) and
+ * Q~(tau_1, tau) = sum_x q~_x, for every sample a_lo .. a_lo+n_a-1,
+ * replica r, slot s and lag tau = 0 .. L_tau-1, sums over tau_1:
+ *   S1 = sum Q~  (= L^2 L_tau times the site average of C_x(tau))
+ *   S2 = sum Q~^2, S4 = sum Q~^4   (L_tau Q_2(tau), L_tau Q_4(tau) of one
+ *                                   configuration)
+ *   SF = sum (|sum_x e^{i 2pi x_1/L} q~_x|^2 + |sum_x e^{i 2pi x_2/L} q~_x|^2)
+ *        (2 L_tau F(tau)); FP64 from the column and row sums of q~, x in
+ *        order 0 .. L-1, with a cos / sin table from the host's libm.
+ * Averages over measurements and replicas are the caller's.  Host arrays
+ * [n_a][n_replicas][n_slots][L_tau] (int64, int64, int64, double).  Spins
+ * are unpacked on the device in chunks through a temporary buffer of at
+ * most 256 MB (or one sample's spins), allocated outside the memory budget.
+ * EINVAL: sample range, L > 32, or 8 L L_tau bytes above 227 KB of shared
+ * memory.  Synchronises. */
+int qisg_tau_observables(qisg_handle *h, int64_t a_lo, int64_t n_a, int64_t *S1, int64_t *S2, int64_t *S4,
+                         double *SF);
+
 /* The uint32 Metropolis table in use: T[s][u_s][u_t] (u_s unsatisfied
  * spatial bonds 0..4, u_t unsatisfied tau bonds 0..2); a spin flips iff
  * T == 0xFFFFFFFF or its draw R < T.  Host uint32 [n_slots][5][3].         */
@@ -497,6 +519,29 @@ size_t qisg_batch_instance_bytes(const qisg_instance_desc *d);
 
 int qisg_batch_sync(qisg_batch *b);
 void qisg_batch_destroy(qisg_batch *b);
+
+/* The transfer-matrix product of the exact-diagonalisation code (Sec. 2.2,
+ * Eq. (transfer-matrix) and Appendix D), the matrix-vector product its
+ * Lanczos iteration is built on: out = T in on the even (parity = +1) or
+ * odd (parity = -1) sector of the transfer matrix
+ *   T = e^{-k H0/2} prod_j [jP 1 + jM sigma^X_j] e^{-k H0/2},
+ *   jP = e^{k_tau} / (e^{k_tau} + e^{-k_tau}), jM = e^{-k_tau} / (...),
+ * of the L x L sample with couplings J (host int8 [L*L][2], +-1: bond 0 of
+ * site x1 + L x2 to (x1+1, x2), bond 1 to (x1, x2+1), periodic; at L = 2
+ * the two bonds between a pair of sites are distinct, as in the sweeps).
+ * k_tau = k is the paper's case (its Gamma from exp(-2k) = tanh(k Gamma));
+ * other pairs are the separate-coupling form of the rest of this library.
+ * in, out: DEVICE arrays of 2^{L^2-1} doubles in the parity-aware basis
+ * |n>_{e,o} = (|n> +- |2^{L^2}-1-n>)/sqrt 2, n < 2^{L^2-1} (bit j of n set
+ * <=> S_j = -1); they may be the same array.  The L^2-1 bit-flip rounds
+ * j = 0 .. L^2-2 are applied in order, then the last factor of Eq. (lr);
+ * the results are those of that order with IEEE double arithmetic.  One GPU
+ * holds L <= 5 (2^24 doubles); the paper splits L = 6 over 256 GPUs.
+ * Allocates nothing; asynchronous on cuda_stream.  EINVAL: NULL pointer,
+ * L outside 2..5, parity not +-1, a coupling not +-1 or a k, k_tau negative
+ * or not finite, vectors not 8-byte aligned. */
+int qisg_transfer_matvec(const double *in, double *out, int L, double k, double k_tau, const int8_t *J,
+                         int parity, void *cuda_stream);
 
 /* Replica overlaps of a caller-owned configuration, computed without
  * allocating device memory.  (The paper has no counterpart: this is a

@@ -74,6 +74,10 @@ def _load():
             lib.orc_energies.restype = None
             lib.orc_pt_only.argtypes = [i32, i32, i64, u64, P, P, u64, P, P, P]
             lib.orc_pt_only.restype = None
+            lib.orc_tau_observables.argtypes = [i32, i32, i32, i32, i64, P, P, P, P, P, P]
+            lib.orc_tau_observables.restype = None
+            lib.orc_transfer_matvec.argtypes = [i32, f64, f64, P, i32, P, P]
+            lib.orc_transfer_matvec.restype = i32
             lib.orc_pow_by_squaring.argtypes = [f64, u64]
             lib.orc_pow_by_squaring.restype = f64
             lib.orc_xoroshiro128pp_step.argtypes = [P]
@@ -242,6 +246,32 @@ def pt_only(a: int, seed: int, k, ktau, t: int, walker_at_a: np.ndarray,
     _load().orc_pt_only(n_slots, n_rep, a, seed, _ptr(k), _ptr(kt), t, _ptr(walker_at_a),
                         _ptr(np.ascontiguousarray(A_a, dtype=np.int64)),
                         _ptr(np.ascontiguousarray(B_a, dtype=np.int64)))
+
+
+def tau_observables(L: int, Ltau: int, S: np.ndarray, walker_at: np.ndarray):
+    """Sums over tau_1 of Q~, Q~^2, Q~^4 and of the two squared Fourier
+    moduli (Appendix E.1) for the configuration at every slot:
+    four arrays [n_a][n_rep][n_slots][L_tau] (int64, int64, int64, float64)."""
+    n_a, n_rep, n_slots, _ = S.shape
+    shp = (n_a, n_rep, n_slots, Ltau)
+    S1, S2, S4 = (np.zeros(shp, dtype=np.int64) for _ in range(3))
+    SF = np.zeros(shp, dtype=np.float64)
+    _load().orc_tau_observables(L, Ltau, n_slots, n_rep, n_a, _ptr(np.ascontiguousarray(S, dtype=np.int8)),
+                                _ptr(np.ascontiguousarray(walker_at, dtype=np.int32)), _ptr(S1), _ptr(S2),
+                                _ptr(S4), _ptr(SF))
+    return S1, S2, S4, SF
+
+
+def transfer_matvec(L: int, k: float, ktau: float, J: np.ndarray, parity: int, v: np.ndarray) -> np.ndarray:
+    """T v on the even (+1) or odd (-1) parity sector (Sec. 2.2, Appendix D):
+    v has 2^(L^2-1) entries; J is [L*L][2] int8 of one sample."""
+    vin = np.ascontiguousarray(v, dtype=np.float64)
+    out = np.zeros_like(vin)
+    rc = _load().orc_transfer_matvec(L, float(k), float(ktau), _ptr(np.ascontiguousarray(J, dtype=np.int8)),
+                                     int(parity), _ptr(vin), _ptr(out))
+    if rc != 0:
+        raise MemoryError("oracle transfer matvec failed")
+    return out
 
 
 @dataclass

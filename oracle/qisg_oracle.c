@@ -614,3 +614,127 @@ void orc_pt_only(int n_slots, int n_rep, int64_t a, uint64_t seed, const double 
 }
 
 double orc_pow_by_squaring(double b, uint64_t e) { return pow_by_squaring(b, e); }
+
+/*
+ * Imaginary-time observables of Appendix E.1 for the configuration now at
+ * each slot: with q~_x(tau_1, tau) = S_{x,tau_1} S_{x,tau_1+tau} (tau_1 + tau
+ * modulo L_tau) and Q~ = sum_x q~, over tau_1 = 0 .. L_tau-1:
+ *   S1 = sum Q~, S2 = sum Q~^2, S4 = sum Q~^4 (int64),
+ *   SF = sum ( |sum_x e^{i 2pi x_1/L} q~_x|^2 + |sum_x e^{i 2pi x_2/L} q~_x|^2 )
+ * (FP64).  The two Fourier sums are taken over the column sums
+ * C(x_1) = sum_{x_2} q~ and the row sums R(x_2) = sum_{x_1} q~, x = 0 .. L-1
+ * in order, real and imaginary parts accumulated separately, no contraction.
+ * S [n_a][n_rep][n_slots walkers][N] int8, walker_at [n_a][n_rep][n_slots];
+ * outputs [n_a][n_rep][n_slots][L_tau].
+ */
+void orc_tau_observables(int L, int Ltau, int n_slots, int n_rep, int64_t n_a, const int8_t *S,
+                         const int32_t *walker_at, int64_t *S1, int64_t *S2, int64_t *S4, double *SF)
+{
+    const double pi = 3.14159265358979323846;
+    const int64_t N = (int64_t)L * L * Ltau, P = (int64_t)L * L;
+    double *cs = (double *)malloc(sizeof(double) * 2 * (size_t)L);
+    double *sn = cs + L;
+    int64_t c;
+    int x;
+    for (x = 0; x < L; ++x) {
+        cs[x] = cos(2.0 * pi * x / L);
+        sn[x] = sin(2.0 * pi * x / L);
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (c = 0; c < n_a * n_rep * n_slots; ++c) {
+        const int64_t ar = c / n_slots;
+        const int w = walker_at[c];
+        const int8_t *Sw = S + (ar * n_slots + w) * N;
+        int tau;
+        for (tau = 0; tau < Ltau; ++tau) {
+            int64_t s1 = 0, s2 = 0, s4 = 0;
+            double sf = 0.0;
+            int t1;
+            for (t1 = 0; t1 < Ltau; ++t1) {
+                const int t2 = (t1 + tau) % Ltau;
+                int64_t q = 0;
+                double re1 = 0.0, im1 = 0.0, re2 = 0.0, im2 = 0.0;
+                int xx;
+                for (xx = 0; xx < L; ++xx) {
+                    int64_t R = 0, C = 0;
+                    int j;
+                    for (j = 0; j < L; ++j) {
+                        R += Sw[j + (int64_t)L * xx + P * t1] * Sw[j + (int64_t)L * xx + P * t2];   /* x_2 = xx */
+                        C += Sw[xx + (int64_t)L * j + P * t1] * Sw[xx + (int64_t)L * j + P * t2];   /* x_1 = xx */
+                    }
+                    q += R;
+                    re1 = re1 + cs[xx] * (double)C;
+                    im1 = im1 + sn[xx] * (double)C;
+                    re2 = re2 + cs[xx] * (double)R;
+                    im2 = im2 + sn[xx] * (double)R;
+                }
+                s1 += q;
+                s2 += q * q;
+                s4 += (q * q) * (q * q);
+                sf = sf + ((re1 * re1 + im1 * im1) + (re2 * re2 + im2 * im2));
+            }
+            S1[c * Ltau + tau] = s1;
+            S2[c * Ltau + tau] = s2;
+            S4[c * Ltau + tau] = s4;
+            SF[c * Ltau + tau] = sf;
+        }
+    }
+    free(cs);
+}
+
+/*
+ * The transfer-matrix product of the exact-diagonalisation code (Sec. 2.2,
+ * Eq. (transfer-matrix); Appendix D): out = T in on the even (parity = +1)
+ * or odd (parity = -1) sector, in the parity-aware basis |n>_{e,o},
+ * n = 0 .. 2^{L^2-1}-1.  With separate couplings (k, k_tau):
+ *   T = e^{-k H0 / 2} prod_j [jP 1_j + jM sigma^X_j] e^{-k H0 / 2},
+ *   jP = e^{k_tau} / (e^{k_tau} + e^{-k_tau}), jM = e^{-k_tau} / (...),
+ * which is Eq. (expH1) when exp(-2 k_tau) = tanh(k Gamma) (k_tau = k for the
+ * paper's equal coupling).  Steps, in the paper's order:
+ *   psi[n] = in[n] w[n],  w[n] = exp((k/2) sum_bonds J S_x S_y), n read as an
+ *            L^2-bit integer with the top bit 0 (bit j set <=> S_j = -1);
+ *   rounds j = 0 .. L^2-2: psi'[n] = jP psi[n] + jM psi[n ^ 2^j];
+ *   the last factor (j = L^2-1, Eq. (lr)): psi'[n] = jP psi[n] +
+ *            parity jM psi[(2^{L^2-1}-1) - n];
+ *   out[n] = psi[n] w[n].
+ * Bonds: J [L*L][2] (+-1), bond 0 of site j = x1 + L x2 joins it to
+ * (x1+1, x2), bond 1 to (x1, x2+1), periodic.  Vectors of 2^{L^2-1} doubles.
+ */
+int orc_transfer_matvec(int L, double k, double ktau, const int8_t *J, int parity, const double *in, double *out)
+{
+    const int nb = L * L - 1;
+    const uint64_t n_el = (uint64_t)1 << nb;
+    const double ek = exp(ktau), emk = exp(-ktau);
+    const double jP = ek / (ek + emk), jM = emk / (ek + emk);
+    double *w = (double *)malloc(sizeof(double) * n_el);
+    double *psi = (double *)malloc(sizeof(double) * n_el);
+    double *scra = (double *)malloc(sizeof(double) * n_el);
+    uint64_t n;
+    int j;
+    if (!w || !psi || !scra) { free(w); free(psi); free(scra); return -1; }
+    for (n = 0; n < n_el; ++n) {
+        int64_t e = 0;
+        int x1, x2;
+        for (x2 = 0; x2 < L; ++x2)
+            for (x1 = 0; x1 < L; ++x1) {
+                const int i = x1 + L * x2;
+                const int ix = (x1 + 1) % L + L * x2, iy = x1 + L * ((x2 + 1) % L);
+                const int si = (n >> i) & 1u ? -1 : 1;
+                const int sx = (n >> ix) & 1u ? -1 : 1;
+                const int sy = (n >> iy) & 1u ? -1 : 1;
+                e += J[2 * i] * si * sx + J[2 * i + 1] * si * sy;
+            }
+        w[n] = exp(0.5 * k * (double)e);
+    }
+    for (n = 0; n < n_el; ++n) psi[n] = in[n] * w[n];
+    for (j = 0; j < nb; ++j) {
+        for (n = 0; n < n_el; ++n) scra[n] = jP * psi[n] + jM * psi[n ^ ((uint64_t)1 << j)];
+        { double *tmp = psi; psi = scra; scra = tmp; }
+    }
+    for (n = 0; n < n_el; ++n) scra[n] = jP * psi[n] + (double)parity * jM * psi[(n_el - 1) - n];
+    for (n = 0; n < n_el; ++n) out[n] = scra[n] * w[n];
+    free(w); free(psi); free(scra);
+    return 0;
+}

@@ -457,6 +457,21 @@ int set_spins_t(qisg_handle *h, const int8_t *S) {
   return rc;
 }
 
+int lanes_stage_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *d) {
+  const int64_t n = n_a * h->n_rep * h->n_slots * h->N;
+  if (n == 0) return QISG_OK;
+  if (h->W == 64)
+    lanes_extract_kernel<unsigned long long><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+        reinterpret_cast<const unsigned long long *>(h->spins), d, a_lo, n_a, h->N, h->n_rep, h->n_slots, h->rpw,
+        h->n_groups);
+  else
+    lanes_extract_kernel<unsigned int><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+        reinterpret_cast<const unsigned int *>(h->spins), d, a_lo, n_a, h->N, h->n_rep, h->n_slots, h->rpw,
+        h->n_groups);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "unpack spins");
+}
+
 int lanes_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
   return h->W == 64 ? get_spins_t<unsigned long long>(h, a_lo, n_a, S) : get_spins_t<unsigned int>(h, a_lo, n_a, S);
 }

@@ -597,6 +597,11 @@ int samples_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S);
 int samples_set_spins(qisg_handle *h, const int8_t *S, const int32_t *walker_at);
 int samples_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J);
 int samples_set_couplings(qisg_handle *h, const int8_t *J);
+// unpack samples a_lo .. a_lo+n_a-1 by walker into a device int8 buffer
+// [n_a][n_rep][n_slots][N] (+-1), on the handle's stream
+int lanes_stage_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *d);
+int sites_stage_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *d);
+int samples_stage_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *d);
 // persistent form: n sweeps (red, blue, PT) in one cooperative launch
 bool samples_persistent_ok(const qisg_handle *h);
 int samples_persistent(qisg_handle *h, int n_sweeps);

@@ -1897,6 +1897,23 @@ int samples_energies_by_slot(qisg_handle *h) {
   h->launches++;
   return cuda_check(cudaGetLastError(), "samples energies");
 }
+int samples_stage_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *d) {
+  const int64_t n = n_a * h->n_rep * h->n_slots * h->N;
+  if (n == 0) return QISG_OK;
+  int rc = samples_materialize(h);
+  if (rc) return rc;
+  if (h->W == 64)
+    samples_extract_kernel<unsigned long long><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+        reinterpret_cast<const unsigned long long *>(h->spins), h->d_walker, d, a_lo, n_a, h->N, h->n_slots, h->n_q,
+        h->n_rep);
+  else
+    samples_extract_kernel<unsigned int><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+        reinterpret_cast<const unsigned int *>(h->spins), h->d_walker, d, a_lo, n_a, h->N, h->n_slots, h->n_q,
+        h->n_rep);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "unpack spins");
+}
+
 int samples_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
   return h->W == 64 ? get_spins_t<unsigned long long>(h, a_lo, n_a, S)
                     : get_spins_t<unsigned int>(h, a_lo, n_a, S);

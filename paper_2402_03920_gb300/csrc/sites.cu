@@ -567,6 +567,16 @@ int sites_measure(qisg_handle *h, int force_to_q) {
   return lanes_finalize(h, force_to_q);
 }
 
+int sites_stage_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *d) {
+  const int M = h->Lt / 32, plane = h->L * h->L, n_words = plane * M;
+  const int64_t n_sys = n_a * h->n_rep * h->n_slots, n = n_sys * h->N;
+  if (n == 0) return QISG_OK;
+  sites_extract_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+      reinterpret_cast<const uint32_t *>(h->spins), d, a_lo * h->n_rep * h->n_slots, n_sys, plane, M, n_words, h->N);
+  h->launches++;
+  return cuda_check(cudaGetLastError(), "unpack spins");
+}
+
 int sites_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
   const int M = h->Lt / 32, plane = h->L * h->L, n_words = plane * M;
   const int64_t per_sys = h->N, n_sys = n_a * h->n_rep * h->n_slots, sys_lo = a_lo * h->n_rep * h->n_slots;

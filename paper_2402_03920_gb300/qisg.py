@@ -75,6 +75,7 @@ def load(build_if_missing: bool = True):
         "qisg_slot_means": (I, [P, P, P, P]),
         "qisg_thresholds": (I, [P, P]),
         "qisg_walk_history": (I, [P, I64, I64, P]),
+        "qisg_tau_observables": (I, [P, I64, I64, P, P, P, P]),
         "qisg_checkpoint_save": (I, [P, ctypes.c_char_p]),
         "qisg_checkpoint_load": (I, [P, ctypes.c_char_p]),
         "qisg_checkpoint_verify": (I, [ctypes.c_char_p, P]),
@@ -110,6 +111,7 @@ def load(build_if_missing: bool = True):
         "qisg_profile_read": (I, [P, I, P, P, P]),
         "qisg_daemon_tables": (I, [D, I, P, P]),
         "qisg_overlaps_noalloc": (I, [P, I, I, I, I, I, I64, P, P]),
+        "qisg_transfer_matvec": (I, [P, P, I, D, D, P, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -124,7 +126,7 @@ def exported_symbols():
     return ["qisg_opts_default", "qisg_ladder_linear", "qisg_create", "qisg_sweep", "qisg_pt_swap",
             "qisg_energies", "qisg_overlaps", "qisg_permutation", "qisg_get_spins",
             "qisg_get_couplings", "qisg_set_couplings", "qisg_set_state", "qisg_pt_given", "qisg_measurements",
-            "qisg_slot_means", "qisg_walk_history", "qisg_block_sums", "qisg_block_means",
+            "qisg_slot_means", "qisg_walk_history", "qisg_block_sums", "qisg_block_means", "qisg_tau_observables",
             "qisg_checkpoint_save", "qisg_checkpoint_load", "qisg_checkpoint_verify",
             "qisg_thresholds", "qisg_sweep_count", "qisg_layout",
             "qisg_launch_count", "qisg_sync", "qisg_destroy", "qisg_strerror", "qisg_last_error",
@@ -133,7 +135,7 @@ def exported_symbols():
             "qisg_batch_run", "qisg_batch_set_schedule", "qisg_batch_set_wait_limit", "qisg_batch_autotune",
             "qisg_batch_status",
             "qisg_batch_results", "qisg_batch_info", "qisg_batch_instance_bytes", "qisg_batch_sync",
-            "qisg_batch_destroy", "qisg_daemon_tables", "qisg_overlaps_noalloc"]
+            "qisg_batch_destroy", "qisg_daemon_tables", "qisg_overlaps_noalloc", "qisg_transfer_matvec"]
 
 
 def _check(rc: int):
@@ -349,6 +351,17 @@ class Instance:
     def checkpoint_load(self, path: str):
         _check(load().qisg_checkpoint_load(self._h, os.fsencode(path)))
 
+    def tau_observables(self, a_lo: int = 0, n_a: int | None = None):
+        """Sums over tau_1 of Q~, Q~^2, Q~^4 and the squared Fourier moduli of
+        q~ (Appendix E.1) for the configuration at every slot of samples
+        a_lo .. a_lo+n_a-1: four arrays [n_a][n_replicas][n_slots][L_tau]."""
+        n_a = self.n_samples - a_lo if n_a is None else n_a
+        shp = (n_a, self.n_rep, self.n_slots, self.L_tau)
+        S1, S2, S4 = (np.zeros(shp, dtype=np.int64) for _ in range(3))
+        SF = np.zeros(shp, dtype=np.float64)
+        _check(load().qisg_tau_observables(self._h, a_lo, n_a, _ptr(S1), _ptr(S2), _ptr(S4), _ptr(SF)))
+        return S1, S2, S4, SF
+
     def walk_history(self, first: int, n: int) -> np.ndarray:
         """Slot of every walker at measurements first .. first+n-1:
         [n][n_samples][n_replicas][n_slots] uint8."""
@@ -437,6 +450,15 @@ def philox4x32_10_device(ctr_dev_ptr: int, key_dev_ptr: int, out_dev_ptr: int, n
                          stream: int | None = None):
     """Device Philox on device buffers (pointers from torch tensors)."""
     _check(load().qisg_philox4x32_10(ctr_dev_ptr, key_dev_ptr, out_dev_ptr, n, stream))
+
+
+def transfer_matvec(in_ptr: int, out_ptr: int, L: int, k: float, k_tau: float, J: np.ndarray, parity: int,
+                    stream: int | None = None):
+    """out = T in on a parity sector (device pointers of 2^(L^2-1) doubles,
+    e.g. from torch tensors); J host int8 [L*L][2]."""
+    Jc = _sized(J, np.int8, L * L * 2, "J [L*L][2]")
+    _check(load().qisg_transfer_matvec(in_ptr, out_ptr, L, float(k), float(k_tau), _ptr(Jc), int(parity),
+                                       stream if stream is not None else current_stream_ptr()))
 
 
 class CheckpointInfo(ctypes.Structure):
