@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--forms", default="batched,per_instance")
-    p.add_argument("--extras", default="uneven,large,paper,daemon,serving,transfer,tau",
+    p.add_argument("--extras", default="uneven,large,paper,daemon,serving,transfer,tau,overlap",
                    help="other workloads measured beside the headline (empty: none)")
     p.add_argument("--serving-requests", type=int, default=100)
     p.add_argument("--tiles", default="",
@@ -155,6 +155,9 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
+OVERLAP = True   # programmatic dependent launch of the batched form's kernels
+
+
 def make_instance(qisg, w, form, seed):
     ladder = qisg.ladder_linear(w.k_lo, w.k_hi, w.n_slots, w.gamma)
     if form == "per_instance":
@@ -164,7 +167,10 @@ def make_instance(qisg, w, form, seed):
     else:
         cfg = qisg.Config(w.L, w.L_tau, ladder, w.n_replicas, w.n_samples, seed, word_bits=0,
                           measure_every=w.measure_every, layout=batched_layout(qisg))
-    return qisg.Instance(cfg)
+    inst = qisg.Instance(cfg)
+    if form != "per_instance" and not OVERLAP:
+        inst.set_launch_overlap(False)
+    return inst
 
 
 def batched_layout(qisg):
@@ -630,6 +636,21 @@ def tau_entry(torch, qisg):
             "ns_per_tau_pair": wall * 1e9 / pairs}
 
 
+def overlap_entry(torch, qisg, steps, warmup, seed):
+    """The batched form with and without programmatic dependent launch of its
+    kernels (same schedule, same trajectory): ps per update of each."""
+    global OVERLAP
+    w = workload()
+    out = {}
+    for on in (True, False):
+        OVERLAP = on
+        total_ms, _, _, _, _ = time_form(torch, qisg, w, "batched", steps, warmup, seed)
+        out["on" if on else "off"] = total_ms * 1e9 / (updates_per_step(w) * steps)
+    OVERLAP = True
+    out["unit"] = UNIT
+    return out
+
+
 def cpu_baseline(w, budget_s=15.0):
     """The oracle as it stands on the host cores: nproc samples of the same
     workload, as many sweeps as fit in about budget_s seconds."""
@@ -740,6 +761,8 @@ def run_gpu(args):
         line["transfer"] = transfer_entry(torch, qisg)
     if "tau" in extras and world == 1:
         line["tau_observables"] = tau_entry(torch, qisg)
+    if "overlap" in extras and world == 1:
+        line["launch_overlap"] = overlap_entry(torch, qisg, args.steps, args.warmup, seed)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(w)
     # the other forms last, so that a tail of the line keeps them

@@ -388,6 +388,13 @@ int qisg_profile_read(qisg_handle *h, int kind, double *total_ms, int64_t *n_tim
  * the same either way. */
 int qisg_set_graphs(qisg_handle *h, int enable);
 
+/* SAMPLES packing: launch the kernels of a sweep with programmatic dependent
+ * launch (enable = 1, the default): each kernel may be scheduled while the
+ * one before it finishes, and waits for it on the device before it reads
+ * its results, which hides the gaps between the red, blue, PT and
+ * measurement launches.  Results are the same either way.  Synchronises. */
+int qisg_set_launch_overlap(qisg_handle *h, int enable);
+
 /* The persistent form of the batched sweep (SAMPLES packing, 32-bit words,
  * PT every sweep; Sec. 2.1's red / blue / PT cycle): enable = 1 runs every
  * stretch of sweeps up to the next measurement (or 64 sweeps when nothing

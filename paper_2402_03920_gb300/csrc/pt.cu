@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsign
                                                          const unsigned long long *d_t, uint2 key,
                                                          int64_t n_samples, int n_rep, int n_slots,
                                                          int explicit_pass, unsigned long long *adv) {
+  pdl_begin();
   constexpr int W = (int)sizeof(Word) * 8, octs = W / 8;
   __shared__ uint32_t bits[8];
   const uint32_t bid = blockIdx.x;
@@ -79,9 +80,9 @@ __global__ void __launch_bounds__(256) pt_samples_kernel(int32_t *walker, unsign
 template <typename Word, bool WIDE>
 void launch_pt_samples(qisg_handle *h, uint2 key, int explicit_pass, unsigned long long *adv) {
   const unsigned blocks = (unsigned)(h->n_b * h->n_rep * (h->W / 8));
-  pt_samples_kernel<Word, WIDE><<<blocks, 256, 0, h->stream>>>(
-      h->d_walker, h->d_U, reinterpret_cast<Word *>(h->d_acc), reinterpret_cast<const PTConst *>(h->d_ptc),
-      h->d_sq, h->d_t, key, h->n_samples, h->n_rep, h->n_slots, explicit_pass, adv);
+  launch_kernel(h->pdl, pt_samples_kernel<Word, WIDE>, dim3(blocks), dim3(256), 0, h->stream, h->d_walker, h->d_U,
+                reinterpret_cast<Word *>(h->d_acc), reinterpret_cast<const PTConst *>(h->d_ptc), h->d_sq, h->d_t, key,
+                h->n_samples, h->n_rep, h->n_slots, explicit_pass, adv);
 }
 
 }  // namespace

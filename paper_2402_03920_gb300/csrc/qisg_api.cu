@@ -657,6 +657,15 @@ int qisg_sweep(qisg_handle *h, int64_t n_sweeps) {
   return QISG_OK;
 }
 
+int qisg_set_launch_overlap(qisg_handle *h, int enable) {
+  if (!h) return fail(QISG_EINVAL, "NULL handle");
+  int rc = sync_handle(h);
+  if (rc) return rc;
+  h->pdl = enable != 0;
+  drop_cycle(h);
+  return QISG_OK;
+}
+
 int qisg_set_persistent(qisg_handle *h, int enable, int64_t wait_ns) {
   if (!h || wait_ns < 0) return fail(QISG_EINVAL, "bad handle or wait_ns < 0");
   if (enable && !samples_persistent_ok(h))

@@ -247,6 +247,35 @@ __device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua
   return acc;
 }
 
+// ---- programmatic dependent launch ----
+//
+// A kernel launched with launch_kernel(pdl = true, ...) may be scheduled
+// while the kernel before it on the stream is finishing; it must call
+// pdl_begin() before it touches global memory that kernel writes (the wait
+// returns once that kernel has completed and its writes are visible; with
+// no such dependency it returns at once).  pdl_begin then lets the next
+// kernel on the stream be scheduled as this one's blocks retire.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_kernel(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // ---- persistent kernels ----
 
 constexpr long long kBarrierTimeoutNs = 5000000000ll;   // default bound of a grid-barrier wait: 5 s
@@ -467,6 +496,8 @@ struct qisg_handle {
   // persistent form (SAMPLES, 32-bit words, PT every sweep): one cooperative
   // launch per run of sweeps between measurements
   bool persistent = false;
+  // SAMPLES sweep-path kernels launched with programmatic dependent launch
+  bool pdl = true;
   unsigned *d_bar = nullptr;        // grid barrier of the persistent kernel
   long long wait_ns = 5000000000ll; // bound of each barrier wait
   cudaStream_t stream = nullptr;

@@ -176,6 +176,7 @@ template <typename Word, bool BLUE, int G2>
 __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<Word> p,
                                                                     const __grid_constant__ SlotThresholds th,
                                                                     int colour, int count_only) {
+  pdl_begin();
   constexpr int W = (int)sizeof(Word) * 8;
   constexpr int KS = G2 + 5;   // u_s sum <= 4 * 4 * 2^G2 per thread
   constexpr int KT = G2 + 4;   // u_t sum <= 2 * 4 * 2^G2 per thread
@@ -394,6 +395,7 @@ using FusedRedArgs = FusedRedArgsT<uint32_t>;
 
 __global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedRedArgs p,
                                                                      const __grid_constant__ SlotThresholds th) {
+  pdl_begin();
   __shared__ uint32_t msk[4][kMaxSlotsPT];
   __shared__ uint4 rnd[kBlock4];   // per warp: [slot in group][quad][replica]
   const uint32_t bid = blockIdx.x;
@@ -717,6 +719,7 @@ __device__ __forceinline__ void red_fusedq_body(const FusedRedArgsT<Word> &p, co
 template <typename Word, int RP>
 __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const FusedRedArgsT<Word> p,
                                                                       const __grid_constant__ SlotThresholds th) {
+  pdl_begin();
   {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
@@ -912,6 +915,7 @@ template <bool BLUE, int G2, bool PF>
 __global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uint32_t> p,
                                                                   const __grid_constant__ SlotThresholds th,
                                                                   int colour, int count_only) {
+  pdl_begin();
   {   // counters / masks the host asked this pass to clear (nothing reads them before the next pass)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
@@ -933,6 +937,7 @@ __global__ void __launch_bounds__(kBlock) samples_permute_kernel(Word *spins, co
                                                                  int n_slots, int n_q, int n_rep,
                                                                  int blocks_per_set,
                                                                  unsigned long long *advance) {
+  pdl_begin();
   __shared__ Word accs[4 * kMaxSlotsPermute];
   __shared__ int any;
   if (advance && blockIdx.x == 0 && threadIdx.x == 0) *advance += 1ull;
@@ -979,6 +984,7 @@ __global__ void __launch_bounds__(kBlock4) samples_permute4_kernel(uint4 *spins,
                                                                     int n_slots, int n_q, int n_rep,
                                                                     int blocks_per_set,
                                                                     unsigned long long *advance) {
+  pdl_begin();
   __shared__ uint32_t msk[4][NS];
   if (advance && blockIdx.x == 0 && threadIdx.x == 0) *advance += 1ull;
   const int64_t set = blockIdx.x / blocks_per_set;     // (b, q)
@@ -1024,6 +1030,7 @@ template <typename Word, int K>
 __global__ void __launch_bounds__(kBlock4) samples_overlap4_kernel(const Word *spins, long long *qcnt, int64_t N,
                                                                     int n_slots, int n_rep, int64_t n_samples,
                                                                     int sites_per_thread, int blocks_per_set) {
+  pdl_begin();
   constexpr int W = (int)sizeof(Word) * 8;
   constexpr int KF = K + kLog2Block4;
   __shared__ Word buf[3 * KF * kBlock4];
@@ -1079,6 +1086,7 @@ __global__ void samples_finalize2_kernel(const unsigned long long *__restrict__ 
                                          long long *__restrict__ sumA, long long *__restrict__ sumB,
                                          long long *__restrict__ sumq, long long *__restrict__ sumq2, int64_t n_a,
                                          int n_rep, int n_slots, int64_t N, int to_q_only) {
+  pdl_begin();
   const int n_pairs = n_rep * (n_rep - 1) / 2;
   const int items = n_rep + n_pairs;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1112,6 +1120,7 @@ __global__ void __launch_bounds__(kBlock) samples_overlap_kernel(const Word *spi
                                                                  int64_t N, int n_slots, int n_q,
                                                                  int n_rep, int64_t n_samples,
                                                                  int sites_per_thread) {
+  pdl_begin();
   constexpr int W = (int)sizeof(Word) * 8;
   __shared__ int acc[W];
   const int n_pairs = n_rep * (n_rep - 1) / 2;
@@ -1364,26 +1373,27 @@ SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
 }
 
 template <typename Word, bool BLUE, int G2>
-void launch_sweep(const SamplesArgs<Word> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
+void launch_sweep(bool pdl, const SamplesArgs<Word> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
                   int colour, int count_only) {
-  samples_half_sweep_kernel<Word, BLUE, G2><<<blocks, kBlock, 0, st>>>(p, th, colour, count_only);
+  launch_kernel(pdl, samples_half_sweep_kernel<Word, BLUE, G2>, dim3(blocks), dim3(kBlock), 0, st, p, th, colour,
+                count_only);
 }
 
 template <typename Word, bool BLUE>
-void launch_sweep_g(const SamplesArgs<Word> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
+void launch_sweep_g(bool pdl, const SamplesArgs<Word> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
                     int colour, int count_only) {
   // counter planes for G sites per thread: G2 = ceil(log2(G / 4))
   int g2 = 0;
   while ((4 << g2) < p.seg_sites) ++g2;
   switch (g2) {
-    case 0: launch_sweep<Word, BLUE, 0>(p, th, blocks, st, colour, count_only); break;
-    case 1: launch_sweep<Word, BLUE, 1>(p, th, blocks, st, colour, count_only); break;
-    case 2: launch_sweep<Word, BLUE, 2>(p, th, blocks, st, colour, count_only); break;
-    case 3: launch_sweep<Word, BLUE, 3>(p, th, blocks, st, colour, count_only); break;
-    case 4: launch_sweep<Word, BLUE, 4>(p, th, blocks, st, colour, count_only); break;
-    case 5: launch_sweep<Word, BLUE, 5>(p, th, blocks, st, colour, count_only); break;
-    case 6: launch_sweep<Word, BLUE, 6>(p, th, blocks, st, colour, count_only); break;
-    default: launch_sweep<Word, BLUE, 7>(p, th, blocks, st, colour, count_only); break;
+    case 0: launch_sweep<Word, BLUE, 0>(pdl, p, th, blocks, st, colour, count_only); break;
+    case 1: launch_sweep<Word, BLUE, 1>(pdl, p, th, blocks, st, colour, count_only); break;
+    case 2: launch_sweep<Word, BLUE, 2>(pdl, p, th, blocks, st, colour, count_only); break;
+    case 3: launch_sweep<Word, BLUE, 3>(pdl, p, th, blocks, st, colour, count_only); break;
+    case 4: launch_sweep<Word, BLUE, 4>(pdl, p, th, blocks, st, colour, count_only); break;
+    case 5: launch_sweep<Word, BLUE, 5>(pdl, p, th, blocks, st, colour, count_only); break;
+    case 6: launch_sweep<Word, BLUE, 6>(pdl, p, th, blocks, st, colour, count_only); break;
+    default: launch_sweep<Word, BLUE, 7>(pdl, p, th, blocks, st, colour, count_only); break;
   }
 }
 
@@ -1421,18 +1431,25 @@ SamplesArgs<uint32_t> make_args4(qisg_handle *h, int colour, SlotThresholds &th)
 }
 
 template <bool BLUE, bool PF>
-void launch_sweep4(const SamplesArgs<uint32_t> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
+void launch_sweep4(bool pdl, const SamplesArgs<uint32_t> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
                    int colour, int count_only) {
   if constexpr (!BLUE) {   // the red pass keeps no counters
-    samples_sweep4_kernel<false, 0, PF><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only);
+    launch_kernel(pdl, samples_sweep4_kernel<false, 0, PF>, dim3(blocks), dim3(kBlock4), 0, st, p, th, colour,
+                  count_only);
   } else {
     int g2 = 0;
     while ((4 << g2) < p.seg_sites) ++g2;
     switch (g2) {
 #define QISG_CASE(n) \
-  case n: samples_sweep4_kernel<true, n, PF><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only); break;
+  case n:                                                                                                      \
+    launch_kernel(pdl, samples_sweep4_kernel<true, n, PF>, dim3(blocks), dim3(kBlock4), 0, st, p, th, colour,    \
+                  count_only);                                                                                 \
+    break;
       QISG_CASE(0) QISG_CASE(1) QISG_CASE(2) QISG_CASE(3) QISG_CASE(4)
-      default: samples_sweep4_kernel<true, 5, PF><<<blocks, kBlock4, 0, st>>>(p, th, colour, count_only); break;
+      default:
+        launch_kernel(pdl, samples_sweep4_kernel<true, 5, PF>, dim3(blocks), dim3(kBlock4), 0, st, p, th, colour,
+                      count_only);
+        break;
 #undef QISG_CASE
     }
   }
@@ -1490,16 +1507,16 @@ int fused_red(qisg_handle *h) {
   if constexpr (sizeof(Word) == 4) {
     const FusedRedArgs &p32 = p;
     if (tpsite == 4)
-      samples_red_fused_kernel<<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p32, th);
+      launch_kernel(h->pdl, samples_red_fused_kernel, dim3((unsigned)blocks), dim3(kBlock4), 0, h->stream, p32, th);
     else if (tpsite == 2)
-      samples_red_fusedq_kernel<uint32_t, 2><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+      launch_kernel(h->pdl, samples_red_fusedq_kernel<uint32_t, 2>, dim3((unsigned)blocks), dim3(kBlock4), 0, h->stream, p, th);
     else
-      samples_red_fusedq_kernel<uint32_t, 4><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+      launch_kernel(h->pdl, samples_red_fusedq_kernel<uint32_t, 4>, dim3((unsigned)blocks), dim3(kBlock4), 0, h->stream, p, th);
   } else {
     if (tpsite == 4)
-      samples_red_fusedq_kernel<Word, 1><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+      launch_kernel(h->pdl, samples_red_fusedq_kernel<Word, 1>, dim3((unsigned)blocks), dim3(kBlock4), 0, h->stream, p, th);
     else
-      samples_red_fusedq_kernel<Word, 2><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(p, th);
+      launch_kernel(h->pdl, samples_red_fusedq_kernel<Word, 2>, dim3((unsigned)blocks), dim3(kBlock4), 0, h->stream, p, th);
   }
   prof_end(h, QISG_KERNEL_SWEEP, tok);
   h->launches++;
@@ -1532,9 +1549,9 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
     // current one (measured: 4% off the production sweep, with the tuner then
     // taking walks of 4 sites)
     if (colour == 1)
-      launch_sweep4<true, true>(p, th, (unsigned)blocks, h->stream, 1, count_only);
+      launch_sweep4<true, true>(h->pdl, p, th, (unsigned)blocks, h->stream, 1, count_only);
     else
-      launch_sweep4<false, false>(p, th, (unsigned)blocks, h->stream, 0, count_only);
+      launch_sweep4<false, false>(h->pdl, p, th, (unsigned)blocks, h->stream, 0, count_only);
     prof_end(h, sweep_kind(colour), tok);
     h->launches++;
     return cuda_check(cudaGetLastError(), "samples half sweep");
@@ -1556,9 +1573,9 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
     return fail(QISG_EINVAL, "lattice too large for one launch");
   const int tok = prof_begin(h, sweep_kind(colour));
   if (colour == 1)
-    launch_sweep_g<Word, true>(p, th, (unsigned)blocks, h->stream, 1, count_only);
+    launch_sweep_g<Word, true>(h->pdl, p, th, (unsigned)blocks, h->stream, 1, count_only);
   else
-    launch_sweep<Word, false, 0>(p, th, (unsigned)blocks, h->stream, 0, count_only);
+    launch_sweep<Word, false, 0>(h->pdl, p, th, (unsigned)blocks, h->stream, 0, count_only);
   prof_end(h, sweep_kind(colour), tok);
   h->launches++;
   return cuda_check(cudaGetLastError(), "samples half sweep");
@@ -1605,20 +1622,20 @@ int permute_t(qisg_handle *h, int advance) {
     uint4 *sp = reinterpret_cast<uint4 *>(h->spins);
     const uint32_t *ac = reinterpret_cast<const uint32_t *>(h->d_acc);
     if (h->n_slots <= 8)
-      samples_permute4_kernel<8><<<blocks, kBlock4, 0, h->stream>>>(sp, ac, h->N, h->n_slots, h->n_q, h->n_rep,
+      launch_kernel(h->pdl, samples_permute4_kernel<8>, dim3(blocks), dim3(kBlock4), 0, h->stream, sp, ac, h->N, h->n_slots, h->n_q, h->n_rep,
                                                                    (int)per_set, adv);
     else if (h->n_slots <= 16)
-      samples_permute4_kernel<16><<<blocks, kBlock4, 0, h->stream>>>(sp, ac, h->N, h->n_slots, h->n_q, h->n_rep,
+      launch_kernel(h->pdl, samples_permute4_kernel<16>, dim3(blocks), dim3(kBlock4), 0, h->stream, sp, ac, h->N, h->n_slots, h->n_q, h->n_rep,
                                                                     (int)per_set, adv);
     else
-      samples_permute4_kernel<32><<<blocks, kBlock4, 0, h->stream>>>(sp, ac, h->N, h->n_slots, h->n_q, h->n_rep,
+      launch_kernel(h->pdl, samples_permute4_kernel<32>, dim3(blocks), dim3(kBlock4), 0, h->stream, sp, ac, h->N, h->n_slots, h->n_q, h->n_rep,
                                                                     (int)per_set, adv);
   } else {
     const int64_t per_set = (h->N * 4 + kBlock - 1) / kBlock;
     const int64_t blocks = h->n_b * h->n_q * per_set;
-    samples_permute_kernel<Word><<<(unsigned)blocks, kBlock, 0, h->stream>>>(
-        reinterpret_cast<Word *>(h->spins), reinterpret_cast<const Word *>(h->d_acc), h->N, h->n_slots,
-        h->n_q, h->n_rep, (int)per_set, adv);
+    launch_kernel(h->pdl, samples_permute_kernel<Word>, dim3((unsigned)blocks), dim3(kBlock), 0, h->stream,
+                  reinterpret_cast<Word *>(h->spins), reinterpret_cast<const Word *>(h->d_acc), h->N, h->n_slots,
+                  h->n_q, h->n_rep, (int)per_set, adv);
   }
   prof_end(h, QISG_KERNEL_PERMUTE, tok);
   h->launches++;
@@ -1636,9 +1653,9 @@ int measure_t(qisg_handle *h, int force_to_q) {
     const int64_t blocks = h->n_b * h->n_slots * per_set;
     if (blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
     const int tok = prof_begin(h, QISG_KERNEL_MEASURE);
-    samples_overlap4_kernel<Word, K><<<(unsigned)blocks, kBlock4, 0, h->stream>>>(
-        reinterpret_cast<const Word *>(h->spins), h->d_q, h->N, h->n_slots, h->n_rep, h->n_samples, spt,
-        (int)per_set);
+    launch_kernel(h->pdl, samples_overlap4_kernel<Word, K>, dim3((unsigned)blocks), dim3(kBlock4), 0, h->stream,
+                  reinterpret_cast<const Word *>(h->spins), h->d_q, h->N, h->n_slots, h->n_rep, h->n_samples, spt,
+                  (int)per_set);
     prof_end(h, QISG_KERNEL_MEASURE, tok);
     h->launches++;
   } else if (n_pairs > 0) {
@@ -1647,16 +1664,16 @@ int measure_t(qisg_handle *h, int force_to_q) {
     const int64_t by = h->n_b * h->n_slots * n_pairs;
     if (by > 65535) return fail(QISG_EINVAL, "too many (block, slot, pair) sets for one launch");
     const int tok = prof_begin(h, QISG_KERNEL_MEASURE);
-    samples_overlap_kernel<Word><<<dim3((unsigned)bx, (unsigned)by), kBlock, 0, h->stream>>>(
-        reinterpret_cast<const Word *>(h->spins), h->d_q, h->N, h->n_slots, h->n_q, h->n_rep,
-        h->n_samples, spt);
+    launch_kernel(h->pdl, samples_overlap_kernel<Word>, dim3((unsigned)bx, (unsigned)by), dim3(kBlock), 0, h->stream,
+                  reinterpret_cast<const Word *>(h->spins), h->d_q, h->N, h->n_slots, h->n_q, h->n_rep,
+                  h->n_samples, spt);
     prof_end(h, QISG_KERNEL_MEASURE, tok);
     h->launches++;
   }
   const int64_t n = h->n_samples * h->n_slots * (h->n_rep + n_pairs);
-  samples_finalize2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
-      h->d_U, h->d_q, h->d_sumA, h->d_sumB, h->d_sumq, h->d_sumq2, h->n_samples, h->n_rep,
-      h->n_slots, h->N, force_to_q);
+  launch_kernel(h->pdl, samples_finalize2_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, h->stream,
+                h->d_U, h->d_q, h->d_sumA, h->d_sumB, h->d_sumq, h->d_sumq2, h->n_samples, h->n_rep,
+                h->n_slots, h->N, force_to_q);
   h->launches++;
   return cuda_check(cudaGetLastError(), "samples measure");
 }

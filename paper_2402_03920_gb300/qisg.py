@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
         "qisg_profile": (I, [P, I]),
         "qisg_set_graphs": (I, [P, I]),
         "qisg_set_persistent": (I, [P, I, I64]),
+        "qisg_set_launch_overlap": (I, [P, I]),
         "qisg_autotune": (I, [P, I, P]),
         "qisg_get_tiles": (I, [P, P, P]),
         "qisg_set_tiles": (I, [P, P, P]),
@@ -131,6 +132,7 @@ def exported_symbols():
             "qisg_thresholds", "qisg_sweep_count", "qisg_layout",
             "qisg_launch_count", "qisg_sync", "qisg_destroy", "qisg_strerror", "qisg_last_error",
             "qisg_philox4x32_10", "qisg_profile", "qisg_profile_read", "qisg_set_graphs", "qisg_set_persistent",
+            "qisg_set_launch_overlap",
             "qisg_autotune", "qisg_get_tiles", "qisg_set_tiles", "qisg_batch_create", "qisg_batch_admit", "qisg_batch_retire",
             "qisg_batch_run", "qisg_batch_set_schedule", "qisg_batch_set_wait_limit", "qisg_batch_autotune",
             "qisg_batch_status",
@@ -400,6 +402,10 @@ class Instance:
 
     def set_graphs(self, enable: bool):
         _check(load().qisg_set_graphs(self._h, 1 if enable else 0))
+
+    def set_launch_overlap(self, enable: bool):
+        """Programmatic dependent launch of the SAMPLES sweep kernels."""
+        _check(load().qisg_set_launch_overlap(self._h, 1 if enable else 0))
 
     def set_persistent(self, enable: bool, wait_ns: int = 0):
         """One cooperative launch per run of sweeps (SAMPLES, 32-bit words)."""

@@ -286,3 +286,27 @@ def test_edge_cases_bit_exact(qisg, W, L, Lt, n_slots, n_rep, n_samples, pt_ever
         assert np.array_equal(sA, st.sumA) and np.array_equal(sB, st.sumB)
         if n_rep > 1:
             assert np.array_equal(sq, st.sumq) and np.array_equal(sq2, st.sumq2)
+
+
+@pytest.mark.parametrize("W", [32, 64])
+def test_launch_overlap_keeps_trajectory(qisg, W):
+    """Programmatic dependent launch on (default) and off, graphs on and off:
+    one trajectory, measurements included, and the oracle's."""
+    kw = dict(layout=qisg.QISG_LAYOUT_SAMPLES, word_bits=W, measure_every=3)
+    a, ladder = make(qisg, 6, 8, 0.2, 0.5, 9, 1.0, 5, 40, 8, **kw)
+    b, _ = make(qisg, 6, 8, 0.2, 0.5, 9, 1.0, 5, 40, 8, **kw)
+    st = oracle_state(ladder, 6, 8, 5, 8, 0, 40)
+    with a, b:
+        b.set_launch_overlap(False)
+        a.set_graphs(False)
+        for n in (2, 13, 30):
+            a.sweep(n)
+            b.sweep(n)
+            oracle.run(st, n, pt_every=1, measure_every=3)
+            assert_same_state(a, st, what=f"overlap on, after {st.t}")
+        a.set_graphs(True)
+        a.sweep(12)
+        b.sweep(12)
+        assert np.array_equal(a.spins(), b.spins()) and np.array_equal(a.permutation(), b.permutation())
+        for x, y in zip(a.measurements(), b.measurements()):
+            assert np.array_equal(np.asarray(x), np.asarray(y))

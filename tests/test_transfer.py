@@ -50,6 +50,12 @@ def test_transfer_power_iteration_and_refusals():
     lam_gpu = float(torch.dot(u, v))
     lam = float(w @ oracle.transfer_matvec(L, k, k, J, 1, w))
     assert lam_gpu == pytest.approx(lam, rel=1e-12)
-    for bad in ((6, 1), (1, 1), (3, 0)):
-        with pytest.raises(qisg.QisgError):
-            qisg.transfer_matvec(v.data_ptr(), u.data_ptr(), bad[0], k, k, J, bad[1])
+    for bad_L, bad_parity in ((6, 1), (1, 1), (3, 0)):
+        Jb = np.ones((bad_L * bad_L, 2), dtype=np.int8)
+        with pytest.raises(qisg.QisgError) as e:
+            qisg.transfer_matvec(v.data_ptr(), u.data_ptr(), bad_L, k, k, Jb, bad_parity)
+        assert e.value.code == -1
+    Jz = J.copy()
+    Jz[0, 0] = 0                       # a coupling that is not +-1
+    with pytest.raises(qisg.QisgError):
+        qisg.transfer_matvec(v.data_ptr(), u.data_ptr(), L, k, k, Jz, 1)
