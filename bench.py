@@ -311,16 +311,19 @@ def kernel_names(layout, wb, tiles):
     return {"red": red, "blue": blue}
 
 
+KERNEL_SOURCES = ("samples.cu", "qisg_internal.cuh")   # where the SAMPLES sweep kernels are defined
+
+
 def source_digest() -> str:
-    """sha256 (16 hex) of the kernel sources: DRAM traffic taken from an ncu
-    capture is used only while the kernels are the ones captured."""
+    """sha256 (16 hex) of the SAMPLES kernels' sources: DRAM traffic taken
+    from an ncu capture is used only while the kernels are the ones
+    captured."""
     import hashlib
     hsh = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2402_03920_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                hsh.update(f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            hsh.update(f.read())
     return hsh.hexdigest()[:16]
 
 
@@ -585,13 +588,18 @@ def serving_entry(qisg, n_requests):
     return out
 
 
+FP64_NOMINAL_GFLOPS = 1250.0   # GB300 dense FP64 (nominal; MEASURED_PEAKS.json holds no FP64 figure)
+
+
 def transfer_entry(torch, qisg, reps=50):
     """The exact-diagonalisation code's transfer-matrix product (Sec. 2.2) at
     the largest lattice one GPU holds, L = 5 (even sector, 2^24 doubles):
-    time per product and its HBM roofline.  Algorithmic bytes: one read of
-    the input and one write of the output (16 B per element); the kernels
-    make three passes over the vector (rounds fused in shared-memory
-    tiles)."""
+    time per product, against the FP64 roofline (on this part FP64 issue, not
+    HBM, bounds it) with the HBM figure beside it.  Algorithmic work: the
+    paper's formulas, 2 multiplies + 1 add per element and round for the
+    L^2 - 1 rounds and the parity factor, 1 multiply for each of the two
+    Boltzmann factors (77 flops per element at L = 5); bytes: one read of the
+    input and one write of the output."""
     L, k = 5, 0.29
     rng = np.random.default_rng(5)
     J = np.where(rng.random((L * L, 2)) < 0.5, 1, -1).astype(np.int8)
@@ -609,13 +617,17 @@ def transfer_entry(torch, qisg, reps=50):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     pk, _ = peaks()
+    flops = float(n) * (3 * (L * L - 1) + 3 + 2)
     alg = 16.0 * n
     hbm = pk.get("hbm_gbs", 6800.0)
+    gflops = flops / (ms * 1e-3) / 1e9
     return {"workload": "EDQSG transfer-matrix product, L=5 even sector (2^24 doubles)", "ms_per_product": ms,
             "unit": "ms", "passes": 3,
-            "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                         "frac": alg / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": alg, "traffic": None,
-                         "note": "three passes move 6 x 8 B per element; the algorithmic 16 B counts input and output"}}
+            "roofline": {"bound": "fp64", "achieved": gflops, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                         "frac": gflops / FP64_NOMINAL_GFLOPS, "flops_per_product": flops, "traffic": None,
+                         "peak_source": "nominal GB300 dense FP64 (no measured FP64 peak on this pool)",
+                         "hbm": {"achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                 "frac": alg / (ms * 1e-3) / 1e9 / hbm, "algorithmic_bytes": alg}}}
 
 
 def tau_entry(torch, qisg):
