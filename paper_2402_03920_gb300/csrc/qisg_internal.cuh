@@ -27,13 +27,15 @@ constexpr int kDaemonLutBits = 12;
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
 
-// Philox4x32-10 (Salmon et al., SC'11), the generator of Sec. 2.1.1.
+// Philox4x32-10 (Salmon et al., SC'11), the generator of Sec. 2.1.1.  Each
+// round's two 32 x 32 -> 64-bit products are taken as one wide multiply
+// each (high and low halves from one instruction).
 __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
-    const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
-    const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    const unsigned long long p0 = (unsigned long long)kPhiloxM0 * c.x;
+    const unsigned long long p1 = (unsigned long long)kPhiloxM1 * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y, (uint32_t)p0);
     k.x += kPhiloxW0;
     k.y += kPhiloxW1;
   }
