@@ -304,7 +304,7 @@ def kernel_names(layout, wb, tiles):
     (t_red, _t_blue), (_v_red, v_blue) = tiles
     if wb == 32:
         red = {1: "samples_red_fused_kernel", 2: "samples_red_fusedq_kernel<2>"}.get(t_red, "samples_red_fusedq_kernel<4>")
-        blue = "samples_sweep4_kernel" if v_blue == 0 else "samples_half_sweep_kernel"
+        blue = {0: "samples_sweep4_kernel", 2: "samples_sweep4_kernel<min 4 blocks>"}.get(v_blue, "samples_half_sweep_kernel")
     else:
         red = "samples_red_fusedq_kernel<u64, 1>" if t_red == 1 else "samples_red_fusedq_kernel<u64, 2>"
         blue = "samples_half_sweep_kernel"

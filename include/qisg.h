@@ -413,23 +413,29 @@ int qisg_set_persistent(qisg_handle *h, int enable, int64_t wait_ns);
 
 /* Choose the SAMPLES sweep schedule by timing sweeps_per_candidate real
  * sweeps per candidate on the handle's own state; the red and blue passes are
- * timed and tuned separately.  Candidates: tiles 1, 2, ..., 64 and, for
- * 32-bit words, both kernel variants of each.  The tile is, for 64-bit words,
- * the site groups of 4 each thread walks along tau; for 32-bit words it
- * selects the red pass's threads per site (1: four, 2: two, else one) and the
- * blue pass's sites per thread (variant 0, a thread per replica quad) or site
- * groups of 4 per thread (variant 1, a thread per replica).  The simulation
- * advances by C * (1 + sweeps_per_candidate) sweeps meanwhile, C = 14
- * candidates for 32-bit words and 7 for 64-bit words (results never depend on
- * the schedule, so the trajectory is the one an untuned run would follow).
+ * timed and tuned separately.  Candidates: tiles 1, 2, 4, ..., 64 and the
+ * default (0) and, for 32-bit words, the three blue kernel variants of each.
+ * The tile is, for 64-bit words, the site groups of 4 each thread walks along
+ * tau; for 32-bit words it selects the red pass's threads per site (1: four,
+ * 2: two, else one) and the blue pass's sites per thread (variants 0 and 2,
+ * a thread per replica quad walking at most `tile` sites, the L_tau / 2 sites
+ * of a column split into ceil(L_tau / 2 / tile) segments whose lengths differ
+ * by at most one; 2 with its registers bounded to four blocks per SM and no
+ * prefetch of the next site) or site groups of 4 per thread (variant 1, a
+ * thread per replica).  The default of variants 0 and 2 picks the segment
+ * count that fills whole waves of resident blocks.  The simulation advances
+ * by C * (1 + sweeps_per_candidate) sweeps meanwhile, C = 24 candidates for
+ * 32-bit words and 8 for 64-bit words (results never depend on the schedule,
+ * so the trajectory is the one an untuned run would follow); with the
+ * persistent form on, C = 21 (3 red x 7 blue tiles, the default among them).
  * chosen: the blue pass's tile (0 for LANES, which has nothing to tune).
  * Synchronises. */
 int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen);
 
 /* Read or pin the SAMPLES sweep schedule: tile[c] and variant[c] of the red
  * (c = 0) and blue (c = 1) pass as qisg_autotune chooses them (tile 0 = the
- * default; variant 0 or 1).  Results never depend on the schedule.  EINVAL:
- * tile outside 0..64 or not a power of two, variant not 0 or 1. */
+ * default, else 1..64 as there; variant 0, 1 or 2).  Results never depend on
+ * the schedule.  EINVAL: tile outside 0..64, variant not 0..2. */
 int qisg_get_tiles(qisg_handle *h, int tile[2], int variant[2]);
 int qisg_set_tiles(qisg_handle *h, const int tile[2], const int variant[2]);
 

@@ -682,7 +682,7 @@ int qisg_set_persistent(qisg_handle *h, int enable, int64_t wait_ns) {
 // pair -- the red pass's threads per site and the number of sites each blue
 // thread walks along tau -- on the handle's own state; keep the fastest.
 static int autotune_persistent(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
-  const int red_tiles[3] = {1, 2, 4}, blue_tiles[6] = {1, 2, 4, 8, 16, 32};
+  const int red_tiles[3] = {1, 2, 4}, blue_tiles[7] = {0, 1, 2, 4, 8, 16, 32};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = cuda_check(cudaEventCreate(&e0), "event");
   if (!rc) rc = cuda_check(cudaEventCreate(&e1), "event");
@@ -699,7 +699,7 @@ static int autotune_persistent(qisg_handle *h, int sweeps_per_candidate, int *ch
     return r;
   };
   for (int i = 0; i < 3 && !rc; ++i)
-    for (int j = 0; j < 6 && !rc; ++j) {
+    for (int j = 0; j < 7 && !rc; ++j) {
       h->sweep_tile[0] = red_tiles[i];
       h->sweep_tile[1] = blue_tiles[j];
       h->sweep_variant[0] = h->sweep_variant[1] = 0;
@@ -740,9 +740,11 @@ int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
     return QISG_OK;
   }
   if (h->persistent) return autotune_persistent(h, sweeps_per_candidate, chosen);
-  // candidates: tiles 1, 2, ..., 64, and for W = 32 each with both kernel
-  // variants; the red and blue passes are timed apart and tuned apart
-  const int n_tiles = 7, n_cand = h->W == 32 ? 2 * n_tiles : n_tiles;
+  // candidates: tiles 1, 2, ..., 64 and the default (0), and for W = 32 each
+  // with the three blue kernel variants; the red and blue passes are timed
+  // apart and tuned apart
+  static const int kTiles[8] = {1, 2, 4, 8, 16, 32, 64, 0};
+  const int n_tiles = 8, n_cand = h->W == 32 ? 3 * n_tiles : n_tiles;
   float best_ms[2] = {0.f, 0.f};
   int best[2] = {0, 0};
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -751,7 +753,7 @@ int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
   const bool graphs = h->use_graphs;
   h->use_graphs = false;
   for (int c = 0; c < n_cand && !rc; ++c) {
-    const int tile = 1 << (c % n_tiles), variant = c / n_tiles;
+    const int tile = kTiles[c % n_tiles], variant = c / n_tiles;
     h->sweep_tile[0] = h->sweep_tile[1] = tile;
     h->sweep_variant[0] = h->sweep_variant[1] = variant;
     rc = one_sweep(h);   // warm the candidate
@@ -776,7 +778,7 @@ int qisg_autotune(qisg_handle *h, int sweeps_per_candidate, int *chosen) {
   h->use_graphs = graphs;
   if (rc) return rc;
   for (int col = 0; col < 2; ++col) {
-    h->sweep_tile[col] = 1 << ((best[col] - 1) % n_tiles);
+    h->sweep_tile[col] = kTiles[(best[col] - 1) % n_tiles];
     h->sweep_variant[col] = (best[col] - 1) / n_tiles;
   }
   drop_cycle(h);
@@ -796,8 +798,8 @@ int qisg_get_tiles(qisg_handle *h, int tile[2], int variant[2]) {
 int qisg_set_tiles(qisg_handle *h, const int tile[2], const int variant[2]) {
   if (!h || !tile || !variant) return fail(QISG_EINVAL, "NULL argument");
   for (int c = 0; c < 2; ++c)
-    if (tile[c] < 0 || tile[c] > 64 || (tile[c] & (tile[c] - 1)) || (variant[c] != 0 && variant[c] != 1))
-      return fail(QISG_EINVAL, "tile must be 0 or a power of two up to 64, variant 0 or 1");
+    if (tile[c] < 0 || tile[c] > 64 || variant[c] < 0 || variant[c] > 2)
+      return fail(QISG_EINVAL, "tile must be 0 .. 64, variant 0, 1 or 2");
   int rc = sync_handle(h);
   if (rc) return rc;
   for (int c = 0; c < 2; ++c) {

@@ -27,15 +27,16 @@ constexpr int kDaemonLutBits = 12;
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
 
-// Philox4x32-10 (Salmon et al., SC'11), the generator of Sec. 2.1.1.  Each
-// round's two 32 x 32 -> 64-bit products are taken as one wide multiply
-// each (high and low halves from one instruction).
+// Philox4x32-10 (Salmon et al., SC'11), the generator of Sec. 2.1.1.  The
+// low and high halves of each product are taken apart: measured faster here
+// than one wide multiply per product (the daemon kernels, whose Philox calls
+// sit between table lookups, use the wide form, philox_wide).
 __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
 #pragma unroll
   for (int i = 0; i < 10; ++i) {
-    const unsigned long long p0 = (unsigned long long)kPhiloxM0 * c.x;
-    const unsigned long long p1 = (unsigned long long)kPhiloxM1 * c.z;
-    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y, (uint32_t)p0);
+    const uint32_t lo0 = kPhiloxM0 * c.x, hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo1 = kPhiloxM1 * c.z, hi1 = __umulhi(kPhiloxM1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
     k.x += kPhiloxW0;
     k.y += kPhiloxW1;
   }
@@ -511,13 +512,16 @@ struct qisg_handle {
   int n_sm = 0;
   // SAMPLES sweep schedule per colour (red, blue); none of it changes results.
   // tile: W = 64 and the W = 32 column walk: site groups of 4 per thread
-  // quad; W = 32 replica-quad kernel: sites per thread along tau; W = 32
-  // red pass: threads per site (1: four, 2: two, else one); 0 = default.
-  // variant (W = 32 blue pass): 0 the replica-quad kernel, 1 the column walk.
+  // quad; W = 32 replica-quad kernel: at most this many sites per thread
+  // along tau; W = 32 red pass: threads per site (1: four, 2: two, else
+  // one); 0 = default.
+  // variant (W = 32 blue pass): 0 the replica-quad kernel, 1 the column walk,
+  // 2 the replica-quad kernel bounded to four blocks per SM (no prefetch).
   // The default grid aims at sweep_min_blocks_per_sm blocks of 256 threads
   // per SM.
   int sweep_tile[2] = {0, 0};
   int sweep_variant[2] = {0, 0};
+  int blue_occ[2][6] = {};   // resident blocks per SM of the W = 32 blue kernel (variant 0 | 2, counter width)
   int sweep_min_blocks_per_sm = 4;
 
   // host tables (FP64, built once)

@@ -37,11 +37,12 @@ struct SamplesArgs {
   uint2 key;
   int64_t N, half_N;
   int L, Lt, plane, half_plane, n_slots, n_rep, n_q, W;
-  int seg_sites;         // G: sites of one colour each quad walks along tau
-  int n_seg;             // (L_tau / 2) / G segments per column
+  int seg_sites;         // G: sites of one colour each quad walks along tau (the most of any thread)
+  int n_seg;             // segments per column
+  int seg_base, seg_rem; // W = 32 replica-quad kernel: segment g of a column holds seg_base + (g < seg_rem)
+                         // sites (n_seg segments covering the L_tau / 2 sites of the colour)
   int blocks_per_set;    // blocks per (b, s, q) word set
-  int t_has_zero;        // some threshold of the table is 0 (always reject)
-  uint32_t one, all_ones;   // 1 and 0xFFFFFFFF as runtime values (flag_imad)
+  uint32_t one;          // 1 as a runtime value (accept_flag)
   unsigned long long *t_copy;   // blue pass, fused mode: copy t here for the PT pass
   int tau_ap;                   // antiperiodic along tau: the wrap tau bond flips sign
   // division by the invariants of the index decomposition (32-bit indices)
@@ -53,52 +54,37 @@ struct SamplesArgs {
   int64_t n_zero_acc;
 };
 
-// Reject flag of a class: reject iff T is not the always-accept sentinel
-// and R >= T.  When no threshold of the table is 0 this is one compare,
-// R > Tm1, with Tm1 = T - 1 for finite thresholds and Tm1 = 0xFFFFFFFF (never
-// exceeded) for the sentinel; otherwise both conditions are tested.
-template <typename Word>
-__device__ __forceinline__ Word rho_gt(uint32_t R, uint32_t Tm1) {
-  return ones_if<Word>(R > Tm1);
-}
-template <typename Word>
-__device__ __forceinline__ Word rho_ge(uint32_t R, uint32_t T) {
-  return ones_if<Word>(T != 0xFFFFFFFFu && R >= T);
-}
-
-// Reject thresholds per slot for the classes (u_t = 0: u_s = 0..4),
-// (u_t = 1: u_s = 0, 1), (u_t = 2: u_s = 0, 1), in the form reject_mask
-// reads them.
+// Accept constants per slot for the classes (u_t = 0: u_s = 0..4),
+// (u_t = 1: u_s = 0, 1), (u_t = 2: u_s = 0, 1); the classes u_t >= 1,
+// u_s >= 2 always accept.  A class with table entry T accepts a draw R iff
+// R < T', T' = T for a finite entry (T = 0: never) and T' = 2^32 for the
+// always-accept sentinel.  The slot holds C = 2^64 - T' (mod 2^64): R + C
+// stays below 2^64 iff R < T', and then its high word is 0xFFFFFFFF (R + C
+// >= 2^64 - 2^32), else 0.  So one 64-bit multiply-add, R * 1 + C, gives the
+// class's accept mask in its high word, on the integer multiply-add pipe
+// (leaving the logic pipe to the bit-sliced arithmetic).
 struct SlotThresholds {
-  uint32_t v[kMaxSlotsPT][9];
+  unsigned long long v[kMaxSlotsPT][9];
 };
 
-// Reject flag on the integer multiply-add pipe (leaving the logic pipe to
-// the bit-sliced arithmetic): with K = ~(T - 1) (K = 0 for the sentinel),
-// R + K >= 2^32 iff R > T - 1, so the high word of the 64-bit R * 1 + K is
-// the flag and its product with 0xFFFFFFFF the mask.  one and all_ones are
-// the runtime values 1 and 0xFFFFFFFF (kernel parameters, so the compiler
-// keeps the multiplies).
-__device__ __forceinline__ uint32_t flag_imad(uint32_t R, uint32_t K, uint32_t one, uint32_t all_ones) {
+// one is the runtime value 1 (a kernel parameter, so the compiler keeps the
+// multiply-add rather than splitting it into two additions)
+__device__ __forceinline__ uint32_t accept_flag(uint32_t R, unsigned long long C, uint32_t one) {
   unsigned long long v;
-  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(v) : "r"(R), "r"(one), "l"((unsigned long long)K));
-  uint32_t m;
-  asm("mul.lo.u32 %0, %1, %2;" : "=r"(m) : "r"((uint32_t)(v >> 32)), "r"(all_ones));
-  return m;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(v) : "r"(R), "r"(one), "l"(C));
+  return (uint32_t)(v >> 32);
 }
 
-// HAS_ZERO: th holds T and the flags are T != sentinel && R >= T; else th
-// holds K = ~(T - 1) (0 for the sentinel) for flag_imad.
-template <bool HAS_ZERO>
-__device__ __forceinline__ uint32_t reject_mask(uint32_t R, const uint32_t *th, uint32_t us0, uint32_t us1,
-                                                uint32_t us2, uint32_t ut0, uint32_t ut1, uint32_t one,
-                                                uint32_t all_ones) {
-#define QISG_F(c) (HAS_ZERO ? rho_ge<uint32_t>(R, th[c]) : flag_imad(R, th[c], one, all_ones))
-  const uint32_t row0 = mux(us2, QISG_F(4), mux(us1, mux(us0, QISG_F(3), QISG_F(2)), mux(us0, QISG_F(1), QISG_F(0))));
-  const uint32_t low = ~(us1 | us2);
-  const uint32_t row1 = low & mux(us0, QISG_F(6), QISG_F(5));
-  const uint32_t row2 = low & mux(us0, QISG_F(8), QISG_F(7));
-#undef QISG_F
+// Accept mask of one 32-bit word: a mux tree over the class planes (u_s in
+// us2 us1 us0, u_t in ut1 ut0) of the per-class accept masks.
+__device__ __forceinline__ uint32_t accept_mask(uint32_t R, const unsigned long long *C, uint32_t us0, uint32_t us1,
+                                                uint32_t us2, uint32_t ut0, uint32_t ut1, uint32_t one) {
+#define QISG_A(c) accept_flag(R, C[c], one)
+  const uint32_t row0 = mux(us2, QISG_A(4), mux(us1, mux(us0, QISG_A(3), QISG_A(2)), mux(us0, QISG_A(1), QISG_A(0))));
+  const uint32_t high = us1 | us2;
+  const uint32_t row1 = high | mux(us0, QISG_A(6), QISG_A(5));
+  const uint32_t row2 = high | mux(us0, QISG_A(8), QISG_A(7));
+#undef QISG_A
   return mux(ut1, row2, mux(ut0, row1, row0));
 }
 
@@ -143,23 +129,24 @@ __device__ __forceinline__ void quad_sum_counters(const VCount<Word, K> &c, Word
   __syncthreads();   // buf is reused by the caller
 }
 
-// Reject mask of one word for class planes (us, ut): the flags are 32-bit
-// masks (flag_imad), widened for 64-bit words.
-template <typename Word, bool HAS_ZERO>
-__device__ __forceinline__ Word reject_word(uint32_t R, const uint32_t *th, Word us0, Word us1, Word us2, Word ut0,
-                                            Word ut1, uint32_t one, uint32_t all_ones) {
-  auto f = [&](int c) -> Word {
-    const uint32_t m = HAS_ZERO ? (uint32_t)rho_ge<uint32_t>(R, th[c]) : flag_imad(R, th[c], one, all_ones);
-    if constexpr (sizeof(Word) == 8)
+// Accept mask of one word for class planes (us, ut): the class masks are 32
+// bits wide (accept_flag), doubled for 64-bit words.
+template <typename Word>
+__device__ __forceinline__ Word accept_word(uint32_t R, const unsigned long long *C, Word us0, Word us1, Word us2,
+                                            Word ut0, Word ut1, uint32_t one) {
+  if constexpr (sizeof(Word) == 4) {
+    return accept_mask(R, C, us0, us1, us2, ut0, ut1, one);
+  } else {
+    auto f = [&](int c) -> Word {
+      const uint32_t m = accept_flag(R, C[c], one);
       return ((Word)m << 32) | (Word)m;
-    else
-      return (Word)m;
-  };
-  const Word row0 = mux(us2, f(4), mux(us1, mux(us0, f(3), f(2)), mux(us0, f(1), f(0))));
-  const Word low = ~(us1 | us2);
-  const Word row1 = low & mux(us0, f(6), f(5));
-  const Word row2 = low & mux(us0, f(8), f(7));
-  return mux(ut1, row2, mux(ut0, row1, row0));
+    };
+    const Word row0 = mux(us2, f(4), mux(us1, mux(us0, f(3), f(2)), mux(us0, f(1), f(0))));
+    const Word high = us1 | us2;
+    const Word row1 = high | mux(us0, f(6), f(5));
+    const Word row2 = high | mux(us0, f(8), f(7));
+    return mux(ut1, row2, mux(ut0, row1, row0));
+  }
 }
 
 // One half sweep, column walk.  Block: one (b, s, q) word set; quad thread j
@@ -200,8 +187,7 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_acc; i += stride)
       p.zero_acc[i] = 0;
   }
-  const uint32_t *T = th.v[s];
-  const bool has_zero = p.t_has_zero != 0;
+  const unsigned long long *C = th.v[s];
 
   const int L = p.L, plane = p.plane, G = p.seg_sites;
   const uint32_t Lt = (uint32_t)p.Lt;
@@ -300,16 +286,8 @@ __global__ void __launch_bounds__(kBlock) samples_half_sweep_kernel(SamplesArgs<
         const Word us2 = c1 & c2;
         const Word ut0 = t1 ^ t2;
         const Word ut1 = t1 & t2;
-        // reject mask: mux tree over (u_t, u_s) of the per-class flags;
-        // classes with u_s >= 2 and u_t >= 1 always accept
-        Word rej;
-        if (count_only)
-          rej = ~Word(0);
-        else if (!has_zero)
-          rej = reject_word<Word, false>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
-        else
-          rej = reject_word<Word, true>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
-        const Word flip = ~rej;
+        // accept mask: mux tree over (u_t, u_s) of the per-class masks
+        const Word flip = count_only ? Word(0) : accept_word<Word>(R, C, us0, us1, us2, ut0, ut1, p.one);
         if (!count_only) base[(size_t)site * 4] = sc ^ flip;
         if (BLUE) {
           // unsatisfied counts after the flip: u -> 4 - u (spatial), 2 - u (tau)
@@ -386,8 +364,8 @@ struct FusedRedArgsT {
   int64_t n_zero_U;
   uint2 key;
   int64_t N;
-  int L, Lt, plane, n_slots, n_q, n_rep, blocks_per_set, t_has_zero;
-  uint32_t one, all_ones;
+  int L, Lt, plane, n_slots, n_q, n_rep, blocks_per_set;
+  uint32_t one;
   int tau_ap;
   FastDiv fd_bps, fd_nq, fd_plane, fd_L;
 };
@@ -447,7 +425,6 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedR
   uint32_t Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
   const unsigned long long t = *p.d_t;
   const uint32_t ctr_w = (DOM_SWEEP << 28) | ((b * 32u) >> 6);
-  const bool has_zero = p.t_has_zero != 0;
   uint32_t cw[7], n1[7];   // carried words at the current slot; words of the next slot
 #pragma unroll
   for (int k = 0; k < 7; ++k) zo[k] = 4 * z[k] + (uint32_t)j;
@@ -500,7 +477,7 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedR
           for (int k = 0; k < 7; ++k) fw[k] = cw[k];
         }
         const uint32_t R = rw[((i * 8 + ql) << 2) + j];
-        const uint32_t *T = th.v[sl];
+        const unsigned long long *C = th.v[sl];
         const uint32_t sc = fw[0];
         const uint32_t b1 = sc ^ fw[3] ^ Jxp;
         const uint32_t b2 = sc ^ fw[4] ^ Jxm;
@@ -516,10 +493,9 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedR
         const uint32_t us2 = c1 & c2;
         const uint32_t ut0 = t1 ^ t2;
         const uint32_t ut1 = t1 & t2;
-        const uint32_t rej = has_zero ? reject_mask<true>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones)
-                                      : reject_mask<false>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
+        const uint32_t acc = accept_mask(R, C, us0, us1, us2, ut0, ut1, p.one);
         uint32_t *pd = db + (int64_t)sl * SS;
-        pd[zo[0]] = sc ^ ~rej;
+        pd[zo[0]] = sc ^ acc;
         pd[zo[1]] = fw[1];
       }
     }
@@ -621,7 +597,6 @@ __device__ __forceinline__ void red_fusedq_body(const FusedRedArgsT<Word> &p, co
   Word Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
   const uint32_t ctr_w = (DOM_SWEEP << 28) | ((b * (uint32_t)W) >> 6);
   const uint32_t site = i2 + off;
-  const bool has_zero = p.t_has_zero != 0;
   const int lane = (int)(threadIdx.x & 31), lane0 = lane & ~(TPS - 1);
   Word cw[7][RP], n1[7][RP];
   if (live) {
@@ -687,7 +662,7 @@ __device__ __forceinline__ void red_fusedq_body(const FusedRedArgsT<Word> &p, co
 #pragma unroll
         for (int jj = 0; jj < RP; ++jj) fw[k][jj] = cw[k][jj];
     }
-    const uint32_t *T = th.v[sl];
+    const unsigned long long *C = th.v[sl];
     Word out[RP];
 #pragma unroll
     for (int jj = 0; jj < RP; ++jj) {
@@ -706,9 +681,7 @@ __device__ __forceinline__ void red_fusedq_body(const FusedRedArgsT<Word> &p, co
       const Word us2 = c1 & c2;
       const Word ut0 = t1 ^ t2;
       const Word ut1 = t1 & t2;
-      const Word rej = has_zero ? reject_word<Word, true>(Rj[jj], T, us0, us1, us2, ut0, ut1, p.one, p.all_ones)
-                                : reject_word<Word, false>(Rj[jj], T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
-      out[jj] = sc ^ ~rej;
+      out[jj] = sc ^ accept_word<Word>(Rj[jj], C, us0, us1, us2, ut0, ut1, p.one);
     }
     Word *pd = db + (int64_t)sl * SS;
     st_rp<Word, RP>(pd + zo[0], out);
@@ -785,15 +758,13 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
   const int q = (int)(set - bs * (uint32_t)p.n_q);
   const uint32_t b = p.fd_ns.div(bs);
   const int s = (int)(bs - b * (uint32_t)p.n_slots);
-  const uint32_t *T = th.v[s];
-  const bool has_zero = p.t_has_zero != 0;
-  const int L = p.L, plane = p.plane, G = p.seg_sites;
+  const unsigned long long *C = th.v[s];
+  const int L = p.L, plane = p.plane;
   const uint32_t Lt = (uint32_t)p.Lt, P = (uint32_t)plane;
   const uint32_t gq = chunk * (uint32_t)kBlock4 + threadIdx.x;
   const bool live = gq < P * (uint32_t)p.n_seg;
   const uint32_t segu = p.fd_plane.div(gq);
   const int i2 = (int)(gq - segu * P);
-  const int seg = (int)segu;
   const int y = (int)p.fd_L.div((uint32_t)i2), x = i2 - y * L;
   const int ixp = (x + 1 == L ? 0 : x + 1) + L * y, ixm = (x == 0 ? L - 1 : x - 1) + L * y;
   const int iyp = x + L * (y + 1 == L ? 0 : y + 1), iym = x + L * (y == 0 ? L - 1 : y - 1);
@@ -802,7 +773,9 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
   uint4 *wc = reinterpret_cast<uint4 *>(p.spins) + ((b * p.n_slots + s) * p.n_q + q) * p.N + i2;
   const uint32_t *Jb = p.J + b * (int64_t)plane * 2;
   uint32_t Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
-  const uint32_t tau0 = 2u * (uint32_t)G * (uint32_t)seg + (uint32_t)((colour + x + y) & 1);
+  const uint32_t tau0 = 2u * (segu * (uint32_t)p.seg_base + min(segu, (uint32_t)p.seg_rem)) +
+                        (uint32_t)((colour + x + y) & 1);
+  const int G = p.seg_base + (segu < (uint32_t)p.seg_rem ? 1 : 0);
   const uint32_t ctr_z = (uint32_t)s | ((uint32_t)q << 16);
   const uint32_t ctr_w = (DOM_SWEEP << 28) | (uint32_t)((b * 32) >> 6);
 
@@ -864,13 +837,7 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
         const uint32_t ut0 = t1 ^ t2;
         const uint32_t ut1 = t1 & t2;
         const uint32_t R = q4(R4, j);
-        uint32_t flip;
-        if (count_only)
-          flip = 0;
-        else if (!has_zero)
-          flip = ~reject_mask<false>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
-        else
-          flip = ~reject_mask<true>(R, T, us0, us1, us2, ut0, ut1, p.one, p.all_ones);
+        const uint32_t flip = count_only ? 0u : accept_mask(R, C, us0, us1, us2, ut0, ut1, p.one);
         f[j] = flip;
         if (BLUE) {
           // unsatisfied counts after the flip: u -> 4 - u (spatial), 2 - u (tau)
@@ -911,8 +878,8 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
 }
 
 
-template <bool BLUE, int G2, bool PF>
-__global__ void __launch_bounds__(kBlock4) samples_sweep4_kernel(SamplesArgs<uint32_t> p,
+template <bool BLUE, int G2, bool PF, int MINB = 0>
+__global__ void __launch_bounds__(kBlock4, MINB) samples_sweep4_kernel(SamplesArgs<uint32_t> p,
                                                                   const __grid_constant__ SlotThresholds th,
                                                                   int colour, int count_only) {
   pdl_begin();
@@ -1337,11 +1304,7 @@ SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
   p.n_zero_U = h->n_a_pad * h->n_rep * h->n_slots * 2;
   p.zero_acc = reinterpret_cast<Word *>(h->d_acc);
   p.n_zero_acc = h->n_b * h->n_rep * h->n_slots;
-  p.t_has_zero = 0;
-  for (uint32_t v : h->T)
-    if (v == 0) p.t_has_zero = 1;
   p.one = 1u;
-  p.all_ones = 0xFFFFFFFFu;
   // sites per quad along tau: as many as possible (cheaper energy flushes)
   // while the grid keeps about sweep_min_blocks_per_sm blocks per SM; G must
   // divide L_tau / 2
@@ -1361,6 +1324,8 @@ SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
   if (half_col % G) G = half_col;   // one segment per column
   p.seg_sites = G;
   p.n_seg = half_col / G;
+  p.seg_base = G;
+  p.seg_rem = 0;
   p.blocks_per_set = (int)(((int64_t)p.plane * p.n_seg + kQuads - 1) / kQuads);
   p.fd_bps = FastDiv((uint32_t)p.blocks_per_set);
   p.fd_nq = FastDiv((uint32_t)p.n_q);
@@ -1397,40 +1362,109 @@ void launch_sweep_g(bool pdl, const SamplesArgs<Word> &p, const SlotThresholds &
   }
 }
 
-// The 9 rejecting classes' thresholds of every slot in the form reject_mask
-// and reject_word read them.
-void fill_thresholds(const qisg_handle *h, int has_zero, SlotThresholds &th) {
+// The 9 classes' accept constants C = 2^64 - T' of every slot, in the form
+// accept_flag reads them (T' = T, or 2^32 for the always-accept sentinel).
+void fill_thresholds(const qisg_handle *h, SlotThresholds &th) {
   std::memset(&th, 0, sizeof(th));
   static const int cls[9] = {0, 3, 6, 9, 12, 1, 4, 2, 5};   // us * 3 + ut of the 9 classes
   for (int sl = 0; sl < h->n_slots; ++sl)
     for (int c = 0; c < 9; ++c) {
       const uint32_t T = h->T[(size_t)sl * 15 + cls[c]];
-      th.v[sl][c] = has_zero ? T : (T == 0xFFFFFFFFu ? 0u : ~(T - 1u));
+      const unsigned long long Tp = T == 0xFFFFFFFFu ? (1ull << 32) : (unsigned long long)T;
+      th.v[sl][c] = 0ull - Tp;
     }
 }
 
-// W = 32 kernel: one thread per column segment of G sites (G = the tile,
-// or by default as many as keep about half the old kernel's thread count).
-SamplesArgs<uint32_t> make_args4(qisg_handle *h, int colour, SlotThresholds &th) {
+// Blocks of the W = 32 blue kernel (variant 0 or 2, counter planes for walks
+// of up to 4 << g2 sites) resident on one SM, cached in the handle.
+int blue_blocks_per_sm(qisg_handle *h, int g2, int variant) {
+  const int v = variant == 2 ? 1 : 0;
+  g2 = std::min(std::max(g2, 0), 5);
+  int &c = h->blue_occ[v][g2];
+  if (c > 0) return c;
+  const void *fn = nullptr;
+#define QISG_OCC(n)                                                                                   \
+  case n:                                                                                             \
+    fn = v ? (const void *)samples_sweep4_kernel<true, n, false, 4> : (const void *)samples_sweep4_kernel<true, n, true>; \
+    break;
+  switch (g2) { QISG_OCC(0) QISG_OCC(1) QISG_OCC(2) QISG_OCC(3) QISG_OCC(4) default: QISG_OCC(5) }
+#undef QISG_OCC
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock4, 0) != cudaSuccess || per_sm < 1) {
+    (void)cudaGetLastError();
+    per_sm = 1;
+  }
+  return c = per_sm;
+}
+
+// Segments per column of the blue pass when no tile is pinned: the count
+// that minimises (waves of blocks over the resident ones) x (work of one
+// thread), a thread's work being its walk of up to G sites (about 490
+// instructions a site for its four replica words) plus its part of the
+// block's counter tree (about 32 instructions per counter plane level),
+// with walks of at most max_walk sites.  resident(g2) gives the resident blocks
+// for counter planes of walks up to 4 << g2 sites.
+template <typename Resident>
+int wave_fill_segments(int64_t sets, int plane, int half_col, int max_walk, Resident resident) {
+  int best = half_col;
+  double best_cost = -1.0;
+  for (int ns = std::max(1, (half_col + max_walk - 1) / max_walk); ns <= half_col; ++ns) {
+    const int gmax = (half_col + ns - 1) / ns;
+    int g2 = 0;
+    while ((4 << g2) < gmax) ++g2;
+    const int64_t R = std::max<int64_t>(1, resident(g2));
+    const int64_t blocks = sets * (((int64_t)plane * ns + kBlock4 - 1) / kBlock4);
+    const int64_t waves = (blocks + R - 1) / R;
+    const double cost = (double)waves * (490.0 * gmax + 32.0 * (2 * g2 + 23));
+    if (best_cost < 0.0 || cost < best_cost) {
+      best_cost = cost;
+      best = ns;
+    }
+  }
+  return best;
+}
+
+// W = 32 kernel: one thread per column segment.  A pinned tile G gives
+// ceil((L_tau / 2) / G) segments of at most G sites; the default gives the
+// blue pass the wave-filling count above (resident_blocks: the launch's
+// resident blocks, 0 = those of the blue kernel itself; walks of at most
+// max_walk sites) and the red pass as many sites per thread as keep about
+// half the old kernel's thread count.
+SamplesArgs<uint32_t> make_args4(qisg_handle *h, int colour, SlotThresholds &th, int64_t resident_blocks = 0,
+                                 int max_walk = 64) {
   SamplesArgs<uint32_t> p = make_args<uint32_t>(h, colour);
   const int half_col = h->Lt / 2;
   const int64_t sets = h->n_b * h->n_slots * h->n_q;
-  const int64_t want_threads = (int64_t)h->sweep_min_blocks_per_sm * std::max(1, h->n_sm) * kBlock / 2;
-  const int tile = h->sweep_tile[colour];
-  int G = tile > 0 ? tile : 64;
-  if (tile <= 0)
+  const int tile = std::min(h->sweep_tile[colour], half_col);
+  int n_seg;
+  if (tile > 0) {
+    n_seg = (half_col + tile - 1) / tile;
+  } else if (colour == 1) {
+    const int variant = h->sweep_variant[1];
+    n_seg = wave_fill_segments(sets, p.plane, half_col, max_walk, [&](int g2) -> int64_t {
+      return resident_blocks > 0 ? resident_blocks : (int64_t)blue_blocks_per_sm(h, g2, variant) * std::max(1, h->n_sm);
+    });
+  } else {
+    const int64_t want_threads = (int64_t)h->sweep_min_blocks_per_sm * std::max(1, h->n_sm) * kBlock / 2;
+    int G = 64;
     while (G > 1 && sets * p.plane * (int64_t)(half_col / std::min(G, half_col)) < want_threads) G >>= 1;
-  if (G > half_col) G = half_col;
-  while (G > 1 && half_col % G) --G;
-  p.seg_sites = G;
-  p.n_seg = half_col / G;
+    if (G > half_col) G = half_col;
+    while (G > 1 && half_col % G) --G;
+    n_seg = half_col / G;
+  }
+  p.n_seg = n_seg;
+  p.seg_base = half_col / n_seg;
+  p.seg_rem = half_col % n_seg;
+  p.seg_sites = p.seg_base + (p.seg_rem > 0 ? 1 : 0);
   p.blocks_per_set = (int)(((int64_t)p.plane * p.n_seg + kBlock4 - 1) / kBlock4);
   p.fd_bps = FastDiv((uint32_t)p.blocks_per_set);
-  fill_thresholds(h, p.t_has_zero, th);
+  fill_thresholds(h, th);
   return p;
 }
 
-template <bool BLUE, bool PF>
+// MINB > 0: the kernel's registers are bounded so that MINB blocks fit on an
+// SM (variant 2 of the blue pass: more resident warps, no prefetch).
+template <bool BLUE, bool PF, int MINB = 0>
 void launch_sweep4(bool pdl, const SamplesArgs<uint32_t> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
                    int colour, int count_only) {
   if constexpr (!BLUE) {   // the red pass keeps no counters
@@ -1440,15 +1474,15 @@ void launch_sweep4(bool pdl, const SamplesArgs<uint32_t> &p, const SlotThreshold
     int g2 = 0;
     while ((4 << g2) < p.seg_sites) ++g2;
     switch (g2) {
-#define QISG_CASE(n) \
-  case n:                                                                                                      \
-    launch_kernel(pdl, samples_sweep4_kernel<true, n, PF>, dim3(blocks), dim3(kBlock4), 0, st, p, th, colour,    \
-                  count_only);                                                                                 \
+#define QISG_CASE(n)                                                                                         \
+  case n:                                                                                                    \
+    launch_kernel(pdl, samples_sweep4_kernel<true, n, PF, MINB>, dim3(blocks), dim3(kBlock4), 0, st, p, th,  \
+                  colour, count_only);                                                                       \
     break;
       QISG_CASE(0) QISG_CASE(1) QISG_CASE(2) QISG_CASE(3) QISG_CASE(4)
       default:
-        launch_kernel(pdl, samples_sweep4_kernel<true, 5, PF>, dim3(blocks), dim3(kBlock4), 0, st, p, th, colour,
-                      count_only);
+        launch_kernel(pdl, samples_sweep4_kernel<true, 5, PF, MINB>, dim3(blocks), dim3(kBlock4), 0, st, p, th,
+                      colour, count_only);
         break;
 #undef QISG_CASE
     }
@@ -1461,7 +1495,7 @@ void launch_sweep4(bool pdl, const SamplesArgs<uint32_t> &p, const SlotThreshold
 template <typename Word>
 int make_red_args(qisg_handle *h, SlotThresholds &th, FusedRedArgsT<Word> &p, int &tpsite, int64_t &blocks) {
   const SamplesArgs<Word> a = make_args<Word>(h, 0);
-  fill_thresholds(h, a.t_has_zero, th);
+  fill_thresholds(h, th);
   p.src = reinterpret_cast<const Word *>(h->spins);
   p.dst = reinterpret_cast<Word *>(h->spins_alt);
   p.J = reinterpret_cast<const Word *>(h->J);
@@ -1477,9 +1511,7 @@ int make_red_args(qisg_handle *h, SlotThresholds &th, FusedRedArgsT<Word> &p, in
   p.n_slots = h->n_slots;
   p.n_q = h->n_q;
   p.n_rep = h->n_rep;
-  p.t_has_zero = a.t_has_zero;
   p.one = 1u;
-  p.all_ones = 0xFFFFFFFFu;
   p.tau_ap = h->tau_ap;
   tpsite = h->sweep_tile[0] == 1 ? 4 : h->sweep_tile[0] == 2 ? 2 : 1;
   if (sizeof(Word) == 8 && tpsite == 1) tpsite = 2;
@@ -1528,9 +1560,10 @@ int fused_red(qisg_handle *h) {
 template <typename Word>
 int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   if (h->fused && colour == 0 && !count_only) return fused_red<Word>(h);
-  // W = 32, blue variant 0 (and the counting red pass): a thread per
-  // (column segment, replica quad); otherwise the column walk, a thread per
-  // (column segment, replica)
+  // W = 32, blue variants 0 and 2 (and the counting red pass): a thread per
+  // (column segment, replica quad), variant 2 with its registers bounded to
+  // four blocks per SM; otherwise the column walk, a thread per (column
+  // segment, replica)
   if (sizeof(Word) == 4 && !(colour == 1 && h->sweep_variant[1] == 1)) {
     SlotThresholds th;
     SamplesArgs<uint32_t> p = make_args4(h, colour, th);
@@ -1548,7 +1581,9 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
     // the blue pass loads the next site of its walk while it updates the
     // current one (measured: 4% off the production sweep, with the tuner then
     // taking walks of 4 sites)
-    if (colour == 1)
+    if (colour == 1 && h->sweep_variant[1] == 2)
+      launch_sweep4<true, false, 4>(h->pdl, p, th, (unsigned)blocks, h->stream, 1, count_only);
+    else if (colour == 1)
       launch_sweep4<true, true>(h->pdl, p, th, (unsigned)blocks, h->stream, 1, count_only);
     else
       launch_sweep4<false, false>(h->pdl, p, th, (unsigned)blocks, h->stream, 0, count_only);
@@ -1558,7 +1593,7 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
   }
   SamplesArgs<Word> p = make_args<Word>(h, colour);
   SlotThresholds th;
-  fill_thresholds(h, p.t_has_zero, th);
+  fill_thresholds(h, th);
   if (colour == 1) {
     p.n_zero_U = 0;
     if (h->fused) {   // masks read by the fused red pass: clear them here
@@ -1836,7 +1871,14 @@ int samples_persistent(qisg_handle *h, int n_sweeps) {
   int rc = make_red_args<uint32_t>(h, th, a.red, tpsite, red_blocks);
   if (rc) return rc;
   a.red.n_zero_U = 0;
-  a.blue = make_args4(h, 1, th_blue);
+  // the blue phase's default segmentation fills the persistent grid (every
+  // form of the kernel is bounded to the same residency), walks of at most
+  // 32 sites
+  int per_sm0 = 0;
+  rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm0, samples_persistent_kernel<1, 0>, kBlock4, 0),
+                  "occupancy");
+  if (rc) return rc;
+  a.blue = make_args4(h, 1, th_blue, (int64_t)std::max(1, per_sm0) * std::max(1, h->n_sm), 32);
   a.blue.n_zero_U = 0;
   a.blue.n_zero_acc = 0;
   a.blue.t_copy = nullptr;

@@ -49,7 +49,7 @@ def test_persistent_autotune_and_switching(qisg):
     with a, b:
         a.set_persistent(True)
         g = a.autotune(1)
-        assert g in (1, 2, 4, 8, 16, 32)
+        assert g in (0, 1, 2, 4, 8, 16, 32)
         n = a.sweep_count()
         a.sweep(9)
         a.set_persistent(False)
