@@ -41,12 +41,15 @@ struct SamplesArgs {
   int n_seg;             // segments per column
   int seg_base, seg_rem; // W = 32 replica-quad kernel: segment g of a column holds seg_base + (g < seg_rem)
                          // sites (n_seg segments covering the L_tau / 2 sites of the colour)
+  int seg_blocks;        // > 0: blocks per segment, each block one segment of 128 columns (plane a
+                         // multiple of 128), so a block's walks have one length; 0: a block takes
+                         // 128 consecutive (segment, column) pairs and seg_rem = 0
   int blocks_per_set;    // blocks per (b, s, q) word set
   uint32_t one;          // 1 as a runtime value (accept_flag)
   unsigned long long *t_copy;   // blue pass, fused mode: copy t here for the PT pass
   int tau_ap;                   // antiperiodic along tau: the wrap tau bond flips sign
   // division by the invariants of the index decomposition (32-bit indices)
-  FastDiv fd_bps, fd_nq, fd_ns, fd_plane, fd_L;
+  FastDiv fd_bps, fd_nq, fd_ns, fd_plane, fd_L, fd_sb;
   // cleared by the red pass (nothing reads them until the blue pass / PT):
   unsigned long long *zero_U;   // bond counters, n_zero_U words
   int64_t n_zero_U;
@@ -352,7 +355,9 @@ __device__ __forceinline__ uint32_t q4(const uint4 &v, int j) {
 // exactly one red site, the one below it), to the other lattice buffer; the
 // blue pass then works on that buffer in place.  The four replica threads of
 // a site share one Philox call per slot, made by one of them per group of
-// four slots and exchanged in shared memory.
+// four slots and exchanged in shared memory.  The kernel is bounded to seven
+// blocks of 128 threads per SM (72 registers), so the 32768 red sites x 4
+// replicas of an L = 16, L_tau = 256 word set run as one wave on 152 SMs.
 template <typename Word>
 struct FusedRedArgsT {
   const Word *src;
@@ -371,7 +376,7 @@ struct FusedRedArgsT {
 };
 using FusedRedArgs = FusedRedArgsT<uint32_t>;
 
-__global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedRedArgs p,
+__global__ void __launch_bounds__(kBlock4, 7) samples_red_fused_kernel(const FusedRedArgs p,
                                                                      const __grid_constant__ SlotThresholds th) {
   pdl_begin();
   __shared__ uint32_t msk[4][kMaxSlotsPT];
@@ -443,7 +448,63 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fused_kernel(const FusedR
   }
   uint32_t *rw = reinterpret_cast<uint32_t *>(rnd) + (threadIdx.x >> 5) * 128;
   const int ql = (int)((threadIdx.x & 31) >> 2);
-  for (int g = 0; 4 * g < n; ++g) {
+  int g = 0;
+  {
+    // groups of four slots that all have two successors: no per-slot checks,
+    // and the bases of slots sl + 2 (loads) and sl (stores) advance by the
+    // slot stride
+    const uint32_t *ps2 = sb + 2 * SS;
+    uint32_t *pd = db;
+    for (; 4 * g + 6 <= n; ++g) {
+      if (live) {
+        const uint4 r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)(4 * g + j) | ((uint32_t)q << 16), ctr_w),
+                                p.key);
+        *reinterpret_cast<uint4 *>(rw + ((j * 8 + ql) << 2)) = r4;
+      }
+      __syncwarp();
+      if (live) {
+#pragma unroll 2   // two slots' loads in flight: 72 registers, seven blocks per SM
+        for (int i = 0; i < 4; ++i) {
+          const int sl = 4 * g + i;
+          uint32_t n2[7], fw[7];
+#pragma unroll
+          for (int k = 0; k < 7; ++k) n2[k] = ps2[zo[k]];
+          const uint32_t m = msk[j][sl];
+#pragma unroll
+          for (int k = 0; k < 7; ++k) {   // lanes of m exchange pair (sl, sl + 1)
+            fw[k] = mux(m, n1[k], cw[k]);
+            cw[k] = mux(m, cw[k], n1[k]);
+            n1[k] = n2[k];
+          }
+          const uint32_t R = rw[((i * 8 + ql) << 2) + j];
+          const unsigned long long *C = th.v[sl];
+          const uint32_t sc = fw[0];
+          const uint32_t b1 = sc ^ fw[3] ^ Jxp;
+          const uint32_t b2 = sc ^ fw[4] ^ Jxm;
+          const uint32_t b3 = sc ^ fw[5] ^ Jyp;
+          const uint32_t b4 = sc ^ fw[6] ^ Jym;
+          const uint32_t t1 = sc ^ fw[1] ^ gtp;
+          const uint32_t t2 = sc ^ fw[2] ^ gtm;
+          const uint32_t s1 = b1 ^ b2 ^ b3;
+          const uint32_t c1 = maj3(b1, b2, b3);
+          const uint32_t us0 = s1 ^ b4;
+          const uint32_t c2 = s1 & b4;
+          const uint32_t us1 = c1 ^ c2;
+          const uint32_t us2 = c1 & c2;
+          const uint32_t ut0 = t1 ^ t2;
+          const uint32_t ut1 = t1 & t2;
+          const uint32_t acc = accept_mask(R, C, us0, us1, us2, ut0, ut1, p.one);
+          pd[zo[0]] = sc ^ acc;
+          pd[zo[1]] = fw[1];
+          ps2 += SS;
+          pd += SS;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // the last groups, slot by slot
+  for (; 4 * g < n; ++g) {
     if (live && 4 * g + j < n) {
       const uint4 r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)(4 * g + j) | ((uint32_t)q << 16), ctr_w),
                               p.key);
@@ -761,10 +822,24 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
   const unsigned long long *C = th.v[s];
   const int L = p.L, plane = p.plane;
   const uint32_t Lt = (uint32_t)p.Lt, P = (uint32_t)plane;
-  const uint32_t gq = chunk * (uint32_t)kBlock4 + threadIdx.x;
-  const bool live = gq < P * (uint32_t)p.n_seg;
-  const uint32_t segu = p.fd_plane.div(gq);
-  const int i2 = (int)(gq - segu * P);
+  // segment segu and column i2 of the thread; segb is the block's segment
+  // when a block holds one segment (else 0, with seg_rem = 0), so the walk
+  // length G is the same for the whole block
+  uint32_t segu, segb, i2u;
+  bool live;
+  if (p.seg_blocks) {
+    segb = p.fd_sb.div(chunk);
+    segu = segb;
+    i2u = (chunk - segb * (uint32_t)p.seg_blocks) * (uint32_t)kBlock4 + threadIdx.x;
+    live = i2u < P;
+  } else {
+    const uint32_t gq = chunk * (uint32_t)kBlock4 + threadIdx.x;
+    live = gq < P * (uint32_t)p.n_seg;
+    segu = p.fd_plane.div(gq);
+    segb = 0;
+    i2u = gq - segu * P;
+  }
+  const int i2 = (int)i2u;
   const int y = (int)p.fd_L.div((uint32_t)i2), x = i2 - y * L;
   const int ixp = (x + 1 == L ? 0 : x + 1) + L * y, ixm = (x == 0 ? L - 1 : x - 1) + L * y;
   const int iyp = x + L * (y + 1 == L ? 0 : y + 1), iym = x + L * (y == 0 ? L - 1 : y - 1);
@@ -775,7 +850,7 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
   uint32_t Jxp = 0, Jxm = 0, Jyp = 0, Jym = 0;
   const uint32_t tau0 = 2u * (segu * (uint32_t)p.seg_base + min(segu, (uint32_t)p.seg_rem)) +
                         (uint32_t)((colour + x + y) & 1);
-  const int G = p.seg_base + (segu < (uint32_t)p.seg_rem ? 1 : 0);
+  const int G = p.seg_base + (segb < (uint32_t)p.seg_rem ? 1 : 0);
   const uint32_t ctr_z = (uint32_t)s | ((uint32_t)q << 16);
   const uint32_t ctr_w = (DOM_SWEEP << 28) | (uint32_t)((b * 32) >> 6);
 
@@ -1326,6 +1401,7 @@ SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
   p.n_seg = half_col / G;
   p.seg_base = G;
   p.seg_rem = 0;
+  p.seg_blocks = 0;
   p.blocks_per_set = (int)(((int64_t)p.plane * p.n_seg + kQuads - 1) / kQuads);
   p.fd_bps = FastDiv((uint32_t)p.blocks_per_set);
   p.fd_nq = FastDiv((uint32_t)p.n_q);
@@ -1397,23 +1473,35 @@ int blue_blocks_per_sm(qisg_handle *h, int g2, int variant) {
   return c = per_sm;
 }
 
+// Blocks of one (b, s, q) set for n_seg segments per column: a block per
+// (segment, 128 columns) when the plane is a multiple of 128 (walk lengths
+// may then differ between segments), else 128 consecutive (segment, column)
+// pairs per block (segments of one length).
+int64_t blocks_per_set4(int plane, int n_seg) {
+  return plane % kBlock4 == 0 ? (int64_t)(plane / kBlock4) * n_seg
+                              : ((int64_t)plane * n_seg + kBlock4 - 1) / kBlock4;
+}
+
 // Segments per column of the blue pass when no tile is pinned: the count
 // that minimises (waves of blocks over the resident ones) x (work of one
 // thread), a thread's work being its walk of up to G sites (about 490
 // instructions a site for its four replica words) plus its part of the
 // block's counter tree (about 32 instructions per counter plane level),
-// with walks of at most max_walk sites.  resident(g2) gives the resident blocks
-// for counter planes of walks up to 4 << g2 sites.
+// with walks of at most max_walk sites.  Counts that leave segments of
+// unequal length are candidates only when a block holds one segment.
+// resident(g2) gives the resident blocks for counter planes of walks up to
+// 4 << g2 sites.
 template <typename Resident>
 int wave_fill_segments(int64_t sets, int plane, int half_col, int max_walk, Resident resident) {
   int best = half_col;
   double best_cost = -1.0;
   for (int ns = std::max(1, (half_col + max_walk - 1) / max_walk); ns <= half_col; ++ns) {
+    if (plane % kBlock4 != 0 && half_col % ns != 0) continue;
     const int gmax = (half_col + ns - 1) / ns;
     int g2 = 0;
     while ((4 << g2) < gmax) ++g2;
     const int64_t R = std::max<int64_t>(1, resident(g2));
-    const int64_t blocks = sets * (((int64_t)plane * ns + kBlock4 - 1) / kBlock4);
+    const int64_t blocks = sets * blocks_per_set4(plane, ns);
     const int64_t waves = (blocks + R - 1) / R;
     const double cost = (double)waves * (490.0 * gmax + 32.0 * (2 * g2 + 23));
     if (best_cost < 0.0 || cost < best_cost) {
@@ -1425,7 +1513,9 @@ int wave_fill_segments(int64_t sets, int plane, int half_col, int max_walk, Resi
 }
 
 // W = 32 kernel: one thread per column segment.  A pinned tile G gives
-// ceil((L_tau / 2) / G) segments of at most G sites; the default gives the
+// ceil((L_tau / 2) / G) segments of at most G sites (planes that are not a
+// multiple of 128: the largest divisor of L_tau / 2 not above G); the
+// default gives the
 // blue pass the wave-filling count above (resident_blocks: the launch's
 // resident blocks, 0 = those of the blue kernel itself; walks of at most
 // max_walk sites) and the red pass as many sites per thread as keep about
@@ -1437,8 +1527,12 @@ SamplesArgs<uint32_t> make_args4(qisg_handle *h, int colour, SlotThresholds &th,
   const int64_t sets = h->n_b * h->n_slots * h->n_q;
   const int tile = std::min(h->sweep_tile[colour], half_col);
   int n_seg;
-  if (tile > 0) {
+  if (tile > 0 && p.plane % kBlock4 == 0) {
     n_seg = (half_col + tile - 1) / tile;
+  } else if (tile > 0) {
+    int G = tile;
+    while (G > 1 && half_col % G) --G;
+    n_seg = half_col / G;
   } else if (colour == 1) {
     const int variant = h->sweep_variant[1];
     n_seg = wave_fill_segments(sets, p.plane, half_col, max_walk, [&](int g2) -> int64_t {
@@ -1456,7 +1550,9 @@ SamplesArgs<uint32_t> make_args4(qisg_handle *h, int colour, SlotThresholds &th,
   p.seg_base = half_col / n_seg;
   p.seg_rem = half_col % n_seg;
   p.seg_sites = p.seg_base + (p.seg_rem > 0 ? 1 : 0);
-  p.blocks_per_set = (int)(((int64_t)p.plane * p.n_seg + kBlock4 - 1) / kBlock4);
+  p.seg_blocks = p.plane % kBlock4 == 0 ? p.plane / kBlock4 : 0;
+  p.fd_sb = FastDiv((uint32_t)std::max(1, p.seg_blocks));
+  p.blocks_per_set = (int)blocks_per_set4(p.plane, n_seg);
   p.fd_bps = FastDiv((uint32_t)p.blocks_per_set);
   fill_thresholds(h, th);
   return p;

@@ -262,17 +262,19 @@ def test_antiperiodic_tau_bit_exact(qisg, W, tiles):
         assert np.array_equal(sq, st.sumq) and np.array_equal(sq2, st.sumq2)
 
 
-@pytest.mark.parametrize("variant,tiles", [(0, (1, 2)), (0, (1, 0)), (1, (2, 4)), (2, (1, 1)), (2, (4, 5)),
-                                           (2, (0, 64)), (2, (2, 0)), (0, (4, 3))])
-def test_blue_variants_bit_exact(qisg, variant, tiles):
+@pytest.mark.parametrize("L,variant,tiles", [(16, 0, (1, 2)), (16, 0, (1, 0)), (8, 1, (2, 4)), (16, 2, (1, 1)),
+                                             (16, 2, (4, 5)), (16, 2, (0, 64)), (16, 2, (2, 0)), (16, 0, (4, 3)),
+                                             (8, 0, (1, 3)), (8, 0, (2, 0))])
+def test_blue_variants_bit_exact(qisg, L, variant, tiles):
     """Each 32-bit blue kernel (replica quads, column walk, replica quads with
     bounded registers) and red tile on a lattice of several blocks per
     (sample word, slot) with a ragged second word: the oracle's trajectory.
-    L_tau / 2 = 13 sites per column and colour, so walks of at most 2, 3 or 5
-    sites split a column into segments of unequal length (7 x 2 -> 2,2,2,2,2,
-    2,1; 5 x 3 -> 3,3,3,2,2; 3 x 5 -> 5,4,4), 64 gives one segment, and 0 the
-    default segmentation."""
-    L, Lt, n_slots, n_rep, n_samples = 8, 26, 6, 5, 45
+    L_tau / 2 = 13 sites per column and colour.  At L = 16 (a plane of 256
+    columns, a block per segment) walks of at most 2, 3 or 5 sites split a
+    column into segments of unequal length (7 x 2 -> 2,2,2,2,2,2,1; 5 x 3 ->
+    3,3,3,2,2; 3 x 5 -> 5,4,4), 64 gives one segment, and 0 the default
+    segmentation; at L = 8 (64 columns) segments have one length."""
+    Lt, n_slots, n_rep, n_samples = 26, 6, 5, 45
     inst, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 0.9, n_rep, n_samples, 71, word_bits=32,
                         layout=qisg.QISG_LAYOUT_SAMPLES, measure_every=2)
     st = oracle_state(ladder, L, Lt, n_rep, 71, 0, n_samples)

@@ -40,6 +40,28 @@ def test_persistent_equals_oracle(qisg, tiles, me, ap, graphs):
         assert np.array_equal(sA, st.sumA) and np.array_equal(sq2, st.sumq2)
 
 
+@pytest.mark.parametrize("tiles", [(1, 5), (2, 0), (4, 3)])
+def test_persistent_uneven_walks_equal_oracle(qisg, tiles):
+    """The persistent form at L = 16 (a block per segment of 128 columns)
+    with L_tau / 2 = 13 sites per column and colour: walks of at most 5 or 3
+    sites give segments of unequal length (5,4,4 and 3,3,3,2,2), 0 the
+    default segmentation for the persistent grid."""
+    L, Lt, n_slots, n_rep, n_a, seed = 16, 26, 5, 4, 36, 29
+    inst, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 0.9, n_rep, n_a, seed, word_bits=32,
+                        layout=qisg.QISG_LAYOUT_SAMPLES, measure_every=3)
+    st = oracle_state(ladder, L, Lt, n_rep, seed, 0, n_a)
+    with inst:
+        inst.set_persistent(True)
+        inst.set_tiles(tiles, (0, 0))
+        for n in (1, 7, 16):
+            inst.sweep(n)
+            oracle.run(st, n, pt_every=1, measure_every=3)
+            assert_same_state(inst, st, what=f"tiles={tiles} after {st.t}")
+        sA, sB, sq, sq2, nm = inst.measurements()
+        assert nm == st.n_meas
+        assert np.array_equal(sA, st.sumA) and np.array_equal(sq2, st.sumq2)
+
+
 def test_persistent_autotune_and_switching(qisg):
     """The autotuner's persistent candidates, and switching the form on and
     off mid-run, keep the trajectory of plain launches."""
