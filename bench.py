@@ -217,7 +217,7 @@ def time_form(torch, qisg, w, form, steps, warmup, seed):
     # untimed: pick the sweep tiles on the live state (results do not depend
     # on them), then realign to the graph cycle of measure_every sweeps
     if TILES is None:
-        inst.autotune(3)
+        inst.autotune(6)
     else:
         inst.set_tiles(TILES[:2], TILES[2:])
     cyc = max(1, w.measure_every)
@@ -296,17 +296,31 @@ def kernel_shares(kern):
     return {k: (kern[k]["ms"] / tot if tot > 0 else 0.0) for k, _ in KINDS if k in kern}
 
 
-def kernel_names(layout, wb, tiles):
+def red_threads_per_site(w, wb, t_red, n_sm):
+    """Threads per red site of the fused red pass: the library's rule (tile
+    1 -> four, 2 -> two, 0 -> four while one thread per site would fill fewer
+    than four waves of 2048 threads per SM, else one; 64-bit words at most
+    two replicas per thread)."""
+    if t_red == 0:
+        site_threads = (-(-w.n_samples // wb)) * (-(-w.n_replicas // 4)) * w.L * w.L * (w.L_tau // 2)
+        tps = 4 if site_threads < 4 * 2048 * max(1, n_sm) else 1
+    else:
+        tps = {1: 4, 2: 2}.get(t_red, 1)
+    return 2 if (wb == 64 and tps == 1) else tps
+
+
+def kernel_names(layout, wb, tiles, w, n_sm):
     """The CUDA kernels behind the red and blue kinds for this schedule."""
     from paper_2402_03920_gb300 import qisg
     if layout != qisg.QISG_LAYOUT_SAMPLES:
         return {"red": "lanes_half_sweep_kernel", "blue": "lanes_half_sweep_kernel"}
     (t_red, _t_blue), (_v_red, v_blue) = tiles
+    tps = red_threads_per_site(w, wb, t_red, n_sm)
     if wb == 32:
-        red = {1: "samples_red_fused_kernel", 2: "samples_red_fusedq_kernel<2>"}.get(t_red, "samples_red_fusedq_kernel<4>")
+        red = {4: "samples_red_fused_kernel", 2: "samples_red_fusedq_kernel<2>"}.get(tps, "samples_red_fusedq_kernel<4>")
         blue = {0: "samples_sweep4_kernel", 2: "samples_sweep4_kernel<min 4 blocks>"}.get(v_blue, "samples_half_sweep_kernel")
     else:
-        red = "samples_red_fusedq_kernel<u64, 1>" if t_red == 1 else "samples_red_fusedq_kernel<u64, 2>"
+        red = "samples_red_fusedq_kernel<u64, 1>" if tps == 4 else "samples_red_fusedq_kernel<u64, 2>"
         blue = "samples_half_sweep_kernel"
     return {"red": red, "blue": blue}
 
@@ -387,7 +401,7 @@ def form_roofline(kern, w, layout, wb, n_sm, pk, steps, ms_per_step, tiles):
     from paper_2402_03920_gb300 import qisg
     key = f"samples{wb}" if layout == qisg.QISG_LAYOUT_SAMPLES else "lanes"
     return roofline(kern, updates_per_step(w), key, n_sm, pk, steps, ms_per_step,
-                    kernel_names(layout, wb, tiles), w.name)
+                    kernel_names(layout, wb, tiles, w, n_sm), w.name)
 
 
 def alu_peak_source(n_sm, pk, pk_kind) -> str:
@@ -471,7 +485,7 @@ def large_batched_entry(torch, qisg, sweeps=20, persistent_sweeps=2000):
             tiles = inst.tiles()
             layout, _ = inst.layout()
         rl, rl_all = roofline(kern, ups_per_sweep, f"samples{wb}", n_sm, pk, sweeps, ms / sweeps,
-                              kernel_names(layout, wb, tiles), w.name)
+                              kernel_names(layout, wb, tiles, w, n_sm), w.name)
         out[f"per_pass_u{wb}"] = {"value": ms * 1e9 / (ups_per_sweep * sweeps), "unit": UNIT, "ms": ms,
                                   "sweeps": sweeps, "share": kernel_shares(kern), "roofline": rl,
                                   "roofline_by_kernel": rl_all}

@@ -417,12 +417,13 @@ int qisg_set_persistent(qisg_handle *h, int enable, int64_t wait_ns);
  * default (0) and, for 32-bit words, the three blue kernel variants of each.
  * The tile is, for 64-bit words, the site groups of 4 each thread walks along
  * tau; for 32-bit words it selects the red pass's threads per site (1: four,
- * 2: two, else one) and the blue pass's sites per thread (variants 0 and 2,
- * a thread per replica quad walking at most `tile` sites, the L_tau / 2 sites
- * of a column split into ceil(L_tau / 2 / tile) segments whose lengths differ
- * by at most one; 2 with its registers bounded to four blocks per SM and no
- * prefetch of the next site) or site groups of 4 per thread (variant 1, a
- * thread per replica).  The default of variants 0 and 2 picks the segment
+ * 2: two, 0: four while one thread per site would fill fewer than four waves
+ * of 2048 threads per SM, else one) and the blue pass's sites per thread
+ * (variants 0 and 2, a thread per replica quad walking at most `tile` sites,
+ * the L_tau / 2 sites of a column split into ceil(L_tau / 2 / tile) segments
+ * whose lengths differ by at most one; 2 with its registers bounded to four
+ * blocks per SM and no prefetch of the next site) or site groups of 4 per
+ * thread (variant 1, a thread per replica).  The default of variants 0 and 2 picks the segment
  * count that fills whole waves of resident blocks.  The simulation advances
  * by C * (1 + sweeps_per_candidate) sweeps meanwhile, C = 24 candidates for
  * 32-bit words and 8 for 64-bit words (results never depend on the schedule,

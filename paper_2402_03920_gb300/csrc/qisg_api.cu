@@ -3,11 +3,13 @@
 // precomputed for every possible value; the PT bases), device memory, and the
 // sweep schedule (Appendix A: EMCS = pt_every sweeps + one PT update, an
 // energy measurement every measure_every sweeps).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "qisg_internal.cuh"
@@ -886,6 +888,26 @@ int qisg_set_couplings(qisg_handle *h, const int8_t *J) {
   return rc;
 }
 
+// Every byte of S[0 .. n) is +1 or -1: (s + 1) & 0xFD == 0, a loop the
+// compiler vectorises, split over host threads for large states.
+static bool spins_are_pm1(const int8_t *S, int64_t n) {
+  auto scan = [S](int64_t lo, int64_t hi) {
+    uint8_t bad = 0;
+    for (int64_t i = lo; i < hi; ++i) bad |= (uint8_t)((uint8_t)S[i] + 1u) & 0xFDu;
+    return bad == 0;
+  };
+  const int64_t per = int64_t(1) << 24;
+  const int nt = (int)std::min<int64_t>(std::max(1u, std::min(16u, std::thread::hardware_concurrency())),
+                                        (n + per - 1) / per);
+  if (nt <= 1) return scan(0, n);
+  std::vector<char> ok((size_t)nt, 1);
+  std::vector<std::thread> pool;
+  for (int k = 0; k < nt; ++k)
+    pool.emplace_back([&, k] { ok[(size_t)k] = scan(n * k / nt, n * (k + 1) / nt) ? 1 : 0; });
+  for (auto &th : pool) th.join();
+  return std::all_of(ok.begin(), ok.end(), [](char c) { return c != 0; });
+}
+
 int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, uint64_t sweep) {
   if (!h || !S || !walker_at) return fail(QISG_EINVAL, "NULL argument");
   const int64_t rows = h->n_samples * h->n_rep;
@@ -899,10 +921,7 @@ int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, ui
     }
   }
   const int64_t nS = rows * h->n_slots * h->N;
-  // +-1 <=> (s + 1) is 0 or 2 <=> (s + 1) & 0xFD == 0 (a loop the compiler vectorises)
-  uint8_t bad = 0;
-  for (int64_t i = 0; i < nS; ++i) bad |= (uint8_t)((uint8_t)S[i] + 1u) & 0xFDu;
-  if (bad) return fail(QISG_ECORRUPT, "spins must be +-1");
+  if (!spins_are_pm1(S, nS)) return fail(QISG_ECORRUPT, "spins must be +-1");
   int rc = sync_handle(h);
   if (rc) return rc;
   // the permutation first (padding lanes keep the identity): SAMPLES packs by

@@ -514,7 +514,8 @@ struct qisg_handle {
   // tile: W = 64 and the W = 32 column walk: site groups of 4 per thread
   // quad; W = 32 replica-quad kernel: at most this many sites per thread
   // along tau; W = 32 red pass: threads per site (1: four, 2: two, else
-  // one); 0 = default.
+  // one; by default four for lattices with few sites per launch); 0 =
+  // default.
   // variant (W = 32 blue pass): 0 the replica-quad kernel, 1 the column walk,
   // 2 the replica-quad kernel bounded to four blocks per SM (no prefetch).
   // The default grid aims at sweep_min_blocks_per_sm blocks of 256 threads

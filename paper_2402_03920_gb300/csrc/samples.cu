@@ -449,19 +449,21 @@ __global__ void __launch_bounds__(kBlock4, 7) samples_red_fused_kernel(const Fus
   uint32_t *rw = reinterpret_cast<uint32_t *>(rnd) + (threadIdx.x >> 5) * 128;
   const int ql = (int)((threadIdx.x & 31) >> 2);
   int g = 0;
+  uint4 r4 = make_uint4(0u, 0u, 0u, 0u);
   {
     // groups of four slots that all have two successors: no per-slot checks,
     // and the bases of slots sl + 2 (loads) and sl (stores) advance by the
     // slot stride
     const uint32_t *ps2 = sb + 2 * SS;
     uint32_t *pd = db;
+    // this thread's Philox call of the group (slot 4 g + j); the next
+    // group's call is made while this group's slots are updated
+    if (live && 6 <= n) r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)j | ((uint32_t)q << 16), ctr_w), p.key);
     for (; 4 * g + 6 <= n; ++g) {
-      if (live) {
-        const uint4 r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)(4 * g + j) | ((uint32_t)q << 16), ctr_w),
-                                p.key);
-        *reinterpret_cast<uint4 *>(rw + ((j * 8 + ql) << 2)) = r4;
-      }
+      if (live) *reinterpret_cast<uint4 *>(rw + ((j * 8 + ql) << 2)) = r4;
       __syncwarp();
+      if (live && 4 * (g + 1) + j < n)
+        r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)(4 * (g + 1) + j) | ((uint32_t)q << 16), ctr_w), p.key);
       if (live) {
 #pragma unroll 2   // two slots' loads in flight: 72 registers, seven blocks per SM
         for (int i = 0; i < 4; ++i) {
@@ -503,11 +505,12 @@ __global__ void __launch_bounds__(kBlock4, 7) samples_red_fused_kernel(const Fus
       __syncwarp();
     }
   }
-  // the last groups, slot by slot
-  for (; 4 * g < n; ++g) {
+  // the last groups, slot by slot (the first of them has its call made by
+  // the loop above when that ran)
+  for (bool made = g > 0; 4 * g < n; ++g, made = false) {
     if (live && 4 * g + j < n) {
-      const uint4 r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)(4 * g + j) | ((uint32_t)q << 16), ctr_w),
-                              p.key);
+      if (!made)
+        r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)(4 * g + j) | ((uint32_t)q << 16), ctr_w), p.key);
       *reinterpret_cast<uint4 *>(rw + ((j * 8 + ql) << 2)) = r4;
     }
     __syncwarp();
@@ -877,8 +880,13 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
     cur.xm = ld_g<CG>(pxm + off);
     cur.yp = ld_g<CG>(pyp + off);
     cur.ym = ld_g<CG>(pym + off);
+    // the draws of the walk's next site are made while this one is updated,
+    // so the Philox chain overlaps independent work
+    uint4 R4 = philox(make_uint4((uint32_t)i2 + off, (uint32_t)t, ctr_z, ctr_w), p.key);
     for (int k = 0; k < G; ++k) {
       const uint32_t tau = tau0 + 2u * (uint32_t)k;
+      uint4 R4n = R4;
+      if (k + 1 < G) R4n = philox(make_uint4((uint32_t)i2 + off + 2 * P, (uint32_t)t, ctr_z, ctr_w), p.key);
       auto load_next = [&](Quad4 &nx) {
         const uint32_t offn = off + 2 * P;
         nx.c = ld_g<CG>(pc + offn);
@@ -890,7 +898,6 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
       };
       Quad4 nxt;
       if (PF && k + 1 < G) load_next(nxt);
-      const uint4 R4 = philox(make_uint4((uint32_t)i2 + off, (uint32_t)t, ctr_z, ctr_w), p.key);
       // the antiperiodic wrap bond is unsatisfied when its spins agree
       const uint32_t gtp = ones_if<uint32_t>(p.tau_ap && tau + 1 == Lt), gtm = ones_if<uint32_t>(p.tau_ap && tau == 0);
       uint32_t f[4];
@@ -924,6 +931,7 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
         }
       }
       if (!count_only) wc[off] = make_uint4(cur.c.x ^ f[0], cur.c.y ^ f[1], cur.c.z ^ f[2], cur.c.w ^ f[3]);
+      R4 = R4n;
       if (k + 1 < G) {
         dn = cur.up;
         if (PF)
@@ -1586,8 +1594,9 @@ void launch_sweep4(bool pdl, const SamplesArgs<uint32_t> &p, const SlotThreshold
 }
 
 // Arguments of the fused red pass (and its threads per site, from the red
-// tile: 1 -> four, 2 -> two, else one; 64-bit words: at most two replicas
-// per thread) and its block count.
+// tile: 1 -> four, 2 -> two, else one, 0 -> four for lattices with few sites
+// per launch; 64-bit words: at most two replicas per thread) and its block
+// count.
 template <typename Word>
 int make_red_args(qisg_handle *h, SlotThresholds &th, FusedRedArgsT<Word> &p, int &tpsite, int64_t &blocks) {
   const SamplesArgs<Word> a = make_args<Word>(h, 0);
@@ -1609,7 +1618,14 @@ int make_red_args(qisg_handle *h, SlotThresholds &th, FusedRedArgsT<Word> &p, in
   p.n_rep = h->n_rep;
   p.one = 1u;
   p.tau_ap = h->tau_ap;
-  tpsite = h->sweep_tile[0] == 1 ? 4 : h->sweep_tile[0] == 2 ? 2 : 1;
+  if (h->sweep_tile[0] == 0) {
+    // default: a thread per site and replica unless one thread per site
+    // already gives a few waves of full SMs (2048 threads each)
+    const int64_t site_threads = h->n_b * h->n_q * (int64_t)a.plane * (h->Lt / 2);
+    tpsite = site_threads < (int64_t)4 * 2048 * std::max(1, h->n_sm) ? 4 : 1;
+  } else {
+    tpsite = h->sweep_tile[0] == 1 ? 4 : h->sweep_tile[0] == 2 ? 2 : 1;
+  }
   if (sizeof(Word) == 8 && tpsite == 1) tpsite = 2;
   const int64_t threads_per_set = (int64_t)a.plane * (h->Lt / 2) * tpsite;
   if (threads_per_set + kBlock4 > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");

@@ -83,6 +83,28 @@ def _summary(lines):
     return cs.summary()
 
 
+def test_kernel_names_follow_the_library_schedule_rule():
+    """The red tile 0 (the default) means four threads per site while one
+    thread per site would fill fewer than four waves of 2048 threads per SM:
+    the 32-sample L = 16, L_tau = 256 word set (32768 red sites) takes the
+    one-replica kernel on 152 SMs, a 1024-sample L = 24, L_tau = 512 batch
+    (32 words x 147456 red sites) the replica-quad kernel."""
+    from types import SimpleNamespace
+    from paper_2402_03920_gb300 import qisg
+    S = qisg.QISG_LAYOUT_SAMPLES
+    small = SimpleNamespace(n_samples=32, n_replicas=4, L=16, L_tau=256)
+    large = SimpleNamespace(n_samples=1024, n_replicas=4, L=24, L_tau=512)
+    assert bench.kernel_names(S, 32, ((0, 0), (0, 0)), small, 152)["red"] == "samples_red_fused_kernel"
+    assert bench.kernel_names(S, 32, ((0, 0), (0, 0)), large, 152)["red"] == "samples_red_fusedq_kernel<4>"
+    assert bench.kernel_names(S, 32, ((2, 0), (0, 2)), large, 152) == {
+        "red": "samples_red_fusedq_kernel<2>", "blue": "samples_sweep4_kernel<min 4 blocks>"}
+    assert bench.kernel_names(S, 32, ((8, 4), (0, 1)), small, 152)["blue"] == "samples_half_sweep_kernel"
+    assert bench.kernel_names(S, 64, ((0, 0), (0, 0)), small, 152)["red"] == "samples_red_fusedq_kernel<u64, 1>"
+    assert bench.kernel_names(S, 64, ((0, 0), (0, 0)), large, 152)["red"] == "samples_red_fusedq_kernel<u64, 2>"
+    assert bench.kernel_names(qisg.QISG_LAYOUT_LANES, 64, ((0, 0), (0, 0)), small, 152)["red"] == \
+        "lanes_half_sweep_kernel"
+
+
 def test_clock_summary_median_max_and_reasons():
     ok = "0, {sm}, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, {pc}"
     rows = [ok.format(sm=sm, pc=pc) for sm, pc in ((2070, "Not Active"), (1950, "Active"), (2010, "Not Active"))]
