@@ -55,11 +55,14 @@ def parse():
                    help="other workloads measured beside the headline (empty: none)")
     p.add_argument("--serving-requests", type=int, default=100)
     p.add_argument("--tiles", default="",
-                   help="pin the sweep schedule 'red_tile,blue_tile,red_variant,blue_variant' instead of autotuning")
+                   help="pin the sweep schedule 'red_tile,blue_tile,red_variant,blue_variant'")
+    p.add_argument("--autotune", action="store_true",
+                   help="tune the sweep schedule on the live state (untimed) instead of the library's default")
     return p.parse_args()
 
 
-TILES = None    # pinned sweep schedule (from --tiles), else autotuned
+TILES = None    # pinned sweep schedule (from --tiles)
+AUTOTUNE = False   # tune the schedule on the live state (--autotune); else the library's default
 TUNED = {}      # form -> schedule used
 
 
@@ -214,12 +217,13 @@ def time_form(torch, qisg, w, form, steps, warmup, seed):
     one and its absolute durations are not used)."""
     inst = make_instance(qisg, w, form, seed)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
-    # untimed: pick the sweep tiles on the live state (results do not depend
-    # on them), then realign to the graph cycle of measure_every sweeps
-    if TILES is None:
-        inst.autotune(6)
-    else:
+    # the library's default schedule unless one is pinned (--tiles) or tuned
+    # on the live state (--autotune, untimed); results do not depend on it.
+    # Then realign to the graph cycle of measure_every sweeps
+    if TILES is not None:
         inst.set_tiles(TILES[:2], TILES[2:])
+    elif AUTOTUNE:
+        inst.autotune(6)
     cyc = max(1, w.measure_every)
     inst.sweep((cyc - inst.sweep_count() % cyc) % cyc)
     TUNED[form] = inst.tiles()
@@ -766,7 +770,8 @@ def run_gpu(args):
                    "word_bits": wb,
                    "sweep_schedule": {"tiles": list(TUNED.get(main, ((0, 0), (0, 0)))[0]),
                                       "variants": list(TUNED.get(main, ((0, 0), (0, 0)))[1]),
-                                      "how": "pinned" if TILES else "autotuned (untimed)"},
+                                      "how": "pinned" if TILES else ("autotuned (untimed)" if AUTOTUNE
+                                                                      else "library default")},
                    "l2": "flushed between steps (2x L2 buffer written); lattice fits in L2 within a step"},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -849,8 +854,9 @@ def run_reference(args):
 
 
 def main():
-    global TILES
+    global TILES, AUTOTUNE
     args = parse()
+    AUTOTUNE = args.autotune
     if args.tiles:
         TILES = [int(v) for v in args.tiles.split(",")]
         if len(TILES) != 4:
