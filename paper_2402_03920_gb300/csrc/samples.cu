@@ -1276,21 +1276,37 @@ __global__ void samples_extract_kernel(const Word *spins, const int32_t *walker,
 // Pack the int8 +-1 spins of replica r of the samples of word group b
 // (staged [a - b W][walker][site], n_a of them) into the lattice: a thread
 // per (slot, site) word, lane a - b W, walker from the device labels.
+// Pack staged int8 spins into the SAMPLES words: the stage holds n_a
+// samples of word group b, each with replicas r0 .. r0 + nr - 1 ([al][rr]
+// [slot][site], slot by walker label); a thread packs four consecutive sites
+// of one (replica, slot) (N is a multiple of 4: L and L_tau are even).
 template <typename Word>
-__global__ void samples_pack_kernel(Word *spins, const int8_t *stage, const int32_t *walker, int64_t b, int r,
-                                    int n_a, int64_t N, int n_slots, int n_q, int n_rep) {
+__global__ void samples_pack_kernel(Word *spins, const int8_t *stage, const int32_t *walker, int64_t b, int r0,
+                                    int nr, int n_a, int64_t N, int n_slots, int n_q, int n_rep) {
   constexpr int W = (int)sizeof(Word) * 8;
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // [s][site]
-  if (c >= (int64_t)n_slots * N) return;
-  const int s = (int)(c / N);
-  const int64_t site = c - (int64_t)s * N;
-  Word v = 0;
+  const int64_t N4 = N / 4;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // [rr][s][site / 4]
+  if (c >= (int64_t)nr * n_slots * N4) return;
+  const int64_t rs = c / N4;
+  const int64_t site = (c - rs * N4) * 4;
+  const int rr = (int)(rs / n_slots), s = (int)(rs - (int64_t)rr * n_slots);
+  const int r = r0 + rr;
+  const int64_t pitch = (int64_t)nr * n_slots * N;   // bytes of one sample in the stage
+  Word v0 = 0, v1 = 0, v2 = 0, v3 = 0;
   for (int al = 0; al < n_a; ++al) {
     const int64_t a = b * W + al;
     const int w = walker[(a * n_rep + r) * n_slots + s];
-    if (stage[((int64_t)al * n_slots + w) * N + site] == -1) v |= Word(1) << al;
+    const char4 x = *reinterpret_cast<const char4 *>(stage + al * pitch + ((int64_t)rr * n_slots + w) * N + site);
+    v0 |= Word(x.x == -1) << al;
+    v1 |= Word(x.y == -1) << al;
+    v2 |= Word(x.z == -1) << al;
+    v3 |= Word(x.w == -1) << al;
   }
-  spins[(((b * n_slots + s) * n_q + (r >> 2)) * N + site) * 4 + (r & 3)] = v;
+  Word *o = spins + (((b * n_slots + s) * n_q + (r >> 2)) * N + site) * 4 + (r & 3);
+  o[0] = v0;
+  o[4] = v1;
+  o[8] = v2;
+  o[12] = v3;
 }
 
 // ---- persistent form: red | blue | PT for a run of sweeps in one launch ----
@@ -1873,12 +1889,14 @@ int set_spins_t(qisg_handle *h, const int8_t *S, const int32_t *walker_at) {
     h->perm_pending = false;
   }
   // the walker labels are on the device already (qisg_set_state uploads
-  // them first); the spins go up one (word group, replica) at a time into a
-  // staging buffer and are packed there
+  // them first); the spins go up one word group at a time (all its replicas
+  // in one copy while that stays within 256 MB of staging, else a few
+  // replicas per copy) into a staging buffer and are packed there
   (void)walker_at;
   const int64_t row = (int64_t)h->n_slots * h->N;   // bytes of one (sample, replica)
+  const int nr = (int)std::max<int64_t>(1, std::min<int64_t>(h->n_rep, ((int64_t)256 << 20) / ((int64_t)W * row)));
   int8_t *stage = nullptr;
-  int rc = cuda_check(cudaMalloc(&stage, (size_t)W * row), "cudaMalloc");
+  int rc = cuda_check(cudaMalloc(&stage, (size_t)W * nr * row), "cudaMalloc");
   if (rc) return rc;
   if ((size_t)h->n_q * 4 > (size_t)h->n_rep) {   // padding replicas of the last quad stay 0
     rc = cuda_check(cudaMemsetAsync(h->spins, 0, (size_t)h->n_b * h->n_slots * h->n_q * h->N * 4 * sizeof(Word),
@@ -1887,14 +1905,16 @@ int set_spins_t(qisg_handle *h, const int8_t *S, const int32_t *walker_at) {
   }
   for (int64_t b = 0; b < h->n_b && !rc; ++b) {
     const int n_a = (int)std::min<int64_t>(W, h->n_samples - b * W);
-    for (int r = 0; r < h->n_rep && !rc; ++r) {
-      rc = cuda_check(cudaMemcpy2DAsync(stage, (size_t)row, S + ((b * W) * h->n_rep + r) * row,
-                                        (size_t)(h->n_rep * row), (size_t)row, (size_t)n_a, cudaMemcpyHostToDevice,
-                                        h->stream),
+    for (int r0 = 0; r0 < h->n_rep && !rc; r0 += nr) {
+      const int k = std::min(nr, h->n_rep - r0);
+      rc = cuda_check(cudaMemcpy2DAsync(stage, (size_t)(k * row), S + ((b * W) * h->n_rep + r0) * row,
+                                        (size_t)(h->n_rep * row), (size_t)(k * row), (size_t)n_a,
+                                        cudaMemcpyHostToDevice, h->stream),
                       "copy spins");
       if (rc) break;
-      samples_pack_kernel<Word><<<(unsigned)((row + 255) / 256), 256, 0, h->stream>>>(
-          reinterpret_cast<Word *>(h->spins), stage, h->d_walker, b, r, n_a, h->N, h->n_slots, h->n_q, h->n_rep);
+      const int64_t threads = (int64_t)k * row / 4;
+      samples_pack_kernel<Word><<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(
+          reinterpret_cast<Word *>(h->spins), stage, h->d_walker, b, r0, k, n_a, h->N, h->n_slots, h->n_q, h->n_rep);
       h->launches++;
       rc = cuda_check(cudaGetLastError(), "pack spins");
     }
