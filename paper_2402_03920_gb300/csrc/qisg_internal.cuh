@@ -522,7 +522,7 @@ struct qisg_handle {
   // per SM.
   int sweep_tile[2] = {0, 0};
   int sweep_variant[2] = {0, 0};
-  int blue_occ[2][6] = {};   // resident blocks per SM of the W = 32 blue kernel (variant 0 | 2, counter width)
+  int blue_occ[2][7] = {};   // resident blocks per SM of the W = 32 blue kernel (variant 0 | 2, 3 .. 9 counter planes)
   int sweep_min_blocks_per_sm = 4;
 
   // host tables (FP64, built once)

@@ -806,11 +806,12 @@ __device__ __forceinline__ void block_sum_counters(const VCount<Word, K> *cnt, W
 
 // Body of the pass for (virtual) block bid of sweep t; CG: read the spins
 // through L2 only (a persistent launch, where other blocks wrote them).
-template <bool BLUE, int G2, bool PF, bool CG>
+// KS: counter planes of a thread's u_s sum (at most 4 G, so KS =
+// counter_planes(G)); the u_t sum (at most 2 G) takes one plane less.
+template <bool BLUE, int KS, bool PF, bool CG>
 __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, const SlotThresholds &th, uint32_t bid,
                                             unsigned long long t, int colour, int count_only) {
-  constexpr int KS = G2 + 5;   // u_s sum <= 4 G per replica and thread
-  constexpr int KT = G2 + 4;   // u_t sum <= 2 G
+  constexpr int KT = KS - 1;
   constexpr int KF = KS + kLog2Block4;
   __shared__ uint32_t buf[BLUE ? 4 * KF * kBlock4 : 1];
   __shared__ int tot[BLUE ? 2 * 4 * 32 : 1];
@@ -961,7 +962,7 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
 }
 
 
-template <bool BLUE, int G2, bool PF, int MINB = 0>
+template <bool BLUE, int KS, bool PF, int MINB = 0>
 __global__ void __launch_bounds__(kBlock4, MINB) samples_sweep4_kernel(SamplesArgs<uint32_t> p,
                                                                   const __grid_constant__ SlotThresholds th,
                                                                   int colour, int count_only) {
@@ -974,7 +975,7 @@ __global__ void __launch_bounds__(kBlock4, MINB) samples_sweep4_kernel(SamplesAr
   }
   const unsigned long long t = *p.d_t;
   if (p.t_copy && blockIdx.x == 0 && threadIdx.x == 0) *p.t_copy = t;
-  sweep4_body<BLUE, G2, PF, false>(p, th, blockIdx.x, t, colour, count_only);
+  sweep4_body<BLUE, KS, PF, false>(p, th, blockIdx.x, t, colour, count_only);
 }
 
 
@@ -1342,7 +1343,7 @@ struct PersistArgs {
   long long wait_ns;
 };
 
-template <int RP, int G2>
+template <int RP, int KS>
 __global__ void __launch_bounds__(kBlock4, 3) samples_persistent_kernel(const PersistArgs a,
                                                                       const __grid_constant__ SlotThresholds th) {
   const unsigned long long t0 = __ldcg(a.d_t);
@@ -1365,7 +1366,7 @@ __global__ void __launch_bounds__(kBlock4, 3) samples_persistent_kernel(const Pe
     SamplesArgs<uint32_t> bp = a.blue;
     bp.spins = a.buf[cur ^ 1];
     for (int vb = blockIdx.x; vb < a.blue_blocks; vb += gridDim.x)
-      sweep4_body<true, G2, true, true>(bp, th, vb, t, 1, 0);
+      sweep4_body<true, KS, true, true>(bp, th, vb, t, 1, 0);
     if (!grid_barrier(a.bar, a.err, a.wait_ns)) return;
     for (int64_t c = gwarp; c < n_chains; c += warps) {   // whole warps: c is uniform over the warp
       const int64_t sa = c / a.n_rep;
@@ -1437,6 +1438,14 @@ SamplesArgs<Word> make_args(qisg_handle *h, int colour) {
   return p;
 }
 
+// Bit planes that hold a sum of at most 4 G per lane (the u_s counter of a
+// walk of G sites; the u_t counter takes one less), at least 3.
+int counter_planes(int G) {
+  int k = 0;
+  while ((4 * G) >> k) ++k;
+  return std::max(k, 3);
+}
+
 template <typename Word, bool BLUE, int G2>
 void launch_sweep(bool pdl, const SamplesArgs<Word> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
                   int colour, int count_only) {
@@ -1475,19 +1484,19 @@ void fill_thresholds(const qisg_handle *h, SlotThresholds &th) {
     }
 }
 
-// Blocks of the W = 32 blue kernel (variant 0 or 2, counter planes for walks
-// of up to 4 << g2 sites) resident on one SM, cached in the handle.
-int blue_blocks_per_sm(qisg_handle *h, int g2, int variant) {
+// Blocks of the W = 32 blue kernel (variant 0 or 2, ks = 3 .. 9 counter
+// planes) resident on one SM, cached in the handle.
+int blue_blocks_per_sm(qisg_handle *h, int ks, int variant) {
   const int v = variant == 2 ? 1 : 0;
-  g2 = std::min(std::max(g2, 0), 5);
-  int &c = h->blue_occ[v][g2];
+  ks = std::min(std::max(ks, 3), 9);
+  int &c = h->blue_occ[v][ks - 3];
   if (c > 0) return c;
   const void *fn = nullptr;
 #define QISG_OCC(n)                                                                                   \
   case n:                                                                                             \
     fn = v ? (const void *)samples_sweep4_kernel<true, n, false, 4> : (const void *)samples_sweep4_kernel<true, n, true>; \
     break;
-  switch (g2) { QISG_OCC(0) QISG_OCC(1) QISG_OCC(2) QISG_OCC(3) QISG_OCC(4) default: QISG_OCC(5) }
+  switch (ks) { QISG_OCC(3) QISG_OCC(4) QISG_OCC(5) QISG_OCC(6) QISG_OCC(7) QISG_OCC(8) default: QISG_OCC(9) }
 #undef QISG_OCC
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock4, 0) != cudaSuccess || per_sm < 1) {
@@ -1513,8 +1522,7 @@ int64_t blocks_per_set4(int plane, int n_seg) {
 // block's counter tree (about 32 instructions per counter plane level),
 // with walks of at most max_walk sites.  Counts that leave segments of
 // unequal length are candidates only when a block holds one segment.
-// resident(g2) gives the resident blocks for counter planes of walks up to
-// 4 << g2 sites.
+// resident(ks) gives the resident blocks for ks counter planes.
 template <typename Resident>
 int wave_fill_segments(int64_t sets, int plane, int half_col, int max_walk, Resident resident) {
   int best = half_col;
@@ -1522,12 +1530,11 @@ int wave_fill_segments(int64_t sets, int plane, int half_col, int max_walk, Resi
   for (int ns = std::max(1, (half_col + max_walk - 1) / max_walk); ns <= half_col; ++ns) {
     if (plane % kBlock4 != 0 && half_col % ns != 0) continue;
     const int gmax = (half_col + ns - 1) / ns;
-    int g2 = 0;
-    while ((4 << g2) < gmax) ++g2;
-    const int64_t R = std::max<int64_t>(1, resident(g2));
+    const int ks = counter_planes(gmax);
+    const int64_t R = std::max<int64_t>(1, resident(ks));
     const int64_t blocks = sets * blocks_per_set4(plane, ns);
     const int64_t waves = (blocks + R - 1) / R;
-    const double cost = (double)waves * (490.0 * gmax + 32.0 * (2 * g2 + 23));
+    const double cost = (double)waves * (490.0 * gmax + 32.0 * (2 * ks + 13));
     if (best_cost < 0.0 || cost < best_cost) {
       best_cost = cost;
       best = ns;
@@ -1559,8 +1566,8 @@ SamplesArgs<uint32_t> make_args4(qisg_handle *h, int colour, SlotThresholds &th,
     n_seg = half_col / G;
   } else if (colour == 1) {
     const int variant = h->sweep_variant[1];
-    n_seg = wave_fill_segments(sets, p.plane, half_col, max_walk, [&](int g2) -> int64_t {
-      return resident_blocks > 0 ? resident_blocks : (int64_t)blue_blocks_per_sm(h, g2, variant) * std::max(1, h->n_sm);
+    n_seg = wave_fill_segments(sets, p.plane, half_col, max_walk, [&](int ks) -> int64_t {
+      return resident_blocks > 0 ? resident_blocks : (int64_t)blue_blocks_per_sm(h, ks, variant) * std::max(1, h->n_sm);
     });
   } else {
     const int64_t want_threads = (int64_t)h->sweep_min_blocks_per_sm * std::max(1, h->n_sm) * kBlock / 2;
@@ -1588,20 +1595,18 @@ template <bool BLUE, bool PF, int MINB = 0>
 void launch_sweep4(bool pdl, const SamplesArgs<uint32_t> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
                    int colour, int count_only) {
   if constexpr (!BLUE) {   // the red pass keeps no counters
-    launch_kernel(pdl, samples_sweep4_kernel<false, 0, PF>, dim3(blocks), dim3(kBlock4), 0, st, p, th, colour,
+    launch_kernel(pdl, samples_sweep4_kernel<false, 3, PF>, dim3(blocks), dim3(kBlock4), 0, st, p, th, colour,
                   count_only);
   } else {
-    int g2 = 0;
-    while ((4 << g2) < p.seg_sites) ++g2;
-    switch (g2) {
+    switch (counter_planes(p.seg_sites)) {   // walks of at most 64 sites: 3 .. 9 planes
 #define QISG_CASE(n)                                                                                         \
   case n:                                                                                                    \
     launch_kernel(pdl, samples_sweep4_kernel<true, n, PF, MINB>, dim3(blocks), dim3(kBlock4), 0, st, p, th,  \
                   colour, count_only);                                                                       \
     break;
-      QISG_CASE(0) QISG_CASE(1) QISG_CASE(2) QISG_CASE(3) QISG_CASE(4)
+      QISG_CASE(3) QISG_CASE(4) QISG_CASE(5) QISG_CASE(6) QISG_CASE(7) QISG_CASE(8)
       default:
-        launch_kernel(pdl, samples_sweep4_kernel<true, 5, PF, MINB>, dim3(blocks), dim3(kBlock4), 0, st, p, th,
+        launch_kernel(pdl, samples_sweep4_kernel<true, 9, PF, MINB>, dim3(blocks), dim3(kBlock4), 0, st, p, th,
                       colour, count_only);
         break;
 #undef QISG_CASE
@@ -2007,7 +2012,7 @@ int samples_persistent(qisg_handle *h, int n_sweeps) {
   // form of the kernel is bounded to the same residency), walks of at most
   // 32 sites
   int per_sm0 = 0;
-  rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm0, samples_persistent_kernel<1, 0>, kBlock4, 0),
+  rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm0, samples_persistent_kernel<1, 5>, kBlock4, 0),
                   "occupancy");
   if (rc) return rc;
   a.blue = make_args4(h, 1, th_blue, (int64_t)std::max(1, per_sm0) * std::max(1, h->n_sm), 32);
@@ -2016,9 +2021,8 @@ int samples_persistent(qisg_handle *h, int n_sweeps) {
   a.blue.t_copy = nullptr;
   const int64_t blue_blocks = h->n_b * h->n_slots * h->n_q * a.blue.blocks_per_set;
   if (blue_blocks > 0x7FFFFFFF) return fail(QISG_EINVAL, "lattice too large for one launch");
-  int g2 = 0;
-  while ((4 << g2) < a.blue.seg_sites) ++g2;
-  if (g2 > 3) return fail(QISG_EINVAL, "persistent form: blue tile above 32 sites");
+  const int ks = counter_planes(a.blue.seg_sites);
+  if (a.blue.seg_sites > 32) return fail(QISG_EINVAL, "persistent form: blue tile above 32 sites");
   a.buf[0] = reinterpret_cast<uint32_t *>(h->spins);
   a.buf[1] = reinterpret_cast<uint32_t *>(h->spins_alt);
   a.red_blocks = (int)red_blocks;
@@ -2041,10 +2045,11 @@ int samples_persistent(qisg_handle *h, int n_sweeps) {
   a.wait_ns = h->wait_ns;
   const int rp = tpsite == 4 ? 1 : tpsite == 2 ? 2 : 4;
   const void *fn = nullptr;
-#define QISG_PK(R, G) \
-  if (rp == R && g2 == G) fn = (const void *)samples_persistent_kernel<R, G>;
-  QISG_PK(1, 0) QISG_PK(1, 1) QISG_PK(1, 2) QISG_PK(1, 3) QISG_PK(2, 0) QISG_PK(2, 1) QISG_PK(2, 2) QISG_PK(2, 3)
-  QISG_PK(4, 0) QISG_PK(4, 1) QISG_PK(4, 2) QISG_PK(4, 3)
+#define QISG_PK(R, K) \
+  if (rp == R && ks == K) fn = (const void *)samples_persistent_kernel<R, K>;
+  QISG_PK(1, 3) QISG_PK(1, 4) QISG_PK(1, 5) QISG_PK(1, 6) QISG_PK(1, 7) QISG_PK(1, 8)
+  QISG_PK(2, 3) QISG_PK(2, 4) QISG_PK(2, 5) QISG_PK(2, 6) QISG_PK(2, 7) QISG_PK(2, 8)
+  QISG_PK(4, 3) QISG_PK(4, 4) QISG_PK(4, 5) QISG_PK(4, 6) QISG_PK(4, 7) QISG_PK(4, 8)
 #undef QISG_PK
   int per_sm = 0;
   rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock4, 0), "occupancy");

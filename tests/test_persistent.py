@@ -125,3 +125,36 @@ def test_persistent_full_size_sampled(qisg):
             states = list(ex.map(replay, picks))
         for s, st in zip(picks, states):
             assert_same_state(inst, st, a_lo=s, what=f"sample {s}")
+
+
+def test_persistent_production_shape_default_schedule(qisg):
+    """The 32-sample L=16, L_tau=256 workload (4 replicas x 16 slots) in the
+    persistent form on the default schedule (walks of unequal length filling
+    the persistent grid) and with the blue variant bounded to four blocks
+    per SM, 20 sweeps with measurements every 10: samples 0 and 17 replayed
+    by the oracle, and the whole state equal to the per-pass launches."""
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2402_03920_gb300.workloads import PRODUCTION as w
+    kw = dict(layout=qisg.QISG_LAYOUT_SAMPLES, word_bits=32, measure_every=w.measure_every)
+    a, ladder = make(qisg, w.L, w.L_tau, w.k_lo, w.k_hi, w.n_slots, w.gamma, w.n_replicas, w.n_samples,
+                     w.seed, **kw)
+    b, _ = make(qisg, w.L, w.L_tau, w.k_lo, w.k_hi, w.n_slots, w.gamma, w.n_replicas, w.n_samples,
+                w.seed, **kw)
+
+    def replay(s):
+        st = oracle_state(ladder, w.L, w.L_tau, w.n_replicas, w.seed, s, 1)
+        return oracle.run(st, 20, measure_every=w.measure_every, n_threads=1)
+
+    with a, b:
+        a.set_persistent(True)
+        a.sweep(20)
+        b.set_tiles((2, 0), (0, 2))
+        b.sweep(20)
+        with ThreadPoolExecutor(max_workers=2) as ex:
+            states = list(ex.map(replay, (0, 17)))
+        for s, st in zip((0, 17), states):
+            assert_same_state(a, st, a_lo=s, what=f"sample {s}")
+        assert np.array_equal(a.spins(), b.spins())
+        assert np.array_equal(a.permutation(), b.permutation())
+        for x, y in zip(a.measurements(), b.measurements()):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
