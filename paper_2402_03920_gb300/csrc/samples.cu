@@ -884,6 +884,9 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
     // the draws of the walk's next site are made while this one is updated,
     // so the Philox chain overlaps independent work
     uint4 R4 = philox(make_uint4((uint32_t)i2 + off, (uint32_t)t, ctr_z, ctr_w), p.key);
+    // two steps per iteration, so the current and next sites' words swap
+    // registers instead of being copied
+#pragma unroll 2
     for (int k = 0; k < G; ++k) {
       const uint32_t tau = tau0 + 2u * (uint32_t)k;
       uint4 R4n = R4;
