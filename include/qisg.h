@@ -395,6 +395,20 @@ int qisg_set_graphs(qisg_handle *h, int enable);
  * measurement launches.  Results are the same either way.  Synchronises. */
 int qisg_set_launch_overlap(qisg_handle *h, int enable);
 
+/* SAMPLES packing with 32-bit words: run each sweep's PT pass (Sec. 2.1) in
+ * the last blocks of the blue pass instead of a launch of its own (enable =
+ * 1, the default).  Each block of the blue pass takes a ticket once its bond
+ * counts are added; the last P = ceil(n_samples * n_rep / 4) blocks wait
+ * until every block has, then decide the chains as the PT pass does, a warp
+ * per chain.  Used when P is at most half the blue pass's blocks and half
+ * its resident blocks, 2N < 2^30 and n_slots <= 32; otherwise the PT pass
+ * has its own launch.  The wait is bounded by wait_ns nanoseconds (0: the
+ * default, 5 s; the bound is shared with qisg_set_persistent's barriers): a
+ * wait that runs out ends the pass without PT and the next synchronising
+ * call returns ETIMEOUT (the handle's state is then undefined: destroy it).
+ * Results are the same either way.  EINVAL: wait_ns < 0.  Synchronises. */
+int qisg_set_pt_in_blue(qisg_handle *h, int enable, int64_t wait_ns);
+
 /* The persistent form of the batched sweep (SAMPLES packing, 32-bit words,
  * PT every sweep; Sec. 2.1's red / blue / PT cycle): enable = 1 runs every
  * stretch of sweeps up to the next measurement (or 64 sweeps when nothing

@@ -356,7 +356,8 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc && h->blk_len) rc = dalloc(h, &h->d_blkB, (size_t)h->blk_len * n_rows * 8);
   if (!rc && layout == QISG_LAYOUT_SAMPLES)
     rc = dalloc(h, &h->d_acc, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8));
-  if (!rc && layout == QISG_LAYOUT_SAMPLES) rc = dalloc(h, &h->d_bar, 2 * sizeof(unsigned));
+  // the persistent kernel's grid barrier (two words) and the blue pass's PT ticket
+  if (!rc && layout == QISG_LAYOUT_SAMPLES) rc = dalloc(h, &h->d_bar, 3 * sizeof(unsigned));
   if (!rc && layout == QISG_LAYOUT_SITES) rc = dalloc(h, &h->d_dcum, (size_t)n_slots * 256 * 8);
   if (!rc && layout == QISG_LAYOUT_SITES) rc = dalloc(h, &h->d_dlut, ((size_t)n_slots << kDaemonLutBits) * 9);
   if (rc) {
@@ -394,6 +395,7 @@ int qisg_create(qisg_handle **out, int L, int L_tau, const qisg_slot *ladder, in
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_t, 0, 16, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_err, 0, 4, h->stream), "memset");
   if (!rc) rc = cuda_check(cudaMemsetAsync(h->d_meas, 0, 8, h->stream), "memset");
+  if (!rc && h->d_bar) rc = cuda_check(cudaMemsetAsync(h->d_bar, 0, 3 * sizeof(unsigned), h->stream), "memset");
   if (!rc && h->d_acc)
     rc = cuda_check(cudaMemsetAsync(h->d_acc, 0, (size_t)h->n_b * n_replicas * n_slots * (h->W / 8), h->stream),
                     "memset");
@@ -664,6 +666,16 @@ int qisg_set_launch_overlap(qisg_handle *h, int enable) {
   int rc = sync_handle(h);
   if (rc) return rc;
   h->pdl = enable != 0;
+  drop_cycle(h);
+  return QISG_OK;
+}
+
+int qisg_set_pt_in_blue(qisg_handle *h, int enable, int64_t wait_ns) {
+  if (!h || wait_ns < 0) return fail(QISG_EINVAL, "bad handle or wait_ns < 0");
+  int rc = sync_handle(h);
+  if (rc) return rc;
+  h->pt_in_blue = enable != 0;
+  h->wait_ns = wait_ns > 0 ? wait_ns : 5000000000ll;
   drop_cycle(h);
   return QISG_OK;
 }

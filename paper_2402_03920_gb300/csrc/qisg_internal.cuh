@@ -546,6 +546,10 @@ struct qisg_handle {
   // after every red pass); perm_pending: the stored lattice still lacks the
   // exchanges of the last PT pass (its masks are in d_acc)
   bool fused = false;
+  // fused mode, 32-bit words: the PT pass runs in the blue pass's last blocks
+  // when eligible (pt_folded: it did for the current sweep)
+  bool pt_in_blue = true;
+  bool pt_folded = false;
   void *spins_alt = nullptr;
   bool perm_pending = false;
   void *J = nullptr;

@@ -371,6 +371,7 @@ struct FusedRedArgsT {
   int64_t N;
   int L, Lt, plane, n_slots, n_q, n_rep, blocks_per_set;
   uint32_t one;
+  unsigned *ticket;   // the blue pass's PT ticket counter, reset here (or null)
   int tau_ap;
   FastDiv fd_bps, fd_nq, fd_plane, fd_L;
 };
@@ -390,6 +391,7 @@ __global__ void __launch_bounds__(kBlock4, 7) samples_red_fused_kernel(const Fus
   {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
+    if (p.ticket && blockIdx.x == 0 && threadIdx.x == 0) *p.ticket = 0u;
   }
   for (int i = threadIdx.x; i < 4 * kMaxSlotsPT; i += blockDim.x) {
     const int jj = i / kMaxSlotsPT, sl = i - jj * kMaxSlotsPT;
@@ -760,6 +762,7 @@ __global__ void __launch_bounds__(kBlock4) samples_red_fusedq_kernel(const Fused
   {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
+    if (p.ticket && blockIdx.x == 0 && threadIdx.x == 0) *p.ticket = 0u;
   }
   red_fusedq_body<Word, RP, false>(p, th, blockIdx.x, *p.d_t);
 }
@@ -884,9 +887,11 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
     // the draws of the walk's next site are made while this one is updated,
     // so the Philox chain overlaps independent work
     uint4 R4 = philox(make_uint4((uint32_t)i2 + off, (uint32_t)t, ctr_z, ctr_w), p.key);
-    // two steps per iteration, so the current and next sites' words swap
-    // registers instead of being copied
-#pragma unroll 2
+    // with the prefetch, two steps per iteration, so the current and next
+    // sites' words swap registers instead of being copied (not in the
+    // persistent kernel, whose register bound would make the unrolled walk
+    // spill)
+#pragma unroll((PF && !CG) ? 2 : 1)
     for (int k = 0; k < G; ++k) {
       const uint32_t tau = tau0 + 2u * (uint32_t)k;
       uint4 R4n = R4;
@@ -965,10 +970,79 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
 }
 
 
+// The PT pass in the blue pass's last blocks (fused mode, 32-bit words; Sec.
+// 2.1's PT update after the sweep).  Instead of a separate PT launch, each
+// block of the blue pass takes a ticket once its bond counts are added; the
+// last P blocks to take one wait (bounded by wait_ns, error flag on expiry)
+// until every block has, then run the chains of the sweep, a warp per chain,
+// exactly as the PT kernel does, and the block with the last ticket advances
+// the sweep counter.  Only the last P blocks wait, so the blocks not yet
+// started always find room on the SMs (P is at most half the grid and half
+// the resident blocks).
+struct PTFold {
+  int P;                         // PT blocks of this launch (0: no PT here)
+  unsigned *ticket;              // blocks done; the red pass resets it
+  int32_t *walker;
+  unsigned long long *U;
+  uint32_t *acc;
+  const PTConst *ptc;
+  const double *sq;
+  unsigned long long *d_t;
+  int *err;
+  long long wait_ns;
+  int64_t n_samples;
+  int n_rep, n_slots;
+};
+
+__device__ __forceinline__ void pt_in_blue_tail(const PTFold &f, uint2 key, unsigned long long t) {
+  __shared__ unsigned s_tk;
+  __shared__ int s_go;
+  __syncthreads();   // every bond-count atomic of this block is issued
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_tk = atomicAdd(f.ticket, 1u);
+  }
+  __syncthreads();
+  const unsigned nb = gridDim.x, tk = s_tk;
+  if (tk + (unsigned)f.P < nb) return;   // not among the last P blocks
+  if (threadIdx.x == 0) {
+    int go = 1;
+    const unsigned long long t0 = gtime();
+    while (*(volatile unsigned *)f.ticket < nb) {
+      if (*(volatile int *)f.err) {
+        go = 0;
+        break;
+      }
+      if (gtime() - t0 > (unsigned long long)f.wait_ns) {
+        atomicExch(f.err, 1);
+        go = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_go = go;
+  }
+  __syncthreads();
+  if (!s_go) return;
+  constexpr int kWarps = kBlock4 / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n_chains = f.n_samples * f.n_rep;
+  for (int64_t c = (int64_t)(tk - (nb - (unsigned)f.P)) * kWarps + warp; c < n_chains; c += (int64_t)f.P * kWarps) {
+    const int64_t sa = c / f.n_rep;   // c is uniform over the warp
+    const int r = (int)(c - sa * f.n_rep);
+    const uint32_t acc = pt_chain<true, true, false>(f.walker + c * f.n_slots, f.U + c * f.n_slots * 2, f.ptc, f.sq,
+                                                     key, (uint32_t)t, sa, r, f.n_slots);
+    if (lane + 1 < f.n_slots && ((acc >> lane) & 1u))
+      atomicOr(f.acc + ((sa >> 5) * f.n_rep + r) * f.n_slots + lane, 1u << (sa & 31));
+  }
+  if (tk == nb - 1 && threadIdx.x == 0) *f.d_t = t + 1;   // every block read t at its start
+}
+
 template <bool BLUE, int KS, bool PF, int MINB = 0>
 __global__ void __launch_bounds__(kBlock4, MINB) samples_sweep4_kernel(SamplesArgs<uint32_t> p,
                                                                   const __grid_constant__ SlotThresholds th,
-                                                                  int colour, int count_only) {
+                                                                  int colour, int count_only, const PTFold f) {
   pdl_begin();
   {   // counters / masks the host asked this pass to clear (nothing reads them before the next pass)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -979,6 +1053,7 @@ __global__ void __launch_bounds__(kBlock4, MINB) samples_sweep4_kernel(SamplesAr
   const unsigned long long t = *p.d_t;
   if (p.t_copy && blockIdx.x == 0 && threadIdx.x == 0) *p.t_copy = t;
   sweep4_body<BLUE, KS, PF, false>(p, th, blockIdx.x, t, colour, count_only);
+  if (BLUE && f.P > 0) pt_in_blue_tail(f, p.key, t);
 }
 
 
@@ -1596,21 +1671,21 @@ SamplesArgs<uint32_t> make_args4(qisg_handle *h, int colour, SlotThresholds &th,
 // SM (variant 2 of the blue pass: more resident warps, no prefetch).
 template <bool BLUE, bool PF, int MINB = 0>
 void launch_sweep4(bool pdl, const SamplesArgs<uint32_t> &p, const SlotThresholds &th, unsigned blocks, cudaStream_t st,
-                   int colour, int count_only) {
+                   int colour, int count_only, const PTFold &f = PTFold{}) {
   if constexpr (!BLUE) {   // the red pass keeps no counters
     launch_kernel(pdl, samples_sweep4_kernel<false, 3, PF>, dim3(blocks), dim3(kBlock4), 0, st, p, th, colour,
-                  count_only);
+                  count_only, f);
   } else {
     switch (counter_planes(p.seg_sites)) {   // walks of at most 64 sites: 3 .. 9 planes
 #define QISG_CASE(n)                                                                                         \
   case n:                                                                                                    \
     launch_kernel(pdl, samples_sweep4_kernel<true, n, PF, MINB>, dim3(blocks), dim3(kBlock4), 0, st, p, th,  \
-                  colour, count_only);                                                                       \
+                  colour, count_only, f);                                                                    \
     break;
       QISG_CASE(3) QISG_CASE(4) QISG_CASE(5) QISG_CASE(6) QISG_CASE(7) QISG_CASE(8)
       default:
         launch_kernel(pdl, samples_sweep4_kernel<true, 9, PF, MINB>, dim3(blocks), dim3(kBlock4), 0, st, p, th,
-                      colour, count_only);
+                      colour, count_only, f);
         break;
 #undef QISG_CASE
     }
@@ -1642,6 +1717,7 @@ int make_red_args(qisg_handle *h, SlotThresholds &th, FusedRedArgsT<Word> &p, in
   p.n_rep = h->n_rep;
   p.one = 1u;
   p.tau_ap = h->tau_ap;
+  p.ticket = h->d_bar ? h->d_bar + 2 : nullptr;
   if (h->sweep_tile[0] == 0) {
     // default: a thread per site and replica unless one thread per site
     // already gives a few waves of full SMs (2048 threads each)
@@ -1713,14 +1789,43 @@ int half_sweep_t(qisg_handle *h, int colour, int count_only) {
     const int64_t blocks = h->n_b * h->n_slots * h->n_q * p.blocks_per_set;
     if (blocks > 0x7FFFFFFF || (int64_t)p.blocks_per_set * kBlock4 > 0x7FFFFFFF)
       return fail(QISG_EINVAL, "lattice too large for one launch");
+    // the PT pass of this sweep in the blue pass's last blocks, when the
+    // chains fit a warp each in at most half the grid and half the resident
+    // blocks, energy differences fit 32 bits and the sweep's PT is due
+    PTFold f{};
+    h->pt_folded = false;
+    if (colour == 1 && h->fused && !count_only && h->pt_in_blue && h->pt_every > 0 &&
+        (h->t + 1) % (uint64_t)h->pt_every == 0 && 2 * h->N < (int64_t(1) << 30) && h->n_slots <= kMaxSlotsPT) {
+      const int64_t chains = h->n_samples * h->n_rep;
+      const int64_t P = (chains + kBlock4 / 32 - 1) / (kBlock4 / 32);
+      const int64_t resident = (int64_t)blue_blocks_per_sm(h, counter_planes(p.seg_sites), h->sweep_variant[1]) *
+                               std::max(1, h->n_sm);
+      if (P >= 1 && 2 * P <= blocks && 2 * P <= resident) {
+        f.P = (int)P;
+        f.ticket = h->d_bar + 2;
+        f.walker = h->d_walker;
+        f.U = h->d_U;
+        f.acc = reinterpret_cast<uint32_t *>(h->d_acc);
+        f.ptc = reinterpret_cast<const PTConst *>(h->d_ptc);
+        f.sq = h->d_sq;
+        f.d_t = h->d_t;
+        f.err = h->d_err;
+        f.wait_ns = h->wait_ns;
+        f.n_samples = h->n_samples;
+        f.n_rep = h->n_rep;
+        f.n_slots = h->n_slots;
+        p.t_copy = nullptr;
+        h->pt_folded = true;
+      }
+    }
     const int tok = prof_begin(h, sweep_kind(colour));
     // the blue pass loads the next site of its walk while it updates the
     // current one (measured: 4% off the production sweep, with the tuner then
     // taking walks of 4 sites)
     if (colour == 1 && h->sweep_variant[1] == 2)
-      launch_sweep4<true, false, 4>(h->pdl, p, th, (unsigned)blocks, h->stream, 1, count_only);
+      launch_sweep4<true, false, 4>(h->pdl, p, th, (unsigned)blocks, h->stream, 1, count_only, f);
     else if (colour == 1)
-      launch_sweep4<true, true>(h->pdl, p, th, (unsigned)blocks, h->stream, 1, count_only);
+      launch_sweep4<true, true>(h->pdl, p, th, (unsigned)blocks, h->stream, 1, count_only, f);
     else
       launch_sweep4<false, false>(h->pdl, p, th, (unsigned)blocks, h->stream, 0, count_only);
     prof_end(h, sweep_kind(colour), tok);
@@ -1773,7 +1878,10 @@ int pt_t(qisg_handle *h, int explicit_pass, int advance) {
   }
   if (rc) return rc;
   if (h->fused && !explicit_pass) {
-    rc = pt_pass(h, 0, 0, h->n_samples, advance ? h->d_t : nullptr);
+    // the blue pass of this sweep ran the PT chains in its last blocks and
+    // advanced the counter
+    if (!h->pt_folded) rc = pt_pass(h, 0, 0, h->n_samples, advance ? h->d_t : nullptr);
+    h->pt_folded = false;
     if (!rc) h->perm_pending = true;
     return rc;
   }

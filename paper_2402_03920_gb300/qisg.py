@@ -93,6 +93,7 @@ def load(build_if_missing: bool = True):
         "qisg_set_graphs": (I, [P, I]),
         "qisg_set_persistent": (I, [P, I, I64]),
         "qisg_set_launch_overlap": (I, [P, I]),
+        "qisg_set_pt_in_blue": (I, [P, I, I64]),
         "qisg_autotune": (I, [P, I, P]),
         "qisg_get_tiles": (I, [P, P, P]),
         "qisg_set_tiles": (I, [P, P, P]),
@@ -406,6 +407,10 @@ class Instance:
     def set_launch_overlap(self, enable: bool):
         """Programmatic dependent launch of the SAMPLES sweep kernels."""
         _check(load().qisg_set_launch_overlap(self._h, 1 if enable else 0))
+
+    def set_pt_in_blue(self, enable: bool, wait_ns: int = 0):
+        """Run each sweep's PT pass in the blue pass's last blocks (the default)."""
+        _check(load().qisg_set_pt_in_blue(self._h, 1 if enable else 0, wait_ns))
 
     def set_persistent(self, enable: bool, wait_ns: int = 0):
         """One cooperative launch per run of sweeps (SAMPLES, 32-bit words)."""

@@ -340,3 +340,53 @@ def test_launch_overlap_keeps_trajectory(qisg, W):
         assert np.array_equal(a.spins(), b.spins()) and np.array_equal(a.permutation(), b.permutation())
         for x, y in zip(a.measurements(), b.measurements()):
             assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_pt_in_blue_pass_equals_pt_launch_and_oracle(qisg, variant):
+    """The PT pass run in the blue pass's last blocks (8 samples x 4
+    replicas = 32 chains, 8 waiting blocks) against the PT pass of its own
+    launch and the oracle, with measurements every 3 sweeps."""
+    L, Lt, n_slots, n_rep, n_samples = 16, 32, 6, 4, 8
+    kw = dict(word_bits=32, layout=qisg.QISG_LAYOUT_SAMPLES, measure_every=3)
+    a, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 0.9, n_rep, n_samples, 41, **kw)
+    b, _ = make(qisg, L, Lt, 0.2, 0.5, n_slots, 0.9, n_rep, n_samples, 41, **kw)
+    st = oracle_state(ladder, L, Lt, n_rep, 41, 0, n_samples)
+    with a, b:
+        a.set_tiles((0, 0), (0, variant))
+        b.set_tiles((0, 0), (0, variant))
+        a.set_pt_in_blue(True)
+        b.set_pt_in_blue(False)
+        for n in (1, 5, 14):
+            a.sweep(n)
+            b.sweep(n)
+            oracle.run(st, n, pt_every=1, measure_every=3)
+            assert_same_state(a, st, what=f"in blue, after {st.t}")
+            assert np.array_equal(a.spins(), b.spins())
+            assert np.array_equal(a.permutation(), b.permutation())
+        for x, y in zip(a.measurements(), b.measurements()):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+        assert a.launch_count() < b.launch_count()   # no PT launches in a
+
+
+def test_pt_in_blue_pass_wait_bound():
+    """A 1 ns bound on the waiting blocks: the pass either completes (the
+    state equal to the PT launch's) or reports ETIMEOUT; it never hangs."""
+    need_gpu()
+    from paper_2402_03920_gb300 import qisg
+    qisg.load()
+    kw = dict(word_bits=32, layout=qisg.QISG_LAYOUT_SAMPLES, measure_every=0)
+    a, _ = make(qisg, 16, 64, 0.2, 0.5, 8, 0.9, 4, 8, 43, **kw)
+    b, _ = make(qisg, 16, 64, 0.2, 0.5, 8, 0.9, 4, 8, 43, **kw)
+    with a, b:
+        a.set_pt_in_blue(True, wait_ns=1)
+        b.set_pt_in_blue(False)
+        b.sweep(20)
+        try:
+            a.sweep(20)
+            a.sync()
+        except qisg.QisgError as e:
+            assert e.code == -4   # QISG_ETIMEOUT
+        else:
+            assert np.array_equal(a.spins(), b.spins())
+            assert np.array_equal(a.permutation(), b.permutation())
