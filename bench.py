@@ -234,10 +234,15 @@ def time_form(torch, qisg, w, form, steps, warmup, seed):
     launches0 = inst.launch_count()
     total_ms = timed_steps(torch, inst, flush, steps)
     launches = inst.launch_count() - launches0
+    # the share pass runs the PT pass as a launch of its own, so each kernel
+    # kind gets its own share (the timed steps run it in the blue pass's last
+    # blocks)
+    inst.set_pt_in_blue(False)
     inst.profile(True)
     pass_ms = timed_steps(torch, inst, flush, steps)
     kern = read_profile(inst, [k for k, _ in KINDS])
     inst.profile(False)
+    inst.set_pt_in_blue(True)
     kern["pass_ms_per_step"] = pass_ms / steps
     layout, wb = inst.layout()
     inst.close()
@@ -482,10 +487,12 @@ def large_batched_entry(torch, qisg, sweeps=20, persistent_sweeps=2000):
             inst.sweep(2)
             inst.sync()
             ms = timed(inst, sweeps)                  # plain: the value
+            inst.set_pt_in_blue(False)                # shares: PT as a launch of its own,
             inst.profile(True)
-            timed(inst, sweeps)                       # shares (event pairs on every launch)
+            timed(inst, sweeps)                       # event pairs on every launch
             kern = read_profile(inst, [k for k, _ in KINDS])
             inst.profile(False)
+            inst.set_pt_in_blue(True)
             tiles = inst.tiles()
             layout, _ = inst.layout()
         rl, rl_all = roofline(kern, ups_per_sweep, f"samples{wb}", n_sm, pk, sweeps, ms / sweeps,
@@ -711,7 +718,8 @@ def cpu_baseline(w, budget_s=15.0):
 
 def kernel_timing(kern, steps):
     return {"how": "second pass of the same steps with event pairs around every launch (pairs serialise "
-                   "the graph); only the shares of its device time are used",
+                   "the graph; the PT pass has its own launch there, while the timed steps run it in the "
+                   "blue pass's last blocks); only the shares of its device time are used",
             "share": kernel_shares(kern),
             "pair_us_per_launch": {k: kern[k]["us_per_launch"] for k, _ in KINDS},
             "launches_per_step": {k: kern[k]["launched"] / steps for k, _ in KINDS},
