@@ -933,9 +933,17 @@ int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, ui
     }
   }
   const int64_t nS = rows * h->n_slots * h->N;
-  if (!spins_are_pm1(S, nS)) return fail(QISG_ECORRUPT, "spins must be +-1");
   int rc = sync_handle(h);
   if (rc) return rc;
+  // SAMPLES states up to 256 MB go up in one copy and are checked on the
+  // device before anything of the handle changes; others are checked here
+  int8_t *d_S = nullptr;
+  if (h->layout == QISG_LAYOUT_SAMPLES && nS <= ((int64_t)256 << 20)) {
+    rc = samples_upload_checked(h, S, nS, &d_S);
+    if (rc) return rc;
+  } else if (!spins_are_pm1(S, nS)) {
+    return fail(QISG_ECORRUPT, "spins must be +-1");
+  }
   // the permutation first (padding lanes keep the identity): SAMPLES packs by
   // slot with the device labels
   std::vector<int32_t> wa((size_t)h->n_a_pad * h->n_rep * h->n_slots);
@@ -943,10 +951,11 @@ int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, ui
   std::memcpy(wa.data(), walker_at, (size_t)rows * h->n_slots * 4);
   rc = cuda_check(cudaMemcpyAsync(h->d_walker, wa.data(), wa.size() * 4, cudaMemcpyHostToDevice, h->stream),
                   "copy walker");
-  if (rc) return rc;
-  rc = h->layout == QISG_LAYOUT_LANES   ? lanes_set_spins(h, S)
-       : h->layout == QISG_LAYOUT_SITES ? sites_set_spins(h, S)
-                                        : samples_set_spins(h, S, walker_at);
+  if (!rc)
+    rc = h->layout == QISG_LAYOUT_LANES   ? lanes_set_spins(h, S)
+         : h->layout == QISG_LAYOUT_SITES ? sites_set_spins(h, S)
+                                          : samples_set_spins(h, S, walker_at, d_S);
+  if (d_S) cudaFree(d_S);
   if (rc) return rc;
   unsigned long long tt = sweep;
   rc = cuda_check(cudaMemcpyAsync(h->d_t, &tt, 8, cudaMemcpyHostToDevice, h->stream), "copy t");

@@ -636,7 +636,8 @@ int samples_materialize(qisg_handle *h);
 int samples_measure(qisg_handle *h, int force_to_q);
 int samples_energies_by_slot(qisg_handle *h);
 int samples_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S);
-int samples_set_spins(qisg_handle *h, const int8_t *S, const int32_t *walker_at);
+int samples_set_spins(qisg_handle *h, const int8_t *S, const int32_t *walker_at, const int8_t *d_S = nullptr);
+int samples_upload_checked(qisg_handle *h, const int8_t *S, int64_t n, int8_t **d_S);
 int samples_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J);
 int samples_set_couplings(qisg_handle *h, const int8_t *J);
 // unpack samples a_lo .. a_lo+n_a-1 by walker into a device int8 buffer

@@ -1996,8 +1996,24 @@ int get_spins_t(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
   return rc;
 }
 
+// Every byte of the staged state is +1 (0x01) or -1 (0xFF); a thread sets
+// *bad when one of its words holds another byte.
+__global__ void pm1_check_kernel(const uint32_t *__restrict__ w, int64_t n_words, int *bad) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  uint32_t any = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_words; i += stride) {
+    const uint32_t v = w[i];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t b = (v >> (8 * k)) & 0xFFu;
+      any |= (uint32_t)(b != 0x01u && b != 0xFFu);
+    }
+  }
+  if (any) atomicOr(bad, 1);
+}
+
 template <typename Word>
-int set_spins_t(qisg_handle *h, const int8_t *S, const int32_t *walker_at) {
+int set_spins_t(qisg_handle *h, const int8_t *S, const int32_t *walker_at, const int8_t *d_S) {
   constexpr int W = (int)sizeof(Word) * 8;
   if (h->perm_pending) {   // the new state replaces the one the masks refer to
     const int rc = clear_masks<Word>(h);
@@ -2005,11 +2021,31 @@ int set_spins_t(qisg_handle *h, const int8_t *S, const int32_t *walker_at) {
     h->perm_pending = false;
   }
   // the walker labels are on the device already (qisg_set_state uploads
-  // them first); the spins go up one word group at a time (all its replicas
-  // in one copy while that stays within 256 MB of staging, else a few
-  // replicas per copy) into a staging buffer and are packed there
+  // them first).  With the state already on the device (d_S) each word
+  // group is packed from there; otherwise the spins go up one word group at
+  // a time (all its replicas in one copy while that stays within 256 MB of
+  // staging, else a few replicas per copy) into a staging buffer and are
+  // packed there
   (void)walker_at;
   const int64_t row = (int64_t)h->n_slots * h->N;   // bytes of one (sample, replica)
+  if (d_S) {
+    int rc = QISG_OK;
+    if ((size_t)h->n_q * 4 > (size_t)h->n_rep)
+      rc = cuda_check(cudaMemsetAsync(h->spins, 0, (size_t)h->n_b * h->n_slots * h->n_q * h->N * 4 * sizeof(Word),
+                                      h->stream),
+                      "memset");
+    for (int64_t b = 0; b < h->n_b && !rc; ++b) {
+      const int n_a = (int)std::min<int64_t>(W, h->n_samples - b * W);
+      const int64_t threads = (int64_t)h->n_rep * row / 4;
+      samples_pack_kernel<Word><<<(unsigned)((threads + 255) / 256), 256, 0, h->stream>>>(
+          reinterpret_cast<Word *>(h->spins), d_S + b * W * h->n_rep * row, h->d_walker, b, 0, h->n_rep, n_a, h->N,
+          h->n_slots, h->n_q, h->n_rep);
+      h->launches++;
+      rc = cuda_check(cudaGetLastError(), "pack spins");
+    }
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+    return rc;
+  }
   const int nr = (int)std::max<int64_t>(1, std::min<int64_t>(h->n_rep, ((int64_t)256 << 20) / ((int64_t)W * row)));
   int8_t *stage = nullptr;
   int rc = cuda_check(cudaMalloc(&stage, (size_t)W * nr * row), "cudaMalloc");
@@ -2225,9 +2261,39 @@ int samples_get_spins(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *S) {
   return h->W == 64 ? get_spins_t<unsigned long long>(h, a_lo, n_a, S)
                     : get_spins_t<unsigned int>(h, a_lo, n_a, S);
 }
-int samples_set_spins(qisg_handle *h, const int8_t *S, const int32_t *walker_at) {
-  return h->W == 64 ? set_spins_t<unsigned long long>(h, S, walker_at)
-                    : set_spins_t<unsigned int>(h, S, walker_at);
+int samples_set_spins(qisg_handle *h, const int8_t *S, const int32_t *walker_at, const int8_t *d_S) {
+  return h->W == 64 ? set_spins_t<unsigned long long>(h, S, walker_at, d_S)
+                    : set_spins_t<unsigned int>(h, S, walker_at, d_S);
+}
+
+// Upload n bytes of +-1 spins to a new device buffer (*d_S, which the caller
+// frees) and check them there: QISG_ECORRUPT (and no buffer) if a byte is
+// neither +1 nor -1.  n is a multiple of 4.
+int samples_upload_checked(qisg_handle *h, const int8_t *S, int64_t n, int8_t **d_S) {
+  *d_S = nullptr;
+  int8_t *buf = nullptr;
+  int rc = cuda_check(cudaMalloc(&buf, (size_t)n + 16), "cudaMalloc");
+  if (rc) return rc;
+  int *bad = reinterpret_cast<int *>(buf + n);   // n is a multiple of 4
+  rc = cuda_check(cudaMemsetAsync(bad, 0, sizeof(int), h->stream), "memset");
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(buf, S, (size_t)n, cudaMemcpyHostToDevice, h->stream), "copy spins");
+  if (!rc) {
+    const int64_t words = n / 4;
+    const unsigned blocks = (unsigned)std::min<int64_t>((words + 255) / 256, (int64_t)8 * std::max(1, h->n_sm) * 8);
+    pm1_check_kernel<<<std::max(1u, blocks), 256, 0, h->stream>>>(reinterpret_cast<const uint32_t *>(buf), words, bad);
+    h->launches++;
+    rc = cuda_check(cudaGetLastError(), "check spins");
+  }
+  int flag = 0;
+  if (!rc) rc = cuda_check(cudaMemcpyAsync(&flag, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "copy flag");
+  if (!rc) rc = cuda_check(cudaStreamSynchronize(h->stream), "sync");
+  if (!rc && flag) rc = fail(QISG_ECORRUPT, "spins must be +-1");
+  if (rc) {
+    cudaFree(buf);
+    return rc;
+  }
+  *d_S = buf;
+  return QISG_OK;
 }
 int samples_get_couplings(qisg_handle *h, int64_t a_lo, int64_t n_a, int8_t *J) {
   return h->W == 64 ? get_couplings_t<unsigned long long>(h, a_lo, n_a, J)
