@@ -201,11 +201,14 @@ int qisg_set_couplings(qisg_handle *h, const int8_t *J);
  * and the sweep counter.  Measurement sums are cleared; energies are
  * recomputed.  Because every draw is a function of the counters, resuming
  * from a saved state is bit-exact with the uninterrupted run.
- * ECORRUPT: a row of walker_at is not a permutation or a spin is not +-1.
- * Packed on the device through a temporary staging buffer (at most 256 MB,
- * or one sample's spins if larger; in the SAMPLES packing one word group's
- * samples of one replica, word_bits * n_slots * N bytes), allocated outside
- * the memory budget and freed before returning.                           */
+ * ECORRUPT: a row of walker_at is not a permutation or a spin is not +-1;
+ * nothing of the handle changes then.  Packed on the device through a
+ * temporary staging buffer, allocated outside the memory budget and freed
+ * before returning: in the SAMPLES packing the whole state when it is at
+ * most 256 MB (one copy, the +-1 check on the device), else up to 256 MB of
+ * one word group's samples at a time (at least one replica's, word_bits *
+ * n_slots * N bytes; the check on the host); in the other packings at most
+ * 256 MB, or one sample's spins if larger.                                 */
 int qisg_set_state(qisg_handle *h, const int8_t *S, const int32_t *walker_at, uint64_t sweep);
 
 /* Test entry: one explicit PT pass (Sec. 2.1) of every chain through the

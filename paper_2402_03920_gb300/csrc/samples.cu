@@ -377,6 +377,15 @@ struct FusedRedArgsT {
 };
 using FusedRedArgs = FusedRedArgsT<uint32_t>;
 
+// Address base + 4 i computed by one 64-bit multiply-add (four is the
+// runtime value 4, so the compiler keeps the multiply-add): measured 1% off
+// the L=16, L_tau=256 sweep against the compiler's own address arithmetic.
+__device__ __forceinline__ uint32_t *addr_mad(const uint32_t *base, uint32_t i, uint32_t four) {
+  unsigned long long a;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(a) : "r"(i), "r"(four), "l"(reinterpret_cast<unsigned long long>(base)));
+  return reinterpret_cast<uint32_t *>(a);
+}
+
 __global__ void __launch_bounds__(kBlock4, 7) samples_red_fused_kernel(const FusedRedArgs p,
                                                                      const __grid_constant__ SlotThresholds th) {
   pdl_begin();
@@ -458,6 +467,7 @@ __global__ void __launch_bounds__(kBlock4, 7) samples_red_fused_kernel(const Fus
     // slot stride
     const uint32_t *ps2 = sb + 2 * SS;
     uint32_t *pd = db;
+    const uint32_t four = p.one << 2;
     // this thread's Philox call of the group (slot 4 g + j); the next
     // group's call is made while this group's slots are updated
     if (live && 6 <= n) r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)j | ((uint32_t)q << 16), ctr_w), p.key);
@@ -472,7 +482,7 @@ __global__ void __launch_bounds__(kBlock4, 7) samples_red_fused_kernel(const Fus
           const int sl = 4 * g + i;
           uint32_t n2[7], fw[7];
 #pragma unroll
-          for (int k = 0; k < 7; ++k) n2[k] = ps2[zo[k]];
+          for (int k = 0; k < 7; ++k) n2[k] = *addr_mad(ps2, zo[k], four);
           const uint32_t m = msk[j][sl];
 #pragma unroll
           for (int k = 0; k < 7; ++k) {   // lanes of m exchange pair (sl, sl + 1)
@@ -498,8 +508,8 @@ __global__ void __launch_bounds__(kBlock4, 7) samples_red_fused_kernel(const Fus
           const uint32_t ut0 = t1 ^ t2;
           const uint32_t ut1 = t1 & t2;
           const uint32_t acc = accept_mask(R, C, us0, us1, us2, ut0, ut1, p.one);
-          pd[zo[0]] = sc ^ acc;
-          pd[zo[1]] = fw[1];
+          *addr_mad(pd, zo[0], four) = sc ^ acc;
+          *addr_mad(pd, zo[1], four) = fw[1];
           ps2 += SS;
           pd += SS;
         }
