@@ -17,6 +17,7 @@
 //   acc    Word [b][r][s]             PT accept masks of the last pass
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "qisg_internal.cuh"
 
@@ -461,61 +462,91 @@ __global__ void __launch_bounds__(kBlock4, 7) samples_red_fused_kernel(const Fus
   const int ql = (int)((threadIdx.x & 31) >> 2);
   int g = 0;
   uint4 r4 = make_uint4(0u, 0u, 0u, 0u);
-  {
-    // groups of four slots that all have two successors: no per-slot checks,
-    // and the bases of slots sl + 2 (loads) and sl (stores) advance by the
-    // slot stride
-    const uint32_t *ps2 = sb + 2 * SS;
-    uint32_t *pd = db;
-    const uint32_t four = p.one << 2;
-    // this thread's Philox call of the group (slot 4 g + j); the next
-    // group's call is made while this group's slots are updated
-    if (live && 6 <= n) r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)j | ((uint32_t)q << 16), ctr_w), p.key);
-    for (; 4 * g + 6 <= n; ++g) {
-      if (live) *reinterpret_cast<uint4 *>(rw + ((j * 8 + ql) << 2)) = r4;
-      __syncwarp();
-      if (live && 4 * (g + 1) + j < n)
-        r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)(4 * (g + 1) + j) | ((uint32_t)q << 16), ctr_w), p.key);
-      if (live) {
-#pragma unroll 2   // two slots' loads in flight: 72 registers, seven blocks per SM
-        for (int i = 0; i < 4; ++i) {
-          const int sl = 4 * g + i;
-          uint32_t n2[7], fw[7];
+  // the bases of slots sl + 2 (loads) and sl (stores) advance by the slot
+  // stride as the slots are taken in order
+  const uint32_t *ps2 = sb + 2 * SS;
+  uint32_t *pd = db;
+  const uint32_t four = p.one << 2;
+  // slot sl = 4 g + i: the words of slot sl after the exchanges of pairs
+  // 0 .. sl, the update of the red site and the stores; H1 / H2: slot sl + 1
+  // / sl + 2 exists (known at compile time, so the slot has no checks)
+  auto update_slot = [&](const int i, const int sl, auto has1, auto has2) {
+    constexpr bool H1 = decltype(has1)::value, H2 = decltype(has2)::value;
+    uint32_t fw[7];
+    if constexpr (H1) {
+      uint32_t n2[7];
+      if constexpr (H2) {
 #pragma unroll
-          for (int k = 0; k < 7; ++k) n2[k] = *addr_mad(ps2, zo[k], four);
-          const uint32_t m = msk[j][sl];
-#pragma unroll
-          for (int k = 0; k < 7; ++k) {   // lanes of m exchange pair (sl, sl + 1)
-            fw[k] = mux(m, n1[k], cw[k]);
-            cw[k] = mux(m, cw[k], n1[k]);
-            n1[k] = n2[k];
-          }
-          const uint32_t R = rw[((i * 8 + ql) << 2) + j];
-          const unsigned long long *C = th.v[sl];
-          const uint32_t sc = fw[0];
-          const uint32_t b1 = sc ^ fw[3] ^ Jxp;
-          const uint32_t b2 = sc ^ fw[4] ^ Jxm;
-          const uint32_t b3 = sc ^ fw[5] ^ Jyp;
-          const uint32_t b4 = sc ^ fw[6] ^ Jym;
-          const uint32_t t1 = sc ^ fw[1] ^ gtp;
-          const uint32_t t2 = sc ^ fw[2] ^ gtm;
-          const uint32_t s1 = b1 ^ b2 ^ b3;
-          const uint32_t c1 = maj3(b1, b2, b3);
-          const uint32_t us0 = s1 ^ b4;
-          const uint32_t c2 = s1 & b4;
-          const uint32_t us1 = c1 ^ c2;
-          const uint32_t us2 = c1 & c2;
-          const uint32_t ut0 = t1 ^ t2;
-          const uint32_t ut1 = t1 & t2;
-          const uint32_t acc = accept_mask(R, C, us0, us1, us2, ut0, ut1, p.one);
-          *addr_mad(pd, zo[0], four) = sc ^ acc;
-          *addr_mad(pd, zo[1], four) = fw[1];
-          ps2 += SS;
-          pd += SS;
-        }
+        for (int k = 0; k < 7; ++k) n2[k] = *addr_mad(ps2, zo[k], four);
       }
-      __syncwarp();
+      const uint32_t m = msk[j][sl];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {   // lanes of m exchange pair (sl, sl + 1)
+        fw[k] = mux(m, n1[k], cw[k]);
+        cw[k] = mux(m, cw[k], n1[k]);
+        if constexpr (H2) n1[k] = n2[k];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) fw[k] = cw[k];
     }
+    const uint32_t R = rw[((i * 8 + ql) << 2) + j];
+    const unsigned long long *C = th.v[sl];
+    const uint32_t sc = fw[0];
+    const uint32_t b1 = sc ^ fw[3] ^ Jxp;
+    const uint32_t b2 = sc ^ fw[4] ^ Jxm;
+    const uint32_t b3 = sc ^ fw[5] ^ Jyp;
+    const uint32_t b4 = sc ^ fw[6] ^ Jym;
+    const uint32_t t1 = sc ^ fw[1] ^ gtp;
+    const uint32_t t2 = sc ^ fw[2] ^ gtm;
+    const uint32_t s1 = b1 ^ b2 ^ b3;
+    const uint32_t c1 = maj3(b1, b2, b3);
+    const uint32_t us0 = s1 ^ b4;
+    const uint32_t c2 = s1 & b4;
+    const uint32_t us1 = c1 ^ c2;
+    const uint32_t us2 = c1 & c2;
+    const uint32_t ut0 = t1 ^ t2;
+    const uint32_t ut1 = t1 & t2;
+    const uint32_t acc = accept_mask(R, C, us0, us1, us2, ut0, ut1, p.one);
+    *addr_mad(pd, zo[0], four) = sc ^ acc;
+    *addr_mad(pd, zo[1], four) = fw[1];
+    ps2 += SS;
+    pd += SS;
+  };
+  const std::integral_constant<bool, true> yes;
+  const std::integral_constant<bool, false> no;
+  // groups of four slots that all have two successors; this thread's Philox
+  // call of the group (slot 4 g + j), the next group's call made while this
+  // group's slots are updated
+  if (live && 6 <= n) r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)j | ((uint32_t)q << 16), ctr_w), p.key);
+  for (; 4 * g + 6 <= n; ++g) {
+    if (live) *reinterpret_cast<uint4 *>(rw + ((j * 8 + ql) << 2)) = r4;
+    __syncwarp();
+    if (live && 4 * (g + 1) + j < n)
+      r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)(4 * (g + 1) + j) | ((uint32_t)q << 16), ctr_w), p.key);
+    if (live) {
+#pragma unroll 2   // two slots' loads in flight: 72 registers, seven blocks per SM
+      for (int i = 0; i < 4; ++i) update_slot(i, 4 * g + i, yes, yes);
+    }
+    __syncwarp();
+  }
+  // a multiple of four slots leaves one group, always of the same shape:
+  // two slots with two successors, one with one, one with none
+  if (n % 4 == 0 && 4 * g < n) {
+    if (live) {
+      if (g == 0)
+        r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)(4 * g + j) | ((uint32_t)q << 16), ctr_w), p.key);
+      *reinterpret_cast<uint4 *>(rw + ((j * 8 + ql) << 2)) = r4;
+    }
+    __syncwarp();
+    if (live) {
+      update_slot(0, 4 * g, yes, yes);
+      update_slot(1, 4 * g + 1, yes, yes);
+      update_slot(2, 4 * g + 2, yes, no);
+      update_slot(3, 4 * g + 3, no, no);
+    }
+    __syncwarp();
+    ++g;
   }
   // the last groups, slot by slot (the first of them has its call made by
   // the loop above when that ran)
