@@ -1214,24 +1214,39 @@ __global__ void __launch_bounds__(kBlock4) samples_overlap4_kernel(const Word *s
 #pragma unroll
   for (int p = 0; p < 6; ++p) c[p].zero();
   const int64_t start = (int64_t)chunk * kBlock4 * sites_per_thread + threadIdx.x;
-  for (int k = 0; k < sites_per_thread; ++k) {
-    const int64_t site = start + (int64_t)k * kBlock4;
-    if (site >= N) break;
-    Word r[4];
-    if constexpr (sizeof(Word) == 4) {
-      const uint4 v = reinterpret_cast<const uint4 *>(w0)[site];
-      r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
-    } else {
-      const ulonglong2 v0 = reinterpret_cast<const ulonglong2 *>(w0)[2 * site];
-      const ulonglong2 v1 = reinterpret_cast<const ulonglong2 *>(w0)[2 * site + 1];
-      r[0] = v0.x; r[1] = v0.y; r[2] = v1.x; r[3] = v1.y;
+  // four sites at a time: per pair, the four difference bits are compressed
+  // to a 3-bit count (a full and two half adders) and added at once
+  for (int k = 0; k < sites_per_thread; k += 4) {
+    Word d[4][6];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t site = start + (int64_t)(k + u) * kBlock4;
+      Word r[4] = {0, 0, 0, 0};
+      if (k + u < sites_per_thread && site < N) {
+        if constexpr (sizeof(Word) == 4) {
+          const uint4 v = reinterpret_cast<const uint4 *>(w0)[site];
+          r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+        } else {
+          const ulonglong2 v0 = reinterpret_cast<const ulonglong2 *>(w0)[2 * site];
+          const ulonglong2 v1 = reinterpret_cast<const ulonglong2 *>(w0)[2 * site + 1];
+          r[0] = v0.x; r[1] = v0.y; r[2] = v1.x; r[3] = v1.y;
+        }
+      }
+      d[u][0] = r[0] ^ r[1];
+      d[u][1] = r[0] ^ r[2];
+      d[u][2] = r[0] ^ r[3];
+      d[u][3] = r[1] ^ r[2];
+      d[u][4] = r[1] ^ r[3];
+      d[u][5] = r[2] ^ r[3];
     }
-    c[0].add1(r[0] ^ r[1]);
-    c[1].add1(r[0] ^ r[2]);
-    c[2].add1(r[0] ^ r[3]);
-    c[3].add1(r[1] ^ r[2]);
-    c[4].add1(r[1] ^ r[3]);
-    c[5].add1(r[2] ^ r[3]);
+#pragma unroll
+    for (int pp = 0; pp < 6; ++pp) {
+      const Word s1 = d[0][pp] ^ d[1][pp] ^ d[2][pp];
+      const Word c1 = maj3(d[0][pp], d[1][pp], d[2][pp]);
+      const Word b0 = s1 ^ d[3][pp];
+      const Word c2 = s1 & d[3][pp];
+      c[pp].add3(b0, c1 ^ c2, c1 & c2);
+    }
   }
   block_sum_counters<K, 3, Word>(c, buf, tot);
   block_sum_counters<K, 3, Word>(c + 3, buf, tot + 3 * W);

@@ -390,3 +390,27 @@ def test_pt_in_blue_pass_wait_bound():
         else:
             assert np.array_equal(a.spins(), b.spins())
             assert np.array_equal(a.permutation(), b.permutation())
+
+
+def test_pt_in_blue_pass_with_pt_every_and_graph_off(qisg):
+    """PT every 3rd sweep (the blue pass runs the chains only on those
+    sweeps), with and without the sweep graph, against the oracle."""
+    L, Lt, n_slots, n_rep, n_samples = 16, 16, 5, 4, 6
+    kw = dict(word_bits=32, layout=qisg.QISG_LAYOUT_SAMPLES, measure_every=4, pt_every=3)
+    a, ladder = make(qisg, L, Lt, 0.2, 0.5, n_slots, 0.9, n_rep, n_samples, 47, **kw)
+    b, _ = make(qisg, L, Lt, 0.2, 0.5, n_slots, 0.9, n_rep, n_samples, 47, **kw)
+    st = oracle_state(ladder, L, Lt, n_rep, 47, 0, n_samples)
+    with a, b:
+        a.set_pt_in_blue(True)
+        b.set_pt_in_blue(True)
+        b.set_graphs(False)
+        for n in (2, 7, 13):
+            a.sweep(n)
+            b.sweep(n)
+            oracle.run(st, n, pt_every=3, measure_every=4)
+            assert_same_state(a, st, what=f"pt_every=3 after {st.t}")
+            assert np.array_equal(a.spins(), b.spins())
+            assert np.array_equal(a.permutation(), b.permutation())
+        sA, sB, sq, sq2, nm = a.measurements()
+        assert nm == st.n_meas
+        assert np.array_equal(sA, st.sumA) and np.array_equal(sq2, st.sumq2)
