@@ -1651,12 +1651,14 @@ int64_t blocks_per_set4(int plane, int n_seg) {
 
 // Segments per column of the blue pass when no tile is pinned: the count
 // that minimises (waves of blocks over the resident ones) x (work of one
-// thread), a thread's work being its walk of up to G sites (about 490
-// instructions a site for its four replica words) plus its part of the
-// block's counter tree (about 32 instructions per counter plane level),
-// with walks of at most max_walk sites.  Counts that leave segments of
-// unequal length are candidates only when a block holds one segment.
-// resident(ks) gives the resident blocks for ks counter planes.
+// block), a block's work being its threads' walks of G sites on average
+// (about 490 instructions a site for the four replica words) plus its
+// counter tree (about 32 instructions per counter plane and level): the
+// pass is latency-bound, so a block takes about the same time whatever the
+// blocks beside it on the SM.  Walks of at most max_walk sites; counts that
+// leave segments of unequal length are candidates only when a block holds
+// one segment.  resident(ks) gives the resident blocks for ks counter
+// planes.
 template <typename Resident>
 int wave_fill_segments(int64_t sets, int plane, int half_col, int max_walk, Resident resident) {
   int best = half_col;
@@ -1668,7 +1670,7 @@ int wave_fill_segments(int64_t sets, int plane, int half_col, int max_walk, Resi
     const int64_t R = std::max<int64_t>(1, resident(ks));
     const int64_t blocks = sets * blocks_per_set4(plane, ns);
     const int64_t waves = (blocks + R - 1) / R;
-    const double cost = (double)waves * (490.0 * gmax + 32.0 * (2 * ks + 13));
+    const double cost = (double)waves * (490.0 * half_col / ns + 32.0 * (2 * ks + 13));
     if (best_cost < 0.0 || cost < best_cost) {
       best_cost = cost;
       best = ns;
