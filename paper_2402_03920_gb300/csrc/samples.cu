@@ -378,6 +378,15 @@ struct FusedRedArgsT {
 };
 using FusedRedArgs = FusedRedArgsT<uint32_t>;
 
+// Address base + i elements of `bytes` bytes (the runtime element size) by
+// one 64-bit multiply-add.
+template <typename T>
+__device__ __forceinline__ T *addr_scaled(T *base, uint32_t i, uint32_t bytes) {
+  unsigned long long a;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(a) : "r"(i), "r"(bytes), "l"(reinterpret_cast<unsigned long long>(base)));
+  return reinterpret_cast<T *>(a);
+}
+
 // Address base + 4 i computed by one 64-bit multiply-add (four is the
 // runtime value 4, so the compiler keeps the multiply-add): measured 1% off
 // the L=16, L_tau=256 sweep against the compiler's own address arithmetic.
@@ -718,7 +727,12 @@ __device__ __forceinline__ void red_fusedq_body(const FusedRedArgsT<Word> &p, co
       for (int k = 0; k < 7; ++k) ld_rp<Word, RP, CG>(n1[k], sb + SS + zo[k]);
   }
   uint4 R4 = make_uint4(0, 0, 0, 0);
-  for (int sl = 0; sl < n; ++sl) {
+  const uint32_t wbytes = p.one * (uint32_t)sizeof(Word);   // the runtime element size (addr_scaled)
+  // slot sl: its draws, the words of slot sl after the exchanges of pairs
+  // 0 .. sl, the update of the red site and the stores; H1 / H2: slot sl + 1
+  // / sl + 2 exists (known at compile time, so the slot has no checks)
+  auto step = [&](const int sl, auto has1, auto has2) {
+    constexpr bool H1 = decltype(has1)::value, H2 = decltype(has2)::value;
     const int i = sl % TPS;   // thread i of the site holds slot sl's call
     if (i == 0) {
       const int sm = sl + h;
@@ -742,14 +756,14 @@ __device__ __forceinline__ void red_fusedq_body(const FusedRedArgsT<Word> &p, co
       const uint32_t v3 = __shfl_sync(0xffffffffu, R4.w, lane0 + i);
       Rj[0] = h == 0 ? v0 : h == 1 ? v1 : h == 2 ? v2 : v3;
     }
-    if (!live) continue;
+    if (!live) return;
     Word fw[7][RP];
-    if (sl + 1 < n) {
+    if constexpr (H1) {
       Word n2[7][RP];
-      if (sl + 2 < n) {
+      if constexpr (H2) {
         const Word *ps = sb + (int64_t)(sl + 2) * SS;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) ld_rp<Word, RP, CG>(n2[k], ps + zo[k]);
+        for (int k = 0; k < 7; ++k) ld_rp<Word, RP, CG>(n2[k], addr_scaled(ps, zo[k], wbytes));
       }
       Word m[RP];
 #pragma unroll
@@ -757,11 +771,10 @@ __device__ __forceinline__ void red_fusedq_body(const FusedRedArgsT<Word> &p, co
 #pragma unroll
       for (int k = 0; k < 7; ++k)
 #pragma unroll
-        for (int jj = 0; jj < RP; ++jj) {
-          const Word xx = (cw[k][jj] ^ n1[k][jj]) & m[jj];
-          fw[k][jj] = cw[k][jj] ^ xx;
-          cw[k][jj] = n1[k][jj] ^ xx;
-          if (sl + 2 < n) n1[k][jj] = n2[k][jj];
+        for (int jj = 0; jj < RP; ++jj) {   // lanes of m exchange pair (sl, sl + 1)
+          fw[k][jj] = mux(m[jj], n1[k][jj], cw[k][jj]);
+          cw[k][jj] = mux(m[jj], cw[k][jj], n1[k][jj]);
+          if constexpr (H2) n1[k][jj] = n2[k][jj];
         }
     } else {
 #pragma unroll
@@ -791,9 +804,15 @@ __device__ __forceinline__ void red_fusedq_body(const FusedRedArgsT<Word> &p, co
       out[jj] = sc ^ accept_word<Word>(Rj[jj], C, us0, us1, us2, ut0, ut1, p.one);
     }
     Word *pd = db + (int64_t)sl * SS;
-    st_rp<Word, RP>(pd + zo[0], out);
-    st_rp<Word, RP>(pd + zo[1], fw[1]);
-  }
+    st_rp<Word, RP>(addr_scaled(pd, zo[0], wbytes), out);
+    st_rp<Word, RP>(addr_scaled(pd, zo[1], wbytes), fw[1]);
+  };
+  const std::integral_constant<bool, true> yes;
+  const std::integral_constant<bool, false> no;
+  int sl = 0;
+  for (; sl + 2 < n; ++sl) step(sl, yes, yes);   // slots with two successors
+  if (sl + 1 < n) step(sl++, yes, no);
+  if (sl < n) step(sl, no, no);
 }
 
 template <typename Word, int RP>
