@@ -412,12 +412,6 @@ __global__ void __launch_bounds__(kBlock4, 7) samples_red_fused_kernel(const Fus
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_zero_U; i += stride) p.zero_U[i] = 0;
     if (p.ticket && blockIdx.x == 0 && threadIdx.x == 0) *p.ticket = 0u;
   }
-  for (int i = threadIdx.x; i < 4 * kMaxSlotsPT; i += blockDim.x) {
-    const int jj = i / kMaxSlotsPT, sl = i - jj * kMaxSlotsPT;
-    const int rr = 4 * q + jj;
-    msk[jj][sl] = (rr < p.n_rep && sl + 1 < n) ? p.acc[((int64_t)b * p.n_rep + rr) * n + sl] : 0u;
-  }
-  __syncthreads();
 
   const uint32_t tid = chunk * (uint32_t)kBlock4 + threadIdx.x;
   const int j = (int)(tid & 3u);
@@ -528,6 +522,14 @@ __global__ void __launch_bounds__(kBlock4, 7) samples_red_fused_kernel(const Fus
   // call of the group (slot 4 g + j), the next group's call made while this
   // group's slots are updated
   if (live && 6 <= n) r4 = philox(make_uint4(z[0], (uint32_t)t, (uint32_t)j | ((uint32_t)q << 16), ctr_w), p.key);
+  // the PT masks of the (b, q) set, staged after the first slots' loads and
+  // draw are issued, so the two round trips to L2 overlap
+  for (int i = threadIdx.x; i < 4 * kMaxSlotsPT; i += blockDim.x) {
+    const int jj = i / kMaxSlotsPT, sl = i - jj * kMaxSlotsPT;
+    const int rr = 4 * q + jj;
+    msk[jj][sl] = (rr < p.n_rep && sl + 1 < n) ? p.acc[((int64_t)b * p.n_rep + rr) * n + sl] : 0u;
+  }
+  __syncthreads();
   for (; 4 * g + 6 <= n; ++g) {
     if (live) *reinterpret_cast<uint4 *>(rw + ((j * 8 + ql) << 2)) = r4;
     __syncwarp();
@@ -671,12 +673,6 @@ __device__ __forceinline__ void red_fusedq_body(const FusedRedArgsT<Word> &p, co
   const int q = (int)(set - b * (uint32_t)p.n_q);
   const int n = p.n_slots;
   __syncthreads();   // msk of the previous (virtual) block is no longer read
-  for (int i = threadIdx.x; i < 4 * kMaxSlotsPT; i += blockDim.x) {
-    const int sl = i >> 2, jj = i & 3;
-    const int rr = 4 * q + jj;
-    msk[sl][jj] = (rr < p.n_rep && sl + 1 < n) ? ld_g<CG>(p.acc + ((int64_t)b * p.n_rep + rr) * n + sl) : Word(0);
-  }
-  __syncthreads();
 
   const uint32_t tid = chunk * (uint32_t)kBlock4 + threadIdx.x;
   const int h = (int)(tid % TPS);                 // which replica group of the site
@@ -726,6 +722,14 @@ __device__ __forceinline__ void red_fusedq_body(const FusedRedArgsT<Word> &p, co
 #pragma unroll
       for (int k = 0; k < 7; ++k) ld_rp<Word, RP, CG>(n1[k], sb + SS + zo[k]);
   }
+  // the PT masks of the (b, q) set, staged after the first slots' loads are
+  // issued, so the two round trips to L2 overlap
+  for (int i = threadIdx.x; i < 4 * kMaxSlotsPT; i += blockDim.x) {
+    const int sl = i >> 2, jj = i & 3;
+    const int rr = 4 * q + jj;
+    msk[sl][jj] = (rr < p.n_rep && sl + 1 < n) ? ld_g<CG>(p.acc + ((int64_t)b * p.n_rep + rr) * n + sl) : Word(0);
+  }
+  __syncthreads();
   uint4 R4 = make_uint4(0, 0, 0, 0);
   const uint32_t wbytes = p.one * (uint32_t)sizeof(Word);   // the runtime element size (addr_scaled)
   // slot sl: its draws, the words of slot sl after the exchanges of pairs
