@@ -948,40 +948,41 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
     cur.xm = ld_g<CG>(pxm + off);
     cur.yp = ld_g<CG>(pyp + off);
     cur.ym = ld_g<CG>(pym + off);
-    // the draws of the walk's next site are made while this one is updated,
-    // so the Philox chain overlaps independent work
     uint4 R4 = philox(make_uint4((uint32_t)i2 + off, (uint32_t)t, ctr_z, ctr_w), p.key);
-    // with the prefetch, two steps per iteration, so the current and next
-    // sites' words swap registers instead of being copied (not in the
-    // persistent kernel, whose register bound would make the unrolled walk
-    // spill)
-#pragma unroll((PF && !CG) ? 2 : 1)
-    for (int k = 0; k < G; ++k) {
+    // the even site's post-flip counts, held until the odd site's are added
+    // with them (the prefetching walk of the per-pass launch)
+    uint32_t h0[4], h1[4], h2[4], g0[4], g1[4];
+    // site k of the walk, its words in cu; with the prefetch the next site's
+    // words go to nx while this one is updated, else to cu after it.  PH: 0
+    // hold this site's counts, 1 add them with the held ones, 2 add them
+    auto site = [&](int k, Quad4 &cu, Quad4 &nx, auto phase) {
+      constexpr int PH = decltype(phase)::value;
       const uint32_t tau = tau0 + 2u * (uint32_t)k;
+      // the draws of the walk's next site are made while this one is
+      // updated, so the Philox chain overlaps independent work
       uint4 R4n = R4;
       if (k + 1 < G) R4n = philox(make_uint4((uint32_t)i2 + off + 2 * P, (uint32_t)t, ctr_z, ctr_w), p.key);
-      auto load_next = [&](Quad4 &nx) {
+      auto load_next = [&](Quad4 &q) {
         const uint32_t offn = off + 2 * P;
-        nx.c = ld_g<CG>(pc + offn);
-        nx.up = ld_g<CG>(pc + (size_t)(tau + 3 == Lt ? 0u : offn + P));
-        nx.xp = ld_g<CG>(pxp + offn);
-        nx.xm = ld_g<CG>(pxm + offn);
-        nx.yp = ld_g<CG>(pyp + offn);
-        nx.ym = ld_g<CG>(pym + offn);
+        q.c = ld_g<CG>(pc + offn);
+        q.up = ld_g<CG>(pc + (size_t)(tau + 3 == Lt ? 0u : offn + P));
+        q.xp = ld_g<CG>(pxp + offn);
+        q.xm = ld_g<CG>(pxm + offn);
+        q.yp = ld_g<CG>(pyp + offn);
+        q.ym = ld_g<CG>(pym + offn);
       };
-      Quad4 nxt;
-      if (PF && k + 1 < G) load_next(nxt);
+      if (PF && k + 1 < G) load_next(nx);
       // the antiperiodic wrap bond is unsatisfied when its spins agree
       const uint32_t gtp = ones_if<uint32_t>(p.tau_ap && tau + 1 == Lt), gtm = ones_if<uint32_t>(p.tau_ap && tau == 0);
       uint32_t f[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const uint32_t sc = q4(cur.c, j);
-        const uint32_t b1 = sc ^ q4(cur.xp, j) ^ Jxp;
-        const uint32_t b2 = sc ^ q4(cur.xm, j) ^ Jxm;
-        const uint32_t b3 = sc ^ q4(cur.yp, j) ^ Jyp;
-        const uint32_t b4 = sc ^ q4(cur.ym, j) ^ Jym;
-        const uint32_t t1 = sc ^ q4(cur.up, j) ^ gtp;
+        const uint32_t sc = q4(cu.c, j);
+        const uint32_t b1 = sc ^ q4(cu.xp, j) ^ Jxp;
+        const uint32_t b2 = sc ^ q4(cu.xm, j) ^ Jxm;
+        const uint32_t b3 = sc ^ q4(cu.yp, j) ^ Jyp;
+        const uint32_t b4 = sc ^ q4(cu.ym, j) ^ Jym;
+        const uint32_t t1 = sc ^ q4(cu.up, j) ^ gtp;
         const uint32_t t2 = sc ^ q4(dn, j) ^ gtm;
         const uint32_t s1 = b1 ^ b2 ^ b3;
         const uint32_t c1 = maj3(b1, b2, b3);
@@ -991,28 +992,59 @@ __device__ __forceinline__ void sweep4_body(const SamplesArgs<uint32_t> &p, cons
         const uint32_t us2 = c1 & c2;
         const uint32_t ut0 = t1 ^ t2;
         const uint32_t ut1 = t1 & t2;
-        const uint32_t R = q4(R4, j);
-        const uint32_t flip = count_only ? 0u : accept_mask(R, C, us0, us1, us2, ut0, ut1, p.one);
+        const uint32_t flip = count_only ? 0u : accept_mask(q4(R4, j), C, us0, us1, us2, ut0, ut1, p.one);
         f[j] = flip;
         if (BLUE) {
           // unsatisfied counts after the flip: u -> 4 - u (spatial), 2 - u (tau)
           const uint32_t vs1 = us1 ^ (flip & us0);
           const uint32_t vs2 = mux(flip, ~(us0 | us1 | us2), us2);
           const uint32_t vt1 = mux(flip, ~(ut0 | ut1), ut1);
-          cs[j].add3(us0, vs1, vs2);
-          ct[j].add2(ut0, vt1);
+          if constexpr (PH == 0) {
+            h0[j] = us0;
+            h1[j] = vs1;
+            h2[j] = vs2;
+            g0[j] = ut0;
+            g1[j] = vt1;
+          } else if constexpr (PH == 1) {
+            cs[j].add3x2(h0[j], h1[j], h2[j], us0, vs1, vs2);
+            ct[j].add2x2(g0[j], g1[j], ut0, vt1);
+          } else {
+            cs[j].add3(us0, vs1, vs2);
+            ct[j].add2(ut0, vt1);
+          }
         }
       }
-      if (!count_only) wc[off] = make_uint4(cur.c.x ^ f[0], cur.c.y ^ f[1], cur.c.z ^ f[2], cur.c.w ^ f[3]);
+      if (!count_only) wc[off] = make_uint4(cu.c.x ^ f[0], cu.c.y ^ f[1], cu.c.z ^ f[2], cu.c.w ^ f[3]);
       R4 = R4n;
-      if (k + 1 < G) {
-        dn = cur.up;
-        if (PF)
-          cur = nxt;
-        else
-          load_next(cur);
-        off += 2 * P;
+      dn = cu.up;
+      if (!PF && k + 1 < G) load_next(nx);
+      off += 2 * P;
+    };
+    using Hold = std::integral_constant<int, 0>;
+    using Pair = std::integral_constant<int, 1>;
+    using One = std::integral_constant<int, 2>;
+    if constexpr (BLUE && PF && !CG) {
+      // two sites per iteration: the current and next sites' words swap
+      // registers instead of being copied, and their counts enter the
+      // counters together (not in the persistent kernel, whose register
+      // bound would make this walk spill)
+      Quad4 nxt;
+      int k = 0;
+      for (; k + 1 < G; k += 2) {
+        site(k, cur, nxt, Hold{});
+        site(k + 1, nxt, cur, Pair{});
       }
+      if (k < G) site(k, cur, nxt, One{});
+    } else if constexpr (PF) {
+      Quad4 nxt;
+#pragma unroll 1
+      for (int k = 0; k < G; ++k) {
+        site(k, cur, nxt, One{});
+        if (k + 1 < G) cur = nxt;
+      }
+    } else {
+#pragma unroll 1
+      for (int k = 0; k < G; ++k) site(k, cur, cur, One{});
     }
   }
 
@@ -1641,6 +1673,15 @@ void fill_thresholds(const qisg_handle *h, SlotThresholds &th) {
     }
 }
 
+// Blocks per SM the blue kernel's registers are bounded to: MINB when the
+// caller asks (variant 2), three for the prefetching walk up to 7 counter
+// planes (168 registers without spills; 7 planes would otherwise take two
+// blocks), none beyond (the bound would spill).
+template <bool PF, int MINB, int KS>
+constexpr int blue_min_blocks() {
+  return MINB > 0 ? MINB : (PF && KS <= 7) ? 3 : 0;
+}
+
 // Blocks of the W = 32 blue kernel (variant 0 or 2, ks = 3 .. 9 counter
 // planes) resident on one SM, cached in the handle.
 int blue_blocks_per_sm(qisg_handle *h, int ks, int variant) {
@@ -1651,7 +1692,8 @@ int blue_blocks_per_sm(qisg_handle *h, int ks, int variant) {
   const void *fn = nullptr;
 #define QISG_OCC(n)                                                                                   \
   case n:                                                                                             \
-    fn = v ? (const void *)samples_sweep4_kernel<true, n, false, 4> : (const void *)samples_sweep4_kernel<true, n, true>; \
+    fn = v ? (const void *)samples_sweep4_kernel<true, n, false, 4>                                   \
+           : (const void *)samples_sweep4_kernel<true, n, true, blue_min_blocks<true, 0, n>()>;         \
     break;
   switch (ks) { QISG_OCC(3) QISG_OCC(4) QISG_OCC(5) QISG_OCC(6) QISG_OCC(7) QISG_OCC(8) default: QISG_OCC(9) }
 #undef QISG_OCC
@@ -1760,13 +1802,13 @@ void launch_sweep4(bool pdl, const SamplesArgs<uint32_t> &p, const SlotThreshold
     switch (counter_planes(p.seg_sites)) {   // walks of at most 64 sites: 3 .. 9 planes
 #define QISG_CASE(n)                                                                                         \
   case n:                                                                                                    \
-    launch_kernel(pdl, samples_sweep4_kernel<true, n, PF, MINB>, dim3(blocks), dim3(kBlock4), 0, st, p, th,  \
-                  colour, count_only, f);                                                                    \
+    launch_kernel(pdl, samples_sweep4_kernel<true, n, PF, blue_min_blocks<PF, MINB, n>()>, dim3(blocks),      \
+                  dim3(kBlock4), 0, st, p, th, colour, count_only, f);                                       \
     break;
       QISG_CASE(3) QISG_CASE(4) QISG_CASE(5) QISG_CASE(6) QISG_CASE(7) QISG_CASE(8)
       default:
-        launch_kernel(pdl, samples_sweep4_kernel<true, 9, PF, MINB>, dim3(blocks), dim3(kBlock4), 0, st, p, th,
-                      colour, count_only, f);
+        launch_kernel(pdl, samples_sweep4_kernel<true, 9, PF, blue_min_blocks<PF, MINB, 9>()>, dim3(blocks),
+                      dim3(kBlock4), 0, st, p, th, colour, count_only, f);
         break;
 #undef QISG_CASE
     }
