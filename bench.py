@@ -158,7 +158,7 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
-OVERLAP = True   # programmatic dependent launch of the batched form's kernels
+OVERLAP = False   # programmatic dependent launch of the batched form's kernels (the library default: off)
 
 
 def make_instance(qisg, w, form, seed):
@@ -171,8 +171,8 @@ def make_instance(qisg, w, form, seed):
         cfg = qisg.Config(w.L, w.L_tau, ladder, w.n_replicas, w.n_samples, seed, word_bits=0,
                           measure_every=w.measure_every, layout=batched_layout(qisg))
     inst = qisg.Instance(cfg)
-    if form != "per_instance" and not OVERLAP:
-        inst.set_launch_overlap(False)
+    if form != "per_instance":
+        inst.set_launch_overlap(OVERLAP)
     return inst
 
 
@@ -691,7 +691,7 @@ def overlap_entry(torch, qisg, steps, warmup, seed):
         OVERLAP = on
         total_ms, _, _, _, _ = time_form(torch, qisg, w, "batched", steps, warmup, seed)
         out["on" if on else "off"] = total_ms * 1e9 / (updates_per_step(w) * steps)
-    OVERLAP = True
+    OVERLAP = False
     out["unit"] = UNIT
     return out
 

@@ -541,7 +541,9 @@ struct qisg_handle {
   // launch per run of sweeps between measurements
   bool persistent = false;
   // SAMPLES sweep-path kernels launched with programmatic dependent launch
-  bool pdl = true;
+  // (off by default: with the sweep replayed from a CUDA graph the device-side
+  // wait cost more than the launch gaps it hid)
+  bool pdl = false;
   unsigned *d_bar = nullptr;        // grid barrier of the persistent kernel
   long long wait_ns = 5000000000ll; // bound of each barrier wait
   cudaStream_t stream = nullptr;
