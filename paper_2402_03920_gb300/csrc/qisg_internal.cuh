@@ -105,9 +105,15 @@ struct PTConst {
 // alpha = exp(+-(k_s - k_{s+1})) and beta = exp(+-(k_tau,s - k_tau,s+1))
 // chosen by the signs of m and n, u = x 2^-32 with x the pair's Philox word.
 //
-// The decision is the one of that exact rule; two shortcuts only skip work:
+// The decision is the one of that exact rule; three shortcuts only skip
+// work:
 //  * when both chosen factors are at least 1 (base >= 1 or exponent 0),
 //    P >= 1 > u: products and squares of numbers >= 1 round to numbers >= 1;
+//  * when both are at most 1 (m dk <= 0 and n dkt <= 0) and one of them has
+//    m dk or n dkt <= -23.5, P <= e^-23.5 (1 + 5e-7) < 6.3e-11 < 2^-32 <= u
+//    for x > 0: products and squares of numbers <= 1 stay <= 1, so no size
+//    of the exponents can overflow (far candidates of a long ladder, whose
+//    exponents pass the range below, land here);
 //  * otherwise ln u (lnu, within 2e-5) is compared in float with
 //    lnP = m dk + n dkt, whose float evaluation is within
 //    (|m dk| + |n dkt|) 2.4e-7 of the double value; the exact power chain
@@ -194,26 +200,61 @@ __device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua
   // energies of the original occupant of slot s+1 (the Y of pair s)
   const ET y_us = E::shfl(us, (lane + 1) & 31);
   const ET y_ut = E::shfl(ut, (lane + 1) & 31);
+  // The decisions of pair s against candidate i <= s form a triangle,
+  // enumerated row by row (f = s (s+1)/2 + i) and taken 32 at a time, one
+  // per lane: ceil(n_p (n_p+1) / 64) rounds of independent work for n_p
+  // pairs instead of n_p dependent steps of one lane per pair.  Lane r keeps
+  // round r's ballots of accepted and of open candidates; row s is then the
+  // bits f = s (s+1)/2 .. s (s+1)/2 + s of their concatenation.
+  const int n_p = n_slots - 1;
+  const int n_tri = n_p * (n_p + 1) / 2;
+  uint32_t Mb = 0, Ob = 0;
+#pragma unroll 4   // rounds overlap (16 slots: four rounds)
+  for (int r0 = 0; r0 * 32 < n_tri; ++r0) {
+    const int f = r0 * 32 + lane;
+    int s = (int)((sqrtf(8.f * (float)f + 1.f) - 1.f) * 0.5f);
+    s += (s + 1) * (s + 2) / 2 <= f ? 1 : 0;   // float rounding guards
+    s -= s * (s + 1) / 2 > f ? 1 : 0;
+    const bool take = f < n_tri;
+    const int sp = take ? s : 0, ci = take ? f - s * (s + 1) / 2 : 0;
+    const ET x_us = E::shfl(us, ci);
+    const ET x_ut = E::shfl(ut, ci);
+    const ET yu = E::shfl(y_us, sp);
+    const ET yt = E::shfl(y_ut, sp);
+    const uint32_t gs = __shfl_sync(0xffffffffu, g, sp), xs = __shfl_sync(0xffffffffu, x, sp);
+    const float dks = __shfl_sync(0xffffffffu, dk, sp), dkts = __shfl_sync(0xffffffffu, dkt, sp);
+    const float lnus = __shfl_sync(0xffffffffu, lnu, sp);
+    const auto m = E::diff2(x_us, yu);   // A_Y - A_X, A = 2N - 2 us
+    const auto n = E::diff2(x_ut, yt);   // B_Y - B_X, B = N - 2 ut
+    // both chosen factors >= 1 (base >= 1 or exponent 0): P >= 1 > u
+    const bool ge = (m == 0 || ((gs >> (m > 0 ? 0 : 1)) & 1u)) && (n == 0 || ((gs >> (n > 0 ? 2 : 3)) & 1u));
+    const float la = (float)m * dks, lb = (float)n * dkts;
+    const bool ok = xs != 0u && fabsf(la) < 700.f && fabsf(lb) < 700.f;
+    const float d = lnus - (la + lb);
+    const float err = 1e-4f + (fabsf(la) + fabsf(lb)) * 4.8e-7f;
+    const bool lo = ok && d < -err;
+    // both chosen factors at most 1 (their squarings and products stay at
+    // most 1, so nothing overflows) and one of them below e^-23.5: the exact
+    // product is below 6.3e-11 < 2^-32 <= u for every x > 0, whatever the
+    // size of the exponents
+    const bool tiny = xs != 0u && la <= 0.f && lb <= 0.f && fminf(la, lb) <= -23.5f;
+    const bool und = !ge && !lo && !tiny && !(ok && d > err);
+    const uint32_t ma = __ballot_sync(0xffffffffu, take && (ge || lo));
+    const uint32_t mo = __ballot_sync(0xffffffffu, take && und);
+    if (lane == r0) {
+      Mb = ma;
+      Ob = mo;
+    }
+  }
   uint32_t D = 0, open = 0;
-  for (int i = 0; i + 1 < n_slots; ++i) {
-    const ET x_us = E::shfl(us, i);
-    const ET x_ut = E::shfl(ut, i);
-    if (has_pair && i <= lane) {
-      const auto m = E::diff2(x_us, y_us);   // A_Y - A_X, A = 2N - 2 us
-      const auto n = E::diff2(x_ut, y_ut);   // B_Y - B_X, B = N - 2 ut
-      // both chosen factors >= 1 (base >= 1 or exponent 0): P >= 1 > u
-      bool acc = (m == 0 || ((g >> (m > 0 ? 0 : 1)) & 1u)) && (n == 0 || ((g >> (n > 0 ? 2 : 3)) & 1u));
-      bool und = false;
-      if (!acc) {
-        const float la = (float)m * dk, lb = (float)n * dkt;
-        const bool ok = x != 0u && fabsf(la) < 700.f && fabsf(lb) < 700.f;
-        const float d = lnu - (la + lb);
-        const float err = 1e-4f + (fabsf(la) + fabsf(lb)) * 4.8e-7f;
-        acc = ok && d < -err;
-        und = !acc && !(ok && d > err);
-      }
-      D |= (uint32_t)acc << i;
-      open |= (uint32_t)und << i;
+  {
+    const int f0 = lane * (lane + 1) / 2, k = f0 >> 5;
+    const uint32_t a0 = __shfl_sync(0xffffffffu, Mb, k & 31), a1 = __shfl_sync(0xffffffffu, Mb, (k + 1) & 31);
+    const uint32_t o0 = __shfl_sync(0xffffffffu, Ob, k & 31), o1 = __shfl_sync(0xffffffffu, Ob, (k + 1) & 31);
+    const uint32_t row = lane >= 31 ? 0xffffffffu : (2u << lane) - 1u;   // bits 0 .. lane
+    if (has_pair) {
+      D = __funnelshift_r(a0, a1, f0 & 31) & row;
+      open = __funnelshift_r(o0, o1, f0 & 31) & row;
     }
   }
   while (open) {   // exact rule for the candidates left open (rare)
@@ -225,16 +266,23 @@ __device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua
     if (pt_exact(sq, lane, m >= 0 ? 0 : 1, n >= 0 ? 2 : 3, m, n, x)) D |= 1u << i;
   }
   __syncwarp();
+  // the scan in runs of eight pairs: a run's decision words first (shuffles
+  // that do not wait on the carried candidate), then its steps in registers
   uint32_t acc = 0;
   int c = 0, mine = lane;   // carried candidate; final occupant of this lane's slot
-  for (int s2 = 0; s2 + 1 < n_slots; ++s2) {
-    const uint32_t Ds = __shfl_sync(0xffffffffu, D, s2);
-    const bool ex = (Ds >> c) & 1u;
-    if (lane == s2) mine = ex ? s2 + 1 : c;
-    if (ex)
-      acc |= 1u << s2;
-    else
-      c = s2 + 1;
+  for (int s0 = 0; s0 < n_p; s0 += 8) {
+    uint32_t Dv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) Dv[k] = __shfl_sync(0xffffffffu, D, (s0 + k) & 31);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int s2 = s0 + k;
+      const bool live = s2 < n_p;
+      const bool ex = live && ((Dv[k] >> c) & 1u);
+      if (live && lane == s2) mine = ex ? s2 + 1 : c;
+      acc |= (uint32_t)ex << (s2 & 31);
+      if (live && !ex) c = s2 + 1;
+    }
   }
   if (lane == n_slots - 1) mine = c;
   const int f_w = __shfl_sync(0xffffffffu, w, mine);
