@@ -209,41 +209,52 @@ __device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua
   const int n_p = n_slots - 1;
   const int n_tri = n_p * (n_p + 1) / 2;
   uint32_t Mb = 0, Ob = 0;
-#pragma unroll 4   // rounds overlap (16 slots: four rounds)
-  for (int r0 = 0; r0 * 32 < n_tri; ++r0) {
-    const int f = r0 * 32 + lane;
-    int s = (int)((sqrtf(8.f * (float)f + 1.f) - 1.f) * 0.5f);
-    s += (s + 1) * (s + 2) / 2 <= f ? 1 : 0;   // float rounding guards
-    s -= s * (s + 1) / 2 > f ? 1 : 0;
-    const bool take = f < n_tri;
-    const int sp = take ? s : 0, ci = take ? f - s * (s + 1) / 2 : 0;
-    const ET x_us = E::shfl(us, ci);
-    const ET x_ut = E::shfl(ut, ci);
-    const ET yu = E::shfl(y_us, sp);
-    const ET yt = E::shfl(y_ut, sp);
-    const uint32_t gs = __shfl_sync(0xffffffffu, g, sp), xs = __shfl_sync(0xffffffffu, x, sp);
-    const float dks = __shfl_sync(0xffffffffu, dk, sp), dkts = __shfl_sync(0xffffffffu, dkt, sp);
-    const float lnus = __shfl_sync(0xffffffffu, lnu, sp);
-    const auto m = E::diff2(x_us, yu);   // A_Y - A_X, A = 2N - 2 us
-    const auto n = E::diff2(x_ut, yt);   // B_Y - B_X, B = N - 2 ut
-    // both chosen factors >= 1 (base >= 1 or exponent 0): P >= 1 > u
-    const bool ge = (m == 0 || ((gs >> (m > 0 ? 0 : 1)) & 1u)) && (n == 0 || ((gs >> (n > 0 ? 2 : 3)) & 1u));
-    const float la = (float)m * dks, lb = (float)n * dkts;
-    const bool ok = xs != 0u && fabsf(la) < 700.f && fabsf(lb) < 700.f;
-    const float d = lnus - (la + lb);
-    const float err = 1e-4f + (fabsf(la) + fabsf(lb)) * 4.8e-7f;
-    const bool lo = ok && d < -err;
-    // both chosen factors at most 1 (their squarings and products stay at
-    // most 1, so nothing overflows) and one of them below e^-23.5: the exact
-    // product is below 6.3e-11 < 2^-32 <= u for every x > 0, whatever the
-    // size of the exponents
-    const bool tiny = xs != 0u && la <= 0.f && lb <= 0.f && fminf(la, lb) <= -23.5f;
-    const bool und = !ge && !lo && !tiny && !(ok && d > err);
-    const uint32_t ma = __ballot_sync(0xffffffffu, take && (ge || lo));
-    const uint32_t mo = __ballot_sync(0xffffffffu, take && und);
-    if (lane == r0) {
-      Mb = ma;
-      Ob = mo;
+  for (int r0 = 0; r0 * 32 < n_tri; r0 += 4) {
+    // four rounds at a time: every operand gathered first, then the
+    // decisions, so the shuffles' latencies overlap (the row of f from the
+    // inverse of f = s (s+1)/2 in float, corrected by one either way)
+    ET xu[4], xt[4], yu[4], yt[4];
+    uint32_t gs[4], xs[4];
+    float dks[4], dkts[4], lnus[4];
+    bool take[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int f = (r0 + k) * 32 + lane;
+      const float q = 8.f * (float)f + 1.f;
+      int s = (int)((q * rsqrtf(q) - 1.f) * 0.5f);
+      s += (s + 1) * (s + 2) / 2 <= f ? 1 : 0;   // rounding guards
+      s -= s * (s + 1) / 2 > f ? 1 : 0;
+      take[k] = f < n_tri;
+      const int sp = take[k] ? s : 0, ci = take[k] ? f - s * (s + 1) / 2 : 0;
+      xu[k] = E::shfl(us, ci);
+      xt[k] = E::shfl(ut, ci);
+      yu[k] = E::shfl(y_us, sp);
+      yt[k] = E::shfl(y_ut, sp);
+      gs[k] = __shfl_sync(0xffffffffu, g, sp);
+      xs[k] = __shfl_sync(0xffffffffu, x, sp);
+      dks[k] = __shfl_sync(0xffffffffu, dk, sp);
+      dkts[k] = __shfl_sync(0xffffffffu, dkt, sp);
+      lnus[k] = __shfl_sync(0xffffffffu, lnu, sp);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const auto m = E::diff2(xu[k], yu[k]);
+      const auto n = E::diff2(xt[k], yt[k]);
+      const bool ge =
+          (m == 0 || ((gs[k] >> (m > 0 ? 0 : 1)) & 1u)) && (n == 0 || ((gs[k] >> (n > 0 ? 2 : 3)) & 1u));
+      const float la = (float)m * dks[k], lb = (float)n * dkts[k];
+      const bool ok = xs[k] != 0u && fabsf(la) < 700.f && fabsf(lb) < 700.f;
+      const float d = lnus[k] - (la + lb);
+      const float err = 1e-4f + (fabsf(la) + fabsf(lb)) * 4.8e-7f;
+      const bool lo = ok && d < -err;
+      const bool tiny = xs[k] != 0u && la <= 0.f && lb <= 0.f && fminf(la, lb) <= -23.5f;
+      const bool und = !ge && !lo && !tiny && !(ok && d > err);
+      const uint32_t ma = __ballot_sync(0xffffffffu, take[k] && (ge || lo));
+      const uint32_t mo = __ballot_sync(0xffffffffu, take[k] && und);
+      if (lane == r0 + k) {
+        Mb = ma;
+        Ob = mo;
+      }
     }
   }
   uint32_t D = 0, open = 0;
