@@ -158,7 +158,7 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
-OVERLAP = False   # programmatic dependent launch of the batched form's kernels (the library default: off)
+OVERLAP = True   # programmatic dependent launch of the batched form's kernels (the library default)
 
 
 def make_instance(qisg, w, form, seed):
@@ -691,7 +691,7 @@ def overlap_entry(torch, qisg, steps, warmup, seed):
         OVERLAP = on
         total_ms, _, _, _, _ = time_form(torch, qisg, w, "batched", steps, warmup, seed)
         out["on" if on else "off"] = total_ms * 1e9 / (updates_per_step(w) * steps)
-    OVERLAP = False
+    OVERLAP = True
     out["unit"] = UNIT
     return out
 

@@ -315,12 +315,11 @@ __device__ __forceinline__ uint32_t pt_chain(int32_t *wa, unsigned long long *Ua
 // while the kernel before it on the stream is finishing; it must call
 // pdl_begin() before it touches global memory that kernel writes (the wait
 // returns once that kernel has completed and its writes are visible; with
-// no such dependency it returns at once).  pdl_begin then lets the next
-// kernel on the stream be scheduled as this one's blocks retire.
-__device__ __forceinline__ void pdl_begin() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// no such dependency it returns at once).  No kernel triggers its
+// dependents early: the trigger is each block's exit, so the next kernel is
+// launched as the last blocks leave instead of taking SM room while this
+// one still runs (the early trigger made the sweep slower than no overlap).
+__device__ __forceinline__ void pdl_begin() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 cudaError_t launch_kernel(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
@@ -600,9 +599,7 @@ struct qisg_handle {
   // launch per run of sweeps between measurements
   bool persistent = false;
   // SAMPLES sweep-path kernels launched with programmatic dependent launch
-  // (off by default: with the sweep replayed from a CUDA graph the device-side
-  // wait cost more than the launch gaps it hid)
-  bool pdl = false;
+  bool pdl = true;
   unsigned *d_bar = nullptr;        // grid barrier of the persistent kernel
   long long wait_ns = 5000000000ll; // bound of each barrier wait
   cudaStream_t stream = nullptr;

@@ -320,7 +320,7 @@ def test_edge_cases_bit_exact(qisg, W, L, Lt, n_slots, n_rep, n_samples, pt_ever
 
 @pytest.mark.parametrize("W", [32, 64])
 def test_launch_overlap_keeps_trajectory(qisg, W):
-    """Programmatic dependent launch on and off (the default), graphs on and
+    """Programmatic dependent launch on (the default) and off, graphs on and
     off: one trajectory, measurements included, and the oracle's."""
     kw = dict(layout=qisg.QISG_LAYOUT_SAMPLES, word_bits=W, measure_every=3)
     a, ladder = make(qisg, 6, 8, 0.2, 0.5, 9, 1.0, 5, 40, 8, **kw)
