@@ -139,9 +139,10 @@ static __device__ __noinline__ bool pt_exact(const double *sq, int s, int ia, in
 // and that pair's Philox word.  In the sequential pass the configuration
 // that meets the original occupant of slot s+1 at pair s is always one of
 // the original occupants of slots 0..s (carried up by accepted exchanges).
-// So lane s first decides pair s against every candidate i = 0..s (bit i of
-// D: accept), with the shortcuts above and the exact rule for the few
-// candidates the shortcuts leave open; the pass is then a uniform scan of
+// So pair s is first decided against every candidate i = 0..s (lane s ends
+// with bit i of D: accept; the decisions themselves are spread over the
+// lanes), with the shortcuts above and the exact rule, in lane s, for the
+// few candidates the shortcuts leave open; the pass is then a uniform scan of
 // bit lookups: with c carried, pair s accepts iff bit c of D_s; the slot then
 // ends with s+1's configuration and c moves on, else it ends with c and s+1
 // is carried.  The decisions are those of the textbook pass.
